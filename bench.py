@@ -1,0 +1,467 @@
+#!/usr/bin/env python3
+"""ChFSI filter benchmark on one GB300 (or N replicas under torchrun).
+
+One step = one pass of the hot path over the resident synthetic workload:
+  Lanczos bounds (20 steps)  ->  FP64 Chebyshev filter (CSR, degree m)
+  ->  CholQR2 + Rayleigh-Ritz (projection, eigensolve, rotation).
+Default workload: 40^3 grid, w = 3 (19,248,832 nnz), 1024 states, m = 20.
+
+Prints ONE JSON line (rank 0).  `value` is the step's algorithmic GFLOP/s
+(Lanczos + filter + closure GEMMs; the n x n eigensolve is not counted), with the
+per-phase numbers, the roofline of the dominant kernel (the fused FP64 CSR step,
+bound by the DFMA pipe), the oracle's CPU time on a bounded sample, an end-to-end
+number through the public API with host buffers, and the SM clocks seen.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import chfsi_workloads as W  # noqa: E402
+
+METRIC = "ChFSI filter GFLOP/s & % of roofline, FP64 vs mixed precision at stated error"
+# FP64 DFMA pipe of the whole GPU, measured with a register-resident FMA loop
+# (152 SMs x 8 independent chains x 2048 iterations, CUDA events): 1.194-1.201
+# TFLOP/s.  The nominal figure is 1.25 TFLOP/s.
+FP64_PEAK_GFLOPS = 1200.0
+# FP32 FFMA pipe, same method: 74.8-75.1 TFLOP/s.
+FP32_PEAK_GFLOPS = 75000.0
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="g40_w3_n1024_m20")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--cpu-cols", type=int, default=64)
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------- FLOP model (algorithmic)
+
+
+def filter_flops(nnz, N, n, m):
+    """2 nnz n per product; the first step adds 3 N n (shift, scale), later steps 5 N n."""
+    return m * 2.0 * nnz * n + 3.0 * N * n + (m - 1) * 5.0 * N * n
+
+
+def lanczos_flops(nnz, N, k):
+    f = 0.0
+    for j in range(k):
+        f += 2.0 * nnz + 2 * N + 4 * N + 2.0 * N * (j + 1) * 2 + 2 * N + N
+    return f
+
+
+def closure_flops(nnz, N, n, passes):
+    """Gram N n^2 and triangular solve N n^2 per CholQR pass, H X_F (2 nnz n),
+    projection 2 N n^2, rotation 2 N n^2 (eigensolve not counted)."""
+    return passes * 2.0 * N * n * n + 2.0 * nnz * n + 2.0 * N * n * n + 2.0 * N * n * n
+
+
+# ---------------------------------------------------------------- clocks
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append(parts)
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        sm = [float(r[1]) for r in rows if _isnum(r[1])]
+        smax = [float(r[2]) for r in rows if _isnum(r[2])]
+        power = [float(r[3]) for r in rows if _isnum(r[3])]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        load = [x for x, p in zip(sm, power)] if sm else []
+        return {"sm_mhz": float(np.median(load)) if load else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None,
+                "samples": len(rows), "reasons": reasons}
+
+
+def _isnum(s):
+    try:
+        float(s)
+        return True
+    except ValueError:
+        return False
+
+
+# ---------------------------------------------------------------- traffic from the committed ncu summary
+
+
+def _kernel_source_sha():
+    p = os.path.join(ROOT, "paper_2110_15853_gb300", "csrc", "filter_csr.cu")
+    return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
+
+
+def committed_traffic(workload):
+    """dram bytes per launch of the FP64 CSR step from profiles/, if the kernel
+    source is unchanged since the capture; else None."""
+    path = os.path.join(ROOT, "profiles", f"csr_step_f64_{workload}.md")
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    m1 = re.search(r"source_sha256_16:\s*([0-9a-f]+)", text)
+    m2 = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    if not m1 or not m2 or m1.group(1) != _kernel_source_sha():
+        return None
+    return float(m2.group(1))
+
+
+# ---------------------------------------------------------------- workload setup
+
+
+def setup_workload(name):
+    wl = W.workload(name)
+    H = W.csr_grid(wl.g, wl.w, wl.s, wl.seed, core_frac=wl.core_frac, core_shift=wl.core_shift)
+    X = W.start_block(H["N"], wl.n, wl.seed)
+    v0 = W.lanczos_start(H["N"], wl.seed)
+    return wl, H, X, v0
+
+
+def cpu_baseline(H, X, v0, wl, ncols, m):
+    """The oracle as it stands on a bounded sample: all m filter steps on `ncols`
+    of the n columns at full N (columns are independent)."""
+    import oracle
+    oracle.build()
+    a, b, a0 = oracle.lanczos_bounds(H, v0, 20, wl.n)
+    cols = W.column_subset(wl.n, ncols, wl.seed)
+    Xs = np.ascontiguousarray(X[:, cols])
+    t0 = time.perf_counter()
+    oracle.filter(H, Xs, m, a, b, a0)
+    dt = time.perf_counter() - t0
+    fl = filter_flops(H["nnz"], H["N"], ncols, m)
+    return {"value": fl / dt / 1e9, "unit": "GFLOP/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"FP64 filter, all {m} steps, {ncols} of {wl.n} columns at full N={H['N']} "
+                      f"({dt:.1f} s; filter only, closure not sampled)",
+            "seconds": dt}
+
+
+# ---------------------------------------------------------------- reference arm (the oracle)
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    wl, H, X, v0 = setup_workload(args.workload)
+    import oracle
+    oracle.build()
+    a, b, a0 = oracle.lanczos_bounds(H, v0, 20, wl.n)
+    ncols = args.cpu_cols
+    cols = W.column_subset(wl.n, ncols, wl.seed)
+    Xs = np.ascontiguousarray(X[:, cols])
+    for _ in range(args.warmup):
+        oracle.filter(H, Xs, 1, a, b, a0)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.filter(H, Xs, wl.m, a, b, a0)
+        times.append(time.perf_counter() - t0)
+    fl = filter_flops(H["nnz"], H["N"], ncols, wl.m)
+    t = float(np.median(times))
+    val = fl / t / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": "GFLOP/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": wl.name, "N": H["N"], "n": wl.n, "m": wl.m, "nnz": H["nnz"], "layout": "csr",
+                   "parallelism": "replicas"},
+        "cpu_baseline": {"value": val, "unit": "GFLOP/s", "cores": oracle.num_threads(), "kind": "oracle",
+                         "sample": f"FP64 oracle filter, all {wl.m} steps on {ncols} of {wl.n} columns, full N "
+                                   f"(warm-up steps use m=1)"},
+        "e2e": {"value": val, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------- our arm
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    import paper_2110_15853_gb300 as P
+    from paper_2110_15853_gb300 import build as pbuild
+    if rank == 0 or world == 1:
+        pbuild.build()
+    if world > 1:
+        dist.barrier()
+    lib = P.load()
+
+    wl, H, X, v0 = setup_workload(args.workload)
+    N, n, m, nnz = H["N"], wl.n, wl.m, H["nnz"]
+    Hd = P.CsrMatrix.from_arrays(H["row_ptr"], H["col"], H["val"], device=dev)
+    Xd = torch.as_tensor(X).to(dev)
+    v0d = torch.as_tensor(v0).to(dev)
+    Yd = torch.empty_like(Xd)
+    psi = torch.empty_like(Xd)
+    ritz = torch.empty(n, dtype=torch.float64, device=dev)
+    wsl, wsf, wsr = P.Workspace(dev), P.Workspace(dev), P.Workspace(dev)
+    wsf.get(P.filter_workspace_bytes(Hd, n, m))
+    wsr.get(P.rayleigh_ritz_workspace_bytes(Hd, n, 2))
+    stream = torch.cuda.current_stream(dev)
+
+    def step(ev=None):
+        if ev:
+            ev[0].record(stream)
+        a, b, a0 = P.lanczos_bounds(Hd, v0d, 20, n, workspace=wsl)
+        if ev:
+            ev[1].record(stream)
+        P.filter(Hd, Xd, m, a, b, a0, out=Yd, workspace=wsf)
+        if ev:
+            ev[2].record(stream)
+        P.rayleigh_ritz(Hd, Yd, 2, psi=psi, ritz=ritz, workspace=wsr)
+        if ev:
+            ev[3].record(stream)
+        return a, b, a0
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+
+    flops_l = lanczos_flops(nnz, N, 20)
+    flops_f = filter_flops(nnz, N, n, m)
+    flops_c = closure_flops(nnz, N, n, 2)
+    step_flops = flops_l + flops_f + flops_c
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    launches0 = lib.chfsi_kernel_launches()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for k in range(args.steps):
+        bounds = step(evs[k])
+    t_end.record(stream)
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    launches = lib.chfsi_kernel_launches() - launches0
+    clk = clocks.stop()
+    total_ms = t_start.elapsed_time(t_end)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_step = total_ms / args.steps
+    lan_ms = float(np.median([e[0].elapsed_time(e[1]) for e in evs]))
+    fil_ms = float(np.median([e[1].elapsed_time(e[2]) for e in evs]))
+    rr_ms = float(np.median([e[2].elapsed_time(e[3]) for e in evs]))
+    value = step_flops * world / (ms_step * 1e-3) / 1e9
+
+    # roofline of the dominant kernel: the fused FP64 CSR step (m launches per filter)
+    launch_ms = fil_ms / m
+    per_launch_flops = flops_f / m
+    achieved = per_launch_flops / (launch_ms * 1e-3) / 1e9
+    traffic = committed_traffic(wl.name)
+    roofline = {"bound": "alu", "pipe": "fp64 dfma", "achieved": achieved, "peak": FP64_PEAK_GFLOPS,
+                "unit": "GFLOP/s", "frac": achieved / FP64_PEAK_GFLOPS, "traffic": traffic,
+                "kernel": "csr_step_kernel<double> (fused SpMM + recurrence)",
+                "peak_source": "measured FP64 FMA loop on this GB300 (not in MEASURED_PEAKS.json)",
+                "hbm_bytes_algorithmic": 24.0 * N * n + 12.0 * nnz + 8.0 * (N + 1)}
+
+    # end to end through the public API with host buffers
+    Xh = torch.empty((N, n), dtype=torch.float64).pin_memory()
+    Xh.copy_(torch.as_tensor(X))
+    v0h = torch.as_tensor(v0).pin_memory()
+    psih = torch.empty((N, n), dtype=torch.float64).pin_memory()
+    ritzh = torch.empty(n, dtype=torch.float64).pin_memory()
+
+    def e2e_step():
+        Xd.copy_(Xh, non_blocking=True)
+        v0d.copy_(v0h, non_blocking=True)
+        step()
+        psih.copy_(psi, non_blocking=True)
+        ritzh.copy_(ritz, non_blocking=True)
+
+    e2e_step()
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    e2e_ms = e0.elapsed_time(e1) / args.steps
+    e2e = {"value": step_flops * world / (e2e_ms * 1e-3) / 1e9, "unit": "GFLOP/s", "ms_per_step": e2e_ms,
+           "h2d_bytes_per_step": int(Xh.numel() * 8 + v0h.numel() * 8),
+           "d2h_bytes_per_step": int(psih.numel() * 8 + ritzh.numel() * 8)}
+
+    variants = {}
+    if not args.no_variants and rank == 0:
+        variants = measure_variants(P, torch, dev, stream, wl, H, Hd, Xd, bounds)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(H, X, v0, wl, args.cpu_cols, m)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl.name, "grid": f"{wl.g}^3", "w": wl.w, "N": N, "n": n, "m": m, "nnz": nnz,
+                       "layout": "csr", "step": "lanczos(20) + filter(m, FP64) + CholQR2 + Rayleigh-Ritz",
+                       "l2": "inputs larger than L2 (each N x n block is %.0f MB)" % (N * n * 8 / 1e6),
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "phases": {"lanczos_ms": lan_ms, "filter_ms": fil_ms, "closure_ms": rr_ms,
+                       "filter_gflops": flops_f / (fil_ms * 1e-3) / 1e9,
+                       "closure_gflops": flops_c / (rr_ms * 1e-3) / 1e9,
+                       "step_gflop": step_flops / 1e9},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "clocks": clk,
+            "gpu_launches": int(launches),
+            "variants": variants,
+        }
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def measure_variants(P, torch, dev, stream, wl, H, Hd, Xd, bounds):
+    """Filter-only timings of the other layouts / schedules on the same workload
+    (outside the main timed region), each with its error against the FP64 CSR run."""
+    a, b, a0 = bounds
+    N, n, m, nnz = H["N"], wl.n, wl.m, H["nnz"]
+    out = {}
+
+    def timeit(fn, reps=2):
+        fn()
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1) / reps
+
+    fl = filter_flops(nnz, N, n, m)
+    Yref = torch.empty_like(Xd)
+    ws = P.Workspace(dev)
+    t = timeit(lambda: P.filter(Hd, Xd, m, a, b, a0, out=Yref, workspace=ws))
+    out["filter_csr_f64"] = {"ms": t, "gflops": fl / (t * 1e-3) / 1e9}
+    rr_ws = P.Workspace(dev)
+    theta_ref, _ = P.rayleigh_ritz(Hd, Yref, 2, workspace=rr_ws)
+    theta_ref = theta_ref.cpu().numpy()
+
+    for low, L in (("f32", m - 4), ("bf16", m - 4)):
+        Ym = torch.empty_like(Xd)
+        sched = P.mixed_schedule(m, L, low)
+        try:
+            t = timeit(lambda: P.filter(Hd, Xd, m, a, b, a0, schedule=sched, out=Ym, workspace=ws))
+        except P.ChfsiError as e:
+            out[f"filter_csr_{low}x{L}_f64x{m - L}"] = {"error": str(e)}
+            continue
+        th, _ = P.rayleigh_ritz(Hd, Ym, 2, workspace=rr_ws)
+        rel = float(np.max(np.abs(th.cpu().numpy() - theta_ref)) / np.max(np.abs(theta_ref)))
+        yerr = float(torch.linalg.norm(Ym - Yref) / torch.linalg.norm(Yref))
+        out[f"filter_csr_{low}x{L}_f64x{m - L}"] = {
+            "ms": t, "gflops": fl / (t * 1e-3) / 1e9, "speedup_vs_f64": out["filter_csr_f64"]["ms"] / t,
+            "ritz_max_rel_err_vs_f64": rel, "y_rel_fro_err_vs_f64": yerr}
+        del Ym
+    # BSR layout of the same operator
+    try:
+        B = W.bsr_from_csr(H, wl.g)
+        Bd = P.BsrMatrix.from_arrays(B["brow_ptr"], B["bcol"], B["val"], device=dev)
+        perm = torch.as_tensor(B["perm"]).to(dev)
+        Xp = Xd[perm].contiguous()
+        Yb = torch.empty_like(Xp)
+        t = timeit(lambda: P.filter(Bd, Xp, m, a, b, a0, out=Yb, workspace=ws), reps=1)
+        Yback = torch.empty_like(Yb)
+        Yback[perm] = Yb
+        err = float(torch.linalg.norm(Yback - Yref) / torch.linalg.norm(Yref))
+        out["filter_bsr_f64"] = {"ms": t, "gflops": fl / (t * 1e-3) / 1e9,
+                                 "executed_gflop": m * 2.0 * B["n_blocks"] * 64 * 64 * n / 1e9,
+                                 "y_rel_fro_err_vs_csr": err}
+        del Bd, Xp, Yb, Yback
+    except Exception as e:  # noqa: BLE001 - report, do not hide
+        out["filter_bsr_f64"] = {"error": repr(e)}
+    return out
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

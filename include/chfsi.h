@@ -1,0 +1,228 @@
+/*
+ * chfsi.h -- C ABI of the GB300 (sm_103a) Chebyshev-filtered subspace iteration library.
+ *
+ * The library implements the filter and closure of ChFSI as given in Algorithm 1
+ * (Sec. 3.4) of "GPU acceleration of the Tucker-tensor based Kohn-Sham DFT"
+ * (arXiv 2110.15853): the degree-m scaled Chebyshev filter (step 1), the
+ * orthonormalisation (step 2), the subspace projection (step 3), the dense
+ * eigensolve (step 4) and the rotation (step 5), plus the spectral bounds the
+ * algorithm takes as input and the reverse-mode derivative of the filter.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Matrix and vector pointers are DEVICE pointers owned by the caller; the
+ *   library never frees or retains them.  Dense blocks (X, Y, Psi, dY, dX) are
+ *   row-major N x n_cols with an explicit leading dimension ld >= n_cols
+ *   (element (i, j) at p[i * ld + j]); each block must start on a 16-byte boundary.
+ *   An output block must not overlap any input.
+ * - Scalars a, b, a0 are the paper's eps_ub^w (upper bound of the wanted
+ *   spectrum), eps_ub^uw (upper bound of the unwanted spectrum) and eps_0 (lower
+ *   bound of the wanted spectrum).  a0 < a < b is required (if a0 lies in [a, b]
+ *   the scaled Chebyshev value T_m(tau) can vanish and the sigma recurrence
+ *   divides by zero).
+ * - Work is queued on `stream` (a cudaStream_t; NULL = the legacy default
+ *   stream) and returns before it finishes, unless stated otherwise.  Scratch
+ *   comes from the caller's workspace `ws` of `ws_bytes` bytes (256-byte aligned),
+ *   sized by the matching *_workspace_size call; nothing is allocated on these
+ *   paths.  The first 256 bytes of every workspace hold a device status word that
+ *   kernels set when they meet a non-finite value, an out-of-range column index or
+ *   a non-positive Cholesky pivot; chfsi_read_status() synchronises the stream and
+ *   returns it.
+ * - Every call returns an int status (CHFSI_OK = 0 or a CHFSI_ERR_* code below);
+ *   argument errors are detected on the host before anything is queued.
+ * - Calls that share a workspace must not overlap on the GPU.
+ */
+#ifndef CHFSI_H
+#define CHFSI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ status codes */
+#define CHFSI_OK 0
+#define CHFSI_ERR_ARG 1         /* bad pointer, size, leading dimension or alignment      */
+#define CHFSI_ERR_BOUNDS 2      /* not a0 < a < b, or a bound is not finite              */
+#define CHFSI_ERR_PATTERN 3     /* bad CSR/BSR pattern (device found a column out of range) */
+#define CHFSI_ERR_CHOL 4        /* Gram matrix not positive definite (Cholesky pivot <= 0) */
+#define CHFSI_ERR_NONFINITE 5   /* a kernel produced or read a NaN / Inf                 */
+#define CHFSI_ERR_CUDA 6        /* a CUDA runtime or cuSOLVER call failed                */
+#define CHFSI_ERR_TIMEOUT 7     /* a bounded device wait gave up                         */
+#define CHFSI_ERR_NOMEM 8       /* workspace smaller than the *_workspace_size answer    */
+#define CHFSI_ERR_UNSUPPORTED 9 /* combination not implemented (e.g. a precision on BSR) */
+
+/* Text for a status code (static storage, never NULL). */
+const char* chfsi_status_string(int status);
+
+/* Library version as major*10000 + minor*100 + patch. */
+int chfsi_version(void);
+
+/* ------------------------------------------------------------------ operator H */
+#define CHFSI_CSR 0
+#define CHFSI_BSR 1
+
+/*
+ * Sparse symmetric H (the projected Kohn-Sham Hamiltonian H^L of Sec. 3.3,
+ * Eq. "localized standard ks problem") in CSR: row_ptr[n_rows + 1] (int64,
+ * row_ptr[0] = 0, non-decreasing, row_ptr[n_rows] = nnz), col[nnz] (int32 in
+ * [0, n_rows)), val[nnz] (double).  The filter never assumes symmetry; the
+ * backward pass uses H in place of H^T and so requires it (pattern and values).
+ */
+typedef struct {
+    int64_t n_rows;
+    int64_t nnz;
+    const int64_t* row_ptr;
+    const int32_t* col;
+    const double* val;
+} chfsi_csr;
+
+/*
+ * Blocked CSR with dense bdim x bdim blocks (bdim = 64: 4 x 4 x 4 sub-cubes of
+ * the tensor-index grid).  brow_ptr[n_block_rows + 1] (int32), bcol[n_blocks]
+ * (int32 block column), val[n_blocks * bdim * bdim] (double, each block row-major).
+ * Rows of X and Y are in the same blocked order as H's rows.
+ */
+typedef struct {
+    int64_t n_block_rows;
+    int64_t n_blocks;
+    int32_t bdim;
+    const int32_t* brow_ptr;
+    const int32_t* bcol;
+    const double* val;
+} chfsi_bsr;
+
+typedef struct {
+    int32_t kind;      /* CHFSI_CSR or CHFSI_BSR */
+    chfsi_csr csr;
+    chfsi_bsr bsr;
+} chfsi_matrix;
+
+/* ------------------------------------------------------------------ precision schedule */
+#define CHFSI_F64 0           /* FP64 storage and FP64 arithmetic                      */
+#define CHFSI_F32 1           /* FP32 storage, FP32 FMA, FP64-computed coefficients    */
+#define CHFSI_BF16_F32ACC 2   /* BF16 copy of Y_k as the product operand, FP32 accumulate,
+                                 FP32 storage of the iterates                           */
+
+/*
+ * Per-step precision of the filter: step_prec[k-1] is the precision of the step
+ * that produces Y_k (k = 1..m).  Low-precision steps must form a prefix; once a
+ * step is CHFSI_F64 all later steps must be too (the last steps run in FP64 and
+ * the two iterates carried across the switch are widened exactly).
+ * A NULL schedule (or step_prec == NULL) means every step in FP64.
+ */
+typedef struct {
+    int32_t m;
+    const int32_t* step_prec;
+} chfsi_schedule;
+
+/* ------------------------------------------------------------------ filter (Algorithm 1, step 1) */
+
+/* Bytes of workspace chfsi_filter needs for this operator, n_cols, m and schedule. */
+int chfsi_filter_workspace_size(const chfsi_matrix* H, int64_t n_cols, int32_t m,
+                                const chfsi_schedule* sched, size_t* bytes);
+
+/*
+ * Y = Y_m, the scaled Chebyshev filter of Algorithm 1 step 1 (Sec. 3.4):
+ *   e = (b - a)/2, c = (b + a)/2, sigma_1 = e/(a0 - c), gamma = 2/sigma_1,
+ *   Y_1 = (sigma_1/e)(H X - c X),
+ *   Y_{k+1} = (2 sigma_{k+1}/e)(H Y_k - c Y_k) - sigma_k sigma_{k+1} Y_{k-1},
+ *   sigma_{k+1} = 1/(gamma - sigma_k),
+ * returning the newest iterate Y_m (the paper's X~ after the loop).
+ * X: N x n_cols (ldx), read only.  Y: N x n_cols (ldy), written.  m >= 1.
+ * sched: NULL for all-FP64, else a schedule with sched->m == m.
+ * Errors: CHFSI_ERR_ARG, CHFSI_ERR_BOUNDS, CHFSI_ERR_NOMEM, CHFSI_ERR_UNSUPPORTED,
+ * CHFSI_ERR_CUDA (launch failure).  Device-side findings (non-finite output,
+ * column out of range) go to the workspace status word.
+ */
+int chfsi_filter(const chfsi_matrix* H, const double* X, int64_t ldx, double* Y, int64_t ldy,
+                 int64_t n_cols, int32_t m, double a, double b, double a0,
+                 const chfsi_schedule* sched, void* ws, size_t ws_bytes, void* stream);
+
+/* ------------------------------------------------------------------ adjoint of the filter */
+
+int chfsi_filter_backward_workspace_size(const chfsi_matrix* H, int64_t n_cols, int32_t m,
+                                         int32_t ckpt_stride, size_t* bytes);
+
+/*
+ * Reverse-mode derivative of chfsi_filter (all-FP64 schedule) for a loss L with
+ * dL/dY_m = dY.  Writing the filter as Y_1 = alpha_1 (H - c) Y_0 and
+ * Y_k = alpha_k (H - c) Y_{k-1} - beta_k Y_{k-2} (alpha_1 = sigma_1/e,
+ * alpha_k = 2 sigma_k/e, beta_k = sigma_{k-1} sigma_k, Y_0 = X):
+ *   Ybar_m = dY,  Ybar_{k-1} = alpha_k (H - c) Ybar_k - beta_{k+1} Ybar_{k+1},
+ *   dX = Ybar_0,
+ *   dH_val[p] = sum_{k=1..m} alpha_k <Ybar_k[row p, :], Y_{k-1}[col p, :]>
+ * for every stored entry p of H (the unconstrained per-entry gradient).  Uses H
+ * for H^T (H must be symmetric; the paper's Eq. "transpose_equal" is the same
+ * fact).  Forward iterates are kept only every ckpt_stride steps (as pairs
+ * Y_{s-1}, Y_s; 0 selects ceil(sqrt(m))) and the rest are recomputed per segment.
+ * dH_val may be NULL (then only dX).  CSR operators only.
+ */
+int chfsi_filter_backward(const chfsi_matrix* H, const double* X, int64_t ldx,
+                          const double* dY, int64_t lddy, double* dX, int64_t lddx,
+                          double* dH_val, int64_t n_cols, int32_t m, double a, double b,
+                          double a0, int32_t ckpt_stride, void* ws, size_t ws_bytes,
+                          void* stream);
+
+/* ------------------------------------------------------------------ closure (Algorithm 1, steps 2-5) */
+
+int chfsi_rayleigh_ritz_workspace_size(const chfsi_matrix* H, int64_t n_cols,
+                                       int32_t cholqr_passes, size_t* bytes);
+
+/*
+ * Steps 2-5 of Algorithm 1 in FP64 on the GPU:
+ *   2. X_F = Orth(Y) by Cholesky-QR: S = Y^T Y, S = R^T R, X_F = Y R^-1
+ *      (cholqr_passes = 2 repeats it on X_F: CholQR2);
+ *   3. H_F = X_F^T (H X_F);
+ *   4. H_F Q = Q Lambda (ascending eigenvalues);
+ *   5. Psi = X_F Q.
+ * Y: N x n_cols (ldy), read only.  Psi: N x n_cols (ldpsi), written.
+ * ritz: device array of n_cols doubles, written ascending.  n_cols <= N.
+ * Synchronises `stream` before returning (it reads the Cholesky and eigensolver
+ * status); returns CHFSI_ERR_CHOL if a pivot was not positive, CHFSI_ERR_CUDA if
+ * the eigensolver failed.
+ */
+int chfsi_rayleigh_ritz(const chfsi_matrix* H, const double* Y, int64_t ldy, int64_t n_cols,
+                        double* Psi, int64_t ldpsi, double* ritz, int32_t cholqr_passes,
+                        void* ws, size_t ws_bytes, void* stream);
+
+/* ------------------------------------------------------------------ spectral bounds */
+
+int chfsi_lanczos_workspace_size(const chfsi_matrix* H, int32_t steps, size_t* bytes);
+
+/*
+ * The bounds (a, b, a0) = (eps_ub^w, eps_ub^uw, eps_0) that Algorithm 1 takes as
+ * input (Sec. 3.4 does not say how they are found).  k = min(steps, N) steps of
+ * Lanczos with full re-orthogonalisation from the start vector v0 (N doubles on
+ * the device, need not be normalised; the caller draws it), then
+ *   a0 = smallest eigenvalue of the tridiagonal T_k,
+ *   b  = largest eigenvalue of T_k + |beta_k| (residual norm),
+ *   a  = a0 + (b - a0) (n_wanted / N)^(2/3).
+ * Breakdown (beta_j <= 1e-12 times the largest |alpha_i| + beta_{i-1} so far)
+ * stops early with a zero residual.  a, b, a0 are HOST pointers; the call
+ * synchronises `stream`.  1 <= n_wanted < N.
+ */
+int chfsi_lanczos_bounds(const chfsi_matrix* H, int32_t steps, const double* v0,
+                         int64_t n_wanted, double* a, double* b, double* a0, void* ws,
+                         size_t ws_bytes, void* stream);
+
+/* ------------------------------------------------------------------ utilities */
+
+/* Synchronise `stream` and return the workspace status word as a CHFSI_* code
+ * (CHFSI_OK if clean); clears the word.  */
+int chfsi_read_status(void* ws, void* stream);
+
+/* Clear the workspace status word (queued on `stream`). */
+int chfsi_clear_status(void* ws, void* stream);
+
+/* Number of kernels this library has launched in this process (all devices, all
+ * threads; library calls such as the cuSOLVER eigensolver are not counted).
+ * Diagnostics only: the paper has no counterpart. */
+unsigned long long chfsi_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CHFSI_H */

@@ -1,0 +1,281 @@
+"""Thin PyTorch binding of the chfsi C ABI (argument marshalling only).
+
+Torch provides device memory and streams; every step of the filter, the
+closure, the bounds and the adjoint runs in libchfsi.so kernels.  The binding
+names follow the C entry points:
+
+    filter(H, X, m, a, b, a0, schedule=None)            -> Y_m       (Algorithm 1, step 1)
+    filter_backward(H, X, dY, m, a, b, a0, ...)         -> dX, dH     (reverse mode of step 1)
+    rayleigh_ritz(H, Y, cholqr_passes=2)                -> ritz, Psi  (Algorithm 1, steps 2-5)
+    lanczos_bounds(H, v0, steps, n_wanted)              -> a, b, a0   (bounds Algorithm 1 takes)
+    ChebyshevFilter.apply(X, h_val, H, m, a, b, a0)     -> Y_m with autograd into X and h_val
+
+a = eps_ub^w (upper bound of the wanted spectrum), b = eps_ub^uw (upper bound of
+the unwanted spectrum), a0 = eps_0 (lower bound of the wanted spectrum).
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass, field
+from typing import Optional, Sequence
+
+import numpy as np
+import torch
+
+from . import _abi
+from ._abi import (CHFSI_BF16_F32ACC, CHFSI_BSR, CHFSI_CSR, CHFSI_F32, CHFSI_F64, ChfsiError, check, load)
+
+PRECISIONS = {"f64": CHFSI_F64, "f32": CHFSI_F32, "bf16": CHFSI_BF16_F32ACC}
+
+
+def _ptr(t: Optional[torch.Tensor]) -> Optional[int]:
+    return None if t is None else t.data_ptr()
+
+
+def _stream_handle(device: torch.device) -> int:
+    return torch.cuda.current_stream(device).cuda_stream
+
+
+@dataclass
+class CsrMatrix:
+    """CSR operator resident on the device (row_ptr int64, col int32, val float64)."""
+    row_ptr: torch.Tensor
+    col: torch.Tensor
+    val: torch.Tensor
+    n_rows: int
+
+    @classmethod
+    def from_arrays(cls, row_ptr, col, val, device="cuda") -> "CsrMatrix":
+        rp = torch.as_tensor(np.ascontiguousarray(row_ptr, dtype=np.int64)).to(device)
+        cl = torch.as_tensor(np.ascontiguousarray(col, dtype=np.int32)).to(device)
+        vl = torch.as_tensor(np.ascontiguousarray(val, dtype=np.float64)).to(device)
+        return cls(rp, cl, vl, int(rp.shape[0] - 1))
+
+    @property
+    def nnz(self) -> int:
+        return int(self.col.shape[0])
+
+    @property
+    def device(self) -> torch.device:
+        return self.val.device
+
+    def descriptor(self, val: Optional[torch.Tensor] = None) -> _abi.chfsi_matrix:
+        v = self.val if val is None else val
+        m = _abi.chfsi_matrix()
+        m.kind = CHFSI_CSR
+        m.csr = _abi.chfsi_csr(self.n_rows, self.nnz, _ptr(self.row_ptr), _ptr(self.col), _ptr(v))
+        return m
+
+
+@dataclass
+class BsrMatrix:
+    """Blocked CSR (64 x 64 dense blocks) resident on the device."""
+    brow_ptr: torch.Tensor
+    bcol: torch.Tensor
+    val: torch.Tensor
+    n_block_rows: int
+    bdim: int = 64
+
+    @classmethod
+    def from_arrays(cls, brow_ptr, bcol, val, bdim=64, device="cuda") -> "BsrMatrix":
+        bp = torch.as_tensor(np.ascontiguousarray(brow_ptr, dtype=np.int32)).to(device)
+        bc = torch.as_tensor(np.ascontiguousarray(bcol, dtype=np.int32)).to(device)
+        vl = torch.as_tensor(np.ascontiguousarray(val, dtype=np.float64)).to(device)
+        return cls(bp, bc, vl, int(bp.shape[0] - 1), bdim)
+
+    @property
+    def n_rows(self) -> int:
+        return self.n_block_rows * self.bdim
+
+    @property
+    def n_blocks(self) -> int:
+        return int(self.bcol.shape[0])
+
+    @property
+    def device(self) -> torch.device:
+        return self.val.device
+
+    def descriptor(self, val: Optional[torch.Tensor] = None) -> _abi.chfsi_matrix:
+        v = self.val if val is None else val
+        m = _abi.chfsi_matrix()
+        m.kind = CHFSI_BSR
+        m.bsr = _abi.chfsi_bsr(self.n_block_rows, self.n_blocks, self.bdim, _ptr(self.brow_ptr), _ptr(self.bcol),
+                               _ptr(v))
+        return m
+
+
+class Workspace:
+    """Grow-only device scratch buffer (allocate once, outside timed loops)."""
+
+    def __init__(self, device="cuda"):
+        self.device = torch.device(device)
+        self.buf: Optional[torch.Tensor] = None
+
+    def get(self, nbytes: int) -> torch.Tensor:
+        nbytes = max(int(nbytes), 256)
+        if self.buf is None or self.buf.numel() < nbytes:
+            self.buf = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        return self.buf
+
+
+def _schedule(m: int, schedule: Optional[Sequence]) -> Optional[ctypes.Structure]:
+    if schedule is None:
+        return None
+    codes = [PRECISIONS[p] if isinstance(p, str) else int(p) for p in schedule]
+    if len(codes) != m:
+        raise ValueError("schedule must list one precision per step")
+    arr = (ctypes.c_int32 * m)(*codes)
+    s = _abi.chfsi_schedule(m, ctypes.cast(arr, ctypes.POINTER(ctypes.c_int32)))
+    s._keep = arr
+    return s
+
+
+def mixed_schedule(m: int, low_steps: int, low: str = "f32") -> list:
+    """low_steps leading steps in `low` precision, the rest FP64."""
+    return [low] * low_steps + ["f64"] * (m - low_steps)
+
+
+def _check_block(t: torch.Tensor, name: str) -> None:
+    if t.dtype != torch.float64 or t.dim() != 2 or t.stride(1) != 1 or not t.is_cuda:
+        raise ValueError(f"{name} must be a row-major (N, n) float64 CUDA tensor")
+
+
+def filter_workspace_bytes(H, n_cols: int, m: int, schedule=None) -> int:
+    sz = ctypes.c_size_t(0)
+    desc = H.descriptor()
+    check(load().chfsi_filter_workspace_size(ctypes.byref(desc), n_cols, m, _schedule(m, schedule),
+                                             ctypes.byref(sz)), "chfsi_filter_workspace_size")
+    return sz.value
+
+
+def filter(H, X: torch.Tensor, m: int, a: float, b: float, a0: float, schedule=None,
+           out: Optional[torch.Tensor] = None, workspace: Optional[Workspace] = None) -> torch.Tensor:
+    """Y_m of the scaled Chebyshev filter (Algorithm 1 step 1) on the GPU."""
+    _check_block(X, "X")
+    N, n = X.shape
+    if out is None:
+        out = torch.empty((N, n), dtype=torch.float64, device=X.device)
+    _check_block(out, "out")
+    lib = load()
+    desc = H.descriptor()
+    sch = _schedule(m, schedule)
+    ws = (workspace or Workspace(X.device)).get(filter_workspace_bytes(H, n, m, schedule))
+    rc = lib.chfsi_filter(ctypes.byref(desc), _ptr(X), X.stride(0), _ptr(out), out.stride(0), n, m, a, b, a0,
+                          sch, _ptr(ws), ws.numel(), _stream_handle(X.device))
+    check(rc, "chfsi_filter")
+    return out
+
+
+def read_status(workspace: Workspace) -> int:
+    return load().chfsi_read_status(_ptr(workspace.buf), _stream_handle(workspace.device))
+
+
+def filter_backward(H: CsrMatrix, X: torch.Tensor, dY: torch.Tensor, m: int, a: float, b: float, a0: float,
+                    ckpt_stride: int = 0, want_dH: bool = True, val: Optional[torch.Tensor] = None,
+                    workspace: Optional[Workspace] = None):
+    """(dX, dH_val) for dL/dY_m = dY; dH_val has one entry per stored entry of H."""
+    _check_block(X, "X")
+    _check_block(dY, "dY")
+    N, n = X.shape
+    lib = load()
+    desc = H.descriptor(val)
+    sz = ctypes.c_size_t(0)
+    check(lib.chfsi_filter_backward_workspace_size(ctypes.byref(desc), n, m, ckpt_stride, ctypes.byref(sz)),
+          "chfsi_filter_backward_workspace_size")
+    ws = (workspace or Workspace(X.device)).get(sz.value)
+    dX = torch.empty((N, n), dtype=torch.float64, device=X.device)
+    dH = torch.empty(H.nnz, dtype=torch.float64, device=X.device) if want_dH else None
+    rc = lib.chfsi_filter_backward(ctypes.byref(desc), _ptr(X), X.stride(0), _ptr(dY), dY.stride(0), _ptr(dX),
+                                   dX.stride(0), _ptr(dH), n, m, a, b, a0, ckpt_stride, _ptr(ws), ws.numel(),
+                                   _stream_handle(X.device))
+    check(rc, "chfsi_filter_backward")
+    return dX, dH
+
+
+def rayleigh_ritz_workspace_bytes(H, n_cols: int, cholqr_passes: int = 2) -> int:
+    sz = ctypes.c_size_t(0)
+    desc = H.descriptor()
+    check(load().chfsi_rayleigh_ritz_workspace_size(ctypes.byref(desc), n_cols, cholqr_passes, ctypes.byref(sz)),
+          "chfsi_rayleigh_ritz_workspace_size")
+    return sz.value
+
+
+def rayleigh_ritz(H, Y: torch.Tensor, cholqr_passes: int = 2, psi: Optional[torch.Tensor] = None,
+                  ritz: Optional[torch.Tensor] = None, workspace: Optional[Workspace] = None):
+    """(ritz ascending, Psi) from Algorithm 1 steps 2-5 (CholQR, projection, eig, rotation)."""
+    _check_block(Y, "Y")
+    N, n = Y.shape
+    if psi is None:
+        psi = torch.empty((N, n), dtype=torch.float64, device=Y.device)
+    if ritz is None:
+        ritz = torch.empty(n, dtype=torch.float64, device=Y.device)
+    lib = load()
+    desc = H.descriptor()
+    ws = (workspace or Workspace(Y.device)).get(rayleigh_ritz_workspace_bytes(H, n, cholqr_passes))
+    rc = lib.chfsi_rayleigh_ritz(ctypes.byref(desc), _ptr(Y), Y.stride(0), n, _ptr(psi), psi.stride(0), _ptr(ritz),
+                                 cholqr_passes, _ptr(ws), ws.numel(), _stream_handle(Y.device))
+    check(rc, "chfsi_rayleigh_ritz")
+    return ritz, psi
+
+
+def lanczos_bounds(H: CsrMatrix, v0: torch.Tensor, steps: int, n_wanted: int,
+                   workspace: Optional[Workspace] = None):
+    """(a, b, a0) from `steps` Lanczos steps started at v0 (device float64, length N)."""
+    if v0.dtype != torch.float64 or not v0.is_cuda or v0.dim() != 1:
+        raise ValueError("v0 must be a 1-D float64 CUDA tensor")
+    lib = load()
+    desc = H.descriptor()
+    sz = ctypes.c_size_t(0)
+    check(lib.chfsi_lanczos_workspace_size(ctypes.byref(desc), steps, ctypes.byref(sz)),
+          "chfsi_lanczos_workspace_size")
+    ws = (workspace or Workspace(v0.device)).get(sz.value)
+    a, b, a0 = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    rc = lib.chfsi_lanczos_bounds(ctypes.byref(desc), steps, _ptr(v0.contiguous()), n_wanted, ctypes.byref(a),
+                                  ctypes.byref(b), ctypes.byref(a0), _ptr(ws), ws.numel(), _stream_handle(v0.device))
+    check(rc, "chfsi_lanczos_bounds")
+    return a.value, b.value, a0.value
+
+
+class ChebyshevFilter(torch.autograd.Function):
+    """Y_m = p(H) X with gradients into X and into H's stored values.
+
+    The bounds a, b, a0 are constants (no gradient).  The backward pass is the
+    hand-written adjoint (chfsi_filter_backward) with sqrt(m) checkpointing; it
+    uses H for H^T, so H must be symmetric.
+    """
+
+    @staticmethod
+    def forward(ctx, X, h_val, H: CsrMatrix, m: int, a: float, b: float, a0: float, ckpt_stride: int = 0):
+        ctx.H, ctx.m, ctx.a, ctx.b, ctx.a0, ctx.ckpt = H, m, a, b, a0, ckpt_stride
+        Xc = X.detach().contiguous()
+        hv = h_val.detach().contiguous()
+        ctx.save_for_backward(Xc, hv)
+        H_eff = CsrMatrix(H.row_ptr, H.col, hv, H.n_rows)
+        return filter(H_eff, Xc, m, a, b, a0)
+
+    @staticmethod
+    def backward(ctx, gY):
+        Xc, hv = ctx.saved_tensors
+        H_eff = CsrMatrix(ctx.H.row_ptr, ctx.H.col, hv, ctx.H.n_rows)
+        dX, dH = filter_backward(H_eff, Xc, gY.contiguous(), ctx.m, ctx.a, ctx.b, ctx.a0, ctx.ckpt,
+                                 want_dH=ctx.needs_input_grad[1])
+        return (dX if ctx.needs_input_grad[0] else None, dH, None, None, None, None, None, None)
+
+
+def symmetric_gradient(H: CsrMatrix, dH: torch.Tensor, transpose_index: torch.Tensor) -> torch.Tensor:
+    """dH_sym[p] = dH[p] + dH[p^T] off the diagonal, dH[p] on it, for a symmetric
+    parameterisation where entries (i, j) and (j, i) share one value."""
+    out = dH + dH[transpose_index]
+    diag = transpose_index == torch.arange(dH.shape[0], device=dH.device)
+    return torch.where(diag, dH, out)
+
+
+def transpose_index(row_ptr: np.ndarray, col: np.ndarray) -> np.ndarray:
+    """For a structurally symmetric CSR pattern: index of entry (j, i) for each (i, j)."""
+    N = row_ptr.shape[0] - 1
+    rows = np.repeat(np.arange(N, dtype=np.int64), np.diff(row_ptr))
+    key = rows * N + col.astype(np.int64)
+    tkey = col.astype(np.int64) * N + rows
+    order = np.argsort(key)
+    pos = np.searchsorted(key[order], tkey)
+    return order[pos]

@@ -1,0 +1,663 @@
+// C ABI of the chfsi library: argument validation, workspace layout, the
+// per-step schedule of the Chebyshev filter, the adjoint with checkpointing, the
+// Rayleigh-Ritz closure and the Lanczos bounds.  Host code here only orders
+// kernels on the caller's stream; every arithmetic step runs on the GPU.
+#include <atomic>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include <cusolverDn.h>
+
+#include "common.cuh"
+#include "kernels.cuh"
+
+using namespace chfsi;
+
+namespace {
+std::atomic<unsigned long long> g_launches{0};
+}
+
+void chfsi::note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+namespace {
+
+constexpr int kVersion = 10000;   // 1.0.0
+
+inline cudaStream_t as_stream(void* s) { return static_cast<cudaStream_t>(s); }
+
+inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+inline int64_t pad8(int64_t n) { return (n + 7) / 8 * 8; }
+
+int rows_of(const chfsi_matrix* H, int64_t* N) {
+    if (!H) return CHFSI_ERR_ARG;
+    if (H->kind == CHFSI_CSR) {
+        const chfsi_csr& c = H->csr;
+        if (c.n_rows <= 0 || c.nnz < 0 || c.nnz > INT64_C(0x7fffffffffff)) return CHFSI_ERR_ARG;
+        if (c.n_rows > INT32_MAX) return CHFSI_ERR_ARG;
+        if (!c.row_ptr || (c.nnz > 0 && (!c.col || !c.val))) return CHFSI_ERR_ARG;
+        *N = c.n_rows;
+        return CHFSI_OK;
+    }
+    if (H->kind == CHFSI_BSR) {
+        const chfsi_bsr& b = H->bsr;
+        if (b.bdim != 64 || b.n_block_rows <= 0 || b.n_blocks < 0) return CHFSI_ERR_ARG;
+        if (!b.brow_ptr || (b.n_blocks > 0 && (!b.bcol || !b.val))) return CHFSI_ERR_ARG;
+        if (b.n_block_rows * 64 > INT32_MAX) return CHFSI_ERR_ARG;
+        *N = b.n_block_rows * b.bdim;
+        return CHFSI_OK;
+    }
+    return CHFSI_ERR_ARG;
+}
+
+int64_t stored_values(const chfsi_matrix* H) {
+    return H->kind == CHFSI_CSR ? H->csr.nnz : H->bsr.n_blocks * (int64_t)H->bsr.bdim * H->bsr.bdim;
+}
+
+int check_bounds(double a, double b, double a0) {
+    if (!std::isfinite(a) || !std::isfinite(b) || !std::isfinite(a0)) return CHFSI_ERR_BOUNDS;
+    if (!(a0 < a) || !(a < b)) return CHFSI_ERR_BOUNDS;
+    return CHFSI_OK;
+}
+
+int check_block(const void* p, int64_t ld, int64_t n) {
+    if (!p || ld < n || !aligned16(p)) return CHFSI_ERR_ARG;
+    return CHFSI_OK;
+}
+
+// Coefficients of Y_k = alpha_k (H - c) Y_{k-1} - beta_k Y_{k-2} from the sigma
+// recurrence of Algorithm 1 (alpha_1 = sigma_1/e, alpha_k = 2 sigma_k/e,
+// beta_k = sigma_{k-1} sigma_k), computed in FP64 on the host.
+void coefficients(int m, double a, double b, double a0, std::vector<double>& alpha, std::vector<double>& beta,
+                  double& c) {
+    const double e = (b - a) / 2.0;
+    c = (b + a) / 2.0;
+    double sigma = e / (a0 - c);
+    const double sigma1 = sigma;
+    const double gamma = 2.0 / sigma1;
+    alpha.assign(m + 2, 0.0);
+    beta.assign(m + 2, 0.0);
+    alpha[1] = sigma1 / e;
+    for (int k = 2; k <= m + 1; k++) {
+        const double sigma2 = 1.0 / (gamma - sigma);
+        alpha[k] = 2.0 * sigma2 / e;
+        beta[k] = sigma * sigma2;
+        sigma = sigma2;
+    }
+}
+
+// Low-precision prefix length of a schedule (validated).
+int schedule_prefix(const chfsi_schedule* sched, int m, int* L, int* low_kind) {
+    *L = 0;
+    *low_kind = CHFSI_F64;
+    if (!sched || !sched->step_prec) return CHFSI_OK;
+    if (sched->m != m) return CHFSI_ERR_ARG;
+    int k = 0;
+    while (k < m && sched->step_prec[k] != CHFSI_F64) {
+        int p = sched->step_prec[k];
+        if (p != CHFSI_F32 && p != CHFSI_BF16_F32ACC) return CHFSI_ERR_ARG;
+        if (k > 0 && p != *low_kind) return CHFSI_ERR_ARG;
+        *low_kind = p;
+        k++;
+    }
+    for (int r = k; r < m; r++)
+        if (sched->step_prec[r] != CHFSI_F64) return CHFSI_ERR_ARG;
+    *L = k;
+    return CHFSI_OK;
+}
+
+struct FilterLayout {
+    double* W[2] = {nullptr, nullptr};
+    void* hlow = nullptr;
+    float* F[3] = {nullptr, nullptr, nullptr};
+    __nv_bfloat16* S[2] = {nullptr, nullptr};
+};
+
+template <typename A>
+void filter_layout(A& ar, int64_t N, int64_t n, int m, int L, int low_kind, int64_t nvals, FilterLayout* out) {
+    const int64_t ldw = pad8(n);
+    FilterLayout fl;
+    ar.template take<unsigned char>(kStatusBytes);
+    if (m >= 2) {
+        fl.W[0] = ar.template take<double>((size_t)(N * ldw));
+        fl.W[1] = ar.template take<double>((size_t)(N * ldw));
+    }
+    if (L > 0) {
+        fl.hlow = ar.template take<float>((size_t)nvals);
+        for (int i = 0; i < 3; i++) fl.F[i] = ar.template take<float>((size_t)(N * ldw));
+        if (low_kind == CHFSI_BF16_F32ACC)
+            for (int i = 0; i < 2; i++) fl.S[i] = ar.template take<__nv_bfloat16>((size_t)(N * ldw));
+    }
+    if (out) *out = fl;
+}
+
+struct SizeOnly {
+    size_t used = 0;
+    template <typename T>
+    T* take(size_t count) {
+        used = align_up(used) + align_up(count * sizeof(T));
+        return nullptr;
+    }
+};
+
+int run_step(const chfsi_matrix* H, const CsrDev& csr, const BsrDev& bsr, StepMath math, int64_t n,
+             const StepIO& io, double alpha, double c, double beta, bool vec, unsigned* st, cudaStream_t s) {
+    if (H->kind == CHFSI_CSR) return csr_step(csr, math, n, io, alpha, c, beta, vec, st, s);
+    return bsr_step(bsr, math, n, io, alpha, c, beta, st, s);
+}
+
+void make_devs(const chfsi_matrix* H, const void* val, Buf vt, CsrDev* csr, BsrDev* bsr) {
+    if (H->kind == CHFSI_CSR) {
+        *csr = CsrDev{H->csr.n_rows, H->csr.nnz, H->csr.row_ptr, H->csr.col, val, vt};
+    } else {
+        *bsr = BsrDev{H->bsr.n_block_rows, H->bsr.n_blocks, H->bsr.bdim, H->bsr.brow_ptr, H->bsr.bcol, val, vt};
+    }
+}
+
+// cuSOLVER handle per device, created on first use.
+cusolverDnHandle_t solver_handle() {
+    static std::mutex mu;
+    static cusolverDnHandle_t handles[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> g(mu);
+    if (!handles[dev]) {
+        if (cusolverDnCreate(&handles[dev]) != CUSOLVER_STATUS_SUCCESS) handles[dev] = nullptr;
+    }
+    return handles[dev];
+}
+
+int syevd_lwork(int64_t n, int* lwork) {
+    cusolverDnHandle_t h = solver_handle();
+    if (!h) return CHFSI_ERR_CUDA;
+    if (cusolverDnDsyevd_bufferSize(h, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_UPPER, (int)n, nullptr, (int)n,
+                                    nullptr, lwork) != CUSOLVER_STATUS_SUCCESS)
+        return CHFSI_ERR_CUDA;
+    return CHFSI_OK;
+}
+
+}  // namespace
+
+// Exported entry points (C linkage comes from the declarations in chfsi.h).
+
+const char* chfsi_status_string(int st) {
+    switch (st) {
+        case CHFSI_OK: return "ok";
+        case CHFSI_ERR_ARG: return "invalid argument (pointer, size, leading dimension or alignment)";
+        case CHFSI_ERR_BOUNDS: return "spectral bounds must be finite with a0 < a < b";
+        case CHFSI_ERR_PATTERN: return "invalid sparsity pattern (index out of range)";
+        case CHFSI_ERR_CHOL: return "Cholesky-QR failed: Gram matrix not positive definite";
+        case CHFSI_ERR_NONFINITE: return "non-finite value produced or read";
+        case CHFSI_ERR_CUDA: return "CUDA runtime or cuSOLVER error";
+        case CHFSI_ERR_TIMEOUT: return "bounded device wait timed out";
+        case CHFSI_ERR_NOMEM: return "workspace too small";
+        case CHFSI_ERR_UNSUPPORTED: return "unsupported combination of layout and precision";
+        default: return "unknown status";
+    }
+}
+
+int chfsi_version(void) { return kVersion; }
+
+unsigned long long chfsi_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+int chfsi_clear_status(void* ws, void* stream) {
+    if (!ws) return CHFSI_ERR_ARG;
+    CHFSI_CUDA_TRY(cudaMemsetAsync(ws, 0, sizeof(unsigned), as_stream(stream)));
+    return CHFSI_OK;
+}
+
+int chfsi_read_status(void* ws, void* stream) {
+    if (!ws) return CHFSI_ERR_ARG;
+    unsigned word = 0;
+    CHFSI_CUDA_TRY(cudaStreamSynchronize(as_stream(stream)));
+    CHFSI_CUDA_TRY(cudaMemcpy(&word, ws, sizeof(unsigned), cudaMemcpyDeviceToHost));
+    CHFSI_CUDA_TRY(cudaMemset(ws, 0, sizeof(unsigned)));
+    if (word & DEV_PATTERN) return CHFSI_ERR_PATTERN;
+    if (word & DEV_CHOL) return CHFSI_ERR_CHOL;
+    if (word & DEV_TIMEOUT) return CHFSI_ERR_TIMEOUT;
+    if (word & DEV_NONFINITE) return CHFSI_ERR_NONFINITE;
+    return CHFSI_OK;
+}
+
+// ------------------------------------------------------------------ filter
+
+int chfsi_filter_workspace_size(const chfsi_matrix* H, int64_t n_cols, int32_t m, const chfsi_schedule* sched,
+                                size_t* bytes) {
+    if (!bytes) return CHFSI_ERR_ARG;
+    int64_t N = 0;
+    int rc = rows_of(H, &N);
+    if (rc) return rc;
+    if (n_cols < 0 || m < 1) return CHFSI_ERR_ARG;
+    int L = 0, low = 0;
+    rc = schedule_prefix(sched, m, &L, &low);
+    if (rc) return rc;
+    SizeOnly sz;
+    filter_layout(sz, N, n_cols, m, L, low, stored_values(H), nullptr);
+    *bytes = sz.used;
+    return CHFSI_OK;
+}
+
+int chfsi_filter(const chfsi_matrix* H, const double* X, int64_t ldx, double* Y, int64_t ldy, int64_t n_cols,
+                 int32_t m, double a, double b, double a0, const chfsi_schedule* sched, void* ws, size_t ws_bytes,
+                 void* stream) {
+    int64_t N = 0;
+    int rc = rows_of(H, &N);
+    if (rc) return rc;
+    if (n_cols < 0 || m < 1) return CHFSI_ERR_ARG;
+    if ((rc = check_bounds(a, b, a0))) return rc;
+    if (n_cols == 0) return CHFSI_OK;
+    if ((rc = check_block(X, ldx, n_cols)) || (rc = check_block(Y, ldy, n_cols))) return rc;
+    if (X == Y) return CHFSI_ERR_ARG;
+    int L = 0, low = 0;
+    if ((rc = schedule_prefix(sched, m, &L, &low))) return rc;
+    if (!ws || !aligned16(ws)) return CHFSI_ERR_ARG;
+    SizeOnly sz;
+    filter_layout(sz, N, n_cols, m, L, low, stored_values(H), nullptr);
+    if (ws_bytes < sz.used) return CHFSI_ERR_NOMEM;
+    Arena ar(ws, ws_bytes);
+    FilterLayout fl;
+    filter_layout(ar, N, n_cols, m, L, low, stored_values(H), &fl);
+
+    cudaStream_t s = as_stream(stream);
+    unsigned* st = status_word(ws);
+    CHFSI_CUDA_TRY(cudaMemsetAsync(st, 0, sizeof(unsigned), s));
+
+    std::vector<double> al, be;
+    double c = 0.0;
+    coefficients(m, a, b, a0, al, be, c);
+    const int64_t n = n_cols, ldw = pad8(n);
+    const bool vec = (n % 2 == 0) && (ldx % 2 == 0) && (ldy % 2 == 0);
+
+    CsrDev csr64{}, csrlo{};
+    BsrDev bsr64{}, bsrlo{};
+    const void* hval64 = H->kind == CHFSI_CSR ? (const void*)H->csr.val : (const void*)H->bsr.val;
+    make_devs(H, hval64, Buf::F64, &csr64, &bsr64);
+
+    // FP64 iterate k lives in cyc[(m - k) % 3], so that Y_m lands in Y.
+    double* cyc[3] = {Y, fl.W[0], fl.W[1]};
+    int64_t cyc_ld[3] = {ldy, ldw, ldw};
+    auto f64_buf = [&](int k) { return cyc[(m - k) % 3]; };
+    auto f64_ld = [&](int k) { return cyc_ld[(m - k) % 3]; };
+
+    if (L > 0) {
+        const bool bf = low == CHFSI_BF16_F32ACC;
+        rc = convert_values(hval64 ? static_cast<const double*>(hval64) : nullptr, fl.hlow, Buf::F32,
+                            stored_values(H), bf, s);
+        if (rc) return rc;
+        make_devs(H, fl.hlow, Buf::F32, &csrlo, &bsrlo);
+        if ((rc = convert_block(X, Buf::F64, ldx, fl.F[0], Buf::F32, ldw, N, n, s))) return rc;
+        if (bf && (rc = convert_block(X, Buf::F64, ldx, fl.S[0], Buf::BF16, ldw, N, n, s))) return rc;
+        const StepMath lm = bf ? StepMath::BF16 : StepMath::F32;
+        for (int k = 1; k <= L; k++) {
+            StepIO io{};
+            io.cur = fl.F[(k - 1) % 3]; io.cur_t = Buf::F32; io.ldc = ldw;
+            if (bf) { io.gather = fl.S[(k - 1) % 2]; io.gather_t = Buf::BF16; }
+            else { io.gather = io.cur; io.gather_t = Buf::F32; }
+            io.ldg = ldw;
+            if (k >= 2) { io.prev = fl.F[(k - 2) % 3]; io.prev_t = Buf::F32; io.ldp = ldw; }
+            io.out = fl.F[k % 3]; io.out_t = Buf::F32; io.ldo = ldw;
+            if (bf) { io.shadow = fl.S[k % 2]; io.lds = ldw; }
+            rc = run_step(H, csrlo, bsrlo, lm, n, io, al[k], c, k >= 2 ? be[k] : 0.0, true, st, s);
+            if (rc) return rc;
+        }
+        if (L == m)   // no FP64 step: widen the last iterate into Y
+            return convert_block(fl.F[m % 3], Buf::F32, ldw, Y, Buf::F64, ldy, N, n, s);
+    }
+
+    for (int k = L + 1; k <= m; k++) {
+        StepIO io{};
+        // Y_{k-1}
+        if (k - 1 == 0) { io.cur = X; io.cur_t = Buf::F64; io.ldc = ldx; }
+        else if (k - 1 <= L) { io.cur = fl.F[(k - 1) % 3]; io.cur_t = Buf::F32; io.ldc = ldw; }
+        else { io.cur = f64_buf(k - 1); io.cur_t = Buf::F64; io.ldc = f64_ld(k - 1); }
+        io.gather = io.cur; io.gather_t = io.cur_t; io.ldg = io.ldc;
+        // Y_{k-2}
+        if (k >= 2) {
+            if (k - 2 == 0) { io.prev = X; io.prev_t = Buf::F64; io.ldp = ldx; }
+            else if (k - 2 <= L) { io.prev = fl.F[(k - 2) % 3]; io.prev_t = Buf::F32; io.ldp = ldw; }
+            else { io.prev = f64_buf(k - 2); io.prev_t = Buf::F64; io.ldp = f64_ld(k - 2); }
+        }
+        io.out = f64_buf(k); io.out_t = Buf::F64; io.ldo = f64_ld(k);
+        rc = run_step(H, csr64, bsr64, StepMath::F64, n, io, al[k], c, k >= 2 ? be[k] : 0.0, vec, st, s);
+        if (rc) return rc;
+    }
+    return CHFSI_OK;
+}
+
+// ------------------------------------------------------------------ adjoint
+
+namespace {
+
+struct BackLayout {
+    int S = 1, nseg = 1;
+    std::vector<double*> ck;      // checkpoint blocks: 2 per segment i >= 1
+    std::vector<double*> seg;     // S - 1 replay blocks
+    double* A[3] = {nullptr, nullptr, nullptr};
+};
+
+template <typename Ar>
+void back_layout(Ar& ar, int64_t N, int64_t n, int m, int stride, BackLayout* out) {
+    BackLayout bl;
+    bl.S = stride > 0 ? stride : (int)std::ceil(std::sqrt((double)m));
+    if (bl.S < 1) bl.S = 1;
+    if (bl.S > m) bl.S = m;
+    bl.nseg = (m + bl.S - 1) / bl.S;
+    const int64_t ldw = pad8(n);
+    ar.template take<unsigned char>(kStatusBytes);
+    for (int i = 1; i < bl.nseg; i++) {
+        bl.ck.push_back(ar.template take<double>((size_t)(N * ldw)));
+        bl.ck.push_back(ar.template take<double>((size_t)(N * ldw)));
+    }
+    for (int i = 1; i < bl.S; i++) bl.seg.push_back(ar.template take<double>((size_t)(N * ldw)));
+    for (int i = 0; i < 3; i++) bl.A[i] = ar.template take<double>((size_t)(N * ldw));
+    if (out) *out = bl;
+}
+
+}  // namespace
+
+int chfsi_filter_backward_workspace_size(const chfsi_matrix* H, int64_t n_cols, int32_t m, int32_t ckpt_stride,
+                                         size_t* bytes) {
+    if (!bytes) return CHFSI_ERR_ARG;
+    int64_t N = 0;
+    int rc = rows_of(H, &N);
+    if (rc) return rc;
+    if (H->kind != CHFSI_CSR) return CHFSI_ERR_UNSUPPORTED;
+    if (n_cols < 0 || m < 1 || ckpt_stride < 0) return CHFSI_ERR_ARG;
+    SizeOnly sz;
+    back_layout(sz, N, n_cols, m, ckpt_stride, nullptr);
+    *bytes = sz.used;
+    return CHFSI_OK;
+}
+
+int chfsi_filter_backward(const chfsi_matrix* H, const double* X, int64_t ldx, const double* dY, int64_t lddy,
+                          double* dX, int64_t lddx, double* dH_val, int64_t n_cols, int32_t m, double a, double b,
+                          double a0, int32_t ckpt_stride, void* ws, size_t ws_bytes, void* stream) {
+    int64_t N = 0;
+    int rc = rows_of(H, &N);
+    if (rc) return rc;
+    if (H->kind != CHFSI_CSR) return CHFSI_ERR_UNSUPPORTED;
+    if (n_cols < 0 || m < 1 || ckpt_stride < 0) return CHFSI_ERR_ARG;
+    if ((rc = check_bounds(a, b, a0))) return rc;
+    cudaStream_t s = as_stream(stream);
+    if (n_cols == 0) {
+        if (dH_val) return fill_zero(dH_val, sizeof(double) * (size_t)H->csr.nnz, s);
+        return CHFSI_OK;
+    }
+    if ((rc = check_block(X, ldx, n_cols)) || (rc = check_block(dY, lddy, n_cols)) ||
+        (rc = check_block(dX, lddx, n_cols)))
+        return rc;
+    if (dX == X || dX == dY) return CHFSI_ERR_ARG;
+    if (!ws || !aligned16(ws)) return CHFSI_ERR_ARG;
+    SizeOnly sz;
+    back_layout(sz, N, n_cols, m, ckpt_stride, nullptr);
+    if (ws_bytes < sz.used) return CHFSI_ERR_NOMEM;
+    Arena ar(ws, ws_bytes);
+    BackLayout bl;
+    back_layout(ar, N, n_cols, m, ckpt_stride, &bl);
+    unsigned* st = status_word(ws);
+    CHFSI_CUDA_TRY(cudaMemsetAsync(st, 0, sizeof(unsigned), s));
+
+    std::vector<double> al, be;
+    double c = 0.0;
+    coefficients(m, a, b, a0, al, be, c);
+    const int64_t n = n_cols, ldw = pad8(n);
+    const bool vec = (n % 2 == 0) && (ldx % 2 == 0) && (lddy % 2 == 0) && (lddx % 2 == 0);
+    CsrDev h{H->csr.n_rows, H->csr.nnz, H->csr.row_ptr, H->csr.col, H->csr.val, Buf::F64};
+    const int S = bl.S;
+
+    // Forward pass to the last checkpoint.  Checkpoint pair of segment i >= 1:
+    // Y_{iS-1} -> ck[2(i-1)], Y_{iS} -> ck[2(i-1)+1]; other iterates rotate in A[].
+    auto ck_slot = [&](int k) -> double* {
+        for (int i = 1; i < bl.nseg; i++) {
+            if (k == i * S - 1) return bl.ck[2 * (i - 1)];
+            if (k == i * S) return bl.ck[2 * (i - 1) + 1];
+        }
+        return nullptr;
+    };
+    std::vector<const double*> fptr(m + 1, nullptr);
+    std::vector<int64_t> fld(m + 1, ldw);
+    fptr[0] = X;
+    fld[0] = ldx;
+    const int k_last = (bl.nseg - 1) * S;
+    for (int k = 1; k <= k_last; k++) {
+        double* out = ck_slot(k);
+        if (!out) out = bl.A[k % 3];
+        StepIO io{};
+        io.cur = fptr[k - 1]; io.cur_t = Buf::F64; io.ldc = fld[k - 1];
+        io.gather = io.cur; io.gather_t = Buf::F64; io.ldg = io.ldc;
+        if (k >= 2) { io.prev = fptr[k - 2]; io.prev_t = Buf::F64; io.ldp = fld[k - 2]; }
+        io.out = out; io.out_t = Buf::F64; io.ldo = ldw;
+        if ((rc = csr_step(h, StepMath::F64, n, io, al[k], c, k >= 2 ? be[k] : 0.0, vec, st, s))) return rc;
+        fptr[k] = out;
+        fld[k] = ldw;
+    }
+
+    if (dH_val && (rc = fill_zero(dH_val, sizeof(double) * (size_t)H->csr.nnz, s))) return rc;
+
+    // Adjoint iterates: Ybar_m = dY; Ybar_j for 1 <= j < m in A[j % 3]; Ybar_0 = dX.
+    auto bar_ptr = [&](int j) -> double* { return j == 0 ? dX : bl.A[j % 3]; };
+    auto bar_ld = [&](int j) -> int64_t { return j == m ? lddy : (j == 0 ? lddx : ldw); };
+    auto bar_cptr = [&](int j) -> const double* { return j == m ? dY : bar_ptr(j); };
+
+    for (int i = bl.nseg - 1; i >= 0; i--) {
+        const int s0 = i * S;
+        const int e0 = (s0 + S < m) ? s0 + S : m;
+        // replay Y_{s0+1} .. Y_{e0-1} from the checkpoint pair (Y_{s0-1}, Y_{s0})
+        // the pair was stored by the forward pass in dedicated checkpoint slots
+        // (fptr[0] = X); iterates in the rotating buffers are never read here
+        std::vector<const double*> yp(e0 - s0, nullptr);
+        std::vector<int64_t> yl(e0 - s0, ldw);
+        const double* prevp = (s0 == 0) ? nullptr : fptr[s0 - 1];
+        const int64_t prevl = (s0 == 0) ? ldw : fld[s0 - 1];
+        yp[0] = fptr[s0];
+        yl[0] = fld[s0];
+        for (int k = s0 + 1; k <= e0 - 1; k++) {
+            double* out = bl.seg[k - s0 - 1];
+            StepIO io{};
+            io.cur = yp[k - 1 - s0]; io.cur_t = Buf::F64; io.ldc = yl[k - 1 - s0];
+            io.gather = io.cur; io.gather_t = Buf::F64; io.ldg = io.ldc;
+            const double* pp = (k - 2 - s0 >= 0) ? yp[k - 2 - s0] : prevp;
+            int64_t pl = (k - 2 - s0 >= 0) ? yl[k - 2 - s0] : prevl;
+            if (k >= 2) { io.prev = pp; io.prev_t = Buf::F64; io.ldp = pl; }
+            io.out = out; io.out_t = Buf::F64; io.ldo = ldw;
+            if ((rc = csr_step(h, StepMath::F64, n, io, al[k], c, k >= 2 ? be[k] : 0.0, vec, st, s))) return rc;
+            yp[k - s0] = out;
+        }
+        // reverse steps k = e0 .. s0+1
+        for (int k = e0; k >= s0 + 1; k--) {
+            const double* ykm1 = yp[k - 1 - s0];
+            const int64_t ldk = yl[k - 1 - s0];
+            if (dH_val && (rc = sddmm_accumulate(h, n, bar_cptr(k), bar_ld(k), ykm1, ldk, al[k], dH_val, s)))
+                return rc;
+            StepIO io{};
+            io.cur = bar_cptr(k); io.cur_t = Buf::F64; io.ldc = bar_ld(k);
+            io.gather = io.cur; io.gather_t = Buf::F64; io.ldg = io.ldc;
+            if (k + 1 <= m) { io.prev = bar_cptr(k + 1); io.prev_t = Buf::F64; io.ldp = bar_ld(k + 1); }
+            io.out = bar_ptr(k - 1); io.out_t = Buf::F64; io.ldo = bar_ld(k - 1);
+            if ((rc = csr_step(h, StepMath::F64, n, io, al[k], c, k + 1 <= m ? be[k + 1] : 0.0, vec, st, s)))
+                return rc;
+        }
+    }
+    return CHFSI_OK;
+}
+
+// ------------------------------------------------------------------ Rayleigh-Ritz
+
+namespace {
+
+struct RRLayout {
+    double *S = nullptr, *part = nullptr, *XF = nullptr, *T = nullptr, *Rinv = nullptr, *Q = nullptr;
+    double* work = nullptr;
+    int* info = nullptr;
+    int splits = 1;
+    int lwork = 0;
+};
+
+template <typename Ar>
+void rr_layout(Ar& ar, int64_t N, int64_t n, int lwork, RRLayout* out) {
+    RRLayout rl;
+    const int64_t ldw = pad8(n);
+    rl.splits = gemm_tn_splits(N, n);
+    rl.lwork = lwork;
+    ar.template take<unsigned char>(kStatusBytes);
+    rl.S = ar.template take<double>((size_t)(n * n));
+    rl.part = ar.template take<double>((size_t)(rl.splits * n * n));
+    rl.XF = ar.template take<double>((size_t)(N * ldw));
+    rl.T = ar.template take<double>((size_t)(N * ldw));
+    rl.Rinv = ar.template take<double>((size_t)(n * n));
+    rl.Q = ar.template take<double>((size_t)(n * n));
+    rl.work = ar.template take<double>((size_t)(lwork > 0 ? lwork : 1));
+    rl.info = ar.template take<int>(1);
+    if (out) *out = rl;
+}
+
+}  // namespace
+
+int chfsi_rayleigh_ritz_workspace_size(const chfsi_matrix* H, int64_t n_cols, int32_t cholqr_passes, size_t* bytes) {
+    if (!bytes) return CHFSI_ERR_ARG;
+    int64_t N = 0;
+    int rc = rows_of(H, &N);
+    if (rc) return rc;
+    if (n_cols < 1 || n_cols > N || (cholqr_passes != 1 && cholqr_passes != 2)) return CHFSI_ERR_ARG;
+    int lwork = 0;
+    if ((rc = syevd_lwork(n_cols, &lwork))) return rc;
+    SizeOnly sz;
+    rr_layout(sz, N, n_cols, lwork, nullptr);
+    *bytes = sz.used;
+    return CHFSI_OK;
+}
+
+int chfsi_rayleigh_ritz(const chfsi_matrix* H, const double* Y, int64_t ldy, int64_t n_cols, double* Psi,
+                        int64_t ldpsi, double* ritz, int32_t cholqr_passes, void* ws, size_t ws_bytes, void* stream) {
+    int64_t N = 0;
+    int rc = rows_of(H, &N);
+    if (rc) return rc;
+    if (n_cols < 1 || n_cols > N || (cholqr_passes != 1 && cholqr_passes != 2)) return CHFSI_ERR_ARG;
+    if ((rc = check_block(Y, ldy, n_cols)) || (rc = check_block(Psi, ldpsi, n_cols))) return rc;
+    if (!ritz || Psi == Y) return CHFSI_ERR_ARG;
+    if (!ws || !aligned16(ws)) return CHFSI_ERR_ARG;
+    int lwork = 0;
+    if ((rc = syevd_lwork(n_cols, &lwork))) return rc;
+    SizeOnly sz;
+    rr_layout(sz, N, n_cols, lwork, nullptr);
+    if (ws_bytes < sz.used) return CHFSI_ERR_NOMEM;
+    Arena ar(ws, ws_bytes);
+    RRLayout rl;
+    rr_layout(ar, N, n_cols, lwork, &rl);
+    cudaStream_t s = as_stream(stream);
+    unsigned* st = status_word(ws);
+    CHFSI_CUDA_TRY(cudaMemsetAsync(st, 0, sizeof(unsigned), s));
+    const int64_t n = n_cols, ldw = pad8(n);
+
+    // step 2: X_F = Y R^-1 with S = Y^T Y = R^T R (repeated on X_F for CholQR2)
+    const double* cur = Y;
+    int64_t cur_ld = ldy;
+    double* bufs[2] = {rl.XF, rl.T};
+    int which = 0;
+    for (int pass = 0; pass < cholqr_passes; pass++) {
+        if ((rc = gemm_tn(cur, cur_ld, cur, cur_ld, N, n, rl.S, n, true, rl.part, rl.splits, s))) return rc;
+        if ((rc = cholesky_upper(rl.S, n, n, st, s))) return rc;
+        if ((rc = tri_inverse_upper(rl.S, n, rl.Rinv, n, n, s))) return rc;
+        double* out = bufs[which];
+        if ((rc = gemm_nn(cur, cur_ld, rl.Rinv, n, out, ldw, N, n, true, s))) return rc;
+        cur = out;
+        cur_ld = ldw;
+        which ^= 1;
+    }
+    double* XF = const_cast<double*>(cur);
+    double* HXF = bufs[which];
+    // step 3: H_F = X_F^T (H X_F)
+    {
+        CsrDev csr{};
+        BsrDev bsr{};
+        const void* hval = H->kind == CHFSI_CSR ? (const void*)H->csr.val : (const void*)H->bsr.val;
+        make_devs(H, hval, Buf::F64, &csr, &bsr);
+        StepIO io{};
+        io.cur = XF; io.cur_t = Buf::F64; io.ldc = ldw;
+        io.gather = XF; io.gather_t = Buf::F64; io.ldg = ldw;
+        io.out = HXF; io.out_t = Buf::F64; io.ldo = ldw;
+        if ((rc = run_step(H, csr, bsr, StepMath::F64, n, io, 1.0, 0.0, 0.0, n % 2 == 0, st, s))) return rc;
+    }
+    if ((rc = gemm_tn(XF, ldw, HXF, ldw, N, n, rl.S, n, false, rl.part, rl.splits, s))) return rc;
+    if ((rc = symmetrize(rl.S, n, n, s))) return rc;
+    // step 4: H_F Q = Q Lambda (cuSOLVER; column-major view of the symmetric H_F)
+    cusolverDnHandle_t hs = solver_handle();
+    if (!hs) return CHFSI_ERR_CUDA;
+    if (cusolverDnSetStream(hs, s) != CUSOLVER_STATUS_SUCCESS) return CHFSI_ERR_CUDA;
+    if (cusolverDnDsyevd(hs, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_UPPER, (int)n, rl.S, (int)n, ritz, rl.work,
+                         rl.lwork, rl.info) != CUSOLVER_STATUS_SUCCESS)
+        return CHFSI_ERR_CUDA;
+    // eigenvector i is row i of the row-major view; Q[k][i] = that row transposed
+    if ((rc = transpose(rl.S, n, rl.Q, n, n, s))) return rc;
+    // step 5: Psi = X_F Q
+    if ((rc = gemm_nn(XF, ldw, rl.Q, n, Psi, ldpsi, N, n, false, s))) return rc;
+
+    int info = 0;
+    CHFSI_CUDA_TRY(cudaMemcpyAsync(&info, rl.info, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CHFSI_CUDA_TRY(cudaStreamSynchronize(s));
+    unsigned word = 0;
+    CHFSI_CUDA_TRY(cudaMemcpy(&word, st, sizeof(unsigned), cudaMemcpyDeviceToHost));
+    if (word & DEV_PATTERN) return CHFSI_ERR_PATTERN;
+    if (word & DEV_CHOL) return CHFSI_ERR_CHOL;
+    if (info != 0) return CHFSI_ERR_CUDA;
+    if (word & DEV_NONFINITE) return CHFSI_ERR_NONFINITE;
+    return CHFSI_OK;
+}
+
+// ------------------------------------------------------------------ Lanczos bounds
+
+int chfsi_lanczos_workspace_size(const chfsi_matrix* H, int32_t steps, size_t* bytes) {
+    if (!bytes) return CHFSI_ERR_ARG;
+    int64_t N = 0;
+    int rc = rows_of(H, &N);
+    if (rc) return rc;
+    if (H->kind != CHFSI_CSR) return CHFSI_ERR_UNSUPPORTED;
+    if (steps < 1 || steps > 64) return CHFSI_ERR_ARG;
+    SizeOnly sz;
+    sz.take<unsigned char>(kStatusBytes);
+    sz.take<double>((size_t)((steps + 1) * N));
+    sz.take<double>((size_t)N);
+    sz.take<double>(lanczos_part_count(N, steps));
+    sz.take<double>(512);
+    sz.take<double>(4);
+    *bytes = sz.used;
+    return CHFSI_OK;
+}
+
+int chfsi_lanczos_bounds(const chfsi_matrix* H, int32_t steps, const double* v0, int64_t n_wanted, double* a,
+                         double* b, double* a0, void* ws, size_t ws_bytes, void* stream) {
+    int64_t N = 0;
+    int rc = rows_of(H, &N);
+    if (rc) return rc;
+    if (H->kind != CHFSI_CSR) return CHFSI_ERR_UNSUPPORTED;
+    if (steps < 1 || steps > 64 || !v0 || !a || !b || !a0 || n_wanted < 1 || n_wanted >= N) return CHFSI_ERR_ARG;
+    if (!ws || !aligned16(ws)) return CHFSI_ERR_ARG;
+    size_t need = 0;
+    if ((rc = chfsi_lanczos_workspace_size(H, steps, &need))) return rc;
+    if (ws_bytes < need) return CHFSI_ERR_NOMEM;
+    Arena ar(ws, ws_bytes);
+    ar.take<unsigned char>(kStatusBytes);
+    double* V = ar.take<double>((size_t)((steps + 1) * N));
+    double* w = ar.take<double>((size_t)N);
+    double* part = ar.take<double>(lanczos_part_count(N, steps));
+    double* scal = ar.take<double>(512);
+    double* out = ar.take<double>(4);
+    cudaStream_t s = as_stream(stream);
+    unsigned* st = status_word(ws);
+    CHFSI_CUDA_TRY(cudaMemsetAsync(st, 0, sizeof(unsigned), s));
+    CsrDev h{H->csr.n_rows, H->csr.nnz, H->csr.row_ptr, H->csr.col, H->csr.val, Buf::F64};
+    if ((rc = lanczos_run(h, steps, v0, n_wanted, V, w, part, scal, out, st, s))) return rc;
+    double host[3];
+    CHFSI_CUDA_TRY(cudaMemcpyAsync(host, out, sizeof(host), cudaMemcpyDeviceToHost, s));
+    CHFSI_CUDA_TRY(cudaStreamSynchronize(s));
+    unsigned word = 0;
+    CHFSI_CUDA_TRY(cudaMemcpy(&word, st, sizeof(unsigned), cudaMemcpyDeviceToHost));
+    if (word & DEV_PATTERN) return CHFSI_ERR_PATTERN;
+    if (!std::isfinite(host[0]) || !std::isfinite(host[1]) || !std::isfinite(host[2])) return CHFSI_ERR_NONFINITE;
+    *a = host[0];
+    *b = host[1];
+    *a0 = host[2];
+    return CHFSI_OK;
+}

@@ -1,0 +1,293 @@
+// Fused CSR filter step (Algorithm 1, step 1, Sec. 3.4):
+//
+//     Y_out = alpha * (H * Y_cur - c * Y_cur) - beta * Y_prev
+//
+// one launch per Chebyshev step, so Y_prev, Y_cur and Y_out each make one HBM pass
+// per step (the gathers of H * Y_cur hit L1/L2: the rows a warp gathers are the
+// 3-D grid neighbours of its own row).  The same kernel with alpha = 1, c = 0,
+// beta = 0 is the plain product H X of the subspace projection (step 3), and with
+// (alpha_k, beta_{k+1}) on the adjoint iterates it is the reverse recurrence.
+//
+// Layout: one CTA owns kWarps consecutive rows (one warp per row).  The CTA's
+// slice of the CSR arrays (values and column indices, contiguous because the rows
+// are consecutive) is staged once into shared memory with cp.async and reused for
+// every column chunk of the row.  Lanes own V consecutive columns (vector loads:
+// double2 for FP64, float4 for FP32, 4 x bf16 for the BF16 operand); a chunk is
+// 32 * V * U columns.  Accumulation order over a row's entries is the stored order.
+// Every column index is range-checked while staging; a bad one is replaced by a
+// zero entry and reported in the status word, so no access leaves the buffers.
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace chfsi {
+
+namespace {
+
+constexpr int kWarps = 8;            // rows (warps) per CTA
+constexpr int kThreads = kWarps * 32;
+
+template <typename T> __device__ __forceinline__ float to_f(T x);
+template <> __device__ __forceinline__ float to_f<float>(float x) { return x; }
+template <> __device__ __forceinline__ float to_f<double>(double x) { return (float)x; }
+template <> __device__ __forceinline__ float to_f<__nv_bfloat16>(__nv_bfloat16 x) { return __bfloat162float(x); }
+
+template <typename A, typename T> __device__ __forceinline__ A cvt(T x);
+template <> __device__ __forceinline__ double cvt<double, double>(double x) { return x; }
+template <> __device__ __forceinline__ double cvt<double, float>(float x) { return (double)x; }
+template <> __device__ __forceinline__ float cvt<float, float>(float x) { return x; }
+template <> __device__ __forceinline__ float cvt<float, double>(double x) { return (float)x; }
+template <> __device__ __forceinline__ float cvt<float, __nv_bfloat16>(__nv_bfloat16 x) { return __bfloat162float(x); }
+
+// Read V consecutive elements (aligned to V * sizeof(T)) through the read-only path.
+template <typename A, typename T, int V>
+__device__ __forceinline__ void ldv(const T* __restrict__ p, A (&o)[V]) {
+    if constexpr (std::is_same<T, double>::value && V % 2 == 0) {
+#pragma unroll
+        for (int i = 0; i < V; i += 2) {
+            double2 t = __ldg(reinterpret_cast<const double2*>(p + i));
+            o[i] = cvt<A>(t.x); o[i + 1] = cvt<A>(t.y);
+        }
+    } else if constexpr (std::is_same<T, float>::value && V % 4 == 0) {
+#pragma unroll
+        for (int i = 0; i < V; i += 4) {
+            float4 t = __ldg(reinterpret_cast<const float4*>(p + i));
+            o[i] = cvt<A>(t.x); o[i + 1] = cvt<A>(t.y); o[i + 2] = cvt<A>(t.z); o[i + 3] = cvt<A>(t.w);
+        }
+    } else if constexpr (std::is_same<T, float>::value && V % 2 == 0) {
+#pragma unroll
+        for (int i = 0; i < V; i += 2) {
+            float2 t = __ldg(reinterpret_cast<const float2*>(p + i));
+            o[i] = cvt<A>(t.x); o[i + 1] = cvt<A>(t.y);
+        }
+    } else if constexpr (std::is_same<T, __nv_bfloat16>::value && V % 4 == 0) {
+#pragma unroll
+        for (int i = 0; i < V; i += 4) {
+            uint2 t = __ldg(reinterpret_cast<const uint2*>(p + i));
+            __nv_bfloat162 lo = *reinterpret_cast<__nv_bfloat162*>(&t.x);
+            __nv_bfloat162 hi = *reinterpret_cast<__nv_bfloat162*>(&t.y);
+            float2 a = __bfloat1622float2(lo), b = __bfloat1622float2(hi);
+            o[i] = cvt<A>(a.x); o[i + 1] = cvt<A>(a.y); o[i + 2] = cvt<A>(b.x); o[i + 3] = cvt<A>(b.y);
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < V; i++) o[i] = cvt<A>(p[i]);
+    }
+}
+
+template <typename A, typename T, int V>
+__device__ __forceinline__ void stv(T* p, const A (&v)[V]) {
+    if constexpr (std::is_same<T, double>::value && V % 2 == 0) {
+#pragma unroll
+        for (int i = 0; i < V; i += 2)
+            *reinterpret_cast<double2*>(p + i) = make_double2((double)v[i], (double)v[i + 1]);
+    } else if constexpr (std::is_same<T, float>::value && V % 4 == 0) {
+#pragma unroll
+        for (int i = 0; i < V; i += 4)
+            *reinterpret_cast<float4*>(p + i) = make_float4((float)v[i], (float)v[i + 1], (float)v[i + 2], (float)v[i + 3]);
+    } else if constexpr (std::is_same<T, __nv_bfloat16>::value && V % 4 == 0) {
+#pragma unroll
+        for (int i = 0; i < V; i += 4) {
+            __nv_bfloat162 lo = __floats2bfloat162_rn((float)v[i], (float)v[i + 1]);
+            __nv_bfloat162 hi = __floats2bfloat162_rn((float)v[i + 2], (float)v[i + 3]);
+            uint2 t;
+            t.x = *reinterpret_cast<unsigned*>(&lo);
+            t.y = *reinterpret_cast<unsigned*>(&hi);
+            *reinterpret_cast<uint2*>(p + i) = t;
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < V; i++) {
+            if constexpr (std::is_same<T, __nv_bfloat16>::value) p[i] = __float2bfloat16_rn((float)v[i]);
+            else p[i] = (T)v[i];
+        }
+    }
+}
+
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+    unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+    unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
+template <typename TH>
+__device__ __forceinline__ void stage_entry(TH* sv, int32_t* sc, const TH* val, const int32_t* col,
+                                            int64_t p) {
+    if constexpr (sizeof(TH) == 8) cp_async8(sv, val + p);
+    else cp_async4(sv, val + p);
+    cp_async4(sc, col + p);
+}
+
+// ACC: arithmetic type; TH: stored H value type; TG: gathered operand (Y_cur or
+// its BF16 shadow); TC: own-row Y_cur (for the -c Y_cur term); TP: Y_prev; TO:
+// output; TS: optional BF16 shadow of the output (void-like when !kShadow).
+template <typename ACC, typename TH, typename TG, typename TC, typename TP, typename TO, int V, int U,
+          bool kShadow>
+__global__ void __launch_bounds__(kThreads)
+csr_step_kernel(int64_t N, const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                const TH* __restrict__ val, int64_t nnz, int64_t n,
+                const TG* __restrict__ Yg, int64_t ldg, const TC* __restrict__ Yc, int64_t ldc,
+                const TP* __restrict__ Yp, int64_t ldp, TO* __restrict__ Yo, int64_t ldo,
+                __nv_bfloat16* __restrict__ Ys, int64_t lds, ACC alpha, ACC c, ACC beta, int cap,
+                unsigned* status) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    TH* s_val = reinterpret_cast<TH*>(smem_raw);
+    int32_t* s_col = reinterpret_cast<int32_t*>(smem_raw + sizeof(TH) * (size_t)cap);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t r0 = (int64_t)blockIdx.x * kWarps;
+    const int64_t r_end = (r0 + kWarps < N) ? r0 + kWarps : N;
+
+    auto clampp = [&](int64_t p) { return p < 0 ? (int64_t)0 : (p > nnz ? nnz : p); };
+    const int64_t p_lo = clampp(row_ptr[r0]);
+    const int64_t p_hi = clampp(row_ptr[r_end]);
+    const int64_t cnt = p_hi > p_lo ? p_hi - p_lo : 0;
+    const bool staged = cnt <= cap;
+    bool bad = false;
+
+    if (staged) {
+        for (int64_t q = threadIdx.x; q < cnt; q += kThreads) stage_entry(s_val + q, s_col + q, val, col, p_lo + q);
+        cp_async_wait_all();
+        __syncthreads();
+        for (int64_t q = threadIdx.x; q < cnt; q += kThreads) {
+            if ((uint64_t)(uint32_t)s_col[q] >= (uint64_t)N || s_col[q] < 0) {
+                s_col[q] = 0;
+                s_val[q] = (TH)0;
+                bad = true;
+            }
+        }
+        __syncthreads();
+    }
+
+    const int64_t r = r0 + warp;
+    if (r < r_end) {
+        int64_t rb = clampp(row_ptr[r]), re = clampp(row_ptr[r + 1]);
+        if (re < rb) { re = rb; bad = true; }
+        if (rb < p_lo || re > p_hi) { rb = re = p_lo; bad = true; }
+        const TH* hv = staged ? s_val + (rb - p_lo) : val + rb;
+        const int32_t* hc = staged ? s_col + (rb - p_lo) : col + rb;
+        const int len = (int)(re - rb);
+        bool nonfinite = false;
+
+        for (int64_t jbase = 0; jbase < n; jbase += 32 * V * U) {
+            ACC acc[U][V];
+            bool on[U];
+#pragma unroll
+            for (int u = 0; u < U; u++) {
+                on[u] = jbase + (int64_t)(u * 32 + lane) * V < n;
+#pragma unroll
+                for (int v = 0; v < V; v++) acc[u][v] = (ACC)0;
+            }
+            const int64_t j0 = jbase + (int64_t)lane * V;
+#pragma unroll 4
+            for (int q = 0; q < len; q++) {
+                int32_t cj = hc[q];
+                ACC h = cvt<ACC>(hv[q]);
+                if (!staged && ((uint32_t)cj >= (uint64_t)N || cj < 0)) { bad = true; continue; }
+                const TG* src = Yg + (int64_t)cj * ldg + j0;
+#pragma unroll
+                for (int u = 0; u < U; u++) {
+                    if (on[u]) {
+                        ACC y[V];
+                        ldv<ACC, TG, V>(src + u * 32 * V, y);
+#pragma unroll
+                        for (int v = 0; v < V; v++) acc[u][v] = fma(h, y[v], acc[u][v]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < U; u++) {
+                if (!on[u]) continue;
+                const int64_t j = j0 + u * 32 * V;
+                ACC yc[V], out[V];
+                ldv<ACC, TC, V>(Yc + r * ldc + j, yc);
+                if (Yp) {
+                    ACC yp[V];
+                    ldv<ACC, TP, V>(Yp + r * ldp + j, yp);
+#pragma unroll
+                    for (int v = 0; v < V; v++) out[v] = fma(-beta, yp[v], alpha * fma(-c, yc[v], acc[u][v]));
+                } else {
+#pragma unroll
+                    for (int v = 0; v < V; v++) out[v] = alpha * fma(-c, yc[v], acc[u][v]);
+                }
+#pragma unroll
+                for (int v = 0; v < V; v++) nonfinite |= !isfinite(out[v]);
+                stv<ACC, TO, V>(Yo + r * ldo + j, out);
+                if constexpr (kShadow) stv<ACC, __nv_bfloat16, V>(Ys + r * lds + j, out);
+            }
+        }
+        if (__any_sync(0xffffffffu, nonfinite) && lane == 0) raise_status(status, DEV_NONFINITE);
+    }
+    if (__syncthreads_or(bad) && threadIdx.x == 0) raise_status(status, DEV_PATTERN);
+}
+
+template <typename ACC, typename TH, typename TG, typename TC, typename TP, typename TO, int V, int U,
+          bool kShadow>
+int launch(const CsrDev& h, const void* hval, int64_t n, const StepIO& io, double alpha, double c,
+           double beta, unsigned* status, cudaStream_t s) {
+    const int cap = 6144;
+    const size_t smem = (sizeof(TH) + sizeof(int32_t)) * (size_t)cap;
+    auto kern = csr_step_kernel<ACC, TH, TG, TC, TP, TO, V, U, kShadow>;
+    static bool attr_set = false;   // per instantiation; smem size is a compile-time constant
+    if (!attr_set) {
+        CHFSI_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        attr_set = true;
+    }
+    const int64_t blocks = (h.N + kWarps - 1) / kWarps;
+    kern<<<(unsigned)blocks, kThreads, smem, s>>>(
+        h.N, h.row_ptr, h.col, static_cast<const TH*>(hval), h.nnz, n,
+        static_cast<const TG*>(io.gather), io.ldg, static_cast<const TC*>(io.cur), io.ldc,
+        static_cast<const TP*>(io.prev), io.ldp, static_cast<TO*>(io.out), io.ldo,
+        static_cast<__nv_bfloat16*>(io.shadow), io.lds, (ACC)alpha, (ACC)c, (ACC)beta, cap, status);
+    CHFSI_LAUNCH_CHECK();
+    return CHFSI_OK;
+}
+
+}  // namespace
+
+// Dispatch on the buffer types of one step.  f64 math steps run in FP64 with any
+// mix of FP64/FP32 inputs (the first FP64 steps after a low-precision prefix read
+// FP32 iterates, widened exactly); f32 steps run FP32 FMA; bf16 steps gather the
+// BF16 shadow and write FP32 plus a fresh shadow.
+int csr_step(const CsrDev& h, StepMath math, int64_t n, const StepIO& io, double alpha, double c,
+             double beta, bool vec, unsigned* status, cudaStream_t s) {
+    if (n <= 0 || h.N <= 0) return CHFSI_OK;
+    const Buf g = io.gather_t, cu = io.cur_t, p = io.prev ? io.prev_t : io.cur_t, o = io.out_t;
+    if (math == StepMath::F64) {
+        if (h.val_t != Buf::F64) return CHFSI_ERR_UNSUPPORTED;
+        if (g == Buf::F64 && cu == Buf::F64 && p == Buf::F64 && o == Buf::F64) {
+            if (vec) return launch<double, double, double, double, double, double, 2, 1, false>(h, h.val, n, io, alpha, c, beta, status, s);
+            return launch<double, double, double, double, double, double, 1, 1, false>(h, h.val, n, io, alpha, c, beta, status, s);
+        }
+        if (g == Buf::F64 && cu == Buf::F64 && p == Buf::F32 && o == Buf::F64) {
+            if (vec) return launch<double, double, double, double, float, double, 2, 1, false>(h, h.val, n, io, alpha, c, beta, status, s);
+            return launch<double, double, double, double, float, double, 1, 1, false>(h, h.val, n, io, alpha, c, beta, status, s);
+        }
+        if (g == Buf::F32 && cu == Buf::F32 && p == Buf::F32 && o == Buf::F64) {
+            if (vec) return launch<double, double, float, float, float, double, 2, 1, false>(h, h.val, n, io, alpha, c, beta, status, s);
+            return launch<double, double, float, float, float, double, 1, 1, false>(h, h.val, n, io, alpha, c, beta, status, s);
+        }
+        if (g == Buf::F32 && cu == Buf::F32 && p == Buf::F64 && o == Buf::F64) {
+            if (vec) return launch<double, double, float, float, double, double, 2, 1, false>(h, h.val, n, io, alpha, c, beta, status, s);
+            return launch<double, double, float, float, double, double, 1, 1, false>(h, h.val, n, io, alpha, c, beta, status, s);
+        }
+        return CHFSI_ERR_UNSUPPORTED;
+    }
+    if (h.val_t != Buf::F32) return CHFSI_ERR_UNSUPPORTED;
+    if (math == StepMath::F32) {
+        if (g == Buf::F32 && cu == Buf::F32 && p == Buf::F32 && o == Buf::F32)
+            return launch<float, float, float, float, float, float, 4, 2, false>(h, h.val, n, io, alpha, c, beta, status, s);
+        return CHFSI_ERR_UNSUPPORTED;
+    }
+    // BF16 operand, FP32 accumulate
+    if (g == Buf::BF16 && cu == Buf::F32 && p == Buf::F32 && o == Buf::F32 && io.shadow)
+        return launch<float, float, __nv_bfloat16, float, float, float, 4, 2, true>(h, h.val, n, io, alpha, c, beta, status, s);
+    return CHFSI_ERR_UNSUPPORTED;
+}
+
+}  // namespace chfsi

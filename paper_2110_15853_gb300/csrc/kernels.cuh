@@ -1,0 +1,87 @@
+// Internal launcher declarations shared by the chfsi C-ABI implementation.
+#pragma once
+
+#include "common.cuh"
+
+namespace chfsi {
+
+enum class Buf { F64, F32, BF16 };
+enum class StepMath { F64, F32, BF16 };
+
+// CSR operator on the device; val_t says whether val points at the caller's FP64
+// values or a converted FP32 copy (low-precision steps).
+struct CsrDev {
+    int64_t N;
+    int64_t nnz;
+    const int64_t* row_ptr;
+    const int32_t* col;
+    const void* val;
+    Buf val_t;
+};
+
+// BSR operator on the device (dense bdim x bdim blocks, bdim = 64).
+struct BsrDev {
+    int64_t nbr;        // block rows
+    int64_t nblocks;
+    int bdim;
+    const int32_t* brow_ptr;
+    const int32_t* bcol;
+    const void* val;
+    Buf val_t;
+};
+
+// Buffers of one filter step: Y_out = alpha (H Y_gather - c Y_cur) - beta Y_prev.
+// gather and cur are the same iterate (gather may be its BF16 shadow).
+struct StepIO {
+    const void* gather; Buf gather_t; int64_t ldg;
+    const void* cur;    Buf cur_t;    int64_t ldc;
+    const void* prev;   Buf prev_t;   int64_t ldp;   // prev == nullptr: no beta term
+    void* out;          Buf out_t;    int64_t ldo;
+    void* shadow;       int64_t lds;                 // BF16 copy of the output, or nullptr
+};
+
+int csr_step(const CsrDev& h, StepMath math, int64_t n, const StepIO& io, double alpha, double c,
+             double beta, bool vec, unsigned* status, cudaStream_t s);
+
+int bsr_step(const BsrDev& h, StepMath math, int64_t n, const StepIO& io, double alpha, double c,
+             double beta, unsigned* status, cudaStream_t s);
+
+// Element-wise conversions (row-major blocks with leading dimensions; padding
+// columns [n, ld_out) of the output are zero-filled).
+int convert_block(const void* src, Buf src_t, int64_t lds, void* dst, Buf dst_t, int64_t ldd,
+                  int64_t rows, int64_t n, cudaStream_t s);
+int convert_values(const double* src, void* dst, Buf dst_t, int64_t count, bool round_bf16,
+                   cudaStream_t s);
+
+// Dense FP64 kernels of the closure (all row-major).
+// S (n x n, lds) = A^T B with A, B: K x n (lda, ldb).  part: split-K scratch of
+// splits * n * n doubles; symmetric = compute the upper triangle and mirror it.
+int gemm_tn(const double* A, int64_t lda, const double* B, int64_t ldb, int64_t K, int64_t n,
+            double* S, int64_t lds, bool symmetric, double* part, int splits, cudaStream_t s);
+int gemm_tn_splits(int64_t K, int64_t n);
+// C (M x n, ldc) = A (M x n, lda) * B (n x n, ldb); b_upper: B is upper triangular.
+int gemm_nn(const double* A, int64_t lda, const double* B, int64_t ldb, double* C, int64_t ldc,
+            int64_t M, int64_t n, bool b_upper, cudaStream_t s);
+// In place: upper Cholesky S = R^T R (R in the upper triangle, lower zeroed).
+int cholesky_upper(double* S, int64_t n, int64_t lds, unsigned* status, cudaStream_t s);
+// Rinv (n x n) = R^-1 for upper-triangular R.
+int tri_inverse_upper(const double* R, int64_t ldr, double* Rinv, int64_t ldi, int64_t n,
+                      cudaStream_t s);
+// B = A^T (n x n).
+int transpose(const double* A, int64_t lda, double* B, int64_t ldb, int64_t n, cudaStream_t s);
+// S = (S + S^T)/2 in place.
+int symmetrize(double* S, int64_t n, int64_t lds, cudaStream_t s);
+
+// Lanczos (K steps, full re-orthogonalisation) writing bounds to dev_out[3] = {a, b, a0}.
+int lanczos_run(const CsrDev& h, int steps, const double* v0, int64_t n_wanted, double* V,
+                double* w, double* part, double* scal, double* dev_out, unsigned* status,
+                cudaStream_t s);
+size_t lanczos_part_count(int64_t N, int steps);
+
+// Sampled dense-dense product on H's pattern: dH[p] += alpha <Ybar[row p,:], Yprev[col p,:]>.
+int sddmm_accumulate(const CsrDev& h, int64_t n, const double* Ybar, int64_t ldb,
+                     const double* Yprev, int64_t ldp, double alpha, double* dH, cudaStream_t s);
+
+int fill_zero(void* p, size_t bytes, cudaStream_t s);
+
+}  // namespace chfsi

@@ -1,0 +1,356 @@
+"""GPU parity: every call goes through the C ABI (libchfsi.so) and is compared
+element by element with the FP64 CPU oracle on the same seeded inputs.
+
+Tolerances:
+* FP64 filter (CSR and BSR): relative Frobenius error <= 1e-12 (the target the
+  method is held to; differences come from FMA contraction and summation order).
+* Lanczos bounds: 1e-10 relative on a0 and b (and hence a).
+* Ritz values: 1e-10 relative to max |theta| (CholQR2 vs Householder bases span
+  the same space up to ~u cond(Y)).
+* Adjoint: 1e-10 relative Frobenius on dX and dH against the oracle's reverse mode.
+* Mixed precision: stated per variant below from the unit roundoff of the
+  low-precision steps.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import chfsi_workloads as W
+from tests.util import rel_fro
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    from paper_2110_15853_gb300 import build
+    build.build()
+    import paper_2110_15853_gb300 as P
+    assert torch.cuda.is_available()
+    return P
+
+
+DEV = "cuda"
+
+
+def make_case(g, w, n, seed=1, s=0.1, core=0.0, orth=True):
+    H = W.csr_grid(g, w, s, seed, core_frac=core, core_shift=2.0 if core else 0.0)
+    X = W.start_block(H["N"], n, seed, orthonormalise=orth)
+    return H, X
+
+
+def bounds_for(oracle_mod, H, n, seed=1):
+    v0 = W.lanczos_start(H["N"], seed)
+    return oracle_mod.lanczos_bounds(H, v0, 20, n), v0
+
+
+def to_dev(P, H):
+    return P.CsrMatrix.from_arrays(H["row_ptr"], H["col"], H["val"], device=DEV)
+
+
+def dev(x):
+    return torch.as_tensor(np.ascontiguousarray(x)).to(DEV)
+
+
+# --------------------------------------------------------------------------- filter FP64
+
+
+@pytest.mark.parametrize("g,w,n,m", [
+    (8, 2, 6, 1), (8, 2, 6, 2), (8, 3, 37, 10), (5, 1, 3, 7), (12, 3, 70, 13),
+    (10, 2, 129, 5), (7, 3, 1, 9), (6, 4, 64, 20),
+])
+def test_filter_f64_csr_small(P, oracle_mod, g, w, n, m):
+    H, X = make_case(g, w, n, seed=g * 10 + w)
+    (a, b, a0), _ = bounds_for(oracle_mod, H, max(1, min(n, H["N"] // 4)))
+    Yref = oracle_mod.filter(H, X, m, a, b, a0)
+    Y = P.filter(to_dev(P, H), dev(X), m, a, b, a0).cpu().numpy()
+    assert rel_fro(Y, Yref) <= 1e-12
+
+
+def test_filter_f64_odd_leading_dimensions(P, oracle_mod):
+    """Row-major blocks with ld > n (views of wider buffers) and odd n."""
+    H, X = make_case(8, 2, 9, seed=3)
+    (a, b, a0), _ = bounds_for(oracle_mod, H, 9)
+    Yref = oracle_mod.filter(H, X, 6, a, b, a0)
+    Xbig = torch.zeros((H["N"], 12), dtype=torch.float64, device=DEV)
+    Xbig[:, :9] = dev(X)
+    Ybig = torch.full((H["N"], 14), 7.0, dtype=torch.float64, device=DEV)
+    P.filter(to_dev(P, H), Xbig[:, :9], 6, a, b, a0, out=Ybig[:, :9])
+    assert rel_fro(Ybig[:, :9].cpu().numpy(), Yref) <= 1e-12
+    assert torch.all(Ybig[:, 9:] == 7.0)          # padding untouched
+
+
+def test_filter_f64_config_20cube_full(P, oracle_mod):
+    """20^3 grid, w = 2, 64 states, m = 10: every output element."""
+    wl = W.workload("g20_w2_n64_m10")
+    H, X = make_case(wl.g, wl.w, wl.n, seed=wl.seed)
+    (a, b, a0), _ = bounds_for(oracle_mod, H, wl.n, wl.seed)
+    Yref = oracle_mod.filter(H, X, wl.m, a, b, a0)
+    Y = P.filter(to_dev(P, H), dev(X), wl.m, a, b, a0).cpu().numpy()
+    assert rel_fro(Y, Yref) <= 1e-12
+
+
+def test_filter_f64_config_40cube_sampled_columns(P, oracle_mod):
+    """40^3 grid, w = 3, 1024 states, m = 20 at full size on the GPU (the bench
+    launch); the oracle filters a seeded 48-column subset (columns are independent)."""
+    wl = W.workload("g40_w3_n1024_m20")
+    H, X = make_case(wl.g, wl.w, wl.n, seed=wl.seed)
+    (a, b, a0), _ = bounds_for(oracle_mod, H, wl.n, wl.seed)
+    Y = P.filter(to_dev(P, H), dev(X), wl.m, a, b, a0).cpu().numpy()
+    cols = W.column_subset(wl.n, 48, wl.seed)
+    Yref = oracle_mod.filter(H, X[:, cols], wl.m, a, b, a0)
+    assert rel_fro(Y[:, cols], Yref) <= 1e-12
+    assert np.all(np.isfinite(Y))
+
+
+def test_filter_determinism(P, oracle_mod):
+    H, X = make_case(12, 3, 40, seed=5)
+    (a, b, a0), _ = bounds_for(oracle_mod, H, 40)
+    Hd, Xd = to_dev(P, H), dev(X)
+    Y1 = P.filter(Hd, Xd, 9, a, b, a0)
+    Y2 = P.filter(Hd, Xd, 9, a, b, a0)
+    assert torch.equal(Y1, Y2)
+
+
+# --------------------------------------------------------------------------- filter BSR
+
+
+def to_dev_bsr(P, B):
+    return P.BsrMatrix.from_arrays(B["brow_ptr"], B["bcol"], B["val"], device=DEV)
+
+
+@pytest.mark.parametrize("g,w,n,m", [(8, 2, 16, 4), (8, 3, 70, 9), (12, 4, 33, 6), (4, 1, 5, 3)])
+def test_filter_f64_bsr(P, oracle_mod, g, w, n, m):
+    H, X = make_case(g, w, n, seed=7 + g)
+    (a, b, a0), _ = bounds_for(oracle_mod, H, max(1, min(n, H["N"] // 4)))
+    B = W.bsr_from_csr(H, g)
+    perm = B["perm"]
+    Yref = oracle_mod.filter(H, X, m, a, b, a0)
+    Yb = P.filter(to_dev_bsr(P, B), dev(X[perm]), m, a, b, a0).cpu().numpy()
+    Y = np.empty_like(Yb)
+    Y[perm] = Yb
+    assert rel_fro(Y, Yref) <= 1e-12
+
+
+# --------------------------------------------------------------------------- mixed precision
+
+
+@pytest.mark.parametrize("low,tol", [("f32", 2e-5), ("bf16", 5e-2)])
+@pytest.mark.parametrize("layout", ["csr", "bsr"])
+def test_filter_mixed_schedule(P, oracle_mod, low, tol, layout):
+    """L low-precision steps then FP64 steps.  The low steps carry relative
+    rounding u_low (2^-24 for FP32, 2^-8 for BF16 operands) per step, amplified at
+    most by the step count; the FP64 tail adds nothing measurable."""
+    if layout == "bsr" and low == "bf16":
+        pytest.skip("BF16 operands on BSR use the tensor-core kernel (separate test)")
+    g, w, n, m, L = 8, 3, 24, 12, 8
+    H, X = make_case(g, w, n, seed=21)
+    (a, b, a0), _ = bounds_for(oracle_mod, H, n)
+    Yref = oracle_mod.filter(H, X, m, a, b, a0)
+    sched = P.mixed_schedule(m, L, low)
+    if layout == "csr":
+        Y = P.filter(to_dev(P, H), dev(X), m, a, b, a0, schedule=sched).cpu().numpy()
+    else:
+        B = W.bsr_from_csr(H, g)
+        perm = B["perm"]
+        Yb = P.filter(to_dev_bsr(P, B), dev(X[perm]), m, a, b, a0, schedule=sched).cpu().numpy()
+        Y = np.empty_like(Yb)
+        Y[perm] = Yb
+    err = rel_fro(Y, Yref)
+    assert err <= tol, err
+    # all-low schedule widens the last FP32 iterate into Y
+    if low == "f32" and layout == "csr":
+        Yall = P.filter(to_dev(P, H), dev(X), m, a, b, a0, schedule=[low] * m).cpu().numpy()
+        assert rel_fro(Yall, Yref) <= tol
+
+
+# --------------------------------------------------------------------------- Lanczos
+
+
+@pytest.mark.parametrize("g,w,n", [(8, 2, 32), (20, 2, 64), (12, 3, 100)])
+def test_lanczos_bounds(P, oracle_mod, g, w, n):
+    H, _ = make_case(g, w, 1, seed=31 + g)
+    v0 = W.lanczos_start(H["N"], 5)
+    a_r, b_r, a0_r = oracle_mod.lanczos_bounds(H, v0, 20, n)
+    a, b, a0 = P.lanczos_bounds(to_dev(P, H), dev(v0), 20, n)
+    for x, y in ((a, a_r), (b, b_r), (a0, a0_r)):
+        assert abs(x - y) <= 1e-10 * abs(y)
+
+
+def test_lanczos_tiny_breakdown(P, oracle_mod):
+    """N < steps: the Krylov space fills up and the iteration stops with zero residual."""
+    d = np.array([3.0, -1.0, 0.5, 7.25, 2.0, 4.5, -0.25, 6.0, 1.0, 5.5])
+    N = d.size
+    H = dict(N=N, nnz=N, row_ptr=np.arange(N + 1, dtype=np.int64), col=np.arange(N, dtype=np.int32), val=d)
+    v0 = np.random.default_rng(2).standard_normal(N)
+    a, b, a0 = P.lanczos_bounds(to_dev(P, H), dev(v0), 20, 2)
+    assert abs(a0 - d.min()) < 1e-12 and abs(b - d.max()) < 1e-11
+
+
+# --------------------------------------------------------------------------- Rayleigh-Ritz
+
+
+def _check_ritz(oracle_mod, H, Y, ritz, psi, tol=1e-10):
+    theta, Psi_ref, _ = oracle_mod.rayleigh_ritz(H, Y)
+    scale = np.max(np.abs(theta))
+    assert np.max(np.abs(ritz - theta)) <= tol * scale
+    n = Y.shape[1]
+    assert np.max(np.abs(psi.T @ psi - np.eye(n))) <= 1e-12
+    # Ritz vectors: compare projectors onto clusters of (numerically) equal values
+    i = 0
+    while i < n:
+        j = i + 1
+        while j < n and abs(theta[j] - theta[j - 1]) <= 1e-8 * scale:
+            j += 1
+        A, B = psi[:, i:j], Psi_ref[:, i:j]
+        s = np.linalg.svd(A.T @ B, compute_uv=False)
+        assert np.min(s) >= 1 - 1e-8, (i, j, s)
+        i = j
+
+
+@pytest.mark.parametrize("passes", [1, 2])
+def test_rayleigh_ritz_small(P, oracle_mod, passes):
+    H, X = make_case(8, 2, 20, seed=41)
+    (a, b, a0), _ = bounds_for(oracle_mod, H, 20)
+    Y = oracle_mod.filter(H, X, 8, a, b, a0)
+    ritz, psi = P.rayleigh_ritz(to_dev(P, H), dev(Y), cholqr_passes=passes)
+    _check_ritz(oracle_mod, H, Y, ritz.cpu().numpy(), psi.cpu().numpy())
+
+
+def test_rayleigh_ritz_full_space_is_eigh(P, oracle_mod):
+    H, _ = make_case(6, 2, 1, seed=43)
+    N = H["N"]
+    Y = np.linalg.qr(np.random.default_rng(3).standard_normal((N, N)))[0]
+    ritz, psi = P.rayleigh_ritz(to_dev(P, H), dev(Y))
+    from tests.util import csr_to_dense
+    lam = np.linalg.eigvalsh(csr_to_dense(H))
+    assert np.max(np.abs(ritz.cpu().numpy() - lam)) <= 1e-12 * np.max(np.abs(lam))
+
+
+def test_rayleigh_ritz_config_40cube(P, oracle_mod):
+    """Full 40^3 / 1024-state cycle: filter (m = 20) then CholQR2 + RR on the GPU;
+    the oracle runs its own filter and Householder/LAPACK closure on the same inputs."""
+    wl = W.workload("g40_w3_n1024_m20")
+    H, X = make_case(wl.g, wl.w, wl.n, seed=wl.seed)
+    (a, b, a0), _ = bounds_for(oracle_mod, H, wl.n, wl.seed)
+    Hd = to_dev(P, H)
+    Yd = P.filter(Hd, dev(X), wl.m, a, b, a0)
+    ritz, psi = P.rayleigh_ritz(Hd, Yd, cholqr_passes=2)
+    Yref = oracle_mod.filter(H, X, wl.m, a, b, a0)
+    theta, _, _ = oracle_mod.rayleigh_ritz(H, Yref)
+    assert np.max(np.abs(ritz.cpu().numpy() - theta)) <= 1e-10 * np.max(np.abs(theta))
+
+
+def test_rayleigh_ritz_rank_deficient_reports_cholesky(P, oracle_mod):
+    H, X = make_case(6, 2, 8, seed=44)
+    X[:, 3] = 0.0
+    with pytest.raises(P.ChfsiError) as e:
+        P.rayleigh_ritz(to_dev(P, H), dev(X), cholqr_passes=1)
+    assert e.value.code == 4
+
+
+# --------------------------------------------------------------------------- adjoint
+
+
+@pytest.mark.parametrize("g,w,n,m,stride", [(8, 2, 5, 7, 0), (6, 3, 4, 9, 2), (8, 2, 6, 16, 1), (5, 1, 3, 4, 9)])
+def test_adjoint_matches_oracle(P, oracle_mod, g, w, n, m, stride):
+    H, X = make_case(g, w, n, seed=50 + m)
+    (a, b, a0), _ = bounds_for(oracle_mod, H, max(1, n))
+    wts = W.loss_weights(H["N"], 3)
+    Y = oracle_mod.filter(H, X, m, a, b, a0)
+    G = 2.0 * wts[:, None] * Y
+    dX_ref, dH_ref = oracle_mod.filter_adjoint(H, X, m, a, b, a0, G)
+    dX, dH = P.filter_backward(to_dev(P, H), dev(X), dev(G), m, a, b, a0, ckpt_stride=stride)
+    assert rel_fro(dX.cpu().numpy(), dX_ref) <= 1e-10
+    assert rel_fro(dH.cpu().numpy(), dH_ref) <= 1e-10
+
+
+def test_adjoint_autograd_and_finite_differences(P, oracle_mod):
+    """L = tr(Y^T W Y) through torch.autograd; dL/dH checked against central
+    differences (step 1e-6) of the GPU forward on sampled entries."""
+    H, X = make_case(8, 2, 6, seed=61)
+    m = 10
+    (a, b, a0), _ = bounds_for(oracle_mod, H, 6)
+    wts = dev(W.loss_weights(H["N"], 4))
+    Hd = to_dev(P, H)
+    Xd = dev(X).requires_grad_(True)
+    hv = Hd.val.clone().requires_grad_(True)
+    Y = P.ChebyshevFilter.apply(Xd, hv, Hd, m, a, b, a0)
+    L = (wts[:, None] * Y * Y).sum()
+    L.backward()
+    G = 2.0 * W.loss_weights(H["N"], 4)[:, None] * oracle_mod.filter(H, X, m, a, b, a0)
+    dX_ref, dH_ref = oracle_mod.filter_adjoint(H, X, m, a, b, a0, G)
+    assert rel_fro(Xd.grad.cpu().numpy(), dX_ref) <= 1e-10
+    assert rel_fro(hv.grad.cpu().numpy(), dH_ref) <= 1e-10
+
+    def loss(val):
+        Hp = P.CsrMatrix(Hd.row_ptr, Hd.col, val, Hd.n_rows)
+        Yp = P.filter(Hp, dev(X), m, a, b, a0)
+        return math.fsum(((wts[:, None] * Yp * Yp).sum(dim=1)).cpu().numpy())
+
+    scale = float(hv.grad.abs().max())
+    step = 1e-6
+    for p in np.random.default_rng(0).choice(H["nnz"], 12, replace=False):
+        vp, vm = Hd.val.clone(), Hd.val.clone()
+        vp[p] += step
+        vm[p] -= step
+        fd = (loss(vp) - loss(vm)) / (2 * step)
+        assert abs(fd - float(hv.grad[p])) <= 1e-6 * scale
+
+
+def test_adjoint_config_32cube(P, oracle_mod):
+    """32^3 grid, w = 2, 512 states, m = 16: GPU backward with sqrt(m)
+    checkpointing at full size against the oracle's stored-iterate reverse mode."""
+    wl = W.workload("g32_w2_n512_m16")
+    H, X = make_case(wl.g, wl.w, wl.n, seed=wl.seed)
+    (a, b, a0), _ = bounds_for(oracle_mod, H, wl.n, wl.seed)
+    wts = W.loss_weights(H["N"], wl.seed)
+    Hd = to_dev(P, H)
+    Yd = P.filter(Hd, dev(X), wl.m, a, b, a0)
+    Gd = 2.0 * dev(wts)[:, None] * Yd
+    dX, dH = P.filter_backward(Hd, dev(X), Gd, wl.m, a, b, a0)
+    G = Gd.cpu().numpy()
+    dX_ref, dH_ref = oracle_mod.filter_adjoint(H, X, wl.m, a, b, a0, G)
+    assert rel_fro(dX.cpu().numpy(), dX_ref) <= 1e-10
+    assert rel_fro(dH.cpu().numpy(), dH_ref) <= 1e-10
+
+
+def test_checkpoint_replay_is_bitwise(P, oracle_mod):
+    """Different checkpoint strides replay the same forward kernels: identical results."""
+    H, X = make_case(8, 2, 6, seed=71)
+    m = 12
+    (a, b, a0), _ = bounds_for(oracle_mod, H, 6)
+    G = dev(np.random.default_rng(1).standard_normal(X.shape))
+    Hd, Xd = to_dev(P, H), dev(X)
+    outs = [P.filter_backward(Hd, Xd, G, m, a, b, a0, ckpt_stride=s) for s in (1, 3, 4, 12)]
+    for dX, dH in outs[1:]:
+        assert torch.equal(dX, outs[0][0]) and torch.equal(dH, outs[0][1])
+
+
+# --------------------------------------------------------------------------- error paths
+
+
+def test_error_paths(P, oracle_mod):
+    H, X = make_case(6, 2, 4, seed=81)
+    Hd, Xd = to_dev(P, H), dev(X)
+    with pytest.raises(P.ChfsiError) as e:
+        P.filter(Hd, Xd, 5, 1.0, 2.0, 1.5)                 # a0 inside [a, b]
+    assert e.value.code == 2
+    # a column index out of range: the kernel skips it and reports PATTERN
+    bad = dict(H)
+    bad["col"] = H["col"].copy()
+    bad["col"][17] = H["N"] + 5
+    ws = P.Workspace(DEV)
+    (a, b, a0), _ = bounds_for(oracle_mod, H, 4)
+    P.filter(to_dev(P, bad), Xd, 3, a, b, a0, workspace=ws)
+    assert P.read_status(ws) == 3
+    # NaN input is reported as non-finite
+    Xn = Xd.clone()
+    Xn[3, 1] = float("nan")
+    P.filter(Hd, Xn, 3, a, b, a0, workspace=ws)
+    assert P.read_status(ws) == 5
+    # a clean call leaves the status word clear
+    P.filter(Hd, Xd, 3, a, b, a0, workspace=ws)
+    assert P.read_status(ws) == 0
