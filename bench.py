@@ -54,6 +54,10 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--cpu-cols", type=int, default=64)
+    ap.add_argument("--cols", type=int, default=0, help="override the workload's state count n")
+    ap.add_argument("--filter-only", action="store_true",
+                    help="set up, run one FP64 filter (m launches of the CSR step) and exit: a profiling case")
+    ap.add_argument("--schedule", default="f64", help="filter-only schedule: f64 | f32:L | bf16:L")
     return ap.parse_args()
 
 
@@ -168,8 +172,11 @@ def committed_traffic(workload):
 # ---------------------------------------------------------------- workload setup
 
 
-def setup_workload(name):
+def setup_workload(name, cols=0):
     wl = W.workload(name)
+    if cols:
+        import dataclasses
+        wl = dataclasses.replace(wl, n=int(cols))
     H = W.csr_grid(wl.g, wl.w, wl.s, wl.seed, core_frac=wl.core_frac, core_shift=wl.core_shift)
     X = W.start_block(H["N"], wl.n, wl.seed)
     v0 = W.lanczos_start(H["N"], wl.seed)
@@ -256,8 +263,10 @@ def run_ours(args):
         dist.barrier()
     lib = P.load()
 
-    wl, H, X, v0 = setup_workload(args.workload)
+    wl, H, X, v0 = setup_workload(args.workload, args.cols)
     N, n, m, nnz = H["N"], wl.n, wl.m, H["nnz"]
+    if args.filter_only:
+        return run_filter_only(P, torch, dev, wl, H, X, v0, args)
     Hd = P.CsrMatrix.from_arrays(H["row_ptr"], H["col"], H["val"], device=dev)
     Xd = torch.as_tensor(X).to(dev)
     v0d = torch.as_tensor(v0).to(dev)
@@ -391,6 +400,25 @@ def run_ours(args):
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
+    return 0
+
+
+def run_filter_only(P, torch, dev, wl, H, X, v0, args):
+    """One filter call on the resident workload (a small, self-ending ncu case)."""
+    Hd = P.CsrMatrix.from_arrays(H["row_ptr"], H["col"], H["val"], device=dev)
+    Xd = torch.as_tensor(X).to(dev)
+    a, b, a0 = P.lanczos_bounds(Hd, torch.as_tensor(v0).to(dev), 20, wl.n)
+    sched = None
+    if args.schedule != "f64":
+        low, L = args.schedule.split(":")
+        sched = P.mixed_schedule(wl.m, int(L), low)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    Y = P.filter(Hd, Xd, wl.m, a, b, a0, schedule=sched)
+    e1.record()
+    torch.cuda.synchronize(dev)
+    print(json.dumps({"filter_only": True, "workload": wl.name, "n": wl.n, "schedule": args.schedule,
+                      "ms": e0.elapsed_time(e1), "finite": bool(torch.isfinite(Y).all().item())}))
     return 0
 
 

@@ -141,6 +141,28 @@ int chfsi_filter(const chfsi_matrix* H, const double* X, int64_t ldx, double* Y,
                  int64_t n_cols, int32_t m, double a, double b, double a0,
                  const chfsi_schedule* sched, void* ws, size_t ws_bytes, void* stream);
 
+/*
+ * chfsi_filter without a caller workspace, for callers that cannot allocate
+ * device memory (a host whose own allocator owns the whole device, and which
+ * must not call cudaMalloc/cudaFree or pass scratch pointers).  The paper has no
+ * counterpart; this is a deployment convenience.
+ *
+ * Same arguments and result as chfsi_filter minus ws/ws_bytes.  The scratch is a
+ * 16 MiB array in the library's device memory (held by every GPU that loads the
+ * library until the process exits).  Problems whose chfsi_filter_workspace_size
+ * exceeds 16 MiB are rejected with CHFSI_ERR_NOMEM (FP64 schedule: about
+ * 2 * N * round_up(n_cols, 8) * 8 bytes, e.g. N = 8000 with 64 columns fits).
+ * The first call on each device looks up the array's device address (with that
+ * device current); make that first call before any stream capture.  Nothing is
+ * allocated.  All calls share the one array: calls that overlap on the GPU (other
+ * streams, other threads) race and must be serialised by the caller.  The status
+ * word kept in the array is cleared at the start of each call and is not readable
+ * through chfsi_read_status.
+ */
+int chfsi_filter_noalloc(const chfsi_matrix* H, const double* X, int64_t ldx, double* Y,
+                         int64_t ldy, int64_t n_cols, int32_t m, double a, double b, double a0,
+                         const chfsi_schedule* sched, void* stream);
+
 /* ------------------------------------------------------------------ adjoint of the filter */
 
 int chfsi_filter_backward_workspace_size(const chfsi_matrix* H, int64_t n_cols, int32_t m,
