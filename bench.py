@@ -464,23 +464,49 @@ def measure_variants(P, torch, dev, stream, wl, H, Hd, Xd, bounds):
             "ms": t, "gflops": fl / (t * 1e-3) / 1e9, "speedup_vs_f64": out["filter_csr_f64"]["ms"] / t,
             "ritz_max_rel_err_vs_f64": rel, "y_rel_fro_err_vs_f64": yerr}
         del Ym
-    # BSR layout of the same operator
+    # BSR layout of the same operator, and the hybrid (blocked CSR + BSR) operator
     try:
         B = W.bsr_from_csr(H, wl.g)
         Bd = P.BsrMatrix.from_arrays(B["brow_ptr"], B["bcol"], B["val"], device=dev)
+        Hpd = P.CsrMatrix.from_arrays(**{k: v for k, v in W.permute_csr(H, B["perm"]).items()
+                                         if k in ("row_ptr", "col", "val")}, device=dev)
+        Hy = P.HybridMatrix(Hpd, Bd)
         perm = torch.as_tensor(B["perm"]).to(dev)
         Xp = Xd[perm].contiguous()
         Yb = torch.empty_like(Xp)
-        t = timeit(lambda: P.filter(Bd, Xp, m, a, b, a0, out=Yb, workspace=ws), reps=1)
         Yback = torch.empty_like(Yb)
-        Yback[perm] = Yb
-        err = float(torch.linalg.norm(Yback - Yref) / torch.linalg.norm(Yref))
+
+        def err_vs_ref():
+            Yback[perm] = Yb
+            return float(torch.linalg.norm(Yback - Yref) / torch.linalg.norm(Yref))
+
+        def ritz_err():
+            Yback[perm] = Yb
+            th, _ = P.rayleigh_ritz(Hd, Yback, 2, workspace=rr_ws)
+            return float(np.max(np.abs(th.cpu().numpy() - theta_ref)) / np.max(np.abs(theta_ref)))
+
+        t = timeit(lambda: P.filter(Bd, Xp, m, a, b, a0, out=Yb, workspace=ws), reps=1)
         out["filter_bsr_f64"] = {"ms": t, "gflops": fl / (t * 1e-3) / 1e9,
                                  "executed_gflop": m * 2.0 * B["n_blocks"] * 64 * 64 * n / 1e9,
-                                 "y_rel_fro_err_vs_csr": err}
-        del Bd, Xp, Yb, Yback
+                                 "y_rel_fro_err_vs_csr": err_vs_ref()}
+        t = timeit(lambda: P.filter(Hy, Xp, m, a, b, a0, out=Yb, workspace=ws))
+        out["filter_csr_blocked_order_f64"] = {"ms": t, "gflops": fl / (t * 1e-3) / 1e9,
+                                               "y_rel_fro_err_vs_csr": err_vs_ref()}
+        sched = ["bf16"] * m
+        t = timeit(lambda: P.filter(Bd, Xp, m, a, b, a0, schedule=sched, out=Yb, workspace=ws))
+        out["filter_bsr_bf16_tc_all_steps"] = {
+            "ms": t, "ms_per_step": t / m, "gflops": fl / (t * 1e-3) / 1e9,
+            "executed_tflops": m * 2.0 * B["n_blocks"] * 64 * 64 * n / (t * 1e-3) / 1e12,
+            "y_rel_fro_err_vs_f64": err_vs_ref()}
+        for low, L in (("bf16", m - 4), ("f32", m - 4), ("f32", m // 2)):
+            sched = P.mixed_schedule(m, L, low)
+            t = timeit(lambda: P.filter(Hy, Xp, m, a, b, a0, schedule=sched, out=Yb, workspace=ws))
+            out[f"filter_hybrid_{low}x{L}_f64x{m - L}"] = {
+                "ms": t, "gflops": fl / (t * 1e-3) / 1e9, "speedup_vs_f64": out["filter_csr_f64"]["ms"] / t,
+                "y_rel_fro_err_vs_f64": err_vs_ref(), "ritz_max_rel_err_vs_f64": ritz_err()}
+        del Bd, Xp, Yb, Yback, Hpd, Hy
     except Exception as e:  # noqa: BLE001 - report, do not hide
-        out["filter_bsr_f64"] = {"error": repr(e)}
+        out["bsr_variants_error"] = repr(e)
     return out
 
 

@@ -36,7 +36,7 @@ import numpy as np
 __all__ = [
     "Workload", "WORKLOADS", "workload", "offsets", "csr_grid", "blocked_permutation",
     "bsr_from_csr", "gaussian", "start_block", "lanczos_start", "loss_weights",
-    "row_subset", "column_subset",
+    "row_subset", "column_subset", "permute_csr",
 ]
 
 SEED_BASE = 2110158530
@@ -199,6 +199,25 @@ def bsr_from_csr(csr: dict, g: int, bs: int = 4) -> dict:
     val[block_of * bdim * bdim + (r_new % bdim) * bdim + (c_new % bdim)] = csr["val"]
     return dict(perm=perm, n_block_rows=nbr, n_blocks=int(nblocks), bdim=bdim,
                 brow_ptr=brow_ptr.astype(np.int32), bcol=ub_c.astype(np.int32), val=val)
+
+
+def permute_csr(csr: dict, perm: np.ndarray) -> dict:
+    """CSR of P H P^T: row r of the result is row perm[r] of H, columns renumbered
+    to the new order and sorted ascending (pure data movement)."""
+    N = csr["N"]
+    inv = np.empty_like(perm)
+    inv[perm] = np.arange(N, dtype=np.int64)
+    counts = np.diff(csr["row_ptr"])[perm]
+    row_ptr = np.zeros(N + 1, dtype=np.int64)
+    np.cumsum(counts, out=row_ptr[1:])
+    starts = csr["row_ptr"][perm]
+    idx = np.repeat(starts - row_ptr[:-1], counts) + np.arange(row_ptr[-1], dtype=np.int64)
+    cols = inv[csr["col"][idx].astype(np.int64)]
+    vals = csr["val"][idx]
+    rows = np.repeat(np.arange(N, dtype=np.int64), counts)
+    order = np.lexsort((cols, rows))
+    return dict(N=N, nnz=int(row_ptr[-1]), row_ptr=row_ptr, col=cols[order].astype(np.int32),
+                val=vals[order].copy())
 
 
 def gaussian(shape, seed: int, stream: int) -> np.ndarray:

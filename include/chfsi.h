@@ -63,6 +63,7 @@ int chfsi_version(void);
 /* ------------------------------------------------------------------ operator H */
 #define CHFSI_CSR 0
 #define CHFSI_BSR 1
+#define CHFSI_HYBRID 2   /* both layouts of one operator, rows in the blocked order (see below) */
 
 /*
  * Sparse symmetric H (the projected Kohn-Sham Hamiltonian H^L of Sec. 3.3,
@@ -94,8 +95,14 @@ typedef struct {
     const double* val;
 } chfsi_bsr;
 
+/*
+ * kind = CHFSI_CSR uses `csr`, CHFSI_BSR uses `bsr`.  CHFSI_HYBRID carries the
+ * same operator in both layouts with the CSR rows in the blocked order: FP64 and
+ * FP32 steps (and the backward pass, the Lanczos bounds and the projection) use
+ * the CSR kernels, BF16-operand steps use the BSR blocks on the tensor cores.
+ */
 typedef struct {
-    int32_t kind;      /* CHFSI_CSR or CHFSI_BSR */
+    int32_t kind;      /* CHFSI_CSR, CHFSI_BSR or CHFSI_HYBRID */
     chfsi_csr csr;
     chfsi_bsr bsr;
 } chfsi_matrix;
@@ -180,7 +187,7 @@ int chfsi_filter_backward_workspace_size(const chfsi_matrix* H, int64_t n_cols, 
  * for H^T (H must be symmetric; the paper's Eq. "transpose_equal" is the same
  * fact).  Forward iterates are kept only every ckpt_stride steps (as pairs
  * Y_{s-1}, Y_s; 0 selects ceil(sqrt(m))) and the rest are recomputed per segment.
- * dH_val may be NULL (then only dX).  CSR operators only.
+ * dH_val may be NULL (then only dX).  Needs the CSR layout (CHFSI_CSR or CHFSI_HYBRID).
  */
 int chfsi_filter_backward(const chfsi_matrix* H, const double* X, int64_t ldx,
                           const double* dY, int64_t lddy, double* dX, int64_t lddx,
@@ -224,7 +231,7 @@ int chfsi_lanczos_workspace_size(const chfsi_matrix* H, int32_t steps, size_t* b
  *   a  = a0 + (b - a0) (n_wanted / N)^(2/3).
  * Breakdown (beta_j <= 1e-12 times the largest |alpha_i| + beta_{i-1} so far)
  * stops early with a zero residual.  a, b, a0 are HOST pointers; the call
- * synchronises `stream`.  1 <= n_wanted < N.
+ * synchronises `stream`.  1 <= n_wanted < N.  Needs the CSR layout (CHFSI_CSR or CHFSI_HYBRID).
  */
 int chfsi_lanczos_bounds(const chfsi_matrix* H, int32_t steps, const double* v0,
                          int64_t n_wanted, double* a, double* b, double* a0, void* ws,

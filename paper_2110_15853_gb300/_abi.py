@@ -24,6 +24,7 @@ CHFSI_ERR_UNSUPPORTED = 9
 
 CHFSI_CSR = 0
 CHFSI_BSR = 1
+CHFSI_HYBRID = 2
 
 CHFSI_F64 = 0
 CHFSI_F32 = 1

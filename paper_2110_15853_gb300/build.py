@@ -22,7 +22,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libchfsi.so")
 
-SOURCES = ["api.cu", "filter_csr.cu", "filter_bsr.cu", "dense.cu", "lanczos.cu", "adjoint.cu", "noalloc.cu"]
+SOURCES = ["api.cu", "filter_csr.cu", "filter_bsr.cu", "dense.cu", "lanczos.cu", "adjoint.cu", "noalloc.cu", "filter_bsr_tc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

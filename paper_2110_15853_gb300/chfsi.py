@@ -104,6 +104,33 @@ class BsrMatrix:
         return m
 
 
+@dataclass
+class HybridMatrix:
+    """One operator in both layouts (CSR rows in the blocked order of the BSR):
+    FP64/FP32 steps use the CSR, BF16-operand steps the BSR blocks on tensor cores."""
+    csr: CsrMatrix
+    bsr: BsrMatrix
+
+    @property
+    def n_rows(self) -> int:
+        return self.csr.n_rows
+
+    @property
+    def nnz(self) -> int:
+        return self.csr.nnz
+
+    @property
+    def device(self) -> torch.device:
+        return self.csr.device
+
+    def descriptor(self, val: Optional[torch.Tensor] = None) -> _abi.chfsi_matrix:
+        m = _abi.chfsi_matrix()
+        m.kind = _abi.CHFSI_HYBRID
+        m.csr = self.csr.descriptor(val).csr
+        m.bsr = self.bsr.descriptor().bsr
+        return m
+
+
 class Workspace:
     """Grow-only device scratch buffer (allocate once, outside timed loops)."""
 

@@ -31,29 +31,43 @@ inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 
 
 inline int64_t pad8(int64_t n) { return (n + 7) / 8 * 8; }
 
-int rows_of(const chfsi_matrix* H, int64_t* N) {
-    if (!H) return CHFSI_ERR_ARG;
-    if (H->kind == CHFSI_CSR) {
-        const chfsi_csr& c = H->csr;
-        if (c.n_rows <= 0 || c.nnz < 0 || c.nnz > INT64_C(0x7fffffffffff)) return CHFSI_ERR_ARG;
-        if (c.n_rows > INT32_MAX) return CHFSI_ERR_ARG;
-        if (!c.row_ptr || (c.nnz > 0 && (!c.col || !c.val))) return CHFSI_ERR_ARG;
-        *N = c.n_rows;
-        return CHFSI_OK;
-    }
-    if (H->kind == CHFSI_BSR) {
-        const chfsi_bsr& b = H->bsr;
-        if (b.bdim != 64 || b.n_block_rows <= 0 || b.n_blocks < 0) return CHFSI_ERR_ARG;
-        if (!b.brow_ptr || (b.n_blocks > 0 && (!b.bcol || !b.val))) return CHFSI_ERR_ARG;
-        if (b.n_block_rows * 64 > INT32_MAX) return CHFSI_ERR_ARG;
-        *N = b.n_block_rows * b.bdim;
-        return CHFSI_OK;
-    }
-    return CHFSI_ERR_ARG;
+int check_csr(const chfsi_csr& c) {
+    if (c.n_rows <= 0 || c.nnz < 0 || c.nnz > INT64_C(0x7fffffffffff)) return CHFSI_ERR_ARG;
+    if (c.n_rows > INT32_MAX) return CHFSI_ERR_ARG;
+    if (!c.row_ptr || (c.nnz > 0 && (!c.col || !c.val))) return CHFSI_ERR_ARG;
+    return CHFSI_OK;
 }
 
-int64_t stored_values(const chfsi_matrix* H) {
-    return H->kind == CHFSI_CSR ? H->csr.nnz : H->bsr.n_blocks * (int64_t)H->bsr.bdim * H->bsr.bdim;
+int check_bsr(const chfsi_bsr& b) {
+    if (b.bdim != 64 || b.n_block_rows <= 0 || b.n_blocks < 0) return CHFSI_ERR_ARG;
+    if (!b.brow_ptr || (b.n_blocks > 0 && (!b.bcol || !b.val))) return CHFSI_ERR_ARG;
+    if (b.n_block_rows * 64 > INT32_MAX) return CHFSI_ERR_ARG;
+    return CHFSI_OK;
+}
+
+inline bool has_csr(const chfsi_matrix* H) { return H->kind == CHFSI_CSR || H->kind == CHFSI_HYBRID; }
+inline bool has_bsr(const chfsi_matrix* H) { return H->kind == CHFSI_BSR || H->kind == CHFSI_HYBRID; }
+
+int rows_of(const chfsi_matrix* H, int64_t* N) {
+    if (!H) return CHFSI_ERR_ARG;
+    if (H->kind != CHFSI_CSR && H->kind != CHFSI_BSR && H->kind != CHFSI_HYBRID) return CHFSI_ERR_ARG;
+    int rc;
+    if (has_csr(H) && (rc = check_csr(H->csr))) return rc;
+    if (has_bsr(H) && (rc = check_bsr(H->bsr))) return rc;
+    if (H->kind == CHFSI_HYBRID && H->csr.n_rows != H->bsr.n_block_rows * H->bsr.bdim) return CHFSI_ERR_ARG;
+    *N = has_csr(H) ? H->csr.n_rows : H->bsr.n_block_rows * H->bsr.bdim;
+    return CHFSI_OK;
+}
+
+int64_t bsr_values(const chfsi_matrix* H) { return H->bsr.n_blocks * (int64_t)H->bsr.bdim * H->bsr.bdim; }
+
+// Values of H converted for the low-precision steps (FP32 copy for CUDA-core
+// steps, BF16 blocks for tensor-core steps): size of the larger candidate.
+int64_t low_values(const chfsi_matrix* H) {
+    int64_t v = 0;
+    if (has_csr(H)) v = H->csr.nnz;
+    if (has_bsr(H) && bsr_values(H) > v) v = bsr_values(H);
+    return v;
 }
 
 int check_bounds(double a, double b, double a0) {
@@ -142,18 +156,18 @@ struct SizeOnly {
     }
 };
 
+// FP64 and FP32 steps run on the CSR operator when one is given (CHFSI_CSR or
+// CHFSI_HYBRID), otherwise on the BSR blocks with the CUDA-core kernel.
 int run_step(const chfsi_matrix* H, const CsrDev& csr, const BsrDev& bsr, StepMath math, int64_t n,
              const StepIO& io, double alpha, double c, double beta, bool vec, unsigned* st, cudaStream_t s) {
-    if (H->kind == CHFSI_CSR) return csr_step(csr, math, n, io, alpha, c, beta, vec, st, s);
+    if (has_csr(H)) return csr_step(csr, math, n, io, alpha, c, beta, vec, st, s);
     return bsr_step(bsr, math, n, io, alpha, c, beta, st, s);
 }
 
-void make_devs(const chfsi_matrix* H, const void* val, Buf vt, CsrDev* csr, BsrDev* bsr) {
-    if (H->kind == CHFSI_CSR) {
-        *csr = CsrDev{H->csr.n_rows, H->csr.nnz, H->csr.row_ptr, H->csr.col, val, vt};
-    } else {
-        *bsr = BsrDev{H->bsr.n_block_rows, H->bsr.n_blocks, H->bsr.bdim, H->bsr.brow_ptr, H->bsr.bcol, val, vt};
-    }
+void make_devs(const chfsi_matrix* H, const void* csr_val, const void* bsr_val, Buf vt, CsrDev* csr, BsrDev* bsr) {
+    if (has_csr(H)) *csr = CsrDev{H->csr.n_rows, H->csr.nnz, H->csr.row_ptr, H->csr.col, csr_val, vt};
+    if (has_bsr(H))
+        *bsr = BsrDev{H->bsr.n_block_rows, H->bsr.n_blocks, H->bsr.bdim, H->bsr.brow_ptr, H->bsr.bcol, bsr_val, vt};
 }
 
 // cuSOLVER handle per device, created on first use.
@@ -234,7 +248,7 @@ int chfsi_filter_workspace_size(const chfsi_matrix* H, int64_t n_cols, int32_t m
     rc = schedule_prefix(sched, m, &L, &low);
     if (rc) return rc;
     SizeOnly sz;
-    filter_layout(sz, N, n_cols, m, L, low, stored_values(H), nullptr);
+    filter_layout(sz, N, n_cols, m, L, low, low_values(H), nullptr);
     *bytes = sz.used;
     return CHFSI_OK;
 }
@@ -254,11 +268,11 @@ int chfsi_filter(const chfsi_matrix* H, const double* X, int64_t ldx, double* Y,
     if ((rc = schedule_prefix(sched, m, &L, &low))) return rc;
     if (!ws || !aligned16(ws)) return CHFSI_ERR_ARG;
     SizeOnly sz;
-    filter_layout(sz, N, n_cols, m, L, low, stored_values(H), nullptr);
+    filter_layout(sz, N, n_cols, m, L, low, low_values(H), nullptr);
     if (ws_bytes < sz.used) return CHFSI_ERR_NOMEM;
     Arena ar(ws, ws_bytes);
     FilterLayout fl;
-    filter_layout(ar, N, n_cols, m, L, low, stored_values(H), &fl);
+    filter_layout(ar, N, n_cols, m, L, low, low_values(H), &fl);
 
     cudaStream_t s = as_stream(stream);
     unsigned* st = status_word(ws);
@@ -272,8 +286,7 @@ int chfsi_filter(const chfsi_matrix* H, const double* X, int64_t ldx, double* Y,
 
     CsrDev csr64{}, csrlo{};
     BsrDev bsr64{}, bsrlo{};
-    const void* hval64 = H->kind == CHFSI_CSR ? (const void*)H->csr.val : (const void*)H->bsr.val;
-    make_devs(H, hval64, Buf::F64, &csr64, &bsr64);
+    make_devs(H, H->csr.val, H->bsr.val, Buf::F64, &csr64, &bsr64);
 
     // FP64 iterate k lives in cyc[(m - k) % 3], so that Y_m lands in Y.
     double* cyc[3] = {Y, fl.W[0], fl.W[1]};
@@ -281,12 +294,25 @@ int chfsi_filter(const chfsi_matrix* H, const double* X, int64_t ldx, double* Y,
     auto f64_buf = [&](int k) { return cyc[(m - k) % 3]; };
     auto f64_ld = [&](int k) { return cyc_ld[(m - k) % 3]; };
 
-    if (L > 0) {
+    if (L > 0 && has_bsr(H) && low == CHFSI_BF16_F32ACC) {
+        // tensor-core path: BF16 blocks, state-major BF16 iterate copies
+        if ((rc = bsr_values_to_bf16(H->bsr.val, fl.hlow, bsr_values(H), s))) return rc;
+        make_devs(H, nullptr, fl.hlow, Buf::BF16, &csrlo, &bsrlo);
+        if ((rc = convert_block(X, Buf::F64, ldx, fl.F[0], Buf::F32, ldw, N, n, s))) return rc;
+        if ((rc = transpose_to_bf16(X, ldx, fl.S[0], N, n, s))) return rc;
+        for (int k = 1; k <= L; k++) {
+            const float* prev = k >= 2 ? fl.F[(k - 2) % 3] : nullptr;
+            rc = bsr_step_tc(bsrlo, n, fl.S[(k - 1) % 2], fl.F[(k - 1) % 3], ldw, prev, ldw, fl.F[k % 3], ldw,
+                             fl.S[k % 2], al[k], c, k >= 2 ? be[k] : 0.0, st, s);
+            if (rc) return rc;
+        }
+        if (L == m) return convert_block(fl.F[m % 3], Buf::F32, ldw, Y, Buf::F64, ldy, N, n, s);
+    } else if (L > 0) {
         const bool bf = low == CHFSI_BF16_F32ACC;
-        rc = convert_values(hval64 ? static_cast<const double*>(hval64) : nullptr, fl.hlow, Buf::F32,
-                            stored_values(H), bf, s);
+        if (has_csr(H)) rc = convert_values(H->csr.val, fl.hlow, Buf::F32, H->csr.nnz, bf, s);
+        else rc = convert_values(H->bsr.val, fl.hlow, Buf::F32, bsr_values(H), bf, s);
         if (rc) return rc;
-        make_devs(H, fl.hlow, Buf::F32, &csrlo, &bsrlo);
+        make_devs(H, fl.hlow, fl.hlow, Buf::F32, &csrlo, &bsrlo);
         if ((rc = convert_block(X, Buf::F64, ldx, fl.F[0], Buf::F32, ldw, N, n, s))) return rc;
         if (bf && (rc = convert_block(X, Buf::F64, ldx, fl.S[0], Buf::BF16, ldw, N, n, s))) return rc;
         const StepMath lm = bf ? StepMath::BF16 : StepMath::F32;
@@ -363,7 +389,7 @@ int chfsi_filter_backward_workspace_size(const chfsi_matrix* H, int64_t n_cols, 
     int64_t N = 0;
     int rc = rows_of(H, &N);
     if (rc) return rc;
-    if (H->kind != CHFSI_CSR) return CHFSI_ERR_UNSUPPORTED;
+    if (!has_csr(H)) return CHFSI_ERR_UNSUPPORTED;
     if (n_cols < 0 || m < 1 || ckpt_stride < 0) return CHFSI_ERR_ARG;
     SizeOnly sz;
     back_layout(sz, N, n_cols, m, ckpt_stride, nullptr);
@@ -377,7 +403,7 @@ int chfsi_filter_backward(const chfsi_matrix* H, const double* X, int64_t ldx, c
     int64_t N = 0;
     int rc = rows_of(H, &N);
     if (rc) return rc;
-    if (H->kind != CHFSI_CSR) return CHFSI_ERR_UNSUPPORTED;
+    if (!has_csr(H)) return CHFSI_ERR_UNSUPPORTED;
     if (n_cols < 0 || m < 1 || ckpt_stride < 0) return CHFSI_ERR_ARG;
     if ((rc = check_bounds(a, b, a0))) return rc;
     cudaStream_t s = as_stream(stream);
@@ -572,8 +598,7 @@ int chfsi_rayleigh_ritz(const chfsi_matrix* H, const double* Y, int64_t ldy, int
     {
         CsrDev csr{};
         BsrDev bsr{};
-        const void* hval = H->kind == CHFSI_CSR ? (const void*)H->csr.val : (const void*)H->bsr.val;
-        make_devs(H, hval, Buf::F64, &csr, &bsr);
+        make_devs(H, H->csr.val, H->bsr.val, Buf::F64, &csr, &bsr);
         StepIO io{};
         io.cur = XF; io.cur_t = Buf::F64; io.ldc = ldw;
         io.gather = XF; io.gather_t = Buf::F64; io.ldg = ldw;
@@ -613,7 +638,7 @@ int chfsi_lanczos_workspace_size(const chfsi_matrix* H, int32_t steps, size_t* b
     int64_t N = 0;
     int rc = rows_of(H, &N);
     if (rc) return rc;
-    if (H->kind != CHFSI_CSR) return CHFSI_ERR_UNSUPPORTED;
+    if (!has_csr(H)) return CHFSI_ERR_UNSUPPORTED;
     if (steps < 1 || steps > 64) return CHFSI_ERR_ARG;
     SizeOnly sz;
     sz.take<unsigned char>(kStatusBytes);
@@ -631,7 +656,7 @@ int chfsi_lanczos_bounds(const chfsi_matrix* H, int32_t steps, const double* v0,
     int64_t N = 0;
     int rc = rows_of(H, &N);
     if (rc) return rc;
-    if (H->kind != CHFSI_CSR) return CHFSI_ERR_UNSUPPORTED;
+    if (!has_csr(H)) return CHFSI_ERR_UNSUPPORTED;
     if (steps < 1 || steps > 64 || !v0 || !a || !b || !a0 || n_wanted < 1 || n_wanted >= N) return CHFSI_ERR_ARG;
     if (!ws || !aligned16(ws)) return CHFSI_ERR_ARG;
     size_t need = 0;

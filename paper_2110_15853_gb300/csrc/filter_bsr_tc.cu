@@ -1,0 +1,338 @@
+// BSR filter step on the 5th-generation tensor cores (tcgen05, BF16 operands,
+// FP32 accumulation in tensor memory), for the low-precision prefix of the
+// filter schedule (Algorithm 1 step 1, Sec. 3.4; the dense-block treatment of H
+// follows the dense diagonal blocks of Sec. 4.1-4.2):
+//
+//     Y_out[R] = alpha (sum_{(R,C)} H_RC Y_cur[C] - c Y_cur[R]) - beta Y_prev[R]
+//
+// computed transposed, so that both MMA operands are K-major: for a block row R
+// (64 grid points) and a tile of 128 states j,
+//     D[j][i] = sum_C sum_k Ysh^T[j][C*64 + k] * H_RC[i][k]      (M = 128, N = 64, K = 64/block)
+// where Ysh^T is the BF16 copy of Y_cur stored state-major (n x N).  The epilogue
+// reads D from TMEM, applies the recurrence in FP32 against the FP32 iterates and
+// writes Y_out (FP32, row-major) plus its BF16 state-major copy for the next step.
+//
+// CTA = 6 warps: warp 0 lane 0 issues TMA loads (128B-swizzled tiles of Ysh^T and
+// H_RC) into a 4-stage ring, warp 1 owns the TMEM allocation and lane 0 issues the
+// MMAs, warps 2-5 run the epilogue (warp w reads TMEM lanes 32*(w%4)..+31).  Every
+// wait is bounded (1 s on %globaltimer); on timeout the CTA flags DEV_TIMEOUT,
+// stops issuing work, waits (bounded) for its copies in flight, frees TMEM and exits.
+#include <cuda.h>
+
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace chfsi {
+
+namespace {
+
+constexpr int kStages = 4;
+constexpr int kTileJ = 128;                       // states per CTA (MMA M)
+constexpr int kBlk = 64;                          // block edge (MMA N and K per block)
+constexpr int kATile = kTileJ * kBlk * 2;         // 16 KB
+constexpr int kBTile = kBlk * kBlk * 2;           // 8 KB
+constexpr int kStageBytes = kATile + kBTile;      // 24 KB
+constexpr int kThreads = 192;
+constexpr uint32_t kTmemCols = 64;
+constexpr uint64_t kTimeoutNs = 1000000000ull;
+
+__device__ __forceinline__ uint32_t sa(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t gtime() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Bounded wait for the phase of `parity` on an mbarrier; false on timeout.
+__device__ bool mbar_wait(uint32_t addr, uint32_t parity) {
+    const uint64_t t0 = gtime();
+    while (true) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(done) : "r"(addr), "r"(parity) : "memory");
+        if (done) return true;
+        if (gtime() - t0 > kTimeoutNs) return false;
+    }
+}
+
+// UMMA shared-memory descriptor: K-major operand, 128-byte swizzle (rows of 64
+// BF16, 8-row atoms of 1024 B), as written by TMA with CU_TENSOR_MAP_SWIZZLE_128B.
+__device__ __forceinline__ uint64_t desc_sw128(uint32_t addr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr & 0x3FFFF) >> 4);   // start address
+    d |= (uint64_t)1 << 16;                   // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)(1024 >> 4) << 32;         // stride byte offset: 8-row atom
+    d |= (uint64_t)1 << 46;                   // descriptor version
+    d |= (uint64_t)2 << 61;                   // 128-byte swizzle
+    return d;
+}
+
+// Instruction descriptor: kind::f16, BF16 x BF16 -> FP32, both K-major, M = 128, N = 64.
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kBlk >> 3) << 17) |
+                            ((uint32_t)(kTileJ >> 4) << 24);
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+        :: "r"(dst), "l"((uint64_t)map), "r"(x), "r"(y), "r"(bar) : "memory");
+}
+
+__global__ void __launch_bounds__(kThreads, 2)
+bsr_tc_kernel(const __grid_constant__ CUtensorMap tmY, const __grid_constant__ CUtensorMap tmH,
+              int64_t nbr, const int32_t* __restrict__ brow_ptr, const int32_t* __restrict__ bcol, int64_t nblocks,
+              int64_t N, int64_t n, const float* __restrict__ Yc, int64_t ldc, const float* __restrict__ Yp,
+              int64_t ldp, float* __restrict__ Yo, int64_t ldo, __nv_bfloat16* __restrict__ Ysh_out,
+              float alpha, float c, float beta, unsigned* status) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    __shared__ __align__(8) uint64_t full_bar[kStages], empty_bar[kStages], accum_bar;
+    __shared__ uint32_t tmem_slot;
+    __shared__ int abort_flag;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t R = blockIdx.x;
+    const int64_t j0 = (int64_t)blockIdx.y * kTileJ;
+
+    int qb = brow_ptr[R], qe = brow_ptr[R + 1];
+    bool bad = false;
+    if (qb < 0) { qb = 0; bad = true; }
+    if (qe > nblocks) { qe = (int)nblocks; bad = true; }
+    if (qe < qb) { qe = qb; bad = true; }
+    const int count = qe - qb;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; s++) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(sa(&full_bar[s])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(sa(&empty_bar[s])));
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(sa(&accum_bar)));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+        asm volatile("fence.proxy.async.shared::cta;");
+        abort_flag = 0;
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" :: "r"(sa(&tmem_slot)),
+                     "r"(kTmemCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = tmem_slot;
+
+    if (warp == 0 && lane == 0) {
+        // ---------------- TMA producer
+        int it = 0;
+        for (; it < count; it++) {
+            const int s = it % kStages;
+            if (it >= kStages) {
+                if (!mbar_wait(sa(&empty_bar[s]), ((it / kStages) - 1) & 1)) {
+                    atomicExch(&abort_flag, 1);
+                    break;
+                }
+            }
+            if (*(volatile int*)&abort_flag) break;
+            int C = bcol[qb + it];
+            if (C < 0 || (int64_t)C >= nbr) { bad = true; C = 0; }   // zero-safe: still a valid tile
+            const uint32_t st = sa(smem + (size_t)s * kStageBytes);
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(sa(&full_bar[s])),
+                         "r"(kStageBytes));
+            tma_load_2d(st, &tmY, C * kBlk, (int)j0, sa(&full_bar[s]));
+            tma_load_2d(st + kATile, &tmH, 0, (qb + it) * kBlk, sa(&full_bar[s]));
+        }
+        // wait (bounded) until every copy this thread issued has landed
+        const int issued = it;
+        for (int s = 0; s < kStages && s < issued; s++) {
+            const int last = s + ((issued - 1 - s) / kStages) * kStages;
+            mbar_wait(sa(&full_bar[s]), (last / kStages) & 1);
+        }
+    } else if (warp == 1 && lane == 0) {
+        // ---------------- MMA issuer
+        int it = 0;
+        for (; it < count; it++) {
+            const int s = it % kStages;
+            if (!mbar_wait(sa(&full_bar[s]), (it / kStages) & 1) || *(volatile int*)&abort_flag) {
+                atomicExch(&abort_flag, 1);
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            const uint32_t st = sa(smem + (size_t)s * kStageBytes);
+            const uint64_t da = desc_sw128(st), db = desc_sw128(st + kATile);
+#pragma unroll
+            for (int k = 0; k < kBlk / 16; k++) {
+                const uint32_t acc = (it > 0 || k > 0) ? 1u : 0u;
+                asm volatile(
+                    "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n"
+                    :: "r"(tmem), "l"(da + 2 * k), "l"(db + 2 * k), "r"(kIdesc), "r"(acc));
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                         :: "r"(sa(&empty_bar[s])));
+        }
+        // accumulator complete (also covers the zero-block case: commit with nothing pending)
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                     :: "r"(sa(&accum_bar)));
+        mbar_wait(sa(&accum_bar), 0);
+    } else if (warp >= 2) {
+        // ---------------- epilogue
+        const int quad = warp & 3;
+        const int64_t j = j0 + quad * 32 + lane;
+        const bool ok = mbar_wait(sa(&accum_bar), 0) && !*(volatile int*)&abort_flag;
+        if (!ok) atomicExch(&abort_flag, 1);
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        bool nonfinite = false;
+        const int64_t row0 = R * kBlk;
+#pragma unroll 1
+        for (int cchunk = 0; cchunk < kBlk / 16; cchunk++) {
+            uint32_t r[16];
+            const uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(cchunk * 16);
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                  "=r"(r[15])
+                : "r"(taddr));
+            asm volatile("tcgen05.wait::ld.sync.aligned;");
+            if (!ok || j >= n) continue;
+            float out[16];
+#pragma unroll
+            for (int t = 0; t < 16; t++) {
+                const int64_t row = row0 + cchunk * 16 + t;
+                const float acc = (count > 0) ? __uint_as_float(r[t]) : 0.0f;
+                const float yc = Yc[row * ldc + j];
+                float v = alpha * fmaf(-c, yc, acc);
+                if (Yp) v = fmaf(-beta, Yp[row * ldp + j], v);
+                nonfinite |= !isfinite(v);
+                Yo[row * ldo + j] = v;
+                out[t] = v;
+            }
+            // 16 consecutive rows of state j -> two 16-byte stores of the state-major copy
+            uint4 pk[2];
+            unsigned* pw = reinterpret_cast<unsigned*>(pk);
+#pragma unroll
+            for (int t = 0; t < 8; t++) {
+                __nv_bfloat162 h2 = __floats2bfloat162_rn(out[2 * t], out[2 * t + 1]);
+                pw[t] = *reinterpret_cast<unsigned*>(&h2);
+            }
+            uint4* dst = reinterpret_cast<uint4*>(Ysh_out + j * N + row0 + cchunk * 16);
+            dst[0] = pk[0];
+            dst[1] = pk[1];
+        }
+        if (nonfinite) raise_status(status, DEV_NONFINITE);
+    }
+
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 1) {
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(kTmemCols));
+    }
+    if (threadIdx.x == 0) {
+        if (abort_flag) raise_status(status, DEV_TIMEOUT);
+    }
+    if (bad) raise_status(status, DEV_PATTERN);
+}
+
+// BF16 copy of FP64 block values (rounded through FP32).
+__global__ void blocks_to_bf16_kernel(const double* __restrict__ src, __nv_bfloat16* dst, int64_t count) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < count) dst[i] = __float2bfloat16_rn((float)src[i]);
+}
+
+// State-major BF16 copy of a row-major FP64 block: dst[j * N + r] = bf16(src[r * lds + j]).
+__global__ void transpose_to_bf16_kernel(const double* __restrict__ src, int64_t lds, __nv_bfloat16* dst, int64_t N,
+                                         int64_t n) {
+    __shared__ float t[32][33];
+    const int64_t r0 = (int64_t)blockIdx.x * 32, j0 = (int64_t)blockIdx.y * 32;
+    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+        const int64_t r = r0 + k, j = j0 + threadIdx.x;
+        t[k][threadIdx.x] = (r < N && j < n) ? (float)src[r * lds + j] : 0.0f;
+    }
+    __syncthreads();
+    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+        const int64_t j = j0 + k, r = r0 + threadIdx.x;
+        if (j < n && r < N) dst[j * N + r] = __float2bfloat16_rn(t[threadIdx.x][k]);
+    }
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    }
+    return fn;
+}
+
+// 2-D BF16 tensor map over a row-major [rows x cols] array, box [box_rows x 64].
+int make_map(CUtensorMap* map, const void* base, int64_t cols, int64_t rows, int box_rows) {
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) return CHFSI_ERR_CUDA;
+    if ((reinterpret_cast<uintptr_t>(base) & 15u) || ((cols * 2) % 16)) return CHFSI_ERR_ARG;
+    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
+    cuuint32_t box[2] = {64, (cuuint32_t)box_rows};
+    cuuint32_t es[2] = {1, 1};
+    CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, es,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? CHFSI_OK : CHFSI_ERR_CUDA;
+}
+
+}  // namespace
+
+int bsr_values_to_bf16(const double* src, void* dst, int64_t count, cudaStream_t s) {
+    if (count <= 0) return CHFSI_OK;
+    blocks_to_bf16_kernel<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(src, static_cast<__nv_bfloat16*>(dst),
+                                                                         count);
+    CHFSI_LAUNCH_CHECK();
+    return CHFSI_OK;
+}
+
+int transpose_to_bf16(const double* src, int64_t lds, void* dst, int64_t N, int64_t n, cudaStream_t s) {
+    if (N <= 0 || n <= 0) return CHFSI_OK;
+    dim3 grid((unsigned)((N + 31) / 32), (unsigned)((n + 31) / 32));
+    transpose_to_bf16_kernel<<<grid, dim3(32, 8), 0, s>>>(src, lds, static_cast<__nv_bfloat16*>(dst), N, n);
+    CHFSI_LAUNCH_CHECK();
+    return CHFSI_OK;
+}
+
+// One BF16-operand BSR step on the tensor cores.  h.val must point at BF16
+// blocks; ysh_in / ysh_out are state-major (n x N) BF16 copies of Y_cur / Y_out.
+int bsr_step_tc(const BsrDev& h, int64_t n, const void* ysh_in, const float* Yc, int64_t ldc, const float* Yp,
+                int64_t ldp, float* Yo, int64_t ldo, void* ysh_out, double alpha, double c, double beta,
+                unsigned* status, cudaStream_t s) {
+    if (n <= 0 || h.nbr <= 0) return CHFSI_OK;
+    if (h.bdim != kBlk || h.val_t != Buf::BF16) return CHFSI_ERR_UNSUPPORTED;
+    const int64_t N = h.nbr * kBlk;
+    if (h.nblocks * kBlk > INT32_MAX || N > INT32_MAX || n > INT32_MAX) return CHFSI_ERR_UNSUPPORTED;
+    CUtensorMap tmY, tmH;
+    int rc = make_map(&tmY, ysh_in, N, n, kTileJ);
+    if (rc) return rc;
+    rc = make_map(&tmH, h.val, kBlk, h.nblocks * kBlk, kBlk);
+    if (rc) return rc;
+    const size_t smem = (size_t)kStages * kStageBytes + 1024;
+    static bool attr = false;
+    if (!attr) {
+        CHFSI_CUDA_TRY(cudaFuncSetAttribute(bsr_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        attr = true;
+    }
+    dim3 grid((unsigned)h.nbr, (unsigned)((n + kTileJ - 1) / kTileJ));
+    bsr_tc_kernel<<<grid, kThreads, smem, s>>>(tmY, tmH, h.nbr, h.brow_ptr, h.bcol, h.nblocks, N, n, Yc, ldc, Yp, ldp,
+                                               Yo, ldo, static_cast<__nv_bfloat16*>(ysh_out), (float)alpha, (float)c,
+                                               (float)beta, status);
+    CHFSI_LAUNCH_CHECK();
+    return CHFSI_OK;
+}
+
+}  // namespace chfsi

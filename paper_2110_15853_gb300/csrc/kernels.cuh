@@ -46,6 +46,14 @@ int csr_step(const CsrDev& h, StepMath math, int64_t n, const StepIO& io, double
 int bsr_step(const BsrDev& h, StepMath math, int64_t n, const StepIO& io, double alpha, double c,
              double beta, unsigned* status, cudaStream_t s);
 
+// Tensor-core (tcgen05) BF16-operand BSR step; h.val holds BF16 blocks, the BF16
+// iterate copies ysh_in / ysh_out are state-major (n x N).
+int bsr_step_tc(const BsrDev& h, int64_t n, const void* ysh_in, const float* Yc, int64_t ldc, const float* Yp,
+                int64_t ldp, float* Yo, int64_t ldo, void* ysh_out, double alpha, double c, double beta,
+                unsigned* status, cudaStream_t s);
+int bsr_values_to_bf16(const double* src, void* dst, int64_t count, cudaStream_t s);
+int transpose_to_bf16(const double* src, int64_t lds, void* dst, int64_t N, int64_t n, cudaStream_t s);
+
 // Element-wise conversions (row-major blocks with leading dimensions; padding
 // columns [n, ld_out) of the output are zero-filled).
 int convert_block(const void* src, Buf src_t, int64_t lds, void* dst, Buf dst_t, int64_t ldd,

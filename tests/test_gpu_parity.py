@@ -143,8 +143,6 @@ def test_filter_mixed_schedule(P, oracle_mod, low, tol, layout):
     """L low-precision steps then FP64 steps.  The low steps carry relative
     rounding u_low (2^-24 for FP32, 2^-8 for BF16 operands) per step, amplified at
     most by the step count; the FP64 tail adds nothing measurable."""
-    if layout == "bsr" and low == "bf16":
-        pytest.skip("BF16 operands on BSR use the tensor-core kernel (separate test)")
     g, w, n, m, L = 8, 3, 24, 12, 8
     H, X = make_case(g, w, n, seed=21)
     (a, b, a0), _ = bounds_for(oracle_mod, H, n)
@@ -164,6 +162,71 @@ def test_filter_mixed_schedule(P, oracle_mod, low, tol, layout):
     if low == "f32" and layout == "csr":
         Yall = P.filter(to_dev(P, H), dev(X), m, a, b, a0, schedule=[low] * m).cpu().numpy()
         assert rel_fro(Yall, Yref) <= tol
+
+
+@pytest.mark.parametrize("g,w,n,m,L", [(8, 3, 200, 9, 6), (12, 4, 128, 7, 7), (4, 1, 5, 4, 2), (8, 2, 64, 5, 5)])
+def test_bsr_tensor_core_bf16_matches_csr_bf16(P, oracle_mod, g, w, n, m, L):
+    """tcgen05 BSR steps (BF16 operands, FP32 accumulation in TMEM) against the
+    CUDA-core CSR steps with the same BF16 rounding of H and of Y_k: the two
+    differ only in FP32 accumulation order (tolerance 20 u_fp32 per step, times
+    the BF16 re-rounding it can flip), and both against the FP64 oracle."""
+    H, X = make_case(g, w, n, seed=90 + g + n)
+    (a, b, a0), _ = bounds_for(oracle_mod, H, max(1, min(n, H["N"] // 4)))
+    sched = P.mixed_schedule(m, L, "bf16")
+    Yc = P.filter(to_dev(P, H), dev(X), m, a, b, a0, schedule=sched).cpu().numpy()
+    B = W.bsr_from_csr(H, g)
+    perm = B["perm"]
+    ws = P.Workspace(DEV)
+    Yb = P.filter(to_dev_bsr(P, B), dev(X[perm]), m, a, b, a0, schedule=sched, workspace=ws).cpu().numpy()
+    assert P.read_status(ws) == 0
+    Y = np.empty_like(Yb)
+    Y[perm] = Yb
+    assert np.all(np.isfinite(Y))
+    assert rel_fro(Y, Yc) <= 2e-2
+    Yref = oracle_mod.filter(H, X, m, a, b, a0)
+    assert rel_fro(Y, Yref) <= 5e-2
+
+
+@pytest.mark.parametrize("low", ["bf16", "f32"])
+def test_hybrid_operator_mixed_schedule(P, oracle_mod, low):
+    """CHFSI_HYBRID: BF16 prefix on the BSR blocks (tensor cores) or FP32 prefix on
+    the blocked-order CSR, then the FP64 tail on the CSR; the backward pass and the
+    bounds also accept the hybrid operator (they use its CSR)."""
+    g, w, n, m, L = 8, 3, 70, 12, 8
+    H, X = make_case(g, w, n, seed=23)
+    (a, b, a0), v0 = bounds_for(oracle_mod, H, n)
+    B = W.bsr_from_csr(H, g)
+    perm = B["perm"]
+    Hp = W.permute_csr(H, perm)
+    Hy = P.HybridMatrix(to_dev(P, Hp), to_dev_bsr(P, B))
+    Yref = oracle_mod.filter(H, X, m, a, b, a0)
+    Yb = P.filter(Hy, dev(X[perm]), m, a, b, a0, schedule=P.mixed_schedule(m, L, low)).cpu().numpy()
+    Y = np.empty_like(Yb)
+    Y[perm] = Yb
+    assert rel_fro(Y, Yref) <= (5e-2 if low == "bf16" else 2e-5)
+    Y64 = P.filter(Hy, dev(X[perm]), m, a, b, a0).cpu().numpy()
+    Y[perm] = Y64
+    assert rel_fro(Y, Yref) <= 1e-12
+    a2, b2, a02 = P.lanczos_bounds(Hy, dev(v0[perm]), 20, n)
+    assert abs(a02 - a0) <= 1e-9 * abs(a0) and abs(b2 - b) <= 1e-9 * abs(b)
+
+
+def test_bsr_tensor_core_single_step_exact_products(P, oracle_mod):
+    """m = 1 with BF16-representable H and X: every product and every partial sum
+    is exact in FP32, so the tensor-core step equals the oracle to FP32 rounding
+    of the result."""
+    g, w, n = 8, 2, 136
+    H = W.csr_grid(g, w, 0.0, 3)
+    H["val"] = np.round(H["val"] * 64) / 64             # few-bit values: exact in BF16
+    Xr = np.random.default_rng(5).integers(-8, 9, size=(H["N"], n)) / 8.0
+    a0, a, b = 1.0, 3.5, 14.0
+    Yref = oracle_mod.filter(H, Xr, 1, a, b, a0)
+    B = W.bsr_from_csr(H, g)
+    perm = B["perm"]
+    Yb = P.filter(to_dev_bsr(P, B), dev(Xr[perm]), 1, a, b, a0, schedule=["bf16"]).cpu().numpy()
+    Y = np.empty_like(Yb)
+    Y[perm] = Yb
+    assert rel_fro(Y, Yref) <= 1e-6
 
 
 # --------------------------------------------------------------------------- Lanczos
