@@ -112,6 +112,9 @@ typedef struct {
 #define CHFSI_F32 1           /* FP32 storage, FP32 FMA, FP64-computed coefficients    */
 #define CHFSI_BF16_F32ACC 2   /* BF16 copy of Y_k as the product operand, FP32 accumulate,
                                  FP32 storage of the iterates                           */
+#define CHFSI_F32X2 3         /* two-float: values as hi + lo FP32 pairs (about 48 bits),
+                                 FP32-pipe arithmetic with error-free transformations;
+                                 CSR layout (CHFSI_CSR or CHFSI_HYBRID) only            */
 
 /*
  * Per-step precision of the filter: step_prec[k-1] is the precision of the step
@@ -216,6 +219,22 @@ int chfsi_rayleigh_ritz_workspace_size(const chfsi_matrix* H, int64_t n_cols,
 int chfsi_rayleigh_ritz(const chfsi_matrix* H, const double* Y, int64_t ldy, int64_t n_cols,
                         double* Psi, int64_t ldpsi, double* ritz, int32_t cholqr_passes,
                         void* ws, size_t ws_bytes, void* stream);
+
+int chfsi_rayleigh_ritz_ex_workspace_size(const chfsi_matrix* H, int64_t n_cols,
+                                          int32_t cholqr_passes, int32_t precision, size_t* bytes);
+
+/*
+ * chfsi_rayleigh_ritz with a choice of arithmetic for the three large products
+ * (Gram / projection A^T B over N, X_F = Y R^-1, Psi = X_F Q) and H X_F:
+ * precision = CHFSI_F64 (the same as chfsi_rayleigh_ritz) or CHFSI_F32X2
+ * (two-float products on the FP32 pipe, about 48 significant bits; needs the CSR
+ * layout).  The Cholesky factorisation, the triangular inverse and the
+ * eigensolve stay FP64 in both.  Same arguments, errors and synchronisation as
+ * chfsi_rayleigh_ritz.
+ */
+int chfsi_rayleigh_ritz_ex(const chfsi_matrix* H, const double* Y, int64_t ldy, int64_t n_cols,
+                           double* Psi, int64_t ldpsi, double* ritz, int32_t cholqr_passes,
+                           int32_t precision, void* ws, size_t ws_bytes, void* stream);
 
 /* ------------------------------------------------------------------ spectral bounds */
 

@@ -29,6 +29,7 @@ CHFSI_HYBRID = 2
 CHFSI_F64 = 0
 CHFSI_F32 = 1
 CHFSI_BF16_F32ACC = 2
+CHFSI_F32X2 = 3
 
 _i32, _i64, _dbl, _vp, _sz = ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_void_p, ctypes.c_size_t
 
@@ -66,6 +67,8 @@ SIGNATURES = {
                                              _dbl, _i32, _vp, _sz, _vp]),
     "chfsi_rayleigh_ritz_workspace_size": (ctypes.c_int, [_MP, _i64, _i32, _SZP]),
     "chfsi_rayleigh_ritz": (ctypes.c_int, [_MP, _vp, _i64, _i64, _vp, _i64, _vp, _i32, _vp, _sz, _vp]),
+    "chfsi_rayleigh_ritz_ex_workspace_size": (ctypes.c_int, [_MP, _i64, _i32, _i32, _SZP]),
+    "chfsi_rayleigh_ritz_ex": (ctypes.c_int, [_MP, _vp, _i64, _i64, _vp, _i64, _vp, _i32, _i32, _vp, _sz, _vp]),
     "chfsi_lanczos_workspace_size": (ctypes.c_int, [_MP, _i32, _SZP]),
     "chfsi_lanczos_bounds": (ctypes.c_int, [_MP, _i32, _vp, _i64, _DP, _DP, _DP, _vp, _sz, _vp]),
     "chfsi_read_status": (ctypes.c_int, [_vp, _vp]),

@@ -23,9 +23,10 @@ import numpy as np
 import torch
 
 from . import _abi
-from ._abi import (CHFSI_BF16_F32ACC, CHFSI_BSR, CHFSI_CSR, CHFSI_F32, CHFSI_F64, ChfsiError, check, load)
+from ._abi import (CHFSI_BF16_F32ACC, CHFSI_BSR, CHFSI_CSR, CHFSI_F32, CHFSI_F32X2, CHFSI_F64, ChfsiError, check,
+                   load)
 
-PRECISIONS = {"f64": CHFSI_F64, "f32": CHFSI_F32, "bf16": CHFSI_BF16_F32ACC}
+PRECISIONS = {"f64": CHFSI_F64, "f32": CHFSI_F32, "bf16": CHFSI_BF16_F32ACC, "f32x2": CHFSI_F32X2}
 
 
 def _ptr(t: Optional[torch.Tensor]) -> Optional[int]:
@@ -219,17 +220,22 @@ def filter_backward(H: CsrMatrix, X: torch.Tensor, dY: torch.Tensor, m: int, a: 
     return dX, dH
 
 
-def rayleigh_ritz_workspace_bytes(H, n_cols: int, cholqr_passes: int = 2) -> int:
+def rayleigh_ritz_workspace_bytes(H, n_cols: int, cholqr_passes: int = 2, precision: str = "f64") -> int:
     sz = ctypes.c_size_t(0)
     desc = H.descriptor()
-    check(load().chfsi_rayleigh_ritz_workspace_size(ctypes.byref(desc), n_cols, cholqr_passes, ctypes.byref(sz)),
-          "chfsi_rayleigh_ritz_workspace_size")
+    check(load().chfsi_rayleigh_ritz_ex_workspace_size(ctypes.byref(desc), n_cols, cholqr_passes,
+                                                       PRECISIONS[precision], ctypes.byref(sz)),
+          "chfsi_rayleigh_ritz_ex_workspace_size")
     return sz.value
 
 
 def rayleigh_ritz(H, Y: torch.Tensor, cholqr_passes: int = 2, psi: Optional[torch.Tensor] = None,
-                  ritz: Optional[torch.Tensor] = None, workspace: Optional[Workspace] = None):
-    """(ritz ascending, Psi) from Algorithm 1 steps 2-5 (CholQR, projection, eig, rotation)."""
+                  ritz: Optional[torch.Tensor] = None, workspace: Optional[Workspace] = None,
+                  precision: str = "f64"):
+    """(ritz ascending, Psi) from Algorithm 1 steps 2-5 (CholQR, projection, eig, rotation).
+
+    precision "f64" runs every product in FP64 (chfsi_rayleigh_ritz); "f32x2" runs
+    the large products in two-float arithmetic (chfsi_rayleigh_ritz_ex)."""
     _check_block(Y, "Y")
     N, n = Y.shape
     if psi is None:
@@ -238,10 +244,15 @@ def rayleigh_ritz(H, Y: torch.Tensor, cholqr_passes: int = 2, psi: Optional[torc
         ritz = torch.empty(n, dtype=torch.float64, device=Y.device)
     lib = load()
     desc = H.descriptor()
-    ws = (workspace or Workspace(Y.device)).get(rayleigh_ritz_workspace_bytes(H, n, cholqr_passes))
-    rc = lib.chfsi_rayleigh_ritz(ctypes.byref(desc), _ptr(Y), Y.stride(0), n, _ptr(psi), psi.stride(0), _ptr(ritz),
-                                 cholqr_passes, _ptr(ws), ws.numel(), _stream_handle(Y.device))
-    check(rc, "chfsi_rayleigh_ritz")
+    ws = (workspace or Workspace(Y.device)).get(rayleigh_ritz_workspace_bytes(H, n, cholqr_passes, precision))
+    args = (ctypes.byref(desc), _ptr(Y), Y.stride(0), n, _ptr(psi), psi.stride(0), _ptr(ritz), cholqr_passes)
+    if precision == "f64":
+        rc = lib.chfsi_rayleigh_ritz(*args, _ptr(ws), ws.numel(), _stream_handle(Y.device))
+        check(rc, "chfsi_rayleigh_ritz")
+    else:
+        rc = lib.chfsi_rayleigh_ritz_ex(*args, PRECISIONS[precision], _ptr(ws), ws.numel(),
+                                        _stream_handle(Y.device))
+        check(rc, "chfsi_rayleigh_ritz_ex")
     return ritz, psi
 
 

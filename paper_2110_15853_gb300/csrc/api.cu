@@ -111,7 +111,7 @@ int schedule_prefix(const chfsi_schedule* sched, int m, int* L, int* low_kind) {
     int k = 0;
     while (k < m && sched->step_prec[k] != CHFSI_F64) {
         int p = sched->step_prec[k];
-        if (p != CHFSI_F32 && p != CHFSI_BF16_F32ACC) return CHFSI_ERR_ARG;
+        if (p != CHFSI_F32 && p != CHFSI_BF16_F32ACC && p != CHFSI_F32X2) return CHFSI_ERR_ARG;
         if (k > 0 && p != *low_kind) return CHFSI_ERR_ARG;
         *low_kind = p;
         k++;
@@ -127,6 +127,7 @@ struct FilterLayout {
     void* hlow = nullptr;
     float* F[3] = {nullptr, nullptr, nullptr};
     __nv_bfloat16* S[2] = {nullptr, nullptr};
+    float2* D[3] = {nullptr, nullptr, nullptr};   // two-float iterates
 };
 
 template <typename A>
@@ -138,7 +139,10 @@ void filter_layout(A& ar, int64_t N, int64_t n, int m, int L, int low_kind, int6
         fl.W[0] = ar.template take<double>((size_t)(N * ldw));
         fl.W[1] = ar.template take<double>((size_t)(N * ldw));
     }
-    if (L > 0) {
+    if (L > 0 && low_kind == CHFSI_F32X2) {
+        fl.hlow = ar.template take<float2>((size_t)nvals);
+        for (int i = 0; i < 3; i++) fl.D[i] = ar.template take<float2>((size_t)(N * ldw));
+    } else if (L > 0) {
         fl.hlow = ar.template take<float>((size_t)nvals);
         for (int i = 0; i < 3; i++) fl.F[i] = ar.template take<float>((size_t)(N * ldw));
         if (low_kind == CHFSI_BF16_F32ACC)
@@ -294,7 +298,23 @@ int chfsi_filter(const chfsi_matrix* H, const double* X, int64_t ldx, double* Y,
     auto f64_buf = [&](int k) { return cyc[(m - k) % 3]; };
     auto f64_ld = [&](int k) { return cyc_ld[(m - k) % 3]; };
 
-    if (L > 0 && has_bsr(H) && low == CHFSI_BF16_F32ACC) {
+    bool widened = false;   // low-precision Y_L, Y_{L-1} already widened into their FP64 slots
+    if (L > 0 && low == CHFSI_F32X2) {
+        if (!has_csr(H)) return CHFSI_ERR_UNSUPPORTED;
+        if ((rc = to_f32x2(H->csr.val, 1, fl.hlow, 1, H->csr.nnz, 1, s))) return rc;
+        const CsrDev h2{H->csr.n_rows, H->csr.nnz, H->csr.row_ptr, H->csr.col, fl.hlow, Buf::F32X2};
+        if ((rc = to_f32x2(X, ldx, fl.D[0], ldw, N, n, s))) return rc;
+        for (int k = 1; k <= L; k++) {
+            const void* prev = k >= 2 ? fl.D[(k - 2) % 3] : nullptr;
+            rc = csr_step_f32x2(h2, n, fl.D[(k - 1) % 3], ldw, prev, ldw, fl.D[k % 3], ldw, al[k], c,
+                                k >= 2 ? be[k] : 0.0, st, s);
+            if (rc) return rc;
+        }
+        if (L == m) return from_f32x2(fl.D[m % 3], ldw, Y, ldy, N, n, s);
+        if ((rc = from_f32x2(fl.D[L % 3], ldw, f64_buf(L), f64_ld(L), N, n, s))) return rc;
+        if (L >= 2 && (rc = from_f32x2(fl.D[(L - 1) % 3], ldw, f64_buf(L - 1), f64_ld(L - 1), N, n, s))) return rc;
+        widened = true;
+    } else if (L > 0 && has_bsr(H) && low == CHFSI_BF16_F32ACC) {
         // tensor-core path: BF16 blocks, state-major BF16 iterate copies
         if ((rc = bsr_values_to_bf16(H->bsr.val, fl.hlow, bsr_values(H), s))) return rc;
         make_devs(H, nullptr, fl.hlow, Buf::BF16, &csrlo, &bsrlo);
@@ -336,13 +356,13 @@ int chfsi_filter(const chfsi_matrix* H, const double* X, int64_t ldx, double* Y,
         StepIO io{};
         // Y_{k-1}
         if (k - 1 == 0) { io.cur = X; io.cur_t = Buf::F64; io.ldc = ldx; }
-        else if (k - 1 <= L) { io.cur = fl.F[(k - 1) % 3]; io.cur_t = Buf::F32; io.ldc = ldw; }
+        else if (k - 1 <= L && !widened) { io.cur = fl.F[(k - 1) % 3]; io.cur_t = Buf::F32; io.ldc = ldw; }
         else { io.cur = f64_buf(k - 1); io.cur_t = Buf::F64; io.ldc = f64_ld(k - 1); }
         io.gather = io.cur; io.gather_t = io.cur_t; io.ldg = io.ldc;
         // Y_{k-2}
         if (k >= 2) {
             if (k - 2 == 0) { io.prev = X; io.prev_t = Buf::F64; io.ldp = ldx; }
-            else if (k - 2 <= L) { io.prev = fl.F[(k - 2) % 3]; io.prev_t = Buf::F32; io.ldp = ldw; }
+            else if (k - 2 <= L && !widened) { io.prev = fl.F[(k - 2) % 3]; io.prev_t = Buf::F32; io.ldp = ldw; }
             else { io.prev = f64_buf(k - 2); io.prev_t = Buf::F64; io.ldp = f64_ld(k - 2); }
         }
         io.out = f64_buf(k); io.out_t = Buf::F64; io.ldo = f64_ld(k);
@@ -519,10 +539,12 @@ struct RRLayout {
     int* info = nullptr;
     int splits = 1;
     int lwork = 0;
+    // two-float closure
+    float2 *Y2 = nullptr, *B2[2] = {nullptr, nullptr}, *HX2 = nullptr, *R2 = nullptr, *Q2 = nullptr, *H2 = nullptr;
 };
 
 template <typename Ar>
-void rr_layout(Ar& ar, int64_t N, int64_t n, int lwork, RRLayout* out) {
+void rr_layout(Ar& ar, int64_t N, int64_t n, int lwork, int precision, int64_t nnz, RRLayout* out) {
     RRLayout rl;
     const int64_t ldw = pad8(n);
     rl.splits = gemm_tn_splits(N, n);
@@ -530,52 +552,133 @@ void rr_layout(Ar& ar, int64_t N, int64_t n, int lwork, RRLayout* out) {
     ar.template take<unsigned char>(kStatusBytes);
     rl.S = ar.template take<double>((size_t)(n * n));
     rl.part = ar.template take<double>((size_t)(rl.splits * n * n));
-    rl.XF = ar.template take<double>((size_t)(N * ldw));
-    rl.T = ar.template take<double>((size_t)(N * ldw));
     rl.Rinv = ar.template take<double>((size_t)(n * n));
     rl.Q = ar.template take<double>((size_t)(n * n));
     rl.work = ar.template take<double>((size_t)(lwork > 0 ? lwork : 1));
     rl.info = ar.template take<int>(1);
+    if (precision == CHFSI_F32X2) {
+        rl.Y2 = ar.template take<float2>((size_t)(N * ldw));
+        rl.B2[0] = ar.template take<float2>((size_t)(N * ldw));
+        rl.B2[1] = ar.template take<float2>((size_t)(N * ldw));
+        rl.R2 = ar.template take<float2>((size_t)(n * n));
+        rl.Q2 = ar.template take<float2>((size_t)(n * n));
+        rl.H2 = ar.template take<float2>((size_t)(nnz > 0 ? nnz : 1));
+    } else {
+        rl.XF = ar.template take<double>((size_t)(N * ldw));
+        rl.T = ar.template take<double>((size_t)(N * ldw));
+    }
     if (out) *out = rl;
+}
+
+int rr_check(const chfsi_matrix* H, int64_t n_cols, int32_t cholqr_passes, int32_t precision, int64_t* N) {
+    int rc = rows_of(H, N);
+    if (rc) return rc;
+    if (n_cols < 1 || n_cols > *N || (cholqr_passes != 1 && cholqr_passes != 2)) return CHFSI_ERR_ARG;
+    if (precision != CHFSI_F64 && precision != CHFSI_F32X2) return CHFSI_ERR_ARG;
+    if (precision == CHFSI_F32X2 && !has_csr(H)) return CHFSI_ERR_UNSUPPORTED;
+    return CHFSI_OK;
+}
+
+// Step 4 (eigensolve) and the status read-back shared by both precisions.
+int rr_eig(const RRLayout& rl, int64_t n, double* ritz, cudaStream_t s) {
+    cusolverDnHandle_t hs = solver_handle();
+    if (!hs) return CHFSI_ERR_CUDA;
+    if (cusolverDnSetStream(hs, s) != CUSOLVER_STATUS_SUCCESS) return CHFSI_ERR_CUDA;
+    if (cusolverDnDsyevd(hs, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_UPPER, (int)n, rl.S, (int)n, ritz, rl.work,
+                         rl.lwork, rl.info) != CUSOLVER_STATUS_SUCCESS)
+        return CHFSI_ERR_CUDA;
+    // eigenvector i is row i of the row-major view; Q[k][i] = that row transposed
+    return transpose(rl.S, n, rl.Q, n, n, s);
+}
+
+int rr_finish(const RRLayout& rl, unsigned* st, cudaStream_t s) {
+    int info = 0;
+    CHFSI_CUDA_TRY(cudaMemcpyAsync(&info, rl.info, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CHFSI_CUDA_TRY(cudaStreamSynchronize(s));
+    unsigned word = 0;
+    CHFSI_CUDA_TRY(cudaMemcpy(&word, st, sizeof(unsigned), cudaMemcpyDeviceToHost));
+    if (word & DEV_PATTERN) return CHFSI_ERR_PATTERN;
+    if (word & DEV_CHOL) return CHFSI_ERR_CHOL;
+    if (info != 0) return CHFSI_ERR_CUDA;
+    if (word & DEV_NONFINITE) return CHFSI_ERR_NONFINITE;
+    return CHFSI_OK;
+}
+
+// Steps 2, 3 and 5 with two-float products (Cholesky, triangular inverse and the
+// eigensolve stay FP64).
+int rr_run_f32x2(const chfsi_matrix* H, const double* Y, int64_t ldy, int64_t N, int64_t n, double* Psi,
+                 int64_t ldpsi, double* ritz, int passes, const RRLayout& rl, unsigned* st, cudaStream_t s) {
+    const int64_t ldw = pad8(n);
+    int rc;
+    if ((rc = to_f32x2(Y, ldy, rl.Y2, ldw, N, n, s))) return rc;
+    const float2* cur = rl.Y2;
+    int which = 0;
+    for (int pass = 0; pass < passes; pass++) {
+        if ((rc = gemm_tn_f32x2(cur, ldw, cur, ldw, N, n, rl.S, n, true, rl.part, rl.splits, s))) return rc;
+        if ((rc = cholesky_upper(rl.S, n, n, st, s))) return rc;
+        if ((rc = tri_inverse_upper(rl.S, n, rl.Rinv, n, n, s))) return rc;
+        if ((rc = to_f32x2(rl.Rinv, n, rl.R2, n, n, n, s))) return rc;
+        float2* out = rl.B2[which];
+        if ((rc = gemm_nn_f32x2(cur, ldw, rl.R2, n, out, ldw, false, N, n, true, s))) return rc;
+        cur = out;
+        which ^= 1;
+    }
+    const float2* XF = cur;
+    float2* HXF = rl.B2[which];
+    if ((rc = to_f32x2(H->csr.val, 1, rl.H2, 1, H->csr.nnz, 1, s))) return rc;
+    const CsrDev h2{H->csr.n_rows, H->csr.nnz, H->csr.row_ptr, H->csr.col, rl.H2, Buf::F32X2};
+    if ((rc = csr_step_f32x2(h2, n, XF, ldw, nullptr, 0, HXF, ldw, 1.0, 0.0, 0.0, st, s))) return rc;
+    if ((rc = gemm_tn_f32x2(XF, ldw, HXF, ldw, N, n, rl.S, n, false, rl.part, rl.splits, s))) return rc;
+    if ((rc = symmetrize(rl.S, n, n, s))) return rc;
+    if ((rc = rr_eig(rl, n, ritz, s))) return rc;
+    if ((rc = to_f32x2(rl.Q, n, rl.Q2, n, n, n, s))) return rc;
+    if ((rc = gemm_nn_f32x2(XF, ldw, rl.Q2, n, Psi, ldpsi, true, N, n, false, s))) return rc;
+    return rr_finish(rl, st, s);
 }
 
 }  // namespace
 
-int chfsi_rayleigh_ritz_workspace_size(const chfsi_matrix* H, int64_t n_cols, int32_t cholqr_passes, size_t* bytes) {
+int chfsi_rayleigh_ritz_ex_workspace_size(const chfsi_matrix* H, int64_t n_cols, int32_t cholqr_passes,
+                                          int32_t precision, size_t* bytes) {
     if (!bytes) return CHFSI_ERR_ARG;
     int64_t N = 0;
-    int rc = rows_of(H, &N);
+    int rc = rr_check(H, n_cols, cholqr_passes, precision, &N);
     if (rc) return rc;
-    if (n_cols < 1 || n_cols > N || (cholqr_passes != 1 && cholqr_passes != 2)) return CHFSI_ERR_ARG;
     int lwork = 0;
     if ((rc = syevd_lwork(n_cols, &lwork))) return rc;
     SizeOnly sz;
-    rr_layout(sz, N, n_cols, lwork, nullptr);
+    rr_layout(sz, N, n_cols, lwork, precision, has_csr(H) ? H->csr.nnz : 0, nullptr);
     *bytes = sz.used;
     return CHFSI_OK;
 }
 
-int chfsi_rayleigh_ritz(const chfsi_matrix* H, const double* Y, int64_t ldy, int64_t n_cols, double* Psi,
-                        int64_t ldpsi, double* ritz, int32_t cholqr_passes, void* ws, size_t ws_bytes, void* stream) {
+int chfsi_rayleigh_ritz_workspace_size(const chfsi_matrix* H, int64_t n_cols, int32_t cholqr_passes, size_t* bytes) {
+    return chfsi_rayleigh_ritz_ex_workspace_size(H, n_cols, cholqr_passes, CHFSI_F64, bytes);
+}
+
+int chfsi_rayleigh_ritz_ex(const chfsi_matrix* H, const double* Y, int64_t ldy, int64_t n_cols, double* Psi,
+                           int64_t ldpsi, double* ritz, int32_t cholqr_passes, int32_t precision, void* ws,
+                           size_t ws_bytes, void* stream) {
     int64_t N = 0;
-    int rc = rows_of(H, &N);
+    int rc = rr_check(H, n_cols, cholqr_passes, precision, &N);
     if (rc) return rc;
-    if (n_cols < 1 || n_cols > N || (cholqr_passes != 1 && cholqr_passes != 2)) return CHFSI_ERR_ARG;
     if ((rc = check_block(Y, ldy, n_cols)) || (rc = check_block(Psi, ldpsi, n_cols))) return rc;
     if (!ritz || Psi == Y) return CHFSI_ERR_ARG;
     if (!ws || !aligned16(ws)) return CHFSI_ERR_ARG;
     int lwork = 0;
     if ((rc = syevd_lwork(n_cols, &lwork))) return rc;
+    const int64_t nnz = has_csr(H) ? H->csr.nnz : 0;
     SizeOnly sz;
-    rr_layout(sz, N, n_cols, lwork, nullptr);
+    rr_layout(sz, N, n_cols, lwork, precision, nnz, nullptr);
     if (ws_bytes < sz.used) return CHFSI_ERR_NOMEM;
     Arena ar(ws, ws_bytes);
     RRLayout rl;
-    rr_layout(ar, N, n_cols, lwork, &rl);
+    rr_layout(ar, N, n_cols, lwork, precision, nnz, &rl);
     cudaStream_t s = as_stream(stream);
     unsigned* st = status_word(ws);
     CHFSI_CUDA_TRY(cudaMemsetAsync(st, 0, sizeof(unsigned), s));
     const int64_t n = n_cols, ldw = pad8(n);
+    if (precision == CHFSI_F32X2) return rr_run_f32x2(H, Y, ldy, N, n, Psi, ldpsi, ritz, cholqr_passes, rl, st, s);
 
     // step 2: X_F = Y R^-1 with S = Y^T Y = R^T R (repeated on X_F for CholQR2)
     const double* cur = Y;
@@ -608,27 +711,16 @@ int chfsi_rayleigh_ritz(const chfsi_matrix* H, const double* Y, int64_t ldy, int
     if ((rc = gemm_tn(XF, ldw, HXF, ldw, N, n, rl.S, n, false, rl.part, rl.splits, s))) return rc;
     if ((rc = symmetrize(rl.S, n, n, s))) return rc;
     // step 4: H_F Q = Q Lambda (cuSOLVER; column-major view of the symmetric H_F)
-    cusolverDnHandle_t hs = solver_handle();
-    if (!hs) return CHFSI_ERR_CUDA;
-    if (cusolverDnSetStream(hs, s) != CUSOLVER_STATUS_SUCCESS) return CHFSI_ERR_CUDA;
-    if (cusolverDnDsyevd(hs, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_UPPER, (int)n, rl.S, (int)n, ritz, rl.work,
-                         rl.lwork, rl.info) != CUSOLVER_STATUS_SUCCESS)
-        return CHFSI_ERR_CUDA;
-    // eigenvector i is row i of the row-major view; Q[k][i] = that row transposed
-    if ((rc = transpose(rl.S, n, rl.Q, n, n, s))) return rc;
+    if ((rc = rr_eig(rl, n, ritz, s))) return rc;
     // step 5: Psi = X_F Q
     if ((rc = gemm_nn(XF, ldw, rl.Q, n, Psi, ldpsi, N, n, false, s))) return rc;
+    return rr_finish(rl, st, s);
+}
 
-    int info = 0;
-    CHFSI_CUDA_TRY(cudaMemcpyAsync(&info, rl.info, sizeof(int), cudaMemcpyDeviceToHost, s));
-    CHFSI_CUDA_TRY(cudaStreamSynchronize(s));
-    unsigned word = 0;
-    CHFSI_CUDA_TRY(cudaMemcpy(&word, st, sizeof(unsigned), cudaMemcpyDeviceToHost));
-    if (word & DEV_PATTERN) return CHFSI_ERR_PATTERN;
-    if (word & DEV_CHOL) return CHFSI_ERR_CHOL;
-    if (info != 0) return CHFSI_ERR_CUDA;
-    if (word & DEV_NONFINITE) return CHFSI_ERR_NONFINITE;
-    return CHFSI_OK;
+int chfsi_rayleigh_ritz(const chfsi_matrix* H, const double* Y, int64_t ldy, int64_t n_cols, double* Psi,
+                        int64_t ldpsi, double* ritz, int32_t cholqr_passes, void* ws, size_t ws_bytes, void* stream) {
+    return chfsi_rayleigh_ritz_ex(H, Y, ldy, n_cols, Psi, ldpsi, ritz, cholqr_passes, CHFSI_F64, ws, ws_bytes,
+                                  stream);
 }
 
 // ------------------------------------------------------------------ Lanczos bounds

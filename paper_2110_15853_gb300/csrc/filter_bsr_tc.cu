@@ -92,8 +92,10 @@ bsr_tc_kernel(const __grid_constant__ CUtensorMap tmY, const __grid_constant__ C
     __shared__ int abort_flag;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t R = blockIdx.x;
-    const int64_t j0 = (int64_t)blockIdx.y * kTileJ;
+    // column tiles vary fastest, so the tiles of one block row run together and
+    // share its H blocks through L2 (each block is then read from DRAM once)
+    const int64_t R = blockIdx.y;
+    const int64_t j0 = (int64_t)blockIdx.x * kTileJ;
 
     int qb = brow_ptr[R], qe = brow_ptr[R + 1];
     bool bad = false;
@@ -327,7 +329,8 @@ int bsr_step_tc(const BsrDev& h, int64_t n, const void* ysh_in, const float* Yc,
         CHFSI_CUDA_TRY(cudaFuncSetAttribute(bsr_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         attr = true;
     }
-    dim3 grid((unsigned)h.nbr, (unsigned)((n + kTileJ - 1) / kTileJ));
+    if (h.nbr > 65535) return CHFSI_ERR_UNSUPPORTED;
+    dim3 grid((unsigned)((n + kTileJ - 1) / kTileJ), (unsigned)h.nbr);
     bsr_tc_kernel<<<grid, kThreads, smem, s>>>(tmY, tmH, h.nbr, h.brow_ptr, h.bcol, h.nblocks, N, n, Yc, ldc, Yp, ldp,
                                                Yo, ldo, static_cast<__nv_bfloat16*>(ysh_out), (float)alpha, (float)c,
                                                (float)beta, status);

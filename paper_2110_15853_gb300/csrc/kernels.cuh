@@ -5,7 +5,7 @@
 
 namespace chfsi {
 
-enum class Buf { F64, F32, BF16 };
+enum class Buf { F64, F32, BF16, F32X2 };
 enum class StepMath { F64, F32, BF16 };
 
 // CSR operator on the device; val_t says whether val points at the caller's FP64
@@ -52,6 +52,19 @@ int bsr_step_tc(const BsrDev& h, int64_t n, const void* ysh_in, const float* Yc,
                 int64_t ldp, float* Yo, int64_t ldo, void* ysh_out, double alpha, double c, double beta,
                 unsigned* status, cudaStream_t s);
 int bsr_values_to_bf16(const double* src, void* dst, int64_t count, cudaStream_t s);
+
+// Two-float (hi + lo FP32 pairs, float2) CSR step and conversions; h.val holds
+// float2 values, ld in float2 elements (even).
+int csr_step_f32x2(const CsrDev& h, int64_t n, const void* Yc, int64_t ldc, const void* Yp, int64_t ldp, void* Yo,
+                   int64_t ldo, double alpha, double c, double beta, unsigned* status, cudaStream_t s);
+int to_f32x2(const double* src, int64_t lds, void* dst, int64_t ldd, int64_t rows, int64_t n, cudaStream_t s);
+int from_f32x2(const void* src, int64_t lds, double* dst, int64_t ldd, int64_t rows, int64_t n, cudaStream_t s);
+// Two-float dense products (float2 operands): S = A^T B (FP64 result, split-K
+// partials in FP64) and C = A B (float2 or FP64 result).
+int gemm_tn_f32x2(const void* A, int64_t lda, const void* B, int64_t ldb, int64_t K, int64_t n, double* S,
+                  int64_t lds, bool symmetric, double* part, int splits, cudaStream_t s);
+int gemm_nn_f32x2(const void* A, int64_t lda, const void* B, int64_t ldb, void* C, int64_t ldc, bool c_f64,
+                  int64_t M, int64_t n, bool b_upper, cudaStream_t s);
 int transpose_to_bf16(const double* src, int64_t lds, void* dst, int64_t N, int64_t n, cudaStream_t s);
 
 // Element-wise conversions (row-major blocks with leading dimensions; padding

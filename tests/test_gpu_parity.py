@@ -229,6 +229,31 @@ def test_bsr_tensor_core_single_step_exact_products(P, oracle_mod):
     assert rel_fro(Y, Yref) <= 1e-6
 
 
+@pytest.mark.parametrize("g,w,n,m,L", [(8, 2, 6, 5, 5), (8, 3, 37, 10, 10), (12, 3, 70, 13, 9), (5, 1, 3, 7, 1),
+                                       (10, 2, 129, 6, 6), (6, 4, 64, 20, 20)])
+def test_filter_f32x2_is_fp64_accurate(P, oracle_mod, g, w, n, m, L):
+    """Two-float steps (hi + lo FP32 pairs, error-free transformations on the
+    FP32 pipe) meet the FP64 filter tolerance against the FP64 oracle."""
+    H, X = make_case(g, w, n, seed=g * 10 + w + 3)
+    (a, b, a0), _ = bounds_for(oracle_mod, H, max(1, min(n, H["N"] // 4)))
+    Yref = oracle_mod.filter(H, X, m, a, b, a0)
+    ws = P.Workspace(DEV)
+    Y = P.filter(to_dev(P, H), dev(X), m, a, b, a0, schedule=P.mixed_schedule(m, L, "f32x2"),
+                 workspace=ws).cpu().numpy()
+    assert P.read_status(ws) == 0
+    assert rel_fro(Y, Yref) <= 1e-12
+
+
+def test_filter_f32x2_config_40cube_sampled_columns(P, oracle_mod):
+    wl = W.workload("g40_w3_n1024_m20")
+    H, X = make_case(wl.g, wl.w, wl.n, seed=wl.seed)
+    (a, b, a0), _ = bounds_for(oracle_mod, H, wl.n, wl.seed)
+    Y = P.filter(to_dev(P, H), dev(X), wl.m, a, b, a0, schedule=["f32x2"] * wl.m).cpu().numpy()
+    cols = W.column_subset(wl.n, 48, wl.seed)
+    Yref = oracle_mod.filter(H, X[:, cols], wl.m, a, b, a0)
+    assert rel_fro(Y[:, cols], Yref) <= 1e-12
+
+
 # --------------------------------------------------------------------------- Lanczos
 
 
@@ -255,12 +280,12 @@ def test_lanczos_tiny_breakdown(P, oracle_mod):
 # --------------------------------------------------------------------------- Rayleigh-Ritz
 
 
-def _check_ritz(oracle_mod, H, Y, ritz, psi, tol=1e-10):
+def _check_ritz(oracle_mod, H, Y, ritz, psi, tol=1e-10, orth_tol=1e-12):
     theta, Psi_ref, _ = oracle_mod.rayleigh_ritz(H, Y)
     scale = np.max(np.abs(theta))
     assert np.max(np.abs(ritz - theta)) <= tol * scale
     n = Y.shape[1]
-    assert np.max(np.abs(psi.T @ psi - np.eye(n))) <= 1e-12
+    assert np.max(np.abs(psi.T @ psi - np.eye(n))) <= orth_tol
     # Ritz vectors: compare projectors onto clusters of (numerically) equal values
     i = 0
     while i < n:
@@ -304,6 +329,34 @@ def test_rayleigh_ritz_config_40cube(P, oracle_mod):
     Yref = oracle_mod.filter(H, X, wl.m, a, b, a0)
     theta, _, _ = oracle_mod.rayleigh_ritz(H, Yref)
     assert np.max(np.abs(ritz.cpu().numpy() - theta)) <= 1e-10 * np.max(np.abs(theta))
+
+
+@pytest.mark.parametrize("passes", [1, 2])
+def test_rayleigh_ritz_f32x2_products(P, oracle_mod, passes):
+    """Two-float Gram / projection / rotation products (FP64 Cholesky and
+    eigensolve): Ritz values and vectors at the FP64 closure's tolerances."""
+    H, X = make_case(8, 2, 20, seed=45)
+    (a, b, a0), _ = bounds_for(oracle_mod, H, 20)
+    Y = oracle_mod.filter(H, X, 8, a, b, a0)
+    ritz, psi = P.rayleigh_ritz(to_dev(P, H), dev(Y), cholqr_passes=passes, precision="f32x2")
+    # one CholQR pass leaves ~u cond(Y)^2 loss of orthogonality, with the two-float
+    # unit roundoff u = 2^-48 (cond(Y) ~ 30 here); the second pass restores ~u
+    _check_ritz(oracle_mod, H, Y, ritz.cpu().numpy(), psi.cpu().numpy(),
+                orth_tol=1e-12 if passes == 2 else 1e-10)
+
+
+def test_rayleigh_ritz_f32x2_config_40cube(P, oracle_mod):
+    wl = W.workload("g40_w3_n1024_m20")
+    H, X = make_case(wl.g, wl.w, wl.n, seed=wl.seed)
+    (a, b, a0), _ = bounds_for(oracle_mod, H, wl.n, wl.seed)
+    Hd = to_dev(P, H)
+    Yd = P.filter(Hd, dev(X), wl.m, a, b, a0, schedule=["f32x2"] * wl.m)
+    ritz, psi = P.rayleigh_ritz(Hd, Yd, cholqr_passes=2, precision="f32x2")
+    Yref = oracle_mod.filter(H, X, wl.m, a, b, a0)
+    theta, _, _ = oracle_mod.rayleigh_ritz(H, Yref)
+    assert np.max(np.abs(ritz.cpu().numpy() - theta)) <= 1e-10 * np.max(np.abs(theta))
+    p = psi.cpu().numpy()
+    assert np.max(np.abs(p.T @ p - np.eye(wl.n))) <= 1e-12
 
 
 def test_rayleigh_ritz_rank_deficient_reports_cholesky(P, oracle_mod):
