@@ -59,6 +59,9 @@ def parse_args():
                     help="set up, run one FP64 filter (m launches of the CSR step) and exit: a profiling case")
     ap.add_argument("--schedule", default="f64", help="filter-only schedule: f64 | f32:L | bf16:L | f32x2:L")
     ap.add_argument("--layout", default="csr", choices=["csr", "bsr", "hybrid"], help="filter-only operator layout")
+    ap.add_argument("--closure-only", action="store_true",
+                    help="set up, run one CholQR2 + Rayleigh-Ritz on X and exit: a profiling case")
+    ap.add_argument("--precision", default="f64", choices=["f64", "f32x2"], help="closure-only product precision")
     return ap.parse_args()
 
 
@@ -170,6 +173,27 @@ def committed_traffic(workload):
     return float(m2.group(1))
 
 
+# ---------------------------------------------------------------- replicas (N > 1)
+
+
+def replica_max_ms(local_ms: float, device) -> float:
+    """Max of the timed region over all ranks (the job ends when the slowest rank
+    does); identity without an initialised process group."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(local_ms)
+    t = torch.tensor([float(local_ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(step_flops: float, world: int, ms_step: float) -> float:
+    """Whole-job GFLOP/s: every rank filters its own replica (weak scaling), so
+    the job's work is world x the per-rank step, over the slowest rank's time."""
+    return step_flops * world / (ms_step * 1e-3) / 1e9
+
+
 # ---------------------------------------------------------------- workload setup
 
 
@@ -268,6 +292,17 @@ def run_ours(args):
     N, n, m, nnz = H["N"], wl.n, wl.m, H["nnz"]
     if args.filter_only:
         return run_filter_only(P, torch, dev, wl, H, X, v0, args)
+    if args.closure_only:
+        Hd = P.CsrMatrix.from_arrays(H["row_ptr"], H["col"], H["val"], device=dev)
+        Xd = torch.as_tensor(X).to(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        ritz, _ = P.rayleigh_ritz(Hd, Xd, 2, precision=args.precision)
+        e1.record()
+        torch.cuda.synchronize(dev)
+        print(json.dumps({"closure_only": True, "workload": wl.name, "n": n, "precision": args.precision,
+                          "ms": e0.elapsed_time(e1), "finite": bool(torch.isfinite(ritz).all().item())}))
+        return 0
     Hd = P.CsrMatrix.from_arrays(H["row_ptr"], H["col"], H["val"], device=dev)
     Xd = torch.as_tensor(X).to(dev)
     v0d = torch.as_tensor(v0).to(dev)
@@ -320,16 +355,12 @@ def run_ours(args):
         dist.barrier()
     launches = lib.chfsi_kernel_launches() - launches0
     clk = clocks.stop()
-    total_ms = t_start.elapsed_time(t_end)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = replica_max_ms(t_start.elapsed_time(t_end), dev)
     ms_step = total_ms / args.steps
     lan_ms = float(np.median([e[0].elapsed_time(e[1]) for e in evs]))
     fil_ms = float(np.median([e[1].elapsed_time(e[2]) for e in evs]))
     rr_ms = float(np.median([e[2].elapsed_time(e[3]) for e in evs]))
-    value = step_flops * world / (ms_step * 1e-3) / 1e9
+    value = replica_throughput(step_flops, world, ms_step)
 
     # roofline of the dominant kernel: the fused FP64 CSR step (m launches per filter)
     launch_ms = fil_ms / m

@@ -42,7 +42,7 @@ __device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
 // Y values as float2 {hi, lo}, row-major with leading dimension ld (in float2 units).
 // Each lane owns 2 consecutive states (one float4 = 2 pairs); U chunks per pass.
 template <int U>
-__global__ void __launch_bounds__(kThreads, 4)
+__global__ void __launch_bounds__(kThreads, (U >= 4 ? 2 : 4))
 csr_step_f32x2_kernel(int64_t N, const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
                       const float2* __restrict__ val, int64_t nnz, int64_t n, const float2* __restrict__ Yc,
                       int64_t ldc, const float2* __restrict__ Yp, int64_t ldp, float2* __restrict__ Yo, int64_t ldo,
@@ -97,42 +97,55 @@ csr_step_f32x2_kernel(int64_t N, const int64_t* __restrict__ row_ptr, const int3
                 sh[u][0] = sh[u][1] = sl[u][0] = sl[u][1] = 0.f;
             }
             const int64_t j0 = jbase + (int64_t)lane * 2;
-            // register pipeline: the gathers of entry q+1 are in flight while entry q is
-            // accumulated (a bad column index becomes a zero entry on row 0)
-            float4 ynext[U];
-            float2 hnext = make_float2(0.f, 0.f);
+            // Register pipeline with two alternating buffers: the gathers of entry q+1
+            // are in flight while entry q is accumulated (no register copies).  Full
+            // chunks take a predicate-free path; a bad column index (unstaged rows only)
+            // becomes a zero entry on row 0.
+            const bool full = jbase + 64 * U <= n;
             auto fetch = [&](int q, float4 (&y)[U], float2& h) {
                 int32_t cj = hc[q];
                 h = hv[q];
-                if (cj < 0 || (int64_t)cj >= N) { bad = true; cj = 0; h = make_float2(0.f, 0.f); }
+                if (!staged && (cj < 0 || (int64_t)cj >= N)) { bad = true; cj = 0; h = make_float2(0.f, 0.f); }
                 const float2* src = Yc + (int64_t)cj * ldc + j0;
+                if (full) {
 #pragma unroll
-                for (int u = 0; u < U; u++)
-                    y[u] = on[u] ? __ldg(reinterpret_cast<const float4*>(src + u * 64)) : make_float4(0.f, 0.f, 0.f, 0.f);
+                    for (int u = 0; u < U; u++) y[u] = __ldg(reinterpret_cast<const float4*>(src + u * 64));
+                } else {
+#pragma unroll
+                    for (int u = 0; u < U; u++)
+                        y[u] = on[u] ? __ldg(reinterpret_cast<const float4*>(src + u * 64))
+                                     : make_float4(0.f, 0.f, 0.f, 0.f);
+                }
             };
-            if (len > 0) fetch(0, ynext, hnext);
-            for (int q = 0; q < len; q++) {
-                float4 y[U];
-#pragma unroll
-                for (int u = 0; u < U; u++) y[u] = ynext[u];
-                const float2 h = hnext;
-                if (q + 1 < len) fetch(q + 1, ynext, hnext);
+            auto accumulate = [&](const float4 (&y)[U], float2 h) {
 #pragma unroll
                 for (int u = 0; u < U; u++) {
                     df_madd(h.x, h.y, y[u].x, y[u].y, sh[u][0], sl[u][0]);
                     df_madd(h.x, h.y, y[u].z, y[u].w, sh[u][1], sl[u][1]);
                 }
-                if ((q & (kRenorm - 1)) == kRenorm - 1) {
+            };
+            auto renorm = [&]() {
 #pragma unroll
-                    for (int u = 0; u < U; u++)
+                for (int u = 0; u < U; u++)
 #pragma unroll
-                        for (int v = 0; v < 2; v++) {
-                            DF t = fast_norm(sh[u][v], sl[u][v]);
-                            sh[u][v] = t.hi;
-                            sl[u][v] = t.lo;
-                        }
-                }
+                    for (int v = 0; v < 2; v++) {
+                        const DF t = fast_norm(sh[u][v], sl[u][v]);
+                        sh[u][v] = t.hi;
+                        sl[u][v] = t.lo;
+                    }
+            };
+            float4 ya[U], yb[U];
+            float2 ha = make_float2(0.f, 0.f), hb = make_float2(0.f, 0.f);
+            if (len > 0) fetch(0, ya, ha);
+            int q = 0;
+            for (; q + 1 < len; q += 2) {
+                fetch(q + 1, yb, hb);
+                accumulate(ya, ha);
+                if (q + 2 < len) fetch(q + 2, ya, ha);
+                accumulate(yb, hb);
+                if ((q & (kRenorm - 1)) == kRenorm - 2) renorm();
             }
+            if (q < len) accumulate(ya, ha);
 #pragma unroll
             for (int u = 0; u < U; u++) {
                 if (!on[u]) continue;
@@ -216,12 +229,20 @@ int csr_step_f32x2(const CsrDev& h, int64_t n, const void* Yc, int64_t ldc, cons
     if (!attr) {
         CHFSI_CUDA_TRY(cudaFuncSetAttribute(csr_step_f32x2_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             (int)((sizeof(float2) + sizeof(int32_t)) * kCapMax)));
+        CHFSI_CUDA_TRY(cudaFuncSetAttribute(csr_step_f32x2_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)((sizeof(float2) + sizeof(int32_t)) * kCapMax)));
         attr = true;
     }
     const int64_t blocks = (h.N + kWarps - 1) / kWarps;
-    csr_step_f32x2_kernel<2><<<(unsigned)blocks, kThreads, smem, s>>>(
-        h.N, h.row_ptr, h.col, static_cast<const float2*>(h.val), h.nnz, n, static_cast<const float2*>(Yc), ldc,
-        static_cast<const float2*>(Yp), ldp, static_cast<float2*>(Yo), ldo, alpha, c, beta, (int)cap, status);
+    // 4 chunks of 64 states per pass when n fills them, else 2
+    if (n >= 256)
+        csr_step_f32x2_kernel<4><<<(unsigned)blocks, kThreads, smem, s>>>(
+            h.N, h.row_ptr, h.col, static_cast<const float2*>(h.val), h.nnz, n, static_cast<const float2*>(Yc), ldc,
+            static_cast<const float2*>(Yp), ldp, static_cast<float2*>(Yo), ldo, alpha, c, beta, (int)cap, status);
+    else
+        csr_step_f32x2_kernel<2><<<(unsigned)blocks, kThreads, smem, s>>>(
+            h.N, h.row_ptr, h.col, static_cast<const float2*>(h.val), h.nnz, n, static_cast<const float2*>(Yc), ldc,
+            static_cast<const float2*>(Yp), ldp, static_cast<float2*>(Yo), ldo, alpha, c, beta, (int)cap, status);
     CHFSI_LAUNCH_CHECK();
     return CHFSI_OK;
 }
