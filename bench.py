@@ -62,6 +62,9 @@ def parse_args():
     ap.add_argument("--closure-only", action="store_true",
                     help="set up, run one CholQR2 + Rayleigh-Ritz on X and exit: a profiling case")
     ap.add_argument("--precision", default="f64", choices=["f64", "f32x2"], help="closure-only product precision")
+    ap.add_argument("--quick", action="store_true",
+                    help="large one-off workloads: variants timed once without warm-up, no BSR-FP64 variant, "
+                         "no end-to-end leg")
     return ap.parse_args()
 
 
@@ -374,36 +377,39 @@ def run_ours(args):
                 "hbm_bytes_algorithmic": 24.0 * N * n + 12.0 * nnz + 8.0 * (N + 1)}
 
     # end to end through the public API with host buffers
-    Xh = torch.empty((N, n), dtype=torch.float64).pin_memory()
-    Xh.copy_(torch.as_tensor(X))
-    v0h = torch.as_tensor(v0).pin_memory()
-    psih = torch.empty((N, n), dtype=torch.float64).pin_memory()
-    ritzh = torch.empty(n, dtype=torch.float64).pin_memory()
+    e2e = None
+    if not args.quick:
+        Xh = torch.empty((N, n), dtype=torch.float64).pin_memory()
+        Xh.copy_(torch.as_tensor(X))
+        v0h = torch.as_tensor(v0).pin_memory()
+        psih = torch.empty((N, n), dtype=torch.float64).pin_memory()
+        ritzh = torch.empty(n, dtype=torch.float64).pin_memory()
 
-    def e2e_step():
-        Xd.copy_(Xh, non_blocking=True)
-        v0d.copy_(v0h, non_blocking=True)
-        step()
-        psih.copy_(psi, non_blocking=True)
-        ritzh.copy_(ritz, non_blocking=True)
+        def e2e_step():
+            Xd.copy_(Xh, non_blocking=True)
+            v0d.copy_(v0h, non_blocking=True)
+            step()
+            psih.copy_(psi, non_blocking=True)
+            ritzh.copy_(ritz, non_blocking=True)
 
-    e2e_step()
-    torch.cuda.synchronize(dev)
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
         e2e_step()
-    e1.record(stream)
-    torch.cuda.synchronize(dev)
-    e2e_ms = e0.elapsed_time(e1) / args.steps
-    e2e = {"value": step_flops * world / (e2e_ms * 1e-3) / 1e9, "unit": "GFLOP/s", "ms_per_step": e2e_ms,
-           "h2d_bytes_per_step": int(Xh.numel() * 8 + v0h.numel() * 8),
-           "d2h_bytes_per_step": int(psih.numel() * 8 + ritzh.numel() * 8)}
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            e2e_step()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        e2e_ms = e0.elapsed_time(e1) / args.steps
+        e2e = {"value": step_flops * world / (e2e_ms * 1e-3) / 1e9, "unit": "GFLOP/s", "ms_per_step": e2e_ms,
+               "h2d_bytes_per_step": int(Xh.numel() * 8 + v0h.numel() * 8),
+               "d2h_bytes_per_step": int(psih.numel() * 8 + ritzh.numel() * 8)}
+        del Xh, psih
 
     variants = {}
     if not args.no_variants and rank == 0:
-        variants = measure_variants(P, torch, dev, stream, wl, H, Hd, Xd, bounds)
+        variants = measure_variants(P, torch, dev, stream, wl, H, Hd, Xd, bounds, quick=args.quick)
         v2 = variants.get("step_f32x2_filter_and_closure")
         if v2 and v2.get("ms"):
             v2["speedup_vs_f64_step"] = ms_step / v2["ms"]
@@ -466,7 +472,7 @@ def run_filter_only(P, torch, dev, wl, H, X, v0, args):
     return 0
 
 
-def measure_variants(P, torch, dev, stream, wl, H, Hd, Xd, bounds):
+def measure_variants(P, torch, dev, stream, wl, H, Hd, Xd, bounds, quick=False):
     """Filter-only timings of the other layouts / schedules on the same workload
     (outside the main timed region), each with its error against the FP64 CSR run."""
     a, b, a0 = bounds
@@ -474,7 +480,10 @@ def measure_variants(P, torch, dev, stream, wl, H, Hd, Xd, bounds):
     out = {}
 
     def timeit(fn, reps=2):
-        fn()
+        if quick:
+            reps = 1
+        else:
+            fn()
         torch.cuda.synchronize(dev)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -556,8 +565,11 @@ def measure_variants(P, torch, dev, stream, wl, H, Hd, Xd, bounds):
             th, _ = P.rayleigh_ritz(Hd, Yback, 2, workspace=rr_ws)
             return float(np.max(np.abs(th.cpu().numpy() - theta_ref)) / np.max(np.abs(theta_ref)))
 
-        t = timeit(lambda: P.filter(Bd, Xp, m, a, b, a0, out=Yb, workspace=ws), reps=1)
-        out["filter_bsr_f64"] = {"ms": t, "gflops": fl / (t * 1e-3) / 1e9,
+        if quick:
+            t = None
+        else:
+            t = timeit(lambda: P.filter(Bd, Xp, m, a, b, a0, out=Yb, workspace=ws), reps=1)
+        out["filter_bsr_f64"] = {"skipped": "--quick"} if t is None else {"ms": t, "gflops": fl / (t * 1e-3) / 1e9,
                                  "executed_gflop": m * 2.0 * B["n_blocks"] * 64 * 64 * n / 1e9,
                                  "y_rel_fro_err_vs_csr": err_vs_ref()}
         t = timeit(lambda: P.filter(Hy, Xp, m, a, b, a0, out=Yb, workspace=ws))
