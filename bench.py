@@ -517,6 +517,27 @@ def measure_variants(P, torch, dev, stream, wl, H, Hd, Xd, bounds, quick=False):
             "ms": t, "gflops": fl / (t * 1e-3) / 1e9, "speedup_vs_f64": out["filter_csr_f64"]["ms"] / t,
             "ritz_max_rel_err_vs_f64": rel, "y_rel_fro_err_vs_f64": yerr}
         del Ym
+    # adjoint (reverse sweep with sqrt(m) checkpoints), FP64 and two-float; algorithmic
+    # work m (4 nnz n + 5 N n) plus one forward replay
+    try:
+        wts = torch.as_tensor(W.loss_weights(N, wl.seed)).to(dev)
+        G = 2.0 * wts[:, None] * Yref
+        adj_fl = m * (4.0 * nnz * n + 5.0 * N * n) + fl
+        bw_ws = P.Workspace(dev)
+        t = timeit(lambda: P.filter_backward(Hd, Xd, G, m, a, b, a0, workspace=bw_ws), reps=1)
+        dX64, dH64 = P.filter_backward(Hd, Xd, G, m, a, b, a0, workspace=bw_ws)
+        out["adjoint_f64"] = {"ms": t, "gflops": adj_fl / (t * 1e-3) / 1e9}
+        t2 = timeit(lambda: P.filter_backward(Hd, Xd, G, m, a, b, a0, workspace=bw_ws, precision="f32x2"), reps=1)
+        dX2, dH2 = P.filter_backward(Hd, Xd, G, m, a, b, a0, workspace=bw_ws, precision="f32x2")
+        out["adjoint_f32x2"] = {
+            "ms": t2, "gflops": adj_fl / (t2 * 1e-3) / 1e9, "speedup_vs_f64_adjoint": t / t2,
+            "speedup_vs_f64_forward_filter": out["filter_csr_f64"]["ms"] / t2,
+            "dX_rel_err_vs_f64": float(torch.linalg.norm(dX2 - dX64) / torch.linalg.norm(dX64)),
+            "dH_rel_err_vs_f64": float(torch.linalg.norm(dH2 - dH64) / torch.linalg.norm(dH64))}
+        del G, dX64, dH64, dX2, dH2, bw_ws
+    except Exception as e:  # noqa: BLE001 - report, do not hide
+        out["adjoint_error"] = repr(e)
+
     # the whole step with the FP64-accurate two-float filter and closure products
     try:
         Ys = torch.empty_like(Xd)

@@ -198,6 +198,22 @@ int chfsi_filter_backward(const chfsi_matrix* H, const double* X, int64_t ldx,
                           double a0, int32_t ckpt_stride, void* ws, size_t ws_bytes,
                           void* stream);
 
+int chfsi_filter_backward_ex_workspace_size(const chfsi_matrix* H, int64_t n_cols, int32_t m,
+                                            int32_t ckpt_stride, int32_t precision, size_t* bytes);
+
+/*
+ * chfsi_filter_backward with a choice of arithmetic for the whole reverse sweep
+ * (forward replay, reverse recurrence and the dH products): precision =
+ * CHFSI_F64 (the same as chfsi_filter_backward) or CHFSI_F32X2 (two-float hi/lo
+ * FP32 pairs on the FP32 pipe, about 48 significant bits; dH accumulates in FP64).
+ * Same arguments, layout requirements and errors as chfsi_filter_backward.
+ */
+int chfsi_filter_backward_ex(const chfsi_matrix* H, const double* X, int64_t ldx,
+                             const double* dY, int64_t lddy, double* dX, int64_t lddx,
+                             double* dH_val, int64_t n_cols, int32_t m, double a, double b,
+                             double a0, int32_t ckpt_stride, int32_t precision, void* ws,
+                             size_t ws_bytes, void* stream);
+
 /* ------------------------------------------------------------------ closure (Algorithm 1, steps 2-5) */
 
 int chfsi_rayleigh_ritz_workspace_size(const chfsi_matrix* H, int64_t n_cols,

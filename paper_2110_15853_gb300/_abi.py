@@ -65,6 +65,9 @@ SIGNATURES = {
     "chfsi_filter_backward_workspace_size": (ctypes.c_int, [_MP, _i64, _i32, _i32, _SZP]),
     "chfsi_filter_backward": (ctypes.c_int, [_MP, _vp, _i64, _vp, _i64, _vp, _i64, _vp, _i64, _i32, _dbl, _dbl,
                                              _dbl, _i32, _vp, _sz, _vp]),
+    "chfsi_filter_backward_ex_workspace_size": (ctypes.c_int, [_MP, _i64, _i32, _i32, _i32, _SZP]),
+    "chfsi_filter_backward_ex": (ctypes.c_int, [_MP, _vp, _i64, _vp, _i64, _vp, _i64, _vp, _i64, _i32, _dbl, _dbl,
+                                                _dbl, _i32, _i32, _vp, _sz, _vp]),
     "chfsi_rayleigh_ritz_workspace_size": (ctypes.c_int, [_MP, _i64, _i32, _SZP]),
     "chfsi_rayleigh_ritz": (ctypes.c_int, [_MP, _vp, _i64, _i64, _vp, _i64, _vp, _i32, _vp, _sz, _vp]),
     "chfsi_rayleigh_ritz_ex_workspace_size": (ctypes.c_int, [_MP, _i64, _i32, _i32, _SZP]),

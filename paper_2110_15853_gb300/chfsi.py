@@ -200,23 +200,31 @@ def read_status(workspace: Workspace) -> int:
 
 def filter_backward(H: CsrMatrix, X: torch.Tensor, dY: torch.Tensor, m: int, a: float, b: float, a0: float,
                     ckpt_stride: int = 0, want_dH: bool = True, val: Optional[torch.Tensor] = None,
-                    workspace: Optional[Workspace] = None):
-    """(dX, dH_val) for dL/dY_m = dY; dH_val has one entry per stored entry of H."""
+                    workspace: Optional[Workspace] = None, precision: str = "f64"):
+    """(dX, dH_val) for dL/dY_m = dY; dH_val has one entry per stored entry of H.
+
+    precision "f64" (chfsi_filter_backward) or "f32x2" (two-float sweep,
+    chfsi_filter_backward_ex)."""
     _check_block(X, "X")
     _check_block(dY, "dY")
     N, n = X.shape
     lib = load()
     desc = H.descriptor(val)
     sz = ctypes.c_size_t(0)
-    check(lib.chfsi_filter_backward_workspace_size(ctypes.byref(desc), n, m, ckpt_stride, ctypes.byref(sz)),
-          "chfsi_filter_backward_workspace_size")
+    code = PRECISIONS[precision]
+    check(lib.chfsi_filter_backward_ex_workspace_size(ctypes.byref(desc), n, m, ckpt_stride, code,
+                                                      ctypes.byref(sz)), "chfsi_filter_backward_ex_workspace_size")
     ws = (workspace or Workspace(X.device)).get(sz.value)
     dX = torch.empty((N, n), dtype=torch.float64, device=X.device)
     dH = torch.empty(H.nnz, dtype=torch.float64, device=X.device) if want_dH else None
-    rc = lib.chfsi_filter_backward(ctypes.byref(desc), _ptr(X), X.stride(0), _ptr(dY), dY.stride(0), _ptr(dX),
-                                   dX.stride(0), _ptr(dH), n, m, a, b, a0, ckpt_stride, _ptr(ws), ws.numel(),
-                                   _stream_handle(X.device))
-    check(rc, "chfsi_filter_backward")
+    args = (ctypes.byref(desc), _ptr(X), X.stride(0), _ptr(dY), dY.stride(0), _ptr(dX), dX.stride(0), _ptr(dH), n, m,
+            a, b, a0, ckpt_stride)
+    if precision == "f64":
+        rc = lib.chfsi_filter_backward(*args, _ptr(ws), ws.numel(), _stream_handle(X.device))
+        check(rc, "chfsi_filter_backward")
+    else:
+        rc = lib.chfsi_filter_backward_ex(*args, code, _ptr(ws), ws.numel(), _stream_handle(X.device))
+        check(rc, "chfsi_filter_backward_ex")
     return dX, dH
 
 

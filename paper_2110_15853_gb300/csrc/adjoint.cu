@@ -68,3 +68,63 @@ int sddmm_accumulate(const CsrDev& h, int64_t n, const double* Ybar, int64_t ldb
 }
 
 }  // namespace chfsi
+
+// ---------------------------------------------------------------- two-float SDDMM
+#include "twofloat.cuh"
+
+namespace chfsi {
+
+namespace {
+
+// dH[p] += alpha * <Ybar[row p, :], Yprev[col p, :]> with both blocks as hi/lo FP32
+// pairs: per-lane two-float dot products, a fixed shuffle tree of two-float adds,
+// and one FP64 multiply-add into dH[p] per entry (one warp per row, no atomics).
+__global__ void __launch_bounds__(256)
+sddmm_f32x2_kernel(int64_t N, const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col, int64_t nnz,
+                   int64_t n, const float2* __restrict__ Yb, int64_t ldb, const float2* __restrict__ Yp, int64_t ldp,
+                   double alpha, double* __restrict__ dH) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t r = (int64_t)blockIdx.x * 8 + warp;
+    if (r >= N) return;
+    int64_t b = row_ptr[r], e = row_ptr[r + 1];
+    if (b < 0) b = 0;
+    if (e > nnz) e = nnz;
+    const float2* yb = Yb + r * ldb;
+    for (int64_t p = b; p < e; p++) {
+        const int32_t q = col[p];
+        float sh = 0.f, sl = 0.f;
+        if (q >= 0 && (int64_t)q < N) {
+            const float2* yp = Yp + (int64_t)q * ldp;
+            for (int64_t j = (int64_t)lane * 2; j < n; j += 64) {
+                const float4 x = __ldg(reinterpret_cast<const float4*>(yb + j));
+                const float4 y = __ldg(reinterpret_cast<const float4*>(yp + j));
+                df_madd(x.x, x.y, y.x, y.y, sh, sl);
+                df_madd(x.z, x.w, y.z, y.w, sh, sl);
+            }
+        }
+        DF acc = fast_norm(sh, sl);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            DF other;
+            other.hi = __shfl_xor_sync(0xffffffffu, acc.hi, o);
+            other.lo = __shfl_xor_sync(0xffffffffu, acc.lo, o);
+            acc = df_add(acc, other);
+        }
+        if (lane == 0) dH[p] = fma(alpha, (double)acc.hi + (double)acc.lo, dH[p]);
+    }
+}
+
+}  // namespace
+
+int sddmm_accumulate_f32x2(const CsrDev& h, int64_t n, const void* Ybar, int64_t ldb, const void* Yprev,
+                           int64_t ldp, double alpha, double* dH, cudaStream_t s) {
+    if (h.N <= 0 || n <= 0) return CHFSI_OK;
+    if ((ldb % 2) || (ldp % 2)) return CHFSI_ERR_UNSUPPORTED;
+    sddmm_f32x2_kernel<<<(unsigned)((h.N + 7) / 8), 256, 0, s>>>(h.N, h.row_ptr, h.col, h.nnz, n,
+                                                                  static_cast<const float2*>(Ybar), ldb,
+                                                                  static_cast<const float2*>(Yprev), ldp, alpha, dH);
+    CHFSI_LAUNCH_CHECK();
+    return CHFSI_OK;
+}
+
+}  // namespace chfsi

@@ -4,6 +4,7 @@
 // kernels on the caller's stream; every arithmetic step runs on the GPU.
 #include <atomic>
 #include <cmath>
+#include <functional>
 #include <cstring>
 #include <mutex>
 #include <vector>
@@ -381,10 +382,13 @@ struct BackLayout {
     std::vector<double*> ck;      // checkpoint blocks: 2 per segment i >= 1
     std::vector<double*> seg;     // S - 1 replay blocks
     double* A[3] = {nullptr, nullptr, nullptr};
+    // two-float run: hi/lo copies of X and dY, Ybar_0, and H's values
+    void *X2 = nullptr, *G2 = nullptr, *D0 = nullptr, *H2 = nullptr;
 };
 
+// Every block holds 8-byte elements (FP64, or a float2 hi/lo pair), N x round_up(n, 8).
 template <typename Ar>
-void back_layout(Ar& ar, int64_t N, int64_t n, int m, int stride, BackLayout* out) {
+void back_layout(Ar& ar, int64_t N, int64_t n, int m, int stride, int precision, int64_t nnz, BackLayout* out) {
     BackLayout bl;
     bl.S = stride > 0 ? stride : (int)std::ceil(std::sqrt((double)m));
     if (bl.S < 1) bl.S = 1;
@@ -398,33 +402,125 @@ void back_layout(Ar& ar, int64_t N, int64_t n, int m, int stride, BackLayout* ou
     }
     for (int i = 1; i < bl.S; i++) bl.seg.push_back(ar.template take<double>((size_t)(N * ldw)));
     for (int i = 0; i < 3; i++) bl.A[i] = ar.template take<double>((size_t)(N * ldw));
+    if (precision == CHFSI_F32X2) {
+        bl.X2 = ar.template take<double>((size_t)(N * ldw));
+        bl.G2 = ar.template take<double>((size_t)(N * ldw));
+        bl.D0 = ar.template take<double>((size_t)(N * ldw));
+        bl.H2 = ar.template take<double>((size_t)(nnz > 0 ? nnz : 1));
+    }
     if (out) *out = bl;
+}
+
+// One filter-form step on 8-byte blocks: out = alpha (H cur - c cur) - beta prev.
+using BackStep = std::function<int(const void* cur, int64_t ldc, const void* prev, int64_t ldp, void* out,
+                                   int64_t ldo, double alpha, double beta)>;
+// dH[p] += alpha <Ybar[row p, :], Yprev[col p, :]>.
+using BackSddmm = std::function<int(const void* ybar, int64_t ldb, const void* yprev, int64_t ldp, double alpha)>;
+
+// Checkpointed reverse sweep shared by both arithmetics (see chfsi.h).
+int backward_sweep(int m, const BackLayout& bl, int64_t ldw, const std::vector<double>& al,
+                   const std::vector<double>& be, const void* X, int64_t ldx, const void* dY, int64_t lddy, void* dX,
+                   int64_t lddx, bool want_dH, const BackStep& step, const BackSddmm& sddmm) {
+    const int S = bl.S;
+    int rc;
+    // Forward pass to the last checkpoint.  Checkpoint pair of segment i >= 1:
+    // Y_{iS-1} -> ck[2(i-1)], Y_{iS} -> ck[2(i-1)+1]; other iterates rotate in A[].
+    auto ck_slot = [&](int k) -> void* {
+        for (int i = 1; i < bl.nseg; i++) {
+            if (k == i * S - 1) return bl.ck[2 * (i - 1)];
+            if (k == i * S) return bl.ck[2 * (i - 1) + 1];
+        }
+        return nullptr;
+    };
+    std::vector<const void*> fptr(m + 1, nullptr);
+    std::vector<int64_t> fld(m + 1, ldw);
+    fptr[0] = X;
+    fld[0] = ldx;
+    const int k_last = (bl.nseg - 1) * S;
+    for (int k = 1; k <= k_last; k++) {
+        void* out = ck_slot(k);
+        if (!out) out = bl.A[k % 3];
+        const void* prev = k >= 2 ? fptr[k - 2] : nullptr;
+        if ((rc = step(fptr[k - 1], fld[k - 1], prev, k >= 2 ? fld[k - 2] : 0, out, ldw, al[k],
+                       k >= 2 ? be[k] : 0.0)))
+            return rc;
+        fptr[k] = out;
+        fld[k] = ldw;
+    }
+
+    // Adjoint iterates: Ybar_m = dY; Ybar_j for 1 <= j < m in A[j % 3]; Ybar_0 = dX.
+    auto bar_ptr = [&](int j) -> void* { return j == 0 ? dX : (void*)bl.A[j % 3]; };
+    auto bar_ld = [&](int j) -> int64_t { return j == m ? lddy : (j == 0 ? lddx : ldw); };
+    auto bar_cptr = [&](int j) -> const void* { return j == m ? dY : (const void*)bar_ptr(j); };
+
+    for (int i = bl.nseg - 1; i >= 0; i--) {
+        const int s0 = i * S;
+        const int e0 = (s0 + S < m) ? s0 + S : m;
+        // replay Y_{s0+1} .. Y_{e0-1} from the checkpoint pair (Y_{s0-1}, Y_{s0}), which the
+        // forward pass stored in dedicated slots (fptr[0] = X); rotating buffers are not read
+        std::vector<const void*> yp(e0 - s0, nullptr);
+        std::vector<int64_t> yl(e0 - s0, ldw);
+        const void* prevp = (s0 == 0) ? nullptr : fptr[s0 - 1];
+        const int64_t prevl = (s0 == 0) ? ldw : fld[s0 - 1];
+        yp[0] = fptr[s0];
+        yl[0] = fld[s0];
+        for (int k = s0 + 1; k <= e0 - 1; k++) {
+            void* out = bl.seg[k - s0 - 1];
+            const void* pp = (k - 2 - s0 >= 0) ? yp[k - 2 - s0] : prevp;
+            const int64_t pl = (k - 2 - s0 >= 0) ? yl[k - 2 - s0] : prevl;
+            if ((rc = step(yp[k - 1 - s0], yl[k - 1 - s0], k >= 2 ? pp : nullptr, pl, out, ldw, al[k],
+                           k >= 2 ? be[k] : 0.0)))
+                return rc;
+            yp[k - s0] = out;
+        }
+        // reverse steps k = e0 .. s0+1
+        for (int k = e0; k >= s0 + 1; k--) {
+            if (want_dH && (rc = sddmm(bar_cptr(k), bar_ld(k), yp[k - 1 - s0], yl[k - 1 - s0], al[k]))) return rc;
+            const void* prev = k + 1 <= m ? bar_cptr(k + 1) : nullptr;
+            if ((rc = step(bar_cptr(k), bar_ld(k), prev, k + 1 <= m ? bar_ld(k + 1) : 0, bar_ptr(k - 1),
+                           bar_ld(k - 1), al[k], k + 1 <= m ? be[k + 1] : 0.0)))
+                return rc;
+        }
+    }
+    return CHFSI_OK;
+}
+
+int backward_check(const chfsi_matrix* H, int64_t n_cols, int32_t m, int32_t ckpt_stride, int32_t precision,
+                   int64_t* N) {
+    int rc = rows_of(H, N);
+    if (rc) return rc;
+    if (!has_csr(H)) return CHFSI_ERR_UNSUPPORTED;
+    if (n_cols < 0 || m < 1 || ckpt_stride < 0) return CHFSI_ERR_ARG;
+    if (precision != CHFSI_F64 && precision != CHFSI_F32X2) return CHFSI_ERR_ARG;
+    return CHFSI_OK;
 }
 
 }  // namespace
 
-int chfsi_filter_backward_workspace_size(const chfsi_matrix* H, int64_t n_cols, int32_t m, int32_t ckpt_stride,
-                                         size_t* bytes) {
+int chfsi_filter_backward_ex_workspace_size(const chfsi_matrix* H, int64_t n_cols, int32_t m, int32_t ckpt_stride,
+                                            int32_t precision, size_t* bytes) {
     if (!bytes) return CHFSI_ERR_ARG;
     int64_t N = 0;
-    int rc = rows_of(H, &N);
+    int rc = backward_check(H, n_cols, m, ckpt_stride, precision, &N);
     if (rc) return rc;
-    if (!has_csr(H)) return CHFSI_ERR_UNSUPPORTED;
-    if (n_cols < 0 || m < 1 || ckpt_stride < 0) return CHFSI_ERR_ARG;
     SizeOnly sz;
-    back_layout(sz, N, n_cols, m, ckpt_stride, nullptr);
+    back_layout(sz, N, n_cols, m, ckpt_stride, precision, H->csr.nnz, nullptr);
     *bytes = sz.used;
     return CHFSI_OK;
 }
 
-int chfsi_filter_backward(const chfsi_matrix* H, const double* X, int64_t ldx, const double* dY, int64_t lddy,
-                          double* dX, int64_t lddx, double* dH_val, int64_t n_cols, int32_t m, double a, double b,
-                          double a0, int32_t ckpt_stride, void* ws, size_t ws_bytes, void* stream) {
+int chfsi_filter_backward_workspace_size(const chfsi_matrix* H, int64_t n_cols, int32_t m, int32_t ckpt_stride,
+                                         size_t* bytes) {
+    return chfsi_filter_backward_ex_workspace_size(H, n_cols, m, ckpt_stride, CHFSI_F64, bytes);
+}
+
+int chfsi_filter_backward_ex(const chfsi_matrix* H, const double* X, int64_t ldx, const double* dY, int64_t lddy,
+                             double* dX, int64_t lddx, double* dH_val, int64_t n_cols, int32_t m, double a, double b,
+                             double a0, int32_t ckpt_stride, int32_t precision, void* ws, size_t ws_bytes,
+                             void* stream) {
     int64_t N = 0;
-    int rc = rows_of(H, &N);
+    int rc = backward_check(H, n_cols, m, ckpt_stride, precision, &N);
     if (rc) return rc;
-    if (!has_csr(H)) return CHFSI_ERR_UNSUPPORTED;
-    if (n_cols < 0 || m < 1 || ckpt_stride < 0) return CHFSI_ERR_ARG;
     if ((rc = check_bounds(a, b, a0))) return rc;
     cudaStream_t s = as_stream(stream);
     if (n_cols == 0) {
@@ -437,11 +533,11 @@ int chfsi_filter_backward(const chfsi_matrix* H, const double* X, int64_t ldx, c
     if (dX == X || dX == dY) return CHFSI_ERR_ARG;
     if (!ws || !aligned16(ws)) return CHFSI_ERR_ARG;
     SizeOnly sz;
-    back_layout(sz, N, n_cols, m, ckpt_stride, nullptr);
+    back_layout(sz, N, n_cols, m, ckpt_stride, precision, H->csr.nnz, nullptr);
     if (ws_bytes < sz.used) return CHFSI_ERR_NOMEM;
     Arena ar(ws, ws_bytes);
     BackLayout bl;
-    back_layout(ar, N, n_cols, m, ckpt_stride, &bl);
+    back_layout(ar, N, n_cols, m, ckpt_stride, precision, H->csr.nnz, &bl);
     unsigned* st = status_word(ws);
     CHFSI_CUDA_TRY(cudaMemsetAsync(st, 0, sizeof(unsigned), s));
 
@@ -449,84 +545,50 @@ int chfsi_filter_backward(const chfsi_matrix* H, const double* X, int64_t ldx, c
     double c = 0.0;
     coefficients(m, a, b, a0, al, be, c);
     const int64_t n = n_cols, ldw = pad8(n);
-    const bool vec = (n % 2 == 0) && (ldx % 2 == 0) && (lddy % 2 == 0) && (lddx % 2 == 0);
-    CsrDev h{H->csr.n_rows, H->csr.nnz, H->csr.row_ptr, H->csr.col, H->csr.val, Buf::F64};
-    const int S = bl.S;
-
-    // Forward pass to the last checkpoint.  Checkpoint pair of segment i >= 1:
-    // Y_{iS-1} -> ck[2(i-1)], Y_{iS} -> ck[2(i-1)+1]; other iterates rotate in A[].
-    auto ck_slot = [&](int k) -> double* {
-        for (int i = 1; i < bl.nseg; i++) {
-            if (k == i * S - 1) return bl.ck[2 * (i - 1)];
-            if (k == i * S) return bl.ck[2 * (i - 1) + 1];
-        }
-        return nullptr;
-    };
-    std::vector<const double*> fptr(m + 1, nullptr);
-    std::vector<int64_t> fld(m + 1, ldw);
-    fptr[0] = X;
-    fld[0] = ldx;
-    const int k_last = (bl.nseg - 1) * S;
-    for (int k = 1; k <= k_last; k++) {
-        double* out = ck_slot(k);
-        if (!out) out = bl.A[k % 3];
-        StepIO io{};
-        io.cur = fptr[k - 1]; io.cur_t = Buf::F64; io.ldc = fld[k - 1];
-        io.gather = io.cur; io.gather_t = Buf::F64; io.ldg = io.ldc;
-        if (k >= 2) { io.prev = fptr[k - 2]; io.prev_t = Buf::F64; io.ldp = fld[k - 2]; }
-        io.out = out; io.out_t = Buf::F64; io.ldo = ldw;
-        if ((rc = csr_step(h, StepMath::F64, n, io, al[k], c, k >= 2 ? be[k] : 0.0, vec, st, s))) return rc;
-        fptr[k] = out;
-        fld[k] = ldw;
-    }
-
     if (dH_val && (rc = fill_zero(dH_val, sizeof(double) * (size_t)H->csr.nnz, s))) return rc;
 
-    // Adjoint iterates: Ybar_m = dY; Ybar_j for 1 <= j < m in A[j % 3]; Ybar_0 = dX.
-    auto bar_ptr = [&](int j) -> double* { return j == 0 ? dX : bl.A[j % 3]; };
-    auto bar_ld = [&](int j) -> int64_t { return j == m ? lddy : (j == 0 ? lddx : ldw); };
-    auto bar_cptr = [&](int j) -> const double* { return j == m ? dY : bar_ptr(j); };
-
-    for (int i = bl.nseg - 1; i >= 0; i--) {
-        const int s0 = i * S;
-        const int e0 = (s0 + S < m) ? s0 + S : m;
-        // replay Y_{s0+1} .. Y_{e0-1} from the checkpoint pair (Y_{s0-1}, Y_{s0})
-        // the pair was stored by the forward pass in dedicated checkpoint slots
-        // (fptr[0] = X); iterates in the rotating buffers are never read here
-        std::vector<const double*> yp(e0 - s0, nullptr);
-        std::vector<int64_t> yl(e0 - s0, ldw);
-        const double* prevp = (s0 == 0) ? nullptr : fptr[s0 - 1];
-        const int64_t prevl = (s0 == 0) ? ldw : fld[s0 - 1];
-        yp[0] = fptr[s0];
-        yl[0] = fld[s0];
-        for (int k = s0 + 1; k <= e0 - 1; k++) {
-            double* out = bl.seg[k - s0 - 1];
+    if (precision == CHFSI_F64) {
+        const bool vec = (n % 2 == 0) && (ldx % 2 == 0) && (lddy % 2 == 0) && (lddx % 2 == 0);
+        const CsrDev h{H->csr.n_rows, H->csr.nnz, H->csr.row_ptr, H->csr.col, H->csr.val, Buf::F64};
+        BackStep step = [&](const void* cur, int64_t ldc, const void* prev, int64_t ldp, void* out, int64_t ldo,
+                            double alpha, double beta) {
             StepIO io{};
-            io.cur = yp[k - 1 - s0]; io.cur_t = Buf::F64; io.ldc = yl[k - 1 - s0];
-            io.gather = io.cur; io.gather_t = Buf::F64; io.ldg = io.ldc;
-            const double* pp = (k - 2 - s0 >= 0) ? yp[k - 2 - s0] : prevp;
-            int64_t pl = (k - 2 - s0 >= 0) ? yl[k - 2 - s0] : prevl;
-            if (k >= 2) { io.prev = pp; io.prev_t = Buf::F64; io.ldp = pl; }
-            io.out = out; io.out_t = Buf::F64; io.ldo = ldw;
-            if ((rc = csr_step(h, StepMath::F64, n, io, al[k], c, k >= 2 ? be[k] : 0.0, vec, st, s))) return rc;
-            yp[k - s0] = out;
-        }
-        // reverse steps k = e0 .. s0+1
-        for (int k = e0; k >= s0 + 1; k--) {
-            const double* ykm1 = yp[k - 1 - s0];
-            const int64_t ldk = yl[k - 1 - s0];
-            if (dH_val && (rc = sddmm_accumulate(h, n, bar_cptr(k), bar_ld(k), ykm1, ldk, al[k], dH_val, s)))
-                return rc;
-            StepIO io{};
-            io.cur = bar_cptr(k); io.cur_t = Buf::F64; io.ldc = bar_ld(k);
-            io.gather = io.cur; io.gather_t = Buf::F64; io.ldg = io.ldc;
-            if (k + 1 <= m) { io.prev = bar_cptr(k + 1); io.prev_t = Buf::F64; io.ldp = bar_ld(k + 1); }
-            io.out = bar_ptr(k - 1); io.out_t = Buf::F64; io.ldo = bar_ld(k - 1);
-            if ((rc = csr_step(h, StepMath::F64, n, io, al[k], c, k + 1 <= m ? be[k + 1] : 0.0, vec, st, s)))
-                return rc;
-        }
+            io.cur = cur; io.cur_t = Buf::F64; io.ldc = ldc;
+            io.gather = cur; io.gather_t = Buf::F64; io.ldg = ldc;
+            if (prev) { io.prev = prev; io.prev_t = Buf::F64; io.ldp = ldp; }
+            io.out = out; io.out_t = Buf::F64; io.ldo = ldo;
+            return csr_step(h, StepMath::F64, n, io, alpha, c, beta, vec, st, s);
+        };
+        BackSddmm sddmm = [&](const void* yb, int64_t ldb, const void* ypv, int64_t ldp, double alpha) {
+            return sddmm_accumulate(h, n, static_cast<const double*>(yb), ldb, static_cast<const double*>(ypv), ldp,
+                                    alpha, dH_val, s);
+        };
+        return backward_sweep(m, bl, ldw, al, be, X, ldx, dY, lddy, dX, lddx, dH_val != nullptr, step, sddmm);
     }
-    return CHFSI_OK;
+
+    // two-float: hi/lo copies of X, dY and H; Ybar_0 widened into dX at the end
+    if ((rc = to_f32x2(H->csr.val, 1, bl.H2, 1, H->csr.nnz, 1, s))) return rc;
+    if ((rc = to_f32x2(X, ldx, bl.X2, ldw, N, n, s))) return rc;
+    if ((rc = to_f32x2(dY, lddy, bl.G2, ldw, N, n, s))) return rc;
+    const CsrDev h2{H->csr.n_rows, H->csr.nnz, H->csr.row_ptr, H->csr.col, bl.H2, Buf::F32X2};
+    BackStep step = [&](const void* cur, int64_t ldc, const void* prev, int64_t ldp, void* out, int64_t ldo,
+                        double alpha, double beta) {
+        return csr_step_f32x2(h2, n, cur, ldc, prev, prev ? ldp : 0, out, ldo, alpha, c, beta, st, s);
+    };
+    BackSddmm sddmm = [&](const void* yb, int64_t ldb, const void* ypv, int64_t ldp, double alpha) {
+        return sddmm_accumulate_f32x2(h2, n, yb, ldb, ypv, ldp, alpha, dH_val, s);
+    };
+    if ((rc = backward_sweep(m, bl, ldw, al, be, bl.X2, ldw, bl.G2, ldw, bl.D0, ldw, dH_val != nullptr, step,
+                             sddmm)))
+        return rc;
+    return from_f32x2(bl.D0, ldw, dX, lddx, N, n, s);
+}
+
+int chfsi_filter_backward(const chfsi_matrix* H, const double* X, int64_t ldx, const double* dY, int64_t lddy,
+                          double* dX, int64_t lddx, double* dH_val, int64_t n_cols, int32_t m, double a, double b,
+                          double a0, int32_t ckpt_stride, void* ws, size_t ws_bytes, void* stream) {
+    return chfsi_filter_backward_ex(H, X, ldx, dY, lddy, dX, lddx, dH_val, n_cols, m, a, b, a0, ckpt_stride,
+                                    CHFSI_F64, ws, ws_bytes, stream);
 }
 
 // ------------------------------------------------------------------ Rayleigh-Ritz

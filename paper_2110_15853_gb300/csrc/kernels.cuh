@@ -103,6 +103,11 @@ size_t lanczos_part_count(int64_t N, int steps);
 int sddmm_accumulate(const CsrDev& h, int64_t n, const double* Ybar, int64_t ldb,
                      const double* Yprev, int64_t ldp, double alpha, double* dH, cudaStream_t s);
 
+// Two-float (float2 hi/lo) variant of sddmm_accumulate; ld in float2 elements (even), n even
+// or padded with zero columns.
+int sddmm_accumulate_f32x2(const CsrDev& h, int64_t n, const void* Ybar, int64_t ldb, const void* Yprev,
+                           int64_t ldp, double alpha, double* dH, cudaStream_t s);
+
 int fill_zero(void* p, size_t bytes, cudaStream_t s);
 
 }  // namespace chfsi

@@ -383,6 +383,20 @@ def test_adjoint_matches_oracle(P, oracle_mod, g, w, n, m, stride):
     assert rel_fro(dH.cpu().numpy(), dH_ref) <= 1e-10
 
 
+@pytest.mark.parametrize("g,w,n,m,stride", [(8, 2, 5, 7, 0), (6, 3, 4, 9, 2), (8, 2, 6, 16, 1), (10, 2, 70, 6, 0)])
+def test_adjoint_f32x2_matches_oracle(P, oracle_mod, g, w, n, m, stride):
+    """Two-float reverse sweep (replay, reverse recurrence, dH products) against the
+    oracle's FP64 reverse mode at the adjoint tolerance."""
+    H, X = make_case(g, w, n, seed=80 + m)
+    (a, b, a0), _ = bounds_for(oracle_mod, H, max(1, n))
+    wts = W.loss_weights(H["N"], 3)
+    G = 2.0 * wts[:, None] * oracle_mod.filter(H, X, m, a, b, a0)
+    dX_ref, dH_ref = oracle_mod.filter_adjoint(H, X, m, a, b, a0, G)
+    dX, dH = P.filter_backward(to_dev(P, H), dev(X), dev(G), m, a, b, a0, ckpt_stride=stride, precision="f32x2")
+    assert rel_fro(dX.cpu().numpy(), dX_ref) <= 1e-10
+    assert rel_fro(dH.cpu().numpy(), dH_ref) <= 1e-10
+
+
 def test_adjoint_autograd_and_finite_differences(P, oracle_mod):
     """L = tr(Y^T W Y) through torch.autograd; dL/dH checked against central
     differences (step 1e-6) of the GPU forward on sampled entries."""
