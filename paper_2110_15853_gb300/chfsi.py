@@ -282,6 +282,31 @@ def lanczos_bounds(H: CsrMatrix, v0: torch.Tensor, steps: int, n_wanted: int,
     return a.value, b.value, a0.value
 
 
+def solve(H, X: torch.Tensor, m: int, cycles: int, v0: torch.Tensor, lanczos_steps: int = 20, schedule=None,
+          rr_precision: str = "f64", cholqr_passes: int = 2, workspace: Optional[Workspace] = None):
+    """Repeated ChFSI cycles: Algorithm 1 applied again with the previous cycle's
+    Psi as X (Sec. 3.4: later SCF iterations start from the previous Psi).
+
+    Cycle 1 takes its bounds from chfsi_lanczos_bounds; later cycles use the
+    Zhou-Saad update a0 = smallest and a = largest Ritz value of the previous
+    cycle, with b (the Lanczos upper bound of the spectrum) kept.  Returns
+    (ritz, Psi, history) with history[i] the Ritz values after cycle i + 1.
+    """
+    N, n = X.shape
+    ws_f, ws_r = workspace or Workspace(X.device), Workspace(X.device)
+    a, b, a0 = lanczos_bounds(H, v0, lanczos_steps, n, workspace=ws_f)
+    Y = torch.empty_like(X)
+    psi = X.clone()
+    ritz = torch.empty(n, dtype=torch.float64, device=X.device)
+    history = []
+    for _ in range(cycles):
+        filter(H, psi, m, a, b, a0, schedule=schedule, out=Y, workspace=ws_f)
+        ritz, psi = rayleigh_ritz(H, Y, cholqr_passes, psi=psi, ritz=ritz, workspace=ws_r, precision=rr_precision)
+        history.append(ritz.clone())
+        a0, a = float(ritz[0]), float(ritz[-1])
+    return ritz, psi, history
+
+
 class ChebyshevFilter(torch.autograd.Function):
     """Y_m = p(H) X with gradients into X and into H's stored values.
 

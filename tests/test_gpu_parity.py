@@ -367,6 +367,29 @@ def test_rayleigh_ritz_rank_deficient_reports_cholesky(P, oracle_mod):
     assert e.value.code == 4
 
 
+@pytest.mark.parametrize("rr_precision,schedule", [("f64", None), ("f32x2", "f32x2")])
+def test_repeated_cycles_converge_to_eigh(P, oracle_mod, rr_precision, schedule):
+    """Several ChFSI cycles (Psi of one cycle is X of the next, Zhou-Saad bound
+    updates): the lowest 36 of 48 Ritz values converge to brute-force eigvalsh."""
+    from tests.util import csr_to_dense
+    g, w, n, m = 10, 2, 48, 10
+    H = W.csr_grid(g, w, 0.1, 7)
+    lam = np.linalg.eigvalsh(csr_to_dense(H))
+    X = W.start_block(H["N"], n, 7)
+    sched = None if schedule is None else [schedule] * m
+    ritz, psi, hist = P.solve(to_dev(P, H), dev(X), m, 9, dev(W.lanczos_start(H["N"], 7)), schedule=sched,
+                              rr_precision=rr_precision)
+    th = ritz.cpu().numpy()
+    assert np.max(np.abs(th[:36] - lam[:36]) / np.abs(lam[:36])) <= 1e-12
+    errs = [np.max(np.abs(h.cpu().numpy()[:36] - lam[:36])) for h in hist]
+    assert errs[0] > 1e-3 and errs[-1] < 1e-11          # it did converge, from far away
+    p = psi.cpu().numpy()
+    A = csr_to_dense(H)
+    assert np.max(np.abs(p.T @ p - np.eye(n))) <= 1e-12
+    r = A @ p[:, :36] - p[:, :36] * th[:36]
+    assert np.max(np.linalg.norm(r, axis=0)) <= 1e-6
+
+
 # --------------------------------------------------------------------------- adjoint
 
 
@@ -484,3 +507,38 @@ def test_error_paths(P, oracle_mod):
     # a clean call leaves the status word clear
     P.filter(Hd, Xd, 3, a, b, a0, workspace=ws)
     assert P.read_status(ws) == 0
+
+
+def test_edge_cases_empty_and_unsupported(P, oracle_mod):
+    """n_cols = 0 is a no-op; two-float needs the CSR layout; a schedule must list
+    the low-precision steps as a prefix; single-row operators work."""
+    import ctypes
+    from paper_2110_15853_gb300 import _abi
+    lib = P.load()
+    H, X = make_case(4, 1, 3, seed=99)
+    Hd = to_dev(P, H)
+    desc = Hd.descriptor()
+    ws = P.Workspace(DEV).get(1 << 20)
+    Xd = dev(X)
+    Y = torch.full_like(Xd, 3.0)
+    stream = torch.cuda.current_stream().cuda_stream
+    rc = lib.chfsi_filter(ctypes.byref(desc), Xd.data_ptr(), 3, Y.data_ptr(), 3, 0, 4, 1.0, 2.0, 0.0, None,
+                          ws.data_ptr(), ws.numel(), stream)
+    assert rc == 0 and torch.all(Y == 3.0)
+    B = W.bsr_from_csr(H, 4)
+    Bd = to_dev_bsr(P, B)
+    with pytest.raises(P.ChfsiError) as e:
+        P.filter(Bd, dev(X[B["perm"]]), 4, 1.0, 2.0, 0.0, schedule=["f32x2"] * 4)
+    assert e.value.code == _abi.CHFSI_ERR_UNSUPPORTED
+    with pytest.raises(P.ChfsiError) as e:
+        P.rayleigh_ritz(Bd, dev(X[B["perm"]]), precision="f32x2")
+    assert e.value.code == _abi.CHFSI_ERR_UNSUPPORTED
+    with pytest.raises(P.ChfsiError) as e:
+        P.filter(Hd, Xd, 4, 1.0, 2.0, 0.0, schedule=["f64", "f32", "f64", "f64"])
+    assert e.value.code == _abi.CHFSI_ERR_ARG
+    # a 1 x 1 operator: the filter is the scalar T_m((h - c)/e) / T_m(tau)
+    one = dict(N=1, nnz=1, row_ptr=np.array([0, 1], dtype=np.int64), col=np.array([0], dtype=np.int32),
+               val=np.array([0.3]))
+    x = np.array([[1.5, -2.0]])
+    y = P.filter(to_dev(P, one), dev(x), 7, 1.0, 2.0, 0.0).cpu().numpy()
+    assert rel_fro(y, oracle_mod.filter(one, x, 7, 1.0, 2.0, 0.0)) <= 1e-14

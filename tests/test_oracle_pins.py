@@ -215,6 +215,20 @@ def test_rayleigh_ritz_subspace_and_interlacing(oracle_mod):
     assert np.max(np.abs(XF.T @ (A @ Psi - Psi * theta))) < 1e-12 * np.max(np.abs(lam))
 
 
+def test_repeated_cycles_converge_to_brute_force(oracle_mod):
+    """Algorithm 1 applied repeatedly (Psi -> X, Zhou-Saad bound updates): the
+    filter and the Rayleigh-Ritz closure together converge to eigvalsh."""
+    g, w, n, m = 10, 2, 48, 10
+    H = W.csr_grid(g, w, 0.1, 7)
+    lam = np.linalg.eigvalsh(csr_to_dense(H))
+    X = W.start_block(H["N"], n, 7)
+    a, b, a0 = oracle_mod.lanczos_bounds(H, W.lanczos_start(H["N"], 7), 20, n)
+    for _ in range(9):
+        theta, X, _ = oracle_mod.rayleigh_ritz(H, oracle_mod.filter(H, X, m, a, b, a0))
+        a0, a = theta[0], theta[-1]
+    assert np.max(np.abs(theta[:36] - lam[:36]) / np.abs(lam[:36])) <= 1e-12
+
+
 # --------------------------------------------------------------------------- Lanczos
 
 
