@@ -48,6 +48,14 @@ struct Sizer {
 
 inline unsigned* status_word(void* ws) { return static_cast<unsigned*>(ws); }
 
+// Kernel attributes (dynamic shared memory limits) are set once per device.
+constexpr int kMaxDevices = 64;
+inline int current_device() {
+    int d = -1;
+    if (cudaGetDevice(&d) != cudaSuccess || d < 0 || d >= kMaxDevices) return -1;
+    return d;
+}
+
 __device__ __forceinline__ void raise_status(unsigned* st, unsigned bits) {
     if (st) atomicOr(st, bits);
 }

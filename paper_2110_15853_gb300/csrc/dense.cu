@@ -122,13 +122,6 @@ __global__ void reduce_parts_kernel(const double* __restrict__ part, int splits,
     C[i * ldc + j] = s;
 }
 
-__global__ void mirror_upper_kernel(double* C, int64_t ldc, int64_t n) {
-    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= n * n) return;
-    int64_t i = idx / n, j = idx % n;
-    if ((i / TB) > (j / TB)) C[i * ldc + j] = C[j * ldc + i];
-}
-
 int run_gemm(const GemmArgs& g, cudaStream_t s) {
     if (g.M <= 0 || g.Nc <= 0) return CHFSI_OK;
     dim3 grid((unsigned)((g.Nc + TB - 1) / TB), (unsigned)((g.M + TB - 1) / TB), (unsigned)g.splits);

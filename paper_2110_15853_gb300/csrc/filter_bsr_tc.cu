@@ -324,10 +324,12 @@ int bsr_step_tc(const BsrDev& h, int64_t n, const void* ysh_in, const float* Yc,
     rc = make_map(&tmH, h.val, kBlk, h.nblocks * kBlk, kBlk);
     if (rc) return rc;
     const size_t smem = (size_t)kStages * kStageBytes + 1024;
-    static bool attr = false;
-    if (!attr) {
+    static bool attr[kMaxDevices] = {};
+    const int dev = current_device();
+    if (dev < 0) return CHFSI_ERR_CUDA;
+    if (!attr[dev]) {
         CHFSI_CUDA_TRY(cudaFuncSetAttribute(bsr_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        attr = true;
+        attr[dev] = true;
     }
     if (h.nbr > 65535) return CHFSI_ERR_UNSUPPORTED;
     dim3 grid((unsigned)((n + kTileJ - 1) / kTileJ), (unsigned)h.nbr);

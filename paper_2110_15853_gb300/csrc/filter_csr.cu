@@ -26,16 +26,10 @@ namespace {
 constexpr int kWarps = 8;            // rows (warps) per CTA
 constexpr int kThreads = kWarps * 32;
 
-template <typename T> __device__ __forceinline__ float to_f(T x);
-template <> __device__ __forceinline__ float to_f<float>(float x) { return x; }
-template <> __device__ __forceinline__ float to_f<double>(double x) { return (float)x; }
-template <> __device__ __forceinline__ float to_f<__nv_bfloat16>(__nv_bfloat16 x) { return __bfloat162float(x); }
-
 template <typename A, typename T> __device__ __forceinline__ A cvt(T x);
 template <> __device__ __forceinline__ double cvt<double, double>(double x) { return x; }
 template <> __device__ __forceinline__ double cvt<double, float>(float x) { return (double)x; }
 template <> __device__ __forceinline__ float cvt<float, float>(float x) { return x; }
-template <> __device__ __forceinline__ float cvt<float, double>(double x) { return (float)x; }
 template <> __device__ __forceinline__ float cvt<float, __nv_bfloat16>(__nv_bfloat16 x) { return __bfloat162float(x); }
 
 // Read V consecutive elements (aligned to V * sizeof(T)) through the read-only path.
@@ -233,10 +227,12 @@ int launch(const CsrDev& h, const void* hval, int64_t n, const StepIO& io, doubl
     const int cap = 6144;
     const size_t smem = (sizeof(TH) + sizeof(int32_t)) * (size_t)cap;
     auto kern = csr_step_kernel<ACC, TH, TG, TC, TP, TO, V, U, kShadow>;
-    static bool attr_set = false;   // per instantiation; smem size is a compile-time constant
-    if (!attr_set) {
+    static bool attr_set[kMaxDevices] = {};   // per instantiation and device
+    const int dev = current_device();
+    if (dev < 0) return CHFSI_ERR_CUDA;
+    if (!attr_set[dev]) {
         CHFSI_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        attr_set = true;
+        attr_set[dev] = true;
     }
     const int64_t blocks = (h.N + kWarps - 1) / kWarps;
     kern<<<(unsigned)blocks, kThreads, smem, s>>>(

@@ -225,13 +225,15 @@ int csr_step_f32x2(const CsrDev& h, int64_t n, const void* Yc, int64_t ldc, cons
     if (cap < 256) cap = 256;
     if (cap > kCapMax) cap = kCapMax;
     const size_t smem = (sizeof(float2) + sizeof(int32_t)) * (size_t)cap;
-    static bool attr = false;
-    if (!attr) {
+    static bool attr[kMaxDevices] = {};
+    const int dev = current_device();
+    if (dev < 0) return CHFSI_ERR_CUDA;
+    if (!attr[dev]) {
         CHFSI_CUDA_TRY(cudaFuncSetAttribute(csr_step_f32x2_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             (int)((sizeof(float2) + sizeof(int32_t)) * kCapMax)));
         CHFSI_CUDA_TRY(cudaFuncSetAttribute(csr_step_f32x2_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             (int)((sizeof(float2) + sizeof(int32_t)) * kCapMax)));
-        attr = true;
+        attr[dev] = true;
     }
     const int64_t blocks = (h.N + kWarps - 1) / kWarps;
     // 4 chunks of 64 states per pass when n fills them, else 2

@@ -542,3 +542,36 @@ def test_edge_cases_empty_and_unsupported(P, oracle_mod):
     x = np.array([[1.5, -2.0]])
     y = P.filter(to_dev(P, one), dev(x), 7, 1.0, 2.0, 0.0).cpu().numpy()
     assert rel_fro(y, oracle_mod.filter(one, x, 7, 1.0, 2.0, 0.0)) <= 1e-14
+
+
+@pytest.mark.parametrize("schedule", [None, "f32x2", "f32"])
+def test_long_rows_use_the_unstaged_path(P, oracle_mod, schedule):
+    """Rows too long for the CTA's shared-memory slice (a dense 1000 x 1000
+    symmetric H: 8 rows x 1000 entries > the staging capacity) read their entries
+    from global memory instead; results are unchanged."""
+    from tests.util import dense_to_csr
+    rng = np.random.default_rng(17)
+    N, n, m = 1000, 16, 5
+    A = rng.standard_normal((N, N)) * 0.01
+    A = 0.5 * (A + A.T) + np.diag(np.linspace(1.0, 3.0, N))
+    H = dense_to_csr(A)
+    X = np.linalg.qr(rng.standard_normal((N, n)))[0]
+    lam = np.linalg.eigvalsh(A)
+    a0, a, b = lam[0] - 0.01, lam[40], lam[-1] + 0.01
+    Yref = oracle_mod.filter(H, X, m, a, b, a0)
+    ws = P.Workspace(DEV)
+    sched = None if schedule is None else [schedule] * m
+    Y = P.filter(to_dev(P, H), dev(X), m, a, b, a0, schedule=sched, workspace=ws).cpu().numpy()
+    assert P.read_status(ws) == 0
+    assert rel_fro(Y, Yref) <= (2e-5 if schedule == "f32" else 1e-12)
+
+
+def test_nonfinite_reported_by_every_arithmetic(P, oracle_mod):
+    H, X = make_case(6, 2, 8, seed=81)
+    (a, b, a0), _ = bounds_for(oracle_mod, H, 8)
+    Xn = dev(X)
+    Xn[5, 3] = float("inf")
+    ws = P.Workspace(DEV)
+    for sched in (None, ["f32x2"] * 3, ["f32"] * 3, ["bf16"] * 3):
+        P.filter(to_dev(P, H), Xn, 3, a, b, a0, schedule=sched, workspace=ws)
+        assert P.read_status(ws) == 5, sched
