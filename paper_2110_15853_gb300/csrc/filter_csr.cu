@@ -178,22 +178,43 @@ csr_step_kernel(int64_t N, const int64_t* __restrict__ row_ptr, const int32_t* _
                 for (int v = 0; v < V; v++) acc[u][v] = (ACC)0;
             }
             const int64_t j0 = jbase + (int64_t)lane * V;
-#pragma unroll 4
-            for (int q = 0; q < len; q++) {
+            // Register pipeline with two alternating buffers: the gathers of entry q+1
+            // are in flight while entry q is accumulated.  Full chunks take a
+            // predicate-free path; a bad column index (unstaged rows only) becomes a
+            // zero entry on row 0.
+            const bool full = jbase + 32 * V * U <= n;
+            auto fetch = [&](int q, ACC (&y)[U][V], ACC& h) {
                 int32_t cj = hc[q];
-                ACC h = cvt<ACC>(hv[q]);
-                if (!staged && ((uint32_t)cj >= (uint64_t)N || cj < 0)) { bad = true; continue; }
+                h = cvt<ACC>(hv[q]);
+                if (!staged && (cj < 0 || (int64_t)cj >= N)) { bad = true; cj = 0; h = (ACC)0; }
                 const TG* src = Yg + (int64_t)cj * ldg + j0;
 #pragma unroll
                 for (int u = 0; u < U; u++) {
-                    if (on[u]) {
-                        ACC y[V];
-                        ldv<ACC, TG, V>(src + u * 32 * V, y);
+                    if (full || on[u]) {
+                        ldv<ACC, TG, V>(src + u * 32 * V, y[u]);
+                    } else {
 #pragma unroll
-                        for (int v = 0; v < V; v++) acc[u][v] = fma(h, y[v], acc[u][v]);
+                        for (int v = 0; v < V; v++) y[u][v] = (ACC)0;
                     }
                 }
+            };
+            auto accumulate = [&](const ACC (&y)[U][V], ACC h) {
+#pragma unroll
+                for (int u = 0; u < U; u++)
+#pragma unroll
+                    for (int v = 0; v < V; v++) acc[u][v] = fma(h, y[u][v], acc[u][v]);
+            };
+            ACC ya[U][V], yb[U][V];
+            ACC ha = (ACC)0, hb = (ACC)0;
+            if (len > 0) fetch(0, ya, ha);
+            int q = 0;
+            for (; q + 1 < len; q += 2) {
+                fetch(q + 1, yb, hb);
+                accumulate(ya, ha);
+                if (q + 2 < len) fetch(q + 2, ya, ha);
+                accumulate(yb, hb);
             }
+            if (q < len) accumulate(ya, ha);
 #pragma unroll
             for (int u = 0; u < U; u++) {
                 if (!on[u]) continue;
@@ -277,12 +298,12 @@ int csr_step(const CsrDev& h, StepMath math, int64_t n, const StepIO& io, double
     if (h.val_t != Buf::F32) return CHFSI_ERR_UNSUPPORTED;
     if (math == StepMath::F32) {
         if (g == Buf::F32 && cu == Buf::F32 && p == Buf::F32 && o == Buf::F32)
-            return launch<float, float, float, float, float, float, 4, 2, false>(h, h.val, n, io, alpha, c, beta, status, s);
+            return launch<float, float, float, float, float, float, 4, 4, false>(h, h.val, n, io, alpha, c, beta, status, s);
         return CHFSI_ERR_UNSUPPORTED;
     }
     // BF16 operand, FP32 accumulate
     if (g == Buf::BF16 && cu == Buf::F32 && p == Buf::F32 && o == Buf::F32 && io.shadow)
-        return launch<float, float, __nv_bfloat16, float, float, float, 4, 2, true>(h, h.val, n, io, alpha, c, beta, status, s);
+        return launch<float, float, __nv_bfloat16, float, float, float, 4, 4, true>(h, h.val, n, io, alpha, c, beta, status, s);
     return CHFSI_ERR_UNSUPPORTED;
 }
 
