@@ -12,11 +12,20 @@
 // reads D from TMEM, applies the recurrence in FP32 against the FP32 iterates and
 // writes Y_out (FP32, row-major) plus its BF16 state-major copy for the next step.
 //
-// CTA = 6 warps: warp 0 lane 0 issues TMA loads (128B-swizzled tiles of Ysh^T and
-// H_RC) into a 4-stage ring, warp 1 owns the TMEM allocation and lane 0 issues the
-// MMAs, warps 2-5 run the epilogue (warp w reads TMEM lanes 32*(w%4)..+31).  Every
-// wait is bounded (1 s on %globaltimer); on timeout the CTA flags DEV_TIMEOUT,
-// stops issuing work, waits (bounded) for its copies in flight, frees TMEM and exits.
+// Persistent, warp-specialised CTA (one per SM), looping over work items
+// (block row, 128-state tile) with column tiles fastest (a block row's H blocks are
+// then shared through L2 by its tiles):
+//   warp 0, lane 0 : TMA producer -- for each item, the FP32 Y_cur / Y_prev tiles of
+//                    the epilogue (64 x 128, double-buffered) and then, per
+//                    neighbouring block, the 128B-swizzled tiles of Ysh^T and H_RC
+//                    into a 4-stage ring;
+//   warp 1         : owns the TMEM allocation (two 64-column FP32 accumulators);
+//                    lane 0 issues the MMAs into accumulator (item & 1);
+//   warps 2-5      : epilogue (warp w reads TMEM lanes 32*(w%4)..+31) of the previous
+//                    item while the MMAs of the next one run.
+// Every mbarrier wait is bounded (1 s on %globaltimer); on timeout the CTA flags
+// DEV_TIMEOUT, stops issuing work, waits (bounded) for its copies and MMAs in
+// flight, frees TMEM and exits.
 #include <cuda.h>
 
 #include "common.cuh"
@@ -27,13 +36,16 @@ namespace chfsi {
 namespace {
 
 constexpr int kStages = 4;
-constexpr int kTileJ = 128;                       // states per CTA (MMA M)
+constexpr int kTileJ = 128;                       // states per work item (MMA M)
 constexpr int kBlk = 64;                          // block edge (MMA N and K per block)
 constexpr int kATile = kTileJ * kBlk * 2;         // 16 KB
 constexpr int kBTile = kBlk * kBlk * 2;           // 8 KB
 constexpr int kStageBytes = kATile + kBTile;      // 24 KB
+constexpr int kEpiTile = kBlk * kTileJ * 4;       // 32 KB: 64 rows x 128 states FP32
+constexpr int kEpiBuf = 2 * kEpiTile;             // Y_cur + Y_prev tiles of one item
+constexpr int kSmemBytes = kStages * kStageBytes + 2 * kEpiBuf + 1024;
 constexpr int kThreads = 192;
-constexpr uint32_t kTmemCols = 64;
+constexpr uint32_t kTmemCols = 128;               // two 64-column accumulators
 constexpr uint64_t kTimeoutNs = 1000000000ull;
 
 __device__ __forceinline__ uint32_t sa(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -79,37 +91,49 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
         :: "r"(dst), "l"((uint64_t)map), "r"(x), "r"(y), "r"(bar) : "memory");
 }
 
-__global__ void __launch_bounds__(kThreads, 2)
+__device__ __forceinline__ void mbar_init(uint64_t* b, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(sa(b)), "r"(count));
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(sa(b)) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(sa(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint64_t* b) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" :: "r"(sa(b))
+                 : "memory");
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
 bsr_tc_kernel(const __grid_constant__ CUtensorMap tmY, const __grid_constant__ CUtensorMap tmH,
+              const __grid_constant__ CUtensorMap tmYc, const __grid_constant__ CUtensorMap tmYp, int has_prev,
               int64_t nbr, const int32_t* __restrict__ brow_ptr, const int32_t* __restrict__ bcol, int64_t nblocks,
-              int64_t N, int64_t n, const float* __restrict__ Yc, int64_t ldc, const float* __restrict__ Yp,
-              int64_t ldp, float* __restrict__ Yo, int64_t ldo, __nv_bfloat16* __restrict__ Ysh_out,
-              float alpha, float c, float beta, unsigned* status) {
+              int64_t N, int64_t n, int64_t ntiles, float* __restrict__ Yo, int64_t ldo,
+              __nv_bfloat16* __restrict__ Ysh_out, float alpha, float c, float beta, unsigned* status) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    __shared__ __align__(8) uint64_t full_bar[kStages], empty_bar[kStages], accum_bar;
+    unsigned char* stages = smem;                                   // kStages x (A | B), 1024-aligned
+    unsigned char* epi = smem + kStages * kStageBytes;              // 2 x (Y_cur tile | Y_prev tile)
+    __shared__ __align__(8) uint64_t full[kStages], empty[kStages], tfull[2], tempty[2], efull[2], eempty[2];
     __shared__ uint32_t tmem_slot;
     __shared__ int abort_flag;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    // column tiles vary fastest, so the tiles of one block row run together and
-    // share its H blocks through L2 (each block is then read from DRAM once)
-    const int64_t R = blockIdx.y;
-    const int64_t j0 = (int64_t)blockIdx.x * kTileJ;
-
-    int qb = brow_ptr[R], qe = brow_ptr[R + 1];
+    const int64_t total = nbr * ntiles;
     bool bad = false;
-    if (qb < 0) { qb = 0; bad = true; }
-    if (qe > nblocks) { qe = (int)nblocks; bad = true; }
-    if (qe < qb) { qe = qb; bad = true; }
-    const int count = qe - qb;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; s++) {
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(sa(&full_bar[s])));
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(sa(&empty_bar[s])));
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
         }
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(sa(&accum_bar)));
+        for (int b = 0; b < 2; b++) {
+            mbar_init(&tfull[b], 1);
+            mbar_init(&tempty[b], 4);
+            mbar_init(&efull[b], 1);
+            mbar_init(&eempty[b], 4);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;");
         asm volatile("fence.proxy.async.shared::cta;");
         abort_flag = 0;
@@ -123,106 +147,152 @@ bsr_tc_kernel(const __grid_constant__ CUtensorMap tmY, const __grid_constant__ C
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = tmem_slot;
+    volatile int* abort_v = &abort_flag;
+
+    // block range of a block row, clamped to the stored blocks
+    auto blocks_of = [&](int64_t R, int& qb, int& qe) {
+        qb = brow_ptr[R];
+        qe = brow_ptr[R + 1];
+        if (qb < 0) { qb = 0; bad = true; }
+        if (qe > nblocks) { qe = (int)nblocks; bad = true; }
+        if (qe < qb) { qe = qb; bad = true; }
+    };
 
     if (warp == 0 && lane == 0) {
         // ---------------- TMA producer
-        int it = 0;
-        for (; it < count; it++) {
-            const int s = it % kStages;
-            if (it >= kStages) {
-                if (!mbar_wait(sa(&empty_bar[s]), ((it / kStages) - 1) & 1)) {
-                    atomicExch(&abort_flag, 1);
-                    break;
-                }
+        int64_t sc = 0;                 // stage loads issued
+        int items = 0;                  // items whose epilogue tiles were issued
+        for (int64_t item = blockIdx.x; item < total && !*abort_v; item += gridDim.x, items++) {
+            const int64_t R = item / ntiles, t = item % ntiles;
+            const int b = items & 1, v = items >> 1;
+            if (v >= 1 && !mbar_wait(sa(&eempty[b]), (v - 1) & 1)) { *abort_v = 1; break; }
+            unsigned char* eb = epi + b * kEpiBuf;
+            mbar_expect_tx(&efull[b], has_prev ? 2 * kEpiTile : kEpiTile);
+            tma_load_2d(sa(eb), &tmYc, (int)(t * kTileJ), (int)(R * kBlk), sa(&efull[b]));
+            if (has_prev) tma_load_2d(sa(eb + kEpiTile), &tmYp, (int)(t * kTileJ), (int)(R * kBlk), sa(&efull[b]));
+            int qb, qe;
+            blocks_of(R, qb, qe);
+            for (int q = qb; q < qe; q++, sc++) {
+                const int s = (int)(sc % kStages), u = (int)(sc / kStages);
+                if (u >= 1 && !mbar_wait(sa(&empty[s]), (u - 1) & 1)) { *abort_v = 1; break; }
+                int C = bcol[q];
+                if (C < 0 || (int64_t)C >= nbr) { bad = true; C = 0; }   // zero-safe: still a valid tile
+                const uint32_t st = sa(stages + (size_t)s * kStageBytes);
+                mbar_expect_tx(&full[s], kStageBytes);
+                tma_load_2d(st, &tmY, C * kBlk, (int)(t * kTileJ), sa(&full[s]));
+                tma_load_2d(st + kATile, &tmH, 0, q * kBlk, sa(&full[s]));
             }
-            if (*(volatile int*)&abort_flag) break;
-            int C = bcol[qb + it];
-            if (C < 0 || (int64_t)C >= nbr) { bad = true; C = 0; }   // zero-safe: still a valid tile
-            const uint32_t st = sa(smem + (size_t)s * kStageBytes);
-            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(sa(&full_bar[s])),
-                         "r"(kStageBytes));
-            tma_load_2d(st, &tmY, C * kBlk, (int)j0, sa(&full_bar[s]));
-            tma_load_2d(st + kATile, &tmH, 0, (qb + it) * kBlk, sa(&full_bar[s]));
         }
         // wait (bounded) until every copy this thread issued has landed
-        const int issued = it;
-        for (int s = 0; s < kStages && s < issued; s++) {
-            const int last = s + ((issued - 1 - s) / kStages) * kStages;
-            mbar_wait(sa(&full_bar[s]), (last / kStages) & 1);
+        for (int s = 0; s < kStages && s < sc; s++) {
+            const int64_t last = s + ((sc - 1 - s) / kStages) * kStages;
+            mbar_wait(sa(&full[s]), (int)(last / kStages) & 1);
+        }
+        for (int b = 0; b < 2 && b < items; b++) {
+            const int last = b + ((items - 1 - b) / 2) * 2;
+            mbar_wait(sa(&efull[b]), (last >> 1) & 1);
         }
     } else if (warp == 1 && lane == 0) {
         // ---------------- MMA issuer
-        int it = 0;
-        for (; it < count; it++) {
-            const int s = it % kStages;
-            if (!mbar_wait(sa(&full_bar[s]), (it / kStages) & 1) || *(volatile int*)&abort_flag) {
-                atomicExch(&abort_flag, 1);
-                break;
-            }
+        int64_t sc = 0;
+        int items = 0;
+        for (int64_t item = blockIdx.x; item < total && !*abort_v; item += gridDim.x, items++) {
+            const int64_t R = item / ntiles;
+            const int b = items & 1, v = items >> 1;
+            if (v >= 1 && !mbar_wait(sa(&tempty[b]), (v - 1) & 1)) { *abort_v = 1; break; }
             asm volatile("tcgen05.fence::after_thread_sync;");
-            const uint32_t st = sa(smem + (size_t)s * kStageBytes);
-            const uint64_t da = desc_sw128(st), db = desc_sw128(st + kATile);
+            const uint32_t acc_addr = tmem + (uint32_t)(b * kBlk);
+            int qb, qe;
+            blocks_of(R, qb, qe);
+            bool ok = true;
+            for (int q = qb; q < qe; q++, sc++) {
+                const int s = (int)(sc % kStages), u = (int)(sc / kStages);
+                if (!mbar_wait(sa(&full[s]), u & 1) || *abort_v) { *abort_v = 1; ok = false; break; }
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                const uint32_t st = sa(stages + (size_t)s * kStageBytes);
+                const uint64_t da = desc_sw128(st), db = desc_sw128(st + kATile);
 #pragma unroll
-            for (int k = 0; k < kBlk / 16; k++) {
-                const uint32_t acc = (it > 0 || k > 0) ? 1u : 0u;
-                asm volatile(
-                    "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n"
-                    :: "r"(tmem), "l"(da + 2 * k), "l"(db + 2 * k), "r"(kIdesc), "r"(acc));
+                for (int k = 0; k < kBlk / 16; k++) {
+                    const uint32_t accumulate = (q > qb || k > 0) ? 1u : 0u;
+                    asm volatile(
+                        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n"
+                        :: "r"(acc_addr), "l"(da + 2 * k), "l"(db + 2 * k), "r"(kIdesc), "r"(accumulate));
+                }
+                umma_commit(&empty[s]);
             }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                         :: "r"(sa(&empty_bar[s])));
+            umma_commit(&tfull[b]);   // accumulator b complete (also with zero blocks)
+            if (!ok) { items++; break; }
         }
-        // accumulator complete (also covers the zero-block case: commit with nothing pending)
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                     :: "r"(sa(&accum_bar)));
-        mbar_wait(sa(&accum_bar), 0);
+        // every MMA this thread issued has completed before TMEM is released
+        if (items > 0) {
+            const int lb = (items - 1) & 1, lv = (items - 1) >> 1;
+            mbar_wait(sa(&tfull[lb]), lv & 1);
+        }
     } else if (warp >= 2) {
         // ---------------- epilogue
         const int quad = warp & 3;
-        const int64_t j = j0 + quad * 32 + lane;
-        const bool ok = mbar_wait(sa(&accum_bar), 0) && !*(volatile int*)&abort_flag;
-        if (!ok) atomicExch(&abort_flag, 1);
-        asm volatile("tcgen05.fence::after_thread_sync;");
-        bool nonfinite = false;
-        const int64_t row0 = R * kBlk;
+        int items = 0;
+        for (int64_t item = blockIdx.x; item < total; item += gridDim.x, items++) {
+            const int64_t R = item / ntiles, t = item % ntiles;
+            const int b = items & 1, v = items >> 1;
+            const bool ok = !*abort_v && mbar_wait(sa(&tfull[b]), v & 1) && mbar_wait(sa(&efull[b]), v & 1);
+            if (!ok) { *abort_v = 1; break; }
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            int qb, qe;
+            blocks_of(R, qb, qe);
+            const bool has_acc = qe > qb;
+            const int jl = quad * 32 + lane;                      // state within the tile
+            const int64_t j = t * kTileJ + jl;
+            const float* ycs = reinterpret_cast<const float*>(epi + b * kEpiBuf);
+            const float* yps = ycs + kBlk * kTileJ;
+            const int64_t row0 = R * kBlk;
+            bool nonfinite = false;
 #pragma unroll 1
-        for (int cchunk = 0; cchunk < kBlk / 16; cchunk++) {
-            uint32_t r[16];
-            const uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(cchunk * 16);
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-                  "=r"(r[15])
-                : "r"(taddr));
-            asm volatile("tcgen05.wait::ld.sync.aligned;");
-            if (!ok || j >= n) continue;
-            float out[16];
+            for (int cchunk = 0; cchunk < kBlk / 16; cchunk++) {
+                uint32_t r[16];
+                const uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(b * kBlk + cchunk * 16);
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+                    "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                    : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                      "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+                      "=r"(r[14]), "=r"(r[15])
+                    : "r"(taddr));
+                asm volatile("tcgen05.wait::ld.sync.aligned;");
+                if (j >= n) continue;
+                float out[16];
 #pragma unroll
-            for (int t = 0; t < 16; t++) {
-                const int64_t row = row0 + cchunk * 16 + t;
-                const float acc = (count > 0) ? __uint_as_float(r[t]) : 0.0f;
-                const float yc = Yc[row * ldc + j];
-                float v = alpha * fmaf(-c, yc, acc);
-                if (Yp) v = fmaf(-beta, Yp[row * ldp + j], v);
-                nonfinite |= !isfinite(v);
-                Yo[row * ldo + j] = v;
-                out[t] = v;
-            }
-            // 16 consecutive rows of state j -> two 16-byte stores of the state-major copy
-            uint4 pk[2];
-            unsigned* pw = reinterpret_cast<unsigned*>(pk);
+                for (int tt = 0; tt < 16; tt++) {
+                    const int rl = cchunk * 16 + tt;
+                    const float acc = has_acc ? __uint_as_float(r[tt]) : 0.0f;
+                    float val = alpha * fmaf(-c, ycs[rl * kTileJ + jl], acc);
+                    if (has_prev) val = fmaf(-beta, yps[rl * kTileJ + jl], val);
+                    nonfinite |= !isfinite(val);
+                    Yo[(row0 + rl) * ldo + j] = val;
+                    out[tt] = val;
+                }
+                // 16 consecutive rows of state j -> two 16-byte stores of the state-major copy
+                uint4 pk[2];
+                unsigned* pw = reinterpret_cast<unsigned*>(pk);
 #pragma unroll
-            for (int t = 0; t < 8; t++) {
-                __nv_bfloat162 h2 = __floats2bfloat162_rn(out[2 * t], out[2 * t + 1]);
-                pw[t] = *reinterpret_cast<unsigned*>(&h2);
+                for (int tt = 0; tt < 8; tt++) {
+                    __nv_bfloat162 h2 = __floats2bfloat162_rn(out[2 * tt], out[2 * tt + 1]);
+                    pw[tt] = *reinterpret_cast<unsigned*>(&h2);
+                }
+                uint4* dst = reinterpret_cast<uint4*>(Ysh_out + j * N + row0 + cchunk * 16);
+                dst[0] = pk[0];
+                dst[1] = pk[1];
             }
-            uint4* dst = reinterpret_cast<uint4*>(Ysh_out + j * N + row0 + cchunk * 16);
-            dst[0] = pk[0];
-            dst[1] = pk[1];
+            if (nonfinite) raise_status(status, DEV_NONFINITE);
+            // release the accumulator and the epilogue tiles of buffer b
+            asm volatile("tcgen05.fence::before_thread_sync;");
+            __syncwarp();
+            if (lane == 0) {
+                mbar_arrive(&tempty[b]);
+                mbar_arrive(&eempty[b]);
+            }
         }
-        if (nonfinite) raise_status(status, DEV_NONFINITE);
     }
 
     asm volatile("tcgen05.fence::before_thread_sync;");
@@ -231,9 +301,7 @@ bsr_tc_kernel(const __grid_constant__ CUtensorMap tmY, const __grid_constant__ C
         asm volatile("tcgen05.fence::after_thread_sync;");
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(kTmemCols));
     }
-    if (threadIdx.x == 0) {
-        if (abort_flag) raise_status(status, DEV_TIMEOUT);
-    }
+    if (threadIdx.x == 0 && abort_flag) raise_status(status, DEV_TIMEOUT);
     if (bad) raise_status(status, DEV_PATTERN);
 }
 
@@ -276,7 +344,8 @@ EncodeTiledFn encode_fn() {
     return fn;
 }
 
-// 2-D BF16 tensor map over a row-major [rows x cols] array, box [box_rows x 64].
+// 2-D BF16 tensor map over a row-major [rows x cols] array, box [box_rows x 64],
+// 128-byte swizzle (MMA operand tiles).
 int make_map(CUtensorMap* map, const void* base, int64_t cols, int64_t rows, int box_rows) {
     EncodeTiledFn enc = encode_fn();
     if (!enc) return CHFSI_ERR_CUDA;
@@ -289,6 +358,34 @@ int make_map(CUtensorMap* map, const void* base, int64_t cols, int64_t rows, int
                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? CHFSI_OK : CHFSI_ERR_CUDA;
+}
+
+// 2-D FP32 tensor map over a row-major [rows x ld] array, box [64 rows x 128 states],
+// no swizzle (epilogue operand tiles; states beyond ld read as zero).
+int make_map_f32(CUtensorMap* map, const float* base, int64_t ld, int64_t rows) {
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) return CHFSI_ERR_CUDA;
+    if ((reinterpret_cast<uintptr_t>(base) & 15u) || ((ld * 4) % 16)) return CHFSI_ERR_ARG;
+    cuuint64_t dims[2] = {(cuuint64_t)ld, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)ld * 4};
+    cuuint32_t box[2] = {(cuuint32_t)kTileJ, (cuuint32_t)kBlk};
+    cuuint32_t es[2] = {1, 1};
+    CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides, box, es,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? CHFSI_OK : CHFSI_ERR_CUDA;
+}
+
+int sm_count() {
+    static int cache[kMaxDevices] = {};
+    const int dev = current_device();
+    if (dev < 0) return 0;
+    if (!cache[dev]) {
+        int v = 0;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+        cache[dev] = v;
+    }
+    return cache[dev];
 }
 
 }  // namespace
@@ -318,24 +415,32 @@ int bsr_step_tc(const BsrDev& h, int64_t n, const void* ysh_in, const float* Yc,
     if (h.bdim != kBlk || h.val_t != Buf::BF16) return CHFSI_ERR_UNSUPPORTED;
     const int64_t N = h.nbr * kBlk;
     if (h.nblocks * kBlk > INT32_MAX || N > INT32_MAX || n > INT32_MAX) return CHFSI_ERR_UNSUPPORTED;
-    CUtensorMap tmY, tmH;
-    int rc = make_map(&tmY, ysh_in, N, n, kTileJ);
-    if (rc) return rc;
-    rc = make_map(&tmH, h.val, kBlk, h.nblocks * kBlk, kBlk);
-    if (rc) return rc;
-    const size_t smem = (size_t)kStages * kStageBytes + 1024;
-    static bool attr[kMaxDevices] = {};
+    CUtensorMap tmY, tmH, tmYc, tmYp;
+    int rc;
+    if ((rc = make_map(&tmY, ysh_in, N, n, kTileJ))) return rc;
+    if ((rc = make_map(&tmH, h.val, kBlk, h.nblocks * kBlk, kBlk))) return rc;
+    if ((rc = make_map_f32(&tmYc, Yc, ldc, N))) return rc;
+    if (Yp) {
+        if ((rc = make_map_f32(&tmYp, Yp, ldp, N))) return rc;
+    } else {
+        tmYp = tmYc;   // not read
+    }
     const int dev = current_device();
     if (dev < 0) return CHFSI_ERR_CUDA;
+    static bool attr[kMaxDevices] = {};
     if (!attr[dev]) {
-        CHFSI_CUDA_TRY(cudaFuncSetAttribute(bsr_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        CHFSI_CUDA_TRY(cudaFuncSetAttribute(bsr_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
         attr[dev] = true;
     }
-    if (h.nbr > 65535) return CHFSI_ERR_UNSUPPORTED;
-    dim3 grid((unsigned)((n + kTileJ - 1) / kTileJ), (unsigned)h.nbr);
-    bsr_tc_kernel<<<grid, kThreads, smem, s>>>(tmY, tmH, h.nbr, h.brow_ptr, h.bcol, h.nblocks, N, n, Yc, ldc, Yp, ldp,
-                                               Yo, ldo, static_cast<__nv_bfloat16*>(ysh_out), (float)alpha, (float)c,
-                                               (float)beta, status);
+    const int64_t ntiles = (n + kTileJ - 1) / kTileJ;
+    const int64_t total = h.nbr * ntiles;
+    const int sms = sm_count();
+    if (sms <= 0) return CHFSI_ERR_CUDA;
+    const unsigned grid = (unsigned)(total < sms ? total : sms);   // persistent: one CTA per SM
+    bsr_tc_kernel<<<grid, kThreads, kSmemBytes, s>>>(tmY, tmH, tmYc, tmYp, Yp ? 1 : 0, h.nbr, h.brow_ptr, h.bcol,
+                                                     h.nblocks, N, n, ntiles, Yo, ldo,
+                                                     static_cast<__nv_bfloat16*>(ysh_out), (float)alpha, (float)c,
+                                                     (float)beta, status);
     CHFSI_LAUNCH_CHECK();
     return CHFSI_OK;
 }
