@@ -8,21 +8,23 @@
 // computed transposed, so that both MMA operands are K-major: for a block row R
 // (64 grid points) and a tile of 128 states j,
 //     D[j][i] = sum_C sum_k Ysh^T[j][C*64 + k] * H_RC[i][k]      (M = 128, N = 64, K = 64/block)
-// where Ysh^T is the BF16 copy of Y_cur stored state-major (n x N).  The epilogue
+// where Ysh^T is the BF16 copy of Y_cur, stored block-major as [N/64][n][64] so that
+// the 128 x 64 operand tile of block C and a state tile is one contiguous 16 KB read
+// (row C*n + j of a 64-wide table holds Y_cur[C*64 .. C*64+63][j]).  The epilogue
 // reads D from TMEM, applies the recurrence in FP32 against the FP32 iterates and
 // writes Y_out (FP32, row-major) plus its BF16 state-major copy for the next step.
 //
 // Persistent, warp-specialised CTA (one per SM), looping over work items
 // (block row, 128-state tile) with column tiles fastest (a block row's H blocks are
 // then shared through L2 by its tiles):
-//   warp 0, lane 0 : TMA producer -- for each item, the FP32 Y_cur / Y_prev tiles of
-//                    the epilogue (64 x 128, double-buffered) and then, per
-//                    neighbouring block, the 128B-swizzled tiles of Ysh^T and H_RC
-//                    into a 4-stage ring;
+//   warp 0, lane 0 : TMA producer of the MMA operands -- per neighbouring block, the
+//                    128B-swizzled tiles of Ysh^T and H_RC into a 6-stage ring;
 //   warp 1         : owns the TMEM allocation (two 64-column FP32 accumulators);
 //                    lane 0 issues the MMAs into accumulator (item & 1);
-//   warps 2-5      : epilogue (warp w reads TMEM lanes 32*(w%4)..+31) of the previous
-//                    item while the MMAs of the next one run.
+//   warp 2, lane 0 : TMA producer of each item's FP32 Y_cur / Y_prev epilogue tiles
+//                    (64 x 128), loaded as soon as the previous epilogue frees them;
+//   warps 3-6      : epilogue (warp w reads TMEM lanes 32*(w%4)..+31) of one item
+//                    while the MMAs of the next one run.
 // Every mbarrier wait is bounded (1 s on %globaltimer); on timeout the CTA flags
 // DEV_TIMEOUT, stops issuing work, waits (bounded) for its copies and MMAs in
 // flight, frees TMEM and exits.
@@ -35,7 +37,7 @@ namespace chfsi {
 
 namespace {
 
-constexpr int kStages = 4;
+constexpr int kStages = 6;
 constexpr int kTileJ = 128;                       // states per work item (MMA M)
 constexpr int kBlk = 64;                          // block edge (MMA N and K per block)
 constexpr int kATile = kTileJ * kBlk * 2;         // 16 KB
@@ -43,8 +45,8 @@ constexpr int kBTile = kBlk * kBlk * 2;           // 8 KB
 constexpr int kStageBytes = kATile + kBTile;      // 24 KB
 constexpr int kEpiTile = kBlk * kTileJ * 4;       // 32 KB: 64 rows x 128 states FP32
 constexpr int kEpiBuf = 2 * kEpiTile;             // Y_cur + Y_prev tiles of one item
-constexpr int kSmemBytes = kStages * kStageBytes + 2 * kEpiBuf + 1024;
-constexpr int kThreads = 192;
+constexpr int kSmemBytes = kStages * kStageBytes + kEpiBuf + 1024;
+constexpr int kThreads = 224;
 constexpr uint32_t kTmemCols = 128;               // two 64-column accumulators
 constexpr uint64_t kTimeoutNs = 1000000000ull;
 
@@ -56,16 +58,21 @@ __device__ __forceinline__ uint64_t gtime() {
     return t;
 }
 
-// Bounded wait for the phase of `parity` on an mbarrier; false on timeout.
+// Bounded wait for the phase of `parity` on an mbarrier; false on timeout.  The
+// clock is read only every 1024 polls so that a completed phase is seen at once.
 __device__ bool mbar_wait(uint32_t addr, uint32_t parity) {
-    const uint64_t t0 = gtime();
-    while (true) {
+    uint64_t t0 = 0;
+    for (uint32_t polls = 1;; polls++) {
         uint32_t done;
         asm volatile(
             "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
             : "=r"(done) : "r"(addr), "r"(parity) : "memory");
         if (done) return true;
-        if (gtime() - t0 > kTimeoutNs) return false;
+        if ((polls & 1023u) == 0) {
+            const uint64_t now = gtime();
+            if (t0 == 0) t0 = now;
+            else if (now - t0 > kTimeoutNs) return false;
+        }
     }
 }
 
@@ -114,8 +121,8 @@ bsr_tc_kernel(const __grid_constant__ CUtensorMap tmY, const __grid_constant__ C
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     unsigned char* stages = smem;                                   // kStages x (A | B), 1024-aligned
-    unsigned char* epi = smem + kStages * kStageBytes;              // 2 x (Y_cur tile | Y_prev tile)
-    __shared__ __align__(8) uint64_t full[kStages], empty[kStages], tfull[2], tempty[2], efull[2], eempty[2];
+    unsigned char* epi = smem + kStages * kStageBytes;              // Y_cur tile | Y_prev tile
+    __shared__ __align__(8) uint64_t full[kStages], empty[kStages], tfull[2], tempty[2], efull, eempty;
     __shared__ uint32_t tmem_slot;
     __shared__ int abort_flag;
 
@@ -131,9 +138,9 @@ bsr_tc_kernel(const __grid_constant__ CUtensorMap tmY, const __grid_constant__ C
         for (int b = 0; b < 2; b++) {
             mbar_init(&tfull[b], 1);
             mbar_init(&tempty[b], 4);
-            mbar_init(&efull[b], 1);
-            mbar_init(&eempty[b], 4);
         }
+        mbar_init(&efull, 1);
+        mbar_init(&eempty, 4);
         asm volatile("fence.mbarrier_init.release.cluster;");
         asm volatile("fence.proxy.async.shared::cta;");
         abort_flag = 0;
@@ -159,17 +166,10 @@ bsr_tc_kernel(const __grid_constant__ CUtensorMap tmY, const __grid_constant__ C
     };
 
     if (warp == 0 && lane == 0) {
-        // ---------------- TMA producer
+        // ---------------- TMA producer of the MMA operands
         int64_t sc = 0;                 // stage loads issued
-        int items = 0;                  // items whose epilogue tiles were issued
-        for (int64_t item = blockIdx.x; item < total && !*abort_v; item += gridDim.x, items++) {
+        for (int64_t item = blockIdx.x; item < total && !*abort_v; item += gridDim.x) {
             const int64_t R = item / ntiles, t = item % ntiles;
-            const int b = items & 1, v = items >> 1;
-            if (v >= 1 && !mbar_wait(sa(&eempty[b]), (v - 1) & 1)) { *abort_v = 1; break; }
-            unsigned char* eb = epi + b * kEpiBuf;
-            mbar_expect_tx(&efull[b], has_prev ? 2 * kEpiTile : kEpiTile);
-            tma_load_2d(sa(eb), &tmYc, (int)(t * kTileJ), (int)(R * kBlk), sa(&efull[b]));
-            if (has_prev) tma_load_2d(sa(eb + kEpiTile), &tmYp, (int)(t * kTileJ), (int)(R * kBlk), sa(&efull[b]));
             int qb, qe;
             blocks_of(R, qb, qe);
             for (int q = qb; q < qe; q++, sc++) {
@@ -179,7 +179,7 @@ bsr_tc_kernel(const __grid_constant__ CUtensorMap tmY, const __grid_constant__ C
                 if (C < 0 || (int64_t)C >= nbr) { bad = true; C = 0; }   // zero-safe: still a valid tile
                 const uint32_t st = sa(stages + (size_t)s * kStageBytes);
                 mbar_expect_tx(&full[s], kStageBytes);
-                tma_load_2d(st, &tmY, C * kBlk, (int)(t * kTileJ), sa(&full[s]));
+                tma_load_2d(st, &tmY, 0, (int)(C * n + t * kTileJ), sa(&full[s]));
                 tma_load_2d(st + kATile, &tmH, 0, q * kBlk, sa(&full[s]));
             }
         }
@@ -188,10 +188,17 @@ bsr_tc_kernel(const __grid_constant__ CUtensorMap tmY, const __grid_constant__ C
             const int64_t last = s + ((sc - 1 - s) / kStages) * kStages;
             mbar_wait(sa(&full[s]), (int)(last / kStages) & 1);
         }
-        for (int b = 0; b < 2 && b < items; b++) {
-            const int last = b + ((items - 1 - b) / 2) * 2;
-            mbar_wait(sa(&efull[b]), (last >> 1) & 1);
+    } else if (warp == 2 && lane == 0) {
+        // ---------------- TMA producer of the epilogue operand tiles
+        int items = 0;
+        for (int64_t item = blockIdx.x; item < total && !*abort_v; item += gridDim.x, items++) {
+            const int64_t R = item / ntiles, t = item % ntiles;
+            if (items >= 1 && !mbar_wait(sa(&eempty), (items - 1) & 1)) { *abort_v = 1; break; }
+            mbar_expect_tx(&efull, has_prev ? 2 * kEpiTile : kEpiTile);
+            tma_load_2d(sa(epi), &tmYc, (int)(t * kTileJ), (int)(R * kBlk), sa(&efull));
+            if (has_prev) tma_load_2d(sa(epi + kEpiTile), &tmYp, (int)(t * kTileJ), (int)(R * kBlk), sa(&efull));
         }
+        if (items > 0) mbar_wait(sa(&efull), (items - 1) & 1);
     } else if (warp == 1 && lane == 0) {
         // ---------------- MMA issuer
         int64_t sc = 0;
@@ -229,14 +236,14 @@ bsr_tc_kernel(const __grid_constant__ CUtensorMap tmY, const __grid_constant__ C
             const int lb = (items - 1) & 1, lv = (items - 1) >> 1;
             mbar_wait(sa(&tfull[lb]), lv & 1);
         }
-    } else if (warp >= 2) {
+    } else if (warp >= 3) {
         // ---------------- epilogue
         const int quad = warp & 3;
         int items = 0;
         for (int64_t item = blockIdx.x; item < total; item += gridDim.x, items++) {
             const int64_t R = item / ntiles, t = item % ntiles;
             const int b = items & 1, v = items >> 1;
-            const bool ok = !*abort_v && mbar_wait(sa(&tfull[b]), v & 1) && mbar_wait(sa(&efull[b]), v & 1);
+            const bool ok = !*abort_v && mbar_wait(sa(&tfull[b]), v & 1) && mbar_wait(sa(&efull), items & 1);
             if (!ok) { *abort_v = 1; break; }
             asm volatile("tcgen05.fence::after_thread_sync;");
             int qb, qe;
@@ -244,7 +251,7 @@ bsr_tc_kernel(const __grid_constant__ CUtensorMap tmY, const __grid_constant__ C
             const bool has_acc = qe > qb;
             const int jl = quad * 32 + lane;                      // state within the tile
             const int64_t j = t * kTileJ + jl;
-            const float* ycs = reinterpret_cast<const float*>(epi + b * kEpiBuf);
+            const float* ycs = reinterpret_cast<const float*>(epi);
             const float* yps = ycs + kBlk * kTileJ;
             const int64_t row0 = R * kBlk;
             bool nonfinite = false;
@@ -280,17 +287,17 @@ bsr_tc_kernel(const __grid_constant__ CUtensorMap tmY, const __grid_constant__ C
                     __nv_bfloat162 h2 = __floats2bfloat162_rn(out[2 * tt], out[2 * tt + 1]);
                     pw[tt] = *reinterpret_cast<unsigned*>(&h2);
                 }
-                uint4* dst = reinterpret_cast<uint4*>(Ysh_out + j * N + row0 + cchunk * 16);
+                uint4* dst = reinterpret_cast<uint4*>(Ysh_out + (R * n + j) * kBlk + cchunk * 16);
                 dst[0] = pk[0];
                 dst[1] = pk[1];
             }
             if (nonfinite) raise_status(status, DEV_NONFINITE);
-            // release the accumulator and the epilogue tiles of buffer b
+            // release accumulator b and the epilogue tiles
             asm volatile("tcgen05.fence::before_thread_sync;");
             __syncwarp();
             if (lane == 0) {
                 mbar_arrive(&tempty[b]);
-                mbar_arrive(&eempty[b]);
+                mbar_arrive(&eempty);
             }
         }
     }
@@ -311,7 +318,8 @@ __global__ void blocks_to_bf16_kernel(const double* __restrict__ src, __nv_bfloa
     if (i < count) dst[i] = __float2bfloat16_rn((float)src[i]);
 }
 
-// State-major BF16 copy of a row-major FP64 block: dst[j * N + r] = bf16(src[r * lds + j]).
+// Block-major BF16 copy of a row-major FP64 block:
+//     dst[((r / 64) * n + j) * 64 + r % 64] = bf16(src[r * lds + j]).
 __global__ void transpose_to_bf16_kernel(const double* __restrict__ src, int64_t lds, __nv_bfloat16* dst, int64_t N,
                                          int64_t n) {
     __shared__ float t[32][33];
@@ -323,7 +331,7 @@ __global__ void transpose_to_bf16_kernel(const double* __restrict__ src, int64_t
     __syncthreads();
     for (int k = threadIdx.y; k < 32; k += blockDim.y) {
         const int64_t j = j0 + k, r = r0 + threadIdx.x;
-        if (j < n && r < N) dst[j * N + r] = __float2bfloat16_rn(t[threadIdx.x][k]);
+        if (j < n && r < N) dst[((r / kBlk) * n + j) * kBlk + (r % kBlk)] = __float2bfloat16_rn(t[threadIdx.x][k]);
     }
 }
 
@@ -414,10 +422,11 @@ int bsr_step_tc(const BsrDev& h, int64_t n, const void* ysh_in, const float* Yc,
     if (n <= 0 || h.nbr <= 0) return CHFSI_OK;
     if (h.bdim != kBlk || h.val_t != Buf::BF16) return CHFSI_ERR_UNSUPPORTED;
     const int64_t N = h.nbr * kBlk;
-    if (h.nblocks * kBlk > INT32_MAX || N > INT32_MAX || n > INT32_MAX) return CHFSI_ERR_UNSUPPORTED;
+    if (h.nblocks * kBlk > INT32_MAX || N > INT32_MAX || n > INT32_MAX || h.nbr * n > INT32_MAX)
+        return CHFSI_ERR_UNSUPPORTED;
     CUtensorMap tmY, tmH, tmYc, tmYp;
     int rc;
-    if ((rc = make_map(&tmY, ysh_in, N, n, kTileJ))) return rc;
+    if ((rc = make_map(&tmY, ysh_in, kBlk, h.nbr * n, kTileJ))) return rc;
     if ((rc = make_map(&tmH, h.val, kBlk, h.nblocks * kBlk, kBlk))) return rc;
     if ((rc = make_map_f32(&tmYc, Yc, ldc, N))) return rc;
     if (Yp) {

@@ -47,7 +47,7 @@ int bsr_step(const BsrDev& h, StepMath math, int64_t n, const StepIO& io, double
              double beta, unsigned* status, cudaStream_t s);
 
 // Tensor-core (tcgen05) BF16-operand BSR step; h.val holds BF16 blocks, the BF16
-// iterate copies ysh_in / ysh_out are state-major (n x N).
+// iterate copies ysh_in / ysh_out are block-major [N/64][n][64].
 int bsr_step_tc(const BsrDev& h, int64_t n, const void* ysh_in, const float* Yc, int64_t ldc, const float* Yp,
                 int64_t ldp, float* Yo, int64_t ldo, void* ysh_out, double alpha, double c, double beta,
                 unsigned* status, cudaStream_t s);
