@@ -4,9 +4,12 @@
 // order), and products with an n x n matrix (X_F = Y R^-1, Psi = X_F Q).
 //
 // Same tiling as the FP64 kernels (64 x 64 output tile, 256 threads, 4 x 4 outputs
-// per thread with stride-16 ownership, 16-deep shared-memory chunks), with hi/lo
-// pairs in shared memory.  Each multiply-add is about 12 FP32 operations, and with
-// 8 pair loads per 16 multiply-adds the kernel is bound by the FP32 pipe.
+// per thread with stride-16 ownership, 16-deep shared-memory chunks).  The products
+// run on the packed FP32 instructions (two lanes per instruction): a thread's output
+// columns tx + 32 P and tx + 32 P + 16 share one register pair, so each two-float
+// multiply-add of two outputs is 12 packed instructions.  Shared memory holds the
+// operands already in packed form -- B as {hi, hi', lo, lo'} for a column pair, A as
+// {hi, hi, -hi, -hi} and {lo, lo} -- so that no register shuffling is needed.
 #include "common.cuh"
 #include "kernels.cuh"
 #include "twofloat.cuh"
@@ -34,8 +37,11 @@ struct Gemm2Args {
 
 template <Out kOut>
 __global__ void __launch_bounds__(256) gemm_f32x2_kernel(Gemm2Args g) {
-    __shared__ float2 As[BK][TB + 1];
-    __shared__ float2 Bs[BK][TB];
+    // As4[k][i] = {hi, hi, -hi, -hi} and Asl[k][i] = {lo, lo} of A(i, k);
+    // Bs4[k][P][t] = {hi, hi', lo, lo'} of B(k, 32 P + t) and B(k, 32 P + t + 16).
+    __shared__ float4 As4[BK][TB];
+    __shared__ float2 Asl[BK][TB];
+    __shared__ float4 Bs4[BK][2][16];
     const int bi = blockIdx.y, bj = blockIdx.x, z = blockIdx.z;
     if (g.upper_tiles && bi > bj) return;
     const int64_t i0 = (int64_t)bi * TB, j0 = (int64_t)bj * TB;
@@ -47,11 +53,12 @@ __global__ void __launch_bounds__(256) gemm_f32x2_kernel(Gemm2Args g) {
     int64_t k_end = k_begin + kc < g.K ? k_begin + kc : g.K;
     if (g.b_upper && k_end > j0 + TB) k_end = j0 + TB;
 
-    float sh[4][4], sl[4][4];
+    // acc[a][P]: rows ty + 16 a, columns (tx + 32 P, tx + 32 P + 16) in the two lanes
+    F2 sh[4][2], sl[4][2];
 #pragma unroll
     for (int a = 0; a < 4; a++)
 #pragma unroll
-        for (int b = 0; b < 4; b++) sh[a][b] = sl[a][b] = 0.f;
+        for (int q = 0; q < 2; q++) sh[a][q] = sl[a][q] = 0ull;
 
     const float2 zero = make_float2(0.f, 0.f);
     for (int64_t k0 = k_begin; k0 < k_end; k0 += BK) {
@@ -67,32 +74,39 @@ __global__ void __launch_bounds__(256) gemm_f32x2_kernel(Gemm2Args g) {
                 const int64_t k = k0 + kk, i = i0 + ii;
                 if (k < k_end && i < g.M) va = g.A[i * g.lda + k];
             }
-            As[kk][ii] = va;
+            As4[kk][ii] = make_float4(va.x, va.x, -va.x, -va.x);
+            Asl[kk][ii] = make_float2(va.y, va.y);
             const int kb = e / TB, jb = e % TB;
             const int64_t k = k0 + kb, j = j0 + jb;
-            Bs[kb][jb] = (k < k_end && j < g.Nc) ? g.B[k * g.ldb + j] : zero;
+            const float2 vb = (k < k_end && j < g.Nc) ? g.B[k * g.ldb + j] : zero;
+            float* bp = reinterpret_cast<float*>(&Bs4[kb][jb >> 5][jb & 15]);
+            const int h = (jb >> 4) & 1;
+            bp[h] = vb.x;
+            bp[2 + h] = vb.y;
         }
         __syncthreads();
 #pragma unroll
         for (int kk = 0; kk < BK; kk++) {
-            float2 av[4], bv[4];
+            F2 yh[2], yl[2];
 #pragma unroll
-            for (int a = 0; a < 4; a++) av[a] = As[kk][ty + 16 * a];
+            for (int q = 0; q < 2; q++) {
+                const float4 b4 = Bs4[kk][q][tx];
+                yh[q] = pk2(b4.x, b4.y);
+                yl[q] = pk2(b4.z, b4.w);
+            }
 #pragma unroll
-            for (int b = 0; b < 4; b++) bv[b] = Bs[kk][tx + 16 * b];
+            for (int a = 0; a < 4; a++) {
+                const float4 a4 = As4[kk][ty + 16 * a];
+                const float2 a2 = Asl[kk][ty + 16 * a];
+                const F2 hh2 = pk2(a4.x, a4.y), nhh2 = pk2(a4.z, a4.w), hl2 = pk2(a2.x, a2.y);
 #pragma unroll
-            for (int a = 0; a < 4; a++)
-#pragma unroll
-                for (int b = 0; b < 4; b++) df_madd(av[a].x, av[a].y, bv[b].x, bv[b].y, sh[a][b], sl[a][b]);
+                for (int q = 0; q < 2; q++) df_madd2(hh2, nhh2, hl2, yh[q], yl[q], sh[a][q], sl[a][q]);
+            }
             if ((kk & (kRenorm - 1)) == kRenorm - 1) {
 #pragma unroll
                 for (int a = 0; a < 4; a++)
 #pragma unroll
-                    for (int b = 0; b < 4; b++) {
-                        const DF t = fast_norm(sh[a][b], sl[a][b]);
-                        sh[a][b] = t.hi;
-                        sl[a][b] = t.lo;
-                    }
+                    for (int q = 0; q < 2; q++) fast_norm2(sh[a][q], sl[a][q]);
             }
         }
         __syncthreads();
@@ -103,16 +117,22 @@ __global__ void __launch_bounds__(256) gemm_f32x2_kernel(Gemm2Args g) {
         const int64_t i = i0 + ty + 16 * a;
         if (i >= g.M) continue;
 #pragma unroll
-        for (int b = 0; b < 4; b++) {
-            const int64_t j = j0 + tx + 16 * b;
-            if (j >= g.Nc) continue;
-            const DF v = fast_norm(sh[a][b], sl[a][b]);
-            if constexpr (kOut == Out::Part) {
-                g.part[((int64_t)z * g.M + i) * g.Nc + j] = (double)v.hi + (double)v.lo;
-            } else if constexpr (kOut == Out::F64) {
-                static_cast<double*>(g.C)[i * g.ldc + j] = (double)v.hi + (double)v.lo;
-            } else {
-                static_cast<float2*>(g.C)[i * g.ldc + j] = make_float2(v.hi, v.lo);
+        for (int q = 0; q < 2; q++) {
+            float hs[2], ls[2];
+            upk2(sh[a][q], hs[0], hs[1]);
+            upk2(sl[a][q], ls[0], ls[1]);
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                const int64_t j = j0 + tx + 32 * q + 16 * h;
+                if (j >= g.Nc) continue;
+                const DF v = fast_norm(hs[h], ls[h]);
+                if constexpr (kOut == Out::Part) {
+                    g.part[((int64_t)z * g.M + i) * g.Nc + j] = (double)v.hi + (double)v.lo;
+                } else if constexpr (kOut == Out::F64) {
+                    static_cast<double*>(g.C)[i * g.ldc + j] = (double)v.hi + (double)v.lo;
+                } else {
+                    static_cast<float2*>(g.C)[i * g.ldc + j] = make_float2(v.hi, v.lo);
+                }
             }
         }
     }

@@ -42,7 +42,7 @@ __device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
 // Y values as float2 {hi, lo}, row-major with leading dimension ld (in float2 units).
 // Each lane owns 2 consecutive states (one float4 = 2 pairs); U chunks per pass.
 template <int U>
-__global__ void __launch_bounds__(kThreads, (U >= 4 ? 2 : 4))
+__global__ void __launch_bounds__(kThreads, (U >= 4 ? 2 : 3))
 csr_step_f32x2_kernel(int64_t N, const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
                       const float2* __restrict__ val, int64_t nnz, int64_t n, const float2* __restrict__ Yc,
                       int64_t ldc, const float2* __restrict__ Yp, int64_t ldp, float2* __restrict__ Yo, int64_t ldo,
@@ -89,12 +89,13 @@ csr_step_f32x2_kernel(int64_t N, const int64_t* __restrict__ row_ptr, const int3
         bool nonfinite = false;
 
         for (int64_t jbase = 0; jbase < n; jbase += 64 * U) {
-            float sh[U][2], sl[U][2];
+            // Packed accumulators: lane 0 of sh2[u]/sl2[u] is state j0 + 64 u, lane 1 the next.
+            F2 sh2[U], sl2[U];
             bool on[U];
 #pragma unroll
             for (int u = 0; u < U; u++) {
                 on[u] = jbase + (int64_t)(u * 32 + lane) * 2 < n;
-                sh[u][0] = sh[u][1] = sl[u][0] = sl[u][1] = 0.f;
+                sh2[u] = sl2[u] = 0ull;
             }
             const int64_t j0 = jbase + (int64_t)lane * 2;
             // Register pipeline with two alternating buffers: the gathers of entry q+1
@@ -118,21 +119,14 @@ csr_step_f32x2_kernel(int64_t N, const int64_t* __restrict__ row_ptr, const int3
                 }
             };
             auto accumulate = [&](const float4 (&y)[U], float2 h) {
+                const F2 hh2 = pk2(h.x, h.x), nhh2 = pk2(-h.x, -h.x), hl2 = pk2(h.y, h.y);
 #pragma unroll
-                for (int u = 0; u < U; u++) {
-                    df_madd(h.x, h.y, y[u].x, y[u].y, sh[u][0], sl[u][0]);
-                    df_madd(h.x, h.y, y[u].z, y[u].w, sh[u][1], sl[u][1]);
-                }
+                for (int u = 0; u < U; u++)
+                    df_madd2(hh2, nhh2, hl2, pk2(y[u].x, y[u].z), pk2(y[u].y, y[u].w), sh2[u], sl2[u]);
             };
             auto renorm = [&]() {
 #pragma unroll
-                for (int u = 0; u < U; u++)
-#pragma unroll
-                    for (int v = 0; v < 2; v++) {
-                        const DF t = fast_norm(sh[u][v], sl[u][v]);
-                        sh[u][v] = t.hi;
-                        sl[u][v] = t.lo;
-                    }
+                for (int u = 0; u < U; u++) fast_norm2(sh2[u], sl2[u]);
             };
             float4 ya[U], yb[U];
             float2 ha = make_float2(0.f, 0.f), hb = make_float2(0.f, 0.f);
@@ -153,10 +147,13 @@ csr_step_f32x2_kernel(int64_t N, const int64_t* __restrict__ row_ptr, const int3
                 const float4 yc = *reinterpret_cast<const float4*>(Yc + r * ldc + j);
                 float4 yp = make_float4(0.f, 0.f, 0.f, 0.f);
                 if (Yp) yp = *reinterpret_cast<const float4*>(Yp + r * ldp + j);
+                float sh[2], sl[2];
+                upk2(sh2[u], sh[0], sh[1]);
+                upk2(sl2[u], sl[0], sl[1]);
                 DF o[2];
 #pragma unroll
                 for (int v = 0; v < 2; v++) {
-                    const DF acc{sh[u][v], sl[u][v]};
+                    const DF acc{sh[v], sl[v]};
                     const DF ycur = v == 0 ? DF{yc.x, yc.y} : DF{yc.z, yc.w};
                     DF t = df_add(acc, df_neg(df_mul(Cs, ycur)));
                     t = df_mul(A, t);
@@ -218,7 +215,7 @@ int csr_step_f32x2(const CsrDev& h, int64_t n, const void* Yc, int64_t ldc, cons
                    int64_t ldo, double alpha, double c, double beta, unsigned* status, cudaStream_t s) {
     if (n <= 0 || h.N <= 0) return CHFSI_OK;
     if (h.val_t != Buf::F32X2 || (ldc % 2) || (ldp % 2) || (ldo % 2)) return CHFSI_ERR_UNSUPPORTED;
-    // stage 8 rows of a typical length (1.25 x the mean, so that 4 CTAs fit per SM);
+    // stage 8 rows of a typical length (1.25 x the mean, so that several CTAs fit per SM);
     // longer row blocks read their entries from global memory instead
     const int64_t mean = (h.nnz + h.N - 1) / h.N;
     int64_t cap = (kWarps * mean * 5 / 4 + 127) / 128 * 128;

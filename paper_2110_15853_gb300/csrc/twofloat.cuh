@@ -66,5 +66,66 @@ __device__ __forceinline__ DF df_from_double(double x) {
 }
 
 
+// Packed form: two independent two-float lanes in one pair of FP32 registers,
+// driven by the sm_100-family packed instructions (add/sub/mul/fma .rn.f32x2),
+// which do the work of two FP32 instructions per issue slot.  Every lane is
+// rounded exactly like the scalar intrinsics above, so the packed routines give
+// bit-identical results to their scalar counterparts.
+typedef unsigned long long F2;
+
+__device__ __forceinline__ F2 pk2(float a, float b) {
+    F2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void upk2(F2 v, float& a, float& b) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ F2 add2(F2 a, F2 b) {
+    F2 r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ F2 sub2(F2 a, F2 b) {
+    F2 r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ F2 mul2(F2 a, F2 b) {
+    F2 r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ F2 fma2(F2 a, F2 b, F2 c) {
+    F2 r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+
+// Packed df_madd: (sh, sl) += h * y in both lanes, h shared by the lanes and given
+// as hh2 = (hh, hh), nhh2 = (-hh, -hh), hl2 = (hl, hl).  The negated product
+// np = -fl(hh*yh) stands in for p (rounding is sign-symmetric), so TwoProduct,
+// TwoSum and the error update are the scalar steps with p replaced by -np.
+__device__ __forceinline__ void df_madd2(F2 hh2, F2 nhh2, F2 hl2, F2 yh2, F2 yl2, F2& sh2, F2& sl2) {
+    const F2 np = mul2(nhh2, yh2);
+    F2 e = fma2(hh2, yh2, np);
+    e = fma2(hh2, yl2, e);
+    e = fma2(hl2, yh2, e);
+    const F2 s = sub2(sh2, np);
+    const F2 z = sub2(s, sh2);
+    const F2 t2 = sub2(sh2, sub2(s, z));
+    const F2 err = sub2(t2, add2(np, z));
+    sh2 = s;
+    sl2 = add2(sl2, add2(err, e));
+}
+
+// Packed fast_norm of both lanes.
+__device__ __forceinline__ void fast_norm2(F2& s, F2& e) {
+    const F2 hi = add2(s, e);
+    e = sub2(e, sub2(hi, s));
+    s = hi;
+}
+
+
 }  // namespace
 }  // namespace chfsi
