@@ -76,9 +76,12 @@ namespace chfsi {
 
 namespace {
 
-// dH[p] += alpha * <Ybar[row p, :], Yprev[col p, :]> with both blocks as hi/lo FP32
-// pairs: per-lane two-float dot products, a fixed shuffle tree of two-float adds,
-// and one FP64 multiply-add into dH[p] per entry (one warp per row, no atomics).
+constexpr int kRenorm = 8;  // renormalise the two-float accumulators every kRenorm terms
+
+// dH[p] += alpha * <Ybar[row p, :], Yprev[col p, :]> with both blocks two-float in the
+// pair-split layout: per-lane two-float dot products on the packed FP32x2 instructions
+// (even and odd states in the two lanes), a fixed shuffle tree of two-float adds, and
+// one FP64 multiply-add into dH[p] per entry (one warp per row, no atomics).
 __global__ void __launch_bounds__(256)
 sddmm_f32x2_kernel(int64_t N, const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col, int64_t nnz,
                    int64_t n, const float2* __restrict__ Yb, int64_t ldb, const float2* __restrict__ Yp, int64_t ldp,
@@ -92,17 +95,24 @@ sddmm_f32x2_kernel(int64_t N, const int64_t* __restrict__ row_ptr, const int32_t
     const float2* yb = Yb + r * ldb;
     for (int64_t p = b; p < e; p++) {
         const int32_t q = col[p];
-        float sh = 0.f, sl = 0.f;
+        F2 sh2 = 0ull, sl2 = 0ull;
         if (q >= 0 && (int64_t)q < N) {
             const float2* yp = Yp + (int64_t)q * ldp;
+            const F2 minus1 = pk2(-1.f, -1.f);
+            int t = 0;
             for (int64_t j = (int64_t)lane * 2; j < n; j += 64) {
                 const float4 x = __ldg(reinterpret_cast<const float4*>(yb + j));
                 const float4 y = __ldg(reinterpret_cast<const float4*>(yp + j));
-                df_madd(x.x, x.y, y.x, y.y, sh, sl);
-                df_madd(x.z, x.w, y.z, y.w, sh, sl);
+                const F2 xh2 = pk2(x.x, x.y);
+                df_madd2(xh2, mul2(xh2, minus1), pk2(x.z, x.w), pk2(y.x, y.y), pk2(y.z, y.w), sh2, sl2);
+                if ((++t & (kRenorm - 1)) == 0) fast_norm2(sh2, sl2);
             }
         }
-        DF acc = fast_norm(sh, sl);
+        fast_norm2(sh2, sl2);
+        float h0, h1, l0, l1;
+        upk2(sh2, h0, h1);
+        upk2(sl2, l0, l1);
+        DF acc = df_add(DF{h0, l0}, DF{h1, l1});
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             DF other;

@@ -302,18 +302,18 @@ int chfsi_filter(const chfsi_matrix* H, const double* X, int64_t ldx, double* Y,
     bool widened = false;   // low-precision Y_L, Y_{L-1} already widened into their FP64 slots
     if (L > 0 && low == CHFSI_F32X2) {
         if (!has_csr(H)) return CHFSI_ERR_UNSUPPORTED;
-        if ((rc = to_f32x2(H->csr.val, 1, fl.hlow, 1, H->csr.nnz, 1, s))) return rc;
+        if ((rc = to_f32x2(H->csr.val, 1, fl.hlow, 1, H->csr.nnz, 1, false, s))) return rc;
         const CsrDev h2{H->csr.n_rows, H->csr.nnz, H->csr.row_ptr, H->csr.col, fl.hlow, Buf::F32X2};
-        if ((rc = to_f32x2(X, ldx, fl.D[0], ldw, N, n, s))) return rc;
+        if ((rc = to_f32x2(X, ldx, fl.D[0], ldw, N, n, true, s))) return rc;
         for (int k = 1; k <= L; k++) {
             const void* prev = k >= 2 ? fl.D[(k - 2) % 3] : nullptr;
             rc = csr_step_f32x2(h2, n, fl.D[(k - 1) % 3], ldw, prev, ldw, fl.D[k % 3], ldw, al[k], c,
                                 k >= 2 ? be[k] : 0.0, st, s);
             if (rc) return rc;
         }
-        if (L == m) return from_f32x2(fl.D[m % 3], ldw, Y, ldy, N, n, s);
-        if ((rc = from_f32x2(fl.D[L % 3], ldw, f64_buf(L), f64_ld(L), N, n, s))) return rc;
-        if (L >= 2 && (rc = from_f32x2(fl.D[(L - 1) % 3], ldw, f64_buf(L - 1), f64_ld(L - 1), N, n, s))) return rc;
+        if (L == m) return from_f32x2(fl.D[m % 3], ldw, Y, ldy, N, n, true, s);
+        if ((rc = from_f32x2(fl.D[L % 3], ldw, f64_buf(L), f64_ld(L), N, n, true, s))) return rc;
+        if (L >= 2 && (rc = from_f32x2(fl.D[(L - 1) % 3], ldw, f64_buf(L - 1), f64_ld(L - 1), N, n, true, s))) return rc;
         widened = true;
     } else if (L > 0 && has_bsr(H) && low == CHFSI_BF16_F32ACC) {
         // tensor-core path: BF16 blocks, state-major BF16 iterate copies
@@ -567,9 +567,9 @@ int chfsi_filter_backward_ex(const chfsi_matrix* H, const double* X, int64_t ldx
     }
 
     // two-float: hi/lo copies of X, dY and H; Ybar_0 widened into dX at the end
-    if ((rc = to_f32x2(H->csr.val, 1, bl.H2, 1, H->csr.nnz, 1, s))) return rc;
-    if ((rc = to_f32x2(X, ldx, bl.X2, ldw, N, n, s))) return rc;
-    if ((rc = to_f32x2(dY, lddy, bl.G2, ldw, N, n, s))) return rc;
+    if ((rc = to_f32x2(H->csr.val, 1, bl.H2, 1, H->csr.nnz, 1, false, s))) return rc;
+    if ((rc = to_f32x2(X, ldx, bl.X2, ldw, N, n, true, s))) return rc;
+    if ((rc = to_f32x2(dY, lddy, bl.G2, ldw, N, n, true, s))) return rc;
     const CsrDev h2{H->csr.n_rows, H->csr.nnz, H->csr.row_ptr, H->csr.col, bl.H2, Buf::F32X2};
     BackStep step = [&](const void* cur, int64_t ldc, const void* prev, int64_t ldp, void* out, int64_t ldo,
                         double alpha, double beta) {
@@ -581,7 +581,7 @@ int chfsi_filter_backward_ex(const chfsi_matrix* H, const double* X, int64_t ldx
     if ((rc = backward_sweep(m, bl, ldw, al, be, bl.X2, ldw, bl.G2, ldw, bl.D0, ldw, dH_val != nullptr, step,
                              sddmm)))
         return rc;
-    return from_f32x2(bl.D0, ldw, dX, lddx, N, n, s);
+    return from_f32x2(bl.D0, ldw, dX, lddx, N, n, true, s);
 }
 
 int chfsi_filter_backward(const chfsi_matrix* H, const double* X, int64_t ldx, const double* dY, int64_t lddy,
@@ -672,14 +672,14 @@ int rr_run_f32x2(const chfsi_matrix* H, const double* Y, int64_t ldy, int64_t N,
                  int64_t ldpsi, double* ritz, int passes, const RRLayout& rl, unsigned* st, cudaStream_t s) {
     const int64_t ldw = pad8(n);
     int rc;
-    if ((rc = to_f32x2(Y, ldy, rl.Y2, ldw, N, n, s))) return rc;
+    if ((rc = to_f32x2(Y, ldy, rl.Y2, ldw, N, n, true, s))) return rc;
     const float2* cur = rl.Y2;
     int which = 0;
     for (int pass = 0; pass < passes; pass++) {
         if ((rc = gemm_tn_f32x2(cur, ldw, cur, ldw, N, n, rl.S, n, true, rl.part, rl.splits, s))) return rc;
         if ((rc = cholesky_upper(rl.S, n, n, st, s))) return rc;
         if ((rc = tri_inverse_upper(rl.S, n, rl.Rinv, n, n, s))) return rc;
-        if ((rc = to_f32x2(rl.Rinv, n, rl.R2, n, n, n, s))) return rc;
+        if ((rc = to_f32x2(rl.Rinv, n, rl.R2, n, n, n, false, s))) return rc;
         float2* out = rl.B2[which];
         if ((rc = gemm_nn_f32x2(cur, ldw, rl.R2, n, out, ldw, false, N, n, true, s))) return rc;
         cur = out;
@@ -687,13 +687,13 @@ int rr_run_f32x2(const chfsi_matrix* H, const double* Y, int64_t ldy, int64_t N,
     }
     const float2* XF = cur;
     float2* HXF = rl.B2[which];
-    if ((rc = to_f32x2(H->csr.val, 1, rl.H2, 1, H->csr.nnz, 1, s))) return rc;
+    if ((rc = to_f32x2(H->csr.val, 1, rl.H2, 1, H->csr.nnz, 1, false, s))) return rc;
     const CsrDev h2{H->csr.n_rows, H->csr.nnz, H->csr.row_ptr, H->csr.col, rl.H2, Buf::F32X2};
     if ((rc = csr_step_f32x2(h2, n, XF, ldw, nullptr, 0, HXF, ldw, 1.0, 0.0, 0.0, st, s))) return rc;
     if ((rc = gemm_tn_f32x2(XF, ldw, HXF, ldw, N, n, rl.S, n, false, rl.part, rl.splits, s))) return rc;
     if ((rc = symmetrize(rl.S, n, n, s))) return rc;
     if ((rc = rr_eig(rl, n, ritz, s))) return rc;
-    if ((rc = to_f32x2(rl.Q, n, rl.Q2, n, n, n, s))) return rc;
+    if ((rc = to_f32x2(rl.Q, n, rl.Q2, n, n, n, false, s))) return rc;
     if ((rc = gemm_nn_f32x2(XF, ldw, rl.Q2, n, Psi, ldpsi, true, N, n, false, s))) return rc;
     return rr_finish(rl, st, s);
 }

@@ -13,7 +13,9 @@
 // Layout and staging follow the FP64 CSR step: one CTA per 8 consecutive rows,
 // the CTA's CSR slice (hi/lo value pairs and column indices) staged once in
 // shared memory by cp.async and reused for every column chunk; a lane owns two
-// consecutive states (one 16-byte load of two hi/lo pairs per gathered row).
+// consecutive states, and the iterate blocks are in the pair-split layout (the 16
+// bytes of states 2t, 2t+1 hold {hi, hi', lo, lo'}), so one 16-byte load per
+// gathered row gives both register pairs of the packed FP32x2 multiply-add.
 // Column indices are range-checked while staging.  Intrinsics with explicit
 // rounding (__fmul_rn, __fadd_rn, __fsub_rn) keep the compiler from contracting
 // the error-free transformations into FMAs.
@@ -39,8 +41,8 @@ __device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem));
 }
 
-// Y values as float2 {hi, lo}, row-major with leading dimension ld (in float2 units).
-// Each lane owns 2 consecutive states (one float4 = 2 pairs); U chunks per pass.
+// Y blocks row-major in the pair-split layout with leading dimension ld (in elements,
+// even).  Each lane owns 2 consecutive states (one float4); U chunks per pass.
 template <int U>
 __global__ void __launch_bounds__(kThreads, (U >= 4 ? 2 : 3))
 csr_step_f32x2_kernel(int64_t N, const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
@@ -122,7 +124,7 @@ csr_step_f32x2_kernel(int64_t N, const int64_t* __restrict__ row_ptr, const int3
                 const F2 hh2 = pk2(h.x, h.x), nhh2 = pk2(-h.x, -h.x), hl2 = pk2(h.y, h.y);
 #pragma unroll
                 for (int u = 0; u < U; u++)
-                    df_madd2(hh2, nhh2, hl2, pk2(y[u].x, y[u].z), pk2(y[u].y, y[u].w), sh2[u], sl2[u]);
+                    df_madd2(hh2, nhh2, hl2, pk2(y[u].x, y[u].y), pk2(y[u].z, y[u].w), sh2[u], sl2[u]);
             };
             auto renorm = [&]() {
 #pragma unroll
@@ -154,17 +156,17 @@ csr_step_f32x2_kernel(int64_t N, const int64_t* __restrict__ row_ptr, const int3
 #pragma unroll
                 for (int v = 0; v < 2; v++) {
                     const DF acc{sh[v], sl[v]};
-                    const DF ycur = v == 0 ? DF{yc.x, yc.y} : DF{yc.z, yc.w};
+                    const DF ycur = v == 0 ? DF{yc.x, yc.z} : DF{yc.y, yc.w};
                     DF t = df_add(acc, df_neg(df_mul(Cs, ycur)));
                     t = df_mul(A, t);
                     if (Yp) {
-                        const DF yprev = v == 0 ? DF{yp.x, yp.y} : DF{yp.z, yp.w};
+                        const DF yprev = v == 0 ? DF{yp.x, yp.z} : DF{yp.y, yp.w};
                         t = df_add(t, df_neg(df_mul(B, yprev)));
                     }
                     nonfinite |= !isfinite(t.hi);
                     o[v] = t;
                 }
-                *reinterpret_cast<float4*>(Yo + r * ldo + j) = make_float4(o[0].hi, o[0].lo, o[1].hi, o[1].lo);
+                *reinterpret_cast<float4*>(Yo + r * ldo + j) = make_float4(o[0].hi, o[1].hi, o[0].lo, o[1].lo);
             }
         }
         if (__any_sync(0xffffffffu, nonfinite) && lane == 0) raise_status(status, DEV_NONFINITE);
@@ -172,41 +174,63 @@ csr_step_f32x2_kernel(int64_t N, const int64_t* __restrict__ row_ptr, const int3
     if (__syncthreads_or(bad) && threadIdx.x == 0) raise_status(status, DEV_PATTERN);
 }
 
+// Element (i, j) of a two-float block: {hi, lo} at [i*ld + j] (pair layout), or, in
+// the pair-split layout, hi at float 2 (i*ld + (j & ~1)) + (j & 1) and lo two floats on.
+__device__ __forceinline__ int64_t split_hi_index(int64_t i, int64_t ld, int64_t j) {
+    return 2 * (i * ld + (j & ~(int64_t)1)) + (j & 1);
+}
+
 __global__ void to_f32x2_kernel(const double* __restrict__ src, int64_t lds, float2* dst, int64_t ldd, int64_t rows,
-                                int64_t n) {
+                                int64_t n, bool split) {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= rows * ldd) return;
     const int64_t i = idx / ldd, j = idx % ldd;
     DF v{0.f, 0.f};
     if (j < n) v = df_from_double(src[i * lds + j]);
-    dst[idx] = make_float2(v.hi, v.lo);
+    if (split) {
+        float* f = reinterpret_cast<float*>(dst) + split_hi_index(i, ldd, j);
+        f[0] = v.hi;
+        f[2] = v.lo;
+    } else {
+        dst[idx] = make_float2(v.hi, v.lo);
+    }
 }
 
 __global__ void from_f32x2_kernel(const float2* __restrict__ src, int64_t lds, double* dst, int64_t ldd, int64_t rows,
-                                  int64_t n) {
+                                  int64_t n, bool split) {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= rows * n) return;
     const int64_t i = idx / n, j = idx % n;
-    const float2 v = src[i * lds + j];
+    float2 v;
+    if (split) {
+        const float* f = reinterpret_cast<const float*>(src) + split_hi_index(i, lds, j);
+        v = make_float2(f[0], f[2]);
+    } else {
+        v = src[i * lds + j];
+    }
     dst[i * ldd + j] = (double)v.x + (double)v.y;
 }
 
 }  // namespace
 
-int to_f32x2(const double* src, int64_t lds, void* dst, int64_t ldd, int64_t rows, int64_t n, cudaStream_t s) {
+int to_f32x2(const double* src, int64_t lds, void* dst, int64_t ldd, int64_t rows, int64_t n, bool split,
+             cudaStream_t s) {
     const int64_t total = rows * ldd;
     if (total <= 0) return CHFSI_OK;
+    if (split && (ldd % 2)) return CHFSI_ERR_UNSUPPORTED;
     to_f32x2_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(src, lds, static_cast<float2*>(dst), ldd, rows,
-                                                                    n);
+                                                                    n, split);
     CHFSI_LAUNCH_CHECK();
     return CHFSI_OK;
 }
 
-int from_f32x2(const void* src, int64_t lds, double* dst, int64_t ldd, int64_t rows, int64_t n, cudaStream_t s) {
+int from_f32x2(const void* src, int64_t lds, double* dst, int64_t ldd, int64_t rows, int64_t n, bool split,
+               cudaStream_t s) {
     const int64_t total = rows * n;
     if (total <= 0) return CHFSI_OK;
+    if (split && (lds % 2)) return CHFSI_ERR_UNSUPPORTED;
     from_f32x2_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(static_cast<const float2*>(src), lds, dst, ldd,
-                                                                      rows, n);
+                                                                      rows, n, split);
     CHFSI_LAUNCH_CHECK();
     return CHFSI_OK;
 }

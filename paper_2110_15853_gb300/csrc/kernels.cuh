@@ -53,14 +53,22 @@ int bsr_step_tc(const BsrDev& h, int64_t n, const void* ysh_in, const float* Yc,
                 unsigned* status, cudaStream_t s);
 int bsr_values_to_bf16(const double* src, void* dst, int64_t count, cudaStream_t s);
 
-// Two-float (hi + lo FP32 pairs, float2) CSR step and conversions; h.val holds
-// float2 values, ld in float2 elements (even).
+// Two-float blocks (a value is hi + lo, two FP32 numbers, 8 bytes per element).
+// Iterate blocks (N x n, leading dimension ld in elements, even) use the pair-split
+// layout: the 16 bytes of columns 2t and 2t + 1 of a row hold {hi_2t, hi_2t+1, lo_2t,
+// lo_2t+1}, so one 16-byte load gives both lanes of a packed FP32x2 operand.  CSR
+// values and small n x n matrices use the pair layout ({hi, lo} per element, float2).
+// csr_step_f32x2: h.val in the pair layout, Y blocks pair-split.
 int csr_step_f32x2(const CsrDev& h, int64_t n, const void* Yc, int64_t ldc, const void* Yp, int64_t ldp, void* Yo,
                    int64_t ldo, double alpha, double c, double beta, unsigned* status, cudaStream_t s);
-int to_f32x2(const double* src, int64_t lds, void* dst, int64_t ldd, int64_t rows, int64_t n, cudaStream_t s);
-int from_f32x2(const void* src, int64_t lds, double* dst, int64_t ldd, int64_t rows, int64_t n, cudaStream_t s);
-// Two-float dense products (float2 operands): S = A^T B (FP64 result, split-K
-// partials in FP64) and C = A B (float2 or FP64 result).
+// FP64 <-> two-float; split selects the pair-split layout for the two-float side.
+int to_f32x2(const double* src, int64_t lds, void* dst, int64_t ldd, int64_t rows, int64_t n, bool split,
+             cudaStream_t s);
+int from_f32x2(const void* src, int64_t lds, double* dst, int64_t ldd, int64_t rows, int64_t n, bool split,
+               cudaStream_t s);
+// Two-float dense products: S = A^T B (FP64 result, split-K partials in FP64), A and B
+// pair-split N x n blocks; C = A B with A a pair-split N x n block, B an n x n matrix in
+// the pair layout, C pair-split two-float or FP64.
 int gemm_tn_f32x2(const void* A, int64_t lda, const void* B, int64_t ldb, int64_t K, int64_t n, double* S,
                   int64_t lds, bool symmetric, double* part, int splits, cudaStream_t s);
 int gemm_nn_f32x2(const void* A, int64_t lda, const void* B, int64_t ldb, void* C, int64_t ldc, bool c_f64,
@@ -103,7 +111,7 @@ size_t lanczos_part_count(int64_t N, int steps);
 int sddmm_accumulate(const CsrDev& h, int64_t n, const double* Ybar, int64_t ldb,
                      const double* Yprev, int64_t ldp, double alpha, double* dH, cudaStream_t s);
 
-// Two-float (float2 hi/lo) variant of sddmm_accumulate; ld in float2 elements (even), n even
+// Two-float variant of sddmm_accumulate on pair-split blocks; ld in elements (even), n even
 // or padded with zero columns.
 int sddmm_accumulate_f32x2(const CsrDev& h, int64_t n, const void* Ybar, int64_t ldb, const void* Yprev,
                            int64_t ldp, double alpha, double* dH, cudaStream_t s);

@@ -230,7 +230,7 @@ def test_bsr_tensor_core_single_step_exact_products(P, oracle_mod):
 
 
 @pytest.mark.parametrize("g,w,n,m,L", [(8, 2, 6, 5, 5), (8, 3, 37, 10, 10), (12, 3, 70, 13, 9), (5, 1, 3, 7, 1),
-                                       (10, 2, 129, 6, 6), (6, 4, 64, 20, 20)])
+                                       (10, 2, 129, 6, 6), (6, 4, 64, 20, 20), (8, 3, 301, 6, 6)])
 def test_filter_f32x2_is_fp64_accurate(P, oracle_mod, g, w, n, m, L):
     """Two-float steps (hi + lo FP32 pairs, error-free transformations on the
     FP32 pipe) meet the FP64 filter tolerance against the FP64 oracle."""
