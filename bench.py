@@ -36,6 +36,7 @@ if ROOT not in sys.path:
 import chfsi_workloads as W  # noqa: E402
 
 METRIC = "ChFSI filter GFLOP/s & % of roofline, FP64 vs mixed precision at stated error"
+SLAB_STATES = 512   # column-slab width of a CSR filter (the library's kSlab)
 # FP64 DFMA pipe of the whole GPU, measured with a register-resident FMA loop
 # (152 SMs x 8 independent chains x 2048 iterations, CUDA events): 1.194-1.201
 # TFLOP/s.  The nominal figure is 1.25 TFLOP/s.
@@ -163,14 +164,14 @@ def _kernel_source_sha():
 
 
 def committed_traffic(workload):
-    """dram bytes per launch of the FP64 CSR step from profiles/, if the kernel
-    source is unchanged since the capture; else None."""
+    """dram bytes per filter step (all column slabs) of the FP64 CSR step from
+    profiles/, if the kernel source is unchanged since the capture; else None."""
     path = os.path.join(ROOT, "profiles", f"csr_step_f64_{workload}.md")
     if not os.path.exists(path):
         return None
     text = open(path).read()
     m1 = re.search(r"source_sha256_16:\s*([0-9a-f]+)", text)
-    m2 = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    m2 = re.search(r"dram_bytes_per_step:\s*([0-9.eE+]+)", text)
     if not m1 or not m2 or m1.group(1) != _kernel_source_sha():
         return None
     return float(m2.group(1))
@@ -367,16 +368,19 @@ def run_ours(args):
     rr_ms = float(np.median([e[2].elapsed_time(e[3]) for e in evs]))
     value = replica_throughput(step_flops, world, ms_step)
 
-    # roofline of the dominant kernel: the fused FP64 CSR step (m launches per filter)
-    launch_ms = fil_ms / m
-    per_launch_flops = flops_f / m
-    achieved = per_launch_flops / (launch_ms * 1e-3) / 1e9
+    # roofline of the dominant kernel: the fused FP64 CSR step.  The unit is one filter
+    # step over all n states: the library runs a CSR filter in column slabs of 512 states
+    # (all m steps per slab), so a step is one launch per slab and H is read once per slab.
+    slabs = -(-n // SLAB_STATES)
+    step_ms = fil_ms / m
+    achieved = (flops_f / m) / (step_ms * 1e-3) / 1e9
     traffic = committed_traffic(wl.name)
     roofline = {"bound": "alu", "pipe": "fp64 dfma", "achieved": achieved, "peak": FP64_PEAK_GFLOPS,
                 "unit": "GFLOP/s", "frac": achieved / FP64_PEAK_GFLOPS, "traffic": traffic,
                 "kernel": "csr_step_kernel<double> (fused SpMM + recurrence)",
+                "unit_of_work": f"one filter step over all {n} states ({slabs} column-slab launches)",
                 "peak_source": "measured FP64 FMA loop on this GB300 (not in MEASURED_PEAKS.json)",
-                "hbm_bytes_algorithmic": 24.0 * N * n + 12.0 * nnz + 8.0 * (N + 1)}
+                "hbm_bytes_algorithmic": 24.0 * N * n + slabs * (12.0 * nnz + 8.0 * (N + 1))}
 
     # End to end through the public API with host buffers: every step copies its X (and
     # the Lanczos start vector) from pinned host memory and reads its Psi and Ritz values

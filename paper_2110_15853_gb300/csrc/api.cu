@@ -32,6 +32,16 @@ inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 
 
 inline int64_t pad8(int64_t n) { return (n + 7) / 8 * 8; }
 
+// A CSR filter over more than kSlab states runs slab by slab (all m steps on kSlab
+// states, then the next kSlab): the columns are independent, and a 512-state slab of
+// the iterate gathered by a window of neighbouring rows stays resident in L2 where the
+// full width would not.  BSR and hybrid operators keep the full width (the tensor-core
+// step's BF16 copy is block-major over all states).
+constexpr int64_t kSlab = 512;
+inline int64_t filter_slab(const chfsi_matrix* H, int64_t n) {
+    return (H->kind == CHFSI_CSR && n > kSlab) ? kSlab : n;
+}
+
 int check_csr(const chfsi_csr& c) {
     if (c.n_rows <= 0 || c.nnz < 0 || c.nnz > INT64_C(0x7fffffffffff)) return CHFSI_ERR_ARG;
     if (c.n_rows > INT32_MAX) return CHFSI_ERR_ARG;
@@ -253,45 +263,43 @@ int chfsi_filter_workspace_size(const chfsi_matrix* H, int64_t n_cols, int32_t m
     rc = schedule_prefix(sched, m, &L, &low);
     if (rc) return rc;
     SizeOnly sz;
-    filter_layout(sz, N, n_cols, m, L, low, low_values(H), nullptr);
+    filter_layout(sz, N, filter_slab(H, n_cols), m, L, low, low_values(H), nullptr);
     *bytes = sz.used;
     return CHFSI_OK;
 }
 
-int chfsi_filter(const chfsi_matrix* H, const double* X, int64_t ldx, double* Y, int64_t ldy, int64_t n_cols,
-                 int32_t m, double a, double b, double a0, const chfsi_schedule* sched, void* ws, size_t ws_bytes,
-                 void* stream) {
-    int64_t N = 0;
-    int rc = rows_of(H, &N);
-    if (rc) return rc;
-    if (n_cols < 0 || m < 1) return CHFSI_ERR_ARG;
-    if ((rc = check_bounds(a, b, a0))) return rc;
-    if (n_cols == 0) return CHFSI_OK;
-    if ((rc = check_block(X, ldx, n_cols)) || (rc = check_block(Y, ldy, n_cols))) return rc;
-    if (X == Y) return CHFSI_ERR_ARG;
-    int L = 0, low = 0;
-    if ((rc = schedule_prefix(sched, m, &L, &low))) return rc;
-    if (!ws || !aligned16(ws)) return CHFSI_ERR_ARG;
-    SizeOnly sz;
-    filter_layout(sz, N, n_cols, m, L, low, low_values(H), nullptr);
-    if (ws_bytes < sz.used) return CHFSI_ERR_NOMEM;
-    Arena ar(ws, ws_bytes);
+namespace {
+
+// Everything a slab of the filter needs besides its columns.
+struct FilterRun {
+    const chfsi_matrix* H;
+    int64_t N;
+    int m, L, low;
+    const std::vector<double>* al;
+    const std::vector<double>* be;
+    double c;
+    CsrDev csr64, csrlo;
+    BsrDev bsr64, bsrlo;
     FilterLayout fl;
-    filter_layout(ar, N, n_cols, m, L, low, low_values(H), &fl);
+    int64_t ldw;
+    unsigned* st;
+    cudaStream_t s;
+};
 
-    cudaStream_t s = as_stream(stream);
-    unsigned* st = status_word(ws);
-    CHFSI_CUDA_TRY(cudaMemsetAsync(st, 0, sizeof(unsigned), s));
-
-    std::vector<double> al, be;
-    double c = 0.0;
-    coefficients(m, a, b, a0, al, be, c);
-    const int64_t n = n_cols, ldw = pad8(n);
+// All m steps on n columns: X and Y point at the slab's first column; the internal
+// buffers of fl are slab-sized with leading dimension ldw.
+int filter_columns(const FilterRun& R, const double* X, int64_t ldx, double* Y, int64_t ldy, int64_t n) {
+    const chfsi_matrix* H = R.H;
+    const FilterLayout& fl = R.fl;
+    const int64_t N = R.N, ldw = R.ldw;
+    const int m = R.m, L = R.L, low = R.low;
+    const std::vector<double>& al = *R.al;
+    const std::vector<double>& be = *R.be;
+    const double c = R.c;
+    unsigned* st = R.st;
+    cudaStream_t s = R.s;
+    int rc = CHFSI_OK;
     const bool vec = (n % 2 == 0) && (ldx % 2 == 0) && (ldy % 2 == 0);
-
-    CsrDev csr64{}, csrlo{};
-    BsrDev bsr64{}, bsrlo{};
-    make_devs(H, H->csr.val, H->bsr.val, Buf::F64, &csr64, &bsr64);
 
     // FP64 iterate k lives in cyc[(m - k) % 3], so that Y_m lands in Y.
     double* cyc[3] = {Y, fl.W[0], fl.W[1]};
@@ -301,8 +309,6 @@ int chfsi_filter(const chfsi_matrix* H, const double* X, int64_t ldx, double* Y,
 
     bool widened = false;   // low-precision Y_L, Y_{L-1} already widened into their FP64 slots
     if (L > 0 && low == CHFSI_F32X2) {
-        if (!has_csr(H)) return CHFSI_ERR_UNSUPPORTED;
-        if ((rc = to_f32x2(H->csr.val, 1, fl.hlow, 1, H->csr.nnz, 1, false, s))) return rc;
         const CsrDev h2{H->csr.n_rows, H->csr.nnz, H->csr.row_ptr, H->csr.col, fl.hlow, Buf::F32X2};
         if ((rc = to_f32x2(X, ldx, fl.D[0], ldw, N, n, true, s))) return rc;
         for (int k = 1; k <= L; k++) {
@@ -316,26 +322,20 @@ int chfsi_filter(const chfsi_matrix* H, const double* X, int64_t ldx, double* Y,
         if (L >= 2 && (rc = from_f32x2(fl.D[(L - 1) % 3], ldw, f64_buf(L - 1), f64_ld(L - 1), N, n, true, s))) return rc;
         widened = true;
     } else if (L > 0 && has_bsr(H) && low == CHFSI_BF16_F32ACC) {
-        // tensor-core path: BF16 blocks, state-major BF16 iterate copies
-        if ((rc = bsr_values_to_bf16(H->bsr.val, fl.hlow, bsr_values(H), s))) return rc;
-        make_devs(H, nullptr, fl.hlow, Buf::BF16, &csrlo, &bsrlo);
-        if ((rc = convert_block(X, Buf::F64, ldx, fl.F[0], Buf::F32, ldw, N, n, s))) return rc;
+        // tensor-core path: BF16 blocks, block-major BF16 iterate copies
+        if ((rc = convert_block(X, Buf::F64, ldx, fl.F[0], Buf::F32, ldw, N, n, ldw, s))) return rc;
         if ((rc = transpose_to_bf16(X, ldx, fl.S[0], N, n, s))) return rc;
         for (int k = 1; k <= L; k++) {
             const float* prev = k >= 2 ? fl.F[(k - 2) % 3] : nullptr;
-            rc = bsr_step_tc(bsrlo, n, fl.S[(k - 1) % 2], fl.F[(k - 1) % 3], ldw, prev, ldw, fl.F[k % 3], ldw,
+            rc = bsr_step_tc(R.bsrlo, n, fl.S[(k - 1) % 2], fl.F[(k - 1) % 3], ldw, prev, ldw, fl.F[k % 3], ldw,
                              fl.S[k % 2], al[k], c, k >= 2 ? be[k] : 0.0, st, s);
             if (rc) return rc;
         }
-        if (L == m) return convert_block(fl.F[m % 3], Buf::F32, ldw, Y, Buf::F64, ldy, N, n, s);
+        if (L == m) return convert_block(fl.F[m % 3], Buf::F32, ldw, Y, Buf::F64, ldy, N, n, n, s);
     } else if (L > 0) {
         const bool bf = low == CHFSI_BF16_F32ACC;
-        if (has_csr(H)) rc = convert_values(H->csr.val, fl.hlow, Buf::F32, H->csr.nnz, bf, s);
-        else rc = convert_values(H->bsr.val, fl.hlow, Buf::F32, bsr_values(H), bf, s);
-        if (rc) return rc;
-        make_devs(H, fl.hlow, fl.hlow, Buf::F32, &csrlo, &bsrlo);
-        if ((rc = convert_block(X, Buf::F64, ldx, fl.F[0], Buf::F32, ldw, N, n, s))) return rc;
-        if (bf && (rc = convert_block(X, Buf::F64, ldx, fl.S[0], Buf::BF16, ldw, N, n, s))) return rc;
+        if ((rc = convert_block(X, Buf::F64, ldx, fl.F[0], Buf::F32, ldw, N, n, ldw, s))) return rc;
+        if (bf && (rc = convert_block(X, Buf::F64, ldx, fl.S[0], Buf::BF16, ldw, N, n, ldw, s))) return rc;
         const StepMath lm = bf ? StepMath::BF16 : StepMath::F32;
         for (int k = 1; k <= L; k++) {
             StepIO io{};
@@ -346,11 +346,11 @@ int chfsi_filter(const chfsi_matrix* H, const double* X, int64_t ldx, double* Y,
             if (k >= 2) { io.prev = fl.F[(k - 2) % 3]; io.prev_t = Buf::F32; io.ldp = ldw; }
             io.out = fl.F[k % 3]; io.out_t = Buf::F32; io.ldo = ldw;
             if (bf) { io.shadow = fl.S[k % 2]; io.lds = ldw; }
-            rc = run_step(H, csrlo, bsrlo, lm, n, io, al[k], c, k >= 2 ? be[k] : 0.0, true, st, s);
+            rc = run_step(H, R.csrlo, R.bsrlo, lm, n, io, al[k], c, k >= 2 ? be[k] : 0.0, true, st, s);
             if (rc) return rc;
         }
         if (L == m)   // no FP64 step: widen the last iterate into Y
-            return convert_block(fl.F[m % 3], Buf::F32, ldw, Y, Buf::F64, ldy, N, n, s);
+            return convert_block(fl.F[m % 3], Buf::F32, ldw, Y, Buf::F64, ldy, N, n, n, s);
     }
 
     for (int k = L + 1; k <= m; k++) {
@@ -367,8 +367,70 @@ int chfsi_filter(const chfsi_matrix* H, const double* X, int64_t ldx, double* Y,
             else { io.prev = f64_buf(k - 2); io.prev_t = Buf::F64; io.ldp = f64_ld(k - 2); }
         }
         io.out = f64_buf(k); io.out_t = Buf::F64; io.ldo = f64_ld(k);
-        rc = run_step(H, csr64, bsr64, StepMath::F64, n, io, al[k], c, k >= 2 ? be[k] : 0.0, vec, st, s);
+        rc = run_step(H, R.csr64, R.bsr64, StepMath::F64, n, io, al[k], c, k >= 2 ? be[k] : 0.0, vec, st, s);
         if (rc) return rc;
+    }
+    return CHFSI_OK;
+}
+
+}  // namespace
+
+int chfsi_filter(const chfsi_matrix* H, const double* X, int64_t ldx, double* Y, int64_t ldy, int64_t n_cols,
+                 int32_t m, double a, double b, double a0, const chfsi_schedule* sched, void* ws, size_t ws_bytes,
+                 void* stream) {
+    int64_t N = 0;
+    int rc = rows_of(H, &N);
+    if (rc) return rc;
+    if (n_cols < 0 || m < 1) return CHFSI_ERR_ARG;
+    if ((rc = check_bounds(a, b, a0))) return rc;
+    if (n_cols == 0) return CHFSI_OK;
+    if ((rc = check_block(X, ldx, n_cols)) || (rc = check_block(Y, ldy, n_cols))) return rc;
+    if (X == Y) return CHFSI_ERR_ARG;
+    int L = 0, low = 0;
+    if ((rc = schedule_prefix(sched, m, &L, &low))) return rc;
+    if (!ws || !aligned16(ws)) return CHFSI_ERR_ARG;
+    const int64_t slab = filter_slab(H, n_cols);
+    SizeOnly sz;
+    filter_layout(sz, N, slab, m, L, low, low_values(H), nullptr);
+    if (ws_bytes < sz.used) return CHFSI_ERR_NOMEM;
+    if (L > 0 && low == CHFSI_F32X2 && !has_csr(H)) return CHFSI_ERR_UNSUPPORTED;
+
+    std::vector<double> al, be;
+    FilterRun R{};
+    R.H = H;
+    R.N = N;
+    R.m = m;
+    R.L = L;
+    R.low = low;
+    R.al = &al;
+    R.be = &be;
+    R.ldw = pad8(slab);
+    R.s = as_stream(stream);
+    R.st = status_word(ws);
+    Arena ar(ws, ws_bytes);
+    filter_layout(ar, N, slab, m, L, low, low_values(H), &R.fl);
+    coefficients(m, a, b, a0, al, be, R.c);
+    CHFSI_CUDA_TRY(cudaMemsetAsync(R.st, 0, sizeof(unsigned), R.s));
+    make_devs(H, H->csr.val, H->bsr.val, Buf::F64, &R.csr64, &R.bsr64);
+
+    // low-precision copies of H's values, once for all slabs
+    cudaStream_t s = R.s;
+    if (L > 0 && low == CHFSI_F32X2) {
+        rc = to_f32x2(H->csr.val, 1, R.fl.hlow, 1, H->csr.nnz, 1, false, s);
+    } else if (L > 0 && has_bsr(H) && low == CHFSI_BF16_F32ACC) {
+        rc = bsr_values_to_bf16(H->bsr.val, R.fl.hlow, bsr_values(H), s);
+        make_devs(H, nullptr, R.fl.hlow, Buf::BF16, &R.csrlo, &R.bsrlo);
+    } else if (L > 0) {
+        const bool bf = low == CHFSI_BF16_F32ACC;
+        if (has_csr(H)) rc = convert_values(H->csr.val, R.fl.hlow, Buf::F32, H->csr.nnz, bf, s);
+        else rc = convert_values(H->bsr.val, R.fl.hlow, Buf::F32, bsr_values(H), bf, s);
+        make_devs(H, R.fl.hlow, R.fl.hlow, Buf::F32, &R.csrlo, &R.bsrlo);
+    }
+    if (rc) return rc;
+
+    for (int64_t j0 = 0; j0 < n_cols; j0 += slab) {
+        const int64_t ns = std::min(slab, n_cols - j0);
+        if ((rc = filter_columns(R, X + j0, ldx, Y + j0, ldy, ns))) return rc;
     }
     return CHFSI_OK;
 }

@@ -252,10 +252,10 @@ __global__ void symmetrize_kernel(double* S, int64_t lds, int64_t n) {
 
 template <typename TS, typename TD>
 __global__ void convert_kernel(const TS* __restrict__ src, int64_t lds, TD* dst, int64_t ldd, int64_t rows,
-                               int64_t n) {
+                               int64_t n, int64_t width) {
     int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= rows * ldd) return;
-    int64_t i = idx / ldd, j = idx % ldd;
+    if (idx >= rows * width) return;
+    const int64_t i = idx / width, j = idx % width;
     float fv;
     double dv;
     if (j < n) {
@@ -264,18 +264,18 @@ __global__ void convert_kernel(const TS* __restrict__ src, int64_t lds, TD* dst,
     } else {
         dv = 0.0; fv = 0.0f;
     }
-    if constexpr (std::is_same<TD, double>::value) dst[idx] = dv;
-    else if constexpr (std::is_same<TD, float>::value) dst[idx] = fv;
-    else dst[idx] = __float2bfloat16_rn(fv);
+    if constexpr (std::is_same<TD, double>::value) dst[i * ldd + j] = dv;
+    else if constexpr (std::is_same<TD, float>::value) dst[i * ldd + j] = fv;
+    else dst[i * ldd + j] = __float2bfloat16_rn(fv);
 }
 
 template <typename TS, typename TD>
-int launch_convert(const void* src, int64_t lds, void* dst, int64_t ldd, int64_t rows, int64_t n,
+int launch_convert(const void* src, int64_t lds, void* dst, int64_t ldd, int64_t rows, int64_t n, int64_t width,
                    cudaStream_t s) {
-    int64_t total = rows * ldd;
+    int64_t total = rows * width;
     if (total <= 0) return CHFSI_OK;
     convert_kernel<TS, TD><<<(unsigned)((total + 255) / 256), 256, 0, s>>>(
-        static_cast<const TS*>(src), lds, static_cast<TD*>(dst), ldd, rows, n);
+        static_cast<const TS*>(src), lds, static_cast<TD*>(dst), ldd, rows, n, width);
     CHFSI_LAUNCH_CHECK();
     return CHFSI_OK;
 }
@@ -371,13 +371,16 @@ int symmetrize(double* S, int64_t n, int64_t lds, cudaStream_t s) {
 }
 
 int convert_block(const void* src, Buf st, int64_t lds, void* dst, Buf dt, int64_t ldd, int64_t rows, int64_t n,
-                  cudaStream_t s) {
-    if (st == Buf::F64 && dt == Buf::F32) return launch_convert<double, float>(src, lds, dst, ldd, rows, n, s);
-    if (st == Buf::F64 && dt == Buf::BF16) return launch_convert<double, __nv_bfloat16>(src, lds, dst, ldd, rows, n, s);
-    if (st == Buf::F32 && dt == Buf::F64) return launch_convert<float, double>(src, lds, dst, ldd, rows, n, s);
-    if (st == Buf::F32 && dt == Buf::BF16) return launch_convert<float, __nv_bfloat16>(src, lds, dst, ldd, rows, n, s);
-    if (st == Buf::F64 && dt == Buf::F64) return launch_convert<double, double>(src, lds, dst, ldd, rows, n, s);
-    if (st == Buf::F32 && dt == Buf::F32) return launch_convert<float, float>(src, lds, dst, ldd, rows, n, s);
+                  int64_t width, cudaStream_t s) {
+    if (width < n || width > ldd) return CHFSI_ERR_ARG;
+    if (st == Buf::F64 && dt == Buf::F32) return launch_convert<double, float>(src, lds, dst, ldd, rows, n, width, s);
+    if (st == Buf::F64 && dt == Buf::BF16)
+        return launch_convert<double, __nv_bfloat16>(src, lds, dst, ldd, rows, n, width, s);
+    if (st == Buf::F32 && dt == Buf::F64) return launch_convert<float, double>(src, lds, dst, ldd, rows, n, width, s);
+    if (st == Buf::F32 && dt == Buf::BF16)
+        return launch_convert<float, __nv_bfloat16>(src, lds, dst, ldd, rows, n, width, s);
+    if (st == Buf::F64 && dt == Buf::F64) return launch_convert<double, double>(src, lds, dst, ldd, rows, n, width, s);
+    if (st == Buf::F32 && dt == Buf::F32) return launch_convert<float, float>(src, lds, dst, ldd, rows, n, width, s);
     return CHFSI_ERR_UNSUPPORTED;
 }
 

@@ -75,10 +75,11 @@ int gemm_nn_f32x2(const void* A, int64_t lda, const void* B, int64_t ldb, void* 
                   int64_t M, int64_t n, bool b_upper, cudaStream_t s);
 int transpose_to_bf16(const double* src, int64_t lds, void* dst, int64_t N, int64_t n, cudaStream_t s);
 
-// Element-wise conversions (row-major blocks with leading dimensions; padding
-// columns [n, ld_out) of the output are zero-filled).
+// Element-wise conversions (row-major blocks with leading dimensions): columns
+// [0, width) of each output row are written, [n, width) as zeros (n <= width <= ldd);
+// internal buffers pass width = ldd, caller blocks width = n.
 int convert_block(const void* src, Buf src_t, int64_t lds, void* dst, Buf dst_t, int64_t ldd,
-                  int64_t rows, int64_t n, cudaStream_t s);
+                  int64_t rows, int64_t n, int64_t width, cudaStream_t s);
 int convert_values(const double* src, void* dst, Buf dst_t, int64_t count, bool round_bf16,
                    cudaStream_t s);
 

@@ -244,6 +244,68 @@ def test_filter_f32x2_is_fp64_accurate(P, oracle_mod, g, w, n, m, L):
     assert rel_fro(Y, Yref) <= 1e-12
 
 
+@pytest.mark.parametrize("schedule", [None, "f32x2"])
+def test_unsorted_rows_with_duplicate_columns(P, oracle_mod, schedule):
+    """Rows in random order with some entries split into two entries on the same
+    column (CSR sums duplicates), on an odd row count: the FP64 step and the
+    two-float row-pair step (whose merge of two rows must emit every entry once
+    whatever the order) match the oracle on the sorted operator."""
+    H, X = make_case(7, 2, 24, seed=57)
+    (a, b, a0), _ = bounds_for(oracle_mod, H, 24)
+    rng = np.random.default_rng(5)
+    rp, col, val = H["row_ptr"], H["col"], H["val"]
+    rows_c, rows_v = [], []
+    for r in range(H["N"]):
+        c, v = col[rp[r]:rp[r + 1]].copy(), val[rp[r]:rp[r + 1]].copy()
+        split = rng.random(len(c)) < 0.2
+        frac = rng.random(int(split.sum()))
+        c = np.concatenate([c, c[split]])
+        v = np.concatenate([np.where(split, 0.0, v), v[split] * frac])
+        v[np.flatnonzero(split)] = val[rp[r]:rp[r + 1]][split] * (1.0 - frac)
+        order = rng.permutation(len(c))
+        rows_c.append(c[order])
+        rows_v.append(v[order])
+    Hs = dict(N=H["N"], nnz=sum(len(c) for c in rows_c),
+              row_ptr=np.concatenate([[0], np.cumsum([len(c) for c in rows_c])]).astype(np.int64),
+              col=np.concatenate(rows_c).astype(np.int32), val=np.concatenate(rows_v))
+    assert Hs["N"] % 2 == 1 and Hs["nnz"] > H["nnz"]
+    m = 9
+    Yref = oracle_mod.filter(H, X, m, a, b, a0)
+    ws = P.Workspace(DEV)
+    sched = None if schedule is None else [schedule] * m
+    Y = P.filter(to_dev(P, Hs), dev(X), m, a, b, a0, schedule=sched, workspace=ws).cpu().numpy()
+    assert P.read_status(ws) == 0
+    assert rel_fro(Y, Yref) <= 1e-12
+
+
+@pytest.mark.parametrize("schedule", [None, "f32", "f32x2", "bf16", "mixed"])
+def test_column_slabs_and_views_of_wider_blocks(P, oracle_mod, schedule):
+    """More than 512 states (the filter runs in column slabs of 512, here 512 + 512 +
+    77 with an odd last slab) with X and Y column views of wider row-major blocks:
+    results match the oracle and Y's columns beyond n are left untouched."""
+    H, Xfull = make_case(8, 2, 1101, seed=61)
+    (a, b, a0), _ = bounds_for(oracle_mod, H, 64)
+    m = 6
+    n = Xfull.shape[1]
+    Xw = torch.zeros((H["N"], 1210), dtype=torch.float64, device=DEV)
+    Xw[:, :n] = dev(Xfull)
+    Yw = torch.full((H["N"], 1306), 7.25, dtype=torch.float64, device=DEV)
+    Xv, Yv = Xw[:, :n], Yw[:, :n]
+    if schedule is None:
+        sched = None
+    elif schedule == "mixed":
+        sched = P.mixed_schedule(m, 4, "f32x2")
+    else:
+        sched = [schedule] * m
+    ws = P.Workspace(DEV)
+    P.filter(to_dev(P, H), Xv, m, a, b, a0, schedule=sched, out=Yv, workspace=ws)
+    assert P.read_status(ws) == 0
+    Yref = oracle_mod.filter(H, Xfull, m, a, b, a0)
+    tol = {"f32": 2e-5, "bf16": 5e-2}.get(schedule, 1e-12)
+    assert rel_fro(Yv.cpu().numpy(), Yref) <= tol
+    assert bool(torch.all(Yw[:, n:] == 7.25))
+
+
 def test_filter_f32x2_config_40cube_sampled_columns(P, oracle_mod):
     wl = W.workload("g40_w3_n1024_m20")
     H, X = make_case(wl.g, wl.w, wl.n, seed=wl.seed)
