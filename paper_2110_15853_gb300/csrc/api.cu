@@ -547,6 +547,10 @@ int backward_sweep(int m, const BackLayout& bl, int64_t ldw, const std::vector<d
     return CHFSI_OK;
 }
 
+// The reverse sweep reads only the CSR, so it runs in column slabs whatever the layout:
+// dX's columns are independent and dH sums over all columns (each slab adds its part).
+inline int64_t backward_slab(int64_t n) { return n > kSlab ? kSlab : n; }
+
 int backward_check(const chfsi_matrix* H, int64_t n_cols, int32_t m, int32_t ckpt_stride, int32_t precision,
                    int64_t* N) {
     int rc = rows_of(H, N);
@@ -566,7 +570,7 @@ int chfsi_filter_backward_ex_workspace_size(const chfsi_matrix* H, int64_t n_col
     int rc = backward_check(H, n_cols, m, ckpt_stride, precision, &N);
     if (rc) return rc;
     SizeOnly sz;
-    back_layout(sz, N, n_cols, m, ckpt_stride, precision, H->csr.nnz, nullptr);
+    back_layout(sz, N, backward_slab(n_cols), m, ckpt_stride, precision, H->csr.nnz, nullptr);
     *bytes = sz.used;
     return CHFSI_OK;
 }
@@ -594,56 +598,65 @@ int chfsi_filter_backward_ex(const chfsi_matrix* H, const double* X, int64_t ldx
         return rc;
     if (dX == X || dX == dY) return CHFSI_ERR_ARG;
     if (!ws || !aligned16(ws)) return CHFSI_ERR_ARG;
+    const int64_t slab = backward_slab(n_cols);
     SizeOnly sz;
-    back_layout(sz, N, n_cols, m, ckpt_stride, precision, H->csr.nnz, nullptr);
+    back_layout(sz, N, slab, m, ckpt_stride, precision, H->csr.nnz, nullptr);
     if (ws_bytes < sz.used) return CHFSI_ERR_NOMEM;
     Arena ar(ws, ws_bytes);
     BackLayout bl;
-    back_layout(ar, N, n_cols, m, ckpt_stride, precision, H->csr.nnz, &bl);
+    back_layout(ar, N, slab, m, ckpt_stride, precision, H->csr.nnz, &bl);
     unsigned* st = status_word(ws);
     CHFSI_CUDA_TRY(cudaMemsetAsync(st, 0, sizeof(unsigned), s));
 
     std::vector<double> al, be;
     double c = 0.0;
     coefficients(m, a, b, a0, al, be, c);
-    const int64_t n = n_cols, ldw = pad8(n);
+    const int64_t ldw = pad8(slab);
     if (dH_val && (rc = fill_zero(dH_val, sizeof(double) * (size_t)H->csr.nnz, s))) return rc;
+    if (precision == CHFSI_F32X2 && (rc = to_f32x2(H->csr.val, 1, bl.H2, 1, H->csr.nnz, 1, false, s))) return rc;
 
-    if (precision == CHFSI_F64) {
-        const bool vec = (n % 2 == 0) && (ldx % 2 == 0) && (lddy % 2 == 0) && (lddx % 2 == 0);
-        const CsrDev h{H->csr.n_rows, H->csr.nnz, H->csr.row_ptr, H->csr.col, H->csr.val, Buf::F64};
+    for (int64_t j0 = 0; j0 < n_cols; j0 += slab) {
+        const int64_t n = std::min(slab, n_cols - j0);
+        const double* Xs = X + j0;
+        const double* dYs = dY + j0;
+        double* dXs = dX + j0;
+        if (precision == CHFSI_F64) {
+            const bool vec = (n % 2 == 0) && (ldx % 2 == 0) && (lddy % 2 == 0) && (lddx % 2 == 0);
+            const CsrDev h{H->csr.n_rows, H->csr.nnz, H->csr.row_ptr, H->csr.col, H->csr.val, Buf::F64};
+            BackStep step = [&](const void* cur, int64_t ldc, const void* prev, int64_t ldp, void* out,
+                                int64_t ldo, double alpha, double beta) {
+                StepIO io{};
+                io.cur = cur; io.cur_t = Buf::F64; io.ldc = ldc;
+                io.gather = cur; io.gather_t = Buf::F64; io.ldg = ldc;
+                if (prev) { io.prev = prev; io.prev_t = Buf::F64; io.ldp = ldp; }
+                io.out = out; io.out_t = Buf::F64; io.ldo = ldo;
+                return csr_step(h, StepMath::F64, n, io, alpha, c, beta, vec, st, s);
+            };
+            BackSddmm sddmm = [&](const void* yb, int64_t ldb, const void* ypv, int64_t ldp, double alpha) {
+                return sddmm_accumulate(h, n, static_cast<const double*>(yb), ldb, static_cast<const double*>(ypv),
+                                        ldp, alpha, dH_val, s);
+            };
+            rc = backward_sweep(m, bl, ldw, al, be, Xs, ldx, dYs, lddy, dXs, lddx, dH_val != nullptr, step, sddmm);
+            if (rc) return rc;
+            continue;
+        }
+        // two-float: hi/lo copies of the slab of X and dY; Ybar_0 widened into dX at the end
+        if ((rc = to_f32x2(Xs, ldx, bl.X2, ldw, N, n, true, s))) return rc;
+        if ((rc = to_f32x2(dYs, lddy, bl.G2, ldw, N, n, true, s))) return rc;
+        const CsrDev h2{H->csr.n_rows, H->csr.nnz, H->csr.row_ptr, H->csr.col, bl.H2, Buf::F32X2};
         BackStep step = [&](const void* cur, int64_t ldc, const void* prev, int64_t ldp, void* out, int64_t ldo,
                             double alpha, double beta) {
-            StepIO io{};
-            io.cur = cur; io.cur_t = Buf::F64; io.ldc = ldc;
-            io.gather = cur; io.gather_t = Buf::F64; io.ldg = ldc;
-            if (prev) { io.prev = prev; io.prev_t = Buf::F64; io.ldp = ldp; }
-            io.out = out; io.out_t = Buf::F64; io.ldo = ldo;
-            return csr_step(h, StepMath::F64, n, io, alpha, c, beta, vec, st, s);
+            return csr_step_f32x2(h2, n, cur, ldc, prev, prev ? ldp : 0, out, ldo, alpha, c, beta, st, s);
         };
         BackSddmm sddmm = [&](const void* yb, int64_t ldb, const void* ypv, int64_t ldp, double alpha) {
-            return sddmm_accumulate(h, n, static_cast<const double*>(yb), ldb, static_cast<const double*>(ypv), ldp,
-                                    alpha, dH_val, s);
+            return sddmm_accumulate_f32x2(h2, n, yb, ldb, ypv, ldp, alpha, dH_val, s);
         };
-        return backward_sweep(m, bl, ldw, al, be, X, ldx, dY, lddy, dX, lddx, dH_val != nullptr, step, sddmm);
+        if ((rc = backward_sweep(m, bl, ldw, al, be, bl.X2, ldw, bl.G2, ldw, bl.D0, ldw, dH_val != nullptr, step,
+                                 sddmm)))
+            return rc;
+        if ((rc = from_f32x2(bl.D0, ldw, dXs, lddx, N, n, true, s))) return rc;
     }
-
-    // two-float: hi/lo copies of X, dY and H; Ybar_0 widened into dX at the end
-    if ((rc = to_f32x2(H->csr.val, 1, bl.H2, 1, H->csr.nnz, 1, false, s))) return rc;
-    if ((rc = to_f32x2(X, ldx, bl.X2, ldw, N, n, true, s))) return rc;
-    if ((rc = to_f32x2(dY, lddy, bl.G2, ldw, N, n, true, s))) return rc;
-    const CsrDev h2{H->csr.n_rows, H->csr.nnz, H->csr.row_ptr, H->csr.col, bl.H2, Buf::F32X2};
-    BackStep step = [&](const void* cur, int64_t ldc, const void* prev, int64_t ldp, void* out, int64_t ldo,
-                        double alpha, double beta) {
-        return csr_step_f32x2(h2, n, cur, ldc, prev, prev ? ldp : 0, out, ldo, alpha, c, beta, st, s);
-    };
-    BackSddmm sddmm = [&](const void* yb, int64_t ldb, const void* ypv, int64_t ldp, double alpha) {
-        return sddmm_accumulate_f32x2(h2, n, yb, ldb, ypv, ldp, alpha, dH_val, s);
-    };
-    if ((rc = backward_sweep(m, bl, ldw, al, be, bl.X2, ldw, bl.G2, ldw, bl.D0, ldw, dH_val != nullptr, step,
-                             sddmm)))
-        return rc;
-    return from_f32x2(bl.D0, ldw, dX, lddx, N, n, true, s);
+    return CHFSI_OK;
 }
 
 int chfsi_filter_backward(const chfsi_matrix* H, const double* X, int64_t ldx, const double* dY, int64_t lddy,

@@ -482,6 +482,26 @@ def test_adjoint_f32x2_matches_oracle(P, oracle_mod, g, w, n, m, stride):
     assert rel_fro(dH.cpu().numpy(), dH_ref) <= 1e-10
 
 
+@pytest.mark.parametrize("precision", ["f64", "f32x2"])
+def test_adjoint_column_slabs_and_views(P, oracle_mod, precision):
+    """More than 512 states: the reverse sweep runs in column slabs (512 + 512 + 7),
+    each slab adding its part of dH; X and dY are column views of wider blocks."""
+    H, Xfull = make_case(6, 2, 1031, seed=67)
+    (a, b, a0), _ = bounds_for(oracle_mod, H, 32)
+    m = 7
+    n = Xfull.shape[1]
+    wts = W.loss_weights(H["N"], 5)
+    G = 2.0 * wts[:, None] * oracle_mod.filter(H, Xfull, m, a, b, a0)
+    dX_ref, dH_ref = oracle_mod.filter_adjoint(H, Xfull, m, a, b, a0, G)
+    Xw = torch.zeros((H["N"], 1100), dtype=torch.float64, device=DEV)
+    Gw = torch.zeros((H["N"], 1042), dtype=torch.float64, device=DEV)
+    Xw[:, :n] = dev(Xfull)
+    Gw[:, :n] = dev(G)
+    dX, dH = P.filter_backward(to_dev(P, H), Xw[:, :n], Gw[:, :n], m, a, b, a0, precision=precision)
+    assert rel_fro(dX.cpu().numpy(), dX_ref) <= 1e-10
+    assert rel_fro(dH.cpu().numpy(), dH_ref) <= 1e-10
+
+
 def test_adjoint_autograd_and_finite_differences(P, oracle_mod):
     """L = tr(Y^T W Y) through torch.autograd; dL/dH checked against central
     differences (step 1e-6) of the GPU forward on sampled entries."""
