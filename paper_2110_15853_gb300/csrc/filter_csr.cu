@@ -109,6 +109,59 @@ __device__ __forceinline__ void cp_async_wait_all() {
     asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
 
+// Gathered operand of one chunk: converted values, or for the BF16 operand the raw
+// bf16 pairs, which the mixed-precision FMA (fma.rn.f32.bf16: BF16 x BF16 product,
+// FP32 addend) consumes without a conversion instruction.
+template <typename ACC, typename TG, int V>
+struct Gathered {
+    ACC v[V];
+    __device__ __forceinline__ void load(const TG* p) { ldv<ACC, TG, V>(p, v); }
+    __device__ __forceinline__ void zero() {
+#pragma unroll
+        for (int i = 0; i < V; i++) v[i] = (ACC)0;
+    }
+    __device__ __forceinline__ void madd(ACC h, ACC (&acc)[V]) const {
+#pragma unroll
+        for (int i = 0; i < V; i++) acc[i] = fma(h, v[i], acc[i]);
+    }
+};
+
+template <int V>
+struct Gathered<float, __nv_bfloat16, V> {
+    static_assert(V % 4 == 0, "BF16 operand chunks are 4-element vectors");
+    uint32_t w[V / 2];
+    __device__ __forceinline__ void load(const __nv_bfloat16* p) {
+#pragma unroll
+        for (int i = 0; i < V; i += 4) {
+            const uint2 t = __ldg(reinterpret_cast<const uint2*>(p + i));
+            w[i / 2] = t.x;
+            w[i / 2 + 1] = t.y;
+        }
+    }
+    __device__ __forceinline__ void zero() {
+#pragma unroll
+        for (int i = 0; i < V / 2; i++) w[i] = 0u;
+    }
+    // h must be exactly representable in BF16 (the BF16 schedule rounds H once).
+    __device__ __forceinline__ void madd(float h, float (&acc)[V]) const {
+        const __nv_bfloat16 hb = __float2bfloat16_rn(h);
+        const unsigned short hbits = *reinterpret_cast<const unsigned short*>(&hb);
+#pragma unroll
+        for (int i = 0; i < V / 2; i++) {
+            unsigned short lo, hi;
+            asm("mov.b32 {%0, %1}, %2;" : "=h"(lo), "=h"(hi) : "r"(w[i]));
+            asm("fma.rn.f32.bf16 %0, %1, %2, %0;" : "+f"(acc[2 * i]) : "h"(hbits), "h"(lo));
+            asm("fma.rn.f32.bf16 %0, %1, %2, %0;" : "+f"(acc[2 * i + 1]) : "h"(hbits), "h"(hi));
+        }
+    }
+};
+
+// Resident CTAs per SM the register budget of a low-precision step is sized for: the
+// FP32 and BF16-operand steps are bound by gather latency, so they trade chunks per
+// pass (U) for resident warps.  (The FP64 step, bound by the FP64 pipe, has no bound.)
+template <typename TG, int U>
+constexpr int lp_min_blocks() { return std::is_same<TG, float>::value && U <= 2 ? 4 : 3; }
+
 template <typename TH>
 __device__ __forceinline__ void stage_entry(TH* sv, int32_t* sc, const TH* val, const int32_t* col,
                                             int64_t p) {
@@ -122,13 +175,13 @@ __device__ __forceinline__ void stage_entry(TH* sv, int32_t* sc, const TH* val, 
 // output; TS: optional BF16 shadow of the output (void-like when !kShadow).
 template <typename ACC, typename TH, typename TG, typename TC, typename TP, typename TO, int V, int U,
           bool kShadow>
-__global__ void __launch_bounds__(kThreads)
-csr_step_kernel(int64_t N, const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
-                const TH* __restrict__ val, int64_t nnz, int64_t n,
-                const TG* __restrict__ Yg, int64_t ldg, const TC* __restrict__ Yc, int64_t ldc,
-                const TP* __restrict__ Yp, int64_t ldp, TO* __restrict__ Yo, int64_t ldo,
-                __nv_bfloat16* __restrict__ Ys, int64_t lds, ACC alpha, ACC c, ACC beta, int cap,
-                unsigned* status) {
+__device__ __forceinline__ void
+csr_step_body(int64_t N, const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+              const TH* __restrict__ val, int64_t nnz, int64_t n,
+              const TG* __restrict__ Yg, int64_t ldg, const TC* __restrict__ Yc, int64_t ldc,
+              const TP* __restrict__ Yp, int64_t ldp, TO* __restrict__ Yo, int64_t ldo,
+              __nv_bfloat16* __restrict__ Ys, int64_t lds, ACC alpha, ACC c, ACC beta, int cap,
+              unsigned* status) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TH* s_val = reinterpret_cast<TH*>(smem_raw);
     int32_t* s_col = reinterpret_cast<int32_t*>(smem_raw + sizeof(TH) * (size_t)cap);
@@ -183,28 +236,23 @@ csr_step_kernel(int64_t N, const int64_t* __restrict__ row_ptr, const int32_t* _
             // predicate-free path; a bad column index (unstaged rows only) becomes a
             // zero entry on row 0.
             const bool full = jbase + 32 * V * U <= n;
-            auto fetch = [&](int q, ACC (&y)[U][V], ACC& h) {
+            using G = Gathered<ACC, TG, V>;
+            auto fetch = [&](int q, G (&y)[U], ACC& h) {
                 int32_t cj = hc[q];
                 h = cvt<ACC>(hv[q]);
                 if (!staged && (cj < 0 || (int64_t)cj >= N)) { bad = true; cj = 0; h = (ACC)0; }
                 const TG* src = Yg + (int64_t)cj * ldg + j0;
 #pragma unroll
                 for (int u = 0; u < U; u++) {
-                    if (full || on[u]) {
-                        ldv<ACC, TG, V>(src + u * 32 * V, y[u]);
-                    } else {
-#pragma unroll
-                        for (int v = 0; v < V; v++) y[u][v] = (ACC)0;
-                    }
+                    if (full || on[u]) y[u].load(src + u * 32 * V);
+                    else y[u].zero();
                 }
             };
-            auto accumulate = [&](const ACC (&y)[U][V], ACC h) {
+            auto accumulate = [&](const G (&y)[U], ACC h) {
 #pragma unroll
-                for (int u = 0; u < U; u++)
-#pragma unroll
-                    for (int v = 0; v < V; v++) acc[u][v] = fma(h, y[u][v], acc[u][v]);
+                for (int u = 0; u < U; u++) y[u].madd(h, acc[u]);
             };
-            ACC ya[U][V], yb[U][V];
+            G ya[U], yb[U];
             ACC ha = (ACC)0, hb = (ACC)0;
             if (len > 0) fetch(0, ya, ha);
             int q = 0;
@@ -241,18 +289,56 @@ csr_step_kernel(int64_t N, const int64_t* __restrict__ row_ptr, const int32_t* _
     if (__syncthreads_or(bad) && threadIdx.x == 0) raise_status(status, DEV_PATTERN);
 }
 
+#define CSR_STEP_PARAMS                                                                                         \
+    int64_t N, const int64_t *__restrict__ row_ptr, const int32_t *__restrict__ col,                           \
+        const TH *__restrict__ val, int64_t nnz, int64_t n, const TG *__restrict__ Yg, int64_t ldg,           \
+        const TC *__restrict__ Yc, int64_t ldc, const TP *__restrict__ Yp, int64_t ldp, TO *__restrict__ Yo, \
+        int64_t ldo, __nv_bfloat16 *__restrict__ Ys, int64_t lds, ACC alpha, ACC c, ACC beta, int cap,        \
+        unsigned *status
+#define CSR_STEP_ARGS N, row_ptr, col, val, nnz, n, Yg, ldg, Yc, ldc, Yp, ldp, Yo, ldo, Ys, lds, alpha, c, beta, cap, status
+
+// FP64 step (and FP64 steps reading FP32 iterates).
+template <typename ACC, typename TH, typename TG, typename TC, typename TP, typename TO, int V, int U,
+          bool kShadow>
+__global__ void __launch_bounds__(kThreads) csr_step_kernel(CSR_STEP_PARAMS) {
+    csr_step_body<ACC, TH, TG, TC, TP, TO, V, U, kShadow>(CSR_STEP_ARGS);
+}
+
+// FP32 and BF16-operand steps.
+template <typename ACC, typename TH, typename TG, typename TC, typename TP, typename TO, int V, int U,
+          bool kShadow>
+__global__ void __launch_bounds__(kThreads, lp_min_blocks<TG, U>()) csr_step_lp_kernel(CSR_STEP_PARAMS) {
+    csr_step_body<ACC, TH, TG, TC, TP, TO, V, U, kShadow>(CSR_STEP_ARGS);
+}
+
+#undef CSR_STEP_PARAMS
+#undef CSR_STEP_ARGS
+
 template <typename ACC, typename TH, typename TG, typename TC, typename TP, typename TO, int V, int U,
           bool kShadow>
 int launch(const CsrDev& h, const void* hval, int64_t n, const StepIO& io, double alpha, double c,
            double beta, unsigned* status, cudaStream_t s) {
-    const int cap = 6144;
+    constexpr int kCapMax = 6144;   // staged entries per CTA (8 rows x up to 768 entries)
+    // The low-precision steps stage 8 rows of a typical length (1.25 x the mean, longer
+    // row blocks read their entries from global memory), so that shared memory leaves
+    // L1 room for the gathers at their higher occupancy.
+    int cap = kCapMax;
+    if (!std::is_same<ACC, double>::value) {
+        const int64_t mean = (h.nnz + h.N - 1) / h.N;
+        int64_t want = (kWarps * mean * 5 / 4 + 127) / 128 * 128;
+        cap = (int)(want < 256 ? 256 : (want > kCapMax ? kCapMax : want));
+    }
     const size_t smem = (sizeof(TH) + sizeof(int32_t)) * (size_t)cap;
-    auto kern = csr_step_kernel<ACC, TH, TG, TC, TP, TO, V, U, kShadow>;
+    const size_t smem_max = (sizeof(TH) + sizeof(int32_t)) * (size_t)kCapMax;
+    auto kern = [] {
+        if constexpr (std::is_same<ACC, double>::value) return csr_step_kernel<ACC, TH, TG, TC, TP, TO, V, U, kShadow>;
+        else return csr_step_lp_kernel<ACC, TH, TG, TC, TP, TO, V, U, kShadow>;
+    }();
     static bool attr_set[kMaxDevices] = {};   // per instantiation and device
     const int dev = current_device();
     if (dev < 0) return CHFSI_ERR_CUDA;
     if (!attr_set[dev]) {
-        CHFSI_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        CHFSI_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max));
         attr_set[dev] = true;
     }
     const int64_t blocks = (h.N + kWarps - 1) / kWarps;
@@ -298,7 +384,7 @@ int csr_step(const CsrDev& h, StepMath math, int64_t n, const StepIO& io, double
     if (h.val_t != Buf::F32) return CHFSI_ERR_UNSUPPORTED;
     if (math == StepMath::F32) {
         if (g == Buf::F32 && cu == Buf::F32 && p == Buf::F32 && o == Buf::F32)
-            return launch<float, float, float, float, float, float, 4, 4, false>(h, h.val, n, io, alpha, c, beta, status, s);
+            return launch<float, float, float, float, float, float, 4, 2, false>(h, h.val, n, io, alpha, c, beta, status, s);
         return CHFSI_ERR_UNSUPPORTED;
     }
     // BF16 operand, FP32 accumulate
