@@ -63,6 +63,9 @@ def parse_args():
     ap.add_argument("--closure-only", action="store_true",
                     help="set up, run one CholQR2 + Rayleigh-Ritz on X and exit: a profiling case")
     ap.add_argument("--precision", default="f64", choices=["f64", "f32x2"], help="closure-only product precision")
+    ap.add_argument("--compact", action="store_true",
+                    help="largest workloads: variants limited to the FP64 filter, the FP32 prefix and the "
+                         "two-float filter (each with its Ritz error) and the two-float step; no adjoint, no BSR")
     ap.add_argument("--quick", action="store_true",
                     help="large one-off workloads: variants timed once without warm-up, no BSR-FP64 variant, "
                          "no end-to-end leg")
@@ -387,7 +390,7 @@ def run_ours(args):
     # back.  The copies run on a second stream with double-buffered device blocks, so the
     # input of step k+1 and the result of step k-1 move while step k computes.
     e2e = None
-    if not args.quick:
+    if not (args.quick or args.compact):
         Xh = torch.empty((N, n), dtype=torch.float64).pin_memory()
         Xh.copy_(torch.as_tensor(X))
         v0h = torch.as_tensor(v0).pin_memory()
@@ -446,7 +449,8 @@ def run_ours(args):
 
     variants = {}
     if not args.no_variants and rank == 0:
-        variants = measure_variants(P, torch, dev, stream, wl, H, Hd, Xd, bounds, quick=args.quick)
+        variants = measure_variants(P, torch, dev, stream, wl, H, Hd, Xd, bounds, quick=args.quick or args.compact,
+                                    compact=args.compact)
         v2 = variants.get("step_f32x2_filter_and_closure")
         if v2 and v2.get("ms"):
             v2["speedup_vs_f64_step"] = ms_step / v2["ms"]
@@ -529,7 +533,11 @@ def run_filter_only(P, torch, dev, wl, H, X, v0, args):
     return 0
 
 
-def measure_variants(P, torch, dev, stream, wl, H, Hd, Xd, bounds, quick=False):
+class _Skipped(Exception):
+    """A variant group left out on purpose (reported as skipped)."""
+
+
+def measure_variants(P, torch, dev, stream, wl, H, Hd, Xd, bounds, quick=False, compact=False):
     """Filter-only timings of the other layouts / schedules on the same workload
     (outside the main timed region), each with its error against the FP64 CSR run."""
     a, b, a0 = bounds
@@ -559,7 +567,9 @@ def measure_variants(P, torch, dev, stream, wl, H, Hd, Xd, bounds, quick=False):
     theta_ref, _ = P.rayleigh_ritz(Hd, Yref, 2, workspace=rr_ws)
     theta_ref = theta_ref.cpu().numpy()
 
-    for low, L in (("f32", m - 4), ("bf16", m - 4), ("f32x2", m), ("f32x2", m - 4)):
+    schedules = (("f32", m - 4), ("f32x2", m)) if compact else (("f32", m - 4), ("bf16", m - 4), ("f32x2", m),
+                                                                  ("f32x2", m - 4))
+    for low, L in schedules:
         Ym = torch.empty_like(Xd)
         sched = P.mixed_schedule(m, L, low)
         try:
@@ -577,6 +587,8 @@ def measure_variants(P, torch, dev, stream, wl, H, Hd, Xd, bounds, quick=False):
     # adjoint (reverse sweep with sqrt(m) checkpoints), FP64 and two-float; algorithmic
     # work m (4 nnz n + 5 N n) plus one forward replay
     try:
+        if compact:
+            raise _Skipped("--compact")
         wts = torch.as_tensor(W.loss_weights(N, wl.seed)).to(dev)
         G = 2.0 * wts[:, None] * Yref
         adj_fl = m * (4.0 * nnz * n + 5.0 * N * n) + fl
@@ -592,6 +604,8 @@ def measure_variants(P, torch, dev, stream, wl, H, Hd, Xd, bounds, quick=False):
             "dX_rel_err_vs_f64": float(torch.linalg.norm(dX2 - dX64) / torch.linalg.norm(dX64)),
             "dH_rel_err_vs_f64": float(torch.linalg.norm(dH2 - dH64) / torch.linalg.norm(dH64))}
         del G, dX64, dH64, dX2, dH2, bw_ws
+    except _Skipped as e:
+        out["adjoint"] = {"skipped": str(e)}
     except Exception as e:  # noqa: BLE001 - report, do not hide
         out["adjoint_error"] = repr(e)
 
@@ -624,6 +638,8 @@ def measure_variants(P, torch, dev, stream, wl, H, Hd, Xd, bounds, quick=False):
 
     # BSR layout of the same operator, and the hybrid (blocked CSR + BSR) operator
     try:
+        if compact:
+            raise _Skipped("--compact")
         B = W.bsr_from_csr(H, wl.g)
         Bd = P.BsrMatrix.from_arrays(B["brow_ptr"], B["bcol"], B["val"], device=dev)
         Hpd = P.CsrMatrix.from_arrays(**{k: v for k, v in W.permute_csr(H, B["perm"]).items()
@@ -666,6 +682,8 @@ def measure_variants(P, torch, dev, stream, wl, H, Hd, Xd, bounds, quick=False):
                 "ms": t, "gflops": fl / (t * 1e-3) / 1e9, "speedup_vs_f64": out["filter_csr_f64"]["ms"] / t,
                 "y_rel_fro_err_vs_f64": err_vs_ref(), "ritz_max_rel_err_vs_f64": ritz_err()}
         del Bd, Xp, Yb, Yback, Hpd, Hy
+    except _Skipped as e:
+        out["bsr_variants"] = {"skipped": str(e)}
     except Exception as e:  # noqa: BLE001 - report, do not hide
         out["bsr_variants_error"] = repr(e)
     return out
