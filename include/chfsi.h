@@ -14,7 +14,8 @@
  *   library never frees or retains them.  Dense blocks (X, Y, Psi, dY, dX) are
  *   row-major N x n_cols with an explicit leading dimension ld >= n_cols
  *   (element (i, j) at p[i * ld + j]); each block must start on a 16-byte boundary.
- *   An output block must not overlap any input.
+ *   Only columns 0 .. n_cols-1 of a row are read or written, so a block may be a
+ *   column view of a wider array.  An output block must not overlap any input.
  * - Scalars a, b, a0 are the paper's eps_ub^w (upper bound of the wanted
  *   spectrum), eps_ub^uw (upper bound of the unwanted spectrum) and eps_0 (lower
  *   bound of the wanted spectrum).  a0 < a < b is required (if a0 lies in [a, b]
@@ -143,6 +144,9 @@ int chfsi_filter_workspace_size(const chfsi_matrix* H, int64_t n_cols, int32_t m
  * returning the newest iterate Y_m (the paper's X~ after the loop).
  * X: N x n_cols (ldx), read only.  Y: N x n_cols (ldy), written.  m >= 1.
  * sched: NULL for all-FP64, else a schedule with sched->m == m.
+ * A CSR operator over more than 512 columns is filtered in column slabs of 512
+ * (all m steps per slab; the columns are independent), so the workspace holds one
+ * slab's iterates.
  * Errors: CHFSI_ERR_ARG, CHFSI_ERR_BOUNDS, CHFSI_ERR_NOMEM, CHFSI_ERR_UNSUPPORTED,
  * CHFSI_ERR_CUDA (launch failure).  Device-side findings (non-finite output,
  * column out of range) go to the workspace status word.
@@ -160,8 +164,9 @@ int chfsi_filter(const chfsi_matrix* H, const double* X, int64_t ldx, double* Y,
  * Same arguments and result as chfsi_filter minus ws/ws_bytes.  The scratch is a
  * 16 MiB array in the library's device memory (held by every GPU that loads the
  * library until the process exits).  Problems whose chfsi_filter_workspace_size
- * exceeds 16 MiB are rejected with CHFSI_ERR_NOMEM (FP64 schedule: about
- * 2 * N * round_up(n_cols, 8) * 8 bytes, e.g. N = 8000 with 64 columns fits).
+ * exceeds 16 MiB are rejected with CHFSI_ERR_NOMEM (FP64 schedule on a CSR
+ * operator: about 2 * N * round_up(min(n_cols, 512), 8) * 8 bytes, e.g. N = 8000
+ * with 64 columns fits).
  * The first call on each device looks up the array's device address (with that
  * device current); make that first call before any stream capture.  Nothing is
  * allocated.  All calls share the one array: calls that overlap on the GPU (other
@@ -191,6 +196,8 @@ int chfsi_filter_backward_workspace_size(const chfsi_matrix* H, int64_t n_cols, 
  * fact).  Forward iterates are kept only every ckpt_stride steps (as pairs
  * Y_{s-1}, Y_s; 0 selects ceil(sqrt(m))) and the rest are recomputed per segment.
  * dH_val may be NULL (then only dX).  Needs the CSR layout (CHFSI_CSR or CHFSI_HYBRID).
+ * More than 512 columns are swept in column slabs of 512 (dX's columns are
+ * independent; each slab adds its part of dH_val), so the workspace holds one slab.
  */
 int chfsi_filter_backward(const chfsi_matrix* H, const double* X, int64_t ldx,
                           const double* dY, int64_t lddy, double* dX, int64_t lddx,
