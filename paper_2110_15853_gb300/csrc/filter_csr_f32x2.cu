@@ -19,6 +19,8 @@
 // Column indices are range-checked while staging.  Intrinsics with explicit
 // rounding (__fmul_rn, __fadd_rn, __fsub_rn) keep the compiler from contracting
 // the error-free transformations into FMAs.
+#include <type_traits>
+
 #include "common.cuh"
 #include "kernels.cuh"
 #include "twofloat.cuh"
@@ -101,47 +103,52 @@ csr_step_f32x2_kernel(int64_t N, const int64_t* __restrict__ row_ptr, const int3
             }
             const int64_t j0 = jbase + (int64_t)lane * 2;
             // Register pipeline with two alternating buffers: the gathers of entry q+1
-            // are in flight while entry q is accumulated (no register copies).  Full
-            // chunks take a predicate-free path; a bad column index (unstaged rows only)
-            // becomes a zero entry on row 0.
+            // are in flight while entry q is accumulated (no register copies).  The
+            // common case -- a staged row slice and a full chunk -- is compiled as its own
+            // loop with no per-entry checks; otherwise a bad column index (unstaged rows
+            // only) becomes a zero entry on row 0 and chunks past n read zeros.
             const bool full = jbase + 64 * U <= n;
-            auto fetch = [&](int q, float4 (&y)[U], float2& h) {
-                int32_t cj = hc[q];
-                h = hv[q];
-                if (!staged && (cj < 0 || (int64_t)cj >= N)) { bad = true; cj = 0; h = make_float2(0.f, 0.f); }
-                const float2* src = Yc + (int64_t)cj * ldc + j0;
-                if (full) {
-#pragma unroll
-                    for (int u = 0; u < U; u++) y[u] = __ldg(reinterpret_cast<const float4*>(src + u * 64));
-                } else {
+            auto pass = [&](auto fast_tag) {
+                constexpr bool kFast = decltype(fast_tag)::value;
+                auto fetch = [&](int q, float4 (&y)[U], float2& h) {
+                    int32_t cj = hc[q];
+                    h = hv[q];
+                    if (!kFast && !staged && (cj < 0 || (int64_t)cj >= N)) {
+                        bad = true;
+                        cj = 0;
+                        h = make_float2(0.f, 0.f);
+                    }
+                    const float2* src = Yc + (int64_t)cj * ldc + j0;
 #pragma unroll
                     for (int u = 0; u < U; u++)
-                        y[u] = on[u] ? __ldg(reinterpret_cast<const float4*>(src + u * 64))
-                                     : make_float4(0.f, 0.f, 0.f, 0.f);
+                        y[u] = (kFast || on[u]) ? __ldg(reinterpret_cast<const float4*>(src + u * 64))
+                                                : make_float4(0.f, 0.f, 0.f, 0.f);
+                };
+                auto accumulate = [&](const float4 (&y)[U], float2 h) {
+                    const F2 hh2 = pk2(h.x, h.x), nhh2 = pk2(-h.x, -h.x), hl2 = pk2(h.y, h.y);
+#pragma unroll
+                    for (int u = 0; u < U; u++)
+                        df_madd2(hh2, nhh2, hl2, pk2(y[u].x, y[u].y), pk2(y[u].z, y[u].w), sh2[u], sl2[u]);
+                };
+                auto renorm = [&]() {
+#pragma unroll
+                    for (int u = 0; u < U; u++) fast_norm2(sh2[u], sl2[u]);
+                };
+                float4 ya[U], yb[U];
+                float2 ha = make_float2(0.f, 0.f), hb = make_float2(0.f, 0.f);
+                if (len > 0) fetch(0, ya, ha);
+                int q = 0;
+                for (; q + 1 < len; q += 2) {
+                    fetch(q + 1, yb, hb);
+                    accumulate(ya, ha);
+                    if (q + 2 < len) fetch(q + 2, ya, ha);
+                    accumulate(yb, hb);
+                    if ((q & (kRenorm - 1)) == kRenorm - 2) renorm();
                 }
+                if (q < len) accumulate(ya, ha);
             };
-            auto accumulate = [&](const float4 (&y)[U], float2 h) {
-                const F2 hh2 = pk2(h.x, h.x), nhh2 = pk2(-h.x, -h.x), hl2 = pk2(h.y, h.y);
-#pragma unroll
-                for (int u = 0; u < U; u++)
-                    df_madd2(hh2, nhh2, hl2, pk2(y[u].x, y[u].y), pk2(y[u].z, y[u].w), sh2[u], sl2[u]);
-            };
-            auto renorm = [&]() {
-#pragma unroll
-                for (int u = 0; u < U; u++) fast_norm2(sh2[u], sl2[u]);
-            };
-            float4 ya[U], yb[U];
-            float2 ha = make_float2(0.f, 0.f), hb = make_float2(0.f, 0.f);
-            if (len > 0) fetch(0, ya, ha);
-            int q = 0;
-            for (; q + 1 < len; q += 2) {
-                fetch(q + 1, yb, hb);
-                accumulate(ya, ha);
-                if (q + 2 < len) fetch(q + 2, ya, ha);
-                accumulate(yb, hb);
-                if ((q & (kRenorm - 1)) == kRenorm - 2) renorm();
-            }
-            if (q < len) accumulate(ya, ha);
+            if (staged && full) pass(std::true_type{});
+            else pass(std::false_type{});
 #pragma unroll
             for (int u = 0; u < U; u++) {
                 if (!on[u]) continue;
