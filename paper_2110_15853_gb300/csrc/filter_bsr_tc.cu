@@ -18,11 +18,13 @@
 // (block row, 128-state tile) with column tiles fastest (a block row's H blocks are
 // then shared through L2 by its tiles):
 //   warp 0, lane 0 : TMA producer of the MMA operands -- per neighbouring block, the
-//                    128B-swizzled tiles of Ysh^T and H_RC into a 6-stage ring;
+//                    128B-swizzled tiles of Ysh^T and H_RC into an 8-stage ring;
 //   warp 1         : owns the TMEM allocation (two 64-column FP32 accumulators);
 //                    lane 0 issues the MMAs into accumulator (item & 1);
-//   warp 2, lane 0 : TMA producer of each item's FP32 Y_cur / Y_prev epilogue tiles
-//                    (64 x 128), loaded as soon as the previous epilogue frees them;
+//   warp 2, lane 0 : TMA producer of each item's FP32 Y_cur / Y_prev epilogue tiles,
+//                    16 rows x 128 states at a time into a two-deep ring, so that
+//                    shared memory goes to the operand ring (whose bytes in flight
+//                    cover the operand latency);
 //   warps 3-6      : epilogue (warp w reads TMEM lanes 32*(w%4)..+31) of one item
 //                    while the MMAs of the next one run.
 // Every mbarrier wait is bounded (1 s on %globaltimer); on timeout the CTA flags
@@ -37,15 +39,17 @@ namespace chfsi {
 
 namespace {
 
-constexpr int kStages = 6;
+constexpr int kStages = 8;
 constexpr int kTileJ = 128;                       // states per work item (MMA M)
 constexpr int kBlk = 64;                          // block edge (MMA N and K per block)
 constexpr int kATile = kTileJ * kBlk * 2;         // 16 KB
 constexpr int kBTile = kBlk * kBlk * 2;           // 8 KB
 constexpr int kStageBytes = kATile + kBTile;      // 24 KB
-constexpr int kEpiTile = kBlk * kTileJ * 4;       // 32 KB: 64 rows x 128 states FP32
-constexpr int kEpiBuf = 2 * kEpiTile;             // Y_cur + Y_prev tiles of one item
-constexpr int kSmemBytes = kStages * kStageBytes + kEpiBuf + 1024;
+constexpr int kEpiRows = 16;                      // rows per epilogue chunk
+constexpr int kEpiChunks = kBlk / kEpiRows;       // chunks per item
+constexpr int kEpiTile = kEpiRows * kTileJ * 4;   // 8 KB: 16 rows x 128 states FP32
+constexpr int kEpiSlot = 2 * kEpiTile;            // Y_cur + Y_prev chunk
+constexpr int kSmemBytes = kStages * kStageBytes + 2 * kEpiSlot + 1024;
 constexpr int kThreads = 224;
 constexpr uint32_t kTmemCols = 128;               // two 64-column accumulators
 constexpr uint64_t kTimeoutNs = 1000000000ull;
@@ -121,8 +125,8 @@ bsr_tc_kernel(const __grid_constant__ CUtensorMap tmY, const __grid_constant__ C
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     unsigned char* stages = smem;                                   // kStages x (A | B), 1024-aligned
-    unsigned char* epi = smem + kStages * kStageBytes;              // Y_cur tile | Y_prev tile
-    __shared__ __align__(8) uint64_t full[kStages], empty[kStages], tfull[2], tempty[2], efull, eempty;
+    unsigned char* epi = smem + kStages * kStageBytes;              // 2 x (Y_cur chunk | Y_prev chunk)
+    __shared__ __align__(8) uint64_t full[kStages], empty[kStages], tfull[2], tempty[2], efull[2], eempty[2];
     __shared__ uint32_t tmem_slot;
     __shared__ int abort_flag;
 
@@ -139,8 +143,10 @@ bsr_tc_kernel(const __grid_constant__ CUtensorMap tmY, const __grid_constant__ C
             mbar_init(&tfull[b], 1);
             mbar_init(&tempty[b], 4);
         }
-        mbar_init(&efull, 1);
-        mbar_init(&eempty, 4);
+        for (int b = 0; b < 2; b++) {
+            mbar_init(&efull[b], 1);
+            mbar_init(&eempty[b], 4);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;");
         asm volatile("fence.proxy.async.shared::cta;");
         abort_flag = 0;
@@ -189,16 +195,27 @@ bsr_tc_kernel(const __grid_constant__ CUtensorMap tmY, const __grid_constant__ C
             mbar_wait(sa(&full[s]), (int)(last / kStages) & 1);
         }
     } else if (warp == 2 && lane == 0) {
-        // ---------------- TMA producer of the epilogue operand tiles
-        int items = 0;
-        for (int64_t item = blockIdx.x; item < total && !*abort_v; item += gridDim.x, items++) {
+        // ---------------- TMA producer of the epilogue operand chunks
+        // chunk g (= item count x kEpiChunks + chunk) goes to slot g & 1, its use g >> 1
+        int64_t g = 0;
+        for (int64_t item = blockIdx.x; item < total && !*abort_v; item += gridDim.x) {
             const int64_t R = item / ntiles, t = item % ntiles;
-            if (items >= 1 && !mbar_wait(sa(&eempty), (items - 1) & 1)) { *abort_v = 1; break; }
-            mbar_expect_tx(&efull, has_prev ? 2 * kEpiTile : kEpiTile);
-            tma_load_2d(sa(epi), &tmYc, (int)(t * kTileJ), (int)(R * kBlk), sa(&efull));
-            if (has_prev) tma_load_2d(sa(epi + kEpiTile), &tmYp, (int)(t * kTileJ), (int)(R * kBlk), sa(&efull));
+            bool ok = true;
+            for (int ch = 0; ch < kEpiChunks; ch++, g++) {
+                const int slot = (int)(g & 1);
+                const int64_t use = g >> 1;
+                if (use >= 1 && !mbar_wait(sa(&eempty[slot]), (int)((use - 1) & 1))) { ok = false; break; }
+                const uint32_t dst = sa(epi + slot * kEpiSlot);
+                const int row = (int)(R * kBlk + ch * kEpiRows);
+                mbar_expect_tx(&efull[slot], has_prev ? 2 * kEpiTile : kEpiTile);
+                tma_load_2d(dst, &tmYc, (int)(t * kTileJ), row, sa(&efull[slot]));
+                if (has_prev) tma_load_2d(dst + kEpiTile, &tmYp, (int)(t * kTileJ), row, sa(&efull[slot]));
+            }
+            if (!ok) { *abort_v = 1; break; }
         }
-        if (items > 0) mbar_wait(sa(&efull), (items - 1) & 1);
+        // wait (bounded) until the last copy into each slot has landed
+        for (int64_t last = g - 1; last >= 0 && last >= g - 2; last--)
+            mbar_wait(sa(&efull[last & 1]), (int)((last >> 1) & 1));
     } else if (warp == 1 && lane == 0) {
         // ---------------- MMA issuer
         int64_t sc = 0;
@@ -243,7 +260,8 @@ bsr_tc_kernel(const __grid_constant__ CUtensorMap tmY, const __grid_constant__ C
         for (int64_t item = blockIdx.x; item < total; item += gridDim.x, items++) {
             const int64_t R = item / ntiles, t = item % ntiles;
             const int b = items & 1, v = items >> 1;
-            const bool ok = !*abort_v && mbar_wait(sa(&tfull[b]), v & 1) && mbar_wait(sa(&efull), items & 1);
+            // the warp decides together (the TMEM loads below are warp-collective)
+            const bool ok = __all_sync(0xffffffffu, !*abort_v && mbar_wait(sa(&tfull[b]), v & 1));
             if (!ok) { *abort_v = 1; break; }
             asm volatile("tcgen05.fence::after_thread_sync;");
             int qb, qe;
@@ -251,12 +269,19 @@ bsr_tc_kernel(const __grid_constant__ CUtensorMap tmY, const __grid_constant__ C
             const bool has_acc = qe > qb;
             const int jl = quad * 32 + lane;                      // state within the tile
             const int64_t j = t * kTileJ + jl;
-            const float* ycs = reinterpret_cast<const float*>(epi);
-            const float* yps = ycs + kBlk * kTileJ;
             const int64_t row0 = R * kBlk;
             bool nonfinite = false;
+            bool chunks_ok = true;
 #pragma unroll 1
-            for (int cchunk = 0; cchunk < kBlk / 16; cchunk++) {
+            for (int cchunk = 0; cchunk < kEpiChunks; cchunk++) {
+                const int64_t g = (int64_t)items * kEpiChunks + cchunk;
+                const int slot = (int)(g & 1);
+                if (!__all_sync(0xffffffffu, mbar_wait(sa(&efull[slot]), (int)((g >> 1) & 1)))) {
+                    chunks_ok = false;
+                    break;
+                }
+                const float* ycs = reinterpret_cast<const float*>(epi + slot * kEpiSlot);
+                const float* yps = ycs + kEpiRows * kTileJ;
                 uint32_t r[16];
                 const uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(b * kBlk + cchunk * 16);
                 asm volatile(
@@ -267,38 +292,40 @@ bsr_tc_kernel(const __grid_constant__ CUtensorMap tmY, const __grid_constant__ C
                       "=r"(r[14]), "=r"(r[15])
                     : "r"(taddr));
                 asm volatile("tcgen05.wait::ld.sync.aligned;");
-                if (j >= n) continue;
-                float out[16];
+                if (j < n) {
+                    float out[16];
 #pragma unroll
-                for (int tt = 0; tt < 16; tt++) {
-                    const int rl = cchunk * 16 + tt;
-                    const float acc = has_acc ? __uint_as_float(r[tt]) : 0.0f;
-                    float val = alpha * fmaf(-c, ycs[rl * kTileJ + jl], acc);
-                    if (has_prev) val = fmaf(-beta, yps[rl * kTileJ + jl], val);
-                    nonfinite |= !isfinite(val);
-                    Yo[(row0 + rl) * ldo + j] = val;
-                    out[tt] = val;
-                }
-                // 16 consecutive rows of state j -> two 16-byte stores of the state-major copy
-                uint4 pk[2];
-                unsigned* pw = reinterpret_cast<unsigned*>(pk);
+                    for (int tt = 0; tt < 16; tt++) {
+                        const int rl = cchunk * 16 + tt;
+                        const float acc = has_acc ? __uint_as_float(r[tt]) : 0.0f;
+                        float val = alpha * fmaf(-c, ycs[tt * kTileJ + jl], acc);
+                        if (has_prev) val = fmaf(-beta, yps[tt * kTileJ + jl], val);
+                        nonfinite |= !isfinite(val);
+                        Yo[(row0 + rl) * ldo + j] = val;
+                        out[tt] = val;
+                    }
+                    // 16 consecutive rows of state j -> two 16-byte stores of the state-major copy
+                    uint4 pk[2];
+                    unsigned* pw = reinterpret_cast<unsigned*>(pk);
 #pragma unroll
-                for (int tt = 0; tt < 8; tt++) {
-                    __nv_bfloat162 h2 = __floats2bfloat162_rn(out[2 * tt], out[2 * tt + 1]);
-                    pw[tt] = *reinterpret_cast<unsigned*>(&h2);
+                    for (int tt = 0; tt < 8; tt++) {
+                        __nv_bfloat162 h2 = __floats2bfloat162_rn(out[2 * tt], out[2 * tt + 1]);
+                        pw[tt] = *reinterpret_cast<unsigned*>(&h2);
+                    }
+                    uint4* dst = reinterpret_cast<uint4*>(Ysh_out + (R * n + j) * kBlk + cchunk * 16);
+                    dst[0] = pk[0];
+                    dst[1] = pk[1];
                 }
-                uint4* dst = reinterpret_cast<uint4*>(Ysh_out + (R * n + j) * kBlk + cchunk * 16);
-                dst[0] = pk[0];
-                dst[1] = pk[1];
+                // release the chunk slot
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&eempty[slot]);
             }
+            if (!chunks_ok) { *abort_v = 1; break; }
             if (nonfinite) raise_status(status, DEV_NONFINITE);
-            // release accumulator b and the epilogue tiles
+            // release accumulator b
             asm volatile("tcgen05.fence::before_thread_sync;");
             __syncwarp();
-            if (lane == 0) {
-                mbar_arrive(&tempty[b]);
-                mbar_arrive(&eempty);
-            }
+            if (lane == 0) mbar_arrive(&tempty[b]);
         }
     }
 
@@ -368,7 +395,7 @@ int make_map(CUtensorMap* map, const void* base, int64_t cols, int64_t rows, int
     return r == CUDA_SUCCESS ? CHFSI_OK : CHFSI_ERR_CUDA;
 }
 
-// 2-D FP32 tensor map over a row-major [rows x ld] array, box [64 rows x 128 states],
+// 2-D FP32 tensor map over a row-major [rows x ld] array, box [16 rows x 128 states],
 // no swizzle (epilogue operand tiles; states beyond ld read as zero).
 int make_map_f32(CUtensorMap* map, const float* base, int64_t ld, int64_t rows) {
     EncodeTiledFn enc = encode_fn();
@@ -376,7 +403,7 @@ int make_map_f32(CUtensorMap* map, const float* base, int64_t ld, int64_t rows) 
     if ((reinterpret_cast<uintptr_t>(base) & 15u) || ((ld * 4) % 16)) return CHFSI_ERR_ARG;
     cuuint64_t dims[2] = {(cuuint64_t)ld, (cuuint64_t)rows};
     cuuint64_t strides[1] = {(cuuint64_t)ld * 4};
-    cuuint32_t box[2] = {(cuuint32_t)kTileJ, (cuuint32_t)kBlk};
+    cuuint32_t box[2] = {(cuuint32_t)kTileJ, (cuuint32_t)kEpiRows};
     cuuint32_t es[2] = {1, 1};
     CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides, box, es,
                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,

@@ -16,6 +16,8 @@
 // 32 * V * U columns.  Accumulation order over a row's entries is the stored order.
 // Every column index is range-checked while staging; a bad one is replaced by a
 // zero entry and reported in the status word, so no access leaves the buffers.
+#include <type_traits>
+
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -157,10 +159,11 @@ struct Gathered<float, __nv_bfloat16, V> {
 };
 
 // Resident CTAs per SM the register budget of a low-precision step is sized for: the
-// FP32 and BF16-operand steps are bound by gather latency, so they trade chunks per
-// pass (U) for resident warps.  (The FP64 step, bound by the FP64 pipe, has no bound.)
+// FP32 and BF16-operand steps are bound by gather latency, so they take fewer chunks
+// per pass (U) for more resident warps.  (The FP64 step, bound by the FP64 pipe, has
+// no bound.)
 template <typename TG, int U>
-constexpr int lp_min_blocks() { return std::is_same<TG, float>::value && U <= 2 ? 4 : 3; }
+constexpr int lp_min_blocks() { return 3; }
 
 template <typename TH>
 __device__ __forceinline__ void stage_entry(TH* sv, int32_t* sc, const TH* val, const int32_t* col,
@@ -234,35 +237,46 @@ csr_step_body(int64_t N, const int64_t* __restrict__ row_ptr, const int32_t* __r
             // Register pipeline with two alternating buffers: the gathers of entry q+1
             // are in flight while entry q is accumulated.  Full chunks take a
             // predicate-free path; a bad column index (unstaged rows only) becomes a
-            // zero entry on row 0.
+            // zero entry on row 0.  In the low-precision steps the common case (a
+            // staged slice and a full chunk) is compiled as its own loop with no
+            // per-entry checks; the FP64 step, bound by its pipe, keeps one loop.
             const bool full = jbase + 32 * V * U <= n;
             using G = Gathered<ACC, TG, V>;
-            auto fetch = [&](int q, G (&y)[U], ACC& h) {
-                int32_t cj = hc[q];
-                h = cvt<ACC>(hv[q]);
-                if (!staged && (cj < 0 || (int64_t)cj >= N)) { bad = true; cj = 0; h = (ACC)0; }
-                const TG* src = Yg + (int64_t)cj * ldg + j0;
+            auto pass = [&](auto fast_tag) {
+                constexpr bool kFast = decltype(fast_tag)::value;
+                auto fetch = [&](int q, G (&y)[U], ACC& h) {
+                    int32_t cj = hc[q];
+                    h = cvt<ACC>(hv[q]);
+                    if (!kFast && !staged && (cj < 0 || (int64_t)cj >= N)) { bad = true; cj = 0; h = (ACC)0; }
+                    const TG* src = Yg + (int64_t)cj * ldg + j0;
 #pragma unroll
-                for (int u = 0; u < U; u++) {
-                    if (full || on[u]) y[u].load(src + u * 32 * V);
-                    else y[u].zero();
+                    for (int u = 0; u < U; u++) {
+                        if (kFast || full || on[u]) y[u].load(src + u * 32 * V);
+                        else y[u].zero();
+                    }
+                };
+                auto accumulate = [&](const G (&y)[U], ACC h) {
+#pragma unroll
+                    for (int u = 0; u < U; u++) y[u].madd(h, acc[u]);
+                };
+                G ya[U], yb[U];
+                ACC ha = (ACC)0, hb = (ACC)0;
+                if (len > 0) fetch(0, ya, ha);
+                int q = 0;
+                for (; q + 1 < len; q += 2) {
+                    fetch(q + 1, yb, hb);
+                    accumulate(ya, ha);
+                    if (q + 2 < len) fetch(q + 2, ya, ha);
+                    accumulate(yb, hb);
                 }
+                if (q < len) accumulate(ya, ha);
             };
-            auto accumulate = [&](const G (&y)[U], ACC h) {
-#pragma unroll
-                for (int u = 0; u < U; u++) y[u].madd(h, acc[u]);
-            };
-            G ya[U], yb[U];
-            ACC ha = (ACC)0, hb = (ACC)0;
-            if (len > 0) fetch(0, ya, ha);
-            int q = 0;
-            for (; q + 1 < len; q += 2) {
-                fetch(q + 1, yb, hb);
-                accumulate(ya, ha);
-                if (q + 2 < len) fetch(q + 2, ya, ha);
-                accumulate(yb, hb);
+            if constexpr (std::is_same<ACC, double>::value) {
+                pass(std::false_type{});
+            } else {
+                if (staged && full) pass(std::true_type{});
+                else pass(std::false_type{});
             }
-            if (q < len) accumulate(ya, ha);
 #pragma unroll
             for (int u = 0; u < U; u++) {
                 if (!on[u]) continue;
