@@ -306,6 +306,54 @@ def test_column_slabs_and_views_of_wider_blocks(P, oracle_mod, schedule):
     assert bool(torch.all(Yw[:, n:] == 7.25))
 
 
+def _block_sparse_with_empty_block_row(seed=23):
+    """A 256 x 256 symmetric operator of 64 x 64 dense blocks on a 4 x 4 block
+    pattern whose block row (and column) 2 is empty: rows 128..191 hold no entry."""
+    rng = np.random.default_rng(seed)
+    pattern = np.array([[1, 1, 0, 1], [1, 1, 0, 0], [0, 0, 0, 0], [1, 0, 0, 1]], dtype=bool)
+    A = np.zeros((256, 256))
+    for I in range(4):
+        for J in range(I, 4):
+            if pattern[I, J]:
+                blk = rng.standard_normal((64, 64)) * (0.05 if I != J else 0.1)
+                if I == J:
+                    blk = 0.5 * (blk + blk.T) + np.diag(np.linspace(1.0, 3.0, 64))
+                A[64 * I:64 * I + 64, 64 * J:64 * J + 64] = blk
+                A[64 * J:64 * J + 64, 64 * I:64 * I + 64] = blk.T
+    brow_ptr, bcol, vals = [0], [], []
+    for I in range(4):
+        for J in range(4):
+            if pattern[I, J]:
+                bcol.append(J)
+                vals.append(A[64 * I:64 * I + 64, 64 * J:64 * J + 64].copy())
+        brow_ptr.append(len(bcol))
+    B = dict(brow_ptr=np.array(brow_ptr, dtype=np.int32), bcol=np.array(bcol, dtype=np.int32),
+             val=np.concatenate([v.ravel() for v in vals]))
+    from tests.util import dense_to_csr
+    return A, dense_to_csr(A, keep_zeros=False), B
+
+
+@pytest.mark.parametrize("layout,schedule,tol", [("csr", None, 1e-12), ("csr", "f32x2", 1e-12), ("csr", "f32", 2e-5),
+                                                 ("csr", "bf16", 5e-2), ("bsr", None, 1e-12), ("bsr", "bf16", 5e-2)])
+def test_empty_rows_and_block_rows(P, oracle_mod, layout, schedule, tol):
+    """Rows with no stored entry (and, in the blocked layout, a block row with no
+    block, so its tensor-core accumulator is never written) filter to
+    alpha (-c Y_k) - beta Y_{k-1}, as the oracle computes them."""
+    A, H, B = _block_sparse_with_empty_block_row()
+    assert np.all(np.diff(H["row_ptr"])[128:192] == 0)
+    n, m = 40, 5
+    X = np.linalg.qr(np.random.default_rng(3).standard_normal((256, n)))[0]
+    lam = np.linalg.eigvalsh(A)          # 64 zero eigenvalues from the empty rows, then ~1..3.8
+    a0, a, b = lam[0] - 0.01, lam[100], lam[-1] + 0.01
+    Yref = oracle_mod.filter(H, X, m, a, b, a0)
+    Hd = to_dev(P, H) if layout == "csr" else to_dev_bsr(P, B)
+    ws = P.Workspace(DEV)
+    sched = None if schedule is None else [schedule] * m
+    Y = P.filter(Hd, dev(X), m, a, b, a0, schedule=sched, workspace=ws).cpu().numpy()
+    assert P.read_status(ws) == 0
+    assert rel_fro(Y, Yref) <= tol
+
+
 def test_filter_f32x2_config_40cube_sampled_columns(P, oracle_mod):
     wl = W.workload("g40_w3_n1024_m20")
     H, X = make_case(wl.g, wl.w, wl.n, seed=wl.seed)
