@@ -302,9 +302,12 @@ def run_ours(args):
     if args.closure_only:
         Hd = P.CsrMatrix.from_arrays(H["row_ptr"], H["col"], H["val"], device=dev)
         Xd = torch.as_tensor(X).to(dev)
+        ws = P.Workspace(dev)
+        P.rayleigh_ritz(Hd, Xd, 2, precision=args.precision, workspace=ws)   # warm-up (workspace, solver setup)
+        torch.cuda.synchronize(dev)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        ritz, _ = P.rayleigh_ritz(Hd, Xd, 2, precision=args.precision)
+        ritz, _ = P.rayleigh_ritz(Hd, Xd, 2, precision=args.precision, workspace=ws)
         e1.record()
         torch.cuda.synchronize(dev)
         print(json.dumps({"closure_only": True, "workload": wl.name, "n": n, "precision": args.precision,
