@@ -79,6 +79,34 @@ def test_workspace_sizes_are_host_arithmetic(lib):
     assert lib.chfsi_filter_backward_workspace_size(ctypes.byref(desc), 64, 16, 0, ctypes.byref(sz)) == 0
 
 
+def test_workspace_is_sized_for_one_column_slab(lib):
+    """A CSR filter (and its adjoint) over more than 512 states runs in 512-state
+    column slabs, so its workspace does not grow with n beyond one slab; a BSR
+    operator keeps the full width (the tensor-core step's copy is block-major)."""
+    from paper_2110_15853_gb300 import _abi
+    desc = _csr_desc(1000, 5000)
+    sizes = {}
+    for n in (512, 513, 2000, 6000):
+        sz = ctypes.c_size_t()
+        assert lib.chfsi_filter_workspace_size(ctypes.byref(desc), n, 10, None, ctypes.byref(sz)) == 0
+        sizes[n] = sz.value
+    assert sizes[513] == sizes[2000] == sizes[6000] == sizes[512]
+    assert sizes[512] >= 2 * 1000 * 512 * 8
+    bw = []
+    for n in (512, 4096):
+        sz = ctypes.c_size_t()
+        assert lib.chfsi_filter_backward_workspace_size(ctypes.byref(desc), n, 16, 0, ctypes.byref(sz)) == 0
+        bw.append(sz.value)
+    assert bw[0] == bw[1]
+    b = _abi.chfsi_matrix()
+    b.kind = _abi.CHFSI_BSR
+    b.bsr = _abi.chfsi_bsr(16, 40, 64, 0x1000, 0x2000, 0x3000)    # N = 1024
+    s1, s2 = ctypes.c_size_t(), ctypes.c_size_t()
+    assert lib.chfsi_filter_workspace_size(ctypes.byref(b), 512, 10, None, ctypes.byref(s1)) == 0
+    assert lib.chfsi_filter_workspace_size(ctypes.byref(b), 2048, 10, None, ctypes.byref(s2)) == 0
+    assert s2.value >= 2 * 1024 * 2048 * 8 > s1.value
+
+
 def test_host_validation_rejects_before_queueing(lib):
     from paper_2110_15853_gb300 import _abi
     desc = _csr_desc()
