@@ -74,10 +74,15 @@ int64_t bsr_values(const chfsi_matrix* H) { return H->bsr.n_blocks * (int64_t)H-
 
 // Values of H converted for the low-precision steps (FP32 copy for CUDA-core
 // steps, BF16 blocks for tensor-core steps): size of the larger candidate.
+// Entries of the low-precision copy of H's values (a BSR copy is followed by one zero
+// block, the tensor-core step's stand-in for a block missing from a block-row pair).
 int64_t low_values(const chfsi_matrix* H) {
     int64_t v = 0;
     if (has_csr(H)) v = H->csr.nnz;
-    if (has_bsr(H) && bsr_values(H) > v) v = bsr_values(H);
+    if (has_bsr(H)) {
+        const int64_t b = bsr_values(H) + (int64_t)H->bsr.bdim * H->bsr.bdim;
+        if (b > v) v = b;
+    }
     return v;
 }
 

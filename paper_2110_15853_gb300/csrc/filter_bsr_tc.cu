@@ -5,26 +5,27 @@
 //
 //     Y_out[R] = alpha (sum_{(R,C)} H_RC Y_cur[C] - c Y_cur[R]) - beta Y_prev[R]
 //
-// computed transposed, so that both MMA operands are K-major: for a block row R
-// (64 grid points) and a tile of 128 states j,
-//     D[j][i] = sum_C sum_k Ysh^T[j][C*64 + k] * H_RC[i][k]      (M = 128, N = 64, K = 64/block)
-// where Ysh^T is the BF16 copy of Y_cur, stored block-major as [N/64][n][64] so that
-// the 128 x 64 operand tile of block C and a state tile is one contiguous 16 KB read
-// (row C*n + j of a 64-wide table holds Y_cur[C*64 .. C*64+63][j]).  The epilogue
+// computed transposed, so that both MMA operands are K-major.  A work item is a pair
+// of block rows (R0 = 2p, R1 = 2p + 1; 128 grid points) and a tile of 128 states j:
+//     D[j][i] = sum_C sum_k Ysh^T[j][C*64 + k] * [H_R0C; H_R1C][i][k]   (M = 128, N = 128, K = 64/block)
+// over the merged block columns C of the two rows (a block missing from one row is a
+// zero block).  Ysh^T is the BF16 copy of Y_cur, stored block-major as [N/64][n][64]
+// so that the 128 x 64 operand tile of block column C and a state tile is one
+// contiguous 16 KB read, shared by both rows of the pair.  Pairing the rows doubles
+// the work of every MMA instruction: with one 64-row block per MMA (N = 64) the single
+// issuing thread, not the tensor pipe or the memory, limited the step.  The epilogue
 // reads D from TMEM, applies the recurrence in FP32 against the FP32 iterates and
-// writes Y_out (FP32, row-major) plus its BF16 state-major copy for the next step.
+// writes Y_out (FP32, row-major) plus its BF16 block-major copy for the next step.
 //
-// Persistent, warp-specialised CTA (one per SM), looping over work items
-// (block row, 128-state tile) with column tiles fastest (a block row's H blocks are
-// then shared through L2 by its tiles):
-//   warp 0, lane 0 : TMA producer of the MMA operands -- per neighbouring block, the
-//                    128B-swizzled tiles of Ysh^T and H_RC into an 8-stage ring;
-//   warp 1         : owns the TMEM allocation (two 64-column FP32 accumulators);
+// Persistent, warp-specialised CTA (one per SM), looping over work items with the
+// state tiles fastest (a pair's H blocks are then shared through L2 by its tiles):
+//   warp 0, lane 0 : TMA producer of the MMA operands -- per merged block column, the
+//                    128B-swizzled Ysh^T tile and the two H blocks into a 6-stage ring,
+//                    with per-stage flags (first / last / empty item) for the issuer;
+//   warp 1         : owns the TMEM allocation (two 128-column FP32 accumulators);
 //                    lane 0 issues the MMAs into accumulator (item & 1);
 //   warp 2, lane 0 : TMA producer of each item's FP32 Y_cur / Y_prev epilogue tiles,
-//                    16 rows x 128 states at a time into a two-deep ring, so that
-//                    shared memory goes to the operand ring (whose bytes in flight
-//                    cover the operand latency);
+//                    16 rows x 128 states at a time into a two-deep ring;
 //   warps 3-6      : epilogue (warp w reads TMEM lanes 32*(w%4)..+31) of one item
 //                    while the MMAs of the next one run.
 // Every mbarrier wait is bounded (1 s on %globaltimer); on timeout the CTA flags
@@ -39,19 +40,22 @@ namespace chfsi {
 
 namespace {
 
-constexpr int kStages = 8;
+constexpr int kStages = 6;
 constexpr int kTileJ = 128;                       // states per work item (MMA M)
-constexpr int kBlk = 64;                          // block edge (MMA N and K per block)
+constexpr int kBlk = 64;                          // block edge (K per block; rows per block row)
+constexpr int kRowsN = 2 * kBlk;                  // rows per item: a block-row pair (MMA N)
 constexpr int kATile = kTileJ * kBlk * 2;         // 16 KB
-constexpr int kBTile = kBlk * kBlk * 2;           // 8 KB
-constexpr int kStageBytes = kATile + kBTile;      // 24 KB
+constexpr int kBTile = kRowsN * kBlk * 2;         // 16 KB: two H blocks
+constexpr int kStageBytes = kATile + kBTile;      // 32 KB
 constexpr int kEpiRows = 16;                      // rows per epilogue chunk
-constexpr int kEpiChunks = kBlk / kEpiRows;       // chunks per item
+constexpr int kEpiChunks = kRowsN / kEpiRows;     // chunks per item
 constexpr int kEpiTile = kEpiRows * kTileJ * 4;   // 8 KB: 16 rows x 128 states FP32
 constexpr int kEpiSlot = 2 * kEpiTile;            // Y_cur + Y_prev chunk
 constexpr int kSmemBytes = kStages * kStageBytes + 2 * kEpiSlot + 1024;
 constexpr int kThreads = 224;
-constexpr uint32_t kTmemCols = 128;               // two 64-column accumulators
+constexpr uint32_t kTmemCols = 2 * kRowsN;        // two 128-column accumulators
+// per-stage flags written by the operand producer for the MMA issuer
+constexpr int kFirst = 1, kLast = 2, kEmptyItem = 4;
 constexpr uint64_t kTimeoutNs = 1000000000ull;
 
 __device__ __forceinline__ uint32_t sa(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -92,8 +96,8 @@ __device__ __forceinline__ uint64_t desc_sw128(uint32_t addr) {
     return d;
 }
 
-// Instruction descriptor: kind::f16, BF16 x BF16 -> FP32, both K-major, M = 128, N = 64.
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kBlk >> 3) << 17) |
+// Instruction descriptor: kind::f16, BF16 x BF16 -> FP32, both K-major, M = 128, N = 128.
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kRowsN >> 3) << 17) |
                             ((uint32_t)(kTileJ >> 4) << 24);
 
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
@@ -121,17 +125,20 @@ bsr_tc_kernel(const __grid_constant__ CUtensorMap tmY, const __grid_constant__ C
               const __grid_constant__ CUtensorMap tmYc, const __grid_constant__ CUtensorMap tmYp, int has_prev,
               int64_t nbr, const int32_t* __restrict__ brow_ptr, const int32_t* __restrict__ bcol, int64_t nblocks,
               int64_t N, int64_t n, int64_t ntiles, float* __restrict__ Yo, int64_t ldo,
+              // the BF16 block table holds a zero block at index nblocks (the missing block of a pair)
               __nv_bfloat16* __restrict__ Ysh_out, float alpha, float c, float beta, unsigned* status) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     unsigned char* stages = smem;                                   // kStages x (A | B), 1024-aligned
     unsigned char* epi = smem + kStages * kStageBytes;              // 2 x (Y_cur chunk | Y_prev chunk)
     __shared__ __align__(8) uint64_t full[kStages], empty[kStages], tfull[2], tempty[2], efull[2], eempty[2];
+    __shared__ int stage_flags[kStages];
     __shared__ uint32_t tmem_slot;
     __shared__ int abort_flag;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t total = nbr * ntiles;
+    const int64_t npairs = (nbr + 1) / 2;
+    const int64_t total = npairs * ntiles;
     bool bad = false;
 
     if (threadIdx.x == 0) {
@@ -162,8 +169,9 @@ bsr_tc_kernel(const __grid_constant__ CUtensorMap tmY, const __grid_constant__ C
     const uint32_t tmem = tmem_slot;
     volatile int* abort_v = &abort_flag;
 
-    // block range of a block row, clamped to the stored blocks
+    // block range of a block row, clamped to the stored blocks (empty past the last row)
     auto blocks_of = [&](int64_t R, int& qb, int& qe) {
+        if (R >= nbr) { qb = qe = 0; return; }
         qb = brow_ptr[R];
         qe = brow_ptr[R + 1];
         if (qb < 0) { qb = 0; bad = true; }
@@ -173,21 +181,50 @@ bsr_tc_kernel(const __grid_constant__ CUtensorMap tmY, const __grid_constant__ C
 
     if (warp == 0 && lane == 0) {
         // ---------------- TMA producer of the MMA operands
-        int64_t sc = 0;                 // stage loads issued
+        int64_t sc = 0;                 // stages issued
+        // next stage: wait until the issuer has released it, then set its flags
+        auto acquire = [&](int flags) -> int {
+            const int s = (int)(sc % kStages), u = (int)(sc / kStages);
+            if (u >= 1 && !mbar_wait(sa(&empty[s]), (u - 1) & 1)) return -1;
+            stage_flags[s] = flags;
+            return s;
+        };
         for (int64_t item = blockIdx.x; item < total && !*abort_v; item += gridDim.x) {
-            const int64_t R = item / ntiles, t = item % ntiles;
-            int qb, qe;
-            blocks_of(R, qb, qe);
-            for (int q = qb; q < qe; q++, sc++) {
-                const int s = (int)(sc % kStages), u = (int)(sc / kStages);
-                if (u >= 1 && !mbar_wait(sa(&empty[s]), (u - 1) & 1)) { *abort_v = 1; break; }
-                int C = bcol[q];
+            const int64_t R0 = 2 * (item / ntiles), t = item % ntiles;
+            int a, ae, b, be;
+            blocks_of(R0, a, ae);
+            blocks_of(R0 + 1, b, be);
+            bool ok = true, first = true;
+            if (a == ae && b == be) {   // no block in either row: an empty stage tells the issuer
+                const int s = acquire(kFirst | kLast | kEmptyItem);
+                if (s < 0) { *abort_v = 1; break; }
+                mbar_arrive(&full[s]);
+                sc++;
+                continue;
+            }
+            // merge the two rows' block columns (each column of either row exactly once)
+            while (a < ae || b < be) {
+                const bool has_a = a < ae, has_b = b < be;
+                const int ca = has_a ? bcol[a] : 0, cb = has_b ? bcol[b] : 0;
+                const bool take_a = has_a && (!has_b || ca <= cb);
+                const bool take_b = has_b && (!has_a || cb <= ca);
+                int C = take_a ? ca : cb;
                 if (C < 0 || (int64_t)C >= nbr) { bad = true; C = 0; }   // zero-safe: still a valid tile
+                const int qa = take_a ? a : (int)nblocks, qb2 = take_b ? b : (int)nblocks;   // nblocks: zero block
+                if (take_a) a++;
+                if (take_b) b++;
+                const bool last = !(a < ae || b < be);
+                const int s = acquire((first ? kFirst : 0) | (last ? kLast : 0));
+                if (s < 0) { ok = false; break; }
+                first = false;
                 const uint32_t st = sa(stages + (size_t)s * kStageBytes);
                 mbar_expect_tx(&full[s], kStageBytes);
                 tma_load_2d(st, &tmY, 0, (int)(C * n + t * kTileJ), sa(&full[s]));
-                tma_load_2d(st + kATile, &tmH, 0, q * kBlk, sa(&full[s]));
+                tma_load_2d(st + kATile, &tmH, 0, qa * kBlk, sa(&full[s]));
+                tma_load_2d(st + kATile + kBTile / 2, &tmH, 0, qb2 * kBlk, sa(&full[s]));
+                sc++;
             }
+            if (!ok) { *abort_v = 1; break; }
         }
         // wait (bounded) until every copy this thread issued has landed
         for (int s = 0; s < kStages && s < sc; s++) {
@@ -199,14 +236,16 @@ bsr_tc_kernel(const __grid_constant__ CUtensorMap tmY, const __grid_constant__ C
         // chunk g (= item count x kEpiChunks + chunk) goes to slot g & 1, its use g >> 1
         int64_t g = 0;
         for (int64_t item = blockIdx.x; item < total && !*abort_v; item += gridDim.x) {
-            const int64_t R = item / ntiles, t = item % ntiles;
+            const int64_t R0 = 2 * (item / ntiles), t = item % ntiles;
             bool ok = true;
             for (int ch = 0; ch < kEpiChunks; ch++, g++) {
                 const int slot = (int)(g & 1);
                 const int64_t use = g >> 1;
                 if (use >= 1 && !mbar_wait(sa(&eempty[slot]), (int)((use - 1) & 1))) { ok = false; break; }
                 const uint32_t dst = sa(epi + slot * kEpiSlot);
-                const int row = (int)(R * kBlk + ch * kEpiRows);
+                int64_t row64 = R0 * kBlk + ch * kEpiRows;
+                if (row64 >= N) row64 = R0 * kBlk;   // second row of an odd last pair: not used
+                const int row = (int)row64;
                 mbar_expect_tx(&efull[slot], has_prev ? 2 * kEpiTile : kEpiTile);
                 tma_load_2d(dst, &tmYc, (int)(t * kTileJ), row, sa(&efull[slot]));
                 if (has_prev) tma_load_2d(dst + kEpiTile, &tmYp, (int)(t * kTileJ), row, sa(&efull[slot]));
@@ -221,31 +260,32 @@ bsr_tc_kernel(const __grid_constant__ CUtensorMap tmY, const __grid_constant__ C
         int64_t sc = 0;
         int items = 0;
         for (int64_t item = blockIdx.x; item < total && !*abort_v; item += gridDim.x, items++) {
-            const int64_t R = item / ntiles;
             const int b = items & 1, v = items >> 1;
             if (v >= 1 && !mbar_wait(sa(&tempty[b]), (v - 1) & 1)) { *abort_v = 1; break; }
             asm volatile("tcgen05.fence::after_thread_sync;");
-            const uint32_t acc_addr = tmem + (uint32_t)(b * kBlk);
-            int qb, qe;
-            blocks_of(R, qb, qe);
+            const uint32_t acc_addr = tmem + (uint32_t)(b * kRowsN);
             bool ok = true;
-            for (int q = qb; q < qe; q++, sc++) {
+            for (;; sc++) {
                 const int s = (int)(sc % kStages), u = (int)(sc / kStages);
                 if (!mbar_wait(sa(&full[s]), u & 1) || *abort_v) { *abort_v = 1; ok = false; break; }
                 asm volatile("tcgen05.fence::after_thread_sync;");
-                const uint32_t st = sa(stages + (size_t)s * kStageBytes);
-                const uint64_t da = desc_sw128(st), db = desc_sw128(st + kATile);
+                const int flags = stage_flags[s];
+                if (!(flags & kEmptyItem)) {
+                    const uint32_t st = sa(stages + (size_t)s * kStageBytes);
+                    const uint64_t da = desc_sw128(st), db = desc_sw128(st + kATile);
 #pragma unroll
-                for (int k = 0; k < kBlk / 16; k++) {
-                    const uint32_t accumulate = (q > qb || k > 0) ? 1u : 0u;
-                    asm volatile(
-                        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n"
-                        :: "r"(acc_addr), "l"(da + 2 * k), "l"(db + 2 * k), "r"(kIdesc), "r"(accumulate));
+                    for (int k = 0; k < kBlk / 16; k++) {
+                        const uint32_t accumulate = ((flags & kFirst) && k == 0) ? 0u : 1u;
+                        asm volatile(
+                            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n"
+                            :: "r"(acc_addr), "l"(da + 2 * k), "l"(db + 2 * k), "r"(kIdesc), "r"(accumulate));
+                    }
                 }
                 umma_commit(&empty[s]);
+                if (flags & kLast) { sc++; break; }
             }
-            umma_commit(&tfull[b]);   // accumulator b complete (also with zero blocks)
+            umma_commit(&tfull[b]);   // accumulator b complete (also for an empty item)
             if (!ok) { items++; break; }
         }
         // every MMA this thread issued has completed before TMEM is released
@@ -258,18 +298,19 @@ bsr_tc_kernel(const __grid_constant__ CUtensorMap tmY, const __grid_constant__ C
         const int quad = warp & 3;
         int items = 0;
         for (int64_t item = blockIdx.x; item < total; item += gridDim.x, items++) {
-            const int64_t R = item / ntiles, t = item % ntiles;
+            const int64_t R0 = 2 * (item / ntiles), t = item % ntiles;
             const int b = items & 1, v = items >> 1;
             // the warp decides together (the TMEM loads below are warp-collective)
             const bool ok = __all_sync(0xffffffffu, !*abort_v && mbar_wait(sa(&tfull[b]), v & 1));
             if (!ok) { *abort_v = 1; break; }
             asm volatile("tcgen05.fence::after_thread_sync;");
-            int qb, qe;
-            blocks_of(R, qb, qe);
-            const bool has_acc = qe > qb;
+            int qa, qae, qb, qbe;
+            blocks_of(R0, qa, qae);
+            blocks_of(R0 + 1, qb, qbe);
+            const bool has_acc = qae > qa || qbe > qb;            // else no MMA wrote the accumulator
             const int jl = quad * 32 + lane;                      // state within the tile
             const int64_t j = t * kTileJ + jl;
-            const int64_t row0 = R * kBlk;
+            const int64_t row0 = R0 * kBlk;
             bool nonfinite = false;
             bool chunks_ok = true;
 #pragma unroll 1
@@ -283,7 +324,7 @@ bsr_tc_kernel(const __grid_constant__ CUtensorMap tmY, const __grid_constant__ C
                 const float* ycs = reinterpret_cast<const float*>(epi + slot * kEpiSlot);
                 const float* yps = ycs + kEpiRows * kTileJ;
                 uint32_t r[16];
-                const uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(b * kBlk + cchunk * 16);
+                const uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(b * kRowsN + cchunk * 16);
                 asm volatile(
                     "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
                     "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
@@ -292,7 +333,7 @@ bsr_tc_kernel(const __grid_constant__ CUtensorMap tmY, const __grid_constant__ C
                       "=r"(r[14]), "=r"(r[15])
                     : "r"(taddr));
                 asm volatile("tcgen05.wait::ld.sync.aligned;");
-                if (j < n) {
+                if (j < n && row0 + cchunk * kEpiRows < N) {
                     float out[16];
 #pragma unroll
                     for (int tt = 0; tt < 16; tt++) {
@@ -312,7 +353,9 @@ bsr_tc_kernel(const __grid_constant__ CUtensorMap tmY, const __grid_constant__ C
                         __nv_bfloat162 h2 = __floats2bfloat162_rn(out[2 * tt], out[2 * tt + 1]);
                         pw[tt] = *reinterpret_cast<unsigned*>(&h2);
                     }
-                    uint4* dst = reinterpret_cast<uint4*>(Ysh_out + (R * n + j) * kBlk + cchunk * 16);
+                    const int64_t Rr = R0 + cchunk / (kBlk / kEpiRows);   // block row of this chunk
+                    uint4* dst = reinterpret_cast<uint4*>(Ysh_out + (Rr * n + j) * kBlk +
+                                                          (cchunk % (kBlk / kEpiRows)) * kEpiRows);
                     dst[0] = pk[0];
                     dst[1] = pk[1];
                 }
@@ -339,10 +382,12 @@ bsr_tc_kernel(const __grid_constant__ CUtensorMap tmY, const __grid_constant__ C
     if (bad) raise_status(status, DEV_PATTERN);
 }
 
-// BF16 copy of FP64 block values (rounded through FP32).
+// BF16 copy of FP64 block values (rounded through FP32), followed by one zero block
+// (the stand-in for a block missing from one row of a block-row pair).
 __global__ void blocks_to_bf16_kernel(const double* __restrict__ src, __nv_bfloat16* dst, int64_t count) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < count) dst[i] = __float2bfloat16_rn((float)src[i]);
+    else if (i < count + kBlk * kBlk) dst[i] = __float2bfloat16_rn(0.0f);
 }
 
 // Block-major BF16 copy of a row-major FP64 block:
@@ -427,7 +472,8 @@ int sm_count() {
 
 int bsr_values_to_bf16(const double* src, void* dst, int64_t count, cudaStream_t s) {
     if (count <= 0) return CHFSI_OK;
-    blocks_to_bf16_kernel<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(src, static_cast<__nv_bfloat16*>(dst),
+    const int64_t total = count + kBlk * kBlk;
+    blocks_to_bf16_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(src, static_cast<__nv_bfloat16*>(dst),
                                                                          count);
     CHFSI_LAUNCH_CHECK();
     return CHFSI_OK;
@@ -449,12 +495,12 @@ int bsr_step_tc(const BsrDev& h, int64_t n, const void* ysh_in, const float* Yc,
     if (n <= 0 || h.nbr <= 0) return CHFSI_OK;
     if (h.bdim != kBlk || h.val_t != Buf::BF16) return CHFSI_ERR_UNSUPPORTED;
     const int64_t N = h.nbr * kBlk;
-    if (h.nblocks * kBlk > INT32_MAX || N > INT32_MAX || n > INT32_MAX || h.nbr * n > INT32_MAX)
+    if ((h.nblocks + 1) * kBlk > INT32_MAX || N > INT32_MAX || n > INT32_MAX || h.nbr * n > INT32_MAX)
         return CHFSI_ERR_UNSUPPORTED;
     CUtensorMap tmY, tmH, tmYc, tmYp;
     int rc;
     if ((rc = make_map(&tmY, ysh_in, kBlk, h.nbr * n, kTileJ))) return rc;
-    if ((rc = make_map(&tmH, h.val, kBlk, h.nblocks * kBlk, kBlk))) return rc;
+    if ((rc = make_map(&tmH, h.val, kBlk, (h.nblocks + 1) * kBlk, kBlk))) return rc;   // + the zero block
     if ((rc = make_map_f32(&tmYc, Yc, ldc, N))) return rc;
     if (Yp) {
         if ((rc = make_map_f32(&tmYp, Yp, ldp, N))) return rc;
@@ -469,7 +515,7 @@ int bsr_step_tc(const BsrDev& h, int64_t n, const void* ysh_in, const float* Yc,
         attr[dev] = true;
     }
     const int64_t ntiles = (n + kTileJ - 1) / kTileJ;
-    const int64_t total = h.nbr * ntiles;
+    const int64_t total = (h.nbr + 1) / 2 * ntiles;
     const int sms = sm_count();
     if (sms <= 0) return CHFSI_ERR_CUDA;
     const unsigned grid = (unsigned)(total < sms ? total : sms);   // persistent: one CTA per SM
