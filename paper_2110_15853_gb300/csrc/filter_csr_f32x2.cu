@@ -6,9 +6,10 @@
 // (|lo| <= ulp(hi)/2, about 48 significant bits) and every operation done on the
 // FP32 pipe with error-free transformations: the exact product error of
 // hi*hi comes from one FMA (TwoProduct), sums use Knuth's TwoSum (Dekker 1971;
-// Knuth, TAOCP vol. 2, 4.2.2).  GB300 issues 64 FP32 operations per FP64 one,
-// so about 12 FP32 operations per multiply-add still run several times faster
-// than the FP64 DFMA pipe, at FP64-level accuracy for the filter.
+// Knuth, TAOCP vol. 2, 4.2.2).  GB300 runs 64 FP32 operations per FP64 one, so
+// the 12 FP32 operations of a two-float multiply-add (6 packed FP32x2 instructions
+// per state, two states per instruction) still run several times faster than the
+// FP64 DFMA pipe, at FP64-level accuracy for the filter.
 //
 // Layout and staging follow the FP64 CSR step: one CTA per 8 consecutive rows,
 // the CTA's CSR slice (hi/lo value pairs and column indices) staged once in
@@ -16,9 +17,9 @@
 // consecutive states, and the iterate blocks are in the pair-split layout (the 16
 // bytes of states 2t, 2t+1 hold {hi, hi', lo, lo'}), so one 16-byte load per
 // gathered row gives both register pairs of the packed FP32x2 multiply-add.
-// Column indices are range-checked while staging.  Intrinsics with explicit
-// rounding (__fmul_rn, __fadd_rn, __fsub_rn) keep the compiler from contracting
-// the error-free transformations into FMAs.
+// Column indices are range-checked while staging.  The packed instructions are
+// inline PTX with explicit rounding (add/sub/mul/fma.rn.f32x2), which the compiler
+// cannot contract, so the error-free transformations stay exact.
 #include <type_traits>
 
 #include "common.cuh"
