@@ -9,6 +9,8 @@
 // the first two levels, then reduce one sum), 6 shuffle-adds per four entries
 // instead of 20; every dH[p] is owned by one warp (no atomics) and the result is
 // reproducible.
+#include <type_traits>
+
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -120,7 +122,7 @@ constexpr int kRenorm = 8;  // renormalise the two-float accumulators every kRen
 // (even and odd states in the two lanes), four entries per pass as in sddmm_kernel, the
 // transposed shuffle tree on two-float sums, and one FP64 multiply-add into dH[p] per
 // entry (one warp per row, no atomics).
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 2)
 sddmm_f32x2_kernel(int64_t N, const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col, int64_t nnz,
                    int64_t n, const float2* __restrict__ Yb, int64_t ldb, const float2* __restrict__ Yp, int64_t ldp,
                    double alpha, double* __restrict__ dH) {
@@ -131,7 +133,7 @@ sddmm_f32x2_kernel(int64_t N, const int64_t* __restrict__ row_ptr, const int32_t
     if (b < 0) b = 0;
     if (e > nnz) e = nnz;
     const float2* yb = Yb + r * ldb;
-    const F2 minus1 = pk2(-1.f, -1.f);
+    constexpr unsigned long long kSigns = 0x8000000080000000ull;   // negates both lanes (ALU, not FMA)
     for (int64_t pb = b; pb < e; pb += kGroup) {
         const float2* yp[kGroup];
         bool ok[kGroup];
@@ -145,21 +147,30 @@ sddmm_f32x2_kernel(int64_t N, const int64_t* __restrict__ row_ptr, const int32_t
         F2 sh2[kGroup], sl2[kGroup];
 #pragma unroll
         for (int g = 0; g < kGroup; g++) sh2[g] = sl2[g] = 0ull;
-        int t = 0;
-        for (int64_t j = (int64_t)lane * 2; j < n; j += 64) {
-            const float4 x = __ldg(reinterpret_cast<const float4*>(yb + j));
-            const F2 xh2 = pk2(x.x, x.y), nxh2 = mul2(xh2, minus1), xl2 = pk2(x.z, x.w);
+        // A group of four valid entries (the common case) runs a loop without per-entry
+        // checks.
+        auto pass = [&](auto all_tag) {
+            constexpr bool kAll = decltype(all_tag)::value;
+            int t = 0;
+            for (int64_t j = (int64_t)lane * 2; j < n; j += 64) {
+                const float4 x = __ldg(reinterpret_cast<const float4*>(yb + j));
+                float4 y[kGroup];
 #pragma unroll
-            for (int g = 0; g < kGroup; g++) {
-                if (!ok[g]) continue;
-                const float4 y = __ldg(reinterpret_cast<const float4*>(yp[g] + j));
-                df_madd2(xh2, nxh2, xl2, pk2(y.x, y.y), pk2(y.z, y.w), sh2[g], sl2[g]);
-            }
-            if ((++t & (kRenorm - 1)) == 0) {
+                for (int g = 0; g < kGroup; g++)
+                    y[g] = (kAll || ok[g]) ? __ldg(reinterpret_cast<const float4*>(yp[g] + j))
+                                           : make_float4(0.f, 0.f, 0.f, 0.f);
+                const F2 xh2 = pk2(x.x, x.y), nxh2 = xh2 ^ kSigns, xl2 = pk2(x.z, x.w);
 #pragma unroll
-                for (int g = 0; g < kGroup; g++) fast_norm2(sh2[g], sl2[g]);
+                for (int g = 0; g < kGroup; g++)
+                    df_madd2(xh2, nxh2, xl2, pk2(y[g].x, y[g].y), pk2(y[g].z, y[g].w), sh2[g], sl2[g]);
+                if ((++t & (kRenorm - 1)) == 0) {
+#pragma unroll
+                    for (int g = 0; g < kGroup; g++) fast_norm2(sh2[g], sl2[g]);
+                }
             }
-        }
+        };
+        if (ok[0] && ok[1] && ok[2] && ok[3]) pass(std::true_type{});
+        else pass(std::false_type{});
         DF v[kGroup];
 #pragma unroll
         for (int g = 0; g < kGroup; g++) {
