@@ -126,7 +126,7 @@ csr_step_f32x2_kernel(int64_t N, const int64_t* __restrict__ row_ptr, const int3
                                                 : make_float4(0.f, 0.f, 0.f, 0.f);
                 };
                 auto accumulate = [&](const float4 (&y)[U], float2 h) {
-                    const F2 hh2 = pk2(h.x, h.x), nhh2 = pk2(-h.x, -h.x), hl2 = pk2(h.y, h.y);
+                    const F2 hh2 = pk2(h.x, h.x), nhh2 = hh2 ^ 0x8000000080000000ull, hl2 = pk2(h.y, h.y);
 #pragma unroll
                     for (int u = 0; u < U; u++)
                         df_madd2(hh2, nhh2, hl2, pk2(y[u].x, y[u].y), pk2(y[u].z, y[u].w), sh2[u], sl2[u]);
