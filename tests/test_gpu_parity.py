@@ -354,6 +354,48 @@ def test_empty_rows_and_block_rows(P, oracle_mod, layout, schedule, tol):
     assert rel_fro(Y, Yref) <= tol
 
 
+def _random_symmetric_csr(rng, N, density, long_rows=0, empty_rows=0):
+    """Random symmetric sparse operator: a random pattern of the given density plus a
+    diagonal, some rows made long (dense) and some emptied, values N(0, 1/nnz-row)."""
+    A = (rng.random((N, N)) < density).astype(float) * rng.standard_normal((N, N))
+    for r in rng.choice(N, size=long_rows, replace=False):
+        A[r, :] = rng.standard_normal(N)
+    A = np.triu(A) + np.triu(A, 1).T
+    A += np.diag(rng.uniform(1.0, 3.0, N))
+    for r in rng.choice(N, size=empty_rows, replace=False):
+        A[r, :] = 0.0
+        A[:, r] = 0.0
+    A /= max(1.0, np.abs(A).sum(axis=1).max() / 4.0)
+    from tests.util import dense_to_csr
+    return A, dense_to_csr(A, keep_zeros=False)
+
+
+@pytest.mark.parametrize("case", range(8))
+def test_random_operators_all_precisions(P, oracle_mod, case):
+    """Seeded random operators (random densities and sizes, a few dense rows that
+    overflow the staged slice, a few empty rows, odd and even state counts) through
+    every CSR arithmetic: FP64 and two-float to 1e-12, FP32 and BF16 operands to
+    their rounding tolerances."""
+    rng = np.random.default_rng(1000 + case)
+    N = int(rng.integers(40, 700))
+    A, H = _random_symmetric_csr(rng, N, float(rng.uniform(0.005, 0.1)), long_rows=int(rng.integers(0, 3)),
+                                 empty_rows=int(rng.integers(0, 3)))
+    n = int(rng.integers(1, 300))
+    m = int(rng.integers(1, 12))
+    X = rng.standard_normal((N, n)) / np.sqrt(N)
+    lam = np.linalg.eigvalsh(A)
+    a0, b = lam[0] - 0.05, lam[-1] + 0.05
+    a = lam[0] + (lam[-1] - lam[0]) * float(rng.uniform(0.2, 0.6))
+    Yref = oracle_mod.filter(H, X, m, a, b, a0)
+    Hd = to_dev(P, H)
+    ws = P.Workspace(DEV)
+    for sched, tol in ((None, 1e-12), ("f32x2", 1e-12), ("f32", 2e-5 * m), ("bf16", 5e-2)):
+        s_ = None if sched is None else [sched] * m
+        Y = P.filter(Hd, dev(X), m, a, b, a0, schedule=s_, workspace=ws).cpu().numpy()
+        assert P.read_status(ws) == 0, sched
+        assert rel_fro(Y, Yref) <= tol, (sched, N, n, m, rel_fro(Y, Yref))
+
+
 def test_filter_f32x2_config_40cube_sampled_columns(P, oracle_mod):
     wl = W.workload("g40_w3_n1024_m20")
     H, X = make_case(wl.g, wl.w, wl.n, seed=wl.seed)
