@@ -396,6 +396,32 @@ def test_random_operators_all_precisions(P, oracle_mod, case):
         assert rel_fro(Y, Yref) <= tol, (sched, N, n, m, rel_fro(Y, Yref))
 
 
+@pytest.mark.parametrize("case", range(4))
+def test_random_operators_closure_and_adjoint(P, oracle_mod, case):
+    """Seeded random operators through the closure (CholQR2 + Rayleigh-Ritz, FP64 and
+    two-float products) and the adjoint (FP64 and two-float sweeps) against the oracle."""
+    rng = np.random.default_rng(2000 + case)
+    N = int(rng.integers(80, 400))
+    A, H = _random_symmetric_csr(rng, N, float(rng.uniform(0.01, 0.08)), long_rows=1, empty_rows=0)
+    n = int(rng.integers(4, 60))
+    m = int(rng.integers(2, 9))
+    X = np.linalg.qr(rng.standard_normal((N, n)))[0]
+    lam = np.linalg.eigvalsh(A)
+    a0, b = lam[0] - 0.05, lam[-1] + 0.05
+    a = lam[0] + (lam[-1] - lam[0]) * 0.4
+    Y = oracle_mod.filter(H, X, m, a, b, a0)
+    Hd = to_dev(P, H)
+    for prec in ("f64", "f32x2"):
+        ritz, psi = P.rayleigh_ritz(Hd, dev(Y), cholqr_passes=2, precision=prec)
+        _check_ritz(oracle_mod, H, Y, ritz.cpu().numpy(), psi.cpu().numpy(), orth_tol=1e-11)
+    G = rng.standard_normal((N, n))
+    dX_ref, dH_ref = oracle_mod.filter_adjoint(H, X, m, a, b, a0, G)
+    for prec in ("f64", "f32x2"):
+        dX, dH = P.filter_backward(Hd, dev(X), dev(G), m, a, b, a0, precision=prec)
+        assert rel_fro(dX.cpu().numpy(), dX_ref) <= 1e-10, prec
+        assert rel_fro(dH.cpu().numpy(), dH_ref) <= 1e-10, prec
+
+
 def test_filter_f32x2_config_40cube_sampled_columns(P, oracle_mod):
     wl = W.workload("g40_w3_n1024_m20")
     H, X = make_case(wl.g, wl.w, wl.n, seed=wl.seed)
