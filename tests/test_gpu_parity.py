@@ -422,6 +422,57 @@ def test_random_operators_closure_and_adjoint(P, oracle_mod, case):
         assert rel_fro(dH.cpu().numpy(), dH_ref) <= 1e-10, prec
 
 
+@pytest.mark.parametrize("case", range(4))
+def test_random_block_operators_bsr_and_tensor_cores(P, oracle_mod, case):
+    """Seeded random symmetric block patterns (odd and even block-row counts, empty
+    block rows possible, unsorted block columns) of dense 64 x 64 blocks: the FP64 BSR
+    step to 1e-12 and the tensor-core BF16 step (block-row pairs, zero block for a
+    missing partner) to the BF16 tolerance, both against the oracle on the same H."""
+    rng = np.random.default_rng(3000 + case)
+    nbr = int(rng.integers(1, 10))
+    pat = rng.random((nbr, nbr)) < float(rng.uniform(0.15, 0.6))
+    pat = np.triu(pat) | np.triu(pat).T
+    np.fill_diagonal(pat, rng.random(nbr) < 0.85)
+    N = 64 * nbr
+    A = np.zeros((N, N))
+    for I in range(nbr):
+        for J in range(I, nbr):
+            if pat[I, J]:
+                blk = rng.standard_normal((64, 64)) * 0.05
+                if I == J:
+                    blk = 0.5 * (blk + blk.T) + np.diag(rng.uniform(1.0, 3.0, 64))
+                A[64 * I:64 * I + 64, 64 * J:64 * J + 64] = blk
+                A[64 * J:64 * J + 64, 64 * I:64 * I + 64] = blk.T
+    brow_ptr, bcol, vals = [0], [], []
+    for I in range(nbr):
+        cols = [J for J in range(nbr) if pat[I, J]]
+        rng.shuffle(cols)
+        for J in cols:
+            bcol.append(J)
+            vals.append(A[64 * I:64 * I + 64, 64 * J:64 * J + 64].copy())
+        brow_ptr.append(len(bcol))
+    if not bcol:
+        pytest.skip("empty operator")
+    B = dict(brow_ptr=np.array(brow_ptr, dtype=np.int32), bcol=np.array(bcol, dtype=np.int32),
+             val=np.concatenate([v.ravel() for v in vals]))
+    from tests.util import dense_to_csr
+    H = dense_to_csr(A, keep_zeros=False)
+    n = int(rng.integers(1, 300))
+    m = int(rng.integers(1, 8))
+    X = rng.standard_normal((N, n)) / np.sqrt(N)
+    lam = np.linalg.eigvalsh(A)
+    a0, b = lam[0] - 0.05, lam[-1] + 0.05
+    a = lam[0] + (lam[-1] - lam[0]) * 0.4
+    Yref = oracle_mod.filter(H, X, m, a, b, a0)
+    Bd = to_dev_bsr(P, B)
+    ws = P.Workspace(DEV)
+    for sched, tol in ((None, 1e-12), ("bf16", 5e-2)):
+        s_ = None if sched is None else [sched] * m
+        Y = P.filter(Bd, dev(X), m, a, b, a0, schedule=s_, workspace=ws).cpu().numpy()
+        assert P.read_status(ws) == 0, sched
+        assert rel_fro(Y, Yref) <= tol, (sched, nbr, n, m, rel_fro(Y, Yref))
+
+
 def test_filter_f32x2_config_40cube_sampled_columns(P, oracle_mod):
     wl = W.workload("g40_w3_n1024_m20")
     H, X = make_case(wl.g, wl.w, wl.n, seed=wl.seed)
