@@ -473,6 +473,25 @@ def test_random_block_operators_bsr_and_tensor_cores(P, oracle_mod, case):
         assert rel_fro(Y, Yref) <= tol, (sched, nbr, n, m, rel_fro(Y, Yref))
 
 
+@pytest.mark.parametrize("case", range(4))
+def test_random_operators_lanczos_bounds(P, oracle_mod, case):
+    """Seeded random operators (with empty rows: the spectrum then contains 0) through
+    the GPU Lanczos bounds against the oracle's, and both bracket the spectrum."""
+    rng = np.random.default_rng(4000 + case)
+    N = int(rng.integers(60, 500))
+    A, H = _random_symmetric_csr(rng, N, float(rng.uniform(0.01, 0.08)), long_rows=1,
+                                 empty_rows=int(rng.integers(0, 3)))
+    steps = int(rng.integers(5, 21))
+    n_want = int(rng.integers(1, N // 4))
+    v0 = rng.standard_normal(N)
+    ra, rb, ra0 = oracle_mod.lanczos_bounds(H, v0, steps, n_want)
+    a, b, a0 = P.lanczos_bounds(to_dev(P, H), dev(v0), steps, n_want)
+    for x, y in ((a, ra), (b, rb), (a0, ra0)):
+        assert abs(x - y) <= 1e-10 * max(1.0, abs(y))
+    lam = np.linalg.eigvalsh(A)
+    assert b >= lam[-1] - 1e-12 and a0 >= lam[0] - 1e-12 and a0 < a < b
+
+
 def test_filter_f32x2_config_40cube_sampled_columns(P, oracle_mod):
     wl = W.workload("g40_w3_n1024_m20")
     H, X = make_case(wl.g, wl.w, wl.n, seed=wl.seed)
