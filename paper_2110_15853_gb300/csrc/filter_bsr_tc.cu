@@ -6,26 +6,29 @@
 //     Y_out[R] = alpha (sum_{(R,C)} H_RC Y_cur[C] - c Y_cur[R]) - beta Y_prev[R]
 //
 // computed transposed, so that both MMA operands are K-major.  A work item is a pair
-// of block rows (R0 = 2p, R1 = 2p + 1; 128 grid points) and a tile of 128 states j:
-//     D[j][i] = sum_C sum_k Ysh^T[j][C*64 + k] * [H_R0C; H_R1C][i][k]   (M = 128, N = 128, K = 64/block)
+// of block rows (R0 = 2p, R1 = 2p + 1; 128 grid points) and a span of 256 states, two
+// tiles of 128 states j:
+//     D_u[j][i] = sum_C sum_k Ysh^T[j][C*64 + k] * [H_R0C; H_R1C][i][k]   (M = 128, N = 128, K = 64/block)
 // over the merged block columns C of the two rows (a block missing from one row is a
 // zero block).  Ysh^T is the BF16 copy of Y_cur, stored block-major as [N/64][n][64]
 // so that the 128 x 64 operand tile of block column C and a state tile is one
-// contiguous 16 KB read, shared by both rows of the pair.  Pairing the rows doubles
-// the work of every MMA instruction: with one 64-row block per MMA (N = 64) the single
-// issuing thread, not the tensor pipe or the memory, limited the step.  The epilogue
-// reads D from TMEM, applies the recurrence in FP32 against the FP32 iterates and
-// writes Y_out (FP32, row-major) plus its BF16 block-major copy for the next step.
+// contiguous 16 KB read.  Pairing the rows doubles the work of every MMA instruction
+// (with one 64-row block per MMA the single issuing thread limited the step), and the
+// two state tiles of an item share each stage's pair of H blocks, so that a stage
+// moves 48 KB into shared memory for the work that took 64 KB in two stages of one
+// tile.  The epilogue reads D from TMEM, applies the recurrence in FP32 against the
+// FP32 iterates and writes Y_out (FP32, row-major) plus its BF16 block-major copy for
+// the next step.
 //
 // Persistent, warp-specialised CTA (one per SM), looping over work items with the
-// state tiles fastest (a pair's H blocks are then shared through L2 by its tiles):
+// state spans fastest (a pair's H blocks are then shared through L2 by its spans):
 //   warp 0, lane 0 : TMA producer of the MMA operands -- per merged block column, the
-//                    128B-swizzled Ysh^T tile and the two H blocks into a 6-stage ring,
-//                    with per-stage flags (first / last / empty item) for the issuer;
-//   warp 1         : owns the TMEM allocation (two 128-column FP32 accumulators);
-//                    lane 0 issues the MMAs into accumulator (item & 1);
+//                    two 128B-swizzled Ysh^T tiles and the two H blocks into a 4-stage
+//                    ring, with per-stage flags (first / last / empty item) for the issuer;
+//   warp 1         : owns the TMEM allocation (all 512 columns: two items of two
+//                    128-column FP32 accumulators); lane 0 issues the MMAs;
 //   warp 2, lane 0 : TMA producer of each item's FP32 Y_cur / Y_prev epilogue tiles,
-//                    16 rows x 128 states at a time into a two-deep ring;
+//                    8 rows x 256 states at a time into a two-deep ring;
 //   warps 3-6      : epilogue (warp w reads TMEM lanes 32*(w%4)..+31) of one item
 //                    while the MMAs of the next one run.
 // Every mbarrier wait is bounded (1 s on %globaltimer); on timeout the CTA flags
@@ -45,20 +48,29 @@ namespace {
 // 1024 states (0.345 against 0.333 ms per step): 54 merged block columns per quad
 // carry 50% zero blocks and the ring holds only 4 of its 48 KB stages.
 constexpr int kRowsPerItem = 2;
-constexpr int kTileJ = 128;                       // states per work item (MMA M)
+// State tiles per work item: the tiles of an item share every stage's H blocks, so a
+// stage carries kTiles operand tiles and one pair of H blocks.  Two tiles (4 stages of
+// 48 KB, TMEM full) measured 0.277 ms per step at 40^3 with 1024 states against 0.333
+// ms for one (6 stages of 32 KB).
+constexpr int kTiles = 2;
+constexpr int kTileJ = 128;                       // states per MMA (M)
+constexpr int kItemJ = kTiles * kTileJ;           // states per work item
 constexpr int kBlk = 64;                          // block edge (K per block; rows per block row)
 constexpr int kRowsN = kRowsPerItem * kBlk;       // rows per item (MMA N)
 constexpr int kATile = kTileJ * kBlk * 2;         // 16 KB
 constexpr int kBTile = kRowsN * kBlk * 2;         // one H block per row of the item
-constexpr int kStageBytes = kATile + kBTile;
+constexpr int kStageBytes = kTiles * kATile + kBTile;
 constexpr int kStages = (192 * 1024) / kStageBytes;
-constexpr int kEpiRows = 16;                      // rows per epilogue chunk
+constexpr int kEpiRows = kTiles == 1 ? 16 : 8;    // rows per epilogue chunk
 constexpr int kEpiChunks = kRowsN / kEpiRows;     // chunks per item
-constexpr int kEpiTile = kEpiRows * kTileJ * 4;   // 8 KB: 16 rows x 128 states FP32
+constexpr int kEpiTile = kEpiRows * kItemJ * 4;   // 8 KB: kEpiRows rows x kItemJ states FP32
 constexpr int kEpiSlot = 2 * kEpiTile;            // Y_cur + Y_prev chunk
 constexpr int kSmemBytes = kStages * kStageBytes + 2 * kEpiSlot + 1024;
 constexpr int kThreads = 224;
-constexpr uint32_t kTmemCols = 2 * kRowsN;        // two accumulators of kRowsN columns
+constexpr uint32_t kAccCols = kTiles * kRowsN;    // TMEM columns of one item's accumulators
+constexpr uint32_t kTmemCols = 2 * kAccCols;      // two items in flight
+static_assert(kTmemCols <= 512 && kEpiRows % 8 == 0 && kBlk % kEpiRows == 0, "tile shape");
+static_assert(kSmemBytes + 1024 <= 227 * 1024, "shared memory per CTA (with the static barriers)");
 // per-stage flags written by the operand producer for the MMA issuer
 constexpr int kFirst = 1, kLast = 2, kEmptyItem = 4;
 constexpr uint64_t kTimeoutNs = 1000000000ull;
@@ -125,11 +137,30 @@ __device__ __forceinline__ void umma_commit(uint64_t* b) {
                  : "memory");
 }
 
+// kEpiRows consecutive accumulator columns of this warp's 32 TMEM lanes (one per lane).
+__device__ __forceinline__ void tmem_ld_chunk(uint32_t taddr, uint32_t (&r)[kEpiRows]) {
+    static_assert(kEpiRows == 8 || kEpiRows == 16, "epilogue chunk of 8 or 16 rows");
+    if constexpr (kEpiRows == 16) {
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+            "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+              "=r"(r[15])
+            : "r"(taddr));
+    } else {
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                     : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                       "=r"(r[7])
+                     : "r"(taddr));
+    }
+}
+
 __global__ void __launch_bounds__(kThreads, 1)
 bsr_tc_kernel(const __grid_constant__ CUtensorMap tmY, const __grid_constant__ CUtensorMap tmH,
               const __grid_constant__ CUtensorMap tmYc, const __grid_constant__ CUtensorMap tmYp, int has_prev,
               int64_t nbr, const int32_t* __restrict__ brow_ptr, const int32_t* __restrict__ bcol, int64_t nblocks,
-              int64_t N, int64_t n, int64_t ntiles, float* __restrict__ Yo, int64_t ldo,
+              int64_t N, int64_t n, int64_t nspans, float* __restrict__ Yo, int64_t ldo,
               // the BF16 block table holds a zero block at index nblocks (the missing block of a pair)
               __nv_bfloat16* __restrict__ Ysh_out, float alpha, float c, float beta, unsigned* status) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -143,8 +174,13 @@ bsr_tc_kernel(const __grid_constant__ CUtensorMap tmY, const __grid_constant__ C
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t ngroups = (nbr + kRowsPerItem - 1) / kRowsPerItem;
-    const int64_t total = ngroups * ntiles;
+    const int64_t total = ngroups * nspans;   // work items: (block-row group, span of kItemJ states)
     bool bad = false;
+    // state tiles of span sp that hold states < n (the last span may hold fewer than kTiles)
+    auto tiles_of = [&](int64_t sp) -> int {
+        const int64_t left = (n - sp * kItemJ + kTileJ - 1) / kTileJ;
+        return left < kTiles ? (int)left : kTiles;
+    };
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; s++) {
@@ -195,7 +231,8 @@ bsr_tc_kernel(const __grid_constant__ CUtensorMap tmY, const __grid_constant__ C
             return s;
         };
         for (int64_t item = blockIdx.x; item < total && !*abort_v; item += gridDim.x) {
-            const int64_t R0 = kRowsPerItem * (item / ntiles), t = item % ntiles;
+            const int64_t R0 = kRowsPerItem * (item / nspans), sp = item % nspans;
+            const int nt = tiles_of(sp);
             int pos[kRowsPerItem], end[kRowsPerItem];
             bool any = false;
 #pragma unroll
@@ -231,11 +268,12 @@ bsr_tc_kernel(const __grid_constant__ CUtensorMap tmY, const __grid_constant__ C
                 if (s < 0) { ok = false; break; }
                 first = false;
                 const uint32_t st = sa(stages + (size_t)s * kStageBytes);
-                mbar_expect_tx(&full[s], kStageBytes);
-                tma_load_2d(st, &tmY, 0, (int)(C * n + t * kTileJ), sa(&full[s]));
+                mbar_expect_tx(&full[s], nt * kATile + kBTile);
+                for (int u = 0; u < nt; u++)
+                    tma_load_2d(st + u * kATile, &tmY, 0, (int)(C * n + sp * kItemJ + u * kTileJ), sa(&full[s]));
 #pragma unroll
                 for (int r = 0; r < kRowsPerItem; r++)
-                    tma_load_2d(st + kATile + r * (kBlk * kBlk * 2), &tmH, 0, q[r] * kBlk, sa(&full[s]));
+                    tma_load_2d(st + kTiles * kATile + r * (kBlk * kBlk * 2), &tmH, 0, q[r] * kBlk, sa(&full[s]));
                 sc++;
                 if (!more) break;
             }
@@ -251,7 +289,7 @@ bsr_tc_kernel(const __grid_constant__ CUtensorMap tmY, const __grid_constant__ C
         // chunk g (= item count x kEpiChunks + chunk) goes to slot g & 1, its use g >> 1
         int64_t g = 0;
         for (int64_t item = blockIdx.x; item < total && !*abort_v; item += gridDim.x) {
-            const int64_t R0 = kRowsPerItem * (item / ntiles), t = item % ntiles;
+            const int64_t R0 = kRowsPerItem * (item / nspans), sp = item % nspans;
             bool ok = true;
             for (int ch = 0; ch < kEpiChunks; ch++, g++) {
                 const int slot = (int)(g & 1);
@@ -262,8 +300,8 @@ bsr_tc_kernel(const __grid_constant__ CUtensorMap tmY, const __grid_constant__ C
                 if (row64 >= N) row64 = R0 * kBlk;   // rows past the last block row: not used
                 const int row = (int)row64;
                 mbar_expect_tx(&efull[slot], has_prev ? 2 * kEpiTile : kEpiTile);
-                tma_load_2d(dst, &tmYc, (int)(t * kTileJ), row, sa(&efull[slot]));
-                if (has_prev) tma_load_2d(dst + kEpiTile, &tmYp, (int)(t * kTileJ), row, sa(&efull[slot]));
+                tma_load_2d(dst, &tmYc, (int)(sp * kItemJ), row, sa(&efull[slot]));
+                if (has_prev) tma_load_2d(dst + kEpiTile, &tmYp, (int)(sp * kItemJ), row, sa(&efull[slot]));
             }
             if (!ok) { *abort_v = 1; break; }
         }
@@ -278,7 +316,8 @@ bsr_tc_kernel(const __grid_constant__ CUtensorMap tmY, const __grid_constant__ C
             const int b = items & 1, v = items >> 1;
             if (v >= 1 && !mbar_wait(sa(&tempty[b]), (v - 1) & 1)) { *abort_v = 1; break; }
             asm volatile("tcgen05.fence::after_thread_sync;");
-            const uint32_t acc_addr = tmem + (uint32_t)(b * kRowsN);
+            const uint32_t acc_addr = tmem + (uint32_t)(b * kAccCols);   // tile u at + u * kRowsN
+            const int nt = tiles_of(item % nspans);
             bool ok = true;
             for (;; sc++) {
                 const int s = (int)(sc % kStages), u = (int)(sc / kStages);
@@ -287,14 +326,20 @@ bsr_tc_kernel(const __grid_constant__ CUtensorMap tmY, const __grid_constant__ C
                 const int flags = stage_flags[s];
                 if (!(flags & kEmptyItem)) {
                     const uint32_t st = sa(stages + (size_t)s * kStageBytes);
-                    const uint64_t da = desc_sw128(st), db = desc_sw128(st + kATile);
+                    const uint64_t db = desc_sw128(st + kTiles * kATile);
 #pragma unroll
-                    for (int k = 0; k < kBlk / 16; k++) {
-                        const uint32_t accumulate = ((flags & kFirst) && k == 0) ? 0u : 1u;
-                        asm volatile(
-                            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n"
-                            :: "r"(acc_addr), "l"(da + 2 * k), "l"(db + 2 * k), "r"(kIdesc), "r"(accumulate));
+                    for (int u = 0; u < kTiles; u++) {
+                        if (u >= nt) break;
+                        const uint64_t da = desc_sw128(st + u * kATile);
+#pragma unroll
+                        for (int k = 0; k < kBlk / 16; k++) {
+                            const uint32_t accumulate = ((flags & kFirst) && k == 0) ? 0u : 1u;
+                            asm volatile(
+                                "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n"
+                                :: "r"(acc_addr + (uint32_t)(u * kRowsN)), "l"(da + 2 * k), "l"(db + 2 * k),
+                                   "r"(kIdesc), "r"(accumulate));
+                        }
                     }
                 }
                 umma_commit(&empty[s]);
@@ -313,7 +358,7 @@ bsr_tc_kernel(const __grid_constant__ CUtensorMap tmY, const __grid_constant__ C
         const int quad = warp & 3;
         int items = 0;
         for (int64_t item = blockIdx.x; item < total; item += gridDim.x, items++) {
-            const int64_t R0 = kRowsPerItem * (item / ntiles), t = item % ntiles;
+            const int64_t R0 = kRowsPerItem * (item / nspans), sp = item % nspans;
             const int b = items & 1, v = items >> 1;
             // the warp decides together (the TMEM loads below are warp-collective)
             const bool ok = __all_sync(0xffffffffu, !*abort_v && mbar_wait(sa(&tfull[b]), v & 1));
@@ -325,8 +370,7 @@ bsr_tc_kernel(const __grid_constant__ CUtensorMap tmY, const __grid_constant__ C
                 blocks_of(R0 + r, qb, qe);
                 has_acc |= qe > qb;
             }
-            const int jl = quad * 32 + lane;                      // state within the tile
-            const int64_t j = t * kTileJ + jl;
+            const int jl = quad * 32 + lane;                      // state within each tile
             const int64_t row0 = R0 * kBlk;
             bool nonfinite = false;
             bool chunks_ok = true;
@@ -338,43 +382,42 @@ bsr_tc_kernel(const __grid_constant__ CUtensorMap tmY, const __grid_constant__ C
                     chunks_ok = false;
                     break;
                 }
-                const float* ycs = reinterpret_cast<const float*>(epi + slot * kEpiSlot);
-                const float* yps = ycs + kEpiRows * kTileJ;
-                uint32_t r[16];
-                const uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(b * kRowsN + cchunk * 16);
-                asm volatile(
-                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
-                    "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-                    : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-                      "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-                      "=r"(r[14]), "=r"(r[15])
-                    : "r"(taddr));
-                asm volatile("tcgen05.wait::ld.sync.aligned;");
-                if (j < n && row0 + cchunk * kEpiRows < N) {
-                    float out[16];
+                const float* ycs = reinterpret_cast<const float*>(epi + slot * kEpiSlot);   // [kEpiRows][kItemJ]
+                const float* yps = ycs + kEpiRows * kItemJ;
+                uint32_t r[kTiles][kEpiRows];
+                const uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(b * kAccCols + cchunk * kEpiRows);
 #pragma unroll
-                    for (int tt = 0; tt < 16; tt++) {
-                        const int rl = cchunk * 16 + tt;
-                        const float acc = has_acc ? __uint_as_float(r[tt]) : 0.0f;
-                        float val = alpha * fmaf(-c, ycs[tt * kTileJ + jl], acc);
-                        if (has_prev) val = fmaf(-beta, yps[tt * kTileJ + jl], val);
+                for (int u = 0; u < kTiles; u++) tmem_ld_chunk(taddr + (uint32_t)(u * kRowsN), r[u]);
+                asm volatile("tcgen05.wait::ld.sync.aligned;");
+                const int64_t rowc = row0 + cchunk * kEpiRows;    // first row of the chunk
+                const int64_t Rr = R0 + cchunk / (kBlk / kEpiRows);   // its block row
+#pragma unroll
+                for (int u = 0; u < kTiles; u++) {
+                    const int64_t j = sp * kItemJ + u * kTileJ + jl;
+                    if (j >= n || rowc >= N) continue;
+                    const int js = u * kTileJ + jl;               // state within the chunk tile
+                    float out[kEpiRows];
+#pragma unroll
+                    for (int tt = 0; tt < kEpiRows; tt++) {
+                        const float acc = has_acc ? __uint_as_float(r[u][tt]) : 0.0f;
+                        float val = alpha * fmaf(-c, ycs[tt * kItemJ + js], acc);
+                        if (has_prev) val = fmaf(-beta, yps[tt * kItemJ + js], val);
                         nonfinite |= !isfinite(val);
-                        Yo[(row0 + rl) * ldo + j] = val;
+                        Yo[(rowc + tt) * ldo + j] = val;
                         out[tt] = val;
                     }
-                    // 16 consecutive rows of state j -> two 16-byte stores of the state-major copy
-                    uint4 pk[2];
+                    // kEpiRows consecutive rows of state j -> 16-byte stores of the block-major copy
+                    uint4 pk[kEpiRows / 8];
                     unsigned* pw = reinterpret_cast<unsigned*>(pk);
 #pragma unroll
-                    for (int tt = 0; tt < 8; tt++) {
+                    for (int tt = 0; tt < kEpiRows / 2; tt++) {
                         __nv_bfloat162 h2 = __floats2bfloat162_rn(out[2 * tt], out[2 * tt + 1]);
                         pw[tt] = *reinterpret_cast<unsigned*>(&h2);
                     }
-                    const int64_t Rr = R0 + cchunk / (kBlk / kEpiRows);   // block row of this chunk
                     uint4* dst = reinterpret_cast<uint4*>(Ysh_out + (Rr * n + j) * kBlk +
                                                           (cchunk % (kBlk / kEpiRows)) * kEpiRows);
-                    dst[0] = pk[0];
-                    dst[1] = pk[1];
+#pragma unroll
+                    for (int w = 0; w < kEpiRows / 8; w++) dst[w] = pk[w];
                 }
                 // release the chunk slot
                 __syncwarp();
@@ -457,15 +500,15 @@ int make_map(CUtensorMap* map, const void* base, int64_t cols, int64_t rows, int
     return r == CUDA_SUCCESS ? CHFSI_OK : CHFSI_ERR_CUDA;
 }
 
-// 2-D FP32 tensor map over a row-major [rows x ld] array, box [16 rows x 128 states],
-// no swizzle (epilogue operand tiles; states beyond ld read as zero).
+// 2-D FP32 tensor map over a row-major [rows x ld] array, box [kEpiRows rows x kItemJ
+// states], no swizzle (epilogue operand chunks; states beyond ld read as zero).
 int make_map_f32(CUtensorMap* map, const float* base, int64_t ld, int64_t rows) {
     EncodeTiledFn enc = encode_fn();
     if (!enc) return CHFSI_ERR_CUDA;
     if ((reinterpret_cast<uintptr_t>(base) & 15u) || ((ld * 4) % 16)) return CHFSI_ERR_ARG;
     cuuint64_t dims[2] = {(cuuint64_t)ld, (cuuint64_t)rows};
     cuuint64_t strides[1] = {(cuuint64_t)ld * 4};
-    cuuint32_t box[2] = {(cuuint32_t)kTileJ, (cuuint32_t)kEpiRows};
+    cuuint32_t box[2] = {(cuuint32_t)kItemJ, (cuuint32_t)kEpiRows};
     cuuint32_t es[2] = {1, 1};
     CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides, box, es,
                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -512,7 +555,7 @@ int bsr_step_tc(const BsrDev& h, int64_t n, const void* ysh_in, const float* Yc,
     if (n <= 0 || h.nbr <= 0) return CHFSI_OK;
     if (h.bdim != kBlk || h.val_t != Buf::BF16) return CHFSI_ERR_UNSUPPORTED;
     const int64_t N = h.nbr * kBlk;
-    if ((h.nblocks + 1) * kBlk > INT32_MAX || N > INT32_MAX || n > INT32_MAX || h.nbr * n > INT32_MAX)
+    if ((h.nblocks + 1) * kBlk > INT32_MAX || N > INT32_MAX || n > INT32_MAX || h.nbr * n + kItemJ > INT32_MAX)
         return CHFSI_ERR_UNSUPPORTED;
     CUtensorMap tmY, tmH, tmYc, tmYp;
     int rc;
@@ -531,13 +574,13 @@ int bsr_step_tc(const BsrDev& h, int64_t n, const void* ysh_in, const float* Yc,
         CHFSI_CUDA_TRY(cudaFuncSetAttribute(bsr_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
         attr[dev] = true;
     }
-    const int64_t ntiles = (n + kTileJ - 1) / kTileJ;
-    const int64_t total = (h.nbr + kRowsPerItem - 1) / kRowsPerItem * ntiles;
+    const int64_t nspans = (n + kItemJ - 1) / kItemJ;
+    const int64_t total = (h.nbr + kRowsPerItem - 1) / kRowsPerItem * nspans;
     const int sms = sm_count();
     if (sms <= 0) return CHFSI_ERR_CUDA;
     const unsigned grid = (unsigned)(total < sms ? total : sms);   // persistent: one CTA per SM
     bsr_tc_kernel<<<grid, kThreads, kSmemBytes, s>>>(tmY, tmH, tmYc, tmYp, Yp ? 1 : 0, h.nbr, h.brow_ptr, h.bcol,
-                                                     h.nblocks, N, n, ntiles, Yo, ldo,
+                                                     h.nblocks, N, n, nspans, Yo, ldo,
                                                      static_cast<__nv_bfloat16*>(ysh_out), (float)alpha, (float)c,
                                                      (float)beta, status);
     CHFSI_LAUNCH_CHECK();

@@ -164,7 +164,8 @@ def test_filter_mixed_schedule(P, oracle_mod, low, tol, layout):
         assert rel_fro(Yall, Yref) <= tol
 
 
-@pytest.mark.parametrize("g,w,n,m,L", [(8, 3, 200, 9, 6), (12, 4, 128, 7, 7), (4, 1, 5, 4, 2), (8, 2, 64, 5, 5)])
+@pytest.mark.parametrize("g,w,n,m,L", [(8, 3, 200, 9, 6), (12, 4, 128, 7, 7), (4, 1, 5, 4, 2), (8, 2, 64, 5, 5),
+                                       (8, 2, 390, 5, 5)])
 def test_bsr_tensor_core_bf16_matches_csr_bf16(P, oracle_mod, g, w, n, m, L):
     """tcgen05 BSR steps (BF16 operands, FP32 accumulation in TMEM) against the
     CUDA-core CSR steps with the same BF16 rounding of H and of Y_k: the two
@@ -211,11 +212,13 @@ def test_hybrid_operator_mixed_schedule(P, oracle_mod, low):
     assert abs(a02 - a0) <= 1e-9 * abs(a0) and abs(b2 - b) <= 1e-9 * abs(b)
 
 
-def test_bsr_tensor_core_single_step_exact_products(P, oracle_mod):
+@pytest.mark.parametrize("n", [136, 300, 520])
+def test_bsr_tensor_core_single_step_exact_products(P, oracle_mod, n):
     """m = 1 with BF16-representable H and X: every product and every partial sum
     is exact in FP32, so the tensor-core step equals the oracle to FP32 rounding
-    of the result."""
-    g, w, n = 8, 2, 136
+    of the result -- for one span of states with a ragged second tile (136), and
+    for several spans whose last one holds a single partial tile (300, 520)."""
+    g, w = 8, 2
     H = W.csr_grid(g, w, 0.0, 3)
     H["val"] = np.round(H["val"] * 64) / 64             # few-bit values: exact in BF16
     Xr = np.random.default_rng(5).integers(-8, 9, size=(H["N"], n)) / 8.0
