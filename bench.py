@@ -89,8 +89,9 @@ def lanczos_flops(nnz, N, k):
 
 def closure_flops(nnz, N, n, passes):
     """Gram N n^2 and triangular solve N n^2 per CholQR pass, H X_F (2 nnz n),
-    projection 2 N n^2, rotation 2 N n^2 (eigensolve not counted)."""
-    return passes * 2.0 * N * n * n + 2.0 * nnz * n + 2.0 * N * n * n + 2.0 * N * n * n
+    projection N n^2 (H_F is symmetric: one triangle, like the Gram), rotation
+    2 N n^2 (eigensolve not counted)."""
+    return passes * 2.0 * N * n * n + 2.0 * nnz * n + 1.0 * N * n * n + 2.0 * N * n * n
 
 
 # ---------------------------------------------------------------- clocks

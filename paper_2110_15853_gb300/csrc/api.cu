@@ -770,7 +770,9 @@ int rr_run_f32x2(const chfsi_matrix* H, const double* Y, int64_t ldy, int64_t N,
     if ((rc = to_f32x2(H->csr.val, 1, rl.H2, 1, H->csr.nnz, 1, false, s))) return rc;
     const CsrDev h2{H->csr.n_rows, H->csr.nnz, H->csr.row_ptr, H->csr.col, rl.H2, Buf::F32X2};
     if ((rc = csr_step_f32x2(h2, n, XF, ldw, nullptr, 0, HXF, ldw, 1.0, 0.0, 0.0, st, s))) return rc;
-    if ((rc = gemm_tn_f32x2(XF, ldw, HXF, ldw, N, n, rl.S, n, false, rl.part, rl.splits, s))) return rc;
+    // H_F is symmetric: only the tiles on and above the diagonal are computed, the others
+    // mirrored, and the diagonal tiles averaged with their transposes
+    if ((rc = gemm_tn_f32x2(XF, ldw, HXF, ldw, N, n, rl.S, n, true, rl.part, rl.splits, s))) return rc;
     if ((rc = symmetrize(rl.S, n, n, s))) return rc;
     if ((rc = rr_eig(rl, n, ritz, s))) return rc;
     if ((rc = to_f32x2(rl.Q, n, rl.Q2, n, n, n, false, s))) return rc;
@@ -850,7 +852,9 @@ int chfsi_rayleigh_ritz_ex(const chfsi_matrix* H, const double* Y, int64_t ldy, 
         io.out = HXF; io.out_t = Buf::F64; io.ldo = ldw;
         if ((rc = run_step(H, csr, bsr, StepMath::F64, n, io, 1.0, 0.0, 0.0, n % 2 == 0, st, s))) return rc;
     }
-    if ((rc = gemm_tn(XF, ldw, HXF, ldw, N, n, rl.S, n, false, rl.part, rl.splits, s))) return rc;
+    // H_F is symmetric: only the tiles on and above the diagonal are computed, the others
+    // mirrored, and the diagonal tiles averaged with their transposes
+    if ((rc = gemm_tn(XF, ldw, HXF, ldw, N, n, rl.S, n, true, rl.part, rl.splits, s))) return rc;
     if ((rc = symmetrize(rl.S, n, n, s))) return rc;
     // step 4: H_F Q = Q Lambda (cuSOLVER; column-major view of the symmetric H_F)
     if ((rc = rr_eig(rl, n, ritz, s))) return rc;
