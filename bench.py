@@ -94,6 +94,16 @@ def closure_flops(nnz, N, n, passes):
     return passes * 2.0 * N * n * n + 2.0 * nnz * n + 1.0 * N * n * n + 2.0 * N * n * n
 
 
+def hbm_peak_gbs():
+    """(GB/s, source): the measured copy bandwidth of the GB300s, else the
+    earlier single measurement used as the fallback."""
+    try:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured (MEASURED_PEAKS.json)"
+    except (OSError, ValueError, KeyError):
+        return 6800.0, "fallback"
+
+
 # ---------------------------------------------------------------- clocks
 
 
@@ -681,6 +691,16 @@ def measure_variants(P, torch, dev, stream, wl, H, Hd, Xd, bounds, quick=False, 
             # stands in for a block missing from one row of a block-row pair)
             "stored_block_tflops": m * 2.0 * B["n_blocks"] * 64 * 64 * n / (t * 1e-3) / 1e12,
             "y_rel_fro_err_vs_f64": err_vs_ref()}
+        # compulsory bytes of one BF16 step: Ysh^T in (2 N n), Y_cur and Y_prev (8 N n), the BF16
+        # blocks (8 KB each), Y_out in FP32 and its BF16 copy (6 N n); the per-step time also
+        # carries the call's one-off conversions, so this fraction is a lower bound for the kernel
+        step_bytes = 16.0 * N * n + 8192.0 * B["n_blocks"]
+        hbm = hbm_peak_gbs()
+        out["filter_bsr_bf16_tc_all_steps"].update({
+            "compulsory_bytes_per_step": step_bytes,
+            "hbm_gbs_per_step": step_bytes / (t / m * 1e-3) / 1e9,
+            "hbm_frac": step_bytes / (t / m * 1e-3) / 1e9 / hbm[0], "hbm_peak_gbs": hbm[0],
+            "hbm_peak_source": hbm[1]})
         for low, L in (("bf16", m - 4), ("f32", m - 4), ("f32", m // 2)):
             sched = P.mixed_schedule(m, L, low)
             t = timeit(lambda: P.filter(Hy, Xp, m, a, b, a0, schedule=sched, out=Yb, workspace=ws))
