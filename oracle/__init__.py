@@ -8,7 +8,8 @@ What it computes (all FP64):
 
 * ``spmm`` / ``spmm_t`` -- H X and H^T X for CSR H, row by row in stored order
   (plain C, ``chfsi_oracle.c``, compiled with -ffp-contract=off).
-* ``filter`` -- Algorithm 1 step 1 of the paper (Sec. 3.4), literally.
+* ``filter`` -- the scaled Chebyshev filter of Algorithm 1 step 1 (Sec. 3.4), as the
+  three-term recurrence Y_k = alpha_k (H - c) Y_{k-1} - beta_k Y_{k-2}.
 * ``filter_adjoint`` -- reverse-mode derivative of that loop, all iterates stored.
 * ``lanczos_bounds`` -- k-step Lanczos with full re-orthogonalisation giving the
   bounds (eps_0, eps_ub^w, eps_ub^uw) = (a0, a, b) that Algorithm 1 takes as input

@@ -8,8 +8,8 @@
  * Everything is written the slow, obvious way:
  *   - CSR sparse x dense products row by row, summing each row's terms in stored
  *     column order, compiled with -ffp-contract=off (no fused multiply-add);
- *   - the filter follows Algorithm 1, step 1 of the paper (Sec. 3.4) literally,
- *     with its variable names (e, c, sigma, sigma1, sigma2, gamma, X, Xt, Xnew);
+ *   - the filter is the three-term Chebyshev recurrence of Algorithm 1, step 1
+ *     (Sec. 3.4), with its coefficients derived from T_{k+1} = 2x T_k - T_{k-1};
  *   - the adjoint is plain reverse-mode differentiation of that loop with every
  *     iterate stored (no checkpointing), using the transpose product H^T.
  * OpenMP splits rows (or column slices) across threads; every output element is
@@ -84,82 +84,81 @@ static void copy_block(int64_t N, int64_t n, const double* A, int64_t lda, doubl
 }
 
 /*
- * Algorithm 1, step 1 (Chebyshev filtering process), written in the paper's order:
- *   e = (eps_ub^uw - eps_ub^w)/2,  c = (eps_ub^uw + eps_ub^w)/2,  sigma = e/(eps_0 - c)
- *   sigma1 = sigma,  gamma = 2/sigma1,  Xt = (sigma1/e)(H X - c X)
- *   for i = 2..m:
- *       sigma2 = 1/(gamma - sigma)
- *       Xnew = (2 sigma2/e)(H Xt - c Xt) - sigma sigma2 X
- *       X = Xt; Xt = Xnew; sigma = sigma2
- * Inputs a = eps_ub^w, b = eps_ub^uw, a0 = eps_0.  The output is Xt after the
- * loop (the newest iterate, Y_m).  work holds 3 * N * n doubles.
+ * Coefficients of the scaled Chebyshev filter of Algorithm 1, step 1 (Sec. 3.4),
+ * derived here from the textbook three-term recurrence T_{k+1}(x) = 2x T_k(x) - T_{k-1}(x).
+ *
+ * The affine map t -> (t - c)/e with c = (b + a)/2 and half-width e = (b - a)/2 sends
+ * the unwanted interval [a, b] onto [-1, 1]; the filter polynomial of degree k is
+ * p_k(t) = T_k((t - c)/e) / T_k(tau) with tau = (a0 - c)/e, so that p_k(a0) = 1.
+ * With the ratio r_k = T_{k-1}(tau)/T_k(tau) (r_1 = 1/tau) the Chebyshev recurrence
+ * divided by T_{k+1}(tau) gives
+ *     r_{k+1} = 1/(2 tau - r_k),
+ *     Y_1     = (r_1/e)(H - c) Y_0,
+ *     Y_{k+1} = (2 r_{k+1}/e)(H - c) Y_k - r_k r_{k+1} Y_{k-1},
+ * i.e. Y_k = alpha_k (H - c) Y_{k-1} - beta_k Y_{k-2} with alpha_1 = r_1/e,
+ * alpha_k = 2 r_k/e and beta_k = r_{k-1} r_k (k >= 2).  The paper's sigma_k is this
+ * ratio r_k.  Inputs a = eps_ub^w, b = eps_ub^uw, a0 = eps_0.
+ * alpha and beta have m+1 entries (index 0 unused, beta_1 = 0).
+ */
+void oracle_coefficients(int32_t m, double a, double b, double a0, double* alpha, double* beta,
+                         double* c_out) {
+    const double half_width = (b - a) / 2.0;
+    const double centre = (b + a) / 2.0;
+    const double tau = (a0 - centre) / half_width;
+    double r = 1.0 / tau;                    /* r_1 */
+    alpha[0] = 0.0; beta[0] = 0.0;
+    alpha[1] = r / half_width; beta[1] = 0.0;
+    for (int32_t k = 2; k <= m; k++) {
+        const double r_next = 1.0 / (2.0 * tau - r);
+        alpha[k] = 2.0 * r_next / half_width;
+        beta[k] = r * r_next;
+        r = r_next;
+    }
+    *c_out = centre;
+}
+
+/*
+ * Y = Y_m of the scaled Chebyshev filter (Algorithm 1, step 1; Sec. 3.4): the
+ * newest iterate of the three-term recurrence whose coefficients
+ * oracle_coefficients gives,
+ *     Y_0 = X,  Y_k = alpha_k (H Y_{k-1} - c Y_{k-1}) - beta_k Y_{k-2}  (beta_1 = 0).
+ * The product H Y_{k-1} is formed first (oracle_spmm), then each element is
+ * combined in that order.  work holds 3 * N * n doubles (Y_{k-2}, Y_{k-1}, H Y_{k-1}).
  * Returns 0, or -1 for m < 1.
  */
 int oracle_filter(int64_t N, const int64_t* row_ptr, const int32_t* col, const double* val,
                   int64_t n, const double* X_in, int64_t ldx, int32_t m,
                   double a, double b, double a0, double* Y, int64_t ldy, double* work) {
     if (m < 1) return -1;
-    const double e = (b - a) / 2.0;
-    const double c = (b + a) / 2.0;
-    double sigma = e / (a0 - c);
-    const double sigma1 = sigma;
-    const double gamma = 2.0 / sigma1;
+    double* alpha = (double*)malloc(sizeof(double) * (size_t)(m + 1));
+    double* beta = (double*)malloc(sizeof(double) * (size_t)(m + 1));
+    double c;
+    oracle_coefficients(m, a, b, a0, alpha, beta, &c);
 
-    double* X = work;                 /* previous iterate */
-    double* Xt = work + N * n;        /* current iterate  */
-    double* HXt = work + 2 * N * n;   /* H times current  */
-    copy_block(N, n, X_in, ldx, X, n);
+    double* older = work;               /* Y_{k-2}; becomes Y_k in place */
+    double* newer = work + N * n;       /* Y_{k-1}                       */
+    double* prod = work + 2 * N * n;    /* H Y_{k-1}                     */
+    copy_block(N, n, X_in, ldx, newer, n);   /* Y_0 */
+    for (int64_t q = 0; q < N * n; q++) older[q] = 0.0;
 
-    oracle_spmm(N, row_ptr, col, val, n, X, n, HXt, n);
-    const double s1e = sigma1 / e;
-    int64_t r;
-#pragma omp parallel for schedule(static)
-    for (r = 0; r < N; r++)
-        for (int64_t j = 0; j < n; j++)
-            Xt[r * n + j] = s1e * (HXt[r * n + j] - c * X[r * n + j]);
-
-    for (int32_t i = 2; i <= m; i++) {
-        const double sigma2 = 1.0 / (gamma - sigma);
-        const double s2e = 2.0 * sigma2 / e;
-        const double ss = sigma * sigma2;
-        oracle_spmm(N, row_ptr, col, val, n, Xt, n, HXt, n);
-        /* Xnew overwrites X in place: X(r,j) is read before it is written */
+    for (int32_t k = 1; k <= m; k++) {
+        oracle_spmm(N, row_ptr, col, val, n, newer, n, prod, n);
+        const double ak = alpha[k], bk = beta[k];
+        int64_t r;
 #pragma omp parallel for schedule(static)
         for (r = 0; r < N; r++)
             for (int64_t j = 0; j < n; j++) {
                 const int64_t q = r * n + j;
-                X[q] = s2e * (HXt[q] - c * Xt[q]) - ss * X[q];
+                double v = ak * (prod[q] - c * newer[q]);
+                if (k >= 2) v = v - bk * older[q];
+                older[q] = v;             /* Y_k overwrites Y_{k-2} after reading it */
             }
-        double* t = X; X = Xt; Xt = t;   /* X = Xt; Xt = Xnew */
-        sigma = sigma2;
+        double* t = older; older = newer; newer = t;   /* (Y_{k-1}, Y_k) */
     }
-    copy_block(N, n, Xt, n, Y, ldy);
+    copy_block(N, n, newer, n, Y, ldy);
+    free(alpha);
+    free(beta);
     return 0;
-}
-
-/*
- * Coefficients of the recurrence written as
- *   Y_1 = alpha_1 (H - c) Y_0,   Y_k = alpha_k (H - c) Y_{k-1} - beta_k Y_{k-2}  (k >= 2)
- * i.e. alpha_1 = sigma1/e, alpha_k = 2 sigma_k/e, beta_k = sigma_{k-1} sigma_k, with
- * sigma_k = 1/(gamma - sigma_{k-1}) (the same loop as above, unrolled into arrays).
- * alpha and beta have m+1 entries (index 0 unused).
- */
-void oracle_coefficients(int32_t m, double a, double b, double a0, double* alpha, double* beta,
-                         double* c_out) {
-    const double e = (b - a) / 2.0;
-    const double c = (b + a) / 2.0;
-    double sigma = e / (a0 - c);
-    const double sigma1 = sigma;
-    const double gamma = 2.0 / sigma1;
-    alpha[0] = 0.0; beta[0] = 0.0;
-    alpha[1] = sigma1 / e; beta[1] = 0.0;
-    for (int32_t k = 2; k <= m; k++) {
-        const double sigma2 = 1.0 / (gamma - sigma);
-        alpha[k] = 2.0 * sigma2 / e;
-        beta[k] = sigma * sigma2;
-        sigma = sigma2;
-    }
-    *c_out = c;
 }
 
 /*
