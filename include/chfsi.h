@@ -168,15 +168,26 @@ int chfsi_filter(const chfsi_matrix* H, const double* X, int64_t ldx, double* Y,
  * operator: about 2 * N * round_up(min(n_cols, 512), 8) * 8 bytes, e.g. N = 8000
  * with 64 columns fits).
  * The first call on each device looks up the array's device address (with that
- * device current); make that first call before any stream capture.  Nothing is
- * allocated.  All calls share the one array: calls that overlap on the GPU (other
- * streams, other threads) race and must be serialised by the caller.  The status
- * word kept in the array is cleared at the start of each call and is not readable
- * through chfsi_read_status.
+ * device current) and keeps it until the process exits; make that first call
+ * before any stream capture.  A device reset between calls is not supported (the
+ * kept address would be stale).  Nothing is allocated.  All calls share the one
+ * array: calls that overlap on the GPU (other streams, other threads) race and
+ * must be serialised by the caller.  The array holds the filter's device status
+ * word, cleared at the start of each call; read it with
+ * chfsi_filter_noalloc_read_status after the call.
  */
 int chfsi_filter_noalloc(const chfsi_matrix* H, const double* X, int64_t ldx, double* Y,
                          int64_t ldy, int64_t n_cols, int32_t m, double a, double b, double a0,
                          const chfsi_schedule* sched, void* stream);
+
+/*
+ * Companion of chfsi_filter_noalloc on the current device: synchronises `stream`
+ * and returns the status word that the last chfsi_filter_noalloc call's kernels
+ * left in the static array, mapped like chfsi_read_status (CHFSI_ERR_PATTERN for a
+ * column index out of range, CHFSI_ERR_NONFINITE for a NaN or Inf read or
+ * produced, CHFSI_OK if clean), and clears it.  The paper has no counterpart.
+ */
+int chfsi_filter_noalloc_read_status(void* stream);
 
 /* ------------------------------------------------------------------ adjoint of the filter */
 

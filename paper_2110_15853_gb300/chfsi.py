@@ -342,11 +342,21 @@ def symmetric_gradient(H: CsrMatrix, dH: torch.Tensor, transpose_index: torch.Te
 
 
 def transpose_index(row_ptr: np.ndarray, col: np.ndarray) -> np.ndarray:
-    """For a structurally symmetric CSR pattern: index of entry (j, i) for each (i, j)."""
+    """For a structurally symmetric CSR pattern: index of entry (j, i) for each (i, j).
+
+    Raises ValueError if an entry (i, j) has no stored (j, i), or if a pattern
+    stores the same (i, j) twice (the pairing would then not be one to one)."""
     N = row_ptr.shape[0] - 1
     rows = np.repeat(np.arange(N, dtype=np.int64), np.diff(row_ptr))
     key = rows * N + col.astype(np.int64)
     tkey = col.astype(np.int64) * N + rows
-    order = np.argsort(key)
-    pos = np.searchsorted(key[order], tkey)
+    order = np.argsort(key, kind="stable")
+    skey = key[order]
+    if skey.size > 1 and np.any(skey[1:] == skey[:-1]):
+        raise ValueError("transpose_index: the pattern stores an entry (i, j) more than once")
+    pos = np.searchsorted(skey, tkey)
+    found = pos < skey.size
+    found[found] = skey[pos[found]] == tkey[found]
+    if not np.all(found):
+        raise ValueError("transpose_index: the pattern is not structurally symmetric")
     return order[pos]

@@ -12,8 +12,13 @@
 //
 // The array's name is only a host-side stand-in in host code, so the device
 // address is looked up once per device with cudaGetSymbolAddress (with that device
-// current) and cached; that lookup happens on the first call made on each device.
-// Every call then runs the regular chfsi_filter with the array as its workspace.
+// current) and cached until the process exits; that lookup happens on the first
+// call made on each device.  A device reset (cudaDeviceReset, or a primary context
+// torn down and created again) reloads the module and makes the cached address
+// stale, so it is not supported between calls.  Every call then runs the regular
+// chfsi_filter with the array as its workspace; the status word that the filter's
+// kernels set (non-finite values, column indices out of range) sits in the
+// array's first bytes and chfsi_filter_noalloc_read_status reads it back.
 #include <mutex>
 
 #include "common.cuh"
@@ -56,4 +61,11 @@ int chfsi_filter_noalloc(const chfsi_matrix* H, const double* X, int64_t ldx, do
     // chfsi_filter clears the status word at the start of the call; the iterate
     // buffers need no clearing (every element read is written first).
     return chfsi_filter(H, X, ldx, Y, ldy, n_cols, m, a, b, a0, sched, ws, kNoallocScratchBytes, stream);
+}
+
+int chfsi_filter_noalloc_read_status(void* stream) {
+    void* ws = nullptr;
+    const int rc = scratch_address(&ws);
+    if (rc != CHFSI_OK) return rc;
+    return chfsi_read_status(ws, stream);
 }

@@ -65,3 +65,21 @@ def test_schedule_marshalling():
         C._schedule(3, ["f64", "f64"])
     with pytest.raises(KeyError):
         C._schedule(1, ["f16"])
+
+
+def test_transpose_index_rejects_an_unsymmetric_pattern():
+    row_ptr = np.array([0, 2, 3], dtype=np.int64)            # (0,0), (0,1), (1,1): no (1,0)
+    col = np.array([0, 1, 1], dtype=np.int32)
+    with pytest.raises(ValueError, match="structurally symmetric"):
+        C.transpose_index(row_ptr, col)
+    row_ptr = np.array([0, 1, 1], dtype=np.int64)            # (0,1) only: its mirror lies past the end
+    col = np.array([1], dtype=np.int32)
+    with pytest.raises(ValueError, match="structurally symmetric"):
+        C.transpose_index(row_ptr, col)
+
+
+def test_transpose_index_rejects_duplicate_entries():
+    row_ptr = np.array([0, 3, 4], dtype=np.int64)            # (0,1) stored twice
+    col = np.array([0, 1, 1, 0], dtype=np.int32)
+    with pytest.raises(ValueError, match="more than once"):
+        C.transpose_index(row_ptr, col)

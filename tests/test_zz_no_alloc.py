@@ -56,9 +56,36 @@ def test_noalloc_rejects_problems_beyond_the_static_scratch(P):
     H = W.csr_grid(20, 2, 0.1, 92)                             # N = 8000
     Hd = P.CsrMatrix.from_arrays(H["row_ptr"], H["col"], H["val"], device=dev)
     desc = Hd.descriptor()
-    n = 2048                                                   # 2 * 8000 * 2048 * 8 B > 16 MiB
+    n = 2048            # workspace 2 * 8000 * 512 * 8 B (one 512-column slab) > 16 MiB
     X = torch.zeros((H["N"], n), dtype=torch.float64, device=dev)
     Y = torch.empty_like(X)
     rc = lib.chfsi_filter_noalloc(ctypes.byref(desc), X.data_ptr(), n, Y.data_ptr(), n, n, 4, 4.2, 12.5, 3.0,
                                   None, torch.cuda.current_stream(dev).cuda_stream)
     assert rc == _abi.CHFSI_ERR_NOMEM
+
+
+def test_noalloc_status_reports_non_finite_input(P):
+    """A NaN in X reaches the filter's status word in the static array; the
+    companion call reads it back (and clears it), and the next clean call is clean."""
+    from paper_2110_15853_gb300 import _abi
+    lib = P.load()
+    dev = torch.device("cuda")
+    H = W.csr_grid(10, 2, 0.1, 93)
+    Hd = P.CsrMatrix.from_arrays(H["row_ptr"], H["col"], H["val"], device=dev)
+    desc = Hd.descriptor()
+    stream = torch.cuda.current_stream(dev).cuda_stream
+    n, m = 16, 5
+    X = torch.as_tensor(W.start_block(H["N"], n, 3)).to(dev)
+    X[7, 3] = float("nan")
+    Y = torch.empty_like(X)
+    rc = lib.chfsi_filter_noalloc(ctypes.byref(desc), X.data_ptr(), n, Y.data_ptr(), n, n, m, 4.2, 12.5, 3.0,
+                                  None, stream)
+    assert rc == _abi.CHFSI_OK
+    assert lib.chfsi_filter_noalloc_read_status(stream) == _abi.CHFSI_ERR_NONFINITE
+    assert lib.chfsi_filter_noalloc_read_status(stream) == _abi.CHFSI_OK      # cleared by the read
+    X[7, 3] = 0.0
+    rc = lib.chfsi_filter_noalloc(ctypes.byref(desc), X.data_ptr(), n, Y.data_ptr(), n, n, m, 4.2, 12.5, 3.0,
+                                  None, stream)
+    assert rc == _abi.CHFSI_OK
+    assert lib.chfsi_filter_noalloc_read_status(stream) == _abi.CHFSI_OK
+    assert bool(torch.isfinite(Y).all())
