@@ -224,19 +224,37 @@ def gaussian(shape, seed: int, stream: int) -> np.ndarray:
     return _rng(seed, stream).standard_normal(shape)
 
 
-def start_block(N: int, n: int, seed: int, orthonormalise: bool | None = None) -> np.ndarray:
+def start_block(N: int, n: int, seed: int, orthonormalise: bool | None = None,
+                out: np.ndarray | None = None) -> np.ndarray:
     """X: N x n Gaussian, orthonormalised by LAPACK Householder QR when affordable.
 
     For N*n^2 above 2e11 (the 48^3 and 64^3 workloads) a host QR takes too long,
-    and X is the Gaussian block scaled by 1/sqrt(N) (columns nearly orthonormal).
+    and X is the Gaussian block scaled by 1/sqrt(N) (columns nearly orthonormal);
+    that block can be written into `out` (a C-contiguous float64 N x n array, e.g.
+    the numpy view of pinned host memory), drawn in row chunks from the same
+    Philox stream so that the values do not depend on the chunking.
     """
-    X = gaussian((N, n), seed, _STREAM_X)
     if orthonormalise is None:
         orthonormalise = N * n * n <= 2e11
     if orthonormalise:
-        X, _ = np.linalg.qr(X)
-        return np.ascontiguousarray(X)
-    return X / math.sqrt(N)
+        X, _ = np.linalg.qr(gaussian((N, n), seed, _STREAM_X))
+        X = np.ascontiguousarray(X)
+        if out is not None:
+            out[...] = X
+            return out
+        return X
+    if out is None:
+        out = np.empty((N, n), dtype=np.float64)
+    if out.shape != (N, n) or out.dtype != np.float64 or not out.flags.c_contiguous:
+        raise ValueError("out must be a C-contiguous float64 (N, n) array")
+    rng = _rng(seed, _STREAM_X)
+    root = math.sqrt(N)
+    rows = max(1, (1 << 24) // max(n, 1))
+    for r0 in range(0, N, rows):
+        blk = out[r0:r0 + rows]
+        rng.standard_normal(out=blk)
+        blk /= root
+    return out
 
 
 def lanczos_start(N: int, seed: int) -> np.ndarray:

@@ -299,6 +299,18 @@ int chfsi_read_status(void* ws, void* stream);
 /* Clear the workspace status word (queued on `stream`). */
 int chfsi_clear_status(void* ws, void* stream);
 
+/*
+ * Measured FMA throughput (FLOP/s, two per fused multiply-add) of the current
+ * device's FP64 (precision = CHFSI_F64: the DFMA pipe) or FP32 (CHFSI_F32: the
+ * FFMA pipe), from a register-resident loop of independent multiply-adds over
+ * 8 blocks of 256 threads per SM, timed with CUDA events on `stream` after one
+ * untimed launch.  Synchronises `stream`.  The denominator of the roofline
+ * fraction of the arithmetic-bound filter steps.  Diagnostics only: the paper
+ * has no counterpart.  Errors: CHFSI_ERR_ARG (bad precision or NULL output),
+ * CHFSI_ERR_CUDA.
+ */
+int chfsi_measure_pipe_peak(int32_t precision, double* flops_per_second, void* stream);
+
 /* Number of kernels this library has launched in this process (all devices, all
  * threads; library calls such as the cuSOLVER eigensolver are not counted).
  * Diagnostics only: the paper has no counterpart. */

@@ -77,6 +77,7 @@ SIGNATURES = {
     "chfsi_read_status": (ctypes.c_int, [_vp, _vp]),
     "chfsi_clear_status": (ctypes.c_int, [_vp, _vp]),
     "chfsi_kernel_launches": (ctypes.c_ulonglong, []),
+    "chfsi_measure_pipe_peak": (ctypes.c_int, [_i32, _DP, _vp]),
     "chfsi_filter_noalloc": (ctypes.c_int, [_MP, _vp, _i64, _vp, _i64, _i64, _i32, _dbl, _dbl, _dbl, _SP, _vp]),
     "chfsi_filter_noalloc_read_status": (ctypes.c_int, [_vp]),
 }

@@ -264,6 +264,25 @@ def rayleigh_ritz(H, Y: torch.Tensor, cholqr_passes: int = 2, psi: Optional[torc
     return ritz, psi
 
 
+def measure_pipe_peak(precision: str = "f64", device="cuda") -> float:
+    """FLOP/s of the FP64 (DFMA) or FP32 (FFMA) pipe of `device`, measured by the
+    library's register-resident FMA loop (chfsi_measure_pipe_peak)."""
+    out = ctypes.c_double(0.0)
+    dev = torch.device(device)
+    with torch.cuda.device(dev):
+        check(load().chfsi_measure_pipe_peak(PRECISIONS[precision], ctypes.byref(out), _stream_handle(dev)),
+              "chfsi_measure_pipe_peak")
+    return out.value
+
+
+def lanczos_workspace_bytes(H, steps: int) -> int:
+    sz = ctypes.c_size_t(0)
+    desc = H.descriptor()
+    check(load().chfsi_lanczos_workspace_size(ctypes.byref(desc), steps, ctypes.byref(sz)),
+          "chfsi_lanczos_workspace_size")
+    return sz.value
+
+
 def lanczos_bounds(H: CsrMatrix, v0: torch.Tensor, steps: int, n_wanted: int,
                    workspace: Optional[Workspace] = None):
     """(a, b, a0) from `steps` Lanczos steps started at v0 (device float64, length N)."""
