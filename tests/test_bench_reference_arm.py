@@ -39,3 +39,13 @@ def test_reference_arm_other_ranks_do_no_work():
     p = _run({"RANK": "1"})
     assert p.returncode == 0, p.stderr[-2000:]
     assert p.stdout.strip() == ""
+
+
+def test_bench_uses_only_exported_binding_names():
+    """Every P.<name> that bench.py calls exists in the package (a host check that
+    catches a missing export before a GPU run)."""
+    import re
+    import paper_2110_15853_gb300 as P
+    src = open(os.path.join(ROOT, "bench.py")).read()
+    names = set(re.findall(r"\bP\.([A-Za-z_]+)", src))
+    assert names and not [n for n in names if not hasattr(P, n)]
