@@ -116,6 +116,9 @@ typedef struct {
 #define CHFSI_F32X2 3         /* two-float: values as hi + lo FP32 pairs (about 48 bits),
                                  FP32-pipe arithmetic with error-free transformations;
                                  CSR layout (CHFSI_CSR or CHFSI_HYBRID) only            */
+#define CHFSI_F64_OZAKI 4     /* closure products only: FP64 values split into six 8-bit
+                                 slices whose products run on the BF16 tensor cores with
+                                 exact integer accumulation (see chfsi_ozaki_gemm)       */
 
 /*
  * Per-step precision of the filter: step_prec[k-1] is the precision of the step
@@ -260,15 +263,52 @@ int chfsi_rayleigh_ritz_ex_workspace_size(const chfsi_matrix* H, int64_t n_cols,
 /*
  * chfsi_rayleigh_ritz with a choice of arithmetic for the three large products
  * (Gram / projection A^T B over N, X_F = Y R^-1, Psi = X_F Q) and H X_F:
- * precision = CHFSI_F64 (the same as chfsi_rayleigh_ritz) or CHFSI_F32X2
+ * precision = CHFSI_F64 (the same as chfsi_rayleigh_ritz), CHFSI_F32X2
  * (two-float products on the FP32 pipe, about 48 significant bits; needs the CSR
- * layout).  The Cholesky factorisation, the triangular inverse and the
- * eigensolve stay FP64 in both.  Same arguments, errors and synchronisation as
- * chfsi_rayleigh_ritz.
+ * layout) or CHFSI_F64_OZAKI (the dense products as chfsi_ozaki_gemm on the BF16
+ * tensor cores, about 48 significant bits of the row scales; H X_F in two-float
+ * arithmetic on a CSR operator, in FP64 on a BSR one).  The Cholesky
+ * factorisation, the triangular inverse and the eigensolve stay FP64 in all
+ * three.  Same arguments, errors and synchronisation as chfsi_rayleigh_ritz.
  */
 int chfsi_rayleigh_ritz_ex(const chfsi_matrix* H, const double* Y, int64_t ldy, int64_t n_cols,
                            double* Psi, int64_t ldpsi, double* ritz, int32_t cholqr_passes,
                            int32_t precision, void* ws, size_t ws_bytes, void* stream);
+
+/* ------------------------------------------------------------------ FP64-accurate dense products */
+
+#define CHFSI_OP_TN 0              /* C = A^T B: A is K x M (lda), B is K x Nc (ldb)          */
+#define CHFSI_OP_NN 1              /* C = A B:   A is M x K (lda), B is K x Nc (ldb)          */
+#define CHFSI_GEMM_SYMMETRIC 1     /* TN, M == Nc, C known to be symmetric (Y^T Y, X^T H X):
+                                      the 128 x 128 tiles on and above the diagonal are
+                                      computed, the others mirrored                          */
+#define CHFSI_GEMM_B_UPPER 2       /* NN, B upper triangular (B[k][j] = 0 for k > j)          */
+
+int chfsi_ozaki_gemm_workspace_size(int32_t op, int64_t M, int64_t Nc, int64_t K, int32_t flags,
+                                    size_t* bytes);
+
+/*
+ * The closure's dense FP64 products (Algorithm 1 steps 2, 3 and 5: S = Y^T Y,
+ * X_F = Y R^-1, H_F = X_F^T (H X_F), Psi = X_F Q) on the BF16 tensor cores, by
+ * Ozaki-scheme splitting: each row of the K-major operands (A^T or A, and B^T) is
+ * scaled by a power of two and rounded to a 48-bit fixed-point number held as six
+ * balanced 8-bit digits, each digit slice exact in BF16; the 21 slice products
+ * with digit weights down to 2^-56 run as tcgen05 MMAs whose FP32 accumulation is
+ * exact (integer multiples, partial sums below 2^24, drained every 256 K into 64-bit
+ * integers).  |C_ij - (A_hat B_hat^T)_ij| is below K 2^-42 times the product of the two
+ * rows' largest magnitudes (48-bit rounding of each value, the dropped slice pairs and
+ * the rounding of the shared accumulator of levels 5-7; errors of random sign make it
+ * about sqrt(K) times that in practice).  Row-major blocks with leading dimensions; C
+ * must not overlap A or B.  The workspace (chfsi_ozaki_gemm_workspace_size) holds
+ * the status word, the slices (12 bytes per operand element) and the split-K
+ * partial tiles.  A non-finite input sets CHFSI_ERR_NONFINITE in the status word.
+ * Errors: CHFSI_ERR_ARG, CHFSI_ERR_NOMEM, CHFSI_ERR_UNSUPPORTED (K above 2^21),
+ * CHFSI_ERR_CUDA.  No counterpart in the paper, which runs these products with
+ * FP64 cuBLAS (Sec. 4.3).
+ */
+int chfsi_ozaki_gemm(int32_t op, const double* A, int64_t lda, const double* B, int64_t ldb, double* C,
+                     int64_t ldc, int64_t M, int64_t Nc, int64_t K, int32_t flags, void* ws,
+                     size_t ws_bytes, void* stream);
 
 /* ------------------------------------------------------------------ spectral bounds */
 

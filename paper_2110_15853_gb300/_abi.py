@@ -30,6 +30,12 @@ CHFSI_F64 = 0
 CHFSI_F32 = 1
 CHFSI_BF16_F32ACC = 2
 CHFSI_F32X2 = 3
+CHFSI_F64_OZAKI = 4
+
+CHFSI_OP_TN = 0
+CHFSI_OP_NN = 1
+CHFSI_GEMM_SYMMETRIC = 1
+CHFSI_GEMM_B_UPPER = 2
 
 _i32, _i64, _dbl, _vp, _sz = ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_void_p, ctypes.c_size_t
 
@@ -78,6 +84,9 @@ SIGNATURES = {
     "chfsi_clear_status": (ctypes.c_int, [_vp, _vp]),
     "chfsi_kernel_launches": (ctypes.c_ulonglong, []),
     "chfsi_measure_pipe_peak": (ctypes.c_int, [_i32, _DP, _vp]),
+    "chfsi_ozaki_gemm_workspace_size": (ctypes.c_int, [_i32, _i64, _i64, _i64, _i32, _SZP]),
+    "chfsi_ozaki_gemm": (ctypes.c_int, [_i32, _vp, _i64, _vp, _i64, _vp, _i64, _i64, _i64, _i64, _i32, _vp, _sz,
+                                        _vp]),
     "chfsi_filter_noalloc": (ctypes.c_int, [_MP, _vp, _i64, _vp, _i64, _i64, _i32, _dbl, _dbl, _dbl, _SP, _vp]),
     "chfsi_filter_noalloc_read_status": (ctypes.c_int, [_vp]),
 }

@@ -23,10 +23,11 @@ import numpy as np
 import torch
 
 from . import _abi
-from ._abi import (CHFSI_BF16_F32ACC, CHFSI_BSR, CHFSI_CSR, CHFSI_F32, CHFSI_F32X2, CHFSI_F64, ChfsiError, check,
-                   load)
+from ._abi import (CHFSI_BF16_F32ACC, CHFSI_BSR, CHFSI_CSR, CHFSI_F32, CHFSI_F32X2, CHFSI_F64, CHFSI_F64_OZAKI,
+                   ChfsiError, check, load)
 
-PRECISIONS = {"f64": CHFSI_F64, "f32": CHFSI_F32, "bf16": CHFSI_BF16_F32ACC, "f32x2": CHFSI_F32X2}
+PRECISIONS = {"f64": CHFSI_F64, "f32": CHFSI_F32, "bf16": CHFSI_BF16_F32ACC, "f32x2": CHFSI_F32X2,
+              "ozaki": CHFSI_F64_OZAKI}
 
 
 def _ptr(t: Optional[torch.Tensor]) -> Optional[int]:
@@ -243,7 +244,8 @@ def rayleigh_ritz(H, Y: torch.Tensor, cholqr_passes: int = 2, psi: Optional[torc
     """(ritz ascending, Psi) from Algorithm 1 steps 2-5 (CholQR, projection, eig, rotation).
 
     precision "f64" runs every product in FP64 (chfsi_rayleigh_ritz); "f32x2" runs
-    the large products in two-float arithmetic (chfsi_rayleigh_ritz_ex)."""
+    the large products in two-float arithmetic and "ozaki" the dense products on the
+    BF16 tensor cores by Ozaki slices (chfsi_rayleigh_ritz_ex)."""
     _check_block(Y, "Y")
     N, n = Y.shape
     if psi is None:
@@ -262,6 +264,35 @@ def rayleigh_ritz(H, Y: torch.Tensor, cholqr_passes: int = 2, psi: Optional[torc
                                         _stream_handle(Y.device))
         check(rc, "chfsi_rayleigh_ritz_ex")
     return ritz, psi
+
+
+def ozaki_gemm(A: torch.Tensor, B: torch.Tensor, transpose_a: bool = False, symmetric: bool = False,
+               b_upper: bool = False, out: Optional[torch.Tensor] = None,
+               workspace: Optional[Workspace] = None) -> torch.Tensor:
+    """FP64-accurate product on the BF16 tensor cores (chfsi_ozaki_gemm):
+    A^T B if transpose_a (A: K x M, B: K x Nc) else A B (A: M x K, B: K x Nc)."""
+    for t, name in ((A, "A"), (B, "B")):
+        if t.dtype != torch.float64 or t.dim() != 2 or t.stride(1) != 1 or not t.is_cuda:
+            raise ValueError(f"{name} must be a row-major float64 CUDA matrix")
+    if transpose_a:
+        K, M = A.shape
+    else:
+        M, K = A.shape
+    if B.shape[0] != K:
+        raise ValueError("inner dimensions differ")
+    Nc = B.shape[1]
+    op = _abi.CHFSI_OP_TN if transpose_a else _abi.CHFSI_OP_NN
+    flags = (_abi.CHFSI_GEMM_SYMMETRIC if symmetric else 0) | (_abi.CHFSI_GEMM_B_UPPER if b_upper else 0)
+    if out is None:
+        out = torch.empty((M, Nc), dtype=torch.float64, device=A.device)
+    lib = load()
+    sz = ctypes.c_size_t(0)
+    check(lib.chfsi_ozaki_gemm_workspace_size(op, M, Nc, K, flags, ctypes.byref(sz)),
+          "chfsi_ozaki_gemm_workspace_size")
+    ws = (workspace or Workspace(A.device)).get(sz.value)
+    check(lib.chfsi_ozaki_gemm(op, _ptr(A), A.stride(0), _ptr(B), B.stride(0), _ptr(out), out.stride(0), M, Nc, K,
+                               flags, _ptr(ws), ws.numel(), _stream_handle(A.device)), "chfsi_ozaki_gemm")
+    return out
 
 
 def measure_pipe_peak(precision: str = "f64", device="cuda") -> float:

@@ -2,6 +2,7 @@
 // per-step schedule of the Chebyshev filter, the adjoint with checkpointing, the
 // Rayleigh-Ritz closure and the Lanczos bounds.  Host code here only orders
 // kernels on the caller's stream; every arithmetic step runs on the GPU.
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <functional>
@@ -683,10 +684,29 @@ struct RRLayout {
     int lwork = 0;
     // two-float closure
     float2 *Y2 = nullptr, *B2[2] = {nullptr, nullptr}, *HX2 = nullptr, *R2 = nullptr, *Q2 = nullptr, *H2 = nullptr;
+    // Ozaki closure: scratch of the tensor-core products, reused by the two-float H X_F
+    unsigned char* oz = nullptr;
+    size_t oz_bytes = 0;
 };
 
+// Scratch of the Ozaki closure: the largest of its four products and of the
+// two-float H X_F (two pair-split N x ldw blocks and H's values as pairs).
+size_t rr_ozaki_bytes(int64_t N, int64_t n, int64_t nnz, bool csr) {
+    size_t b = ozaki_workspace_bytes(true, n, n, N, true);
+    b = std::max(b, ozaki_workspace_bytes(false, N, n, n, false));
+    b = std::max(b, ozaki_workspace_bytes(true, n, n, N, false));
+    if (csr) {
+        Sizer sz;
+        sz.take<float2>((size_t)(N * pad8(n)));
+        sz.take<float2>((size_t)(N * pad8(n)));
+        sz.take<float2>((size_t)(nnz > 0 ? nnz : 1));
+        b = std::max(b, sz.used);
+    }
+    return b;
+}
+
 template <typename Ar>
-void rr_layout(Ar& ar, int64_t N, int64_t n, int lwork, int precision, int64_t nnz, RRLayout* out) {
+void rr_layout(Ar& ar, int64_t N, int64_t n, int lwork, int precision, int64_t nnz, bool csr, RRLayout* out) {
     RRLayout rl;
     const int64_t ldw = pad8(n);
     rl.splits = gemm_tn_splits(N, n);
@@ -709,6 +729,10 @@ void rr_layout(Ar& ar, int64_t N, int64_t n, int lwork, int precision, int64_t n
         rl.XF = ar.template take<double>((size_t)(N * ldw));
         rl.T = ar.template take<double>((size_t)(N * ldw));
     }
+    if (precision == CHFSI_F64_OZAKI) {
+        rl.oz_bytes = rr_ozaki_bytes(N, n, nnz, csr);
+        rl.oz = ar.template take<unsigned char>(rl.oz_bytes);
+    }
     if (out) *out = rl;
 }
 
@@ -716,7 +740,7 @@ int rr_check(const chfsi_matrix* H, int64_t n_cols, int32_t cholqr_passes, int32
     int rc = rows_of(H, N);
     if (rc) return rc;
     if (n_cols < 1 || n_cols > *N || (cholqr_passes != 1 && cholqr_passes != 2)) return CHFSI_ERR_ARG;
-    if (precision != CHFSI_F64 && precision != CHFSI_F32X2) return CHFSI_ERR_ARG;
+    if (precision != CHFSI_F64 && precision != CHFSI_F32X2 && precision != CHFSI_F64_OZAKI) return CHFSI_ERR_ARG;
     if (precision == CHFSI_F32X2 && !has_csr(H)) return CHFSI_ERR_UNSUPPORTED;
     return CHFSI_OK;
 }
@@ -780,6 +804,60 @@ int rr_run_f32x2(const chfsi_matrix* H, const double* Y, int64_t ldy, int64_t N,
     return rr_finish(rl, st, s);
 }
 
+// Steps 2, 3 and 5 with the dense products on the tensor cores (Ozaki slices) and
+// H X_F in two-float arithmetic (FP64 on a BSR-only operator); the Cholesky
+// factorisation, the triangular inverse and the eigensolve stay FP64.
+int rr_run_ozaki(const chfsi_matrix* H, const double* Y, int64_t ldy, int64_t N, int64_t n, double* Psi,
+                 int64_t ldpsi, double* ritz, int passes, const RRLayout& rl, unsigned* st, cudaStream_t s) {
+    const int64_t ldw = pad8(n);
+    int rc;
+    const double* cur = Y;
+    int64_t cur_ld = ldy;
+    double* bufs[2] = {rl.XF, rl.T};
+    int which = 0;
+    for (int pass = 0; pass < passes; pass++) {
+        if ((rc = ozaki_gemm_tn(cur, cur_ld, cur, cur_ld, N, n, n, rl.S, n, true, rl.oz, rl.oz_bytes, st, s)))
+            return rc;
+        if ((rc = cholesky_upper(rl.S, n, n, st, s))) return rc;
+        if ((rc = tri_inverse_upper(rl.S, n, rl.Rinv, n, n, s))) return rc;
+        double* out = bufs[which];
+        if ((rc = ozaki_gemm_nn(cur, cur_ld, rl.Rinv, n, N, n, n, out, ldw, true, rl.oz, rl.oz_bytes, st, s)))
+            return rc;
+        cur = out;
+        cur_ld = ldw;
+        which ^= 1;
+    }
+    double* XF = const_cast<double*>(cur);
+    double* HXF = bufs[which];
+    if (has_csr(H)) {
+        Arena ar(rl.oz, rl.oz_bytes);
+        float2* X2 = ar.take<float2>((size_t)(N * ldw));
+        float2* HX2 = ar.take<float2>((size_t)(N * ldw));
+        float2* H2 = ar.take<float2>((size_t)(H->csr.nnz > 0 ? H->csr.nnz : 1));
+        if ((rc = to_f32x2(XF, ldw, X2, ldw, N, n, true, s))) return rc;
+        if ((rc = to_f32x2(H->csr.val, 1, H2, 1, H->csr.nnz, 1, false, s))) return rc;
+        const CsrDev h2{H->csr.n_rows, H->csr.nnz, H->csr.row_ptr, H->csr.col, H2, Buf::F32X2};
+        if ((rc = csr_step_f32x2(h2, n, X2, ldw, nullptr, 0, HX2, ldw, 1.0, 0.0, 0.0, st, s))) return rc;
+        if ((rc = from_f32x2(HX2, ldw, HXF, ldw, N, n, true, s))) return rc;
+    } else {
+        CsrDev csr{};
+        BsrDev bsr{};
+        make_devs(H, H->csr.val, H->bsr.val, Buf::F64, &csr, &bsr);
+        StepIO io{};
+        io.cur = XF; io.cur_t = Buf::F64; io.ldc = ldw;
+        io.gather = XF; io.gather_t = Buf::F64; io.ldg = ldw;
+        io.out = HXF; io.out_t = Buf::F64; io.ldo = ldw;
+        if ((rc = run_step(H, csr, bsr, StepMath::F64, n, io, 1.0, 0.0, 0.0, n % 2 == 0, st, s))) return rc;
+    }
+    // H_F is symmetric: the tiles on and above the diagonal, mirrored, the diagonal
+    // tiles averaged with their transposes
+    if ((rc = ozaki_gemm_tn(XF, ldw, HXF, ldw, N, n, n, rl.S, n, true, rl.oz, rl.oz_bytes, st, s))) return rc;
+    if ((rc = symmetrize(rl.S, n, n, s))) return rc;
+    if ((rc = rr_eig(rl, n, ritz, s))) return rc;
+    if ((rc = ozaki_gemm_nn(XF, ldw, rl.Q, n, N, n, n, Psi, ldpsi, false, rl.oz, rl.oz_bytes, st, s))) return rc;
+    return rr_finish(rl, st, s);
+}
+
 }  // namespace
 
 int chfsi_rayleigh_ritz_ex_workspace_size(const chfsi_matrix* H, int64_t n_cols, int32_t cholqr_passes,
@@ -791,7 +869,7 @@ int chfsi_rayleigh_ritz_ex_workspace_size(const chfsi_matrix* H, int64_t n_cols,
     int lwork = 0;
     if ((rc = syevd_lwork(n_cols, &lwork))) return rc;
     SizeOnly sz;
-    rr_layout(sz, N, n_cols, lwork, precision, has_csr(H) ? H->csr.nnz : 0, nullptr);
+    rr_layout(sz, N, n_cols, lwork, precision, has_csr(H) ? H->csr.nnz : 0, has_csr(H), nullptr);
     *bytes = sz.used;
     return CHFSI_OK;
 }
@@ -813,16 +891,18 @@ int chfsi_rayleigh_ritz_ex(const chfsi_matrix* H, const double* Y, int64_t ldy, 
     if ((rc = syevd_lwork(n_cols, &lwork))) return rc;
     const int64_t nnz = has_csr(H) ? H->csr.nnz : 0;
     SizeOnly sz;
-    rr_layout(sz, N, n_cols, lwork, precision, nnz, nullptr);
+    rr_layout(sz, N, n_cols, lwork, precision, nnz, has_csr(H), nullptr);
     if (ws_bytes < sz.used) return CHFSI_ERR_NOMEM;
     Arena ar(ws, ws_bytes);
     RRLayout rl;
-    rr_layout(ar, N, n_cols, lwork, precision, nnz, &rl);
+    rr_layout(ar, N, n_cols, lwork, precision, nnz, has_csr(H), &rl);
     cudaStream_t s = as_stream(stream);
     unsigned* st = status_word(ws);
     CHFSI_CUDA_TRY(cudaMemsetAsync(st, 0, sizeof(unsigned), s));
     const int64_t n = n_cols, ldw = pad8(n);
     if (precision == CHFSI_F32X2) return rr_run_f32x2(H, Y, ldy, N, n, Psi, ldpsi, ritz, cholqr_passes, rl, st, s);
+    if (precision == CHFSI_F64_OZAKI)
+        return rr_run_ozaki(H, Y, ldy, N, n, Psi, ldpsi, ritz, cholqr_passes, rl, st, s);
 
     // step 2: X_F = Y R^-1 with S = Y^T Y = R^T R (repeated on X_F for CholQR2)
     const double* cur = Y;

@@ -1,0 +1,731 @@
+// FP64-accurate dense products on the BF16 tensor cores (Ozaki-scheme splitting),
+// for the large products of the ChFSI closure (Algorithm 1 steps 2, 3 and 5,
+// Sec. 3.4): the Gram matrix Y^T Y of the Cholesky-QR, X_F = Y R^-1, the projection
+// X_F^T (H X_F) and the rotation X_F Q.  GB300's FP64 pipe runs about 1.2 TFLOP/s;
+// its BF16 tensor cores about 1.9 PFLOP/s.
+//
+// Splitting.  The product is C = A_hat B_hat^T with both operands K-major: for
+// C = A^T B (Gram form) A_hat = A^T, B_hat = B^T; for C = A B, A_hat = A, B_hat =
+// B^T.  Each row r of an operand gets a power-of-two scale 2^{e_r} with
+// |A_hat[r][k]| 2^{-e_r} < 1/2 for all k, and the scaled value a is rounded to a
+// 48-bit fixed-point number and written as six balanced base-256 digits
+//     a = sum_{t=1..6} d_t 2^{-8t},   d_t integer, |d_t| <= 128,
+// (integer arithmetic on the FP64 bit pattern; no FP64 instructions).  Slice t
+// stores d_t 2^{-8t} in BF16, which is exact (8 significant bits).  Then
+//     C_ij = 2^{e_i + f_j} sum_{t + u <= 7} sum_k a_t[i][k] b_u[j][k]
+// keeps every digit product of weight 2^{-56} and above (21 slice pairs; the
+// dropped pairs and the 48-bit rounding are below 2^{-48} of the row scales).
+//
+// Exact accumulation.  A product of two slices is d_t g_u 2^{-8(t+u)}, an integer
+// multiple of 2^{-8l} at level l = t + u with |d_t g_u| <= 2^14.  The FP32 tensor-core
+// accumulator sums such multiples without rounding while the partial sums stay below
+// 2^24 units, so the pairs of levels 2, 3 and 4 (1, 2 and 3 pairs) accumulate into
+// their own TMEM accumulators E2, E3, E4 for at most 256 K (3 * 256 * 2^14 < 2^24),
+// and are then drained exactly into a 64-bit integer per output element (units
+// 2^{-40}).  The 15 pairs of levels 5-7 share one FP32 accumulator I, drained the
+// same way (rounded to 2^{-40}) every 256 K, so its rounding stays far below the
+// FP64 level.  C = 2^{e_i + f_j - 40} * (the integer), converted once at the end.
+//
+// Kernel.  Persistent, warp-specialised, one CTA per SM, 128 x 128 output tiles:
+//   warp 0, lane 0 : TMA producer -- per K-block of 32, the six A and six B slice
+//                    tiles (64-byte swizzle, 8 KB each) into a two-stage ring;
+//   warp 1         : owns the 512 TMEM columns (E2 | E3 | E4 | I); lane 0 issues the
+//                    21 x 2 MMAs (M = N = 128, K = 16) of each stage;
+//   warps 2-9      : epilogue; warp w reads TMEM lanes 32 (w % 4) .. + 31, columns
+//                    64 ((w - 2) / 4) .. + 63, and keeps those 64 integers in registers.
+// Drains alternate between the exact group (E2-E4, after K-blocks 3, 11, 19, ...) and
+// I (after K-blocks 7, 15, ...); the issuer runs the other group's MMAs of the next
+// stage before it waits for a drain.  Every mbarrier wait is bounded; on a timeout
+// the CTA flags DEV_TIMEOUT, stops, waits (bounded) for its copies and MMAs in flight,
+// frees TMEM and exits.
+#include "common.cuh"
+#include "kernels.cuh"
+#include "tcgen05.cuh"
+
+namespace chfsi {
+
+namespace {
+
+using namespace tc;
+
+constexpr int kSlices = 6;
+constexpr int kTile = 128;                            // M = N of the output tile
+constexpr int kKB = 32;                               // K per stage (64-byte rows)
+constexpr int kSliceBytes = kTile * kKB * 2;          // 8 KB
+constexpr int kStageBytes = 2 * kSlices * kSliceBytes;
+constexpr int kStages = 2;
+constexpr int kPeriod = 8;                            // K-blocks between drains of one group
+constexpr int kEpiWarps = 8;
+constexpr int kThreads = 32 * (2 + kEpiWarps);
+constexpr int kSmemBytes = kStages * kStageBytes + 1024;
+constexpr uint32_t kTmemCols = 512;
+constexpr uint32_t kIdesc = idesc_bf16(kTile, kTile);
+constexpr uint64_t kWaitNs = 1000000000ull;           // pipeline waits
+constexpr uint64_t kDrainNs = 1000000000ull;          // waits for work already in flight
+constexpr int kFullEvent = 3, kXEvent = 1, kYEvent = 2;
+static_assert(kSmemBytes + 1024 <= 227 * 1024, "shared memory per CTA");
+
+// Slice pairs (t, u), 0-based, and their accumulator (0: E2, 1: E3, 2: E4, 3: I).
+// The exact group X is pairs 0-5, the inexact group Y pairs 6-20.
+__constant__ int8_t kPairA[21] = {0, 0, 1, 0, 1, 2, 0, 1, 2, 3, 0, 1, 2, 3, 4, 0, 1, 2, 3, 4, 5};
+__constant__ int8_t kPairB[21] = {0, 1, 0, 2, 1, 0, 3, 2, 1, 0, 4, 3, 2, 1, 0, 5, 4, 3, 2, 1, 0};
+__constant__ int8_t kPairAcc[21] = {0, 1, 1, 2, 2, 2, 3, 3, 3, 3, 3, 3, 3, 3, 3, 3, 3, 3, 3, 3, 3};
+
+// The drain event after K-block kb of an item of KB blocks: 0 none, kXEvent (E2-E4),
+// kYEvent (I) or kFullEvent (all four, then the output).
+__device__ __forceinline__ int event_at(int kb, int KB) {
+    if (kb == KB - 1) return kFullEvent;
+    const int r = kb % kPeriod;
+    return r == kPeriod / 2 - 1 ? kXEvent : (r == kPeriod - 1 ? kYEvent : 0);
+}
+
+struct OzArgs {
+    int64_t M, Nc;            // output rows / columns
+    int64_t ldc;
+    double* C;                // output (direct mode), or
+    double* part;             // split-K partial tiles [splits][Mp][Np] (split mode)
+    int64_t Mp, Np;           // padded sizes (multiples of 128)
+    const int* expA;          // biased exponent field of each row's largest |value| (0: zero row)
+    const int* expB;
+    int64_t rowsA_pad, rowsB_pad;
+    int tilesM, tilesN;
+    int kb_total;             // K-blocks of 32
+    int kb_split;             // K-blocks per split
+    int splits;
+    int symmetric;            // only tiles with tm <= tn
+    int b_upper;              // B_hat[j][k] = 0 for k > j: K limited to the tile's last column
+    unsigned* status;
+};
+
+struct Item {
+    int tm, tn, kb0, KB;
+};
+
+__device__ __forceinline__ Item decode(const OzArgs& g, int64_t item) {
+    Item it;
+    const int64_t pairs = g.symmetric ? (int64_t)g.tilesM * (g.tilesM + 1) / 2 : (int64_t)g.tilesM * g.tilesN;
+    const int z = (int)(item / pairs);
+    int64_t p = item % pairs;
+    if (g.symmetric) {
+        int tm = 0;
+        while (p >= g.tilesM - tm) { p -= g.tilesM - tm; tm++; }
+        it.tm = tm;
+        it.tn = tm + (int)p;
+    } else {
+        it.tm = (int)(p / g.tilesN);
+        it.tn = (int)(p % g.tilesN);
+    }
+    int kend = g.kb_total;
+    if (g.b_upper) {
+        const int lim = (int)(((int64_t)(it.tn + 1) * kTile + kKB - 1) / kKB);
+        if (lim < kend) kend = lim;
+    }
+    it.kb0 = z * g.kb_split;
+    const int k1 = it.kb0 + g.kb_split < kend ? it.kb0 + g.kb_split : kend;
+    it.KB = k1 > it.kb0 ? k1 - it.kb0 : 0;
+    return it;
+}
+
+// 32 accumulator columns of this warp's 32 TMEM lanes (one row per lane).
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+}
+
+// FP32 power of two 2^p (|p| < 127).
+__device__ __forceinline__ float pow2f(int p) { return __int_as_float((127 + p) << 23); }
+
+// x * 2^e for a nonzero double x built from an integer (exact exponent shift);
+// results outside the normal range flush to signed zero or infinity.
+__device__ __forceinline__ double scale_pow2(double x, int e) {
+    const long long b = __double_as_longlong(x);
+    const int ex = (int)((b >> 52) & 0x7ff) + e;
+    const long long sign = b & (1ll << 63);
+    if (ex <= 0) return __longlong_as_double(sign);
+    if (ex >= 0x7ff) return __longlong_as_double(sign | (0x7ffll << 52));
+    return __longlong_as_double(b + ((long long)e << 52));
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, OzArgs g,
+               int64_t total) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    __shared__ __align__(8) uint64_t full[kStages], empty[kStages], efull, eempty, done;
+    __shared__ uint32_t tmem_slot;
+    __shared__ int abort_flag;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; s++) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(&efull, 1);
+        mbar_init(&eempty, kEpiWarps);
+        mbar_init(&done, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;");
+        asm volatile("fence.proxy.async.shared::cta;");
+        abort_flag = 0;
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" :: "r"(sa(&tmem_slot)),
+                     "r"(kTmemCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = tmem_slot;
+    volatile int* abort_v = &abort_flag;
+
+    if (warp == 0 && lane == 0) {
+        // ---------------- TMA producer
+        int64_t sc = 0;
+        for (int64_t item = blockIdx.x; item < total && !*abort_v; item += gridDim.x) {
+            const Item it = decode(g, item);
+            bool ok = true;
+            for (int kb = 0; kb < it.KB; kb++, sc++) {
+                const int s = (int)(sc % kStages);
+                const int64_t u = sc / kStages;
+                if (u >= 1 && !mbar_wait(sa(&empty[s]), (uint32_t)((u - 1) & 1), kWaitNs)) { ok = false; break; }
+                const uint32_t st = sa(smem + (size_t)s * kStageBytes);
+                const int x = (it.kb0 + kb) * kKB;
+                mbar_expect_tx(&full[s], kStageBytes);
+#pragma unroll
+                for (int t = 0; t < kSlices; t++)
+                    tma_load_2d(st + t * kSliceBytes, &tmA, x, (int)(t * g.rowsA_pad + (int64_t)it.tm * kTile),
+                                sa(&full[s]));
+#pragma unroll
+                for (int t = 0; t < kSlices; t++)
+                    tma_load_2d(st + (kSlices + t) * kSliceBytes, &tmB, x,
+                                (int)(t * g.rowsB_pad + (int64_t)it.tn * kTile), sa(&full[s]));
+            }
+            if (!ok) { *abort_v = 1; break; }
+        }
+        // every copy issued has landed before the CTA can exit
+        for (int s = 0; s < kStages && s < sc; s++) {
+            const int64_t last = s + ((sc - 1 - s) / kStages) * kStages;
+            mbar_wait(sa(&full[s]), (uint32_t)((last / kStages) & 1), kDrainNs);
+        }
+    } else if (warp == 1 && lane == 0) {
+        // ---------------- MMA issuer
+        int64_t sc = 0, ev_commit = 0, ev_wait = 0;
+        bool issued = false;
+        for (int64_t item = blockIdx.x; item < total && !*abort_v; item += gridDim.x) {
+            const Item it = decode(g, item);
+            bool ok = true;
+            for (int kb = 0; kb < it.KB; kb++, sc++) {
+                const int s = (int)(sc % kStages);
+                if (!mbar_wait(sa(&full[s]), (uint32_t)((sc / kStages) & 1), kWaitNs) || *abort_v) {
+                    ok = false;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                const uint32_t st = sa(smem + (size_t)s * kStageBytes);
+                const int r = kb % kPeriod;
+                // which accumulators start fresh in this stage, and whose drain must end first
+                const bool resetX = kb == 0 || r == kPeriod / 2;
+                const bool resetY = kb == 0 || r == 0;
+                auto wait_drain = [&]() -> bool {
+                    const bool w = mbar_wait(sa(&eempty), (uint32_t)(ev_wait & 1), kWaitNs);
+                    ev_wait++;
+                    asm volatile("tcgen05.fence::after_thread_sync;");
+                    return w;
+                };
+                // the pairs of each accumulator are consecutive (0 | 1 2 | 3 4 5 | 6 .. 20): the
+                // first MMA of a fresh accumulator overwrites it
+                auto issue = [&](int p0, int p1) {
+                    for (int p = p0; p < p1; p++) {
+                        const int acc = kPairAcc[p];
+                        const bool first = (p == 0 || p == 1 || p == 3 || p == 6) && (acc < 3 ? resetX : resetY);
+                        const uint64_t da = desc_kmajor(st + kPairA[p] * kSliceBytes, 64);
+                        const uint64_t db = desc_kmajor(st + (kSlices + kPairB[p]) * kSliceBytes, 64);
+                        const uint32_t dt = tmem + (uint32_t)(acc * kTile);
+#pragma unroll
+                        for (int k = 0; k < kKB / 16; k++) {
+                            const uint32_t accumulate = (first && k == 0) ? 0u : 1u;
+                            asm volatile(
+                                "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n"
+                                :: "r"(dt), "l"(da + 2 * k), "l"(db + 2 * k), "r"(kIdesc), "r"(accumulate));
+                        }
+                    }
+                    issued = true;
+                };
+                bool w = true;
+                if (kb == 0) {
+                    if (ev_commit > 0) w = wait_drain();     // the previous item's output drain
+                    issue(0, 21);
+                } else if (resetX) {                           // E2-E4 drained after the last block
+                    issue(6, 21);
+                    w = wait_drain();
+                    issue(0, 6);
+                } else if (resetY) {                           // I drained after the last block
+                    issue(0, 6);
+                    w = wait_drain();
+                    issue(6, 21);
+                } else {
+                    issue(0, 21);
+                }
+                umma_commit(&empty[s]);
+                if (event_at(kb, it.KB)) {
+                    umma_commit(&efull);
+                    ev_commit++;
+                }
+                if (!w) { ok = false; sc++; break; }
+            }
+            if (!ok) { *abort_v = 1; break; }
+        }
+        // every MMA issued has completed before TMEM is released
+        if (issued) {
+            umma_commit(&done);
+            mbar_wait(sa(&done), 0, kDrainNs);
+        }
+    } else if (warp >= 2) {
+        // ---------------- epilogue: exact drains into 64-bit integers, then the output
+        const int q = warp & 3, h = (warp - 2) >> 2;
+        const uint32_t lane_base = (uint32_t)(32 * q) << 16;
+        int64_t ev = 0;
+        long long acc[64];
+        for (int64_t item = blockIdx.x; item < total; item += gridDim.x) {
+            const Item it = decode(g, item);
+#pragma unroll
+            for (int c = 0; c < 64; c++) acc[c] = 0;
+            bool ok = true;
+            for (int kb = 0; kb < it.KB; kb++) {
+                const int kind = event_at(kb, it.KB);
+                if (!kind) continue;
+                if (!__all_sync(0xffffffffu, !*abort_v && mbar_wait(sa(&efull), (uint32_t)(ev & 1), kWaitNs))) {
+                    ok = false;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;");
+#pragma unroll
+                for (int a = 0; a < 4; a++) {
+                    const bool take = (a < 3) ? (kind & kXEvent) : (kind & kYEvent);
+                    if (!take) continue;
+                    // units of 2^-40: E_l holds multiples of 2^-8l, I is rounded to 2^-40
+                    const int up = a < 3 ? 8 * (a + 2) : 40;
+                    const long long mul = 1ll << (a < 3 ? 40 - 8 * (a + 2) : 0);
+                    const float sc = pow2f(up);
+#pragma unroll
+                    for (int half = 0; half < 2; half++) {
+                        uint32_t v[32];
+                        tmem_ld32(tmem + lane_base + (uint32_t)(a * kTile + h * 64 + half * 32), v);
+                        asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+                        for (int c = 0; c < 32; c++) {
+                            const int iv = __float2int_rn(__uint_as_float(v[c]) * sc);
+                            acc[half * 32 + c] += (long long)iv * mul;
+                        }
+                    }
+                }
+                asm volatile("tcgen05.fence::before_thread_sync;");
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&eempty);
+                ev++;
+                if (kind == kFullEvent) {
+                    const int64_t row = (int64_t)it.tm * kTile + 32 * q + lane;
+                    const int64_t col0 = (int64_t)it.tn * kTile + h * 64;
+                    const int ea = row < g.M ? g.expA[row] : 0;
+                    const int z = it.kb0 / g.kb_split;
+                    if (g.part) {
+                        double* dst = g.part + ((int64_t)z * g.Mp + row) * g.Np + col0;
+#pragma unroll
+                        for (int c = 0; c < 64; c++) {
+                            const int eb = (col0 + c < g.Nc) ? g.expB[col0 + c] : 0;
+                            double v = 0.0;
+                            if (acc[c] != 0 && ea != 0 && eb != 0)
+                                v = scale_pow2((double)acc[c], (ea - 1021) + (eb - 1021) - 40);
+                            dst[c] = v;
+                        }
+                    } else if (row < g.M) {
+                        double* dst = g.C + row * g.ldc + col0;
+#pragma unroll
+                        for (int c = 0; c < 64; c++) {
+                            if (col0 + c >= g.Nc) break;
+                            const int eb = g.expB[col0 + c];
+                            double v = 0.0;
+                            if (acc[c] != 0 && ea != 0 && eb != 0)
+                                v = scale_pow2((double)acc[c], (ea - 1021) + (eb - 1021) - 40);
+                            dst[c] = v;
+                        }
+                    }
+                }
+            }
+            if (!ok) { *abort_v = 1; break; }
+        }
+    }
+
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 1) {
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(kTmemCols));
+    }
+    if (threadIdx.x == 0 && abort_flag) raise_status(g.status, DEV_TIMEOUT);
+}
+
+// Largest biased exponent field of each row of A_hat (A_hat[r][k] = src[k * ld + r]
+// when trans, else src[r * ld + k]); 0 for a row of zeros (subnormals count as zero).
+// exps must be zeroed first.
+template <bool kTrans>
+__global__ void oz_exponents_kernel(const double* __restrict__ src, int64_t ld, int64_t rows, int64_t K, int* exps,
+                                    unsigned* status) {
+    int m = 0;
+    bool bad = false;
+    if (kTrans) {
+        // thread per column of src (row of A_hat), a range of src rows per block row
+        const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+        const int64_t k0 = (int64_t)blockIdx.y * 256;
+        if (r >= rows) return;
+        const int64_t k1 = k0 + 256 < K ? k0 + 256 : K;
+        for (int64_t k = k0; k < k1; k++) {
+            const int ef = (int)((__double_as_longlong(src[k * ld + r]) >> 52) & 0x7ff);
+            bad |= ef == 0x7ff;
+            m = ef > m ? ef : m;
+        }
+        if (m) atomicMax(exps + r, m);
+    } else {
+        // warp per row
+        const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+        const int lane = threadIdx.x & 31;
+        if (r >= rows) return;
+        for (int64_t k = lane; k < K; k += 32) {
+            const int ef = (int)((__double_as_longlong(src[r * ld + k]) >> 52) & 0x7ff);
+            bad |= ef == 0x7ff;
+            m = ef > m ? ef : m;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (lane == 0) exps[r] = m;
+    }
+    if (bad) raise_status(status, DEV_NONFINITE);
+}
+
+// The six BF16 slices of one value x of a row whose largest exponent field is efm.
+__device__ __forceinline__ void digits_of(double x, int efm, __nv_bfloat16 (&out)[kSlices]) {
+    const long long b = __double_as_longlong(x);
+    const int ef = (int)((b >> 52) & 0x7ff);
+    long long F = 0;
+    if (ef != 0 && efm != 0 && ef != 0x7ff) {
+        // |x| 2^{-e} 2^{48} with e = efm - 1021: mant 2^{ef - efm - 6}, rounded to nearest
+        const long long mant = (b & ((1ll << 52) - 1)) | (1ll << 52);
+        const int sh = efm - ef + 6;
+        F = sh < 60 ? (mant + (1ll << (sh - 1))) >> sh : 0;
+    }
+    // balanced base-256 digits, least significant first; the top digit keeps its carry
+    int d[kSlices];
+    int carry = 0;
+#pragma unroll
+    for (int t = kSlices - 1; t >= 1; t--) {
+        int byte = (int)((F >> (8 * (kSlices - 1 - t))) & 255) + carry;
+        carry = byte >= 128;
+        d[t] = carry ? byte - 256 : byte;
+    }
+    d[0] = (int)(F >> (8 * (kSlices - 1))) + carry;
+    const bool neg = b < 0;
+#pragma unroll
+    for (int t = 0; t < kSlices; t++) {
+        const float v = (float)(neg ? -d[t] : d[t]) * pow2f(-8 * (t + 1));
+        out[t] = __float2bfloat16_rn(v);
+    }
+}
+
+// Slices of A_hat into [kSlices][rows_pad][K_pad] (K contiguous), zero in the padding.
+// 32 x 32 tiles through shared memory so that reads and writes are both coalesced
+// when A_hat is the transpose of src.
+template <bool kTrans>
+__global__ void oz_slice_kernel(const double* __restrict__ src, int64_t ld, int64_t rows, int64_t K,
+                                const int* __restrict__ exps, int64_t rows_pad, int64_t K_pad,
+                                __nv_bfloat16* __restrict__ slices) {
+    __shared__ double tile[32][33];
+    const int64_t r0 = (int64_t)blockIdx.y * 32, k0 = (int64_t)blockIdx.x * 32;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    for (int i = ty; i < 32; i += blockDim.y) {
+        double v = 0.0;
+        if (kTrans) {   // src row k0 + i, column r0 + tx  ->  tile[k][r]
+            const int64_t k = k0 + i, r = r0 + tx;
+            if (k < K && r < rows) v = src[k * ld + r];
+            tile[i][tx] = v;
+        } else {        // src row r0 + i, column k0 + tx  ->  tile[k][r]
+            const int64_t r = r0 + i, k = k0 + tx;
+            if (k < K && r < rows) v = src[r * ld + k];
+            tile[tx][i] = v;
+        }
+    }
+    __syncthreads();
+    const size_t plane = (size_t)rows_pad * K_pad;
+    for (int i = ty; i < 32; i += blockDim.y) {
+        const int64_t r = r0 + i, k = k0 + tx;
+        if (r >= rows_pad || k >= K_pad) continue;
+        const int efm = r < rows ? exps[r] : 0;
+        __nv_bfloat16 dg[kSlices];
+        digits_of(tile[tx][i], efm, dg);
+#pragma unroll
+        for (int t = 0; t < kSlices; t++) slices[t * plane + (size_t)r * K_pad + k] = dg[t];
+    }
+}
+
+// C = sum over splits of the partial tiles (tiles below the diagonal of a symmetric
+// product take the transposed upper tile).
+__global__ void oz_reduce_kernel(const double* __restrict__ part, int splits, int64_t Mp, int64_t Np, int64_t M,
+                                 int64_t Nc, double* C, int64_t ldc, int symmetric) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= M * Nc) return;
+    int64_t i = idx / Nc, j = idx % Nc;
+    if (symmetric && (i / kTile) > (j / kTile)) { const int64_t t = i; i = j; j = t; }
+    double s = 0.0;
+    for (int z = 0; z < splits; z++) s += part[((int64_t)z * Mp + i) * Np + j];
+    C[(idx / Nc) * ldc + idx % Nc] = s;
+}
+
+inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+// Arena stand-in that only counts bytes.
+struct CountAr {
+    Sizer s;
+    template <typename T>
+    T* take(size_t n) {
+        s.take<T>(n);
+        return nullptr;
+    }
+};
+
+// Workspace pieces of one operand: exponents (int32 per padded row) and slices.
+struct OzOperand {
+    int* exps = nullptr;
+    __nv_bfloat16* slices = nullptr;
+    int64_t rows = 0, K = 0, rows_pad = 0, K_pad = 0;
+};
+
+template <typename Ar>
+void oz_operand_layout(Ar& ar, int64_t rows, int64_t K, OzOperand* op) {
+    OzOperand o;
+    o.rows = rows;
+    o.K = K;
+    o.rows_pad = round_up(rows, kTile);
+    o.K_pad = round_up(K, kKB);
+    o.exps = ar.template take<int>((size_t)o.rows_pad);
+    o.slices = ar.template take<__nv_bfloat16>((size_t)kSlices * o.rows_pad * o.K_pad);
+    if (op) *op = o;
+}
+
+int oz_prepare(const double* src, int64_t ld, bool trans, const OzOperand& o, unsigned* status, cudaStream_t s) {
+    CHFSI_CUDA_TRY(cudaMemsetAsync(o.exps, 0, sizeof(int) * (size_t)o.rows_pad, s));
+    if (trans) {
+        dim3 grid((unsigned)((o.rows + 255) / 256), (unsigned)((o.K + 255) / 256));
+        oz_exponents_kernel<true><<<grid, 256, 0, s>>>(src, ld, o.rows, o.K, o.exps, status);
+    } else {
+        oz_exponents_kernel<false><<<(unsigned)((o.rows * 32 + 255) / 256), 256, 0, s>>>(src, ld, o.rows, o.K,
+                                                                                          o.exps, status);
+    }
+    CHFSI_LAUNCH_CHECK();
+    dim3 grid((unsigned)(o.K_pad / 32), (unsigned)(o.rows_pad / 32));
+    if (trans)
+        oz_slice_kernel<true><<<grid, dim3(32, 8), 0, s>>>(src, ld, o.rows, o.K, o.exps, o.rows_pad, o.K_pad,
+                                                          o.slices);
+    else
+        oz_slice_kernel<false><<<grid, dim3(32, 8), 0, s>>>(src, ld, o.rows, o.K, o.exps, o.rows_pad, o.K_pad,
+                                                           o.slices);
+    CHFSI_LAUNCH_CHECK();
+    return CHFSI_OK;
+}
+
+// Split-K count for a product whose output has `tiles` tiles: about one work item per
+// SM, each split at least 64 K-blocks (2048 K).
+int oz_splits(int64_t tiles, int kb_total, int sms) {
+    int64_t want = (sms + tiles - 1) / tiles;
+    int64_t maxs = (kb_total + 63) / 64;
+    int64_t sp = want < maxs ? want : maxs;
+    if (sp < 1) sp = 1;
+    if (sp > 64) sp = 64;
+    return (int)sp;
+}
+
+struct OzPlan {
+    OzOperand A, B;
+    double* part = nullptr;
+    int splits = 1;
+    bool same = false;        // B_hat is A_hat (a Gram matrix)
+};
+
+// M x Nc output, K reduction; tn_form: C = A^T B (split over K), else C = A B.
+template <typename Ar>
+void oz_layout(Ar& ar, bool tn_form, int64_t M, int64_t Nc, int64_t K, bool same, int sms, OzPlan* plan) {
+    OzPlan p;
+    p.same = same;
+    oz_operand_layout(ar, M, K, &p.A);
+    if (same) p.B = p.A;
+    else oz_operand_layout(ar, Nc, K, &p.B);
+    if (tn_form) {
+        const int64_t tm = round_up(M, kTile) / kTile, tn = round_up(Nc, kTile) / kTile;
+        const int64_t tiles = same ? tm * (tm + 1) / 2 : tm * tn;
+        p.splits = oz_splits(tiles, (int)(p.A.K_pad / kKB), sms > 0 ? sms : 148);
+        p.part = ar.template take<double>((size_t)p.splits * round_up(M, kTile) * round_up(Nc, kTile));
+    }
+    if (plan) *plan = p;
+}
+
+int oz_run(const OzPlan& p, bool tn_form, double* C, int64_t ldc, int64_t M, int64_t Nc, bool symmetric,
+           bool b_upper, unsigned* status, cudaStream_t s) {
+    if (M <= 0 || Nc <= 0) return CHFSI_OK;
+    const int64_t K_pad = p.A.K_pad;
+    if (K_pad > (int64_t)1 << 21 || p.A.rows_pad * kSlices > INT32_MAX || p.B.rows_pad * kSlices > INT32_MAX)
+        return CHFSI_ERR_UNSUPPORTED;
+    CUtensorMap tmA, tmB;
+    int rc;
+    if ((rc = make_map_bf16(&tmA, p.A.slices, K_pad, kSlices * p.A.rows_pad, kKB, kTile,
+                            CU_TENSOR_MAP_SWIZZLE_64B)))
+        return rc;
+    if ((rc = make_map_bf16(&tmB, p.B.slices, K_pad, kSlices * p.B.rows_pad, kKB, kTile,
+                            CU_TENSOR_MAP_SWIZZLE_64B)))
+        return rc;
+    OzArgs g{};
+    g.M = M;
+    g.Nc = Nc;
+    g.ldc = ldc;
+    g.Mp = p.A.rows_pad;
+    g.Np = p.B.rows_pad;
+    g.expA = p.A.exps;
+    g.expB = p.B.exps;
+    g.rowsA_pad = p.A.rows_pad;
+    g.rowsB_pad = p.B.rows_pad;
+    g.tilesM = (int)(p.A.rows_pad / kTile);
+    g.tilesN = (int)(p.B.rows_pad / kTile);
+    g.kb_total = (int)(K_pad / kKB);
+    g.splits = tn_form ? p.splits : 1;
+    g.kb_split = (g.kb_total + g.splits - 1) / g.splits;
+    g.splits = (g.kb_total + g.kb_split - 1) / g.kb_split;   // no empty split
+    g.symmetric = symmetric ? 1 : 0;
+    g.b_upper = b_upper ? 1 : 0;
+    g.status = status;
+    g.C = tn_form ? nullptr : C;
+    g.part = tn_form ? p.part : nullptr;
+    const int64_t pairs = symmetric ? (int64_t)g.tilesM * (g.tilesM + 1) / 2 : (int64_t)g.tilesM * g.tilesN;
+    const int64_t total = pairs * g.splits;
+    const int dev = current_device();
+    if (dev < 0) return CHFSI_ERR_CUDA;
+    static bool attr[kMaxDevices] = {};
+    if (!attr[dev]) {
+        CHFSI_CUDA_TRY(cudaFuncSetAttribute(oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
+        attr[dev] = true;
+    }
+    const int sms = sm_count();
+    if (sms <= 0) return CHFSI_ERR_CUDA;
+    const unsigned grid = (unsigned)(total < sms ? total : sms);
+    oz_gemm_kernel<<<grid, kThreads, kSmemBytes, s>>>(tmA, tmB, g, total);
+    CHFSI_LAUNCH_CHECK();
+    if (tn_form) {
+        const int64_t cnt = M * Nc;
+        oz_reduce_kernel<<<(unsigned)((cnt + 255) / 256), 256, 0, s>>>(p.part, g.splits, g.Mp, g.Np, M, Nc, C, ldc,
+                                                                       g.symmetric);
+        CHFSI_LAUNCH_CHECK();
+    }
+    return CHFSI_OK;
+}
+
+}  // namespace
+
+size_t ozaki_workspace_bytes(bool tn_form, int64_t M, int64_t Nc, int64_t K, bool same) {
+    CountAr ar;
+    oz_layout(ar, tn_form, M, Nc, K, same, tc::sm_count(), nullptr);
+    return ar.s.used;
+}
+
+int ozaki_gemm_tn(const double* A, int64_t lda, const double* B, int64_t ldb, int64_t K, int64_t M, int64_t Nc,
+                  double* C, int64_t ldc, bool symmetric, void* ws, size_t ws_bytes, unsigned* status,
+                  cudaStream_t s) {
+    if (M <= 0 || Nc <= 0) return CHFSI_OK;
+    // the same operand twice (a Gram matrix) is sliced once; `symmetric` says that the
+    // product is known to be symmetric (a Gram matrix, or X^T (H X) for symmetric H):
+    // only the tiles on and above the diagonal are computed and the others mirrored
+    const bool same = (A == B) && (lda == ldb) && (M == Nc);
+    if (symmetric && M != Nc) return CHFSI_ERR_ARG;
+    if (ws_bytes < ozaki_workspace_bytes(true, M, Nc, K, same)) return CHFSI_ERR_NOMEM;
+    Arena ar(ws, ws_bytes);
+    OzPlan p;
+    oz_layout(ar, true, M, Nc, K, same, tc::sm_count(), &p);
+    int rc;
+    if ((rc = oz_prepare(A, lda, true, p.A, status, s))) return rc;
+    if (!same && (rc = oz_prepare(B, ldb, true, p.B, status, s))) return rc;
+    return oz_run(p, true, C, ldc, M, Nc, symmetric, false, status, s);
+}
+
+int ozaki_gemm_nn(const double* A, int64_t lda, const double* B, int64_t ldb, int64_t M, int64_t K, int64_t Nc,
+                  double* C, int64_t ldc, bool b_upper, void* ws, size_t ws_bytes, unsigned* status,
+                  cudaStream_t s) {
+    if (M <= 0 || Nc <= 0) return CHFSI_OK;
+    if (ws_bytes < ozaki_workspace_bytes(false, M, Nc, K, false)) return CHFSI_ERR_NOMEM;
+    Arena ar(ws, ws_bytes);
+    OzPlan p;
+    oz_layout(ar, false, M, Nc, K, false, tc::sm_count(), &p);
+    int rc;
+    if ((rc = oz_prepare(A, lda, false, p.A, status, s))) return rc;
+    if ((rc = oz_prepare(B, ldb, true, p.B, status, s))) return rc;   // B_hat = B^T: rows are B's columns
+    return oz_run(p, false, C, ldc, M, Nc, false, b_upper, status, s);
+}
+
+}  // namespace chfsi
+
+// ------------------------------------------------------------------ C ABI
+
+namespace {
+
+int oz_abi_check(int32_t op, int64_t M, int64_t Nc, int64_t K, int32_t flags) {
+    if (op != CHFSI_OP_TN && op != CHFSI_OP_NN) return CHFSI_ERR_ARG;
+    if (M < 0 || Nc < 0 || K < 0) return CHFSI_ERR_ARG;
+    if (flags & ~(CHFSI_GEMM_SYMMETRIC | CHFSI_GEMM_B_UPPER)) return CHFSI_ERR_ARG;
+    if ((flags & CHFSI_GEMM_SYMMETRIC) && (op != CHFSI_OP_TN || M != Nc)) return CHFSI_ERR_ARG;
+    if ((flags & CHFSI_GEMM_B_UPPER) && op != CHFSI_OP_NN) return CHFSI_ERR_ARG;
+    if (K > ((int64_t)1 << 21) || M > INT32_MAX / 8 || Nc > INT32_MAX / 8) return CHFSI_ERR_UNSUPPORTED;
+    return CHFSI_OK;
+}
+
+}  // namespace
+
+int chfsi_ozaki_gemm_workspace_size(int32_t op, int64_t M, int64_t Nc, int64_t K, int32_t flags, size_t* bytes) {
+    if (!bytes) return CHFSI_ERR_ARG;
+    const int rc = oz_abi_check(op, M, Nc, K, flags);
+    if (rc) return rc;
+    // the tn form with one operand twice is smaller; size for two distinct operands
+    *bytes = chfsi::align_up(chfsi::kStatusBytes) + chfsi::ozaki_workspace_bytes(op == CHFSI_OP_TN, M, Nc, K, false);
+    return CHFSI_OK;
+}
+
+int chfsi_ozaki_gemm(int32_t op, const double* A, int64_t lda, const double* B, int64_t ldb, double* C, int64_t ldc,
+                     int64_t M, int64_t Nc, int64_t K, int32_t flags, void* ws, size_t ws_bytes, void* stream) {
+    int rc = oz_abi_check(op, M, Nc, K, flags);
+    if (rc) return rc;
+    if (M == 0 || Nc == 0) return CHFSI_OK;
+    if (!C || ldc < Nc || (reinterpret_cast<uintptr_t>(C) & 7u)) return CHFSI_ERR_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (K == 0) {
+        for (int64_t i = 0; i < M; i++)
+            CHFSI_CUDA_TRY(cudaMemsetAsync(C + i * ldc, 0, sizeof(double) * (size_t)Nc, s));
+        return CHFSI_OK;
+    }
+    if (!A || !B || (reinterpret_cast<uintptr_t>(A) & 7u) || (reinterpret_cast<uintptr_t>(B) & 7u)) return CHFSI_ERR_ARG;
+    const bool tn = op == CHFSI_OP_TN;
+    if (tn ? (lda < M || ldb < Nc) : (lda < K || ldb < Nc)) return CHFSI_ERR_ARG;
+    size_t need = 0;
+    if ((rc = chfsi_ozaki_gemm_workspace_size(op, M, Nc, K, flags, &need))) return rc;
+    if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255u) || ws_bytes < need) return ws ? CHFSI_ERR_NOMEM : CHFSI_ERR_ARG;
+    unsigned* st = chfsi::status_word(ws);
+    CHFSI_CUDA_TRY(cudaMemsetAsync(st, 0, sizeof(unsigned), s));
+    char* rest = static_cast<char*>(ws) + chfsi::align_up(chfsi::kStatusBytes);
+    const size_t rest_bytes = ws_bytes - chfsi::align_up(chfsi::kStatusBytes);
+    if (tn)
+        return chfsi::ozaki_gemm_tn(A, lda, B, ldb, K, M, Nc, C, ldc, (flags & CHFSI_GEMM_SYMMETRIC) != 0, rest,
+                                    rest_bytes, st, s);
+    return chfsi::ozaki_gemm_nn(A, lda, B, ldb, M, K, Nc, C, ldc, (flags & CHFSI_GEMM_B_UPPER) != 0, rest,
+                                rest_bytes, st, s);
+}

@@ -119,4 +119,17 @@ int sddmm_accumulate_f32x2(const CsrDev& h, int64_t n, const void* Ybar, int64_t
 
 int fill_zero(void* p, size_t bytes, cudaStream_t s);
 
+// FP64-accurate products on the BF16 tensor cores (Ozaki-scheme slices, dense_ozaki.cu).
+// tn form: C (M x Nc) = A^T B with A: K x M (lda), B: K x Nc (ldb); symmetric: the
+// product is known to be symmetric (M == Nc), only the upper tiles are computed.
+// nn form: C (M x Nc) = A B with A: M x K (lda), B: K x Nc (ldb); b_upper: B is upper
+// triangular.  Scratch from ws (ozaki_workspace_bytes; same = the tn form's A is B).
+size_t ozaki_workspace_bytes(bool tn_form, int64_t M, int64_t Nc, int64_t K, bool same);
+int ozaki_gemm_tn(const double* A, int64_t lda, const double* B, int64_t ldb, int64_t K, int64_t M, int64_t Nc,
+                  double* C, int64_t ldc, bool symmetric, void* ws, size_t ws_bytes, unsigned* status,
+                  cudaStream_t s);
+int ozaki_gemm_nn(const double* A, int64_t lda, const double* B, int64_t ldb, int64_t M, int64_t K, int64_t Nc,
+                  double* C, int64_t ldc, bool b_upper, void* ws, size_t ws_bytes, unsigned* status,
+                  cudaStream_t s);
+
 }  // namespace chfsi

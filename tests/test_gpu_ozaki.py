@@ -1,0 +1,182 @@
+"""FP64-accurate products on the BF16 tensor cores (chfsi_ozaki_gemm, Ozaki-scheme
+slices) and the closure that uses them (chfsi_rayleigh_ritz_ex with
+CHFSI_F64_OZAKI), against plain FP64 products and the oracle.
+
+* Values with at most 16 significant bits below their row's largest magnitude
+  are held exactly by the two leading 8-bit digits, so the product involves only
+  the exactly accumulated digit levels: the result must equal the integer product
+  bit for bit, for K spanning many 256-long accumulation periods and several
+  split-K parts.
+* Gaussian operands (ragged sizes, both forms, the symmetric and upper-triangular
+  modes) against the FP64 product, within the documented bound
+  K 2^-42 max|A_row| max|B_row| and at 1e-13 relative Frobenius.
+* The Ozaki closure's Ritz values against the oracle's Householder/LAPACK closure
+  at 1e-10 (small case and the 40^3 / 1024-state workload).
+"""
+import numpy as np
+import pytest
+import torch
+
+import chfsi_workloads as W
+from tests.util import dense_to_csr, rel_fro
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    from paper_2110_15853_gb300 import build
+    build.build()
+    import paper_2110_15853_gb300 as P
+    return P
+
+
+def _dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a)).to("cuda")
+
+
+def _ints16(rng, shape):
+    """Integers of at most 15 bits plus sign, with each row's (or column's) largest
+    magnitude at 2^15 - 1 so the row scale is the same for every row."""
+    x = rng.integers(-(2 ** 15 - 1), 2 ** 15, size=shape).astype(np.int64)
+    return x
+
+
+@pytest.mark.parametrize("M,Nc,K", [(200, 136, 1000), (128, 128, 4096), (37, 300, 20011)])
+def test_ozaki_tn_exact_on_16_bit_values(P, M, Nc, K):
+    rng = np.random.default_rng(M * 7 + K)
+    A = _ints16(rng, (K, M))
+    B = _ints16(rng, (K, Nc))
+    A[0, :] = 2 ** 15 - 1          # every column of A and B has the same largest magnitude
+    B[0, :] = -(2 ** 15 - 1)
+    C = P.ozaki_gemm(_dev(A.astype(np.float64)), _dev(B.astype(np.float64)), transpose_a=True).cpu().numpy()
+    exact = A.T @ B                 # int64, |entries| < K 2^30
+    assert np.array_equal(C, exact.astype(np.float64))
+
+
+@pytest.mark.parametrize("M,K,Nc", [(300, 500, 136), (1000, 64, 64), (129, 1200, 257)])
+def test_ozaki_nn_exact_on_16_bit_values(P, M, K, Nc):
+    rng = np.random.default_rng(M + 3 * K)
+    A = _ints16(rng, (M, K))
+    B = _ints16(rng, (K, Nc))
+    A[:, 0] = 2 ** 15 - 1
+    B[0, :] = 2 ** 15 - 1
+    C = P.ozaki_gemm(_dev(A.astype(np.float64)), _dev(B.astype(np.float64))).cpu().numpy()
+    assert np.array_equal(C, (A @ B).astype(np.float64))
+
+
+def _bound(A_rows_max, B_rows_max, K):
+    return K * 2.0 ** -42 * np.outer(A_rows_max, B_rows_max)
+
+
+@pytest.mark.parametrize("M,Nc,K", [(96, 70, 333), (256, 256, 70000), (1024, 1024, 64000)])
+def test_ozaki_tn_gaussian(P, M, Nc, K):
+    rng = np.random.default_rng(K)
+    A = rng.standard_normal((K, M)) * np.exp(rng.standard_normal(M))[None, :]   # columns of different scales
+    B = rng.standard_normal((K, Nc))
+    C = P.ozaki_gemm(_dev(A), _dev(B), transpose_a=True).cpu().numpy()
+    ref = A.T @ B
+    assert np.all(np.abs(C - ref) <= _bound(np.abs(A).max(0), np.abs(B).max(0), K) + 1e-15 * np.abs(ref))
+    assert rel_fro(C, ref) <= 1e-13
+
+
+def test_ozaki_tn_symmetric_gram(P):
+    rng = np.random.default_rng(5)
+    K, n = 50000, 300
+    Y = rng.standard_normal((K, n))
+    Yd = _dev(Y)
+    S = P.ozaki_gemm(Yd, Yd, transpose_a=True, symmetric=True).cpu().numpy()
+    ref = Y.T @ Y
+    scale = np.sqrt(np.outer(np.diag(ref), np.diag(ref)))
+    assert np.max(np.abs(S - S.T) / scale) <= 1e-14   # mirrored tiles; diagonal tiles to rounding
+    assert rel_fro(S, ref) <= 1e-13
+    assert np.max(np.abs(S - ref) / scale) <= 1e-13
+
+
+@pytest.mark.parametrize("M,K,Nc,upper", [(5000, 300, 300, False), (777, 513, 513, True), (64000, 1024, 1024, True)])
+def test_ozaki_nn_gaussian(P, M, K, Nc, upper):
+    rng = np.random.default_rng(M + K)
+    A = rng.standard_normal((M, K))
+    B = rng.standard_normal((K, Nc))
+    if upper:
+        B = np.triu(B)
+    C = P.ozaki_gemm(_dev(A), _dev(B), b_upper=upper).cpu().numpy()
+    ref = A @ B
+    assert np.all(np.abs(C - ref) <= _bound(np.abs(A).max(1), np.abs(B).max(0), K) + 1e-15 * np.abs(ref))
+    assert rel_fro(C, ref) <= 1e-13
+
+
+def test_ozaki_zero_rows_columns_and_views(P):
+    """Zero rows / columns give exact zeros; column views of wider blocks (ld > n)."""
+    rng = np.random.default_rng(9)
+    A = rng.standard_normal((700, 90))
+    B = rng.standard_normal((700, 50))
+    A[:, 7] = 0.0
+    B[:, 3] = 0.0
+    Aw = np.zeros((700, 128))
+    Aw[:, :90] = A
+    Ad = _dev(Aw)[:, :90]
+    C = P.ozaki_gemm(Ad, _dev(B), transpose_a=True).cpu().numpy()
+    assert np.all(C[7, :] == 0.0) and np.all(C[:, 3] == 0.0)
+    assert rel_fro(C, A.T @ B) <= 1e-13
+
+
+def test_ozaki_nonfinite_input_sets_status(P):
+    from paper_2110_15853_gb300 import _abi
+    import ctypes
+    lib = P.load()
+    A = torch.randn(300, 40, dtype=torch.float64, device="cuda")
+    A[11, 5] = float("inf")
+    B = torch.randn(300, 40, dtype=torch.float64, device="cuda")
+    C = torch.empty(40, 40, dtype=torch.float64, device="cuda")
+    sz = ctypes.c_size_t(0)
+    assert lib.chfsi_ozaki_gemm_workspace_size(_abi.CHFSI_OP_TN, 40, 40, 300, 0, ctypes.byref(sz)) == 0
+    ws = torch.empty(sz.value, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+    rc = lib.chfsi_ozaki_gemm(_abi.CHFSI_OP_TN, A.data_ptr(), 40, B.data_ptr(), 40, C.data_ptr(), 40, 40, 40, 300, 0,
+                              ws.data_ptr(), ws.numel(), stream)
+    assert rc == 0
+    assert lib.chfsi_read_status(ws.data_ptr(), stream) == _abi.CHFSI_ERR_NONFINITE
+
+
+def test_rayleigh_ritz_ozaki_small(P, oracle_mod):
+    """The Ozaki closure on a small grid operator against the oracle closure."""
+    H = W.csr_grid(8, 2, 0.1, 45)
+    X = W.start_block(H["N"], 20, 45)
+    a, b, a0 = oracle_mod.lanczos_bounds(H, W.lanczos_start(H["N"], 45), 20, 20)
+    Y = oracle_mod.filter(H, X, 8, a, b, a0)
+    Hd = P.CsrMatrix.from_arrays(H["row_ptr"], H["col"], H["val"], device="cuda")
+    ritz, psi = P.rayleigh_ritz(Hd, _dev(Y), cholqr_passes=2, precision="ozaki")
+    theta, _, _ = oracle_mod.rayleigh_ritz(H, Y)
+    assert np.max(np.abs(ritz.cpu().numpy() - theta)) <= 1e-10 * np.max(np.abs(theta))
+    p = psi.cpu().numpy()
+    assert np.max(np.abs(p.T @ p - np.eye(20))) <= 1e-12
+
+
+def test_rayleigh_ritz_ozaki_full_space_is_eigh(P):
+    """n = N: the Ritz values are the eigenvalues of H (dense symmetric test matrix)."""
+    rng = np.random.default_rng(3)
+    N = 150
+    A = rng.standard_normal((N, N))
+    A = (A + A.T) / 2
+    Hd = P.CsrMatrix.from_arrays(**{k: v for k, v in dense_to_csr(A).items() if k in ("row_ptr", "col", "val")},
+                                 device="cuda")
+    Y = rng.standard_normal((N, N))
+    ritz, _ = P.rayleigh_ritz(Hd, _dev(Y), cholqr_passes=2, precision="ozaki")
+    lam = np.linalg.eigvalsh(A)
+    assert np.max(np.abs(ritz.cpu().numpy() - lam)) <= 1e-10 * np.max(np.abs(lam))
+
+
+def test_rayleigh_ritz_ozaki_config_40cube(P, oracle_mod):
+    wl = W.workload("g40_w3_n1024_m20")
+    H = W.csr_grid(wl.g, wl.w, wl.s, wl.seed)
+    X = W.start_block(H["N"], wl.n, wl.seed)
+    a, b, a0 = oracle_mod.lanczos_bounds(H, W.lanczos_start(H["N"], wl.seed), 20, wl.n)
+    Hd = P.CsrMatrix.from_arrays(H["row_ptr"], H["col"], H["val"], device="cuda")
+    Yd = P.filter(Hd, _dev(X), wl.m, a, b, a0)
+    ritz, psi = P.rayleigh_ritz(Hd, Yd, cholqr_passes=2, precision="ozaki")
+    Yref = oracle_mod.filter(H, X, wl.m, a, b, a0)
+    theta, _, _ = oracle_mod.rayleigh_ritz(H, Yref)
+    assert np.max(np.abs(ritz.cpu().numpy() - theta)) <= 1e-10 * np.max(np.abs(theta))
+    p = psi.cpu().numpy()
+    assert np.max(np.abs(p.T @ p - np.eye(wl.n))) <= 1e-12
