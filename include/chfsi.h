@@ -291,19 +291,19 @@ int chfsi_ozaki_gemm_workspace_size(int32_t op, int64_t M, int64_t Nc, int64_t K
  * The closure's dense FP64 products (Algorithm 1 steps 2, 3 and 5: S = Y^T Y,
  * X_F = Y R^-1, H_F = X_F^T (H X_F), Psi = X_F Q) on the BF16 tensor cores, by
  * Ozaki-scheme splitting: each row of the K-major operands (A^T or A, and B^T) is
- * scaled by a power of two and rounded to a 48-bit fixed-point number held as six
- * balanced 8-bit digits, each digit slice exact in BF16; the 21 slice products
- * with digit weights down to 2^-56 run as tcgen05 MMAs whose FP32 accumulation is
- * exact (integer multiples, partial sums below 2^24, drained every 256 K into 64-bit
- * integers).  |C_ij - (A_hat B_hat^T)_ij| is below K 2^-42 times the product of the two
- * rows' largest magnitudes (48-bit rounding of each value, the dropped slice pairs and
- * the rounding of the shared accumulator of levels 5-7; errors of random sign make it
- * about sqrt(K) times that in practice).  Row-major blocks with leading dimensions; C
+ * scaled by a power of two and rounded to a 56-bit fixed-point number held as seven
+ * balanced 8-bit digits, each digit slice exact in BF16; the 28 slice products
+ * with digit weights down to 2^-64 run as tcgen05 MMAs whose FP32 accumulation is
+ * exact for the leading levels (integer multiples, partial sums below 2^24, drained
+ * every 256 K into 64-bit integers of unit 2^-48) and rounded to 2^-48 for the rest.
+ * |C_ij - (A_hat B_hat^T)_ij| is below K 2^-46 times the product of the two rows'
+ * largest magnitudes (errors of random sign make it about sqrt(K) times that in
+ * practice, about 2^-48 of a typical term).  Row-major blocks with leading dimensions; C
  * must not overlap A or B.  The workspace (chfsi_ozaki_gemm_workspace_size) holds
- * the status word, the slices (12 bytes per operand element) and the split-K
+ * the status word, the slices (14 bytes per operand element) and the split-K
  * partial tiles.  A non-finite input sets CHFSI_ERR_NONFINITE in the status word.
- * Errors: CHFSI_ERR_ARG, CHFSI_ERR_NOMEM, CHFSI_ERR_UNSUPPORTED (K above 2^21),
- * CHFSI_ERR_CUDA.  No counterpart in the paper, which runs these products with
+ * Errors: CHFSI_ERR_ARG, CHFSI_ERR_NOMEM, CHFSI_ERR_UNSUPPORTED (K above 2^21 in
+ * the TN form, above 8192 in the NN form), CHFSI_ERR_CUDA.  No counterpart in the paper, which runs these products with
  * FP64 cuBLAS (Sec. 4.3).
  */
 int chfsi_ozaki_gemm(int32_t op, const double* A, int64_t lda, const double* B, int64_t ldb, double* C,
@@ -344,7 +344,8 @@ int chfsi_clear_status(void* ws, void* stream);
  * device's FP64 (precision = CHFSI_F64: the DFMA pipe) or FP32 (CHFSI_F32: the
  * FFMA pipe), from a register-resident loop of independent multiply-adds over
  * 8 blocks of 256 threads per SM, timed with CUDA events on `stream` after one
- * untimed launch.  Synchronises `stream`.  The denominator of the roofline
+ * untimed launch (the fastest of three timed launches of about 70 ms of FP64 work
+ * each).  Synchronises `stream`.  The denominator of the roofline
  * fraction of the arithmetic-bound filter steps.  Diagnostics only: the paper
  * has no counterpart.  Errors: CHFSI_ERR_ARG (bad precision or NULL output),
  * CHFSI_ERR_CUDA.

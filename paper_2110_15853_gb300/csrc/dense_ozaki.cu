@@ -8,13 +8,14 @@
 // C = A^T B (Gram form) A_hat = A^T, B_hat = B^T; for C = A B, A_hat = A, B_hat =
 // B^T.  Each row r of an operand gets a power-of-two scale 2^{e_r} with
 // |A_hat[r][k]| 2^{-e_r} < 1/2 for all k, and the scaled value a is rounded to a
-// 48-bit fixed-point number and written as six balanced base-256 digits
-//     a = sum_{t=1..6} d_t 2^{-8t},   d_t integer, |d_t| <= 128,
+// 56-bit fixed-point number and written as seven balanced base-256 digits
+//     a = sum_{t=1..7} d_t 2^{-8t},   d_t integer, |d_t| <= 128,
 // (integer arithmetic on the FP64 bit pattern; no FP64 instructions).  Slice t
 // stores d_t 2^{-8t} in BF16, which is exact (8 significant bits).  Then
-//     C_ij = 2^{e_i + f_j} sum_{t + u <= 7} sum_k a_t[i][k] b_u[j][k]
-// keeps every digit product of weight 2^{-56} and above (21 slice pairs; the
-// dropped pairs and the 48-bit rounding are below 2^{-48} of the row scales).
+//     C_ij = 2^{e_i + f_j} sum_{t + u <= 8} sum_k a_t[i][k] b_u[j][k]
+// keeps every digit product of weight 2^{-64} and above (28 slice pairs; the
+// dropped pairs and the 56-bit rounding are below about 2^{-55} of the row scales
+// per term, i.e. about 2^{-48} of a typical term).
 //
 // Exact accumulation.  A product of two slices is d_t g_u 2^{-8(t+u)}, an integer
 // multiple of 2^{-8l} at level l = t + u with |d_t g_u| <= 2^14.  The FP32 tensor-core
@@ -22,22 +23,25 @@
 // 2^24 units, so the pairs of levels 2, 3 and 4 (1, 2 and 3 pairs) accumulate into
 // their own TMEM accumulators E2, E3, E4 for at most 256 K (3 * 256 * 2^14 < 2^24),
 // and are then drained exactly into a 64-bit integer per output element (units
-// 2^{-40}).  The 15 pairs of levels 5-7 share one FP32 accumulator I, drained the
-// same way (rounded to 2^{-40}) every 256 K, so its rounding stays far below the
-// FP64 level.  C = 2^{e_i + f_j - 40} * (the integer), converted once at the end.
+// 2^{-48}).  The 22 pairs of levels 5-8 share one FP32 accumulator I, drained the
+// same way (rounded to 2^{-48}) every 256 K, so its rounding stays at the FP64
+// level.  A work item spans at most 8192 K (longer sums are split over items and
+// the FP64 partial tiles added), which bounds the integer by 2^59.
+// C = 2^{e_i + f_j - 48} * (the integer), converted once at the end.
 //
-// Kernel.  Persistent, warp-specialised, one CTA per SM, 128 x 128 output tiles:
-//   warp 0, lane 0 : TMA producer -- per K-block of 32, the six A and six B slice
-//                    tiles (64-byte swizzle, 8 KB each) into a two-stage ring;
-//   warp 1         : owns the 512 TMEM columns (E2 | E3 | E4 | I); lane 0 issues the
-//                    21 x 2 MMAs (M = N = 128, K = 16) of each stage;
-//   warps 2-9      : epilogue; warp w reads TMEM lanes 32 (w % 4) .. + 31, columns
-//                    64 ((w - 2) / 4) .. + 63, and keeps those 64 integers in registers.
-// Drains alternate between the exact group (E2-E4, after K-blocks 3, 11, 19, ...) and
-// I (after K-blocks 7, 15, ...); the issuer runs the other group's MMAs of the next
-// stage before it waits for a drain.  Every mbarrier wait is bounded; on a timeout
-// the CTA flags DEV_TIMEOUT, stops, waits (bounded) for its copies and MMAs in flight,
-// frees TMEM and exits.
+// Kernel.  Persistent, warp-specialised, one CTA per SM, 128 x 64 output tiles:
+//   warp 0, lane 0 : TMA producer -- per K-block of 32, the seven A (128-row) and
+//                    seven B (64-row) slice tiles (64-byte swizzle) into a two-stage ring;
+//   warp 1         : owns the 512 TMEM columns, two sets of four 64-column FP32
+//                    accumulators (E2 | E3 | E4 | I); lane 0 issues the 28 x 2 MMAs
+//                    (M = 128, N = 64, K = 16) of each stage into the current set;
+//   warps 2-5      : epilogue; warp w reads TMEM lanes 32 (w % 4) .. + 31 (one output
+//                    row per thread) and keeps the row's 64 integers in registers.
+// All four accumulators of a set are drained together after every 8 K-blocks (256 K)
+// and at the end of a work item; the issuer fills the other set meanwhile, so a drain
+// holds up the MMAs only if it takes longer than a whole period.  Every mbarrier wait
+// is bounded; on a timeout the CTA flags DEV_TIMEOUT, stops, waits (bounded) for its
+// copies and MMAs in flight, frees TMEM and exits.
 #include "common.cuh"
 #include "kernels.cuh"
 #include "tcgen05.cuh"
@@ -48,43 +52,47 @@ namespace {
 
 using namespace tc;
 
-constexpr int kSlices = 6;
-constexpr int kTile = 128;                            // M = N of the output tile
+constexpr int kSlices = 7;
+constexpr int kPairs = kSlices * (kSlices + 1) / 2;   // slice pairs with t + u <= 8 (1-based)
+constexpr int kMaxItemKB = 256;                       // K-blocks per work item (8192 K)
+constexpr int kTileM = 128;                           // output rows per tile (TMEM lanes)
+constexpr int kTileN = 64;                            // output columns per tile
+constexpr int kRowPad = 128;                          // operand rows are padded to this
 constexpr int kKB = 32;                               // K per stage (64-byte rows)
-constexpr int kSliceBytes = kTile * kKB * 2;          // 8 KB
-constexpr int kStageBytes = 2 * kSlices * kSliceBytes;
+constexpr int kSliceA = kTileM * kKB * 2;             // 8 KB
+constexpr int kSliceB = kTileN * kKB * 2;             // 4 KB
+constexpr int kStageBytes = kSlices * (kSliceA + kSliceB);
 constexpr int kStages = 2;
-constexpr int kPeriod = 8;                            // K-blocks between drains of one group
-constexpr int kEpiWarps = 8;
+constexpr int kPeriod = 8;                            // K-blocks between drains (256 K)
+constexpr int kEpiWarps = 4;
 constexpr int kThreads = 32 * (2 + kEpiWarps);
 constexpr int kSmemBytes = kStages * kStageBytes + 1024;
 constexpr uint32_t kTmemCols = 512;
-constexpr uint32_t kIdesc = idesc_bf16(kTile, kTile);
+constexpr uint32_t kIdesc = idesc_bf16(kTileM, kTileN);
 constexpr uint64_t kWaitNs = 1000000000ull;           // pipeline waits
 constexpr uint64_t kDrainNs = 1000000000ull;          // waits for work already in flight
-constexpr int kFullEvent = 3, kXEvent = 1, kYEvent = 2;
 static_assert(kSmemBytes + 1024 <= 227 * 1024, "shared memory per CTA");
+static_assert(2 * 4 * kTileN <= (int)kTmemCols, "two sets of four accumulators");
 
-// Slice pairs (t, u), 0-based, and their accumulator (0: E2, 1: E3, 2: E4, 3: I).
-// The exact group X is pairs 0-5, the inexact group Y pairs 6-20.
-__constant__ int8_t kPairA[21] = {0, 0, 1, 0, 1, 2, 0, 1, 2, 3, 0, 1, 2, 3, 4, 0, 1, 2, 3, 4, 5};
-__constant__ int8_t kPairB[21] = {0, 1, 0, 2, 1, 0, 3, 2, 1, 0, 4, 3, 2, 1, 0, 5, 4, 3, 2, 1, 0};
-__constant__ int8_t kPairAcc[21] = {0, 1, 1, 2, 2, 2, 3, 3, 3, 3, 3, 3, 3, 3, 3, 3, 3, 3, 3, 3, 3};
+// Slice pairs (t, u), 0-based, by level, and their accumulator (0: E2, 1: E3, 2: E4,
+// 3: I).  The first pair of each accumulator: 0, 1, 3, 6.
+__constant__ int8_t kPairA[kPairs] = {0, 0, 1, 0, 1, 2, 0, 1, 2, 3, 0, 1, 2, 3, 4,
+                                      0, 1, 2, 3, 4, 5, 0, 1, 2, 3, 4, 5, 6};
+__constant__ int8_t kPairB[kPairs] = {0, 1, 0, 2, 1, 0, 3, 2, 1, 0, 4, 3, 2, 1, 0,
+                                      5, 4, 3, 2, 1, 0, 6, 5, 4, 3, 2, 1, 0};
+__constant__ int8_t kPairAcc[kPairs] = {0, 1, 1, 2, 2, 2, 3, 3, 3, 3, 3, 3, 3, 3, 3,
+                                        3, 3, 3, 3, 3, 3, 3, 3, 3, 3, 3, 3, 3};
 
-// The drain event after K-block kb of an item of KB blocks: 0 none, kXEvent (E2-E4),
-// kYEvent (I) or kFullEvent (all four, then the output).
-__device__ __forceinline__ int event_at(int kb, int KB) {
-    if (kb == KB - 1) return kFullEvent;
-    const int r = kb % kPeriod;
-    return r == kPeriod / 2 - 1 ? kXEvent : (r == kPeriod - 1 ? kYEvent : 0);
-}
+// A drain follows K-block kb of an item of KB blocks at the end of every period and
+// at the end of the item.
+__device__ __forceinline__ bool drain_after(int kb, int KB) { return kb == KB - 1 || kb % kPeriod == kPeriod - 1; }
 
 struct OzArgs {
     int64_t M, Nc;            // output rows / columns
     int64_t ldc;
     double* C;                // output (direct mode), or
     double* part;             // split-K partial tiles [splits][Mp][Np] (split mode)
-    int64_t Mp, Np;           // padded sizes (multiples of 128)
+    int64_t Mp, Np;           // padded sizes
     const int* expA;          // biased exponent field of each row's largest |value| (0: zero row)
     const int* expB;
     int64_t rowsA_pad, rowsB_pad;
@@ -92,8 +100,9 @@ struct OzArgs {
     int kb_total;             // K-blocks of 32
     int kb_split;             // K-blocks per split
     int splits;
-    int symmetric;            // only tiles with tm <= tn
+    int symmetric;            // only tiles that reach the upper triangle (j >= i)
     int b_upper;              // B_hat[j][k] = 0 for k > j: K limited to the tile's last column
+    int64_t pairs;            // tiles per split
     unsigned* status;
 };
 
@@ -101,23 +110,25 @@ struct Item {
     int tm, tn, kb0, KB;
 };
 
+// First column tile of row tile tm that reaches the upper triangle.
+__device__ __forceinline__ int first_upper_tn(int tm) { return (tm * kTileM) / kTileN; }
+
 __device__ __forceinline__ Item decode(const OzArgs& g, int64_t item) {
     Item it;
-    const int64_t pairs = g.symmetric ? (int64_t)g.tilesM * (g.tilesM + 1) / 2 : (int64_t)g.tilesM * g.tilesN;
-    const int z = (int)(item / pairs);
-    int64_t p = item % pairs;
+    const int z = (int)(item / g.pairs);
+    int64_t p = item % g.pairs;
     if (g.symmetric) {
         int tm = 0;
-        while (p >= g.tilesM - tm) { p -= g.tilesM - tm; tm++; }
+        while (tm < g.tilesM - 1 && p >= g.tilesN - first_upper_tn(tm)) { p -= g.tilesN - first_upper_tn(tm); tm++; }
         it.tm = tm;
-        it.tn = tm + (int)p;
+        it.tn = first_upper_tn(tm) + (int)p;
     } else {
         it.tm = (int)(p / g.tilesN);
         it.tn = (int)(p % g.tilesN);
     }
     int kend = g.kb_total;
     if (g.b_upper) {
-        const int lim = (int)(((int64_t)(it.tn + 1) * kTile + kKB - 1) / kKB);
+        const int lim = (int)(((int64_t)(it.tn + 1) * kTileN + kKB - 1) / kKB);
         if (lim < kend) kend = lim;
     }
     it.kb0 = z * g.kb_split;
@@ -158,7 +169,7 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                int64_t total) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    __shared__ __align__(8) uint64_t full[kStages], empty[kStages], efull, eempty, done;
+    __shared__ __align__(8) uint64_t full[kStages], empty[kStages], efull[2], eempty[2], done;
     __shared__ uint32_t tmem_slot;
     __shared__ int abort_flag;
 
@@ -168,8 +179,10 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
-        mbar_init(&efull, 1);
-        mbar_init(&eempty, kEpiWarps);
+        for (int b = 0; b < 2; b++) {
+            mbar_init(&efull[b], 1);
+            mbar_init(&eempty[b], kEpiWarps);
+        }
         mbar_init(&done, 1);
         asm volatile("fence.mbarrier_init.release.cluster;");
         asm volatile("fence.proxy.async.shared::cta;");
@@ -201,12 +214,12 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                 mbar_expect_tx(&full[s], kStageBytes);
 #pragma unroll
                 for (int t = 0; t < kSlices; t++)
-                    tma_load_2d(st + t * kSliceBytes, &tmA, x, (int)(t * g.rowsA_pad + (int64_t)it.tm * kTile),
+                    tma_load_2d(st + t * kSliceA, &tmA, x, (int)(t * g.rowsA_pad + (int64_t)it.tm * kTileM),
                                 sa(&full[s]));
 #pragma unroll
                 for (int t = 0; t < kSlices; t++)
-                    tma_load_2d(st + (kSlices + t) * kSliceBytes, &tmB, x,
-                                (int)(t * g.rowsB_pad + (int64_t)it.tn * kTile), sa(&full[s]));
+                    tma_load_2d(st + kSlices * kSliceA + t * kSliceB, &tmB, x,
+                                (int)(t * g.rowsB_pad + (int64_t)it.tn * kTileN), sa(&full[s]));
             }
             if (!ok) { *abort_v = 1; break; }
         }
@@ -217,7 +230,7 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         }
     } else if (warp == 1 && lane == 0) {
         // ---------------- MMA issuer
-        int64_t sc = 0, ev_commit = 0, ev_wait = 0;
+        int64_t sc = 0, period = 0;
         bool issued = false;
         for (int64_t item = blockIdx.x; item < total && !*abort_v; item += gridDim.x) {
             const Item it = decode(g, item);
@@ -228,59 +241,37 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                     ok = false;
                     break;
                 }
+                const int b = (int)(period & 1);
+                const bool fresh = kb % kPeriod == 0;   // a period starts in this stage
+                if (fresh && period >= 2 &&
+                    !mbar_wait(sa(&eempty[b]), (uint32_t)(((period >> 1) - 1) & 1), kWaitNs)) {
+                    ok = false;
+                    break;
+                }
                 asm volatile("tcgen05.fence::after_thread_sync;");
                 const uint32_t st = sa(smem + (size_t)s * kStageBytes);
-                const int r = kb % kPeriod;
-                // which accumulators start fresh in this stage, and whose drain must end first
-                const bool resetX = kb == 0 || r == kPeriod / 2;
-                const bool resetY = kb == 0 || r == 0;
-                auto wait_drain = [&]() -> bool {
-                    const bool w = mbar_wait(sa(&eempty), (uint32_t)(ev_wait & 1), kWaitNs);
-                    ev_wait++;
-                    asm volatile("tcgen05.fence::after_thread_sync;");
-                    return w;
-                };
-                // the pairs of each accumulator are consecutive (0 | 1 2 | 3 4 5 | 6 .. 20): the
-                // first MMA of a fresh accumulator overwrites it
-                auto issue = [&](int p0, int p1) {
-                    for (int p = p0; p < p1; p++) {
-                        const int acc = kPairAcc[p];
-                        const bool first = (p == 0 || p == 1 || p == 3 || p == 6) && (acc < 3 ? resetX : resetY);
-                        const uint64_t da = desc_kmajor(st + kPairA[p] * kSliceBytes, 64);
-                        const uint64_t db = desc_kmajor(st + (kSlices + kPairB[p]) * kSliceBytes, 64);
-                        const uint32_t dt = tmem + (uint32_t)(acc * kTile);
+                const uint32_t set = tmem + (uint32_t)(b * 4 * kTileN);
+                for (int p = 0; p < kPairs; p++) {
+                    const int acc = kPairAcc[p];
+                    const bool first = fresh && (p == 0 || p == 1 || p == 3 || p == 6);
+                    const uint64_t da = desc_kmajor(st + kPairA[p] * kSliceA, 64);
+                    const uint64_t db = desc_kmajor(st + kSlices * kSliceA + kPairB[p] * kSliceB, 64);
+                    const uint32_t dt = set + (uint32_t)(acc * kTileN);
 #pragma unroll
-                        for (int k = 0; k < kKB / 16; k++) {
-                            const uint32_t accumulate = (first && k == 0) ? 0u : 1u;
-                            asm volatile(
-                                "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n"
-                                :: "r"(dt), "l"(da + 2 * k), "l"(db + 2 * k), "r"(kIdesc), "r"(accumulate));
-                        }
+                    for (int k = 0; k < kKB / 16; k++) {
+                        const uint32_t accumulate = (first && k == 0) ? 0u : 1u;
+                        asm volatile(
+                            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n"
+                            :: "r"(dt), "l"(da + 2 * k), "l"(db + 2 * k), "r"(kIdesc), "r"(accumulate));
                     }
-                    issued = true;
-                };
-                bool w = true;
-                if (kb == 0) {
-                    if (ev_commit > 0) w = wait_drain();     // the previous item's output drain
-                    issue(0, 21);
-                } else if (resetX) {                           // E2-E4 drained after the last block
-                    issue(6, 21);
-                    w = wait_drain();
-                    issue(0, 6);
-                } else if (resetY) {                           // I drained after the last block
-                    issue(0, 6);
-                    w = wait_drain();
-                    issue(6, 21);
-                } else {
-                    issue(0, 21);
                 }
+                issued = true;
                 umma_commit(&empty[s]);
-                if (event_at(kb, it.KB)) {
-                    umma_commit(&efull);
-                    ev_commit++;
+                if (drain_after(kb, it.KB)) {
+                    umma_commit(&efull[b]);
+                    period++;
                 }
-                if (!w) { ok = false; sc++; break; }
             }
             if (!ok) { *abort_v = 1; break; }
         }
@@ -291,71 +282,72 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         }
     } else if (warp >= 2) {
         // ---------------- epilogue: exact drains into 64-bit integers, then the output
-        const int q = warp & 3, h = (warp - 2) >> 2;
+        const int q = warp & 3;
         const uint32_t lane_base = (uint32_t)(32 * q) << 16;
-        int64_t ev = 0;
-        long long acc[64];
+        int64_t period = 0;
+        long long acc[kTileN];
         for (int64_t item = blockIdx.x; item < total; item += gridDim.x) {
             const Item it = decode(g, item);
 #pragma unroll
-            for (int c = 0; c < 64; c++) acc[c] = 0;
+            for (int c = 0; c < kTileN; c++) acc[c] = 0;
             bool ok = true;
             for (int kb = 0; kb < it.KB; kb++) {
-                const int kind = event_at(kb, it.KB);
-                if (!kind) continue;
-                if (!__all_sync(0xffffffffu, !*abort_v && mbar_wait(sa(&efull), (uint32_t)(ev & 1), kWaitNs))) {
+                if (!drain_after(kb, it.KB)) continue;
+                const int b = (int)(period & 1);
+                if (!__all_sync(0xffffffffu, !*abort_v &&
+                                                 mbar_wait(sa(&efull[b]), (uint32_t)((period >> 1) & 1), kWaitNs))) {
                     ok = false;
                     break;
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;");
+                const uint32_t set = tmem + lane_base + (uint32_t)(b * 4 * kTileN);
 #pragma unroll
                 for (int a = 0; a < 4; a++) {
-                    const bool take = (a < 3) ? (kind & kXEvent) : (kind & kYEvent);
-                    if (!take) continue;
-                    // units of 2^-40: E_l holds multiples of 2^-8l, I is rounded to 2^-40
-                    const int up = a < 3 ? 8 * (a + 2) : 40;
-                    const long long mul = 1ll << (a < 3 ? 40 - 8 * (a + 2) : 0);
-                    const float sc = pow2f(up);
+                    // units of 2^-48: E_l holds multiples of 2^-8l (|value| < 2^24 units),
+                    // I is rounded to 2^-48 (|value| < 2^32 units)
+                    const float sc = pow2f(a < 3 ? 8 * (a + 2) : 48);
+                    const long long mul = 1ll << (a < 3 ? 48 - 8 * (a + 2) : 0);
 #pragma unroll
-                    for (int half = 0; half < 2; half++) {
+                    for (int half = 0; half < kTileN / 32; half++) {
                         uint32_t v[32];
-                        tmem_ld32(tmem + lane_base + (uint32_t)(a * kTile + h * 64 + half * 32), v);
+                        tmem_ld32(set + (uint32_t)(a * kTileN + half * 32), v);
                         asm volatile("tcgen05.wait::ld.sync.aligned;");
 #pragma unroll
                         for (int c = 0; c < 32; c++) {
-                            const int iv = __float2int_rn(__uint_as_float(v[c]) * sc);
-                            acc[half * 32 + c] += (long long)iv * mul;
+                            const float x = __uint_as_float(v[c]) * sc;
+                            if (a < 3) acc[half * 32 + c] += (long long)__float2int_rn(x) * mul;
+                            else acc[half * 32 + c] += __float2ll_rn(x);
                         }
                     }
                 }
                 asm volatile("tcgen05.fence::before_thread_sync;");
                 __syncwarp();
-                if (lane == 0) mbar_arrive(&eempty);
-                ev++;
-                if (kind == kFullEvent) {
-                    const int64_t row = (int64_t)it.tm * kTile + 32 * q + lane;
-                    const int64_t col0 = (int64_t)it.tn * kTile + h * 64;
+                if (lane == 0) mbar_arrive(&eempty[b]);
+                period++;
+                if (kb == it.KB - 1) {
+                    const int64_t row = (int64_t)it.tm * kTileM + 32 * q + lane;
+                    const int64_t col0 = (int64_t)it.tn * kTileN;
                     const int ea = row < g.M ? g.expA[row] : 0;
-                    const int z = it.kb0 / g.kb_split;
                     if (g.part) {
+                        const int z = it.kb0 / g.kb_split;
                         double* dst = g.part + ((int64_t)z * g.Mp + row) * g.Np + col0;
 #pragma unroll
-                        for (int c = 0; c < 64; c++) {
+                        for (int c = 0; c < kTileN; c++) {
                             const int eb = (col0 + c < g.Nc) ? g.expB[col0 + c] : 0;
                             double v = 0.0;
                             if (acc[c] != 0 && ea != 0 && eb != 0)
-                                v = scale_pow2((double)acc[c], (ea - 1021) + (eb - 1021) - 40);
+                                v = scale_pow2((double)acc[c], (ea - 1021) + (eb - 1021) - 48);
                             dst[c] = v;
                         }
                     } else if (row < g.M) {
                         double* dst = g.C + row * g.ldc + col0;
 #pragma unroll
-                        for (int c = 0; c < 64; c++) {
+                        for (int c = 0; c < kTileN; c++) {
                             if (col0 + c >= g.Nc) break;
                             const int eb = g.expB[col0 + c];
                             double v = 0.0;
                             if (acc[c] != 0 && ea != 0 && eb != 0)
-                                v = scale_pow2((double)acc[c], (ea - 1021) + (eb - 1021) - 40);
+                                v = scale_pow2((double)acc[c], (ea - 1021) + (eb - 1021) - 48);
                             dst[c] = v;
                         }
                     }
@@ -411,16 +403,18 @@ __global__ void oz_exponents_kernel(const double* __restrict__ src, int64_t ld, 
     if (bad) raise_status(status, DEV_NONFINITE);
 }
 
-// The six BF16 slices of one value x of a row whose largest exponent field is efm.
+// The seven BF16 slices of one value x of a row whose largest exponent field is efm.
 __device__ __forceinline__ void digits_of(double x, int efm, __nv_bfloat16 (&out)[kSlices]) {
     const long long b = __double_as_longlong(x);
     const int ef = (int)((b >> 52) & 0x7ff);
     long long F = 0;
     if (ef != 0 && efm != 0 && ef != 0x7ff) {
-        // |x| 2^{-e} 2^{48} with e = efm - 1021: mant 2^{ef - efm - 6}, rounded to nearest
+        // F = |x| 2^{-e} 2^{56} < 2^55 with e = efm - 1021: mant 2^{ef - efm + 2}, the
+        // right shifts rounded to nearest
         const long long mant = (b & ((1ll << 52) - 1)) | (1ll << 52);
-        const int sh = efm - ef + 6;
-        F = sh < 60 ? (mant + (1ll << (sh - 1))) >> sh : 0;
+        const int sh = efm - ef - 2;
+        if (sh <= 0) F = mant << (-sh);
+        else F = sh < 60 ? (mant + (1ll << (sh - 1))) >> sh : 0;
     }
     // balanced base-256 digits, least significant first; the top digit keeps its carry
     int d[kSlices];
@@ -475,14 +469,14 @@ __global__ void oz_slice_kernel(const double* __restrict__ src, int64_t ld, int6
     }
 }
 
-// C = sum over splits of the partial tiles (tiles below the diagonal of a symmetric
-// product take the transposed upper tile).
+// C = sum over splits of the partial tiles; for a symmetric product an element
+// below the diagonal takes its mirror above it (always in a computed tile).
 __global__ void oz_reduce_kernel(const double* __restrict__ part, int splits, int64_t Mp, int64_t Np, int64_t M,
                                  int64_t Nc, double* C, int64_t ldc, int symmetric) {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= M * Nc) return;
     int64_t i = idx / Nc, j = idx % Nc;
-    if (symmetric && (i / kTile) > (j / kTile)) { const int64_t t = i; i = j; j = t; }
+    if (symmetric && i > j) { const int64_t t = i; i = j; j = t; }
     double s = 0.0;
     for (int z = 0; z < splits; z++) s += part[((int64_t)z * Mp + i) * Np + j];
     C[(idx / Nc) * ldc + idx % Nc] = s;
@@ -512,7 +506,7 @@ void oz_operand_layout(Ar& ar, int64_t rows, int64_t K, OzOperand* op) {
     OzOperand o;
     o.rows = rows;
     o.K = K;
-    o.rows_pad = round_up(rows, kTile);
+    o.rows_pad = round_up(rows, kRowPad);
     o.K_pad = round_up(K, kKB);
     o.exps = ar.template take<int>((size_t)o.rows_pad);
     o.slices = ar.template take<__nv_bfloat16>((size_t)kSlices * o.rows_pad * o.K_pad);
@@ -540,15 +534,16 @@ int oz_prepare(const double* src, int64_t ld, bool trans, const OzOperand& o, un
     return CHFSI_OK;
 }
 
-// Split-K count for a product whose output has `tiles` tiles: about one work item per
-// SM, each split at least 64 K-blocks (2048 K).
+// Split-K count for a product whose output has `tiles` tiles: at most kMaxItemKB
+// K-blocks per work item (the range of the 64-bit accumulators), and enough items
+// for about one per SM while each split keeps at least 64 K-blocks (2048 K).
 int oz_splits(int64_t tiles, int kb_total, int sms) {
+    const int64_t need = (kb_total + kMaxItemKB - 1) / kMaxItemKB;
     int64_t want = (sms + tiles - 1) / tiles;
-    int64_t maxs = (kb_total + 63) / 64;
-    int64_t sp = want < maxs ? want : maxs;
-    if (sp < 1) sp = 1;
-    if (sp > 64) sp = 64;
-    return (int)sp;
+    const int64_t maxs = (kb_total + 63) / 64;
+    if (want > maxs) want = maxs;
+    const int64_t sp = want > need ? want : need;
+    return (int)(sp < 1 ? 1 : sp);
 }
 
 struct OzPlan {
@@ -567,10 +562,9 @@ void oz_layout(Ar& ar, bool tn_form, int64_t M, int64_t Nc, int64_t K, bool same
     if (same) p.B = p.A;
     else oz_operand_layout(ar, Nc, K, &p.B);
     if (tn_form) {
-        const int64_t tm = round_up(M, kTile) / kTile, tn = round_up(Nc, kTile) / kTile;
-        const int64_t tiles = same ? tm * (tm + 1) / 2 : tm * tn;
-        p.splits = oz_splits(tiles, (int)(p.A.K_pad / kKB), sms > 0 ? sms : 148);
-        p.part = ar.template take<double>((size_t)p.splits * round_up(M, kTile) * round_up(Nc, kTile));
+        const int64_t tm = p.A.rows_pad / kTileM, tn = p.B.rows_pad / kTileN;
+        p.splits = oz_splits(tm * tn, (int)(p.A.K_pad / kKB), sms > 0 ? sms : 148);
+        p.part = ar.template take<double>((size_t)p.splits * p.A.rows_pad * p.B.rows_pad);
     }
     if (plan) *plan = p;
 }
@@ -581,12 +575,13 @@ int oz_run(const OzPlan& p, bool tn_form, double* C, int64_t ldc, int64_t M, int
     const int64_t K_pad = p.A.K_pad;
     if (K_pad > (int64_t)1 << 21 || p.A.rows_pad * kSlices > INT32_MAX || p.B.rows_pad * kSlices > INT32_MAX)
         return CHFSI_ERR_UNSUPPORTED;
+    if (!tn_form && K_pad > (int64_t)kMaxItemKB * kKB) return CHFSI_ERR_UNSUPPORTED;   // no split-K in the nn form
     CUtensorMap tmA, tmB;
     int rc;
-    if ((rc = make_map_bf16(&tmA, p.A.slices, K_pad, kSlices * p.A.rows_pad, kKB, kTile,
+    if ((rc = make_map_bf16(&tmA, p.A.slices, K_pad, kSlices * p.A.rows_pad, kKB, kTileM,
                             CU_TENSOR_MAP_SWIZZLE_64B)))
         return rc;
-    if ((rc = make_map_bf16(&tmB, p.B.slices, K_pad, kSlices * p.B.rows_pad, kKB, kTile,
+    if ((rc = make_map_bf16(&tmB, p.B.slices, K_pad, kSlices * p.B.rows_pad, kKB, kTileN,
                             CU_TENSOR_MAP_SWIZZLE_64B)))
         return rc;
     OzArgs g{};
@@ -599,8 +594,8 @@ int oz_run(const OzPlan& p, bool tn_form, double* C, int64_t ldc, int64_t M, int
     g.expB = p.B.exps;
     g.rowsA_pad = p.A.rows_pad;
     g.rowsB_pad = p.B.rows_pad;
-    g.tilesM = (int)(p.A.rows_pad / kTile);
-    g.tilesN = (int)(p.B.rows_pad / kTile);
+    g.tilesM = (int)(p.A.rows_pad / kTileM);
+    g.tilesN = (int)(p.B.rows_pad / kTileN);
     g.kb_total = (int)(K_pad / kKB);
     g.splits = tn_form ? p.splits : 1;
     g.kb_split = (g.kb_total + g.splits - 1) / g.splits;
@@ -610,7 +605,16 @@ int oz_run(const OzPlan& p, bool tn_form, double* C, int64_t ldc, int64_t M, int
     g.status = status;
     g.C = tn_form ? nullptr : C;
     g.part = tn_form ? p.part : nullptr;
-    const int64_t pairs = symmetric ? (int64_t)g.tilesM * (g.tilesM + 1) / 2 : (int64_t)g.tilesM * g.tilesN;
+    int64_t pairs = 0;
+    if (symmetric) {
+        for (int tm = 0; tm < g.tilesM; tm++) {
+            const int first = (tm * kTileM) / kTileN;
+            if (first < g.tilesN) pairs += g.tilesN - first;
+        }
+    } else {
+        pairs = (int64_t)g.tilesM * g.tilesN;
+    }
+    g.pairs = pairs;
     const int64_t total = pairs * g.splits;
     const int dev = current_device();
     if (dev < 0) return CHFSI_ERR_CUDA;
@@ -687,6 +691,7 @@ int oz_abi_check(int32_t op, int64_t M, int64_t Nc, int64_t K, int32_t flags) {
     if ((flags & CHFSI_GEMM_SYMMETRIC) && (op != CHFSI_OP_TN || M != Nc)) return CHFSI_ERR_ARG;
     if ((flags & CHFSI_GEMM_B_UPPER) && op != CHFSI_OP_NN) return CHFSI_ERR_ARG;
     if (K > ((int64_t)1 << 21) || M > INT32_MAX / 8 || Nc > INT32_MAX / 8) return CHFSI_ERR_UNSUPPORTED;
+    if (op == CHFSI_OP_NN && K > 8192) return CHFSI_ERR_UNSUPPORTED;
     return CHFSI_OK;
 }
 
