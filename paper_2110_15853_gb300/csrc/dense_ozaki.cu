@@ -19,29 +19,30 @@
 //
 // Exact accumulation.  A product of two slices is d_t g_u 2^{-8(t+u)}, an integer
 // multiple of 2^{-8l} at level l = t + u with |d_t g_u| <= 2^14.  The FP32 tensor-core
-// accumulator sums such multiples without rounding while the partial sums stay below
-// 2^24 units, so the pairs of levels 2, 3 and 4 (1, 2 and 3 pairs) accumulate into
-// their own TMEM accumulators E2, E3, E4 for at most 256 K (3 * 256 * 2^14 < 2^24),
-// and are then drained exactly into a 64-bit integer per output element (units
-// 2^{-48}).  The 22 pairs of levels 5-8 share one FP32 accumulator I, drained the
-// same way (rounded to 2^{-48}) every 256 K, so its rounding stays at the FP64
-// level.  A work item spans at most 8192 K (longer sums are split over items and
-// the FP64 partial tiles added), which bounds the integer by 2^59.
-// C = 2^{e_i + f_j - 48} * (the integer), converted once at the end.
+// accumulator sums such multiples without rounding while the partial sums stay at or
+// below 2^24 units, so the pairs of levels 2, 3, 4 and 5 (1, 2, 3 and 4 pairs) each
+// accumulate into their own TMEM accumulator E2 .. E5 for at most 256 K (4 * 256 *
+// 2^14 = 2^24) and are then drained exactly into a 64-bit integer per output element
+// (units 2^{-48}).  The 18 pairs of levels 6-8 share one FP32 accumulator I; its sums
+// stay near 2^{-31} of the row scales, so their FP32 rounding is below 2^{-55}, and it
+// is drained the same way (rounded to 2^{-48}) every 256 K.  A work item spans at
+// most 8192 K (longer sums are split over items and the FP64 partial tiles added),
+// which bounds the integer by 2^59.  C = 2^{e_i + f_j - 48} * (the integer),
+// converted once at the end.
 //
-// Kernel.  Persistent, warp-specialised, one CTA per SM, 128 x 64 output tiles:
+// Kernel.  Persistent, warp-specialised, one CTA per SM, 128 x 96 output tiles:
 //   warp 0, lane 0 : TMA producer -- per K-block of 32, the seven A (128-row) and
-//                    seven B (64-row) slice tiles (64-byte swizzle) into a two-stage ring;
-//   warp 1         : owns the 512 TMEM columns, two sets of four 64-column FP32
-//                    accumulators (E2 | E3 | E4 | I); lane 0 issues the 28 x 2 MMAs
-//                    (M = 128, N = 64, K = 16) of each stage into the current set;
+//                    seven B (96-row) slice tiles (64-byte swizzle) into a two-stage ring;
+//   warp 1         : owns 512 TMEM columns: five 96-column FP32 accumulators
+//                    E2 | E3 | E4 | E5 | I; lane 0 issues the 28 x 2 MMAs (M = 128,
+//                    N = 96, K = 16) of each stage;
 //   warps 2-5      : epilogue; warp w reads TMEM lanes 32 (w % 4) .. + 31 (one output
-//                    row per thread) and keeps the row's 64 integers in registers.
-// All four accumulators of a set are drained together after every 8 K-blocks (256 K)
-// and at the end of a work item; the issuer fills the other set meanwhile, so a drain
-// holds up the MMAs only if it takes longer than a whole period.  Every mbarrier wait
-// is bounded; on a timeout the CTA flags DEV_TIMEOUT, stops, waits (bounded) for its
-// copies and MMAs in flight, frees TMEM and exits.
+//                    row per thread) and keeps the row's 96 integers in registers.
+// Drains alternate between group X (E2, E3: after K-blocks 3, 11, 19, ...) and group Y
+// (E4, E5, I: after K-blocks 7, 15, ...); the issuer runs the other group's MMAs of the
+// next stage before it waits for a drain.  Every mbarrier wait is bounded; on a
+// timeout the CTA flags DEV_TIMEOUT, stops, waits (bounded) for its copies and MMAs in
+// flight, frees TMEM and exits.
 #include "common.cuh"
 #include "kernels.cuh"
 #include "tcgen05.cuh"
@@ -54,16 +55,18 @@ using namespace tc;
 
 constexpr int kSlices = 7;
 constexpr int kPairs = kSlices * (kSlices + 1) / 2;   // slice pairs with t + u <= 8 (1-based)
+constexpr int kAccs = 5;                              // E2, E3, E4, E5, I
+constexpr int kGroupX = 3;                            // pairs 0-2 (E2, E3); pairs 3-27 are group Y
 constexpr int kMaxItemKB = 256;                       // K-blocks per work item (8192 K)
 constexpr int kTileM = 128;                           // output rows per tile (TMEM lanes)
-constexpr int kTileN = 64;                            // output columns per tile
+constexpr int kTileN = 96;                            // output columns per tile
 constexpr int kRowPad = 128;                          // operand rows are padded to this
 constexpr int kKB = 32;                               // K per stage (64-byte rows)
 constexpr int kSliceA = kTileM * kKB * 2;             // 8 KB
-constexpr int kSliceB = kTileN * kKB * 2;             // 4 KB
+constexpr int kSliceB = kTileN * kKB * 2;             // 6 KB
 constexpr int kStageBytes = kSlices * (kSliceA + kSliceB);
 constexpr int kStages = 2;
-constexpr int kPeriod = 8;                            // K-blocks between drains (256 K)
+constexpr int kPeriod = 8;                            // K-blocks between drains of one group
 constexpr int kEpiWarps = 4;
 constexpr int kThreads = 32 * (2 + kEpiWarps);
 constexpr int kSmemBytes = kStages * kStageBytes + 1024;
@@ -71,28 +74,34 @@ constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t kIdesc = idesc_bf16(kTileM, kTileN);
 constexpr uint64_t kWaitNs = 1000000000ull;           // pipeline waits
 constexpr uint64_t kDrainNs = 1000000000ull;          // waits for work already in flight
+constexpr int kXEvent = 1, kYEvent = 2, kFullEvent = 3;
 static_assert(kSmemBytes + 1024 <= 227 * 1024, "shared memory per CTA");
-static_assert(2 * 4 * kTileN <= (int)kTmemCols, "two sets of four accumulators");
+static_assert(kAccs * kTileN <= (int)kTmemCols, "five accumulators in TMEM");
+static_assert(kSliceB % 512 == 0 && kStageBytes % 1024 == 0, "swizzle-atom alignment of the tiles");
 
-// Slice pairs (t, u), 0-based, by level, and their accumulator (0: E2, 1: E3, 2: E4,
-// 3: I).  The first pair of each accumulator: 0, 1, 3, 6.
+// Slice pairs (t, u), 0-based, by level, and their accumulator (0: E2 .. 3: E5, 4: I).
+// The first pair of each accumulator: 0, 1, 3, 6, 10.
 __constant__ int8_t kPairA[kPairs] = {0, 0, 1, 0, 1, 2, 0, 1, 2, 3, 0, 1, 2, 3, 4,
                                       0, 1, 2, 3, 4, 5, 0, 1, 2, 3, 4, 5, 6};
 __constant__ int8_t kPairB[kPairs] = {0, 1, 0, 2, 1, 0, 3, 2, 1, 0, 4, 3, 2, 1, 0,
                                       5, 4, 3, 2, 1, 0, 6, 5, 4, 3, 2, 1, 0};
-__constant__ int8_t kPairAcc[kPairs] = {0, 1, 1, 2, 2, 2, 3, 3, 3, 3, 3, 3, 3, 3, 3,
-                                        3, 3, 3, 3, 3, 3, 3, 3, 3, 3, 3, 3, 3};
+__constant__ int8_t kPairAcc[kPairs] = {0, 1, 1, 2, 2, 2, 3, 3, 3, 3, 4, 4, 4, 4, 4,
+                                        4, 4, 4, 4, 4, 4, 4, 4, 4, 4, 4, 4, 4};
 
-// A drain follows K-block kb of an item of KB blocks at the end of every period and
-// at the end of the item.
-__device__ __forceinline__ bool drain_after(int kb, int KB) { return kb == KB - 1 || kb % kPeriod == kPeriod - 1; }
+// The drain after K-block kb of an item of KB blocks: 0 none, kXEvent (E2, E3),
+// kYEvent (E4, E5, I) or kFullEvent (all five, then the output).
+__device__ __forceinline__ int event_at(int kb, int KB) {
+    if (kb == KB - 1) return kFullEvent;
+    const int r = kb % kPeriod;
+    return r == kPeriod / 2 - 1 ? kXEvent : (r == kPeriod - 1 ? kYEvent : 0);
+}
 
 struct OzArgs {
     int64_t M, Nc;            // output rows / columns
     int64_t ldc;
     double* C;                // output (direct mode), or
     double* part;             // split-K partial tiles [splits][Mp][Np] (split mode)
-    int64_t Mp, Np;           // padded sizes
+    int64_t Mp, Np;           // partial-tile extents: tilesM * 128, tilesN * 96
     const int* expA;          // biased exponent field of each row's largest |value| (0: zero row)
     const int* expB;
     int64_t rowsA_pad, rowsB_pad;
@@ -110,8 +119,8 @@ struct Item {
     int tm, tn, kb0, KB;
 };
 
-// First column tile of row tile tm that reaches the upper triangle.
-__device__ __forceinline__ int first_upper_tn(int tm) { return (tm * kTileM) / kTileN; }
+// First column tile of row tile tm that reaches the upper triangle (j >= i).
+__device__ __host__ __forceinline__ int first_upper_tn(int tm) { return (tm * kTileM) / kTileN; }
 
 __device__ __forceinline__ Item decode(const OzArgs& g, int64_t item) {
     Item it;
@@ -169,7 +178,7 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                int64_t total) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    __shared__ __align__(8) uint64_t full[kStages], empty[kStages], efull[2], eempty[2], done;
+    __shared__ __align__(8) uint64_t full[kStages], empty[kStages], efull, eempty, done;
     __shared__ uint32_t tmem_slot;
     __shared__ int abort_flag;
 
@@ -179,10 +188,8 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
-        for (int b = 0; b < 2; b++) {
-            mbar_init(&efull[b], 1);
-            mbar_init(&eempty[b], kEpiWarps);
-        }
+        mbar_init(&efull, 1);
+        mbar_init(&eempty, kEpiWarps);
         mbar_init(&done, 1);
         asm volatile("fence.mbarrier_init.release.cluster;");
         asm volatile("fence.proxy.async.shared::cta;");
@@ -230,7 +237,7 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         }
     } else if (warp == 1 && lane == 0) {
         // ---------------- MMA issuer
-        int64_t sc = 0, period = 0;
+        int64_t sc = 0, ev_commit = 0, ev_wait = 0;
         bool issued = false;
         for (int64_t item = blockIdx.x; item < total && !*abort_v; item += gridDim.x) {
             const Item it = decode(g, item);
@@ -241,37 +248,60 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                     ok = false;
                     break;
                 }
-                const int b = (int)(period & 1);
-                const bool fresh = kb % kPeriod == 0;   // a period starts in this stage
-                if (fresh && period >= 2 &&
-                    !mbar_wait(sa(&eempty[b]), (uint32_t)(((period >> 1) - 1) & 1), kWaitNs)) {
-                    ok = false;
-                    break;
-                }
                 asm volatile("tcgen05.fence::after_thread_sync;");
                 const uint32_t st = sa(smem + (size_t)s * kStageBytes);
-                const uint32_t set = tmem + (uint32_t)(b * 4 * kTileN);
-                for (int p = 0; p < kPairs; p++) {
-                    const int acc = kPairAcc[p];
-                    const bool first = fresh && (p == 0 || p == 1 || p == 3 || p == 6);
-                    const uint64_t da = desc_kmajor(st + kPairA[p] * kSliceA, 64);
-                    const uint64_t db = desc_kmajor(st + kSlices * kSliceA + kPairB[p] * kSliceB, 64);
-                    const uint32_t dt = set + (uint32_t)(acc * kTileN);
+                const int r = kb % kPeriod;
+                // which group starts fresh in this stage (its drain must have ended first)
+                const bool resetX = kb == 0 || r == kPeriod / 2;
+                const bool resetY = kb == 0 || r == 0;
+                auto wait_drain = [&]() -> bool {
+                    const bool w = mbar_wait(sa(&eempty), (uint32_t)(ev_wait & 1), kWaitNs);
+                    ev_wait++;
+                    asm volatile("tcgen05.fence::after_thread_sync;");
+                    return w;
+                };
+                // the pairs of each accumulator are consecutive: the first MMA of a fresh
+                // accumulator overwrites it
+                auto issue = [&](int p0, int p1) {
+                    for (int p = p0; p < p1; p++) {
+                        const int acc = kPairAcc[p];
+                        const bool first =
+                            (p == 0 || p == 1 || p == 3 || p == 6 || p == 10) && (p < kGroupX ? resetX : resetY);
+                        const uint64_t da = desc_kmajor(st + kPairA[p] * kSliceA, 64);
+                        const uint64_t db = desc_kmajor(st + kSlices * kSliceA + kPairB[p] * kSliceB, 64);
+                        const uint32_t dt = tmem + (uint32_t)(acc * kTileN);
 #pragma unroll
-                    for (int k = 0; k < kKB / 16; k++) {
-                        const uint32_t accumulate = (first && k == 0) ? 0u : 1u;
-                        asm volatile(
-                            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n"
-                            :: "r"(dt), "l"(da + 2 * k), "l"(db + 2 * k), "r"(kIdesc), "r"(accumulate));
+                        for (int k = 0; k < kKB / 16; k++) {
+                            const uint32_t accumulate = (first && k == 0) ? 0u : 1u;
+                            asm volatile(
+                                "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n"
+                                :: "r"(dt), "l"(da + 2 * k), "l"(db + 2 * k), "r"(kIdesc), "r"(accumulate));
+                        }
                     }
+                    issued = true;
+                };
+                bool w = true;
+                if (kb == 0) {
+                    if (ev_commit > 0) w = wait_drain();     // the previous item's output drain
+                    issue(0, kPairs);
+                } else if (resetX) {                           // E2, E3 drained after the last block
+                    issue(kGroupX, kPairs);
+                    w = wait_drain();
+                    issue(0, kGroupX);
+                } else if (resetY) {                           // E4, E5, I drained after the last block
+                    issue(0, kGroupX);
+                    w = wait_drain();
+                    issue(kGroupX, kPairs);
+                } else {
+                    issue(0, kPairs);
                 }
-                issued = true;
                 umma_commit(&empty[s]);
-                if (drain_after(kb, it.KB)) {
-                    umma_commit(&efull[b]);
-                    period++;
+                if (event_at(kb, it.KB)) {
+                    umma_commit(&efull);
+                    ev_commit++;
                 }
+                if (!w) { ok = false; sc++; break; }
             }
             if (!ok) { *abort_v = 1; break; }
         }
@@ -284,7 +314,7 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         // ---------------- epilogue: exact drains into 64-bit integers, then the output
         const int q = warp & 3;
         const uint32_t lane_base = (uint32_t)(32 * q) << 16;
-        int64_t period = 0;
+        int64_t ev = 0;
         long long acc[kTileN];
         for (int64_t item = blockIdx.x; item < total; item += gridDim.x) {
             const Item it = decode(g, item);
@@ -292,39 +322,36 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             for (int c = 0; c < kTileN; c++) acc[c] = 0;
             bool ok = true;
             for (int kb = 0; kb < it.KB; kb++) {
-                if (!drain_after(kb, it.KB)) continue;
-                const int b = (int)(period & 1);
-                if (!__all_sync(0xffffffffu, !*abort_v &&
-                                                 mbar_wait(sa(&efull[b]), (uint32_t)((period >> 1) & 1), kWaitNs))) {
+                const int kind = event_at(kb, it.KB);
+                if (!kind) continue;
+                if (!__all_sync(0xffffffffu, !*abort_v && mbar_wait(sa(&efull), (uint32_t)(ev & 1), kWaitNs))) {
                     ok = false;
                     break;
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;");
-                const uint32_t set = tmem + lane_base + (uint32_t)(b * 4 * kTileN);
 #pragma unroll
-                for (int a = 0; a < 4; a++) {
-                    // units of 2^-48: E_l holds multiples of 2^-8l (|value| < 2^24 units),
-                    // I is rounded to 2^-48 (|value| < 2^32 units)
-                    const float sc = pow2f(a < 3 ? 8 * (a + 2) : 48);
-                    const long long mul = 1ll << (a < 3 ? 48 - 8 * (a + 2) : 0);
+                for (int a = 0; a < kAccs; a++) {
+                    const bool take = (a < 2) ? (kind & kXEvent) : (kind & kYEvent);
+                    if (!take) continue;
+                    // units of 2^-48: E_l holds multiples of 2^-8l (|value| <= 2^24 units),
+                    // I is rounded to 2^-48 (|value| < 2^27 units)
+                    const float sc = pow2f(a < 4 ? 8 * (a + 2) : 48);
+                    const long long mul = 1ll << (a < 4 ? 48 - 8 * (a + 2) : 0);
 #pragma unroll
-                    for (int half = 0; half < kTileN / 32; half++) {
+                    for (int part = 0; part < kTileN / 32; part++) {
                         uint32_t v[32];
-                        tmem_ld32(set + (uint32_t)(a * kTileN + half * 32), v);
+                        tmem_ld32(tmem + lane_base + (uint32_t)(a * kTileN + part * 32), v);
                         asm volatile("tcgen05.wait::ld.sync.aligned;");
 #pragma unroll
-                        for (int c = 0; c < 32; c++) {
-                            const float x = __uint_as_float(v[c]) * sc;
-                            if (a < 3) acc[half * 32 + c] += (long long)__float2int_rn(x) * mul;
-                            else acc[half * 32 + c] += __float2ll_rn(x);
-                        }
+                        for (int c = 0; c < 32; c++)
+                            acc[part * 32 + c] += (long long)__float2int_rn(__uint_as_float(v[c]) * sc) * mul;
                     }
                 }
                 asm volatile("tcgen05.fence::before_thread_sync;");
                 __syncwarp();
-                if (lane == 0) mbar_arrive(&eempty[b]);
-                period++;
-                if (kb == it.KB - 1) {
+                if (lane == 0) mbar_arrive(&eempty);
+                ev++;
+                if (kind == kFullEvent) {
                     const int64_t row = (int64_t)it.tm * kTileM + 32 * q + lane;
                     const int64_t col0 = (int64_t)it.tn * kTileN;
                     const int ea = row < g.M ? g.expA[row] : 0;
@@ -562,9 +589,9 @@ void oz_layout(Ar& ar, bool tn_form, int64_t M, int64_t Nc, int64_t K, bool same
     if (same) p.B = p.A;
     else oz_operand_layout(ar, Nc, K, &p.B);
     if (tn_form) {
-        const int64_t tm = p.A.rows_pad / kTileM, tn = p.B.rows_pad / kTileN;
+        const int64_t tm = (M + kTileM - 1) / kTileM, tn = (Nc + kTileN - 1) / kTileN;
         p.splits = oz_splits(tm * tn, (int)(p.A.K_pad / kKB), sms > 0 ? sms : 148);
-        p.part = ar.template take<double>((size_t)p.splits * p.A.rows_pad * p.B.rows_pad);
+        p.part = ar.template take<double>((size_t)p.splits * (tm * kTileM) * (tn * kTileN));
     }
     if (plan) *plan = p;
 }
@@ -588,14 +615,14 @@ int oz_run(const OzPlan& p, bool tn_form, double* C, int64_t ldc, int64_t M, int
     g.M = M;
     g.Nc = Nc;
     g.ldc = ldc;
-    g.Mp = p.A.rows_pad;
-    g.Np = p.B.rows_pad;
+    g.tilesM = (int)((M + kTileM - 1) / kTileM);
+    g.tilesN = (int)((Nc + kTileN - 1) / kTileN);
+    g.Mp = (int64_t)g.tilesM * kTileM;
+    g.Np = (int64_t)g.tilesN * kTileN;
     g.expA = p.A.exps;
     g.expB = p.B.exps;
     g.rowsA_pad = p.A.rows_pad;
     g.rowsB_pad = p.B.rows_pad;
-    g.tilesM = (int)(p.A.rows_pad / kTileM);
-    g.tilesN = (int)(p.B.rows_pad / kTileN);
     g.kb_total = (int)(K_pad / kKB);
     g.splits = tn_form ? p.splits : 1;
     g.kb_split = (g.kb_total + g.splits - 1) / g.splits;
@@ -608,7 +635,7 @@ int oz_run(const OzPlan& p, bool tn_form, double* C, int64_t ldc, int64_t M, int
     int64_t pairs = 0;
     if (symmetric) {
         for (int tm = 0; tm < g.tilesM; tm++) {
-            const int first = (tm * kTileM) / kTileN;
+            const int first = first_upper_tn(tm);
             if (first < g.tilesN) pairs += g.tilesN - first;
         }
     } else {
