@@ -70,7 +70,8 @@ def parse_args(argv=None):
     ap.add_argument("--layout", default="csr", choices=["csr", "bsr", "hybrid"], help="filter-only operator layout")
     ap.add_argument("--closure-only", action="store_true",
                     help="set up, run one CholQR2 + Rayleigh-Ritz on X and exit: a profiling case")
-    ap.add_argument("--precision", default="f64", choices=["f64", "f32x2"], help="closure-only product precision")
+    ap.add_argument("--precision", default="f64", choices=["f64", "f32x2", "ozaki"],
+                    help="closure-only product precision")
     return ap.parse_args(argv)
 
 
@@ -355,9 +356,6 @@ def run_ours(args):
     def ev():
         return torch.cuda.Event(enable_timing=True)
 
-    peak64 = P.measure_pipe_peak("f64", dev) / 1e9
-    peak32 = P.measure_pipe_peak("f32", dev) / 1e9
-
     # spectral bounds (the first phase of the hot path), timed once
     wsl = P.Workspace(dev)
     P.lanczos_bounds(Hd, v0d, 20, n, workspace=wsl)
@@ -376,6 +374,9 @@ def run_ours(args):
     if args.warmup > 0:
         P.filter(Hd, Xd, args.warmup, a, b, a0, out=YK, workspace=wsf)
     torch.cuda.synchronize(dev)
+    # pipe peaks measured warm, right before the timed region, at the same clocks
+    peak64 = P.measure_pipe_peak("f64", dev) / 1e9
+    peak32 = P.measure_pipe_peak("f32", dev) / 1e9
     clocks = ClockSampler(local)
     clocks.start()
     launches0 = lib.chfsi_kernel_launches()
@@ -465,7 +466,19 @@ def run_ours(args):
         torch.cuda.synchronize(dev)
         closure_ms = e0.elapsed_time(e1)
         theta_ref = theta_ref.cpu().numpy()
-        del psi, wsr
+        del wsr
+        # the same closure with its dense products on the tensor cores (Ozaki slices)
+        P.rayleigh_ritz(Hd, Xd[:, :8], 2, precision="ozaki")
+        wso = P.Workspace(dev)
+        wso.get(P.rayleigh_ritz_workspace_bytes(Hd, n, 2, "ozaki"))
+        e0, e1 = ev(), ev()
+        e0.record(stream)
+        theta_oz, _ = P.rayleigh_ritz(Hd, Ym, 2, psi=psi, workspace=wso, precision="ozaki")
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        closure_oz_ms = e0.elapsed_time(e1)
+        oz_errs = _ritz_errors(theta_oz.cpu().numpy(), theta_ref, a)
+        del psi, wso
         fl_l, fl_c = lanczos_flops(nnz, N, 20), closure_flops(nnz, N, n, 2)
         line["phases"] = {
             "lanczos_ms": lanczos_ms, "filter_ms": filter_ms, "filter_gflops": flops_m / (filter_ms * 1e-3) / 1e9,
@@ -473,8 +486,15 @@ def run_ours(args):
             "closure_gflops": fl_c / (closure_ms * 1e-3) / 1e9,
             "whole_step_ms": lanczos_ms + filter_ms + closure_ms,
             "whole_step_gflops": (fl_l + flops_m + fl_c) / ((lanczos_ms + filter_ms + closure_ms) * 1e-3) / 1e9,
+            "closure_ozaki_ms": closure_oz_ms, "closure_ozaki_gflops": fl_c / (closure_oz_ms * 1e-3) / 1e9,
+            "closure_ozaki_speedup_vs_f64": closure_ms / closure_oz_ms,
+            "closure_ozaki_vs_f64_closure": oz_errs,
+            "whole_step_ozaki_closure_ms": lanczos_ms + filter_ms + closure_oz_ms,
+            "whole_step_ozaki_closure_gflops": (fl_l + flops_m + fl_c) /
+                                               ((lanczos_ms + filter_ms + closure_oz_ms) * 1e-3) / 1e9,
             "what": "whole hot path = Lanczos(20) + FP64 filter(m) + CholQR2 + Rayleigh-Ritz, each phase timed "
-                    "once on the resident workload"}
+                    "once on the resident workload; the closure with FP64 (DFMA) products, and with its dense "
+                    "products as Ozaki slices on the BF16 tensor cores"}
 
         if not args.no_variants and rank == 0:
             line["mixed_precision"] = mixed_variants(P, torch, dev, stream, wl, Hd, Xd, v0d, Ym, theta_ref,
@@ -539,6 +559,20 @@ def mixed_variants(P, torch, dev, stream, wl, Hd, Xd, v0d, Yref, theta_ref, boun
         out["whole_step_two_float"] = dict(
             ms=t_all, closure_ms=t_c, speedup_vs_f64_step=line["phases"]["whole_step_ms"] / t_all,
             closure_speedup_vs_f64=line["phases"]["closure_ms"] / t_c, **errs)
+        # the same filter output through the Ozaki closure: the fastest FP64-accurate step
+        wso = P.Workspace(dev)
+        wso.get(P.rayleigh_ritz_workspace_bytes(Hd, n, 2, "ozaki"))
+        e0, e1 = ev(), ev()
+        e0.record(stream)
+        th, _ = P.rayleigh_ritz(Hd, Y, 2, workspace=wso, precision="ozaki")
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        t_oz = e0.elapsed_time(e1)
+        t_step = evs[0].elapsed_time(evs[2]) + t_oz
+        out["whole_step_two_float_filter_ozaki_closure"] = dict(
+            ms=t_step, closure_ms=t_oz, speedup_vs_f64_step=line["phases"]["whole_step_ms"] / t_step,
+            **_ritz_errors(th.cpu().numpy(), theta_ref, a))
+        del wso
     except Exception as e:  # noqa: BLE001 - report, do not hide
         out["two_float_error"] = repr(e)
 

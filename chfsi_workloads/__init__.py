@@ -36,7 +36,7 @@ import numpy as np
 __all__ = [
     "Workload", "WORKLOADS", "workload", "offsets", "csr_grid", "blocked_permutation",
     "bsr_from_csr", "gaussian", "start_block", "lanczos_start", "loss_weights",
-    "row_subset", "column_subset", "permute_csr",
+    "row_subset", "column_subset", "permute_csr", "banded_operator", "split_from_csr",
 ]
 
 SEED_BASE = 2110158530
@@ -48,6 +48,8 @@ _STREAM_X = 1000
 _STREAM_V0 = 1001
 _STREAM_W = 1002
 _STREAM_SUBSET = 1003
+_STREAM_BAND = 2000
+_STREAM_FAR = 2001
 
 
 @dataclasses.dataclass(frozen=True)
@@ -275,3 +277,65 @@ def row_subset(N: int, k: int, seed: int) -> np.ndarray:
 def column_subset(n: int, k: int, seed: int) -> np.ndarray:
     """k distinct sorted column indices (column independence of the filter)."""
     return np.sort(_rng(seed, _STREAM_SUBSET + 1).permutation(n)[:k])
+
+
+def banded_operator(N: int, band: int, far: int, s: float, seed: int) -> dict:
+    """Symmetric H whose density decays away from the diagonal, in CSR (columns
+    ascending): every (i, j) with |i - j| <= band is stored (dense near the diagonal),
+    with H_ij = H_ji = exp(-|i - j| / (band / 4)) (-0.5 + s z_ij) off the diagonal and
+    H_ii = 2.5 + s z_ii; outside the band about `far` random couplings per row (pairs
+    drawn uniformly with |i - j| > band, value 0.01 z, mirrored) -- a stand-in for the
+    paper's H^L, whose diagonal blocks are much denser than the rest (Sec. 4.1).
+    """
+    rng = _rng(seed, _STREAM_BAND)
+    d = np.arange(-band, band + 1)
+    i = np.repeat(np.arange(N, dtype=np.int64), d.size)
+    j = i + np.tile(d, N)
+    keep = (j >= 0) & (j < N)
+    i, j = i[keep], j[keep]
+    lo, hi = np.minimum(i, j), np.maximum(i, j)
+    # one draw per unordered pair, keyed by (lo, offset) so that (i, j) and (j, i) agree
+    zz = rng.standard_normal((N, band + 1))
+    z = zz[lo, hi - lo]
+    off = np.abs(i - j)
+    val = np.where(off == 0, 2.5 + s * z, np.exp(-off / (band / 4.0)) * (-0.5 + s * z))
+    # far couplings
+    r2 = _rng(seed, _STREAM_FAR)
+    cnt = N * far // 2
+    a = r2.integers(0, N, size=cnt)
+    b = r2.integers(0, N, size=cnt)
+    ok = np.abs(a - b) > band
+    a, b = a[ok], b[ok]
+    pair = np.unique(np.minimum(a, b) * N + np.maximum(a, b))
+    fa, fb = pair // N, pair % N
+    fz = 0.01 * r2.standard_normal(pair.size)
+    rows = np.concatenate([i, fa, fb])
+    cols = np.concatenate([j, fb, fa])
+    vals = np.concatenate([val, fz, fz])
+    order = np.lexsort((cols, rows))
+    rows, cols, vals = rows[order], cols[order], vals[order]
+    row_ptr = np.zeros(N + 1, dtype=np.int64)
+    np.cumsum(np.bincount(rows, minlength=N), out=row_ptr[1:])
+    return dict(N=N, nnz=int(row_ptr[-1]), row_ptr=row_ptr, col=cols.astype(np.int32), val=vals.copy())
+
+
+def split_from_csr(csr: dict, block: int) -> dict:
+    """The split storage of H (pure data movement): rows in blocks of `block`; the
+    entries whose column lies in the row's own block go to a dense block x block
+    diagonal block (stacked, zero-padded past N), the rest to an off-diagonal CSR in
+    stored order.  Returns dict(block, n_blocks, diag[float64, n_blocks*block*block],
+    off=dict(N, nnz, row_ptr, col, val))."""
+    N = csr["N"]
+    nblk = (N + block - 1) // block
+    rows = np.repeat(np.arange(N, dtype=np.int64), np.diff(csr["row_ptr"]))
+    cols = csr["col"].astype(np.int64)
+    inside = (rows // block) == (cols // block)
+    diag = np.zeros(nblk * block * block, dtype=np.float64)
+    ri, ci = rows[inside], cols[inside]
+    diag[(ri // block) * block * block + (ri % block) * block + (ci % block)] = csr["val"][inside]
+    out_rows = rows[~inside]
+    row_ptr = np.zeros(N + 1, dtype=np.int64)
+    np.cumsum(np.bincount(out_rows, minlength=N), out=row_ptr[1:])
+    off = dict(N=N, nnz=int(row_ptr[-1]), row_ptr=row_ptr, col=csr["col"][~inside].copy(),
+               val=csr["val"][~inside].copy())
+    return dict(block=block, n_blocks=nblk, diag=diag, off=off)

@@ -65,6 +65,7 @@ int chfsi_version(void);
 #define CHFSI_CSR 0
 #define CHFSI_BSR 1
 #define CHFSI_HYBRID 2   /* both layouts of one operator, rows in the blocked order (see below) */
+#define CHFSI_SPLIT 3    /* dense diagonal blocks + CSR of the rest (Sec. 4.1-4.2, see below) */
 
 /*
  * Sparse symmetric H (the projected Kohn-Sham Hamiltonian H^L of Sec. 3.3,
@@ -97,15 +98,36 @@ typedef struct {
 } chfsi_bsr;
 
 /*
- * kind = CHFSI_CSR uses `csr`, CHFSI_BSR uses `bsr`.  CHFSI_HYBRID carries the
- * same operator in both layouts with the CSR rows in the blocked order: FP64 and
- * FP32 steps (and the backward pass, the Lanczos bounds and the projection) use
- * the CSR kernels, BF16-operand steps use the BSR blocks on the tensor cores.
+ * The paper's split storage of a row-partitioned H (Sec. 4.1-4.2: the dense diagonal
+ * block H^{L(D)}_k and the sparse off-diagonal part H^{L(OD)}_k of each row block):
+ * rows in consecutive blocks of `block` rows; diagonal block k (rows and columns
+ * k*block .. (k+1)*block - 1) is stored dense, every entry outside the diagonal
+ * blocks in the CSR `off` over all n_rows rows with global column indices (an entry
+ * inside a diagonal block must not appear in `off`).  block is a multiple of 128 and
+ * at most 8192; diag holds ceil(n_rows / block) blocks of block x block doubles, each
+ * row-major, stacked (rows and columns past n_rows zero).  The filter runs the dense
+ * blocks on the BF16 tensor cores by Ozaki slices (see chfsi_ozaki_gemm) and the
+ * sparse part with the CSR kernel, FP64 schedule only.
  */
 typedef struct {
-    int32_t kind;      /* CHFSI_CSR, CHFSI_BSR or CHFSI_HYBRID */
+    int64_t n_rows;
+    int32_t block;
+    const double* diag;
+    chfsi_csr off;
+} chfsi_split;
+
+/*
+ * kind = CHFSI_CSR uses `csr`, CHFSI_BSR uses `bsr`, CHFSI_SPLIT uses `split`.
+ * CHFSI_HYBRID carries the same operator in both layouts with the CSR rows in the
+ * blocked order: FP64 and FP32 steps (and the backward pass, the Lanczos bounds and
+ * the projection) use the CSR kernels, BF16-operand steps use the BSR blocks on the
+ * tensor cores.  CHFSI_SPLIT is accepted by the filter (FP64 schedule) only.
+ */
+typedef struct {
+    int32_t kind;      /* CHFSI_CSR, CHFSI_BSR, CHFSI_HYBRID or CHFSI_SPLIT */
     chfsi_csr csr;
     chfsi_bsr bsr;
+    chfsi_split split;
 } chfsi_matrix;
 
 /* ------------------------------------------------------------------ precision schedule */
@@ -293,12 +315,13 @@ int chfsi_ozaki_gemm_workspace_size(int32_t op, int64_t M, int64_t Nc, int64_t K
  * Ozaki-scheme splitting: each row of the K-major operands (A^T or A, and B^T) is
  * scaled by a power of two and rounded to a 56-bit fixed-point number held as seven
  * balanced 8-bit digits, each digit slice exact in BF16; the 28 slice products
- * with digit weights down to 2^-64 run as tcgen05 MMAs whose FP32 accumulation is
- * exact for the leading levels (integer multiples, partial sums below 2^24, drained
- * every 256 K into 64-bit integers of unit 2^-48) and rounded to 2^-48 for the rest.
- * |C_ij - (A_hat B_hat^T)_ij| is below K 2^-46 times the product of the two rows'
- * largest magnitudes (errors of random sign make it about sqrt(K) times that in
- * practice, about 2^-48 of a typical term).  Row-major blocks with leading dimensions; C
+ * with digit weights down to 2^-64 run as tcgen05 MMAs, one FP32 accumulator per digit
+ * level, each drained before its sums pass 2^24 units, so that the accumulation is
+ * exact (integer multiples, whatever the tensor cores' rounding) and ends in two
+ * 64-bit integers per element.  The only errors are the 56-bit rounding of the inputs
+ * and the dropped slice pairs: |C_ij - (A_hat B_hat^T)_ij| is below K 2^-50 times the
+ * product of the two rows' largest magnitudes (errors of random sign make it about
+ * sqrt(K) times that in practice).  Row-major blocks with leading dimensions; C
  * must not overlap A or B.  The workspace (chfsi_ozaki_gemm_workspace_size) holds
  * the status word, the slices (14 bytes per operand element) and the split-K
  * partial tiles.  A non-finite input sets CHFSI_ERR_NONFINITE in the status word.

@@ -25,6 +25,7 @@ CHFSI_ERR_UNSUPPORTED = 9
 CHFSI_CSR = 0
 CHFSI_BSR = 1
 CHFSI_HYBRID = 2
+CHFSI_SPLIT = 3
 
 CHFSI_F64 = 0
 CHFSI_F32 = 1
@@ -49,8 +50,12 @@ class chfsi_bsr(ctypes.Structure):
                 ("val", _vp)]
 
 
+class chfsi_split(ctypes.Structure):
+    _fields_ = [("n_rows", _i64), ("block", _i32), ("diag", _vp), ("off", chfsi_csr)]
+
+
 class chfsi_matrix(ctypes.Structure):
-    _fields_ = [("kind", _i32), ("csr", chfsi_csr), ("bsr", chfsi_bsr)]
+    _fields_ = [("kind", _i32), ("csr", chfsi_csr), ("bsr", chfsi_bsr), ("split", chfsi_split)]
 
 
 class chfsi_schedule(ctypes.Structure):

@@ -133,6 +133,33 @@ class HybridMatrix:
         return m
 
 
+@dataclass
+class SplitMatrix:
+    """The paper's split storage (Sec. 4.1-4.2): dense block x block diagonal blocks
+    (stacked, row-major) and the off-diagonal entries in CSR, resident on the device.
+    Accepted by the filter (FP64 schedule); the dense blocks run on the tensor cores."""
+    diag: torch.Tensor
+    off: CsrMatrix
+    block: int
+    n_rows: int
+
+    @classmethod
+    def from_arrays(cls, diag, block, off_row_ptr, off_col, off_val, device="cuda") -> "SplitMatrix":
+        off = CsrMatrix.from_arrays(off_row_ptr, off_col, off_val, device=device)
+        dg = torch.as_tensor(np.ascontiguousarray(diag, dtype=np.float64)).to(device)
+        return cls(dg, off, int(block), off.n_rows)
+
+    @property
+    def device(self) -> torch.device:
+        return self.diag.device
+
+    def descriptor(self, val: Optional[torch.Tensor] = None) -> _abi.chfsi_matrix:
+        m = _abi.chfsi_matrix()
+        m.kind = _abi.CHFSI_SPLIT
+        m.split = _abi.chfsi_split(self.n_rows, self.block, _ptr(self.diag), self.off.descriptor().csr)
+        return m
+
+
 class Workspace:
     """Grow-only device scratch buffer (allocate once, outside timed loops)."""
 

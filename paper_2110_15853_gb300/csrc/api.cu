@@ -40,7 +40,7 @@ inline int64_t pad8(int64_t n) { return (n + 7) / 8 * 8; }
 // step's BF16 copy is block-major over all states).
 constexpr int64_t kSlab = 512;
 inline int64_t filter_slab(const chfsi_matrix* H, int64_t n) {
-    return (H->kind == CHFSI_CSR && n > kSlab) ? kSlab : n;
+    return ((H->kind == CHFSI_CSR || H->kind == CHFSI_SPLIT) && n > kSlab) ? kSlab : n;
 }
 
 int check_csr(const chfsi_csr& c) {
@@ -60,8 +60,22 @@ int check_bsr(const chfsi_bsr& b) {
 inline bool has_csr(const chfsi_matrix* H) { return H->kind == CHFSI_CSR || H->kind == CHFSI_HYBRID; }
 inline bool has_bsr(const chfsi_matrix* H) { return H->kind == CHFSI_BSR || H->kind == CHFSI_HYBRID; }
 
+int check_split(const chfsi_split& sp) {
+    int rc = check_csr(sp.off);
+    if (rc) return rc;
+    if (sp.n_rows != sp.off.n_rows || !sp.diag) return CHFSI_ERR_ARG;
+    if (sp.block <= 0 || sp.block % 128 || sp.block > 8192) return CHFSI_ERR_UNSUPPORTED;
+    return CHFSI_OK;
+}
+
 int rows_of(const chfsi_matrix* H, int64_t* N) {
     if (!H) return CHFSI_ERR_ARG;
+    if (H->kind == CHFSI_SPLIT) {
+        const int rc = check_split(H->split);
+        if (rc) return rc;
+        *N = H->split.n_rows;
+        return CHFSI_OK;
+    }
     if (H->kind != CHFSI_CSR && H->kind != CHFSI_BSR && H->kind != CHFSI_HYBRID) return CHFSI_ERR_ARG;
     int rc;
     if (has_csr(H) && (rc = check_csr(H->csr))) return rc;
@@ -72,6 +86,8 @@ int rows_of(const chfsi_matrix* H, int64_t* N) {
 }
 
 int64_t bsr_values(const chfsi_matrix* H) { return H->bsr.n_blocks * (int64_t)H->bsr.bdim * H->bsr.bdim; }
+
+inline int split_block(const chfsi_matrix* H) { return H->kind == CHFSI_SPLIT ? H->split.block : 0; }
 
 // Values of H converted for the low-precision steps (FP32 copy for CUDA-core
 // steps, BF16 blocks for tensor-core steps): size of the larger candidate.
@@ -141,6 +157,9 @@ int schedule_prefix(const chfsi_schedule* sched, int m, int* L, int* low_kind) {
 
 struct FilterLayout {
     double* W[2] = {nullptr, nullptr};
+    double* T = nullptr;               // split layout: the dense-block product of a step
+    unsigned char* bd = nullptr;       // split layout: scratch of the block-diagonal product
+    size_t bd_bytes = 0;
     void* hlow = nullptr;
     float* F[3] = {nullptr, nullptr, nullptr};
     __nv_bfloat16* S[2] = {nullptr, nullptr};
@@ -148,13 +167,19 @@ struct FilterLayout {
 };
 
 template <typename A>
-void filter_layout(A& ar, int64_t N, int64_t n, int m, int L, int low_kind, int64_t nvals, FilterLayout* out) {
+void filter_layout(A& ar, int64_t N, int64_t n, int m, int L, int low_kind, int64_t nvals, FilterLayout* out,
+                   int split_block = 0) {
     const int64_t ldw = pad8(n);
     FilterLayout fl;
     ar.template take<unsigned char>(kStatusBytes);
     if (m >= 2) {
         fl.W[0] = ar.template take<double>((size_t)(N * ldw));
         fl.W[1] = ar.template take<double>((size_t)(N * ldw));
+    }
+    if (split_block > 0) {
+        fl.T = ar.template take<double>((size_t)(N * ldw));
+        fl.bd_bytes = ozaki_blockdiag_bytes(N, split_block, n);
+        fl.bd = ar.template take<unsigned char>(fl.bd_bytes);
     }
     if (L > 0 && low_kind == CHFSI_F32X2) {
         fl.hlow = ar.template take<float2>((size_t)nvals);
@@ -268,8 +293,9 @@ int chfsi_filter_workspace_size(const chfsi_matrix* H, int64_t n_cols, int32_t m
     int L = 0, low = 0;
     rc = schedule_prefix(sched, m, &L, &low);
     if (rc) return rc;
+    if (H->kind == CHFSI_SPLIT && L > 0) return CHFSI_ERR_UNSUPPORTED;
     SizeOnly sz;
-    filter_layout(sz, N, filter_slab(H, n_cols), m, L, low, low_values(H), nullptr);
+    filter_layout(sz, N, filter_slab(H, n_cols), m, L, low, low_values(H), nullptr, split_block(H));
     *bytes = sz.used;
     return CHFSI_OK;
 }
@@ -373,7 +399,17 @@ int filter_columns(const FilterRun& R, const double* X, int64_t ldx, double* Y, 
             else { io.prev = f64_buf(k - 2); io.prev_t = Buf::F64; io.ldp = f64_ld(k - 2); }
         }
         io.out = f64_buf(k); io.out_t = Buf::F64; io.ldo = f64_ld(k);
-        rc = run_step(H, R.csr64, R.bsr64, StepMath::F64, n, io, al[k], c, k >= 2 ? be[k] : 0.0, vec, st, s);
+        if (H->kind == CHFSI_SPLIT) {
+            // dense diagonal blocks on the tensor cores, then the sparse rest with that sum added
+            rc = ozaki_blockdiag_apply(static_cast<const double*>(io.cur), io.ldc, N, H->split.block, n, fl.T, ldw,
+                                       fl.bd, fl.bd_bytes, st, s);
+            if (rc) return rc;
+            io.addend = fl.T;
+            io.lda = ldw;
+            rc = csr_step(R.csr64, StepMath::F64, n, io, al[k], c, k >= 2 ? be[k] : 0.0, vec, st, s);
+        } else {
+            rc = run_step(H, R.csr64, R.bsr64, StepMath::F64, n, io, al[k], c, k >= 2 ? be[k] : 0.0, vec, st, s);
+        }
         if (rc) return rc;
     }
     return CHFSI_OK;
@@ -396,8 +432,9 @@ int chfsi_filter(const chfsi_matrix* H, const double* X, int64_t ldx, double* Y,
     if ((rc = schedule_prefix(sched, m, &L, &low))) return rc;
     if (!ws || !aligned16(ws)) return CHFSI_ERR_ARG;
     const int64_t slab = filter_slab(H, n_cols);
+    if (H->kind == CHFSI_SPLIT && L > 0) return CHFSI_ERR_UNSUPPORTED;
     SizeOnly sz;
-    filter_layout(sz, N, slab, m, L, low, low_values(H), nullptr);
+    filter_layout(sz, N, slab, m, L, low, low_values(H), nullptr, split_block(H));
     if (ws_bytes < sz.used) return CHFSI_ERR_NOMEM;
     if (L > 0 && low == CHFSI_F32X2 && !has_csr(H)) return CHFSI_ERR_UNSUPPORTED;
 
@@ -414,10 +451,18 @@ int chfsi_filter(const chfsi_matrix* H, const double* X, int64_t ldx, double* Y,
     R.s = as_stream(stream);
     R.st = status_word(ws);
     Arena ar(ws, ws_bytes);
-    filter_layout(ar, N, slab, m, L, low, low_values(H), &R.fl);
+    filter_layout(ar, N, slab, m, L, low, low_values(H), &R.fl, split_block(H));
     coefficients(m, a, b, a0, al, be, R.c);
     CHFSI_CUDA_TRY(cudaMemsetAsync(R.st, 0, sizeof(unsigned), R.s));
     make_devs(H, H->csr.val, H->bsr.val, Buf::F64, &R.csr64, &R.bsr64);
+    if (H->kind == CHFSI_SPLIT) {
+        // the off-diagonal part through the CSR kernel; the dense blocks sliced once
+        const chfsi_csr& o = H->split.off;
+        R.csr64 = CsrDev{o.n_rows, o.nnz, o.row_ptr, o.col, o.val, Buf::F64};
+        if ((rc = ozaki_blockdiag_prepare(H->split.diag, N, H->split.block, slab, R.fl.bd, R.fl.bd_bytes, R.st,
+                                          R.s)))
+            return rc;
+    }
 
     // low-precision copies of H's values, once for all slabs
     cudaStream_t s = R.s;
@@ -739,6 +784,7 @@ void rr_layout(Ar& ar, int64_t N, int64_t n, int lwork, int precision, int64_t n
 int rr_check(const chfsi_matrix* H, int64_t n_cols, int32_t cholqr_passes, int32_t precision, int64_t* N) {
     int rc = rows_of(H, N);
     if (rc) return rc;
+    if (H->kind == CHFSI_SPLIT) return CHFSI_ERR_UNSUPPORTED;
     if (n_cols < 1 || n_cols > *N || (cholqr_passes != 1 && cholqr_passes != 2)) return CHFSI_ERR_ARG;
     if (precision != CHFSI_F64 && precision != CHFSI_F32X2 && precision != CHFSI_F64_OZAKI) return CHFSI_ERR_ARG;
     if (precision == CHFSI_F32X2 && !has_csr(H)) return CHFSI_ERR_UNSUPPORTED;

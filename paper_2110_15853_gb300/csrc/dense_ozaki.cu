@@ -18,29 +18,29 @@
 // per term, i.e. about 2^{-48} of a typical term).
 //
 // Exact accumulation.  A product of two slices is d_t g_u 2^{-8(t+u)}, an integer
-// multiple of 2^{-8l} at level l = t + u with |d_t g_u| <= 2^14.  The FP32 tensor-core
-// accumulator sums such multiples without rounding while the partial sums stay at or
-// below 2^24 units, so the pairs of levels 2, 3, 4 and 5 (1, 2, 3 and 4 pairs) each
-// accumulate into their own TMEM accumulator E2 .. E5 for at most 256 K (4 * 256 *
-// 2^14 = 2^24) and are then drained exactly into a 64-bit integer per output element
-// (units 2^{-48}).  The 18 pairs of levels 6-8 share one FP32 accumulator I; its sums
-// stay near 2^{-31} of the row scales, so their FP32 rounding is below 2^{-55}, and it
-// is drained the same way (rounded to 2^{-48}) every 256 K.  A work item spans at
-// most 8192 K (longer sums are split over items and the FP64 partial tiles added),
-// which bounds the integer by 2^59.  C = 2^{e_i + f_j - 48} * (the integer),
-// converted once at the end.
+// multiple of 2^{-8l} at level l = t + u with |d_t g_u| <= 2^14.  Every level l = 2 .. 8
+// has its own FP32 accumulator E_l in TMEM, and each is drained before its sums can
+// pass 2^24 units (levels 2-5 every 256 K, levels 6-8 every 128 K; at most 4 and 7
+// pairs per level), so the tensor-core accumulation -- which truncates rather than
+// rounds -- never rounds at all: the sums are exact integers.  The drains add them to
+// two 64-bit integers per output element, levels 2-5 in units of 2^{-40} and levels
+// 6-8 in units of 2^{-64}.  A work item spans at most 8192 K (longer sums are split
+// over items and the FP64 partial tiles added), which bounds the integers by 2^51 and
+// 2^46.  C = 2^{e_i + f_j} (2^{-40} hi + 2^{-64} lo), converted once at the end, so the
+// only errors are the 56-bit rounding of the inputs and the dropped pairs (weights
+// 2^{-72} and below).
 //
-// Kernel.  Persistent, warp-specialised, one CTA per SM, 128 x 96 output tiles:
+// Kernel.  Persistent, warp-specialised, one CTA per SM, 128 x 64 output tiles:
 //   warp 0, lane 0 : TMA producer -- per K-block of 32, the seven A (128-row) and
-//                    seven B (96-row) slice tiles (64-byte swizzle) into a two-stage ring;
-//   warp 1         : owns 512 TMEM columns: five 96-column FP32 accumulators
-//                    E2 | E3 | E4 | E5 | I; lane 0 issues the 28 x 2 MMAs (M = 128,
-//                    N = 96, K = 16) of each stage;
-//   warps 2-5      : epilogue; warp w reads TMEM lanes 32 (w % 4) .. + 31 (one output
-//                    row per thread) and keeps the row's 96 integers in registers.
-// Drains alternate between group X (E2, E3: after K-blocks 3, 11, 19, ...) and group Y
-// (E4, E5, I: after K-blocks 7, 15, ...); the issuer runs the other group's MMAs of the
-// next stage before it waits for a drain.  Every mbarrier wait is bounded; on a
+//                    seven B (64-row) slice tiles (64-byte swizzle) into a two-stage ring;
+//   warp 1         : owns 512 TMEM columns, seven 64-column FP32 accumulators E2 .. E8;
+//                    lane 0 issues the 28 x 2 MMAs (M = 128, N = 64, K = 16) per stage;
+//   warps 2-17     : epilogue; warp w reads TMEM lanes 32 (w % 4) .. + 31 (one output
+//                    row per thread), columns 16 ((w - 2) / 4) .. + 15, and keeps those
+//                    16 x 2 integers in registers.
+// Drains alternate between group X (E2 .. E5, after K-blocks 5, 13, 21, ...) and group
+// Y (E6 .. E8, after K-blocks 3, 7, 11, ...); the issuer runs the other group's MMAs of
+// the next stage before it waits for a drain.  Every mbarrier wait is bounded; on a
 // timeout the CTA flags DEV_TIMEOUT, stops, waits (bounded) for its copies and MMAs in
 // flight, frees TMEM and exits.
 #include "common.cuh"
@@ -55,19 +55,21 @@ using namespace tc;
 
 constexpr int kSlices = 7;
 constexpr int kPairs = kSlices * (kSlices + 1) / 2;   // slice pairs with t + u <= 8 (1-based)
-constexpr int kAccs = 5;                              // E2, E3, E4, E5, I
-constexpr int kGroupX = 3;                            // pairs 0-2 (E2, E3); pairs 3-27 are group Y
+constexpr int kAccs = 7;                              // E2 .. E8
+constexpr int kGroupX = 10;                           // pairs 0-9 (E2 .. E5); pairs 10-27 are group Y
 constexpr int kMaxItemKB = 256;                       // K-blocks per work item (8192 K)
 constexpr int kTileM = 128;                           // output rows per tile (TMEM lanes)
-constexpr int kTileN = 96;                            // output columns per tile
+constexpr int kTileN = 64;                            // output columns per tile
 constexpr int kRowPad = 128;                          // operand rows are padded to this
 constexpr int kKB = 32;                               // K per stage (64-byte rows)
 constexpr int kSliceA = kTileM * kKB * 2;             // 8 KB
-constexpr int kSliceB = kTileN * kKB * 2;             // 6 KB
+constexpr int kSliceB = kTileN * kKB * 2;             // 4 KB
 constexpr int kStageBytes = kSlices * (kSliceA + kSliceB);
 constexpr int kStages = 2;
-constexpr int kPeriod = 8;                            // K-blocks between drains of one group
-constexpr int kEpiWarps = 4;
+constexpr int kPeriodX = 8;                           // K-blocks between drains of group X (256 K)
+constexpr int kPeriodY = 4;                           // K-blocks between drains of group Y (128 K)
+constexpr int kEpiWarps = 16;
+constexpr int kColsPerThread = kTileN / (kEpiWarps / 4);   // 16
 constexpr int kThreads = 32 * (2 + kEpiWarps);
 constexpr int kSmemBytes = kStages * kStageBytes + 1024;
 constexpr uint32_t kTmemCols = 512;
@@ -76,24 +78,26 @@ constexpr uint64_t kWaitNs = 1000000000ull;           // pipeline waits
 constexpr uint64_t kDrainNs = 1000000000ull;          // waits for work already in flight
 constexpr int kXEvent = 1, kYEvent = 2, kFullEvent = 3;
 static_assert(kSmemBytes + 1024 <= 227 * 1024, "shared memory per CTA");
-static_assert(kAccs * kTileN <= (int)kTmemCols, "five accumulators in TMEM");
+static_assert(kAccs * kTileN <= (int)kTmemCols, "seven accumulators in TMEM");
 static_assert(kSliceB % 512 == 0 && kStageBytes % 1024 == 0, "swizzle-atom alignment of the tiles");
+static_assert(kColsPerThread == 16, "16-column TMEM loads");
 
-// Slice pairs (t, u), 0-based, by level, and their accumulator (0: E2 .. 3: E5, 4: I).
-// The first pair of each accumulator: 0, 1, 3, 6, 10.
+// Slice pairs (t, u), 0-based, by level, and their accumulator (level - 2).  The first
+// pair of each accumulator: 0, 1, 3, 6, 10, 15, 21.
 __constant__ int8_t kPairA[kPairs] = {0, 0, 1, 0, 1, 2, 0, 1, 2, 3, 0, 1, 2, 3, 4,
                                       0, 1, 2, 3, 4, 5, 0, 1, 2, 3, 4, 5, 6};
 __constant__ int8_t kPairB[kPairs] = {0, 1, 0, 2, 1, 0, 3, 2, 1, 0, 4, 3, 2, 1, 0,
                                       5, 4, 3, 2, 1, 0, 6, 5, 4, 3, 2, 1, 0};
 __constant__ int8_t kPairAcc[kPairs] = {0, 1, 1, 2, 2, 2, 3, 3, 3, 3, 4, 4, 4, 4, 4,
-                                        4, 4, 4, 4, 4, 4, 4, 4, 4, 4, 4, 4, 4};
+                                        5, 5, 5, 5, 5, 5, 6, 6, 6, 6, 6, 6, 6};
 
-// The drain after K-block kb of an item of KB blocks: 0 none, kXEvent (E2, E3),
-// kYEvent (E4, E5, I) or kFullEvent (all five, then the output).
+// The drain after K-block kb of an item of KB blocks: 0 none, kXEvent (E2 .. E5),
+// kYEvent (E6 .. E8) or kFullEvent (all seven, then the output).
 __device__ __forceinline__ int event_at(int kb, int KB) {
     if (kb == KB - 1) return kFullEvent;
-    const int r = kb % kPeriod;
-    return r == kPeriod / 2 - 1 ? kXEvent : (r == kPeriod - 1 ? kYEvent : 0);
+    if (kb % kPeriodY == kPeriodY - 1) return kYEvent;
+    if (kb % kPeriodX == kPeriodX - 3) return kXEvent;
+    return 0;
 }
 
 struct OzArgs {
@@ -101,7 +105,7 @@ struct OzArgs {
     int64_t ldc;
     double* C;                // output (direct mode), or
     double* part;             // split-K partial tiles [splits][Mp][Np] (split mode)
-    int64_t Mp, Np;           // partial-tile extents: tilesM * 128, tilesN * 96
+    int64_t Mp, Np;           // partial-tile extents: tilesM * 128, tilesN * 64
     const int* expA;          // biased exponent field of each row's largest |value| (0: zero row)
     const int* expB;
     int64_t rowsA_pad, rowsB_pad;
@@ -111,12 +115,15 @@ struct OzArgs {
     int splits;
     int symmetric;            // only tiles that reach the upper triangle (j >= i)
     int b_upper;              // B_hat[j][k] = 0 for k > j: K limited to the tile's last column
-    int64_t pairs;            // tiles per split
+    int64_t pairs;            // tiles per split and batch
+    int nbatch;               // independent products (diagonal blocks of the split layout)
+    int64_t m_batch;          // output rows per batch (M when nbatch = 1)
+    int64_t a_batch_rows, b_batch_rows;   // operand rows per batch in the slice arrays
     unsigned* status;
 };
 
 struct Item {
-    int tm, tn, kb0, KB;
+    int batch, tm, tn, kb0, KB;
 };
 
 // First column tile of row tile tm that reaches the upper triangle (j >= i).
@@ -124,7 +131,9 @@ __device__ __host__ __forceinline__ int first_upper_tn(int tm) { return (tm * kT
 
 __device__ __forceinline__ Item decode(const OzArgs& g, int64_t item) {
     Item it;
-    const int z = (int)(item / g.pairs);
+    const int64_t per_split = g.pairs * g.nbatch;
+    const int z = (int)(item / per_split);
+    it.batch = (int)((item % per_split) / g.pairs);
     int64_t p = item % g.pairs;
     if (g.symmetric) {
         int tm = 0;
@@ -146,16 +155,13 @@ __device__ __forceinline__ Item decode(const OzArgs& g, int64_t item) {
     return it;
 }
 
-// 32 accumulator columns of this warp's 32 TMEM lanes (one row per lane).
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+// 16 accumulator columns of this warp's 32 TMEM lanes (one row per lane).
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
         : "r"(taddr));
 }
 
@@ -171,6 +177,14 @@ __device__ __forceinline__ double scale_pow2(double x, int e) {
     if (ex <= 0) return __longlong_as_double(sign);
     if (ex >= 0x7ff) return __longlong_as_double(sign | (0x7ffll << 52));
     return __longlong_as_double(b + ((long long)e << 52));
+}
+
+// 2^{e} (hi 2^{-40} + lo 2^{-64}) from the two exact integers of an output element.
+__device__ __forceinline__ double combine(long long hi, long long lo, int e) {
+    double v = 0.0;
+    if (hi != 0) v = scale_pow2((double)hi, e - 40);
+    if (lo != 0) v += scale_pow2((double)lo, e - 64);
+    return v;
 }
 
 __global__ void __launch_bounds__(kThreads, 1)
@@ -221,12 +235,14 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                 mbar_expect_tx(&full[s], kStageBytes);
 #pragma unroll
                 for (int t = 0; t < kSlices; t++)
-                    tma_load_2d(st + t * kSliceA, &tmA, x, (int)(t * g.rowsA_pad + (int64_t)it.tm * kTileM),
+                    tma_load_2d(st + t * kSliceA, &tmA, x,
+                                (int)(t * g.rowsA_pad + it.batch * g.a_batch_rows + (int64_t)it.tm * kTileM),
                                 sa(&full[s]));
 #pragma unroll
                 for (int t = 0; t < kSlices; t++)
                     tma_load_2d(st + kSlices * kSliceA + t * kSliceB, &tmB, x,
-                                (int)(t * g.rowsB_pad + (int64_t)it.tn * kTileN), sa(&full[s]));
+                                (int)(t * g.rowsB_pad + it.batch * g.b_batch_rows + (int64_t)it.tn * kTileN),
+                                sa(&full[s]));
             }
             if (!ok) { *abort_v = 1; break; }
         }
@@ -250,10 +266,9 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;");
                 const uint32_t st = sa(smem + (size_t)s * kStageBytes);
-                const int r = kb % kPeriod;
                 // which group starts fresh in this stage (its drain must have ended first)
-                const bool resetX = kb == 0 || r == kPeriod / 2;
-                const bool resetY = kb == 0 || r == 0;
+                const bool resetX = kb == 0 || kb % kPeriodX == kPeriodX - 2;
+                const bool resetY = kb == 0 || kb % kPeriodY == 0;
                 auto wait_drain = [&]() -> bool {
                     const bool w = mbar_wait(sa(&eempty), (uint32_t)(ev_wait & 1), kWaitNs);
                     ev_wait++;
@@ -265,8 +280,8 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                 auto issue = [&](int p0, int p1) {
                     for (int p = p0; p < p1; p++) {
                         const int acc = kPairAcc[p];
-                        const bool first =
-                            (p == 0 || p == 1 || p == 3 || p == 6 || p == 10) && (p < kGroupX ? resetX : resetY);
+                        const bool head = p == 0 || p == 1 || p == 3 || p == 6 || p == 10 || p == 15 || p == 21;
+                        const bool first = head && (p < kGroupX ? resetX : resetY);
                         const uint64_t da = desc_kmajor(st + kPairA[p] * kSliceA, 64);
                         const uint64_t db = desc_kmajor(st + kSlices * kSliceA + kPairB[p] * kSliceB, 64);
                         const uint32_t dt = tmem + (uint32_t)(acc * kTileN);
@@ -285,11 +300,11 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                 if (kb == 0) {
                     if (ev_commit > 0) w = wait_drain();     // the previous item's output drain
                     issue(0, kPairs);
-                } else if (resetX) {                           // E2, E3 drained after the last block
+                } else if (resetX) {                           // E2 .. E5 drained after the last block
                     issue(kGroupX, kPairs);
                     w = wait_drain();
                     issue(0, kGroupX);
-                } else if (resetY) {                           // E4, E5, I drained after the last block
+                } else if (resetY) {                           // E6 .. E8 drained after the last block
                     issue(0, kGroupX);
                     w = wait_drain();
                     issue(kGroupX, kPairs);
@@ -312,14 +327,14 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         }
     } else if (warp >= 2) {
         // ---------------- epilogue: exact drains into 64-bit integers, then the output
-        const int q = warp & 3;
+        const int q = warp & 3, h = (warp - 2) >> 2;
         const uint32_t lane_base = (uint32_t)(32 * q) << 16;
         int64_t ev = 0;
-        long long acc[kTileN];
+        long long hi[kColsPerThread], lo[kColsPerThread];
         for (int64_t item = blockIdx.x; item < total; item += gridDim.x) {
             const Item it = decode(g, item);
 #pragma unroll
-            for (int c = 0; c < kTileN; c++) acc[c] = 0;
+            for (int c = 0; c < kColsPerThread; c++) hi[c] = lo[c] = 0;
             bool ok = true;
             for (int kb = 0; kb < it.KB; kb++) {
                 const int kind = event_at(kb, it.KB);
@@ -331,20 +346,19 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                 asm volatile("tcgen05.fence::after_thread_sync;");
 #pragma unroll
                 for (int a = 0; a < kAccs; a++) {
-                    const bool take = (a < 2) ? (kind & kXEvent) : (kind & kYEvent);
+                    const bool take = (a < 4) ? (kind & kXEvent) : (kind & kYEvent);
                     if (!take) continue;
-                    // units of 2^-48: E_l holds multiples of 2^-8l (|value| <= 2^24 units),
-                    // I is rounded to 2^-48 (|value| < 2^27 units)
-                    const float sc = pow2f(a < 4 ? 8 * (a + 2) : 48);
-                    const long long mul = 1ll << (a < 4 ? 48 - 8 * (a + 2) : 0);
+                    // E_l (l = a + 2) holds an exact multiple of 2^-8l below 2^24 units
+                    const float up = pow2f(8 * (a + 2));
+                    const long long mul = 1ll << (a < 4 ? 40 - 8 * (a + 2) : 64 - 8 * (a + 2));
+                    uint32_t v[16];
+                    tmem_ld16(tmem + lane_base + (uint32_t)(a * kTileN + h * kColsPerThread), v);
+                    asm volatile("tcgen05.wait::ld.sync.aligned;");
 #pragma unroll
-                    for (int part = 0; part < kTileN / 32; part++) {
-                        uint32_t v[32];
-                        tmem_ld32(tmem + lane_base + (uint32_t)(a * kTileN + part * 32), v);
-                        asm volatile("tcgen05.wait::ld.sync.aligned;");
-#pragma unroll
-                        for (int c = 0; c < 32; c++)
-                            acc[part * 32 + c] += (long long)__float2int_rn(__uint_as_float(v[c]) * sc) * mul;
+                    for (int c = 0; c < 16; c++) {
+                        const long long iv = (long long)__float2int_rn(__uint_as_float(v[c]) * up) * mul;
+                        if (a < 4) hi[c] += iv;
+                        else lo[c] += iv;
                     }
                 }
                 asm volatile("tcgen05.fence::before_thread_sync;");
@@ -352,30 +366,27 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                 if (lane == 0) mbar_arrive(&eempty);
                 ev++;
                 if (kind == kFullEvent) {
-                    const int64_t row = (int64_t)it.tm * kTileM + 32 * q + lane;
-                    const int64_t col0 = (int64_t)it.tn * kTileN;
-                    const int ea = row < g.M ? g.expA[row] : 0;
+                    const int64_t row = (int64_t)it.tm * kTileM + 32 * q + lane;        // within the batch
+                    const int64_t orow = it.batch * g.m_batch + row;                     // output row
+                    const int64_t col0 = (int64_t)it.tn * kTileN + h * kColsPerThread;
+                    const bool valid = row < g.m_batch && orow < g.M;
+                    const int ea = valid ? g.expA[it.batch * g.a_batch_rows + row] : 0;
+                    const int* expB = g.expB + it.batch * g.b_batch_rows;
                     if (g.part) {
                         const int z = it.kb0 / g.kb_split;
                         double* dst = g.part + ((int64_t)z * g.Mp + row) * g.Np + col0;
 #pragma unroll
-                        for (int c = 0; c < kTileN; c++) {
-                            const int eb = (col0 + c < g.Nc) ? g.expB[col0 + c] : 0;
-                            double v = 0.0;
-                            if (acc[c] != 0 && ea != 0 && eb != 0)
-                                v = scale_pow2((double)acc[c], (ea - 1021) + (eb - 1021) - 48);
-                            dst[c] = v;
+                        for (int c = 0; c < kColsPerThread; c++) {
+                            const int eb = (col0 + c < g.Nc) ? expB[col0 + c] : 0;
+                            dst[c] = (ea != 0 && eb != 0) ? combine(hi[c], lo[c], (ea - 1021) + (eb - 1021)) : 0.0;
                         }
-                    } else if (row < g.M) {
-                        double* dst = g.C + row * g.ldc + col0;
+                    } else if (valid) {
+                        double* dst = g.C + orow * g.ldc + col0;
 #pragma unroll
-                        for (int c = 0; c < kTileN; c++) {
+                        for (int c = 0; c < kColsPerThread; c++) {
                             if (col0 + c >= g.Nc) break;
-                            const int eb = g.expB[col0 + c];
-                            double v = 0.0;
-                            if (acc[c] != 0 && ea != 0 && eb != 0)
-                                v = scale_pow2((double)acc[c], (ea - 1021) + (eb - 1021) - 48);
-                            dst[c] = v;
+                            const int eb = expB[col0 + c];
+                            dst[c] = (ea != 0 && eb != 0) ? combine(hi[c], lo[c], (ea - 1021) + (eb - 1021)) : 0.0;
                         }
                     }
                 }
@@ -395,10 +406,16 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
 
 // Largest biased exponent field of each row of A_hat (A_hat[r][k] = src[k * ld + r]
 // when trans, else src[r * ld + k]); 0 for a row of zeros (subnormals count as zero).
-// exps must be zeroed first.
+// Batch z = blockIdx.z reads src + z * src_bstride over K_z = min(Kb, Ktot - z Kb) and
+// writes exps + z * rows_pad.  exps must be zeroed first.
 template <bool kTrans>
-__global__ void oz_exponents_kernel(const double* __restrict__ src, int64_t ld, int64_t rows, int64_t K, int* exps,
+__global__ void oz_exponents_kernel(const double* __restrict__ src, int64_t ld, int64_t rows, int64_t Kb,
+                                    int64_t Ktot, int64_t src_bstride, int64_t rows_pad, int* exps,
                                     unsigned* status) {
+    const int64_t z = blockIdx.z;
+    src += z * src_bstride;
+    exps += z * rows_pad;
+    const int64_t K = Ktot - z * Kb < Kb ? Ktot - z * Kb : Kb;
     int m = 0;
     bool bad = false;
     if (kTrans) {
@@ -461,14 +478,20 @@ __device__ __forceinline__ void digits_of(double x, int efm, __nv_bfloat16 (&out
     }
 }
 
-// Slices of A_hat into [kSlices][rows_pad][K_pad] (K contiguous), zero in the padding.
+// Slices of A_hat into [kSlices][nbatch * rows_pad][K_pad] (K contiguous), zero in
+// the padding; batch z = blockIdx.z as in oz_exponents_kernel, at rows z * rows_pad.
 // 32 x 32 tiles through shared memory so that reads and writes are both coalesced
 // when A_hat is the transpose of src.
 template <bool kTrans>
-__global__ void oz_slice_kernel(const double* __restrict__ src, int64_t ld, int64_t rows, int64_t K,
-                                const int* __restrict__ exps, int64_t rows_pad, int64_t K_pad,
-                                __nv_bfloat16* __restrict__ slices) {
+__global__ void oz_slice_kernel(const double* __restrict__ src, int64_t ld, int64_t rows, int64_t Kb, int64_t Ktot,
+                                int64_t src_bstride, const int* __restrict__ exps, int64_t rows_pad, int64_t K_pad,
+                                size_t plane, __nv_bfloat16* __restrict__ slices) {
     __shared__ double tile[32][33];
+    const int64_t z = blockIdx.z;
+    src += z * src_bstride;
+    exps += z * rows_pad;
+    slices += (size_t)z * rows_pad * K_pad;
+    const int64_t K = Ktot - z * Kb < Kb ? Ktot - z * Kb : Kb;
     const int64_t r0 = (int64_t)blockIdx.y * 32, k0 = (int64_t)blockIdx.x * 32;
     const int tx = threadIdx.x, ty = threadIdx.y;
     for (int i = ty; i < 32; i += blockDim.y) {
@@ -484,7 +507,6 @@ __global__ void oz_slice_kernel(const double* __restrict__ src, int64_t ld, int6
         }
     }
     __syncthreads();
-    const size_t plane = (size_t)rows_pad * K_pad;
     for (int i = ty; i < 32; i += blockDim.y) {
         const int64_t r = r0 + i, k = k0 + tx;
         if (r >= rows_pad || k >= K_pad) continue;
@@ -521,42 +543,52 @@ struct CountAr {
     }
 };
 
-// Workspace pieces of one operand: exponents (int32 per padded row) and slices.
+// Workspace pieces of one operand: exponents (int32 per padded row) and slices
+// [kSlices][nbatch * rows_pad][K_pad]; batch b holds rows b * rows_pad ...
 struct OzOperand {
     int* exps = nullptr;
     __nv_bfloat16* slices = nullptr;
     int64_t rows = 0, K = 0, rows_pad = 0, K_pad = 0;
+    int nbatch = 1;
+    int64_t plane_rows() const { return (int64_t)nbatch * rows_pad; }
 };
 
 template <typename Ar>
-void oz_operand_layout(Ar& ar, int64_t rows, int64_t K, OzOperand* op) {
+void oz_operand_layout(Ar& ar, int64_t rows, int64_t K, int nbatch, int64_t row_pad, OzOperand* op) {
     OzOperand o;
     o.rows = rows;
     o.K = K;
-    o.rows_pad = round_up(rows, kRowPad);
+    o.nbatch = nbatch;
+    o.rows_pad = round_up(rows, row_pad);
     o.K_pad = round_up(K, kKB);
-    o.exps = ar.template take<int>((size_t)o.rows_pad);
-    o.slices = ar.template take<__nv_bfloat16>((size_t)kSlices * o.rows_pad * o.K_pad);
+    o.exps = ar.template take<int>((size_t)o.plane_rows());
+    o.slices = ar.template take<__nv_bfloat16>((size_t)kSlices * o.plane_rows() * o.K_pad);
     if (op) *op = o;
 }
 
-int oz_prepare(const double* src, int64_t ld, bool trans, const OzOperand& o, unsigned* status, cudaStream_t s) {
-    CHFSI_CUDA_TRY(cudaMemsetAsync(o.exps, 0, sizeof(int) * (size_t)o.rows_pad, s));
+// Exponents and slices of an operand; batch b reads src + b * src_bstride over
+// min(o.K, Ktot - b o.K) of the K dimension.
+int oz_prepare(const double* src, int64_t ld, bool trans, const OzOperand& o, int64_t Ktot, int64_t src_bstride,
+               unsigned* status, cudaStream_t s) {
+    CHFSI_CUDA_TRY(cudaMemsetAsync(o.exps, 0, sizeof(int) * (size_t)o.plane_rows(), s));
     if (trans) {
-        dim3 grid((unsigned)((o.rows + 255) / 256), (unsigned)((o.K + 255) / 256));
-        oz_exponents_kernel<true><<<grid, 256, 0, s>>>(src, ld, o.rows, o.K, o.exps, status);
+        dim3 grid((unsigned)((o.rows + 255) / 256), (unsigned)((o.K + 255) / 256), (unsigned)o.nbatch);
+        oz_exponents_kernel<true><<<grid, 256, 0, s>>>(src, ld, o.rows, o.K, Ktot, src_bstride, o.rows_pad, o.exps,
+                                                      status);
     } else {
-        oz_exponents_kernel<false><<<(unsigned)((o.rows * 32 + 255) / 256), 256, 0, s>>>(src, ld, o.rows, o.K,
-                                                                                          o.exps, status);
+        dim3 grid((unsigned)((o.rows * 32 + 255) / 256), 1, (unsigned)o.nbatch);
+        oz_exponents_kernel<false><<<grid, 256, 0, s>>>(src, ld, o.rows, o.K, Ktot, src_bstride, o.rows_pad, o.exps,
+                                                       status);
     }
     CHFSI_LAUNCH_CHECK();
-    dim3 grid((unsigned)(o.K_pad / 32), (unsigned)(o.rows_pad / 32));
+    dim3 grid((unsigned)(o.K_pad / 32), (unsigned)(o.rows_pad / 32), (unsigned)o.nbatch);
+    const size_t plane = (size_t)o.plane_rows() * o.K_pad;
     if (trans)
-        oz_slice_kernel<true><<<grid, dim3(32, 8), 0, s>>>(src, ld, o.rows, o.K, o.exps, o.rows_pad, o.K_pad,
-                                                          o.slices);
+        oz_slice_kernel<true><<<grid, dim3(32, 8), 0, s>>>(src, ld, o.rows, o.K, Ktot, src_bstride, o.exps, o.rows_pad,
+                                                          o.K_pad, plane, o.slices);
     else
-        oz_slice_kernel<false><<<grid, dim3(32, 8), 0, s>>>(src, ld, o.rows, o.K, o.exps, o.rows_pad, o.K_pad,
-                                                           o.slices);
+        oz_slice_kernel<false><<<grid, dim3(32, 8), 0, s>>>(src, ld, o.rows, o.K, Ktot, src_bstride, o.exps,
+                                                           o.rows_pad, o.K_pad, plane, o.slices);
     CHFSI_LAUNCH_CHECK();
     return CHFSI_OK;
 }
@@ -585,9 +617,9 @@ template <typename Ar>
 void oz_layout(Ar& ar, bool tn_form, int64_t M, int64_t Nc, int64_t K, bool same, int sms, OzPlan* plan) {
     OzPlan p;
     p.same = same;
-    oz_operand_layout(ar, M, K, &p.A);
+    oz_operand_layout(ar, M, K, 1, kRowPad, &p.A);
     if (same) p.B = p.A;
-    else oz_operand_layout(ar, Nc, K, &p.B);
+    else oz_operand_layout(ar, Nc, K, 1, kRowPad, &p.B);
     if (tn_form) {
         const int64_t tm = (M + kTileM - 1) / kTileM, tn = (Nc + kTileN - 1) / kTileN;
         p.splits = oz_splits(tm * tn, (int)(p.A.K_pad / kKB), sms > 0 ? sms : 148);
@@ -596,33 +628,43 @@ void oz_layout(Ar& ar, bool tn_form, int64_t M, int64_t Nc, int64_t K, bool same
     if (plan) *plan = p;
 }
 
+// The product of prepared operands.  nbatch > 1: independent products, batch b of the
+// output at rows b * m_batch (m_batch rows each, the last one clipped at M).
 int oz_run(const OzPlan& p, bool tn_form, double* C, int64_t ldc, int64_t M, int64_t Nc, bool symmetric,
-           bool b_upper, unsigned* status, cudaStream_t s) {
+           bool b_upper, unsigned* status, cudaStream_t s, int nbatch = 1, int64_t m_batch = 0) {
     if (M <= 0 || Nc <= 0) return CHFSI_OK;
     const int64_t K_pad = p.A.K_pad;
-    if (K_pad > (int64_t)1 << 21 || p.A.rows_pad * kSlices > INT32_MAX || p.B.rows_pad * kSlices > INT32_MAX)
+    if (K_pad > (int64_t)1 << 21 || p.A.plane_rows() * kSlices > INT32_MAX || p.B.plane_rows() * kSlices > INT32_MAX)
         return CHFSI_ERR_UNSUPPORTED;
     if (!tn_form && K_pad > (int64_t)kMaxItemKB * kKB) return CHFSI_ERR_UNSUPPORTED;   // no split-K in the nn form
+    if (nbatch > 1 && (tn_form || symmetric || p.A.nbatch != nbatch || p.B.nbatch != nbatch || m_batch <= 0 ||
+                       m_batch > p.A.rows_pad))
+        return CHFSI_ERR_ARG;
     CUtensorMap tmA, tmB;
     int rc;
-    if ((rc = make_map_bf16(&tmA, p.A.slices, K_pad, kSlices * p.A.rows_pad, kKB, kTileM,
+    if ((rc = make_map_bf16(&tmA, p.A.slices, K_pad, kSlices * p.A.plane_rows(), kKB, kTileM,
                             CU_TENSOR_MAP_SWIZZLE_64B)))
         return rc;
-    if ((rc = make_map_bf16(&tmB, p.B.slices, K_pad, kSlices * p.B.rows_pad, kKB, kTileN,
+    if ((rc = make_map_bf16(&tmB, p.B.slices, K_pad, kSlices * p.B.plane_rows(), kKB, kTileN,
                             CU_TENSOR_MAP_SWIZZLE_64B)))
         return rc;
     OzArgs g{};
+    const int64_t mb = nbatch > 1 ? m_batch : M;
     g.M = M;
     g.Nc = Nc;
     g.ldc = ldc;
-    g.tilesM = (int)((M + kTileM - 1) / kTileM);
+    g.nbatch = nbatch;
+    g.m_batch = mb;
+    g.a_batch_rows = p.A.rows_pad;
+    g.b_batch_rows = p.B.rows_pad;
+    g.tilesM = (int)((mb + kTileM - 1) / kTileM);
     g.tilesN = (int)((Nc + kTileN - 1) / kTileN);
     g.Mp = (int64_t)g.tilesM * kTileM;
     g.Np = (int64_t)g.tilesN * kTileN;
     g.expA = p.A.exps;
     g.expB = p.B.exps;
-    g.rowsA_pad = p.A.rows_pad;
-    g.rowsB_pad = p.B.rows_pad;
+    g.rowsA_pad = p.A.plane_rows();
+    g.rowsB_pad = p.B.plane_rows();
     g.kb_total = (int)(K_pad / kKB);
     g.splits = tn_form ? p.splits : 1;
     g.kb_split = (g.kb_total + g.splits - 1) / g.splits;
@@ -642,7 +684,7 @@ int oz_run(const OzPlan& p, bool tn_form, double* C, int64_t ldc, int64_t M, int
         pairs = (int64_t)g.tilesM * g.tilesN;
     }
     g.pairs = pairs;
-    const int64_t total = pairs * g.splits;
+    const int64_t total = pairs * g.splits * nbatch;
     const int dev = current_device();
     if (dev < 0) return CHFSI_ERR_CUDA;
     static bool attr[kMaxDevices] = {};
@@ -662,6 +704,21 @@ int oz_run(const OzPlan& p, bool tn_form, double* C, int64_t ldc, int64_t M, int
         CHFSI_LAUNCH_CHECK();
     }
     return CHFSI_OK;
+}
+
+// Block-diagonal product of the split layout: D slices (prepared once) and the slices
+// of the multiplied block (prepared per product).
+struct OzBlockDiag {
+    OzOperand D, Y;
+};
+
+template <typename Ar>
+void oz_blockdiag_layout(Ar& ar, int64_t N, int B, int64_t n, OzBlockDiag* out) {
+    OzBlockDiag b;
+    const int nblk = (int)((N + B - 1) / B);
+    oz_operand_layout(ar, (int64_t)nblk * B, B, 1, kRowPad, &b.D);   // rows of all blocks, K = B
+    oz_operand_layout(ar, n, B, nblk, 32, &b.Y);                      // per block: n rows (Y columns), K = B
+    if (out) *out = b;
 }
 
 }  // namespace
@@ -686,8 +743,8 @@ int ozaki_gemm_tn(const double* A, int64_t lda, const double* B, int64_t ldb, in
     OzPlan p;
     oz_layout(ar, true, M, Nc, K, same, tc::sm_count(), &p);
     int rc;
-    if ((rc = oz_prepare(A, lda, true, p.A, status, s))) return rc;
-    if (!same && (rc = oz_prepare(B, ldb, true, p.B, status, s))) return rc;
+    if ((rc = oz_prepare(A, lda, true, p.A, K, 0, status, s))) return rc;
+    if (!same && (rc = oz_prepare(B, ldb, true, p.B, K, 0, status, s))) return rc;
     return oz_run(p, true, C, ldc, M, Nc, symmetric, false, status, s);
 }
 
@@ -700,9 +757,45 @@ int ozaki_gemm_nn(const double* A, int64_t lda, const double* B, int64_t ldb, in
     OzPlan p;
     oz_layout(ar, false, M, Nc, K, false, tc::sm_count(), &p);
     int rc;
-    if ((rc = oz_prepare(A, lda, false, p.A, status, s))) return rc;
-    if ((rc = oz_prepare(B, ldb, true, p.B, status, s))) return rc;   // B_hat = B^T: rows are B's columns
+    if ((rc = oz_prepare(A, lda, false, p.A, K, 0, status, s))) return rc;
+    if ((rc = oz_prepare(B, ldb, true, p.B, K, 0, status, s))) return rc;   // B_hat = B^T: rows are B's columns
     return oz_run(p, false, C, ldc, M, Nc, false, b_upper, status, s);
+}
+
+size_t ozaki_blockdiag_bytes(int64_t N, int B, int64_t n) {
+    CountAr ar;
+    oz_blockdiag_layout(ar, N, B, n, nullptr);
+    return ar.s.used;
+}
+
+int ozaki_blockdiag_prepare(const double* diag, int64_t N, int B, int64_t n, void* ws, size_t ws_bytes,
+                            unsigned* status, cudaStream_t s) {
+    if (B <= 0 || B % kTileM || B > kMaxItemKB * kKB) return CHFSI_ERR_UNSUPPORTED;
+    if (ws_bytes < ozaki_blockdiag_bytes(N, B, n)) return CHFSI_ERR_NOMEM;
+    Arena ar(ws, ws_bytes);
+    OzBlockDiag bd;
+    oz_blockdiag_layout(ar, N, B, n, &bd);
+    // every block is B x B row-major, the blocks stacked: one direct operand of nblk * B rows
+    return oz_prepare(diag, B, false, bd.D, B, 0, status, s);
+}
+
+int ozaki_blockdiag_apply(const double* Y, int64_t ldy, int64_t N, int B, int64_t n, double* T, int64_t ldt,
+                          void* ws, size_t ws_bytes, unsigned* status, cudaStream_t s) {
+    if (n <= 0 || N <= 0) return CHFSI_OK;
+    if (B <= 0 || B % kTileM || B > kMaxItemKB * kKB) return CHFSI_ERR_UNSUPPORTED;
+    if (ws_bytes < ozaki_blockdiag_bytes(N, B, n)) return CHFSI_ERR_NOMEM;
+    Arena ar(ws, ws_bytes);
+    OzBlockDiag bd;
+    oz_blockdiag_layout(ar, N, B, n, &bd);
+    // Y_hat of block k = (rows kB .. kB + B - 1 of Y)^T: n rows, K = B (the last block clipped at N)
+    int rc;
+    if ((rc = oz_prepare(Y, ldy, true, bd.Y, N, (int64_t)B * ldy, status, s))) return rc;
+    OzPlan p;
+    p.A = bd.D;
+    p.A.nbatch = bd.Y.nbatch;
+    p.A.rows_pad = B;      // rows per batch in the stacked D operand
+    p.B = bd.Y;
+    return oz_run(p, false, T, ldt, N, n, false, false, status, s, bd.Y.nbatch, B);
 }
 
 }  // namespace chfsi

@@ -2,6 +2,9 @@
 //
 //     Y_out = alpha * (H * Y_cur - c * Y_cur) - beta * Y_prev
 //
+// (FP64 steps may add a precomputed block Y_add to H * Y_cur: the dense-diagonal-block
+// product of the split layout, Sec. 4.1-4.2, with H the off-diagonal part.)
+//
 // one launch per Chebyshev step, so Y_prev, Y_cur and Y_out each make one HBM pass
 // per step (the gathers of H * Y_cur hit L1/L2: the rows a warp gathers are the
 // 3-D grid neighbours of its own row).  The same kernel with alpha = 1, c = 0,
@@ -183,8 +186,8 @@ csr_step_body(int64_t N, const int64_t* __restrict__ row_ptr, const int32_t* __r
               const TH* __restrict__ val, int64_t nnz, int64_t n,
               const TG* __restrict__ Yg, int64_t ldg, const TC* __restrict__ Yc, int64_t ldc,
               const TP* __restrict__ Yp, int64_t ldp, TO* __restrict__ Yo, int64_t ldo,
-              __nv_bfloat16* __restrict__ Ys, int64_t lds, ACC alpha, ACC c, ACC beta, int cap,
-              unsigned* status) {
+              __nv_bfloat16* __restrict__ Ys, int64_t lds, const double* __restrict__ Ya, int64_t lda,
+              ACC alpha, ACC c, ACC beta, int cap, unsigned* status) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TH* s_val = reinterpret_cast<TH*>(smem_raw);
     int32_t* s_col = reinterpret_cast<int32_t*>(smem_raw + sizeof(TH) * (size_t)cap);
@@ -227,13 +230,16 @@ csr_step_body(int64_t N, const int64_t* __restrict__ row_ptr, const int32_t* __r
         for (int64_t jbase = 0; jbase < n; jbase += 32 * V * U) {
             ACC acc[U][V];
             bool on[U];
+            const int64_t j0 = jbase + (int64_t)lane * V;
 #pragma unroll
             for (int u = 0; u < U; u++) {
                 on[u] = jbase + (int64_t)(u * 32 + lane) * V < n;
 #pragma unroll
                 for (int v = 0; v < V; v++) acc[u][v] = (ACC)0;
+                if constexpr (std::is_same<ACC, double>::value) {
+                    if (Ya && on[u]) ldv<double, double, V>(Ya + r * lda + j0 + u * 32 * V, acc[u]);
+                }
             }
-            const int64_t j0 = jbase + (int64_t)lane * V;
             // Register pipeline with two alternating buffers: the gathers of entry q+1
             // are in flight while entry q is accumulated.  Full chunks take a
             // predicate-free path; a bad column index (unstaged rows only) becomes a
@@ -307,9 +313,10 @@ csr_step_body(int64_t N, const int64_t* __restrict__ row_ptr, const int32_t* __r
     int64_t N, const int64_t *__restrict__ row_ptr, const int32_t *__restrict__ col,                           \
         const TH *__restrict__ val, int64_t nnz, int64_t n, const TG *__restrict__ Yg, int64_t ldg,           \
         const TC *__restrict__ Yc, int64_t ldc, const TP *__restrict__ Yp, int64_t ldp, TO *__restrict__ Yo, \
-        int64_t ldo, __nv_bfloat16 *__restrict__ Ys, int64_t lds, ACC alpha, ACC c, ACC beta, int cap,        \
-        unsigned *status
-#define CSR_STEP_ARGS N, row_ptr, col, val, nnz, n, Yg, ldg, Yc, ldc, Yp, ldp, Yo, ldo, Ys, lds, alpha, c, beta, cap, status
+        int64_t ldo, __nv_bfloat16 *__restrict__ Ys, int64_t lds, const double *__restrict__ Ya, int64_t lda,   \
+        ACC alpha, ACC c, ACC beta, int cap, unsigned *status
+#define CSR_STEP_ARGS \
+    N, row_ptr, col, val, nnz, n, Yg, ldg, Yc, ldc, Yp, ldp, Yo, ldo, Ys, lds, Ya, lda, alpha, c, beta, cap, status
 
 // FP64 step (and FP64 steps reading FP32 iterates).
 template <typename ACC, typename TH, typename TG, typename TC, typename TP, typename TO, int V, int U,
@@ -360,7 +367,8 @@ int launch(const CsrDev& h, const void* hval, int64_t n, const StepIO& io, doubl
         h.N, h.row_ptr, h.col, static_cast<const TH*>(hval), h.nnz, n,
         static_cast<const TG*>(io.gather), io.ldg, static_cast<const TC*>(io.cur), io.ldc,
         static_cast<const TP*>(io.prev), io.ldp, static_cast<TO*>(io.out), io.ldo,
-        static_cast<__nv_bfloat16*>(io.shadow), io.lds, (ACC)alpha, (ACC)c, (ACC)beta, cap, status);
+        static_cast<__nv_bfloat16*>(io.shadow), io.lds, std::is_same<ACC, double>::value ? io.addend : nullptr,
+        io.lda, (ACC)alpha, (ACC)c, (ACC)beta, cap, status);
     CHFSI_LAUNCH_CHECK();
     return CHFSI_OK;
 }

@@ -38,6 +38,7 @@ struct StepIO {
     const void* prev;   Buf prev_t;   int64_t ldp;   // prev == nullptr: no beta term
     void* out;          Buf out_t;    int64_t ldo;
     void* shadow;       int64_t lds;                 // BF16 copy of the output, or nullptr
+    const double* addend; int64_t lda;               // FP64 steps: added to H Y_gather (nullptr: none)
 };
 
 int csr_step(const CsrDev& h, StepMath math, int64_t n, const StepIO& io, double alpha, double c,
@@ -131,5 +132,14 @@ int ozaki_gemm_tn(const double* A, int64_t lda, const double* B, int64_t ldb, in
 int ozaki_gemm_nn(const double* A, int64_t lda, const double* B, int64_t ldb, int64_t M, int64_t K, int64_t Nc,
                   double* C, int64_t ldc, bool b_upper, void* ws, size_t ws_bytes, unsigned* status,
                   cudaStream_t s);
+// Block-diagonal product of the split layout: T[kB + i][j] = sum_l D_k[i][l] Y[kB + l][j]
+// for every diagonal block k (B x B, row-major, stacked; B a multiple of 128, at most
+// 8192).  ozaki_blockdiag_prepare slices the blocks once; ozaki_blockdiag_apply slices
+// Y and runs the batched product.  Both use the same workspace (ozaki_blockdiag_bytes).
+size_t ozaki_blockdiag_bytes(int64_t N, int B, int64_t n);
+int ozaki_blockdiag_prepare(const double* diag, int64_t N, int B, int64_t n, void* ws, size_t ws_bytes,
+                            unsigned* status, cudaStream_t s);
+int ozaki_blockdiag_apply(const double* Y, int64_t ldy, int64_t N, int B, int64_t n, double* T, int64_t ldt,
+                          void* ws, size_t ws_bytes, unsigned* status, cudaStream_t s);
 
 }  // namespace chfsi

@@ -22,17 +22,21 @@ constexpr int kBlocksPerSm = 8;
 // every FMA; no allocation is needed for it.
 __device__ double g_probe_sink;
 
+// Each chain multiplies and adds its own registers: with one operand register shared
+// by every chain the DFMA issue rate measured about 16% lower on GB300.
 template <typename T>
 __global__ void __launch_bounds__(kThreads) fma_loop_kernel(T seed) {
-    T a[kChains];
+    T a[kChains], b[kChains];
     const T x = seed + (T)threadIdx.x * (T)1e-7;
-    const T y = (T)0.999999;
 #pragma unroll
-    for (int c = 0; c < kChains; c++) a[c] = x + (T)c;
+    for (int c = 0; c < kChains; c++) {
+        a[c] = x + (T)c;
+        b[c] = (T)0.999999 - (T)c * (T)1e-9;
+    }
 #pragma unroll 4
     for (int i = 0; i < kIters; i++) {
 #pragma unroll
-        for (int c = 0; c < kChains; c++) a[c] = fma(a[c], y, x);
+        for (int c = 0; c < kChains; c++) a[c] = fma(a[c], b[c], b[c]);
     }
     T s = 0;
 #pragma unroll
