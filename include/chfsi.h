@@ -333,6 +333,23 @@ int chfsi_ozaki_gemm(int32_t op, const double* A, int64_t lda, const double* B, 
                      int64_t ldc, int64_t M, int64_t Nc, int64_t K, int32_t flags, void* ws,
                      size_t ws_bytes, void* stream);
 
+/* ------------------------------------------------------------------ dense symmetric eigensolver */
+
+int chfsi_eigh_workspace_size(int64_t n, size_t* bytes);
+
+/*
+ * A = Q diag(w) Q^T for a symmetric n x n A (row-major, lda, both triangles stored),
+ * the dense eigenproblem of Algorithm 1 step 4 (Sec. 3.4), in FP64 on the GPU:
+ * Householder tridiagonalisation, divide and conquer on the tridiagonal matrix
+ * (deflation, secular equation by bisection, eigenvector weights recomputed from the
+ * roots), back-transformation in panels of 64 reflectors.  w: n doubles, ascending.
+ * Q: n x n (ldq), Q[k * ldq + i] = component k of the eigenvector of w[i].  A is
+ * overwritten.  Q must not overlap A.  The call synchronises `stream` once per merge
+ * of the divide and conquer.  Errors: CHFSI_ERR_ARG, CHFSI_ERR_NOMEM, CHFSI_ERR_CUDA.
+ */
+int chfsi_eigh(double* A, int64_t lda, int64_t n, double* w, double* Q, int64_t ldq, void* ws,
+               size_t ws_bytes, void* stream);
+
 /* ------------------------------------------------------------------ spectral bounds */
 
 int chfsi_lanczos_workspace_size(const chfsi_matrix* H, int32_t steps, size_t* bytes);

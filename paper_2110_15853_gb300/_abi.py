@@ -89,6 +89,8 @@ SIGNATURES = {
     "chfsi_clear_status": (ctypes.c_int, [_vp, _vp]),
     "chfsi_kernel_launches": (ctypes.c_ulonglong, []),
     "chfsi_measure_pipe_peak": (ctypes.c_int, [_i32, _DP, _vp]),
+    "chfsi_eigh_workspace_size": (ctypes.c_int, [_i64, _SZP]),
+    "chfsi_eigh": (ctypes.c_int, [_vp, _i64, _i64, _vp, _vp, _i64, _vp, _sz, _vp]),
     "chfsi_ozaki_gemm_workspace_size": (ctypes.c_int, [_i32, _i64, _i64, _i64, _i32, _SZP]),
     "chfsi_ozaki_gemm": (ctypes.c_int, [_i32, _vp, _i64, _vp, _i64, _vp, _i64, _i64, _i64, _i64, _i32, _vp, _sz,
                                         _vp]),

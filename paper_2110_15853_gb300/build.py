@@ -23,7 +23,7 @@ BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libchfsi.so")
 
 SOURCES = ["api.cu", "filter_csr.cu", "filter_bsr.cu", "dense.cu", "lanczos.cu", "adjoint.cu", "noalloc.cu", "filter_bsr_tc.cu",
-           "filter_csr_f32x2.cu", "dense_f32x2.cu", "probe.cu", "dense_ozaki.cu"]
+           "filter_csr_f32x2.cu", "dense_f32x2.cu", "probe.cu", "dense_ozaki.cu", "eigh.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

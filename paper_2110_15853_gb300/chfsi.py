@@ -322,6 +322,24 @@ def ozaki_gemm(A: torch.Tensor, B: torch.Tensor, transpose_a: bool = False, symm
     return out
 
 
+def eigh(A: torch.Tensor, workspace: Optional[Workspace] = None):
+    """(w ascending, Q) of a symmetric FP64 CUDA matrix by the library's dense
+    eigensolver (chfsi_eigh); A is not modified (a copy is factorised)."""
+    if A.dtype != torch.float64 or A.dim() != 2 or A.shape[0] != A.shape[1] or not A.is_cuda:
+        raise ValueError("A must be a square float64 CUDA matrix")
+    n = A.shape[0]
+    work = A.contiguous().clone()
+    w = torch.empty(n, dtype=torch.float64, device=A.device)
+    Q = torch.empty((n, n), dtype=torch.float64, device=A.device)
+    lib = load()
+    sz = ctypes.c_size_t(0)
+    check(lib.chfsi_eigh_workspace_size(n, ctypes.byref(sz)), "chfsi_eigh_workspace_size")
+    ws = (workspace or Workspace(A.device)).get(sz.value)
+    check(lib.chfsi_eigh(_ptr(work), n, n, _ptr(w), _ptr(Q), n, _ptr(ws), ws.numel(), _stream_handle(A.device)),
+          "chfsi_eigh")
+    return w, Q
+
+
 def measure_pipe_peak(precision: str = "f64", device="cuda") -> float:
     """FLOP/s of the FP64 (DFMA) or FP32 (FFMA) pipe of `device`, measured by the
     library's register-resident FMA loop (chfsi_measure_pipe_peak)."""

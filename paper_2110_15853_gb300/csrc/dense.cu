@@ -319,6 +319,13 @@ int gemm_nn(const double* A, int64_t lda, const double* B, int64_t ldb, double* 
     return run_gemm(g, s);
 }
 
+int gemm_general(const double* A, int64_t lda, bool a_t, const double* B, int64_t ldb, double* C, int64_t ldc,
+                 int64_t M, int64_t Nc, int64_t K, double alpha, bool accumulate, cudaStream_t s) {
+    if (M <= 0 || Nc <= 0) return CHFSI_OK;
+    GemmArgs g{A, lda, a_t, B, ldb, C, ldc, M, Nc, K, alpha, accumulate, false, false, 1, nullptr};
+    return run_gemm(g, s);
+}
+
 int cholesky_upper(double* S, int64_t n, int64_t lds, unsigned* status, cudaStream_t s) {
     for (int64_t k0 = 0; k0 < n; k0 += NB) {
         int nb = (int)((n - k0) < NB ? (n - k0) : NB);

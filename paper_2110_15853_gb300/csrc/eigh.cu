@@ -1,0 +1,733 @@
+// Dense symmetric eigensolver of the Rayleigh-Ritz step (Algorithm 1 step 4, Sec. 3.4:
+// H_F Q = Q Lambda), FP64, written for the GPU:
+//   1. Householder tridiagonalisation  A = Q_H T Q_H^T, one reflector per column
+//      (reflector of row j, symmetric matrix-vector product with the trailing block,
+//      symmetric rank-2 update);
+//   2. divide and conquer on T (Cuppen's splitting T = diag(T1, T2) + rho u u^T):
+//      leaves of 32 rows by parallel-ordered Jacobi in shared memory; each merge
+//      deflates (small components of z, nearly equal poles rotated together), finds
+//      the roots of the secular equation 1 + rho sum z_j^2 / (d_j - lambda) by
+//      bisection measured from the nearer pole, recomputes z from the roots (the
+//      Gu-Eisenstat formula, so that the eigenvectors come out orthogonal), and
+//      multiplies the subproblem vectors by the eigenvectors of D + rho z z^T;
+//   3. back-transformation Q = Q_H Q_T in panels of 64 reflectors (compact WY form
+//      I - V T V^T, three matrix products per panel).
+// Everything runs in this library's kernels (FP64 on the DFMA pipe); the host only
+// orders the launches.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace chfsi {
+
+namespace {
+
+constexpr double kEps = 2.220446049250313e-16;
+constexpr int kLeaf = 32;
+constexpr int kPanel = 64;
+constexpr int kSecularSmem = 6144;   // poles and weights staged in shared memory up to this size
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Sum over the block (blockDim.x a multiple of 32, at most 1024); every thread gets it.
+__device__ double block_sum(double v) {
+    __shared__ double part[32];
+    __shared__ double total;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    v = warp_sum(v);
+    __syncthreads();
+    if (lane == 0) part[w] = v;
+    __syncthreads();
+    if (w == 0) {
+        double t = lane < (int)(blockDim.x >> 5) ? part[lane] : 0.0;
+        t = warp_sum(t);
+        if (lane == 0) total = t;
+    }
+    __syncthreads();
+    return total;
+}
+
+// ------------------------------------------------------------------ 1. tridiagonalisation
+
+// Reflector of row j (columns j+1 .. n-1 of the symmetric A): H = I - tau v v^T with
+// v_0 = 1 maps x = A[j][j+1:] to beta e_1.  v is kept in A's row j (it is not read
+// again by the reduction) and in vbuf.  One block.
+__global__ void house_kernel(double* A, int64_t lda, int64_t n, int64_t j, double* d, double* e, double* tau,
+                             double* vbuf) {
+    const int64_t m = n - j - 1;
+    double* x = A + j * lda + j + 1;
+    double s = 0.0;
+    for (int64_t i = 1 + threadIdx.x; i < m; i += blockDim.x) s += x[i] * x[i];
+    s = block_sum(s);
+    const double x0 = x[0];
+    double beta, t, scale;
+    if (s == 0.0) {
+        beta = x0;
+        t = 0.0;
+        scale = 0.0;
+    } else {
+        const double nrm = sqrt(x0 * x0 + s);
+        beta = x0 >= 0.0 ? -nrm : nrm;
+        t = (beta - x0) / beta;
+        scale = 1.0 / (x0 - beta);
+    }
+    __syncthreads();
+    for (int64_t i = threadIdx.x; i < m; i += blockDim.x) {
+        const double vi = i == 0 ? 1.0 : x[i] * scale;
+        vbuf[i] = vi;
+        x[i] = vi;
+    }
+    if (threadIdx.x == 0) {
+        d[j] = A[j * lda + j];
+        e[j] = beta;
+        tau[j] = t;
+    }
+}
+
+// p = tau_j A22 v with A22 = A[j+1:, j+1:]; one warp per row.
+__global__ void symv_kernel(const double* __restrict__ A, int64_t lda, int64_t n, int64_t j,
+                            const double* __restrict__ tau, const double* __restrict__ v, double* p) {
+    const int64_t m = n - j - 1;
+    const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (r >= m) return;
+    const double* row = A + (j + 1 + r) * lda + j + 1;
+    double s = 0.0;
+    for (int64_t i = lane; i < m; i += 32) s = fma(row[i], v[i], s);
+    s = warp_sum(s);
+    if (lane == 0) p[r] = tau[j] * s;
+}
+
+// w = p - (tau_j / 2)(p . v) v, in place in p.  One block.
+__global__ void house_w_kernel(int64_t m, int64_t j, const double* __restrict__ tau, const double* __restrict__ v,
+                               double* p) {
+    double s = 0.0;
+    for (int64_t i = threadIdx.x; i < m; i += blockDim.x) s = fma(p[i], v[i], s);
+    s = block_sum(s);
+    const double K = 0.5 * tau[j] * s;
+    for (int64_t i = threadIdx.x; i < m; i += blockDim.x) p[i] -= K * v[i];
+}
+
+// A22 -= v w^T + w v^T (both triangles).
+__global__ void rank2_kernel(double* A, int64_t lda, int64_t n, int64_t j, const double* __restrict__ v,
+                             const double* __restrict__ w) {
+    const int64_t m = n - j - 1;
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t r = blockIdx.y;
+    if (c >= m || r >= m) return;
+    A[(j + 1 + r) * lda + j + 1 + c] -= v[r] * w[c] + w[r] * v[c];
+}
+
+// The last 2 x 2 (or 1 x 1) block of T.
+__global__ void tridiag_tail_kernel(const double* A, int64_t lda, int64_t n, double* d, double* e, double* tau) {
+    if (threadIdx.x != 0) return;
+    if (n >= 2) {
+        d[n - 2] = A[(n - 2) * lda + n - 2];
+        e[n - 2] = A[(n - 2) * lda + n - 1];
+        tau[n - 2] = 0.0;
+    }
+    d[n - 1] = A[(n - 1) * lda + n - 1];
+}
+
+// ------------------------------------------------------------------ 2. divide and conquer
+
+// Cuppen's splitting at every leaf boundary m: d[m-1] and d[m] lose rho = e[m-1];
+// the original off-diagonal is kept in ebak.
+__global__ void dc_split_kernel(int64_t n, double* d, const double* e, double* ebak) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n - 1) ebak[i] = e[i];
+    const int64_t m = (i + 1) * kLeaf;   // boundary number i
+    if (m < n) {
+        const double rho = e[m - 1];
+        d[m - 1] -= rho;
+        d[m] -= rho;
+    }
+}
+
+// Leaf eigenproblems by parallel (round-robin ordered) Jacobi; one block per leaf.
+// Writes ascending eigenvalues to w[l ..] and the eigenvectors into the diagonal block
+// Q[l.., l..] (the rest of Q is zero).
+__global__ void __launch_bounds__(256) dc_leaf_kernel(int64_t n, const double* d, const double* e, double* w,
+                                                      double* Q, int64_t ldq) {
+    __shared__ double A[kLeaf][kLeaf + 1];
+    __shared__ double V[kLeaf][kLeaf + 1];
+    __shared__ double rc[kLeaf / 2], rs[kLeaf / 2];
+    __shared__ int rp[kLeaf / 2], rq[kLeaf / 2];
+    __shared__ int rank[kLeaf];
+    const int64_t l = (int64_t)blockIdx.x * kLeaf;
+    const int s = (int)((n - l) < kLeaf ? (n - l) : kLeaf);
+    for (int idx = threadIdx.x; idx < kLeaf * kLeaf; idx += blockDim.x) {
+        const int i = idx / kLeaf, j = idx % kLeaf;
+        double v = 0.0;
+        if (i < s && j < s) {
+            if (i == j) v = d[l + i];
+            else if (j == i + 1) v = e[l + i];
+            else if (i == j + 1) v = e[l + j];
+        }
+        A[i][j] = v;
+        V[i][j] = i == j ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    for (int sweep = 0; sweep < 20; sweep++) {
+        double o = 0.0, t2 = 0.0;
+        for (int idx = threadIdx.x; idx < kLeaf * kLeaf; idx += blockDim.x) {
+            const int i = idx / kLeaf, j = idx % kLeaf;
+            const double a2 = A[i][j] * A[i][j];
+            t2 += a2;
+            if (i != j) o += a2;
+        }
+        o = block_sum(o);
+        t2 = block_sum(t2);
+        if (o <= 1e-30 * t2 || o == 0.0) break;   // off-diagonal below about 1e-15 |A|
+        for (int round = 0; round < kLeaf - 1; round++) {
+            // pairs of this round: players 0 .. kLeaf-1, player 0 fixed, the others rotating
+            if (threadIdx.x < kLeaf / 2) {
+                const int k = threadIdx.x;
+                auto player = [&](int pos) { return pos == 0 ? 0 : ((pos - 1 + round) % (kLeaf - 1)) + 1; };
+                int p = player(k), q = player(kLeaf - 1 - k);
+                if (p > q) { const int t = p; p = q; q = t; }
+                const double apq = A[p][q];
+                double c = 1.0, sn = 0.0;
+                if (apq != 0.0 && fabs(apq) > 1e-300) {
+                    const double theta = (A[q][q] - A[p][p]) / (2.0 * apq);
+                    const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+                    c = 1.0 / sqrt(t * t + 1.0);
+                    sn = t * c;
+                }
+                rp[k] = p; rq[k] = q; rc[k] = c; rs[k] = sn;
+            }
+            __syncthreads();
+            // rows p, q of A (rotations of one round touch disjoint rows)
+            for (int idx = threadIdx.x; idx < (kLeaf / 2) * kLeaf; idx += blockDim.x) {
+                const int k = idx / kLeaf, col = idx % kLeaf;
+                const int p = rp[k], q = rq[k];
+                const double c = rc[k], sn = rs[k];
+                const double ap = A[p][col], aq = A[q][col];
+                A[p][col] = c * ap - sn * aq;
+                A[q][col] = sn * ap + c * aq;
+            }
+            __syncthreads();
+            // columns p, q of A and of V
+            for (int idx = threadIdx.x; idx < (kLeaf / 2) * kLeaf; idx += blockDim.x) {
+                const int k = idx / kLeaf, row = idx % kLeaf;
+                const int p = rp[k], q = rq[k];
+                const double c = rc[k], sn = rs[k];
+                const double ap = A[row][p], aq = A[row][q];
+                A[row][p] = c * ap - sn * aq;
+                A[row][q] = sn * ap + c * aq;
+                const double vp = V[row][p], vq = V[row][q];
+                V[row][p] = c * vp - sn * vq;
+                V[row][q] = sn * vp + c * vq;
+            }
+            __syncthreads();
+        }
+    }
+    // ascending order of the s real eigenvalues (the padding rows never mix with them)
+    if (threadIdx.x < s) {
+        const int i = threadIdx.x;
+        const double li = A[i][i];
+        int r = 0;
+        for (int j = 0; j < s; j++) {
+            const double lj = A[j][j];
+            r += (lj < li) || (lj == li && j < i);
+        }
+        rank[i] = r;
+    }
+    __syncthreads();
+    if (threadIdx.x < s) w[l + rank[threadIdx.x]] = A[threadIdx.x][threadIdx.x];
+    for (int idx = threadIdx.x; idx < s * s; idx += blockDim.x) {
+        const int r = idx / s, i = idx % s;
+        Q[(l + r) * ldq + l + rank[i]] = V[r][i];
+    }
+}
+
+// Per-merge scratch (device arrays of n, or of n x n for the matrices).
+struct MergeBufs {
+    double *D, *z, *Dnd, *znd, *tau_r, *zhat, *norm, *val, *rot_c, *rot_s, *par;
+    int *perm, *defl, *ndidx, *pos, *org, *rot_a, *rot_b, *rank;
+    double *G, *U, *Gn;
+};
+
+// par[] = {rho_hat, sign, k_nd, nrot}.
+// Merge preparation: z from the boundary rows, signs, the sorted poles, deflation with
+// the Givens rotations of nearly equal poles.  One block (the scans on thread 0).
+__global__ void __launch_bounds__(1024) dc_merge_prep_kernel(int64_t l, int64_t m, int64_t r, const double* w,
+                                                             const double* Q, int64_t ldq, const double* ebak,
+                                                             MergeBufs b) {
+    const int64_t n1 = m - l, k = r - l;
+    const double rho0 = ebak[m - 1];
+    const double sg = rho0 >= 0.0 ? 1.0 : -1.0;
+    double zz = 0.0;
+    for (int64_t p = threadIdx.x; p < k; p += blockDim.x) {
+        const double zp = p < n1 ? Q[(m - 1) * ldq + l + p] : Q[m * ldq + m + (p - n1)];
+        b.z[p] = zp;
+        b.D[p] = sg * w[l + p];
+        zz += zp * zp;
+    }
+    zz = block_sum(zz);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const double rho_hat = fabs(rho0) * zz;
+        const double zs = 1.0 / sqrt(zz > 0.0 ? zz : 1.0);
+        // merge the two sorted halves (ascending when sg > 0, descending otherwise)
+        int64_t i = 0, j = 0, o = 0;
+        auto at1 = [&](int64_t t) { return sg > 0.0 ? t : n1 - 1 - t; };
+        auto at2 = [&](int64_t t) { return sg > 0.0 ? n1 + t : k - 1 - t; };
+        while (i < n1 || j < k - n1) {
+            if (j >= k - n1 || (i < n1 && b.D[at1(i)] <= b.D[at2(j)])) b.perm[o++] = (int)at1(i++);
+            else b.perm[o++] = (int)at2(j++);
+        }
+        double dmax = 0.0;
+        for (int64_t p = 0; p < k; p++) {
+            const int q = b.perm[p];
+            b.val[p] = b.D[q];                 // sorted poles (modified by the rotations below)
+            b.tau_r[p] = b.z[q] * zs;          // sorted, normalised z (temporarily)
+            dmax = fmax(dmax, fabs(b.val[p]));
+        }
+        const double tol = 8.0 * kEps * fmax(dmax, rho_hat);
+        int nrot = 0;
+        int64_t last = -1;
+        for (int64_t p = 0; p < k; p++) {
+            b.defl[p] = fabs(rho_hat * b.tau_r[p]) <= tol;
+            if (b.defl[p]) continue;
+            if (last >= 0 && fabs(b.val[p] - b.val[last]) <= tol) {
+                const double zl = b.tau_r[last], zp = b.tau_r[p];
+                const double rr = hypot(zl, zp), c = zp / rr, s = -zl / rr;
+                const double dl = b.val[last], dp = b.val[p];
+                b.val[last] = c * c * dl + s * s * dp;
+                b.val[p] = s * s * dl + c * c * dp;
+                b.tau_r[p] = rr;
+                b.tau_r[last] = 0.0;
+                b.defl[last] = 1;
+                b.rot_a[nrot] = (int)last;
+                b.rot_b[nrot] = (int)p;
+                b.rot_c[nrot] = c;
+                b.rot_s[nrot] = s;
+                nrot++;
+            }
+            last = p;
+        }
+        int64_t kn = 0;
+        for (int64_t p = 0; p < k; p++) {
+            if (!b.defl[p]) {
+                b.ndidx[kn] = (int)p;
+                b.pos[p] = (int)kn;
+                b.Dnd[kn] = b.val[p];
+                b.znd[kn] = b.tau_r[p];
+                kn++;
+            } else {
+                b.pos[p] = -1;
+            }
+        }
+        b.par[0] = rho_hat;
+        b.par[1] = sg;
+        b.par[2] = (double)kn;
+        b.par[3] = (double)nrot;
+    }
+}
+
+// The deflation rotations on the block's columns (column p of the sorted problem is
+// block column perm[p]); one thread per row applies them in order.
+__global__ void dc_rotate_kernel(int64_t l, int64_t k, double* Q, int64_t ldq, MergeBufs b) {
+    const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (row >= k) return;
+    const int nrot = (int)b.par[3];
+    double* q = Q + (l + row) * ldq + l;
+    for (int t = 0; t < nrot; t++) {
+        const int a = b.perm[b.rot_a[t]], c2 = b.perm[b.rot_b[t]];
+        const double c = b.rot_c[t], s = b.rot_s[t];
+        const double qa = q[a], qb = q[c2];
+        q[a] = c * qa + s * qb;
+        q[c2] = -s * qa + c * qb;
+    }
+}
+
+// Roots of 1 + rho sum_j z_j^2 / (d_j - lambda) (rho > 0, d ascending, sum z^2 = 1):
+// root i lies in (d_i, d_{i+1}), the last in (d_k, d_k + rho).  Each root is found by
+// bisection on tau = lambda - d_org, measured from the nearer pole d_org, so that the
+// differences d_j - lambda = (d_j - d_org) - tau keep their relative accuracy.
+__global__ void dc_secular_kernel(MergeBufs b, int cap) {
+    extern __shared__ double sh[];
+    const int k = (int)b.par[2];
+    const double rho = b.par[0];
+    const bool staged = k <= cap;   // cap: poles the dynamic shared memory was sized for
+    double* Ds = sh;
+    double* z2 = sh + (staged ? k : 0);
+    if (staged) {
+        for (int j = threadIdx.x; j < k; j += blockDim.x) {
+            Ds[j] = b.Dnd[j];
+            z2[j] = b.znd[j] * b.znd[j];
+        }
+    }
+    __syncthreads();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= k) return;
+    auto Dj = [&](int j) { return staged ? Ds[j] : b.Dnd[j]; };
+    auto Zj = [&](int j) { return staged ? z2[j] : b.znd[j] * b.znd[j]; };
+    const double lo = Dj(i);
+    const double gap = (i + 1 < k) ? Dj(i + 1) - lo : rho;
+    // f at the midpoint decides which pole is nearer
+    const double mid = lo + 0.5 * gap;
+    double fm = 1.0;
+    for (int j = 0; j < k; j++) fm += rho * Zj(j) / (Dj(j) - mid);
+    int org;
+    double a, c;
+    if (i + 1 == k) {
+        org = i;
+        if (fm < 0.0) { a = 0.5 * gap; c = gap; }
+        else { a = 0.0; c = 0.5 * gap; }
+    } else if (fm >= 0.0) {
+        org = i; a = 0.0; c = 0.5 * gap;
+    } else {
+        org = i + 1; a = -0.5 * gap; c = 0.0;
+    }
+    const double dorg = Dj(org);
+    for (int it = 0; it < 400; it++) {
+        const double t = 0.5 * (a + c);
+        if (t == a || t == c) break;
+        double f = 1.0;
+        for (int j = 0; j < k; j++) f += rho * Zj(j) / ((Dj(j) - dorg) - t);
+        if (f > 0.0) c = t;     // f increases with lambda between consecutive poles
+        else a = t;
+        if (c - a <= 2.0 * kEps * fmax(fabs(a), fabs(c))) break;
+    }
+    b.org[i] = org;
+    b.tau_r[i] = 0.5 * (a + c);
+}
+
+// Recomputed weights zhat_i^2 = prod_j (lambda_j - d_i) / (rho prod_{j != i} (d_j - d_i))
+// (sign of the original z_i), and the norms of the eigenvectors
+// u_i = (zhat_j / (d_j - lambda_i))_j.
+__global__ void dc_lowner_kernel(MergeBufs b) {
+    const int k = (int)b.par[2];
+    const double rho = b.par[0];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= k) return;
+    const double di = b.Dnd[i];
+    double prod = 1.0;
+    for (int j = 0; j < k; j++) {
+        const double lmd = (b.Dnd[b.org[j]] - di) + b.tau_r[j];   // lambda_j - d_i
+        prod *= (j == i) ? lmd / rho : lmd / (b.Dnd[j] - di);
+    }
+    const double zh = sqrt(fabs(prod));
+    b.zhat[i] = b.znd[i] >= 0.0 ? zh : -zh;
+}
+
+__global__ void dc_norm_kernel(MergeBufs b) {
+    const int k = (int)b.par[2];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= k) return;
+    const double dorg = b.Dnd[b.org[i]], t = b.tau_r[i];
+    double s = 0.0;
+    for (int j = 0; j < k; j++) {
+        const double q = b.zhat[j] / ((b.Dnd[j] - dorg) - t);
+        s = fma(q, q, s);
+    }
+    b.norm[i] = sqrt(s);
+}
+
+// U[j][i] = zhat_j / (d_j - lambda_i) / |u_i|  (k_nd x k_nd, row-major).
+__global__ void dc_build_u_kernel(MergeBufs b) {
+    const int k = (int)b.par[2];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y;
+    if (i >= k || j >= k) return;
+    b.U[(int64_t)j * k + i] = b.zhat[j] / ((b.Dnd[j] - b.Dnd[b.org[i]]) - b.tau_r[i]) / b.norm[i];
+}
+
+// G[row][c] = block column perm[ndidx[c]] of Q.
+__global__ void dc_gather_kernel(int64_t l, int64_t k, const double* Q, int64_t ldq, MergeBufs b) {
+    const int kn = (int)b.par[2];
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t row = blockIdx.y;
+    if (c >= kn || row >= k) return;
+    b.G[row * kn + c] = Q[(l + row) * ldq + l + b.perm[b.ndidx[c]]];
+}
+
+// Final eigenvalues of the merged problem (sign restored) and their ascending ranks.
+__global__ void dc_rank_kernel(int64_t k, MergeBufs b) {
+    const double sg = b.par[1];
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < k; p += (int64_t)gridDim.x * blockDim.x) {
+        const int q = b.pos[p];
+        b.D[p] = sg * (q < 0 ? b.val[p] : b.Dnd[b.org[q]] + b.tau_r[q]);
+    }
+}
+
+__global__ void dc_rank2_kernel(int64_t k, MergeBufs b) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= k) return;
+    const double vp = b.D[p];
+    int r = 0;
+    for (int64_t q = 0; q < k; q++) {
+        const double vq = b.D[q];
+        r += (vq < vp) || (vq == vp && q < p);
+    }
+    b.rank[p] = r;
+}
+
+// Writes the merged eigenvalues w[l + rank] and the block's new columns into F
+// (k x k): deflated columns from Q, the others from Gn = G U.
+__global__ void dc_scatter_kernel(int64_t l, int64_t k, const double* Q, int64_t ldq, double* w, double* F,
+                                  MergeBufs b) {
+    const int kn = (int)b.par[2];
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t row = blockIdx.y;
+    if (p >= k || row >= k) return;
+    const int dst = b.rank[p];
+    const int q = b.pos[p];
+    F[row * k + dst] = q < 0 ? Q[(l + row) * ldq + l + b.perm[p]] : b.Gn[row * kn + q];
+    if (row == 0) w[l + dst] = b.D[p];
+}
+
+__global__ void copy_block_kernel(const double* F, int64_t k, double* Q, int64_t ldq, int64_t l) {
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t row = blockIdx.y;
+    if (c >= k || row >= k) return;
+    Q[(l + row) * ldq + l + c] = F[row * k + c];
+}
+
+// ------------------------------------------------------------------ 3. back-transformation
+
+// Vp[t][i] = component j0 + 1 + i of reflector j0 + t (rows j0 + 1 .. n - 1), zero above its 1.
+__global__ void panel_v_kernel(const double* A, int64_t lda, int64_t n, int64_t j0, int nb, double* Vp) {
+    const int64_t mr = n - j0 - 1;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int t = blockIdx.y;
+    if (i >= mr || t >= nb) return;
+    const int64_t j = j0 + t, row = j0 + 1 + i;
+    double v = 0.0;
+    if (row == j + 1) v = 1.0;
+    else if (row > j + 1) v = A[j * lda + row];
+    Vp[t * mr + i] = v;
+}
+
+// Gv[s][t] = Vp[s] . Vp[t] (s <= t), one block per pair.
+__global__ void panel_gram_kernel(const double* Vp, int64_t mr, int nb, double* Gv) {
+    const int s = blockIdx.x, t = blockIdx.y;
+    if (s > t) return;
+    double acc = 0.0;
+    for (int64_t i = threadIdx.x; i < mr; i += blockDim.x) acc = fma(Vp[s * mr + i], Vp[t * mr + i], acc);
+    acc = block_sum(acc);
+    if (threadIdx.x == 0) Gv[s * nb + t] = acc;
+}
+
+// T of H_j0 ... H_{j0+nb-1} = I - V T V^T (upper triangular, forward accumulation):
+// T[t][t] = tau_t, T[0:t, t] = -tau_t T[0:t, 0:t] Gv[0:t, t].  One block.
+__global__ void panel_t_kernel(const double* Gv, const double* tau, int64_t j0, int nb, double* T) {
+    for (int idx = threadIdx.x; idx < nb * nb; idx += blockDim.x) T[idx] = 0.0;
+    __syncthreads();
+    for (int t = 0; t < nb; t++) {
+        const double tt = tau[j0 + t];
+        if (threadIdx.x < t) {
+            const int s = threadIdx.x;
+            double acc = 0.0;
+            for (int u = s; u < t; u++) acc = fma(T[s * nb + u], Gv[u * nb + t], acc);
+            T[s * nb + t] = -tt * acc;
+        }
+        if (threadIdx.x == 0) T[t * nb + t] = tt;
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------ workspace
+
+inline int64_t round8(int64_t x) { return (x + 7) / 8 * 8; }
+
+template <typename Ar>
+void eigh_layout(Ar& ar, int64_t n, double** d, double** e, double** tau, double** ebak, double** vbuf, double** pbuf,
+                 MergeBufs* mb, double** Vp, double** Gv, double** T, double** W1, double** W2) {
+    *d = ar.template take<double>(n);
+    *e = ar.template take<double>(n);
+    *tau = ar.template take<double>(n);
+    *ebak = ar.template take<double>(n);
+    *vbuf = ar.template take<double>(n);
+    *pbuf = ar.template take<double>(n);
+    MergeBufs b;
+    b.D = ar.template take<double>(n);
+    b.z = ar.template take<double>(n);
+    b.Dnd = ar.template take<double>(n);
+    b.znd = ar.template take<double>(n);
+    b.tau_r = ar.template take<double>(n);
+    b.zhat = ar.template take<double>(n);
+    b.norm = ar.template take<double>(n);
+    b.val = ar.template take<double>(n);
+    b.rot_c = ar.template take<double>(n);
+    b.rot_s = ar.template take<double>(n);
+    b.par = ar.template take<double>(8);
+    b.perm = ar.template take<int>(n);
+    b.defl = ar.template take<int>(n);
+    b.ndidx = ar.template take<int>(n);
+    b.pos = ar.template take<int>(n);
+    b.org = ar.template take<int>(n);
+    b.rot_a = ar.template take<int>(n);
+    b.rot_b = ar.template take<int>(n);
+    b.rank = ar.template take<int>(n);
+    b.G = ar.template take<double>((size_t)n * n);
+    b.U = ar.template take<double>((size_t)n * n);
+    b.Gn = ar.template take<double>((size_t)n * n);
+    if (mb) *mb = b;
+    *Vp = ar.template take<double>((size_t)kPanel * n);
+    *Gv = ar.template take<double>((size_t)kPanel * kPanel);
+    *T = ar.template take<double>((size_t)kPanel * kPanel);
+    *W1 = ar.template take<double>((size_t)kPanel * n);
+    *W2 = ar.template take<double>((size_t)kPanel * n);
+}
+
+struct CountOnly {
+    Sizer s;
+    template <typename T>
+    T* take(size_t n) {
+        s.take<T>(n);
+        return nullptr;
+    }
+};
+
+}  // namespace
+
+size_t eigh_workspace_bytes(int64_t n) {
+    CountOnly ar;
+    double *d, *e, *tau, *ebak, *vb, *pb, *Vp, *Gv, *T, *W1, *W2;
+    eigh_layout(ar, n > 0 ? n : 1, &d, &e, &tau, &ebak, &vb, &pb, nullptr, &Vp, &Gv, &T, &W1, &W2);
+    return ar.s.used;
+}
+
+int eigh(double* A, int64_t lda, int64_t n, double* w, double* Q, int64_t ldq, void* ws, size_t ws_bytes,
+         unsigned* status, cudaStream_t s) {
+    (void)status;
+    if (n <= 0) return CHFSI_OK;
+    if (ws_bytes < eigh_workspace_bytes(n)) return CHFSI_ERR_NOMEM;
+    Arena ar(ws, ws_bytes);
+    double *d, *e, *tau, *ebak, *vbuf, *pbuf, *Vp, *Gv, *T, *W1, *W2;
+    MergeBufs mb;
+    eigh_layout(ar, n, &d, &e, &tau, &ebak, &vbuf, &pbuf, &mb, &Vp, &Gv, &T, &W1, &W2);
+
+    // 1. tridiagonalisation
+    for (int64_t j = 0; j + 2 < n; j++) {
+        const int64_t m = n - j - 1;
+        house_kernel<<<1, 1024, 0, s>>>(A, lda, n, j, d, e, tau, vbuf);
+        CHFSI_LAUNCH_CHECK();
+        symv_kernel<<<(unsigned)((m * 32 + 255) / 256), 256, 0, s>>>(A, lda, n, j, tau, vbuf, pbuf);
+        CHFSI_LAUNCH_CHECK();
+        house_w_kernel<<<1, 1024, 0, s>>>(m, j, tau, vbuf, pbuf);
+        CHFSI_LAUNCH_CHECK();
+        rank2_kernel<<<dim3((unsigned)((m + 255) / 256), (unsigned)m), 256, 0, s>>>(A, lda, n, j, vbuf, pbuf);
+        CHFSI_LAUNCH_CHECK();
+    }
+    tridiag_tail_kernel<<<1, 32, 0, s>>>(A, lda, n, d, e, tau);
+    CHFSI_LAUNCH_CHECK();
+
+    // 2. divide and conquer on (d, e): Q starts as the leaf eigenvectors
+    for (int64_t i = 0; i < n; i++) CHFSI_CUDA_TRY(cudaMemsetAsync(Q + i * ldq, 0, sizeof(double) * (size_t)n, s));
+    dc_split_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, d, e, ebak);
+    CHFSI_LAUNCH_CHECK();
+    const int64_t nleaf = (n + kLeaf - 1) / kLeaf;
+    dc_leaf_kernel<<<(unsigned)nleaf, 256, 0, s>>>(n, d, e, w, Q, ldq);
+    CHFSI_LAUNCH_CHECK();
+    std::vector<int64_t> bounds;
+    for (int64_t i = 0; i <= nleaf; i++) bounds.push_back(std::min(i * kLeaf, n));
+    while (bounds.size() > 2) {
+        std::vector<int64_t> next;
+        next.push_back(bounds[0]);
+        for (size_t i = 0; i + 2 < bounds.size(); i += 2) {
+            const int64_t l = bounds[i], m = bounds[i + 1], r = bounds[i + 2];
+            const int64_t k = r - l;
+            dc_merge_prep_kernel<<<1, 1024, 0, s>>>(l, m, r, w, Q, ldq, ebak, mb);
+            CHFSI_LAUNCH_CHECK();
+            dc_rotate_kernel<<<(unsigned)((k + 255) / 256), 256, 0, s>>>(l, k, Q, ldq, mb);
+            CHFSI_LAUNCH_CHECK();
+            const size_t sh = k <= kSecularSmem ? 2 * sizeof(double) * (size_t)k : 0;
+            if (sh > 48 * 1024) {
+                static bool attr[kMaxDevices] = {};
+                const int dev = current_device();
+                if (dev < 0) return CHFSI_ERR_CUDA;
+                if (!attr[dev]) {
+                    CHFSI_CUDA_TRY(cudaFuncSetAttribute(dc_secular_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                        (int)(2 * sizeof(double) * kSecularSmem)));
+                    attr[dev] = true;
+                }
+            }
+            // the non-deflated count is only known on the device: size the grids for k
+            dc_secular_kernel<<<(unsigned)((k + 127) / 128), 128, sh, s>>>(mb, sh ? (int)k : 0);
+            CHFSI_LAUNCH_CHECK();
+            dc_lowner_kernel<<<(unsigned)((k + 127) / 128), 128, 0, s>>>(mb);
+            CHFSI_LAUNCH_CHECK();
+            dc_norm_kernel<<<(unsigned)((k + 127) / 128), 128, 0, s>>>(mb);
+            CHFSI_LAUNCH_CHECK();
+            dc_build_u_kernel<<<dim3((unsigned)((k + 255) / 256), (unsigned)k), 256, 0, s>>>(mb);
+            CHFSI_LAUNCH_CHECK();
+            dc_gather_kernel<<<dim3((unsigned)((k + 255) / 256), (unsigned)k), 256, 0, s>>>(l, k, Q, ldq, mb);
+            CHFSI_LAUNCH_CHECK();
+            // Gn (k x kn) = G (k x kn) U (kn x kn); kn <= k is read on the device, so the
+            // product runs at the full size k with G, U and Gn laid out for kn: a host copy
+            // of kn keeps the shapes exact
+            double kn_d = 0.0;
+            CHFSI_CUDA_TRY(cudaMemcpyAsync(&kn_d, mb.par + 2, sizeof(double), cudaMemcpyDeviceToHost, s));
+            CHFSI_CUDA_TRY(cudaStreamSynchronize(s));
+            const int64_t kn = (int64_t)kn_d;
+            int rc = gemm_general(mb.G, kn, false, mb.U, kn, mb.Gn, kn, k, kn, kn, 1.0, false, s);
+            if (rc) return rc;
+            dc_rank_kernel<<<(unsigned)((k + 255) / 256), 256, 0, s>>>(k, mb);
+            CHFSI_LAUNCH_CHECK();
+            dc_rank2_kernel<<<(unsigned)((k + 255) / 256), 256, 0, s>>>(k, mb);
+            CHFSI_LAUNCH_CHECK();
+            dc_scatter_kernel<<<dim3((unsigned)((k + 255) / 256), (unsigned)k), 256, 0, s>>>(l, k, Q, ldq, w, mb.U,
+                                                                                          mb);
+            CHFSI_LAUNCH_CHECK();
+            copy_block_kernel<<<dim3((unsigned)((k + 255) / 256), (unsigned)k), 256, 0, s>>>(mb.U, k, Q, ldq, l);
+            CHFSI_LAUNCH_CHECK();
+            next.push_back(r);
+        }
+        if (bounds.size() % 2 == 0) next.push_back(bounds.back());   // an unpaired last block carries over
+        bounds.swap(next);
+    }
+
+    // 3. back-transformation Q = H_0 H_1 ... H_{n-3} Q, panels from the last
+    const int64_t nref = n - 2;   // reflectors j = 0 .. n - 3
+    for (int64_t j0 = ((nref - 1) / kPanel) * kPanel; nref > 0 && j0 >= 0; j0 -= kPanel) {
+        const int nb = (int)std::min<int64_t>(kPanel, nref - j0);
+        const int64_t mr = n - j0 - 1;
+        panel_v_kernel<<<dim3((unsigned)((mr + 255) / 256), (unsigned)nb), 256, 0, s>>>(A, lda, n, j0, nb, Vp);
+        CHFSI_LAUNCH_CHECK();
+        panel_gram_kernel<<<dim3((unsigned)nb, (unsigned)nb), 256, 0, s>>>(Vp, mr, nb, Gv);
+        CHFSI_LAUNCH_CHECK();
+        panel_t_kernel<<<1, 128, 0, s>>>(Gv, tau, j0, nb, T);
+        CHFSI_LAUNCH_CHECK();
+        double* ZR = Q + (j0 + 1) * ldq;
+        int rc;
+        if ((rc = gemm_general(Vp, mr, false, ZR, ldq, W1, n, nb, n, mr, 1.0, false, s))) return rc;
+        if ((rc = gemm_general(T, nb, false, W1, n, W2, n, nb, n, nb, 1.0, false, s))) return rc;
+        if ((rc = gemm_general(Vp, mr, true, W2, n, ZR, ldq, mr, n, nb, -1.0, true, s))) return rc;
+    }
+    return CHFSI_OK;
+}
+
+}  // namespace chfsi
+
+int chfsi_eigh_workspace_size(int64_t n, size_t* bytes) {
+    if (!bytes || n < 0) return CHFSI_ERR_ARG;
+    *bytes = chfsi::align_up(chfsi::kStatusBytes) + chfsi::eigh_workspace_bytes(n);
+    return CHFSI_OK;
+}
+
+int chfsi_eigh(double* A, int64_t lda, int64_t n, double* w, double* Q, int64_t ldq, void* ws, size_t ws_bytes,
+               void* stream) {
+    if (n < 0 || (n > 0 && (!A || !w || !Q || lda < n || ldq < n))) return CHFSI_ERR_ARG;
+    if (n == 0) return CHFSI_OK;
+    size_t need = 0;
+    int rc = chfsi_eigh_workspace_size(n, &need);
+    if (rc) return rc;
+    if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255u)) return CHFSI_ERR_ARG;
+    if (ws_bytes < need) return CHFSI_ERR_NOMEM;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    unsigned* st = chfsi::status_word(ws);
+    CHFSI_CUDA_TRY(cudaMemsetAsync(st, 0, sizeof(unsigned), s));
+    char* rest = static_cast<char*>(ws) + chfsi::align_up(chfsi::kStatusBytes);
+    return chfsi::eigh(A, lda, n, w, Q, ldq, rest, ws_bytes - chfsi::align_up(chfsi::kStatusBytes), st, s);
+}

@@ -93,6 +93,10 @@ int gemm_tn_splits(int64_t K, int64_t n);
 // C (M x n, ldc) = A (M x n, lda) * B (n x n, ldb); b_upper: B is upper triangular.
 int gemm_nn(const double* A, int64_t lda, const double* B, int64_t ldb, double* C, int64_t ldc,
             int64_t M, int64_t n, bool b_upper, cudaStream_t s);
+// C (M x Nc, ldc) = alpha op(A) B (+ C when accumulate), op(A) = A (M x K, lda) or, when
+// a_t, the transpose of A stored K x M; B: K x Nc (ldb).  FP64 on the DFMA pipe.
+int gemm_general(const double* A, int64_t lda, bool a_t, const double* B, int64_t ldb, double* C, int64_t ldc,
+                 int64_t M, int64_t Nc, int64_t K, double alpha, bool accumulate, cudaStream_t s);
 // In place: upper Cholesky S = R^T R (R in the upper triangle, lower zeroed).
 int cholesky_upper(double* S, int64_t n, int64_t lds, unsigned* status, cudaStream_t s);
 // Rinv (n x n) = R^-1 for upper-triangular R.
@@ -119,6 +123,13 @@ int sddmm_accumulate_f32x2(const CsrDev& h, int64_t n, const void* Ybar, int64_t
                            int64_t ldp, double alpha, double* dH, cudaStream_t s);
 
 int fill_zero(void* p, size_t bytes, cudaStream_t s);
+
+// Hand-written dense symmetric eigensolver (eigh.cu): A (n x n, lda, both triangles)
+// = Q diag(w) Q^T with w ascending and Q[k][i] (ldq) component k of eigenvector i.
+// A is overwritten.  Scratch from ws (eigh_workspace_bytes).
+size_t eigh_workspace_bytes(int64_t n);
+int eigh(double* A, int64_t lda, int64_t n, double* w, double* Q, int64_t ldq, void* ws, size_t ws_bytes,
+         unsigned* status, cudaStream_t s);
 
 // FP64-accurate products on the BF16 tensor cores (Ozaki-scheme slices, dense_ozaki.cu).
 // tn form: C (M x Nc) = A^T B with A: K x M (lda), B: K x Nc (ldb); symmetric: the
