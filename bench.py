@@ -604,7 +604,8 @@ def mixed_variants(P, torch, dev, stream, wl, Hd, Xd, v0d, Yref, theta_ref, boun
 
 def secondary_variants(P, torch, dev, stream):
     """Layouts and schedules at 40^3/1024/m=20 (CSR, BSR, hybrid, the tcgen05 BF16
-    BSR step) and the adjoint at 32^3/512/m=16, outside the timed region."""
+    BSR step, the mixed prefixes after three cycles), the split storage on a banded
+    operator, and the adjoint at 32^3/512/m=16, outside the timed region."""
     out = {}
     try:
         wl = W.workload("g40_w3_n1024_m20")
@@ -614,9 +615,14 @@ def secondary_variants(P, torch, dev, stream):
         v0d = torch.as_tensor(W.lanczos_start(H["N"], wl.seed)).to(dev)
         bounds = P.lanczos_bounds(Hd, v0d, 20, wl.n)
         out[wl.name] = layout_variants(P, torch, dev, stream, wl, H, Hd, Xd, bounds)
+        out[wl.name]["mixed_after_cycles"] = cycles_variant(P, torch, dev, wl, Hd, Xd, v0d)
         del Hd, Xd
     except Exception as e:  # noqa: BLE001 - report, do not hide
         out["g40_w3_n1024_m20_error"] = repr(e)
+    try:
+        out["split_band65536"] = split_variant(P, torch, dev, stream)
+    except Exception as e:  # noqa: BLE001 - report, do not hide
+        out["split_band65536_error"] = repr(e)
     try:
         wl = W.workload("g32_w2_n512_m16")
         H = operator_of(wl)
@@ -627,6 +633,54 @@ def secondary_variants(P, torch, dev, stream):
         out[wl.name] = adjoint_variants(P, torch, dev, stream, wl, H, Hd, Xd, bounds)
     except Exception as e:  # noqa: BLE001 - report, do not hide
         out["g32_w2_n512_m16_error"] = repr(e)
+    return out
+
+
+def split_variant(P, torch, dev, stream):
+    """The paper's split storage (dense diagonal blocks + sparse rest, Sec. 4.1-4.2) on
+    an operator whose density decays away from the diagonal: N = 65536, every entry
+    within 512 of the diagonal stored, about 8 far couplings per row, diagonal blocks
+    of 2048 rows (about 40% dense); 512 states, degree 20.  The FP64 filter through the
+    CSR kernel against the split filter (dense blocks as Ozaki products on the tensor
+    cores), with their difference."""
+    N, band, far, B, n, m = 65536, 512, 8, 2048, 512, 20
+    H = W.banded_operator(N, band, far, 0.1, 2110158540)
+    S = W.split_from_csr(H, B)
+    Hd = P.CsrMatrix.from_arrays(H["row_ptr"], H["col"], H["val"], device=dev)
+    o = S["off"]
+    Sd = P.SplitMatrix.from_arrays(S["diag"], B, o["row_ptr"], o["col"], o["val"], device=dev)
+    Xd = torch.as_tensor(W.start_block(N, n, 2110158541)).to(dev)
+    a, b, a0 = P.lanczos_bounds(Hd, torch.as_tensor(W.lanczos_start(N, 2110158542)).to(dev), 20, n)
+    fl = filter_flops(H["nnz"], N, n, m)
+    ws = P.Workspace(dev)
+    Yc = torch.empty_like(Xd)
+    Ys = torch.empty_like(Xd)
+    t_csr = _timeit(torch, dev, stream, lambda: P.filter(Hd, Xd, m, a, b, a0, out=Yc, workspace=ws), reps=1)
+    ws2 = P.Workspace(dev)
+    t_split = _timeit(torch, dev, stream, lambda: P.filter(Sd, Xd, m, a, b, a0, out=Ys, workspace=ws2), reps=1)
+    dense_nnz = int(np.count_nonzero(S["diag"]))
+    return {"N": N, "band": band, "block": B, "n": n, "m": m, "nnz": H["nnz"], "off_nnz": o["nnz"],
+            "diag_block_density": dense_nnz / (S["n_blocks"] * B * B),
+            "csr_f64_ms": t_csr, "csr_f64_gflops": fl / (t_csr * 1e-3) / 1e9,
+            "split_ms": t_split, "split_gflops_algorithmic": fl / (t_split * 1e-3) / 1e9,
+            "speedup_split_vs_csr": t_csr / t_split,
+            "split_tensor_core_products_tflops": m * 28 * 2.0 * S["n_blocks"] * B * B * n / (t_split * 1e-3) / 1e12,
+            "y_rel_fro_split_vs_csr": float(torch.linalg.norm(Ys - Yc) / torch.linalg.norm(Yc))}
+
+
+def cycles_variant(P, torch, dev, wl, Hd, Xd, v0d, cycles=3):
+    """Ritz values after `cycles` ChFSI cycles (each cycle's Psi filters again, the
+    bounds updated from the Ritz values) with the FP32 and BF16 prefixes against the
+    all-FP64 cycles: max relative error over all n values and over those below the
+    filter edge a of the first cycle."""
+    m = wl.m
+    a, b, a0 = P.lanczos_bounds(Hd, v0d, 20, wl.n)
+    ref, _, _ = P.solve(Hd, Xd, m, cycles, v0d)
+    ref = ref.cpu().numpy()
+    out = {"cycles": cycles}
+    for low in ("f32", "bf16"):
+        th, _, _ = P.solve(Hd, Xd, m, cycles, v0d, schedule=P.mixed_schedule(m, m - 4, low))
+        out[f"{low}x{m - 4}_f64x4"] = _ritz_errors(th.cpu().numpy(), ref, a)
     return out
 
 
