@@ -345,7 +345,9 @@ int chfsi_eigh_workspace_size(int64_t n, size_t* bytes);
  * roots), back-transformation in panels of 64 reflectors.  w: n doubles, ascending.
  * Q: n x n (ldq), Q[k * ldq + i] = component k of the eigenvector of w[i].  A is
  * overwritten.  Q must not overlap A.  The call synchronises `stream` once per merge
- * of the divide and conquer.  Errors: CHFSI_ERR_ARG, CHFSI_ERR_NOMEM, CHFSI_ERR_CUDA.
+ * of the divide and conquer.  Workspace (chfsi_eigh_workspace_size): the status word
+ * and about 3 n^2 + 200 n doubles.  Errors: CHFSI_ERR_ARG, CHFSI_ERR_NOMEM,
+ * CHFSI_ERR_UNSUPPORTED (n above 65535), CHFSI_ERR_CUDA.
  */
 int chfsi_eigh(double* A, int64_t lda, int64_t n, double* w, double* Q, int64_t ldq, void* ws,
                size_t ws_bytes, void* stream);

@@ -720,6 +720,7 @@ int chfsi_eigh(double* A, int64_t lda, int64_t n, double* w, double* Q, int64_t 
                void* stream) {
     if (n < 0 || (n > 0 && (!A || !w || !Q || lda < n || ldq < n))) return CHFSI_ERR_ARG;
     if (n == 0) return CHFSI_OK;
+    if (n > 65535) return CHFSI_ERR_UNSUPPORTED;   // one grid row per matrix row in several launches
     size_t need = 0;
     int rc = chfsi_eigh_workspace_size(n, &need);
     if (rc) return rc;
