@@ -332,7 +332,8 @@ def split_from_csr(csr: dict, block: int) -> dict:
     inside = (rows // block) == (cols // block)
     diag = np.zeros(nblk * block * block, dtype=np.float64)
     ri, ci = rows[inside], cols[inside]
-    diag[(ri // block) * block * block + (ri % block) * block + (ci % block)] = csr["val"][inside]
+    # duplicate (row, column) entries add up, as they do in the CSR product
+    np.add.at(diag, (ri // block) * block * block + (ri % block) * block + (ci % block), csr["val"][inside])
     out_rows = rows[~inside]
     row_ptr = np.zeros(N + 1, dtype=np.int64)
     np.cumsum(np.bincount(out_rows, minlength=N), out=row_ptr[1:])

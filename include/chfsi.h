@@ -399,6 +399,21 @@ int chfsi_measure_pipe_peak(int32_t precision, double* flops_per_second, void* s
  * Diagnostics only: the paper has no counterpart. */
 unsigned long long chfsi_kernel_launches(void);
 
+/*
+ * Limit, in nanoseconds, of the mbarrier waits in which one role of a tensor-core
+ * kernel (chfsi_filter's BF16 steps on a BSR or hybrid operator, chfsi_ozaki_gemm and
+ * the products that use it) waits on another: a copy producer on a free stage, the
+ * MMA issuer on a loaded stage or a drained accumulator, the epilogue on a finished
+ * accumulator.  A wait that runs out makes its CTA stop, wait for its own copies and
+ * MMAs in flight (those waits keep a fixed 1 s bound), free its tensor memory and exit;
+ * the call's status word then holds CHFSI_ERR_TIMEOUT and its outputs are undefined.
+ * 0 restores the default of 1 s.  Process-wide, read at each launch; meant for tests
+ * of that abort path (a limit of a few nanoseconds makes the first wait that does not
+ * succeed at once run out).  Diagnostics only: the paper has no counterpart.
+ * Returns CHFSI_OK.
+ */
+int chfsi_set_pipeline_wait_limit(uint64_t ns);
+
 #ifdef __cplusplus
 }
 #endif

@@ -9,12 +9,12 @@ from ._abi import ChfsiError, LIB_PATH, load, status_string
 from .chfsi import (BsrMatrix, ChebyshevFilter, CsrMatrix, HybridMatrix, SplitMatrix, Workspace, eigh, filter,
                     filter_backward,
                     filter_workspace_bytes, lanczos_bounds, lanczos_workspace_bytes, measure_pipe_peak,
-                    mixed_schedule, ozaki_gemm, rayleigh_ritz,
+                    mixed_schedule, ozaki_gemm, rayleigh_ritz, split_block_density, split_block_size,
                     rayleigh_ritz_workspace_bytes, read_status, solve, symmetric_gradient, transpose_index)
 
 __all__ = [
     "ChfsiError", "LIB_PATH", "load", "status_string", "BsrMatrix", "ChebyshevFilter", "CsrMatrix", "HybridMatrix",
-    "SplitMatrix", "eigh",
+    "SplitMatrix", "eigh", "split_block_density", "split_block_size",
     "Workspace", "filter", "filter_backward", "filter_workspace_bytes", "lanczos_bounds",
     "lanczos_workspace_bytes", "measure_pipe_peak", "ozaki_gemm",
     "mixed_schedule", "rayleigh_ritz", "rayleigh_ritz_workspace_bytes", "read_status",

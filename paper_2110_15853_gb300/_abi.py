@@ -88,6 +88,7 @@ SIGNATURES = {
     "chfsi_read_status": (ctypes.c_int, [_vp, _vp]),
     "chfsi_clear_status": (ctypes.c_int, [_vp, _vp]),
     "chfsi_kernel_launches": (ctypes.c_ulonglong, []),
+    "chfsi_set_pipeline_wait_limit": (ctypes.c_int, [ctypes.c_uint64]),
     "chfsi_measure_pipe_peak": (ctypes.c_int, [_i32, _DP, _vp]),
     "chfsi_eigh_workspace_size": (ctypes.c_int, [_i64, _SZP]),
     "chfsi_eigh": (ctypes.c_int, [_vp, _i64, _i64, _vp, _vp, _i64, _vp, _sz, _vp]),

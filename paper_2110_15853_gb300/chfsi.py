@@ -133,6 +133,45 @@ class HybridMatrix:
         return m
 
 
+def _block_density(rows: np.ndarray, cols: np.ndarray, N: int, block: int) -> float:
+    inside = int(np.count_nonzero(rows // block == cols // block))
+    full, rem = divmod(N, block)
+    return inside / float(full * block * block + rem * rem)
+
+
+def split_block_density(row_ptr, col, block: int) -> float:
+    """Fraction of the diagonal blocks' entries (blocks of `block` rows, the last one
+    ragged) that the operator stores: the density the paper compares with 5% when it
+    chooses the rows of a dense diagonal block H^{L(D)} (Sec. 4.1)."""
+    row_ptr = np.asarray(row_ptr, dtype=np.int64)
+    N = len(row_ptr) - 1
+    if N <= 0:
+        return 0.0
+    rows = np.repeat(np.arange(N, dtype=np.int64), np.diff(row_ptr))
+    return _block_density(rows, np.asarray(col, dtype=np.int64), N, int(block))
+
+
+def split_block_size(row_ptr, col, min_density: float = 0.05, max_block: int = 8192) -> int:
+    """The largest diagonal-block size among 128, 256, ..., max_block (and no larger
+    than N rounded up to 128) whose diagonal blocks are at least `min_density` dense.
+    Sec. 4.1 sizes the dense diagonal block as large as memory allows while its density
+    stays above 5%, the point above which dense products beat sparse ones; 128 is the
+    fallback when no size reaches the threshold."""
+    row_ptr = np.asarray(row_ptr, dtype=np.int64)
+    N = len(row_ptr) - 1
+    if N <= 0:
+        return 128
+    rows = np.repeat(np.arange(N, dtype=np.int64), np.diff(row_ptr))
+    cols = np.asarray(col, dtype=np.int64)
+    top = min(int(max_block), (N + 127) // 128 * 128)
+    best, B = 128, 128
+    while B <= top:
+        if _block_density(rows, cols, N, B) >= min_density:
+            best = B
+        B *= 2
+    return best
+
+
 @dataclass
 class SplitMatrix:
     """The paper's split storage (Sec. 4.1-4.2): dense block x block diagonal blocks
@@ -148,6 +187,29 @@ class SplitMatrix:
         off = CsrMatrix.from_arrays(off_row_ptr, off_col, off_val, device=device)
         dg = torch.as_tensor(np.ascontiguousarray(diag, dtype=np.float64)).to(device)
         return cls(dg, off, int(block), off.n_rows)
+
+    @classmethod
+    def from_csr(cls, row_ptr, col, val, block: Optional[int] = None, min_density: float = 0.05,
+                 device="cuda") -> "SplitMatrix":
+        """Split a host CSR operator: the entries whose column falls in the row's own
+        block of `block` rows go to the dense diagonal blocks (duplicates add up), the rest
+        stay in CSR.  Without `block`, the block is split_block_size(row_ptr, col,
+        min_density)."""
+        row_ptr = np.asarray(row_ptr, dtype=np.int64)
+        col = np.asarray(col)
+        val = np.asarray(val, dtype=np.float64)
+        N = len(row_ptr) - 1
+        B = int(block) if block is not None else split_block_size(row_ptr, col, min_density)
+        nblk = (N + B - 1) // B
+        rows = np.repeat(np.arange(N, dtype=np.int64), np.diff(row_ptr))
+        cols = col.astype(np.int64)
+        inside = (rows // B) == (cols // B)
+        diag = np.zeros(nblk * B * B, dtype=np.float64)
+        ri, ci = rows[inside], cols[inside]
+        np.add.at(diag, (ri // B) * B * B + (ri % B) * B + (ci % B), val[inside])
+        off_ptr = np.zeros(N + 1, dtype=np.int64)
+        np.cumsum(np.bincount(rows[~inside], minlength=N), out=off_ptr[1:])
+        return cls.from_arrays(diag, B, off_ptr, col[~inside].astype(np.int32), val[~inside], device=device)
 
     @property
     def device(self) -> torch.device:

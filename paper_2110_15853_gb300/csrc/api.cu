@@ -24,6 +24,13 @@ std::atomic<unsigned long long> g_launches{0};
 void chfsi::note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 namespace {
+constexpr uint64_t kPipelineWaitNs = 1000000000ull;
+std::atomic<uint64_t> g_pipeline_wait_ns{kPipelineWaitNs};
+}  // namespace
+
+uint64_t chfsi::pipeline_wait_ns() { return g_pipeline_wait_ns.load(std::memory_order_relaxed); }
+
+namespace {
 
 constexpr int kVersion = 10000;   // 1.0.0
 
@@ -261,6 +268,11 @@ const char* chfsi_status_string(int st) {
 int chfsi_version(void) { return kVersion; }
 
 unsigned long long chfsi_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+int chfsi_set_pipeline_wait_limit(uint64_t ns) {
+    g_pipeline_wait_ns.store(ns == 0 ? kPipelineWaitNs : ns, std::memory_order_relaxed);
+    return CHFSI_OK;
+}
 
 int chfsi_clear_status(void* ws, void* stream) {
     if (!ws) return CHFSI_ERR_ARG;

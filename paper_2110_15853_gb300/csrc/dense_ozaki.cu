@@ -74,8 +74,6 @@ constexpr int kThreads = 32 * (2 + kEpiWarps);
 constexpr int kSmemBytes = kStages * kStageBytes + 1024;
 constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t kIdesc = idesc_bf16(kTileM, kTileN);
-constexpr uint64_t kWaitNs = 1000000000ull;           // pipeline waits
-constexpr uint64_t kDrainNs = 1000000000ull;          // waits for work already in flight
 constexpr int kXEvent = 1, kYEvent = 2, kFullEvent = 3;
 static_assert(kSmemBytes + 1024 <= 227 * 1024, "shared memory per CTA");
 static_assert(kAccs * kTileN <= (int)kTmemCols, "seven accumulators in TMEM");
@@ -119,6 +117,7 @@ struct OzArgs {
     int nbatch;               // independent products (diagonal blocks of the split layout)
     int64_t m_batch;          // output rows per batch (M when nbatch = 1)
     int64_t a_batch_rows, b_batch_rows;   // operand rows per batch in the slice arrays
+    uint64_t wait_ns;         // limit of the waits on the other roles (drains keep kDrainNs)
     unsigned* status;
 };
 
@@ -229,7 +228,7 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             for (int kb = 0; kb < it.KB; kb++, sc++) {
                 const int s = (int)(sc % kStages);
                 const int64_t u = sc / kStages;
-                if (u >= 1 && !mbar_wait(sa(&empty[s]), (uint32_t)((u - 1) & 1), kWaitNs)) { ok = false; break; }
+                if (u >= 1 && !mbar_wait(sa(&empty[s]), (uint32_t)((u - 1) & 1), g.wait_ns)) { ok = false; break; }
                 const uint32_t st = sa(smem + (size_t)s * kStageBytes);
                 const int x = (it.kb0 + kb) * kKB;
                 mbar_expect_tx(&full[s], kStageBytes);
@@ -260,7 +259,7 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             bool ok = true;
             for (int kb = 0; kb < it.KB; kb++, sc++) {
                 const int s = (int)(sc % kStages);
-                if (!mbar_wait(sa(&full[s]), (uint32_t)((sc / kStages) & 1), kWaitNs) || *abort_v) {
+                if (!mbar_wait(sa(&full[s]), (uint32_t)((sc / kStages) & 1), g.wait_ns) || *abort_v) {
                     ok = false;
                     break;
                 }
@@ -270,7 +269,7 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                 const bool resetX = kb == 0 || kb % kPeriodX == kPeriodX - 2;
                 const bool resetY = kb == 0 || kb % kPeriodY == 0;
                 auto wait_drain = [&]() -> bool {
-                    const bool w = mbar_wait(sa(&eempty), (uint32_t)(ev_wait & 1), kWaitNs);
+                    const bool w = mbar_wait(sa(&eempty), (uint32_t)(ev_wait & 1), g.wait_ns);
                     ev_wait++;
                     asm volatile("tcgen05.fence::after_thread_sync;");
                     return w;
@@ -296,27 +295,29 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                     }
                     issued = true;
                 };
+                // after a drain wait that gave up, nothing more is issued into the
+                // accumulators that the epilogue may still be reading
                 bool w = true;
                 if (kb == 0) {
                     if (ev_commit > 0) w = wait_drain();     // the previous item's output drain
-                    issue(0, kPairs);
+                    if (w) issue(0, kPairs);
                 } else if (resetX) {                           // E2 .. E5 drained after the last block
                     issue(kGroupX, kPairs);
                     w = wait_drain();
-                    issue(0, kGroupX);
+                    if (w) issue(0, kGroupX);
                 } else if (resetY) {                           // E6 .. E8 drained after the last block
                     issue(0, kGroupX);
                     w = wait_drain();
-                    issue(kGroupX, kPairs);
+                    if (w) issue(kGroupX, kPairs);
                 } else {
                     issue(0, kPairs);
                 }
                 umma_commit(&empty[s]);
+                if (!w) { ok = false; sc++; break; }
                 if (event_at(kb, it.KB)) {
                     umma_commit(&efull);
                     ev_commit++;
                 }
-                if (!w) { ok = false; sc++; break; }
             }
             if (!ok) { *abort_v = 1; break; }
         }
@@ -339,7 +340,7 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             for (int kb = 0; kb < it.KB; kb++) {
                 const int kind = event_at(kb, it.KB);
                 if (!kind) continue;
-                if (!__all_sync(0xffffffffu, !*abort_v && mbar_wait(sa(&efull), (uint32_t)(ev & 1), kWaitNs))) {
+                if (!__all_sync(0xffffffffu, !*abort_v && mbar_wait(sa(&efull), (uint32_t)(ev & 1), g.wait_ns))) {
                     ok = false;
                     break;
                 }
@@ -671,6 +672,7 @@ int oz_run(const OzPlan& p, bool tn_form, double* C, int64_t ldc, int64_t M, int
     g.splits = (g.kb_total + g.kb_split - 1) / g.kb_split;   // no empty split
     g.symmetric = symmetric ? 1 : 0;
     g.b_upper = b_upper ? 1 : 0;
+    g.wait_ns = pipeline_wait_ns();
     g.status = status;
     g.C = tn_form ? nullptr : C;
     g.part = tn_form ? p.part : nullptr;

@@ -31,13 +31,17 @@
 //                    8 rows x 256 states at a time into a two-deep ring;
 //   warps 3-6      : epilogue (warp w reads TMEM lanes 32*(w%4)..+31) of one item
 //                    while the MMAs of the next one run.
-// Every mbarrier wait is bounded (1 s on %globaltimer); on timeout the CTA flags
-// DEV_TIMEOUT, stops issuing work, waits (bounded) for its copies and MMAs in
-// flight, frees TMEM and exits.
+// Every mbarrier wait is bounded on %globaltimer.  A wait of one role on another
+// (a stage, an accumulator, an epilogue chunk) gives up after the pipeline limit
+// (1 s, shorter only when a test sets chfsi_set_pipeline_wait_limit); the CTA then
+// flags DEV_TIMEOUT, stops issuing work, waits for its own copies and MMAs in flight
+// (those drains keep a fixed 1 s bound: they end as soon as the hardware does), frees
+// TMEM and exits.
 #include <cuda.h>
 
 #include "common.cuh"
 #include "kernels.cuh"
+#include "tcgen05.cuh"
 
 namespace chfsi {
 
@@ -73,69 +77,10 @@ static_assert(kTmemCols <= 512 && kEpiRows % 8 == 0 && kBlk % kEpiRows == 0, "ti
 static_assert(kSmemBytes + 1024 <= 227 * 1024, "shared memory per CTA (with the static barriers)");
 // per-stage flags written by the operand producer for the MMA issuer
 constexpr int kFirst = 1, kLast = 2, kEmptyItem = 4;
-constexpr uint64_t kTimeoutNs = 1000000000ull;
+using namespace tc;
 
-__device__ __forceinline__ uint32_t sa(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ uint64_t gtime() {
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-// Bounded wait for the phase of `parity` on an mbarrier; false on timeout.  The
-// clock is read only every 1024 polls so that a completed phase is seen at once.
-__device__ bool mbar_wait(uint32_t addr, uint32_t parity) {
-    uint64_t t0 = 0;
-    for (uint32_t polls = 1;; polls++) {
-        uint32_t done;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
-            : "=r"(done) : "r"(addr), "r"(parity) : "memory");
-        if (done) return true;
-        if ((polls & 1023u) == 0) {
-            const uint64_t now = gtime();
-            if (t0 == 0) t0 = now;
-            else if (now - t0 > kTimeoutNs) return false;
-        }
-    }
-}
-
-// UMMA shared-memory descriptor: K-major operand, 128-byte swizzle (rows of 64
-// BF16, 8-row atoms of 1024 B), as written by TMA with CU_TENSOR_MAP_SWIZZLE_128B.
-__device__ __forceinline__ uint64_t desc_sw128(uint32_t addr) {
-    uint64_t d = 0;
-    d |= (uint64_t)((addr & 0x3FFFF) >> 4);   // start address
-    d |= (uint64_t)1 << 16;                   // leading byte offset (unused for swizzled K-major)
-    d |= (uint64_t)(1024 >> 4) << 32;         // stride byte offset: 8-row atom
-    d |= (uint64_t)1 << 46;                   // descriptor version
-    d |= (uint64_t)2 << 61;                   // 128-byte swizzle
-    return d;
-}
-
-// Instruction descriptor: kind::f16, BF16 x BF16 -> FP32, both K-major, M = 128, N = 128.
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kRowsN >> 3) << 17) |
-                            ((uint32_t)(kTileJ >> 4) << 24);
-
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
-        :: "r"(dst), "l"((uint64_t)map), "r"(x), "r"(y), "r"(bar) : "memory");
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* b, unsigned count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(sa(b)), "r"(count));
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(sa(b)) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, unsigned bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(sa(b)), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void umma_commit(uint64_t* b) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" :: "r"(sa(b))
-                 : "memory");
-}
+// Instruction descriptor: kind::f16, BF16 x BF16 -> FP32, both K-major, M = 128 states, N = 128 rows.
+constexpr uint32_t kIdesc = idesc_bf16(kTileJ, kRowsN);
 
 // kEpiRows consecutive accumulator columns of this warp's 32 TMEM lanes (one per lane).
 __device__ __forceinline__ void tmem_ld_chunk(uint32_t taddr, uint32_t (&r)[kEpiRows]) {
@@ -162,7 +107,8 @@ bsr_tc_kernel(const __grid_constant__ CUtensorMap tmY, const __grid_constant__ C
               int64_t nbr, const int32_t* __restrict__ brow_ptr, const int32_t* __restrict__ bcol, int64_t nblocks,
               int64_t N, int64_t n, int64_t nspans, float* __restrict__ Yo, int64_t ldo,
               // the BF16 block table holds a zero block at index nblocks (the missing block of a pair)
-              __nv_bfloat16* __restrict__ Ysh_out, float alpha, float c, float beta, unsigned* status) {
+              __nv_bfloat16* __restrict__ Ysh_out, float alpha, float c, float beta, uint64_t wait_ns,
+              unsigned* status) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     unsigned char* stages = smem;                                   // kStages x (A | B), 1024-aligned
@@ -226,7 +172,7 @@ bsr_tc_kernel(const __grid_constant__ CUtensorMap tmY, const __grid_constant__ C
         // next stage: wait until the issuer has released it, then set its flags
         auto acquire = [&](int flags) -> int {
             const int s = (int)(sc % kStages), u = (int)(sc / kStages);
-            if (u >= 1 && !mbar_wait(sa(&empty[s]), (u - 1) & 1)) return -1;
+            if (u >= 1 && !mbar_wait(sa(&empty[s]), (u - 1) & 1, wait_ns)) return -1;
             stage_flags[s] = flags;
             return s;
         };
@@ -282,7 +228,7 @@ bsr_tc_kernel(const __grid_constant__ CUtensorMap tmY, const __grid_constant__ C
         // wait (bounded) until every copy this thread issued has landed
         for (int s = 0; s < kStages && s < sc; s++) {
             const int64_t last = s + ((sc - 1 - s) / kStages) * kStages;
-            mbar_wait(sa(&full[s]), (int)(last / kStages) & 1);
+            mbar_wait(sa(&full[s]), (int)(last / kStages) & 1, kDrainNs);
         }
     } else if (warp == 2 && lane == 0) {
         // ---------------- TMA producer of the epilogue operand chunks
@@ -294,7 +240,7 @@ bsr_tc_kernel(const __grid_constant__ CUtensorMap tmY, const __grid_constant__ C
             for (int ch = 0; ch < kEpiChunks; ch++, g++) {
                 const int slot = (int)(g & 1);
                 const int64_t use = g >> 1;
-                if (use >= 1 && !mbar_wait(sa(&eempty[slot]), (int)((use - 1) & 1))) { ok = false; break; }
+                if (use >= 1 && !mbar_wait(sa(&eempty[slot]), (int)((use - 1) & 1), wait_ns)) { ok = false; break; }
                 const uint32_t dst = sa(epi + slot * kEpiSlot);
                 int64_t row64 = R0 * kBlk + ch * kEpiRows;
                 if (row64 >= N) row64 = R0 * kBlk;   // rows past the last block row: not used
@@ -307,30 +253,30 @@ bsr_tc_kernel(const __grid_constant__ CUtensorMap tmY, const __grid_constant__ C
         }
         // wait (bounded) until the last copy into each slot has landed
         for (int64_t last = g - 1; last >= 0 && last >= g - 2; last--)
-            mbar_wait(sa(&efull[last & 1]), (int)((last >> 1) & 1));
+            mbar_wait(sa(&efull[last & 1]), (int)((last >> 1) & 1), kDrainNs);
     } else if (warp == 1 && lane == 0) {
         // ---------------- MMA issuer
         int64_t sc = 0;
         int items = 0;
         for (int64_t item = blockIdx.x; item < total && !*abort_v; item += gridDim.x, items++) {
             const int b = items & 1, v = items >> 1;
-            if (v >= 1 && !mbar_wait(sa(&tempty[b]), (v - 1) & 1)) { *abort_v = 1; break; }
+            if (v >= 1 && !mbar_wait(sa(&tempty[b]), (v - 1) & 1, wait_ns)) { *abort_v = 1; break; }
             asm volatile("tcgen05.fence::after_thread_sync;");
             const uint32_t acc_addr = tmem + (uint32_t)(b * kAccCols);   // tile u at + u * kRowsN
             const int nt = tiles_of(item % nspans);
             bool ok = true;
             for (;; sc++) {
                 const int s = (int)(sc % kStages), u = (int)(sc / kStages);
-                if (!mbar_wait(sa(&full[s]), u & 1) || *abort_v) { *abort_v = 1; ok = false; break; }
+                if (!mbar_wait(sa(&full[s]), u & 1, wait_ns) || *abort_v) { *abort_v = 1; ok = false; break; }
                 asm volatile("tcgen05.fence::after_thread_sync;");
                 const int flags = stage_flags[s];
                 if (!(flags & kEmptyItem)) {
                     const uint32_t st = sa(stages + (size_t)s * kStageBytes);
-                    const uint64_t db = desc_sw128(st + kTiles * kATile);
+                    const uint64_t db = desc_kmajor(st + kTiles * kATile, 128);
 #pragma unroll
                     for (int u = 0; u < kTiles; u++) {
                         if (u >= nt) break;
-                        const uint64_t da = desc_sw128(st + u * kATile);
+                        const uint64_t da = desc_kmajor(st + u * kATile, 128);
 #pragma unroll
                         for (int k = 0; k < kBlk / 16; k++) {
                             const uint32_t accumulate = ((flags & kFirst) && k == 0) ? 0u : 1u;
@@ -351,7 +297,7 @@ bsr_tc_kernel(const __grid_constant__ CUtensorMap tmY, const __grid_constant__ C
         // every MMA this thread issued has completed before TMEM is released
         if (items > 0) {
             const int lb = (items - 1) & 1, lv = (items - 1) >> 1;
-            mbar_wait(sa(&tfull[lb]), lv & 1);
+            mbar_wait(sa(&tfull[lb]), lv & 1, kDrainNs);
         }
     } else if (warp >= 3) {
         // ---------------- epilogue
@@ -361,7 +307,7 @@ bsr_tc_kernel(const __grid_constant__ CUtensorMap tmY, const __grid_constant__ C
             const int64_t R0 = kRowsPerItem * (item / nspans), sp = item % nspans;
             const int b = items & 1, v = items >> 1;
             // the warp decides together (the TMEM loads below are warp-collective)
-            const bool ok = __all_sync(0xffffffffu, !*abort_v && mbar_wait(sa(&tfull[b]), v & 1));
+            const bool ok = __all_sync(0xffffffffu, !*abort_v && mbar_wait(sa(&tfull[b]), v & 1, wait_ns));
             if (!ok) { *abort_v = 1; break; }
             asm volatile("tcgen05.fence::after_thread_sync;");
             bool has_acc = false;                                 // else no MMA wrote the accumulator
@@ -378,7 +324,7 @@ bsr_tc_kernel(const __grid_constant__ CUtensorMap tmY, const __grid_constant__ C
             for (int cchunk = 0; cchunk < kEpiChunks; cchunk++) {
                 const int64_t g = (int64_t)items * kEpiChunks + cchunk;
                 const int slot = (int)(g & 1);
-                if (!__all_sync(0xffffffffu, mbar_wait(sa(&efull[slot]), (int)((g >> 1) & 1)))) {
+                if (!__all_sync(0xffffffffu, mbar_wait(sa(&efull[slot]), (int)((g >> 1) & 1), wait_ns))) {
                     chunks_ok = false;
                     break;
                 }
@@ -467,37 +413,10 @@ __global__ void transpose_to_bf16_kernel(const double* __restrict__ src, int64_t
     }
 }
 
-typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
-                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-EncodeTiledFn encode_fn() {
-    static EncodeTiledFn fn = nullptr;
-    if (!fn) {
-        void* p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-                cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<EncodeTiledFn>(p);
-    }
-    return fn;
-}
-
 // 2-D BF16 tensor map over a row-major [rows x cols] array, box [box_rows x 64],
 // 128-byte swizzle (MMA operand tiles).
 int make_map(CUtensorMap* map, const void* base, int64_t cols, int64_t rows, int box_rows) {
-    EncodeTiledFn enc = encode_fn();
-    if (!enc) return CHFSI_ERR_CUDA;
-    if ((reinterpret_cast<uintptr_t>(base) & 15u) || ((cols * 2) % 16)) return CHFSI_ERR_ARG;
-    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
-    cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
-    cuuint32_t box[2] = {64, (cuuint32_t)box_rows};
-    cuuint32_t es[2] = {1, 1};
-    CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, es,
-                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    return r == CUDA_SUCCESS ? CHFSI_OK : CHFSI_ERR_CUDA;
+    return make_map_bf16(map, base, cols, rows, 64, box_rows, CU_TENSOR_MAP_SWIZZLE_128B);
 }
 
 // 2-D FP32 tensor map over a row-major [rows x ld] array, box [kEpiRows rows x kItemJ
@@ -514,18 +433,6 @@ int make_map_f32(CUtensorMap* map, const float* base, int64_t ld, int64_t rows) 
                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? CHFSI_OK : CHFSI_ERR_CUDA;
-}
-
-int sm_count() {
-    static int cache[kMaxDevices] = {};
-    const int dev = current_device();
-    if (dev < 0) return 0;
-    if (!cache[dev]) {
-        int v = 0;
-        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-        cache[dev] = v;
-    }
-    return cache[dev];
 }
 
 }  // namespace
@@ -582,7 +489,7 @@ int bsr_step_tc(const BsrDev& h, int64_t n, const void* ysh_in, const float* Yc,
     bsr_tc_kernel<<<grid, kThreads, kSmemBytes, s>>>(tmY, tmH, tmYc, tmYp, Yp ? 1 : 0, h.nbr, h.brow_ptr, h.bcol,
                                                      h.nblocks, N, n, nspans, Yo, ldo,
                                                      static_cast<__nv_bfloat16*>(ysh_out), (float)alpha, (float)c,
-                                                     (float)beta, status);
+                                                     (float)beta, pipeline_wait_ns(), status);
     CHFSI_LAUNCH_CHECK();
     return CHFSI_OK;
 }

@@ -5,6 +5,10 @@
 
 namespace chfsi {
 
+// Limit, in ns, of the waits of one role of a tensor-core kernel on another: 1 s, or
+// the shorter value set by chfsi_set_pipeline_wait_limit (tests of the abort path).
+uint64_t pipeline_wait_ns();
+
 enum class Buf { F64, F32, BF16, F32X2 };
 enum class StepMath { F64, F32, BF16 };
 

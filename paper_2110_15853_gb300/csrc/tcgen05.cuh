@@ -18,10 +18,17 @@ __device__ __forceinline__ uint64_t gtime() {
     return t;
 }
 
+// Limit of the waits that drain a CTA's own copies and MMAs before it exits: they
+// end by themselves once the hardware finishes, so they keep this bound whatever the
+// pipeline limit (chfsi_set_pipeline_wait_limit) is.
+constexpr uint64_t kDrainNs = 1000000000ull;
+
 // Wait for the phase of `parity` on an mbarrier for at most `limit_ns`; false on
-// timeout.  The clock is read only every 1024 polls so that a completed phase is
-// seen at once.
+// timeout.  The clock is read every 1024 polls so that a completed phase is seen at
+// once; limits below a millisecond (the short limits of the abort-path tests) read
+// it at every poll.
 __device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t parity, uint64_t limit_ns) {
+    const uint32_t mask = limit_ns < 1000000ull ? 0u : 1023u;
     uint64_t t0 = 0;
     for (uint32_t polls = 1;; polls++) {
         uint32_t done;
@@ -29,7 +36,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t parity, uint64
             "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
             : "=r"(done) : "r"(addr), "r"(parity) : "memory");
         if (done) return true;
-        if ((polls & 1023u) == 0) {
+        if ((polls & mask) == 0) {
             const uint64_t now = gtime();
             if (t0 == 0) t0 = now;
             else if (now - t0 > limit_ns) return false;

@@ -71,3 +71,18 @@ def test_split_rejects_unsupported_uses(P):
     with pytest.raises(P.ChfsiError) as e:
         P.filter(bad, X, 4, 4.0, 12.0, 2.0)
     assert e.value.code == _abi.CHFSI_ERR_UNSUPPORTED
+
+
+def test_split_from_csr_with_the_density_rule(P, oracle_mod):
+    """SplitMatrix.from_csr without a block: the largest power-of-two block whose
+    diagonal blocks stay at least 5% dense (Sec. 4.1), through the filter."""
+    N = 3000
+    H = W.banded_operator(N, 60, 3, 0.1, 31)
+    B = P.split_block_size(H["row_ptr"], H["col"])
+    assert B == 2048 and P.split_block_density(H["row_ptr"], H["col"], B) >= 0.05
+    Sd = P.SplitMatrix.from_csr(H["row_ptr"], H["col"], H["val"], device="cuda")
+    assert Sd.block == B
+    X = W.start_block(N, 24, 32)
+    a, b, a0 = oracle_mod.lanczos_bounds(H, W.lanczos_start(N, 33), 20, 24)
+    Y = P.filter(Sd, torch.as_tensor(X).cuda(), 6, a, b, a0)
+    assert rel_fro(Y.cpu().numpy(), oracle_mod.filter(H, X, 6, a, b, a0)) <= 1e-12
