@@ -6,8 +6,9 @@
 //   2. divide and conquer on T (Cuppen's splitting T = diag(T1, T2) + rho u u^T):
 //      leaves of 32 rows by parallel-ordered Jacobi in shared memory; each merge
 //      deflates (small components of z, nearly equal poles rotated together), finds
-//      the roots of the secular equation 1 + rho sum z_j^2 / (d_j - lambda) by
-//      bisection measured from the nearer pole, recomputes z from the roots (the
+//      the roots of the secular equation 1 + rho sum z_j^2 / (d_j - lambda) (one warp
+//      per root, bracketed Newton steps measured from the nearer pole), recomputes z
+//      from the roots (the
 //      Gu-Eisenstat formula, so that the eigenvectors come out orthogonal), and
 //      multiplies the subproblem vectors by the eigenvectors of D + rho z z^T;
 //   3. back-transformation Q = Q_H Q_T in panels of 64 reflectors (compact WY form
@@ -349,11 +350,23 @@ __global__ void dc_rotate_kernel(int64_t l, int64_t k, double* Q, int64_t ldq, M
     }
 }
 
-// Roots of 1 + rho sum_j z_j^2 / (d_j - lambda) (rho > 0, d ascending, sum z^2 = 1):
-// root i lies in (d_i, d_{i+1}), the last in (d_k, d_k + rho).  Each root is found by
-// bisection on tau = lambda - d_org, measured from the nearer pole d_org, so that the
-// differences d_j - lambda = (d_j - d_org) - tau keep their relative accuracy.
-__global__ void dc_secular_kernel(MergeBufs b, int cap) {
+constexpr int kRootWarps = 8;        // roots (one warp each) per block of the secular-equation kernels
+
+__device__ __forceinline__ double warp_prod(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v *= __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Roots of 1 + rho sum_j z_j^2 / (d_j - lambda) (rho > 0, d ascending, sum z^2 <= 1):
+// root i lies in (d_i, d_{i+1}), the last in (d_k, d_k + rho).  One warp per root, the
+// lanes sharing the sum over the poles (the xor-butterfly sums leave the same value in
+// every lane, so the warp's control flow stays uniform).  Each root is found in
+// tau = lambda - d_org, measured from the nearer pole d_org, so that the differences
+// d_j - lambda = (d_j - d_org) - tau keep their relative accuracy: Newton steps on the
+// increasing function g(tau) inside a bracket [lo, hi] with g(lo) < 0 < g(hi), a
+// bisection step whenever Newton would leave the bracket.
+__global__ void __launch_bounds__(32 * kRootWarps) dc_secular_kernel(MergeBufs b, int cap) {
     extern __shared__ double sh[];
     const int k = (int)b.par[2];
     const double rho = b.par[0];
@@ -367,70 +380,93 @@ __global__ void dc_secular_kernel(MergeBufs b, int cap) {
         }
     }
     __syncthreads();
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const int i = blockIdx.x * kRootWarps + (threadIdx.x >> 5);
     if (i >= k) return;
     auto Dj = [&](int j) { return staged ? Ds[j] : b.Dnd[j]; };
     auto Zj = [&](int j) { return staged ? z2[j] : b.znd[j] * b.znd[j]; };
-    const double lo = Dj(i);
-    const double gap = (i + 1 < k) ? Dj(i + 1) - lo : rho;
-    // f at the midpoint decides which pole is nearer
-    const double mid = lo + 0.5 * gap;
-    double fm = 1.0;
-    for (int j = 0; j < k; j++) fm += rho * Zj(j) / (Dj(j) - mid);
+    const double d_i = Dj(i);
+    const double gap = (i + 1 < k) ? Dj(i + 1) - d_i : rho;
+    // g at the midpoint decides which pole is nearer
+    const double mid = d_i + 0.5 * gap;
+    double fm = 0.0;
+    for (int j = lane; j < k; j += 32) fm += Zj(j) / (Dj(j) - mid);
+    fm = 1.0 + rho * warp_sum(fm);
     int org;
-    double a, c;
+    double lo, hi;
     if (i + 1 == k) {
         org = i;
-        if (fm < 0.0) { a = 0.5 * gap; c = gap; }
-        else { a = 0.0; c = 0.5 * gap; }
+        if (fm < 0.0) { lo = 0.5 * gap; hi = gap; }
+        else { lo = 0.0; hi = 0.5 * gap; }
     } else if (fm >= 0.0) {
-        org = i; a = 0.0; c = 0.5 * gap;
+        org = i; lo = 0.0; hi = 0.5 * gap;
     } else {
-        org = i + 1; a = -0.5 * gap; c = 0.0;
+        org = i + 1; lo = -0.5 * gap; hi = 0.0;
     }
     const double dorg = Dj(org);
-    for (int it = 0; it < 400; it++) {
-        const double t = 0.5 * (a + c);
-        if (t == a || t == c) break;
-        double f = 1.0;
-        for (int j = 0; j < k; j++) f += rho * Zj(j) / ((Dj(j) - dorg) - t);
-        if (f > 0.0) c = t;     // f increases with lambda between consecutive poles
-        else a = t;
-        if (c - a <= 2.0 * kEps * fmax(fabs(a), fabs(c))) break;
+    double t = 0.5 * (lo + hi);
+    for (int it = 0; it < 200; it++) {
+        double g = 0.0, dg = 0.0;
+        for (int j = lane; j < k; j += 32) {
+            const double r = 1.0 / ((Dj(j) - dorg) - t);
+            const double q = Zj(j) * r;
+            g += q;
+            dg = fma(q, r, dg);
+        }
+        g = 1.0 + rho * warp_sum(g);
+        dg = rho * warp_sum(dg);
+        if (g == 0.0) break;
+        if (g > 0.0) hi = t;
+        else lo = t;
+        double tn = t - g / dg;
+        if (!(tn > lo && tn < hi)) tn = 0.5 * (lo + hi);
+        const bool done = fabs(tn - t) <= 2.0 * kEps * fabs(tn) || hi - lo <= 2.0 * kEps * fmax(fabs(lo), fabs(hi));
+        t = tn;
+        if (done) break;
     }
-    b.org[i] = org;
-    b.tau_r[i] = 0.5 * (a + c);
+    if (lane == 0) {
+        b.org[i] = org;
+        b.tau_r[i] = t;
+    }
 }
 
 // Recomputed weights zhat_i^2 = prod_j (lambda_j - d_i) / (rho prod_{j != i} (d_j - d_i))
-// (sign of the original z_i), and the norms of the eigenvectors
-// u_i = (zhat_j / (d_j - lambda_i))_j.
-__global__ void dc_lowner_kernel(MergeBufs b) {
+// (sign of the original z_i); one warp per i, each lane a strided part of the product.
+// By interlacing, every partial product of the ratios stays between the bounds of the
+// telescoping products, far from overflow.
+__global__ void __launch_bounds__(32 * kRootWarps) dc_lowner_kernel(MergeBufs b) {
     const int k = (int)b.par[2];
     const double rho = b.par[0];
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const int i = blockIdx.x * kRootWarps + (threadIdx.x >> 5);
     if (i >= k) return;
     const double di = b.Dnd[i];
     double prod = 1.0;
-    for (int j = 0; j < k; j++) {
+    for (int j = lane; j < k; j += 32) {
         const double lmd = (b.Dnd[b.org[j]] - di) + b.tau_r[j];   // lambda_j - d_i
         prod *= (j == i) ? lmd / rho : lmd / (b.Dnd[j] - di);
     }
-    const double zh = sqrt(fabs(prod));
-    b.zhat[i] = b.znd[i] >= 0.0 ? zh : -zh;
+    prod = warp_prod(prod);
+    if (lane == 0) {
+        const double zh = sqrt(fabs(prod));
+        b.zhat[i] = b.znd[i] >= 0.0 ? zh : -zh;
+    }
 }
 
-__global__ void dc_norm_kernel(MergeBufs b) {
+// Norms of the eigenvectors u_i = (zhat_j / (d_j - lambda_i))_j; one warp per i.
+__global__ void __launch_bounds__(32 * kRootWarps) dc_norm_kernel(MergeBufs b) {
     const int k = (int)b.par[2];
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const int i = blockIdx.x * kRootWarps + (threadIdx.x >> 5);
     if (i >= k) return;
     const double dorg = b.Dnd[b.org[i]], t = b.tau_r[i];
     double s = 0.0;
-    for (int j = 0; j < k; j++) {
+    for (int j = lane; j < k; j += 32) {
         const double q = b.zhat[j] / ((b.Dnd[j] - dorg) - t);
         s = fma(q, q, s);
     }
-    b.norm[i] = sqrt(s);
+    s = warp_sum(s);
+    if (lane == 0) b.norm[i] = sqrt(s);
 }
 
 // U[j][i] = zhat_j / (d_j - lambda_i) / |u_i|  (k_nd x k_nd, row-major).
@@ -460,16 +496,20 @@ __global__ void dc_rank_kernel(int64_t k, MergeBufs b) {
     }
 }
 
-__global__ void dc_rank2_kernel(int64_t k, MergeBufs b) {
-    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+// Ascending rank of each merged eigenvalue (ties by index); one warp per value.
+__global__ void __launch_bounds__(32 * kRootWarps) dc_rank2_kernel(int64_t k, MergeBufs b) {
+    const int lane = threadIdx.x & 31;
+    const int64_t p = (int64_t)blockIdx.x * kRootWarps + (threadIdx.x >> 5);
     if (p >= k) return;
     const double vp = b.D[p];
     int r = 0;
-    for (int64_t q = 0; q < k; q++) {
+    for (int64_t q = lane; q < k; q += 32) {
         const double vq = b.D[q];
         r += (vq < vp) || (vq == vp && q < p);
     }
-    b.rank[p] = r;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+    if (lane == 0) b.rank[p] = r;
 }
 
 // Writes the merged eigenvalues w[l + rank] and the block's new columns into F
@@ -654,11 +694,12 @@ int eigh(double* A, int64_t lda, int64_t n, double* w, double* Q, int64_t ldq, v
                 }
             }
             // the non-deflated count is only known on the device: size the grids for k
-            dc_secular_kernel<<<(unsigned)((k + 127) / 128), 128, sh, s>>>(mb, sh ? (int)k : 0);
+            const unsigned root_blocks = (unsigned)((k + kRootWarps - 1) / kRootWarps);
+            dc_secular_kernel<<<root_blocks, 32 * kRootWarps, sh, s>>>(mb, sh ? (int)k : 0);
             CHFSI_LAUNCH_CHECK();
-            dc_lowner_kernel<<<(unsigned)((k + 127) / 128), 128, 0, s>>>(mb);
+            dc_lowner_kernel<<<root_blocks, 32 * kRootWarps, 0, s>>>(mb);
             CHFSI_LAUNCH_CHECK();
-            dc_norm_kernel<<<(unsigned)((k + 127) / 128), 128, 0, s>>>(mb);
+            dc_norm_kernel<<<root_blocks, 32 * kRootWarps, 0, s>>>(mb);
             CHFSI_LAUNCH_CHECK();
             dc_build_u_kernel<<<dim3((unsigned)((k + 255) / 256), (unsigned)k), 256, 0, s>>>(mb);
             CHFSI_LAUNCH_CHECK();
@@ -675,7 +716,7 @@ int eigh(double* A, int64_t lda, int64_t n, double* w, double* Q, int64_t ldq, v
             if (rc) return rc;
             dc_rank_kernel<<<(unsigned)((k + 255) / 256), 256, 0, s>>>(k, mb);
             CHFSI_LAUNCH_CHECK();
-            dc_rank2_kernel<<<(unsigned)((k + 255) / 256), 256, 0, s>>>(k, mb);
+            dc_rank2_kernel<<<root_blocks, 32 * kRootWarps, 0, s>>>(k, mb);
             CHFSI_LAUNCH_CHECK();
             dc_scatter_kernel<<<dim3((unsigned)((k + 255) / 256), (unsigned)k), 256, 0, s>>>(l, k, Q, ldq, w, mb.U,
                                                                                           mb);
