@@ -57,73 +57,127 @@ __device__ double block_sum(double v) {
 
 // ------------------------------------------------------------------ 1. tridiagonalisation
 
-// Reflector of row j (columns j+1 .. n-1 of the symmetric A): H = I - tau v v^T with
-// v_0 = 1 maps x = A[j][j+1:] to beta e_1.  v is kept in A's row j (it is not read
-// again by the reduction) and in vbuf.  One block.
-__global__ void house_kernel(double* A, int64_t lda, int64_t n, int64_t j, double* d, double* e, double* tau,
-                             double* vbuf) {
-    const int64_t m = n - j - 1;
-    double* x = A + j * lda + j + 1;
-    double s = 0.0;
-    for (int64_t i = 1 + threadIdx.x; i < m; i += blockDim.x) s += x[i] * x[i];
-    s = block_sum(s);
-    const double x0 = x[0];
-    double beta, t, scale;
-    if (s == 0.0) {
+// Column j takes two launches.  The product kernel forms the reflector of row j
+// (columns j+1 .. n-1 of the symmetric A): H = I - tau v v^T with v_0 = 1 maps
+// x = A[j][j+1:] to beta e_1, every block recomputing beta, tau and the scale of v
+// from x_0 and sum_{i>=1} x_i^2; it computes p = tau A22 v (A22 = A[j+1:, j+1:], one
+// warp per row) and p . v.  The update kernel applies A22 -= v w^T + w v^T with
+// w = p - (tau/2)(p . v) v, stores v in A's row j (not read again by the reduction),
+// and sums the squares of the next reflector's row, A[j+1][j+3:].  The two sums are
+// reduced in block order by the last block to finish (a completion counter, no
+// waiting), so the results do not depend on the blocks' timing.
+struct TriScalars {
+    double sumsq;            // sum_{i>=1} x_i^2 of the current reflector's row
+    double dot;              // p . v of the current column
+    unsigned cnt_a, cnt_b;   // completion counters of the two kernels
+};
+
+__device__ __forceinline__ void reflector(double x0, double sumsq, double& beta, double& t, double& scale) {
+    if (sumsq == 0.0) {
         beta = x0;
         t = 0.0;
         scale = 0.0;
     } else {
-        const double nrm = sqrt(x0 * x0 + s);
+        const double nrm = sqrt(x0 * x0 + sumsq);
         beta = x0 >= 0.0 ? -nrm : nrm;
         t = (beta - x0) / beta;
         scale = 1.0 / (x0 - beta);
     }
-    __syncthreads();
-    for (int64_t i = threadIdx.x; i < m; i += blockDim.x) {
-        const double vi = i == 0 ? 1.0 : x[i] * scale;
-        vbuf[i] = vi;
-        x[i] = vi;
-    }
-    if (threadIdx.x == 0) {
-        d[j] = A[j * lda + j];
-        e[j] = beta;
-        tau[j] = t;
-    }
 }
 
-// p = tau_j A22 v with A22 = A[j+1:, j+1:]; one warp per row.
-__global__ void symv_kernel(const double* __restrict__ A, int64_t lda, int64_t n, int64_t j,
-                            const double* __restrict__ tau, const double* __restrict__ v, double* p) {
-    const int64_t m = n - j - 1;
-    const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (r >= m) return;
-    const double* row = A + (j + 1 + r) * lda + j + 1;
+// Sum of squares of A[0][2:] (the first reflector's row past its leading entry).  One block.
+__global__ void tri_init_kernel(const double* A, int64_t n, TriScalars* tri) {
     double s = 0.0;
-    for (int64_t i = lane; i < m; i += 32) s = fma(row[i], v[i], s);
-    s = warp_sum(s);
-    if (lane == 0) p[r] = tau[j] * s;
-}
-
-// w = p - (tau_j / 2)(p . v) v, in place in p.  One block.
-__global__ void house_w_kernel(int64_t m, int64_t j, const double* __restrict__ tau, const double* __restrict__ v,
-                               double* p) {
-    double s = 0.0;
-    for (int64_t i = threadIdx.x; i < m; i += blockDim.x) s = fma(p[i], v[i], s);
+    for (int64_t c = 2 + threadIdx.x; c < n; c += blockDim.x) s = fma(A[c], A[c], s);
     s = block_sum(s);
-    const double K = 0.5 * tau[j] * s;
-    for (int64_t i = threadIdx.x; i < m; i += blockDim.x) p[i] -= K * v[i];
+    if (threadIdx.x == 0) {
+        tri->sumsq = s;
+        tri->cnt_a = tri->cnt_b = 0;
+    }
 }
 
-// A22 -= v w^T + w v^T (both triangles).
-__global__ void rank2_kernel(double* A, int64_t lda, int64_t n, int64_t j, const double* __restrict__ v,
-                             const double* __restrict__ w) {
+constexpr int kTriRows = 8;   // rows (one warp each) per block of the product kernel
+
+__global__ void __launch_bounds__(32 * kTriRows) tri_product_kernel(const double* __restrict__ A, int64_t lda,
+                                                                    int64_t n, int64_t j, TriScalars* tri,
+                                                                    double* part, double* d, double* e, double* tau,
+                                                                    double* vbuf, double* pbuf) {
+    const int64_t m = n - j - 1;
+    const double* x = A + j * lda + j + 1;
+    double beta, t, scale;
+    reflector(x[0], tri->sumsq, beta, t, scale);
+    auto v_at = [&](int64_t i) { return i == 0 ? 1.0 : x[i] * scale; };
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t r = (int64_t)blockIdx.x * kTriRows + warp;
+    double pv = 0.0;
+    if (r < m) {
+        const double* row = A + (j + 1 + r) * lda + j + 1;
+        double acc = 0.0;
+        for (int64_t i = lane; i < m; i += 32) acc = fma(row[i], v_at(i), acc);
+        const double pr = t * warp_sum(acc);
+        if (lane == 0) pbuf[r] = pr;
+        pv = pr * v_at(r);
+    }
+    if (blockIdx.x == 0)
+        for (int64_t i = threadIdx.x; i < m; i += blockDim.x) vbuf[i] = v_at(i);
+    __shared__ double wpart[kTriRows];
+    if (lane == 0) wpart[warp] = pv;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double bs = 0.0;
+        for (int w = 0; w < kTriRows; w++) bs += wpart[w];
+        part[blockIdx.x] = bs;
+        __threadfence();
+        if (atomicAdd(&tri->cnt_a, 1u) == gridDim.x - 1) {   // the last block: reduce in block order
+            __threadfence();
+            const volatile double* pp = part;
+            double tot = 0.0;
+            for (unsigned b = 0; b < gridDim.x; b++) tot += pp[b];
+            tri->dot = tot;
+            tri->cnt_a = 0;
+            d[j] = A[j * lda + j];
+            e[j] = beta;
+            tau[j] = t;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) tri_update_kernel(double* A, int64_t lda, int64_t n, int64_t j,
+                                                         TriScalars* tri, double* part,
+                                                         const double* __restrict__ tau,
+                                                         const double* __restrict__ vbuf,
+                                                         const double* __restrict__ pbuf) {
     const int64_t m = n - j - 1;
     const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t r = blockIdx.y;
-    if (c >= m || r >= m) return;
-    A[(j + 1 + r) * lda + j + 1 + c] -= v[r] * w[c] + w[r] * v[c];
+    const double K = 0.5 * tau[j] * tri->dot;
+    double sq = 0.0;
+    if (c < m) {
+        const double vr = vbuf[r], vc = vbuf[c];
+        const double wr = pbuf[r] - K * vr, wc = pbuf[c] - K * vc;
+        double* a = A + (j + 1 + r) * lda + j + 1 + c;
+        const double v = *a - (vr * wc + wr * vc);
+        *a = v;
+        if (r == 0) {
+            if (c >= 2) sq = v * v;            // the next reflector's row past its leading entry
+            A[j * lda + j + 1 + c] = vc;       // v kept in row j for the back-transformation
+        }
+    }
+    if (r == 0) {   // block-uniform: the blocks of the first row sum the next reflector's squares
+        const double bs = block_sum(sq);
+        if (threadIdx.x == 0) {
+            part[blockIdx.x] = bs;
+            __threadfence();
+            if (atomicAdd(&tri->cnt_b, 1u) == gridDim.x - 1) {
+                __threadfence();
+                const volatile double* pp = part;
+                double tot = 0.0;
+                for (unsigned b = 0; b < gridDim.x; b++) tot += pp[b];
+                tri->sumsq = tot;
+                tri->cnt_b = 0;
+            }
+        }
+    }
 }
 
 // The last 2 x 2 (or 1 x 1) block of T.
@@ -580,16 +634,40 @@ __global__ void panel_t_kernel(const double* Gv, const double* tau, int64_t j0, 
 
 inline int64_t round8(int64_t x) { return (x + 7) / 8 * 8; }
 
+// Products of the merges (G U) and of the back-transformation run as Ozaki products on
+// the tensor cores for 256 <= n <= 8192 (the NN form takes inner dimensions up to
+// 8192), otherwise as FP64 products on the DFMA pipe (small n: a few tiles, where the
+// slicing passes would cost more than they save).
+constexpr int64_t kOzakiMinN = 256, kOzakiMaxN = 8192;
+
+struct EighBufs {
+    double *d, *e, *tau, *ebak, *vbuf, *pbuf, *part_a, *part_b;
+    TriScalars* tri;
+    MergeBufs mb;
+    double *Vp, *Gv, *T, *W1, *W2;
+    unsigned char* oz;      // Ozaki product scratch (nullptr for n > kOzakiMaxN)
+    size_t oz_bytes;
+};
+
+size_t eigh_ozaki_bytes(int64_t n) {
+    if (n < kOzakiMinN || n > kOzakiMaxN) return 0;
+    return std::max({ozaki_workspace_bytes(false, n, n, n, false), ozaki_workspace_bytes(false, kPanel, n, n, false),
+                     ozaki_workspace_bytes(true, n, n, kPanel, false)});
+}
+
 template <typename Ar>
-void eigh_layout(Ar& ar, int64_t n, double** d, double** e, double** tau, double** ebak, double** vbuf, double** pbuf,
-                 MergeBufs* mb, double** Vp, double** Gv, double** T, double** W1, double** W2) {
-    *d = ar.template take<double>(n);
-    *e = ar.template take<double>(n);
-    *tau = ar.template take<double>(n);
-    *ebak = ar.template take<double>(n);
-    *vbuf = ar.template take<double>(n);
-    *pbuf = ar.template take<double>(n);
-    MergeBufs b;
+void eigh_layout(Ar& ar, int64_t n, EighBufs* out) {
+    EighBufs u{};
+    u.d = ar.template take<double>(n);
+    u.e = ar.template take<double>(n);
+    u.tau = ar.template take<double>(n);
+    u.ebak = ar.template take<double>(n);
+    u.vbuf = ar.template take<double>(n);
+    u.pbuf = ar.template take<double>(n);
+    u.part_a = ar.template take<double>((size_t)(n / kTriRows + 1));
+    u.part_b = ar.template take<double>((size_t)(n / 256 + 1));
+    u.tri = ar.template take<TriScalars>(1);
+    MergeBufs& b = u.mb;
     b.D = ar.template take<double>(n);
     b.z = ar.template take<double>(n);
     b.Dnd = ar.template take<double>(n);
@@ -612,12 +690,22 @@ void eigh_layout(Ar& ar, int64_t n, double** d, double** e, double** tau, double
     b.G = ar.template take<double>((size_t)n * n);
     b.U = ar.template take<double>((size_t)n * n);
     b.Gn = ar.template take<double>((size_t)n * n);
-    if (mb) *mb = b;
-    *Vp = ar.template take<double>((size_t)kPanel * n);
-    *Gv = ar.template take<double>((size_t)kPanel * kPanel);
-    *T = ar.template take<double>((size_t)kPanel * kPanel);
-    *W1 = ar.template take<double>((size_t)kPanel * n);
-    *W2 = ar.template take<double>((size_t)kPanel * n);
+    u.Vp = ar.template take<double>((size_t)kPanel * n);
+    u.Gv = ar.template take<double>((size_t)kPanel * kPanel);
+    u.T = ar.template take<double>((size_t)kPanel * kPanel);
+    u.W1 = ar.template take<double>((size_t)kPanel * n);
+    u.W2 = ar.template take<double>((size_t)kPanel * n);
+    u.oz_bytes = eigh_ozaki_bytes(n);
+    u.oz = u.oz_bytes ? ar.template take<unsigned char>(u.oz_bytes) : nullptr;
+    if (out) *out = u;
+}
+
+// Z[i][c] -= D[i][c] (rows x cols; Z with leading dimension ldz, D dense).
+__global__ void sub_block_kernel(double* Z, int64_t ldz, const double* __restrict__ D, int64_t rows, int64_t cols) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= rows * cols) return;
+    const int64_t i = idx / cols, c = idx % cols;
+    Z[i * ldz + c] -= D[idx];
 }
 
 struct CountOnly {
@@ -633,38 +721,41 @@ struct CountOnly {
 
 size_t eigh_workspace_bytes(int64_t n) {
     CountOnly ar;
-    double *d, *e, *tau, *ebak, *vb, *pb, *Vp, *Gv, *T, *W1, *W2;
-    eigh_layout(ar, n > 0 ? n : 1, &d, &e, &tau, &ebak, &vb, &pb, nullptr, &Vp, &Gv, &T, &W1, &W2);
+    eigh_layout(ar, n > 0 ? n : 1, nullptr);
     return ar.s.used;
 }
 
 int eigh(double* A, int64_t lda, int64_t n, double* w, double* Q, int64_t ldq, void* ws, size_t ws_bytes,
          unsigned* status, cudaStream_t s) {
-    (void)status;
     if (n <= 0) return CHFSI_OK;
     if (ws_bytes < eigh_workspace_bytes(n)) return CHFSI_ERR_NOMEM;
     Arena ar(ws, ws_bytes);
-    double *d, *e, *tau, *ebak, *vbuf, *pbuf, *Vp, *Gv, *T, *W1, *W2;
-    MergeBufs mb;
-    eigh_layout(ar, n, &d, &e, &tau, &ebak, &vbuf, &pbuf, &mb, &Vp, &Gv, &T, &W1, &W2);
+    EighBufs u;
+    eigh_layout(ar, n, &u);
+    double *d = u.d, *e = u.e, *tau = u.tau, *ebak = u.ebak, *Vp = u.Vp, *Gv = u.Gv, *T = u.T, *W1 = u.W1,
+           *W2 = u.W2;
+    MergeBufs& mb = u.mb;
+    const bool oz = u.oz != nullptr;
 
-    // 1. tridiagonalisation
+    // 1. tridiagonalisation, two launches per column
+    if (n >= 3) {
+        tri_init_kernel<<<1, 1024, 0, s>>>(A, n, u.tri);
+        CHFSI_LAUNCH_CHECK();
+    }
     for (int64_t j = 0; j + 2 < n; j++) {
         const int64_t m = n - j - 1;
-        house_kernel<<<1, 1024, 0, s>>>(A, lda, n, j, d, e, tau, vbuf);
+        tri_product_kernel<<<(unsigned)((m + kTriRows - 1) / kTriRows), 32 * kTriRows, 0, s>>>(
+            A, lda, n, j, u.tri, u.part_a, d, e, tau, u.vbuf, u.pbuf);
         CHFSI_LAUNCH_CHECK();
-        symv_kernel<<<(unsigned)((m * 32 + 255) / 256), 256, 0, s>>>(A, lda, n, j, tau, vbuf, pbuf);
-        CHFSI_LAUNCH_CHECK();
-        house_w_kernel<<<1, 1024, 0, s>>>(m, j, tau, vbuf, pbuf);
-        CHFSI_LAUNCH_CHECK();
-        rank2_kernel<<<dim3((unsigned)((m + 255) / 256), (unsigned)m), 256, 0, s>>>(A, lda, n, j, vbuf, pbuf);
+        tri_update_kernel<<<dim3((unsigned)((m + 255) / 256), (unsigned)m), 256, 0, s>>>(A, lda, n, j, u.tri, u.part_b,
+                                                                                       tau, u.vbuf, u.pbuf);
         CHFSI_LAUNCH_CHECK();
     }
     tridiag_tail_kernel<<<1, 32, 0, s>>>(A, lda, n, d, e, tau);
     CHFSI_LAUNCH_CHECK();
 
     // 2. divide and conquer on (d, e): Q starts as the leaf eigenvectors
-    for (int64_t i = 0; i < n; i++) CHFSI_CUDA_TRY(cudaMemsetAsync(Q + i * ldq, 0, sizeof(double) * (size_t)n, s));
+    CHFSI_CUDA_TRY(cudaMemset2DAsync(Q, sizeof(double) * (size_t)ldq, 0, sizeof(double) * (size_t)n, (size_t)n, s));
     dc_split_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, d, e, ebak);
     CHFSI_LAUNCH_CHECK();
     const int64_t nleaf = (n + kLeaf - 1) / kLeaf;
@@ -712,7 +803,8 @@ int eigh(double* A, int64_t lda, int64_t n, double* w, double* Q, int64_t ldq, v
             CHFSI_CUDA_TRY(cudaMemcpyAsync(&kn_d, mb.par + 2, sizeof(double), cudaMemcpyDeviceToHost, s));
             CHFSI_CUDA_TRY(cudaStreamSynchronize(s));
             const int64_t kn = (int64_t)kn_d;
-            int rc = gemm_general(mb.G, kn, false, mb.U, kn, mb.Gn, kn, k, kn, kn, 1.0, false, s);
+            int rc = oz ? ozaki_gemm_nn(mb.G, kn, mb.U, kn, k, kn, kn, mb.Gn, kn, false, u.oz, u.oz_bytes, status, s)
+                        : gemm_general(mb.G, kn, false, mb.U, kn, mb.Gn, kn, k, kn, kn, 1.0, false, s);
             if (rc) return rc;
             dc_rank_kernel<<<(unsigned)((k + 255) / 256), 256, 0, s>>>(k, mb);
             CHFSI_LAUNCH_CHECK();
@@ -742,9 +834,18 @@ int eigh(double* A, int64_t lda, int64_t n, double* w, double* Q, int64_t ldq, v
         CHFSI_LAUNCH_CHECK();
         double* ZR = Q + (j0 + 1) * ldq;
         int rc;
-        if ((rc = gemm_general(Vp, mr, false, ZR, ldq, W1, n, nb, n, mr, 1.0, false, s))) return rc;
-        if ((rc = gemm_general(T, nb, false, W1, n, W2, n, nb, n, nb, 1.0, false, s))) return rc;
-        if ((rc = gemm_general(Vp, mr, true, W2, n, ZR, ldq, mr, n, nb, -1.0, true, s))) return rc;
+        if (oz) {
+            // W1 = V^T Z, W2 = T W1 (small, DFMA), Z -= V W2 through a product block
+            if ((rc = ozaki_gemm_nn(Vp, mr, ZR, ldq, nb, mr, n, W1, n, false, u.oz, u.oz_bytes, status, s))) return rc;
+            if ((rc = gemm_general(T, nb, false, W1, n, W2, n, nb, n, nb, 1.0, false, s))) return rc;
+            if ((rc = ozaki_gemm_tn(Vp, mr, W2, n, nb, mr, n, mb.G, n, false, u.oz, u.oz_bytes, status, s))) return rc;
+            sub_block_kernel<<<(unsigned)((mr * n + 255) / 256), 256, 0, s>>>(ZR, ldq, mb.G, mr, n);
+            CHFSI_LAUNCH_CHECK();
+        } else {
+            if ((rc = gemm_general(Vp, mr, false, ZR, ldq, W1, n, nb, n, mr, 1.0, false, s))) return rc;
+            if ((rc = gemm_general(T, nb, false, W1, n, W2, n, nb, n, nb, 1.0, false, s))) return rc;
+            if ((rc = gemm_general(Vp, mr, true, W2, n, ZR, ldq, mr, n, nb, -1.0, true, s))) return rc;
+        }
     }
     return CHFSI_OK;
 }
