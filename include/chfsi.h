@@ -138,16 +138,20 @@ typedef struct {
 #define CHFSI_F32X2 3         /* two-float: values as hi + lo FP32 pairs (about 48 bits),
                                  FP32-pipe arithmetic with error-free transformations;
                                  CSR layout (CHFSI_CSR or CHFSI_HYBRID) only            */
-#define CHFSI_F64_OZAKI 4     /* closure products only: FP64 values split into six 8-bit
-                                 slices whose products run on the BF16 tensor cores with
-                                 exact integer accumulation (see chfsi_ozaki_gemm)       */
+#define CHFSI_F64_OZAKI 4     /* FP64-accurate products on the BF16 tensor cores: FP64
+                                 values split into seven 8-bit slices, exact integer
+                                 accumulation (see chfsi_ozaki_gemm).  In the closure
+                                 (chfsi_rayleigh_ritz_ex) its dense products; in a filter
+                                 schedule the FP64 steps of a BSR or hybrid operator, its
+                                 64 x 64 blocks as Ozaki products (rows of at most 128
+                                 blocks), FP64 iterates and recurrence                   */
 
 /*
  * Per-step precision of the filter: step_prec[k-1] is the precision of the step
- * that produces Y_k (k = 1..m).  Low-precision steps must form a prefix; once a
- * step is CHFSI_F64 all later steps must be too (the last steps run in FP64 and
- * the two iterates carried across the switch are widened exactly).
- * A NULL schedule (or step_prec == NULL) means every step in FP64.
+ * that produces Y_k (k = 1..m).  Low-precision steps (CHFSI_F32, CHFSI_BF16_F32ACC,
+ * CHFSI_F32X2, one kind) must form a prefix; the steps after it are all CHFSI_F64 or
+ * all CHFSI_F64_OZAKI (the two iterates carried across the switch are widened
+ * exactly).  A NULL schedule (or step_prec == NULL) means every step in FP64.
  */
 typedef struct {
     int32_t m;
@@ -172,9 +176,11 @@ int chfsi_filter_workspace_size(const chfsi_matrix* H, int64_t n_cols, int32_t m
  * A CSR operator over more than 512 columns is filtered in column slabs of 512
  * (all m steps per slab; the columns are independent), so the workspace holds one
  * slab's iterates.
- * Errors: CHFSI_ERR_ARG, CHFSI_ERR_BOUNDS, CHFSI_ERR_NOMEM, CHFSI_ERR_UNSUPPORTED,
- * CHFSI_ERR_CUDA (launch failure).  Device-side findings (non-finite output,
- * column out of range) go to the workspace status word.
+ * Errors: CHFSI_ERR_ARG, CHFSI_ERR_BOUNDS, CHFSI_ERR_NOMEM, CHFSI_ERR_UNSUPPORTED
+ * (e.g. CHFSI_F64_OZAKI steps without BSR blocks or with a block row of more than
+ * 128 blocks; checking the latter copies the block-row pointers to the host and
+ * synchronises `stream` once), CHFSI_ERR_CUDA (launch failure).  Device-side findings
+ * (non-finite output, column out of range) go to the workspace status word.
  */
 int chfsi_filter(const chfsi_matrix* H, const double* X, int64_t ldx, double* Y, int64_t ldy,
                  int64_t n_cols, int32_t m, double a, double b, double a0,

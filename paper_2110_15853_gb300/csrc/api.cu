@@ -142,24 +142,35 @@ void coefficients(int m, double a, double b, double a0, std::vector<double>& alp
     }
 }
 
-// Low-precision prefix length of a schedule (validated).
-int schedule_prefix(const chfsi_schedule* sched, int m, int* L, int* low_kind) {
+// Low-precision prefix length of a schedule (validated) and the kind of its FP64
+// tail: plain FP64 steps or FP64-accurate Ozaki steps (CHFSI_F64_OZAKI), one kind for
+// the whole tail.
+int schedule_prefix(const chfsi_schedule* sched, int m, int* L, int* low_kind, int* tail_kind) {
     *L = 0;
     *low_kind = CHFSI_F64;
+    *tail_kind = CHFSI_F64;
     if (!sched || !sched->step_prec) return CHFSI_OK;
     if (sched->m != m) return CHFSI_ERR_ARG;
+    auto is_tail = [](int p) { return p == CHFSI_F64 || p == CHFSI_F64_OZAKI; };
     int k = 0;
-    while (k < m && sched->step_prec[k] != CHFSI_F64) {
+    while (k < m && !is_tail(sched->step_prec[k])) {
         int p = sched->step_prec[k];
         if (p != CHFSI_F32 && p != CHFSI_BF16_F32ACC && p != CHFSI_F32X2) return CHFSI_ERR_ARG;
         if (k > 0 && p != *low_kind) return CHFSI_ERR_ARG;
         *low_kind = p;
         k++;
     }
+    if (k < m) *tail_kind = sched->step_prec[k];
     for (int r = k; r < m; r++)
-        if (sched->step_prec[r] != CHFSI_F64) return CHFSI_ERR_ARG;
+        if (sched->step_prec[r] != *tail_kind) return CHFSI_ERR_ARG;
     *L = k;
     return CHFSI_OK;
+}
+
+// Scratch of the Ozaki BSR steps (0 when the schedule has none).
+size_t ozaki_tail_bytes(const chfsi_matrix* H, int64_t n, int m, int L, int tail) {
+    if (tail != CHFSI_F64_OZAKI || L >= m || !has_bsr(H)) return 0;
+    return ozaki_bsr_bytes(H->bsr.n_block_rows, H->bsr.n_blocks, n);
 }
 
 struct FilterLayout {
@@ -171,11 +182,13 @@ struct FilterLayout {
     float* F[3] = {nullptr, nullptr, nullptr};
     __nv_bfloat16* S[2] = {nullptr, nullptr};
     float2* D[3] = {nullptr, nullptr, nullptr};   // two-float iterates
+    unsigned char* oz = nullptr;       // Ozaki BSR steps: slices of H and of Y_cur
+    size_t oz_bytes = 0;
 };
 
 template <typename A>
 void filter_layout(A& ar, int64_t N, int64_t n, int m, int L, int low_kind, int64_t nvals, FilterLayout* out,
-                   int split_block = 0) {
+                   int split_block = 0, size_t oz_bytes = 0) {
     const int64_t ldw = pad8(n);
     FilterLayout fl;
     ar.template take<unsigned char>(kStatusBytes);
@@ -187,6 +200,10 @@ void filter_layout(A& ar, int64_t N, int64_t n, int m, int L, int low_kind, int6
         fl.T = ar.template take<double>((size_t)(N * ldw));
         fl.bd_bytes = ozaki_blockdiag_bytes(N, split_block, n);
         fl.bd = ar.template take<unsigned char>(fl.bd_bytes);
+    }
+    if (oz_bytes) {
+        fl.oz_bytes = oz_bytes;
+        fl.oz = ar.template take<unsigned char>(oz_bytes);
     }
     if (L > 0 && low_kind == CHFSI_F32X2) {
         fl.hlow = ar.template take<float2>((size_t)nvals);
@@ -302,12 +319,14 @@ int chfsi_filter_workspace_size(const chfsi_matrix* H, int64_t n_cols, int32_t m
     int rc = rows_of(H, &N);
     if (rc) return rc;
     if (n_cols < 0 || m < 1) return CHFSI_ERR_ARG;
-    int L = 0, low = 0;
-    rc = schedule_prefix(sched, m, &L, &low);
+    int L = 0, low = 0, tail = 0;
+    rc = schedule_prefix(sched, m, &L, &low, &tail);
     if (rc) return rc;
     if (H->kind == CHFSI_SPLIT && L > 0) return CHFSI_ERR_UNSUPPORTED;
+    if (tail == CHFSI_F64_OZAKI && L < m && !has_bsr(H)) return CHFSI_ERR_UNSUPPORTED;
+    const int64_t slab = filter_slab(H, n_cols);
     SizeOnly sz;
-    filter_layout(sz, N, filter_slab(H, n_cols), m, L, low, low_values(H), nullptr, split_block(H));
+    filter_layout(sz, N, slab, m, L, low, low_values(H), nullptr, split_block(H), ozaki_tail_bytes(H, slab, m, L, tail));
     *bytes = sz.used;
     return CHFSI_OK;
 }
@@ -318,7 +337,7 @@ namespace {
 struct FilterRun {
     const chfsi_matrix* H;
     int64_t N;
-    int m, L, low;
+    int m, L, low, tail;
     const std::vector<double>* al;
     const std::vector<double>* be;
     double c;
@@ -397,6 +416,15 @@ int filter_columns(const FilterRun& R, const double* X, int64_t ldx, double* Y, 
             return convert_block(fl.F[m % 3], Buf::F32, ldw, Y, Buf::F64, ldy, N, n, n, s);
     }
 
+    const bool oz_tail = R.tail == CHFSI_F64_OZAKI;
+    if (oz_tail && L > 0 && L < m && !widened) {
+        // the Ozaki steps read FP64 iterates: widen Y_L and Y_{L-1} (exact)
+        if ((rc = convert_block(fl.F[L % 3], Buf::F32, ldw, f64_buf(L), Buf::F64, f64_ld(L), N, n, n, s))) return rc;
+        if (L >= 2 && (rc = convert_block(fl.F[(L - 1) % 3], Buf::F32, ldw, f64_buf(L - 1), Buf::F64, f64_ld(L - 1), N,
+                                          n, n, s)))
+            return rc;
+        widened = true;
+    }
     for (int k = L + 1; k <= m; k++) {
         StepIO io{};
         // Y_{k-1}
@@ -411,7 +439,12 @@ int filter_columns(const FilterRun& R, const double* X, int64_t ldx, double* Y, 
             else { io.prev = f64_buf(k - 2); io.prev_t = Buf::F64; io.ldp = f64_ld(k - 2); }
         }
         io.out = f64_buf(k); io.out_t = Buf::F64; io.ldo = f64_ld(k);
-        if (H->kind == CHFSI_SPLIT) {
+        if (oz_tail) {
+            // H's blocks as Ozaki products on the tensor cores, FP64 recurrence
+            rc = ozaki_bsr_step(R.bsr64, n, static_cast<const double*>(io.cur), io.ldc,
+                                static_cast<const double*>(io.prev), io.ldp, static_cast<double*>(io.out), io.ldo,
+                                al[k], c, k >= 2 ? be[k] : 0.0, fl.oz, fl.oz_bytes, st, s);
+        } else if (H->kind == CHFSI_SPLIT) {
             // dense diagonal blocks on the tensor cores, then the sparse rest with that sum added
             rc = ozaki_blockdiag_apply(static_cast<const double*>(io.cur), io.ldc, N, H->split.block, n, fl.T, ldw,
                                        fl.bd, fl.bd_bytes, st, s);
@@ -440,15 +473,28 @@ int chfsi_filter(const chfsi_matrix* H, const double* X, int64_t ldx, double* Y,
     if (n_cols == 0) return CHFSI_OK;
     if ((rc = check_block(X, ldx, n_cols)) || (rc = check_block(Y, ldy, n_cols))) return rc;
     if (X == Y) return CHFSI_ERR_ARG;
-    int L = 0, low = 0;
-    if ((rc = schedule_prefix(sched, m, &L, &low))) return rc;
+    int L = 0, low = 0, tail = 0;
+    if ((rc = schedule_prefix(sched, m, &L, &low, &tail))) return rc;
     if (!ws || !aligned16(ws)) return CHFSI_ERR_ARG;
     const int64_t slab = filter_slab(H, n_cols);
     if (H->kind == CHFSI_SPLIT && L > 0) return CHFSI_ERR_UNSUPPORTED;
+    const bool oz_tail = tail == CHFSI_F64_OZAKI && L < m;
+    if (oz_tail && (!has_bsr(H) || H->bsr.bdim != 64)) return CHFSI_ERR_UNSUPPORTED;
+    const size_t oz_bytes = ozaki_tail_bytes(H, slab, m, L, tail);
     SizeOnly sz;
-    filter_layout(sz, N, slab, m, L, low, low_values(H), nullptr, split_block(H));
+    filter_layout(sz, N, slab, m, L, low, low_values(H), nullptr, split_block(H), oz_bytes);
     if (ws_bytes < sz.used) return CHFSI_ERR_NOMEM;
     if (L > 0 && low == CHFSI_F32X2 && !has_csr(H)) return CHFSI_ERR_UNSUPPORTED;
+    if (oz_tail) {
+        // an Ozaki work item holds one block row: at most 128 blocks (8192 columns) per row
+        std::vector<int32_t> bp((size_t)H->bsr.n_block_rows + 1);
+        cudaStream_t s0 = as_stream(stream);
+        CHFSI_CUDA_TRY(cudaMemcpyAsync(bp.data(), H->bsr.brow_ptr, sizeof(int32_t) * bp.size(), cudaMemcpyDeviceToHost,
+                                       s0));
+        CHFSI_CUDA_TRY(cudaStreamSynchronize(s0));
+        for (size_t r = 0; r + 1 < bp.size(); r++)
+            if (bp[r + 1] - bp[r] > 128) return CHFSI_ERR_UNSUPPORTED;
+    }
 
     std::vector<double> al, be;
     FilterRun R{};
@@ -457,16 +503,18 @@ int chfsi_filter(const chfsi_matrix* H, const double* X, int64_t ldx, double* Y,
     R.m = m;
     R.L = L;
     R.low = low;
+    R.tail = tail;
     R.al = &al;
     R.be = &be;
     R.ldw = pad8(slab);
     R.s = as_stream(stream);
     R.st = status_word(ws);
     Arena ar(ws, ws_bytes);
-    filter_layout(ar, N, slab, m, L, low, low_values(H), &R.fl, split_block(H));
+    filter_layout(ar, N, slab, m, L, low, low_values(H), &R.fl, split_block(H), oz_bytes);
     coefficients(m, a, b, a0, al, be, R.c);
     CHFSI_CUDA_TRY(cudaMemsetAsync(R.st, 0, sizeof(unsigned), R.s));
     make_devs(H, H->csr.val, H->bsr.val, Buf::F64, &R.csr64, &R.bsr64);
+    if (oz_tail && (rc = ozaki_bsr_prepare(R.bsr64, slab, R.fl.oz, R.fl.oz_bytes, R.st, R.s))) return rc;
     if (H->kind == CHFSI_SPLIT) {
         // the off-diagonal part through the CSR kernel; the dense blocks sliced once
         const chfsi_csr& o = H->split.off;

@@ -119,17 +119,60 @@ struct OzArgs {
     int64_t a_batch_rows, b_batch_rows;   // operand rows per batch in the slice arrays
     uint64_t wait_ns;         // limit of the waits on the other roles (drains keep kDrainNs)
     unsigned* status;
+    // BSR filter-step mode (bsr != 0): A_hat = Y_cur^T (states x grid points), B_hat = the
+    // 64 x 64 blocks of H stacked by rows; a work item is one block row (the 64 output
+    // columns, grid rows R * 64 ..) against one tile of 128 states, its K the block
+    // columns of the row, and the epilogue applies the recurrence
+    // Y_out = alpha (H Y_cur - c Y_cur) - beta Y_prev in FP64 (output in C, ldc).
+    int bsr;
+    const int32_t* brow_ptr;
+    const int32_t* bcol;
+    int64_t nbr, nblocks;
+    const int* expH;          // exponent field of each grid row of H (over its block row)
+    const double* Ycur;
+    int64_t ldcur;
+    const double* Yprev;      // nullptr: no beta term
+    int64_t ldprev;
+    double alpha, cshift, beta;
 };
 
 struct Item {
     int batch, tm, tn, kb0, KB;
+    int qb;                   // BSR mode: first block of the row
 };
+
+// Stored block range of block row R, clamped to [0, nblocks] and to kMaxItemKB / 2
+// blocks (the host rejects longer rows); `bad` is set for a malformed row pointer.
+__device__ __forceinline__ void bsr_row_range(const OzArgs& g, int64_t R, int& qb, int& nq, bool& bad) {
+    int b0 = g.brow_ptr[R], b1 = g.brow_ptr[R + 1];
+    if (b0 < 0) { b0 = 0; bad = true; }
+    if (b1 > g.nblocks) { b1 = (int)g.nblocks; bad = true; }
+    if (b1 < b0) { b1 = b0; bad = true; }
+    if (b1 - b0 > kMaxItemKB / 2) { b1 = b0 + kMaxItemKB / 2; bad = true; }
+    qb = b0;
+    nq = b1 - b0;
+}
 
 // First column tile of row tile tm that reaches the upper triangle (j >= i).
 __device__ __host__ __forceinline__ int first_upper_tn(int tm) { return (tm * kTileM) / kTileN; }
 
 __device__ __forceinline__ Item decode(const OzArgs& g, int64_t item) {
     Item it;
+    if (g.bsr) {
+        // the state tiles of a block row are consecutive, so its H slices are shared
+        // through L2
+        const int64_t R = item / g.tilesM;
+        bool bad = false;
+        int nq;
+        bsr_row_range(g, R, it.qb, nq, bad);
+        it.batch = 0;
+        it.tm = (int)(item % g.tilesM);
+        it.tn = (int)R;
+        it.kb0 = 0;
+        it.KB = 2 * nq;
+        return it;
+    }
+    it.qb = 0;
     const int64_t per_split = g.pairs * g.nbatch;
     const int z = (int)(item / per_split);
     it.batch = (int)((item % per_split) / g.pairs);
@@ -196,6 +239,7 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     __shared__ int abort_flag;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    bool nonfinite = false, bad_pattern = false;
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; s++) {
             mbar_init(&full[s], 1);
@@ -224,23 +268,36 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         int64_t sc = 0;
         for (int64_t item = blockIdx.x; item < total && !*abort_v; item += gridDim.x) {
             const Item it = decode(g, item);
+            if (g.bsr) {
+                int qb, nq;
+                bsr_row_range(g, it.tn, qb, nq, bad_pattern);
+            }
             bool ok = true;
             for (int kb = 0; kb < it.KB; kb++, sc++) {
                 const int s = (int)(sc % kStages);
                 const int64_t u = sc / kStages;
                 if (u >= 1 && !mbar_wait(sa(&empty[s]), (uint32_t)((u - 1) & 1), g.wait_ns)) { ok = false; break; }
                 const uint32_t st = sa(smem + (size_t)s * kStageBytes);
-                const int x = (it.kb0 + kb) * kKB;
+                // K offset in A_hat and in B_hat, and B_hat's first row
+                int xa = (it.kb0 + kb) * kKB, xb = xa;
+                int64_t rb = it.batch * g.b_batch_rows + (int64_t)it.tn * kTileN;
+                if (g.bsr) {
+                    const int q = it.qb + kb / 2, half = kb & 1;
+                    int C = g.bcol[q];
+                    if (C < 0 || (int64_t)C >= g.nbr) { C = 0; bad_pattern = true; }   // still a valid tile
+                    xa = C * 64 + half * kKB;
+                    xb = half * kKB;
+                    rb = (int64_t)q * 64;
+                }
                 mbar_expect_tx(&full[s], kStageBytes);
 #pragma unroll
                 for (int t = 0; t < kSlices; t++)
-                    tma_load_2d(st + t * kSliceA, &tmA, x,
+                    tma_load_2d(st + t * kSliceA, &tmA, xa,
                                 (int)(t * g.rowsA_pad + it.batch * g.a_batch_rows + (int64_t)it.tm * kTileM),
                                 sa(&full[s]));
 #pragma unroll
                 for (int t = 0; t < kSlices; t++)
-                    tma_load_2d(st + kSlices * kSliceA + t * kSliceB, &tmB, x,
-                                (int)(t * g.rowsB_pad + it.batch * g.b_batch_rows + (int64_t)it.tn * kTileN),
+                    tma_load_2d(st + kSlices * kSliceA + t * kSliceB, &tmB, xb, (int)(t * g.rowsB_pad + rb),
                                 sa(&full[s]));
             }
             if (!ok) { *abort_v = 1; break; }
@@ -332,10 +389,33 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         const uint32_t lane_base = (uint32_t)(32 * q) << 16;
         int64_t ev = 0;
         long long hi[kColsPerThread], lo[kColsPerThread];
+        // BSR mode: Y_out at grid rows col0 + c of state `row` from the product D of
+        // the tile (zero for an empty block row)
+        auto bsr_out = [&](const Item& it, bool have) {
+            const int64_t j = (int64_t)it.tm * kTileM + 32 * q + lane;      // state
+            if (j >= g.M) return;
+            const int64_t i0 = (int64_t)it.tn * kTileN + h * kColsPerThread;   // first grid row
+            const int ea = have ? g.expA[j] : 0;
+#pragma unroll
+            for (int c = 0; c < kColsPerThread; c++) {
+                const int64_t i = i0 + c;
+                const int eb = have ? g.expH[i] : 0;
+                const double D = (ea != 0 && eb != 0) ? combine(hi[c], lo[c], (ea - 1021) + (eb - 1021)) : 0.0;
+                double y = g.alpha * fma(-g.cshift, g.Ycur[i * g.ldcur + j], D);
+                if (g.Yprev) y = fma(-g.beta, g.Yprev[i * g.ldprev + j], y);
+                nonfinite |= !isfinite(y);
+                g.C[i * g.ldc + j] = y;
+            }
+        };
         for (int64_t item = blockIdx.x; item < total; item += gridDim.x) {
             const Item it = decode(g, item);
 #pragma unroll
             for (int c = 0; c < kColsPerThread; c++) hi[c] = lo[c] = 0;
+            if (g.bsr && it.KB == 0) {   // empty block row: no MMA, no drain
+                if (*abort_v) break;
+                bsr_out(it, false);
+                continue;
+            }
             bool ok = true;
             for (int kb = 0; kb < it.KB; kb++) {
                 const int kind = event_at(kb, it.KB);
@@ -366,7 +446,9 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&eempty);
                 ev++;
-                if (kind == kFullEvent) {
+                if (kind == kFullEvent && g.bsr) {
+                    bsr_out(it, true);
+                } else if (kind == kFullEvent) {
                     const int64_t row = (int64_t)it.tm * kTileM + 32 * q + lane;        // within the batch
                     const int64_t orow = it.batch * g.m_batch + row;                     // output row
                     const int64_t col0 = (int64_t)it.tn * kTileN + h * kColsPerThread;
@@ -403,6 +485,8 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(kTmemCols));
     }
     if (threadIdx.x == 0 && abort_flag) raise_status(g.status, DEV_TIMEOUT);
+    if (nonfinite) raise_status(g.status, DEV_NONFINITE);
+    if (bad_pattern) raise_status(g.status, DEV_PATTERN);
 }
 
 // Largest biased exponent field of each row of A_hat (A_hat[r][k] = src[k * ld + r]
@@ -629,6 +713,24 @@ void oz_layout(Ar& ar, bool tn_form, int64_t M, int64_t Nc, int64_t K, bool same
     if (plan) *plan = p;
 }
 
+// One persistent CTA per SM (or per work item, if fewer).
+int launch_oz(const CUtensorMap& tmA, const CUtensorMap& tmB, const OzArgs& g, int64_t total, cudaStream_t s) {
+    if (total <= 0) return CHFSI_OK;
+    const int dev = current_device();
+    if (dev < 0) return CHFSI_ERR_CUDA;
+    static bool attr[kMaxDevices] = {};
+    if (!attr[dev]) {
+        CHFSI_CUDA_TRY(cudaFuncSetAttribute(oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
+        attr[dev] = true;
+    }
+    const int sms = sm_count();
+    if (sms <= 0) return CHFSI_ERR_CUDA;
+    const unsigned grid = (unsigned)(total < sms ? total : sms);
+    oz_gemm_kernel<<<grid, kThreads, kSmemBytes, s>>>(tmA, tmB, g, total);
+    CHFSI_LAUNCH_CHECK();
+    return CHFSI_OK;
+}
+
 // The product of prepared operands.  nbatch > 1: independent products, batch b of the
 // output at rows b * m_batch (m_batch rows each, the last one clipped at M).
 int oz_run(const OzPlan& p, bool tn_form, double* C, int64_t ldc, int64_t M, int64_t Nc, bool symmetric,
@@ -687,18 +789,7 @@ int oz_run(const OzPlan& p, bool tn_form, double* C, int64_t ldc, int64_t M, int
     }
     g.pairs = pairs;
     const int64_t total = pairs * g.splits * nbatch;
-    const int dev = current_device();
-    if (dev < 0) return CHFSI_ERR_CUDA;
-    static bool attr[kMaxDevices] = {};
-    if (!attr[dev]) {
-        CHFSI_CUDA_TRY(cudaFuncSetAttribute(oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
-        attr[dev] = true;
-    }
-    const int sms = sm_count();
-    if (sms <= 0) return CHFSI_ERR_CUDA;
-    const unsigned grid = (unsigned)(total < sms ? total : sms);
-    oz_gemm_kernel<<<grid, kThreads, kSmemBytes, s>>>(tmA, tmB, g, total);
-    CHFSI_LAUNCH_CHECK();
+    if ((rc = launch_oz(tmA, tmB, g, total, s))) return rc;
     if (tn_form) {
         const int64_t cnt = M * Nc;
         oz_reduce_kernel<<<(unsigned)((cnt + 255) / 256), 256, 0, s>>>(p.part, g.splits, g.Mp, g.Np, M, Nc, C, ldc,
@@ -723,7 +814,130 @@ void oz_blockdiag_layout(Ar& ar, int64_t N, int B, int64_t n, OzBlockDiag* out) 
     if (out) *out = b;
 }
 
+// BSR filter step: slices of H's blocks (made once per filter call; rows = the 64
+// rows of every stored block, K = the block's 64 columns, each row scaled by the
+// largest exponent of its grid row over the whole block row, so that the products of
+// all block columns share one scale) and of Y_cur^T (made per step; rows = states,
+// K = grid points).
+struct OzBsr {
+    OzOperand H, Y;
+    int* expH = nullptr;      // per grid row
+};
+
+template <typename Ar>
+void oz_bsr_layout(Ar& ar, int64_t nbr, int64_t nblocks, int64_t n, OzBsr* out) {
+    OzBsr b;
+    // at least one tile of rows, so that the tensor map is valid without stored blocks
+    oz_operand_layout(ar, (nblocks > 2 ? nblocks : 2) * 64, 64, 1, kRowPad, &b.H);
+    oz_operand_layout(ar, n, nbr * 64, 1, kRowPad, &b.Y);
+    b.expH = ar.template take<int>((size_t)(nbr * 64));
+    if (out) *out = b;
+}
+
+// Largest exponent field of each grid row of H over its block row: thread r of block R
+// scans row r of every block of the row; the result goes to expH[R * 64 + r] and to
+// the slice exponent of that row in each of the row's blocks.
+__global__ void bsr_row_exponents_kernel(const double* __restrict__ val, const int32_t* __restrict__ brow_ptr,
+                                         int64_t nblocks, int* expH, int* exps, unsigned* status) {
+    const int64_t R = blockIdx.x;
+    const int r = threadIdx.x;
+    int b0 = brow_ptr[R], b1 = brow_ptr[R + 1];
+    b0 = b0 < 0 ? 0 : (b0 > nblocks ? (int)nblocks : b0);
+    b1 = b1 < b0 ? b0 : (b1 > nblocks ? (int)nblocks : b1);
+    int m = 0;
+    bool bad = false;
+    for (int q = b0; q < b1; q++) {
+        const double* row = val + ((int64_t)q * 64 + r) * 64;
+        for (int k = 0; k < 64; k++) {
+            const int ef = (int)((__double_as_longlong(row[k]) >> 52) & 0x7ff);
+            bad |= ef == 0x7ff;
+            m = ef > m ? ef : m;
+        }
+    }
+    expH[R * 64 + r] = m;
+    for (int q = b0; q < b1; q++) exps[(int64_t)q * 64 + r] = m;
+    if (bad) raise_status(status, DEV_NONFINITE);
+}
+
 }  // namespace
+
+size_t ozaki_bsr_bytes(int64_t nbr, int64_t nblocks, int64_t n) {
+    CountAr ar;
+    oz_bsr_layout(ar, nbr, nblocks, n, nullptr);
+    return ar.s.used;
+}
+
+int ozaki_bsr_prepare(const BsrDev& h, int64_t n, void* ws, size_t ws_bytes, unsigned* status, cudaStream_t s) {
+    if (h.bdim != 64 || h.nbr <= 0) return CHFSI_ERR_UNSUPPORTED;
+    if (ws_bytes < ozaki_bsr_bytes(h.nbr, h.nblocks, n)) return CHFSI_ERR_NOMEM;
+    Arena ar(ws, ws_bytes);
+    OzBsr b;
+    oz_bsr_layout(ar, h.nbr, h.nblocks, n, &b);
+    if (b.H.plane_rows() * kSlices > INT32_MAX || b.Y.plane_rows() * kSlices > INT32_MAX) return CHFSI_ERR_UNSUPPORTED;
+    const double* val = static_cast<const double*>(h.val);
+    CHFSI_CUDA_TRY(cudaMemsetAsync(b.H.exps, 0, sizeof(int) * (size_t)b.H.plane_rows(), s));
+    bsr_row_exponents_kernel<<<(unsigned)h.nbr, 64, 0, s>>>(val, h.brow_ptr, h.nblocks, b.expH, b.H.exps, status);
+    CHFSI_LAUNCH_CHECK();
+    dim3 grid((unsigned)(b.H.K_pad / 32), (unsigned)(b.H.rows_pad / 32), 1);
+    oz_slice_kernel<false><<<grid, dim3(32, 8), 0, s>>>(val, 64, h.nblocks * 64, 64, 64, 0, b.H.exps, b.H.rows_pad,
+                                                       b.H.K_pad, (size_t)b.H.plane_rows() * b.H.K_pad, b.H.slices);
+    CHFSI_LAUNCH_CHECK();
+    return CHFSI_OK;
+}
+
+int ozaki_bsr_step(const BsrDev& h, int64_t n, const double* Yc, int64_t ldc, const double* Yp, int64_t ldp,
+                   double* Yo, int64_t ldo, double alpha, double c, double beta, void* ws, size_t ws_bytes,
+                   unsigned* status, cudaStream_t s) {
+    if (n <= 0 || h.nbr <= 0) return CHFSI_OK;
+    if (ws_bytes < ozaki_bsr_bytes(h.nbr, h.nblocks, n)) return CHFSI_ERR_NOMEM;
+    Arena ar(ws, ws_bytes);
+    OzBsr b;
+    oz_bsr_layout(ar, h.nbr, h.nblocks, n, &b);
+    const int64_t N = h.nbr * 64;
+    int rc;
+    if ((rc = oz_prepare(Yc, ldc, true, b.Y, N, 0, status, s))) return rc;
+    CUtensorMap tmA, tmB;
+    if ((rc = make_map_bf16(&tmA, b.Y.slices, b.Y.K_pad, kSlices * b.Y.plane_rows(), kKB, kTileM,
+                            CU_TENSOR_MAP_SWIZZLE_64B)))
+        return rc;
+    if ((rc = make_map_bf16(&tmB, b.H.slices, b.H.K_pad, kSlices * b.H.plane_rows(), kKB, kTileN,
+                            CU_TENSOR_MAP_SWIZZLE_64B)))
+        return rc;
+    OzArgs g{};
+    g.M = n;
+    g.Nc = N;
+    g.ldc = ldo;
+    g.C = Yo;
+    g.nbatch = 1;
+    g.m_batch = n;
+    g.a_batch_rows = b.Y.rows_pad;
+    g.tilesM = (int)((n + kTileM - 1) / kTileM);
+    g.tilesN = (int)h.nbr;
+    g.expA = b.Y.exps;
+    g.expB = b.H.exps;
+    g.rowsA_pad = b.Y.plane_rows();
+    g.rowsB_pad = b.H.plane_rows();
+    g.kb_total = kMaxItemKB;
+    g.kb_split = kMaxItemKB;
+    g.splits = 1;
+    g.pairs = (int64_t)g.tilesM * h.nbr;
+    g.wait_ns = pipeline_wait_ns();
+    g.status = status;
+    g.bsr = 1;
+    g.brow_ptr = h.brow_ptr;
+    g.bcol = h.bcol;
+    g.nbr = h.nbr;
+    g.nblocks = h.nblocks;
+    g.expH = b.expH;
+    g.Ycur = Yc;
+    g.ldcur = ldc;
+    g.Yprev = Yp;
+    g.ldprev = ldp;
+    g.alpha = alpha;
+    g.cshift = c;
+    g.beta = beta;
+    return launch_oz(tmA, tmB, g, g.pairs, s);
+}
 
 size_t ozaki_workspace_bytes(bool tn_form, int64_t M, int64_t Nc, int64_t K, bool same) {
     CountAr ar;

@@ -72,6 +72,17 @@ struct TriScalars {
     unsigned cnt_a, cnt_b;   // completion counters of the two kernels
 };
 
+// Sum of the nparts partial sums written by the other blocks (called by the whole block
+// that finished last): strided per thread, then the block reduction, so the order of
+// the additions is fixed.
+__device__ double last_block_sum(const double* part, unsigned nparts) {
+    __threadfence();
+    const volatile double* pp = part;
+    double t = 0.0;
+    for (unsigned b = threadIdx.x; b < nparts; b += blockDim.x) t += pp[b];
+    return block_sum(t);
+}
+
 __device__ __forceinline__ void reflector(double x0, double sumsq, double& beta, double& t, double& scale) {
     if (sumsq == 0.0) {
         beta = x0;
@@ -121,6 +132,7 @@ __global__ void __launch_bounds__(32 * kTriRows) tri_product_kernel(const double
     if (blockIdx.x == 0)
         for (int64_t i = threadIdx.x; i < m; i += blockDim.x) vbuf[i] = v_at(i);
     __shared__ double wpart[kTriRows];
+    __shared__ bool last;
     if (lane == 0) wpart[warp] = pv;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -128,11 +140,12 @@ __global__ void __launch_bounds__(32 * kTriRows) tri_product_kernel(const double
         for (int w = 0; w < kTriRows; w++) bs += wpart[w];
         part[blockIdx.x] = bs;
         __threadfence();
-        if (atomicAdd(&tri->cnt_a, 1u) == gridDim.x - 1) {   // the last block: reduce in block order
-            __threadfence();
-            const volatile double* pp = part;
-            double tot = 0.0;
-            for (unsigned b = 0; b < gridDim.x; b++) tot += pp[b];
+        last = atomicAdd(&tri->cnt_a, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (last) {   // the last block to finish reduces the partial sums (fixed order)
+        const double tot = last_block_sum(part, gridDim.x);
+        if (threadIdx.x == 0) {
             tri->dot = tot;
             tri->cnt_a = 0;
             d[j] = A[j * lda + j];
@@ -164,15 +177,17 @@ __global__ void __launch_bounds__(256) tri_update_kernel(double* A, int64_t lda,
         }
     }
     if (r == 0) {   // block-uniform: the blocks of the first row sum the next reflector's squares
+        __shared__ bool last;
         const double bs = block_sum(sq);
         if (threadIdx.x == 0) {
             part[blockIdx.x] = bs;
             __threadfence();
-            if (atomicAdd(&tri->cnt_b, 1u) == gridDim.x - 1) {
-                __threadfence();
-                const volatile double* pp = part;
-                double tot = 0.0;
-                for (unsigned b = 0; b < gridDim.x; b++) tot += pp[b];
+            last = atomicAdd(&tri->cnt_b, 1u) == gridDim.x - 1;
+        }
+        __syncthreads();
+        if (last) {
+            const double tot = last_block_sum(part, gridDim.x);
+            if (threadIdx.x == 0) {
                 tri->sumsq = tot;
                 tri->cnt_b = 0;
             }

@@ -151,6 +151,15 @@ int ozaki_gemm_nn(const double* A, int64_t lda, const double* B, int64_t ldb, in
 // for every diagonal block k (B x B, row-major, stacked; B a multiple of 128, at most
 // 8192).  ozaki_blockdiag_prepare slices the blocks once; ozaki_blockdiag_apply slices
 // Y and runs the batched product.  Both use the same workspace (ozaki_blockdiag_bytes).
+// FP64-accurate BSR filter step with H's 64 x 64 blocks as Ozaki products on the tensor
+// cores: Y_out = alpha (H Y_cur - c Y_cur) - beta Y_prev (Y_prev may be null), FP64
+// iterates.  ozaki_bsr_prepare slices H once (rows of at most 128 blocks);
+// ozaki_bsr_step slices Y_cur and runs the step.  Both use one workspace (ozaki_bsr_bytes).
+size_t ozaki_bsr_bytes(int64_t nbr, int64_t nblocks, int64_t n);
+int ozaki_bsr_prepare(const BsrDev& h, int64_t n, void* ws, size_t ws_bytes, unsigned* status, cudaStream_t s);
+int ozaki_bsr_step(const BsrDev& h, int64_t n, const double* Yc, int64_t ldc, const double* Yp, int64_t ldp,
+                   double* Yo, int64_t ldo, double alpha, double c, double beta, void* ws, size_t ws_bytes,
+                   unsigned* status, cudaStream_t s);
 size_t ozaki_blockdiag_bytes(int64_t N, int B, int64_t n);
 int ozaki_blockdiag_prepare(const double* diag, int64_t N, int B, int64_t n, void* ws, size_t ws_bytes,
                             unsigned* status, cudaStream_t s);

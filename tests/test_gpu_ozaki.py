@@ -12,6 +12,9 @@ CHFSI_F64_OZAKI), against plain FP64 products and the oracle.
   K 2^-50 max|A_row| max|B_row| and at 1e-13 relative Frobenius.
 * The Ozaki closure's Ritz values against the oracle's Householder/LAPACK closure
   at 1e-10 (small case and the 40^3 / 1024-state workload).
+* FP64-accurate BSR filter steps (H's 64 x 64 blocks as Ozaki products) against the
+  FP64 oracle at 1e-12, with empty block rows, unsorted block columns and after
+  low-precision prefixes on a hybrid operator.
 """
 import numpy as np
 import pytest
@@ -180,3 +183,116 @@ def test_rayleigh_ritz_ozaki_config_40cube(P, oracle_mod):
     assert np.max(np.abs(ritz.cpu().numpy() - theta)) <= 1e-10 * np.max(np.abs(theta))
     p = psi.cpu().numpy()
     assert np.max(np.abs(p.T @ p - np.eye(wl.n))) <= 1e-12
+
+
+# ------------------------------------------------------------------ BSR filter steps
+
+
+def _bsr_dev(P, B):
+    return P.BsrMatrix.from_arrays(B["brow_ptr"], B["bcol"], B["val"], device="cuda")
+
+
+def _unpermute(Yb, perm):
+    Y = np.empty_like(Yb)
+    Y[perm] = Yb
+    return Y
+
+
+@pytest.mark.parametrize("g,w,n,m", [(8, 2, 64, 5), (8, 3, 200, 9), (12, 4, 130, 6), (4, 1, 5, 3), (16, 3, 300, 4),
+                                     (8, 2, 1, 2)])
+def test_bsr_ozaki_filter_is_fp64_accurate(P, oracle_mod, g, w, n, m):
+    """FP64-accurate filter steps with H's 64 x 64 blocks as Ozaki products on the
+    tensor cores (schedule CHFSI_F64_OZAKI) against the FP64 oracle at the FP64
+    tolerance: one or more spans of 128 states with ragged tails, block rows of 8 to 27
+    blocks, m = 2 .. 9."""
+    H = W.csr_grid(g, w, 0.1, 300 + g + n)
+    X = W.start_block(H["N"], n, 301 + g)
+    a, b, a0 = oracle_mod.lanczos_bounds(H, W.lanczos_start(H["N"], 302), 20, max(1, min(n, H["N"] // 4)))
+    B = W.bsr_from_csr(H, g)
+    ws = P.Workspace("cuda")
+    Yb = P.filter(_bsr_dev(P, B), _dev(X[B["perm"]]), m, a, b, a0, schedule=["ozaki"] * m, workspace=ws)
+    assert P.read_status(ws) == 0
+    Y = _unpermute(Yb.cpu().numpy(), B["perm"])
+    assert rel_fro(Y, oracle_mod.filter(H, X, m, a, b, a0)) <= 1e-12
+
+
+def _bsr_to_csr(B):
+    """CSR of the blocked operator (rows and columns in blocked order), stored entries only."""
+    nbr, bd = B["n_block_rows"], B["bdim"]
+    N = nbr * bd
+    A = np.zeros((N, N))
+    vals = B["val"].reshape(-1, bd, bd)
+    for R in range(nbr):
+        for q in range(B["brow_ptr"][R], B["brow_ptr"][R + 1]):
+            C = B["bcol"][q]
+            A[R * bd:(R + 1) * bd, C * bd:(C + 1) * bd] += vals[q]
+    return dense_to_csr(A, keep_zeros=False)
+
+
+def test_bsr_ozaki_filter_empty_block_rows_and_unsorted_blocks(P, oracle_mod):
+    """Block rows without stored blocks (the recurrence's -c Y_cur and beta terms only)
+    and block columns in unsorted order, against the oracle on the same blocked operator."""
+    H = W.csr_grid(8, 2, 0.1, 41)
+    B = W.bsr_from_csr(H, 8)
+    bp, bc, val = B["brow_ptr"].astype(np.int64), B["bcol"].copy(), B["val"].reshape(-1, 64, 64).copy()
+    keep = np.ones(B["n_blocks"], dtype=bool)
+    for R in (2, 5):                                    # empty these block rows
+        keep[bp[R]:bp[R + 1]] = False
+    new_bc, new_val, new_bp = [], [], [0]
+    rng = np.random.default_rng(3)
+    for R in range(B["n_block_rows"]):
+        qs = [q for q in range(bp[R], bp[R + 1]) if keep[q]]
+        rng.shuffle(qs)                                 # unsorted block columns
+        new_bc += [bc[q] for q in qs]
+        new_val += [val[q] for q in qs]
+        new_bp.append(new_bp[-1] + len(qs))
+    B2 = dict(n_block_rows=B["n_block_rows"], bdim=64, brow_ptr=np.array(new_bp, dtype=np.int32),
+              bcol=np.array(new_bc, dtype=np.int32), val=np.concatenate([v.ravel() for v in new_val]),
+              n_blocks=len(new_bc))
+    Hb = _bsr_to_csr(B2)
+    n, m = 70, 6
+    X = W.start_block(Hb["N"], n, 42)
+    a, b, a0 = 4.0, 12.0, 2.0
+    ws = P.Workspace("cuda")
+    Y = P.filter(_bsr_dev(P, B2), _dev(X), m, a, b, a0, schedule=["ozaki"] * m, workspace=ws).cpu().numpy()
+    assert P.read_status(ws) == 0
+    assert rel_fro(Y, oracle_mod.filter(Hb, X, m, a, b, a0)) <= 1e-12
+
+
+@pytest.mark.parametrize("low,L,tol", [("bf16", 5, 5e-2), ("f32", 5, 2e-5), ("f32x2", 6, 1e-12)])
+def test_hybrid_low_prefix_then_ozaki_tail(P, oracle_mod, low, L, tol):
+    """A low-precision prefix (BF16 on the tensor cores, FP32, or two-float on the CSR)
+    widened into FP64, then Ozaki steps on the blocks of the same hybrid operator."""
+    g, w, n, m = 8, 3, 96, 9
+    H = W.csr_grid(g, w, 0.1, 55)
+    X = W.start_block(H["N"], n, 56)
+    a, b, a0 = oracle_mod.lanczos_bounds(H, W.lanczos_start(H["N"], 57), 20, n)
+    B = W.bsr_from_csr(H, g)
+    perm = B["perm"]
+    Hy = P.HybridMatrix(P.CsrMatrix.from_arrays(**{k: v for k, v in W.permute_csr(H, perm).items()
+                                                    if k in ("row_ptr", "col", "val")}, device="cuda"),
+                        _bsr_dev(P, B))
+    sched = [low] * L + ["ozaki"] * (m - L)
+    Y = _unpermute(P.filter(Hy, _dev(X[perm]), m, a, b, a0, schedule=sched).cpu().numpy(), perm)
+    assert rel_fro(Y, oracle_mod.filter(H, X, m, a, b, a0)) <= tol
+
+
+def test_bsr_ozaki_rejects_long_rows_and_csr(P):
+    """Block rows of more than 128 blocks (K beyond the exact 64-bit accumulation of one
+    work item) and operators without blocks are rejected before any launch."""
+    from paper_2110_15853_gb300 import _abi
+    nbr = 130
+    bp = np.array([0, 130] + [130 + r for r in range(1, nbr)], dtype=np.int32)
+    bc = np.concatenate([np.arange(130), np.arange(1, nbr)]).astype(np.int32)
+    val = np.zeros(len(bc) * 4096)
+    Bd = P.BsrMatrix.from_arrays(bp, bc, val, device="cuda")
+    X = torch.zeros(nbr * 64, 8, dtype=torch.float64, device="cuda")
+    with pytest.raises(P.ChfsiError) as e:
+        P.filter(Bd, X, 2, 4.0, 12.0, 2.0, schedule=["ozaki"] * 2)
+    assert e.value.code == _abi.CHFSI_ERR_UNSUPPORTED
+    H = W.csr_grid(4, 1, 0.1, 3)
+    Hd = P.CsrMatrix.from_arrays(H["row_ptr"], H["col"], H["val"], device="cuda")
+    with pytest.raises(P.ChfsiError) as e:
+        P.filter(Hd, torch.zeros(H["N"], 4, dtype=torch.float64, device="cuda"), 2, 4.0, 12.0, 2.0,
+                 schedule=["ozaki"] * 2)
+    assert e.value.code == _abi.CHFSI_ERR_UNSUPPORTED
