@@ -499,6 +499,11 @@ def run_ours(args):
         if not args.no_variants and rank == 0:
             line["mixed_precision"] = mixed_variants(P, torch, dev, stream, wl, Hd, Xd, v0d, Ym, theta_ref,
                                                      (a, b, a0), line)
+            try:
+                line["mixed_precision"]["whole_step_ozaki_bsr_filter_ozaki_closure"] = ozaki_whole_step(
+                    P, torch, dev, stream, wl, H, Xd, Ym, theta_ref, (a, b, a0), line)
+            except Exception as e:  # noqa: BLE001 - report, do not hide
+                line["mixed_precision"]["ozaki_bsr_error"] = repr(e)
         del Ym
     if not args.no_variants and not args.no_secondary and not args.quick and rank == 0:
         line["secondary"] = secondary_variants(P, torch, dev, stream)
@@ -600,6 +605,59 @@ def mixed_variants(P, torch, dev, stream, wl, Hd, Xd, v0d, Yref, theta_ref, boun
             out["schedules"][key] = {"error": repr(e)}
     del Y, ws, wsr
     return out
+
+
+def ozaki_whole_step(P, torch, dev, stream, wl, H, Xd, Yref, theta_ref, bounds, line):
+    """The whole step FP64-accurate on the tensor cores: the filter with H's 64 x 64
+    blocks (4 x 4 x 4 sub-cubes) as Ozaki products, then the Ozaki closure, in the
+    blocked row order (X permuted on the device; the layout conversion on the host is
+    not timed).  Lanczos as in the FP64 step."""
+    a, b, a0 = bounds
+    N, n, m = H["N"], wl.n, wl.m
+    t0 = time.time()
+    B = W.bsr_from_csr(H, wl.g)
+    Hp = W.permute_csr(H, B["perm"])
+    host_s = time.time() - t0
+    perm = torch.as_tensor(B["perm"]).to(dev)
+    Bd = P.BsrMatrix.from_arrays(B["brow_ptr"], B["bcol"], B["val"], device=dev)
+    Hy = P.HybridMatrix(P.CsrMatrix.from_arrays(Hp["row_ptr"], Hp["col"], Hp["val"], device=dev), Bd)
+    nblocks = B["n_blocks"]
+    del B, Hp
+    Xp = Xd[perm].contiguous()
+    Yp = torch.empty_like(Xp)
+    sched = ["ozaki"] * m
+    ws = P.Workspace(dev)
+    ws.get(P.filter_workspace_bytes(Bd, n, m, sched))
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    P.filter(Bd, Xp[:, :8], 2, a, b, a0, schedule=["ozaki"] * 2)   # first call: attributes, code load
+    torch.cuda.synchronize(dev)
+    e[0].record(stream)
+    P.filter(Bd, Xp, m, a, b, a0, schedule=sched, out=Yp, workspace=ws)
+    e[1].record(stream)
+    torch.cuda.synchronize(dev)
+    status = P.read_status(ws)
+    del ws
+    t_f = e[0].elapsed_time(e[1])
+    Yback = torch.empty_like(Yp)
+    Yback[perm] = Yp
+    y_err = float(torch.linalg.norm(Yback - Yref) / torch.linalg.norm(Yref))
+    del Yback, Xp
+    wso = P.Workspace(dev)
+    wso.get(P.rayleigh_ritz_workspace_bytes(Hy, n, 2, "ozaki"))
+    e[2].record(stream)
+    th, _ = P.rayleigh_ritz(Hy, Yp, 2, workspace=wso, precision="ozaki")
+    e[3].record(stream)
+    torch.cuda.synchronize(dev)
+    t_c = e[2].elapsed_time(e[3])
+    del wso, Yp
+    fl = filter_flops(H["nnz"], N, n, m)
+    t_step = line["phases"]["lanczos_ms"] + t_f + t_c
+    return dict(filter_ms=t_f, filter_gflops=fl / (t_f * 1e-3) / 1e9,
+                filter_speedup_vs_f64=line["phases"]["filter_ms"] / t_f,
+                slice_product_tflops=m * 28 * 2.0 * nblocks * 4096 * n / (t_f * 1e-3) / 1e12,
+                y_rel_fro_err_vs_f64=y_err, status=status, closure_ms=t_c, ms=t_step,
+                speedup_vs_f64_step=line["phases"]["whole_step_ms"] / t_step,
+                host_layout_seconds_untimed=host_s, **_ritz_errors(th.cpu().numpy(), theta_ref, a))
 
 
 def secondary_variants(P, torch, dev, stream):
@@ -790,7 +848,22 @@ def layout_variants(P, torch, dev, stream, wl, H, Hd, Xd, bounds):
         out[f"filter_hybrid_{low}x{L}_f64x{m - L}"] = dict(
             ms=t, gflops=fl / (t * 1e-3) / 1e9, speedup_vs_f64=out["filter_csr_f64"]["ms"] / t,
             y_rel_fro_err_vs_f64=err_vs_ref(), **ritz_err())
+    out["filter_bsr_ozaki_f64"] = ozaki_bsr_variant(P, torch, dev, stream, Bd, Xp, Yb, m, a, b, a0, fl,
+                                                    B["n_blocks"], out["filter_csr_f64"]["ms"], err_vs_ref, ritz_err)
     return out
+
+
+def ozaki_bsr_variant(P, torch, dev, stream, Bd, Xp, Yb, m, a, b, a0, fl, nblocks, t_f64, err_vs_ref, ritz_err):
+    """All m steps FP64-accurate with H's 64 x 64 blocks as Ozaki products on the tensor
+    cores (28 BF16 slice products per stored block element and state), against the FP64
+    CSR filter of the same run."""
+    ws = P.Workspace(dev)
+    t = _timeit(torch, dev, stream,
+                lambda: P.filter(Bd, Xp, m, a, b, a0, schedule=["ozaki"] * m, out=Yb, workspace=ws), reps=1)
+    n = Xp.shape[1]
+    return dict(ms=t, ms_per_step=t / m, gflops=fl / (t * 1e-3) / 1e9, speedup_vs_f64=t_f64 / t,
+                slice_product_tflops=m * 28 * 2.0 * nblocks * 4096 * n / (t * 1e-3) / 1e12,
+                status=P.read_status(ws), y_rel_fro_err_vs_f64=err_vs_ref(), **ritz_err())
 
 
 def run_filter_only(P, torch, dev, wl, H, Hd, Xd, v0d, args):

@@ -43,6 +43,8 @@
 // the next stage before it waits for a drain.  Every mbarrier wait is bounded; on a
 // timeout the CTA flags DEV_TIMEOUT, stops, waits (bounded) for its copies and MMAs in
 // flight, frees TMEM and exits.
+#include <algorithm>
+
 #include "common.cuh"
 #include "kernels.cuh"
 #include "tcgen05.cuh"
@@ -577,29 +579,34 @@ __global__ void oz_slice_kernel(const double* __restrict__ src, int64_t ld, int6
     exps += z * rows_pad;
     slices += (size_t)z * rows_pad * K_pad;
     const int64_t K = Ktot - z * Kb < Kb ? Ktot - z * Kb : Kb;
-    const int64_t r0 = (int64_t)blockIdx.y * 32, k0 = (int64_t)blockIdx.x * 32;
+    const int64_t k0 = (int64_t)blockIdx.x * 32;
     const int tx = threadIdx.x, ty = threadIdx.y;
-    for (int i = ty; i < 32; i += blockDim.y) {
-        double v = 0.0;
-        if (kTrans) {   // src row k0 + i, column r0 + tx  ->  tile[k][r]
-            const int64_t k = k0 + i, r = r0 + tx;
-            if (k < K && r < rows) v = src[k * ld + r];
-            tile[i][tx] = v;
-        } else {        // src row r0 + i, column k0 + tx  ->  tile[k][r]
-            const int64_t r = r0 + i, k = k0 + tx;
-            if (k < K && r < rows) v = src[r * ld + k];
-            tile[tx][i] = v;
+    // row tiles in a grid-stride loop: gridDim.y is at most 65535
+    for (int64_t rt = blockIdx.y; rt * 32 < rows_pad; rt += gridDim.y) {
+        const int64_t r0 = rt * 32;
+        __syncthreads();   // the previous tile has been read
+        for (int i = ty; i < 32; i += blockDim.y) {
+            double v = 0.0;
+            if (kTrans) {   // src row k0 + i, column r0 + tx  ->  tile[k][r]
+                const int64_t k = k0 + i, r = r0 + tx;
+                if (k < K && r < rows) v = src[k * ld + r];
+                tile[i][tx] = v;
+            } else {        // src row r0 + i, column k0 + tx  ->  tile[k][r]
+                const int64_t r = r0 + i, k = k0 + tx;
+                if (k < K && r < rows) v = src[r * ld + k];
+                tile[tx][i] = v;
+            }
         }
-    }
-    __syncthreads();
-    for (int i = ty; i < 32; i += blockDim.y) {
-        const int64_t r = r0 + i, k = k0 + tx;
-        if (r >= rows_pad || k >= K_pad) continue;
-        const int efm = r < rows ? exps[r] : 0;
-        __nv_bfloat16 dg[kSlices];
-        digits_of(tile[tx][i], efm, dg);
+        __syncthreads();
+        for (int i = ty; i < 32; i += blockDim.y) {
+            const int64_t r = r0 + i, k = k0 + tx;
+            if (r >= rows_pad || k >= K_pad) continue;
+            const int efm = r < rows ? exps[r] : 0;
+            __nv_bfloat16 dg[kSlices];
+            digits_of(tile[tx][i], efm, dg);
 #pragma unroll
-        for (int t = 0; t < kSlices; t++) slices[t * plane + (size_t)r * K_pad + k] = dg[t];
+            for (int t = 0; t < kSlices; t++) slices[t * plane + (size_t)r * K_pad + k] = dg[t];
+        }
     }
 }
 
@@ -666,7 +673,7 @@ int oz_prepare(const double* src, int64_t ld, bool trans, const OzOperand& o, in
                                                        status);
     }
     CHFSI_LAUNCH_CHECK();
-    dim3 grid((unsigned)(o.K_pad / 32), (unsigned)(o.rows_pad / 32), (unsigned)o.nbatch);
+    dim3 grid((unsigned)(o.K_pad / 32), (unsigned)std::min<int64_t>(o.rows_pad / 32, 65535), (unsigned)o.nbatch);
     const size_t plane = (size_t)o.plane_rows() * o.K_pad;
     if (trans)
         oz_slice_kernel<true><<<grid, dim3(32, 8), 0, s>>>(src, ld, o.rows, o.K, Ktot, src_bstride, o.exps, o.rows_pad,
@@ -878,7 +885,7 @@ int ozaki_bsr_prepare(const BsrDev& h, int64_t n, void* ws, size_t ws_bytes, uns
     CHFSI_CUDA_TRY(cudaMemsetAsync(b.H.exps, 0, sizeof(int) * (size_t)b.H.plane_rows(), s));
     bsr_row_exponents_kernel<<<(unsigned)h.nbr, 64, 0, s>>>(val, h.brow_ptr, h.nblocks, b.expH, b.H.exps, status);
     CHFSI_LAUNCH_CHECK();
-    dim3 grid((unsigned)(b.H.K_pad / 32), (unsigned)(b.H.rows_pad / 32), 1);
+    dim3 grid((unsigned)(b.H.K_pad / 32), (unsigned)std::min<int64_t>(b.H.rows_pad / 32, 65535), 1);
     oz_slice_kernel<false><<<grid, dim3(32, 8), 0, s>>>(val, 64, h.nblocks * 64, 64, 64, 0, b.H.exps, b.H.rows_pad,
                                                        b.H.K_pad, (size_t)b.H.plane_rows() * b.H.K_pad, b.H.slices);
     CHFSI_LAUNCH_CHECK();

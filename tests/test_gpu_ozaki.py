@@ -296,3 +296,19 @@ def test_bsr_ozaki_rejects_long_rows_and_csr(P):
         P.filter(Hd, torch.zeros(H["N"], 4, dtype=torch.float64, device="cuda"), 2, 4.0, 12.0, 2.0,
                  schedule=["ozaki"] * 2)
     assert e.value.code == _abi.CHFSI_ERR_UNSUPPORTED
+
+
+def test_bsr_ozaki_filter_many_blocks(P, oracle_mod):
+    """The 48^3 grid with w = 3: 39,304 stored blocks, so the slicing of H's blocks
+    spans more than 65,535 row tiles (grid-stride rows), on a few states."""
+    H = W.csr_grid(48, 3, 0.1, 2110158534)
+    n, m = 20, 2
+    X = W.start_block(H["N"], n, 7, orthonormalise=False)
+    a, b, a0 = 4.5, 12.5, 3.0
+    B = W.bsr_from_csr(H, 48)
+    assert B["n_blocks"] * 64 // 32 > 65535
+    ws = P.Workspace("cuda")
+    Yb = P.filter(_bsr_dev(P, B), _dev(X[B["perm"]]), m, a, b, a0, schedule=["ozaki"] * m, workspace=ws)
+    assert P.read_status(ws) == 0
+    Y = _unpermute(Yb.cpu().numpy(), B["perm"])
+    assert rel_fro(Y, oracle_mod.filter(H, X, m, a, b, a0)) <= 1e-12
