@@ -347,7 +347,7 @@ int chfsi_eigh_workspace_size(int64_t n, size_t* bytes);
  * A = Q diag(w) Q^T for a symmetric n x n A (row-major, lda, both triangles stored),
  * the dense eigenproblem of Algorithm 1 step 4 (Sec. 3.4), in FP64 on the GPU:
  * Householder tridiagonalisation, divide and conquer on the tridiagonal matrix
- * (deflation, secular equation by bracketed Newton steps, eigenvector weights recomputed from the
+ * (deflation, secular equation by bracketed rational-model steps, eigenvector weights recomputed from the
  * roots), back-transformation in panels of 64 reflectors.  w: n doubles, ascending.
  * Q: n x n (ldq), Q[k * ldq + i] = component k of the eigenvector of w[i].  A is
  * overwritten.  Q must not overlap A.  The call synchronises `stream` once per merge

@@ -7,7 +7,7 @@
 //      leaves of 32 rows by parallel-ordered Jacobi in shared memory; each merge
 //      deflates (small components of z, nearly equal poles rotated together), finds
 //      the roots of the secular equation 1 + rho sum z_j^2 / (d_j - lambda) (one warp
-//      per root, bracketed Newton steps measured from the nearer pole), recomputes z
+//      per root, bracketed steps of a two-pole rational model from the nearer pole), recomputes z
 //      from the roots (the
 //      Gu-Eisenstat formula, so that the eigenvectors come out orthogonal), and
 //      multiplies the subproblem vectors by the eigenvectors of D + rho z z^T;
@@ -432,9 +432,12 @@ __device__ __forceinline__ double warp_prod(double v) {
 // lanes sharing the sum over the poles (the xor-butterfly sums leave the same value in
 // every lane, so the warp's control flow stays uniform).  Each root is found in
 // tau = lambda - d_org, measured from the nearer pole d_org, so that the differences
-// d_j - lambda = (d_j - d_org) - tau keep their relative accuracy: Newton steps on the
-// increasing function g(tau) inside a bracket [lo, hi] with g(lo) < 0 < g(hi), a
-// bisection step whenever Newton would leave the bracket.
+// d_j - lambda = (d_j - d_org) - tau keep their relative accuracy.  Steps to the zero
+// of a rational model with the two neighbouring poles (constant plus one pole term for
+// each side, fitted to the value and slope of each side's sum: the interpolation
+// behind the classical secular-equation solvers of Bunch, Nielsen and Sorensen and of
+// R.-C. Li), kept inside a bracket [lo, hi] with g(lo) < 0 < g(hi) by a bisection step
+// whenever the model's step would leave it.
 __global__ void __launch_bounds__(32 * kRootWarps) dc_secular_kernel(MergeBufs b, int cap) {
     extern __shared__ double sh[];
     const int k = (int)b.par[2];
@@ -473,22 +476,67 @@ __global__ void __launch_bounds__(32 * kRootWarps) dc_secular_kernel(MergeBufs b
         org = i + 1; lo = -0.5 * gap; hi = 0.0;
     }
     const double dorg = Dj(org);
+    const bool last = i + 1 == k;
     double t = 0.5 * (lo + hi);
     for (int it = 0; it < 200; it++) {
-        double g = 0.0, dg = 0.0;
+        // g = 1 + psi + phi (poles j <= i and j > i) and the derivatives of both parts
+        double psi = 0.0, phi = 0.0, dpsi = 0.0, dphi = 0.0;
         for (int j = lane; j < k; j += 32) {
             const double r = 1.0 / ((Dj(j) - dorg) - t);
             const double q = Zj(j) * r;
-            g += q;
-            dg = fma(q, r, dg);
+            if (j <= i) {
+                psi += q;
+                dpsi = fma(q, r, dpsi);
+            } else {
+                phi += q;
+                dphi = fma(q, r, dphi);
+            }
         }
-        g = 1.0 + rho * warp_sum(g);
-        dg = rho * warp_sum(dg);
+        psi = rho * warp_sum(psi);
+        phi = rho * warp_sum(phi);
+        dpsi = rho * warp_sum(dpsi);
+        dphi = rho * warp_sum(dphi);
+        const double g = 1.0 + psi + phi;
         if (g == 0.0) break;
         if (g > 0.0) hi = t;
         else lo = t;
-        double tn = t - g / dg;
-        if (!(tn > lo && tn < hi)) tn = 0.5 * (lo + hi);
+        // the step to the zero of the model c + s / (Di - eta) + S / (Dn - eta), which has
+        // the poles d_i and d_{i+1} and matches g and g' at tau (the last root: d_i only);
+        // of its two zeros the one nearer tau
+        const double Di = (d_i - dorg) - t;
+        const double s = Di * Di * dpsi;
+        double eta = 0.0;
+        bool have = false;
+        if (last) {
+            const double c = g - s / Di;
+            if (c != 0.0) {
+                eta = Di + s / c;
+                have = true;
+            }
+        } else {
+            const double Dn = (Dj(i + 1) - dorg) - t;
+            const double S = Dn * Dn * dphi;
+            const double c = g - s / Di - S / Dn;
+            const double qa = c, qb = -(c * (Di + Dn) + s + S), qc = c * Di * Dn + s * Dn + S * Di;
+            if (qa == 0.0) {
+                if (qb != 0.0) {
+                    eta = -qc / qb;
+                    have = true;
+                }
+            } else {
+                const double disc = qb * qb - 4.0 * qa * qc;
+                if (disc >= 0.0) {
+                    const double qq = -0.5 * (qb + copysign(sqrt(disc), qb));
+                    const double e1 = qq / qa, e2 = qq != 0.0 ? qc / qq : e1;
+                    eta = fabs(e1) <= fabs(e2) ? e1 : e2;
+                    have = true;
+                }
+            }
+        }
+        have = have && isfinite(eta);
+        if (have && fabs(eta) <= 2.0 * kEps * fabs(t)) break;   // converged
+        double tn = have ? t + eta : 0.5 * (lo + hi);
+        if (!(tn > lo && tn < hi)) tn = 0.5 * (lo + hi);        // a bisection step instead
         const bool done = fabs(tn - t) <= 2.0 * kEps * fabs(tn) || hi - lo <= 2.0 * kEps * fmax(fabs(lo), fabs(hi));
         t = tn;
         if (done) break;
