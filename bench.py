@@ -66,7 +66,8 @@ def parse_args(argv=None):
     ap.add_argument("--cols", type=int, default=0, help="override the workload's state count n")
     ap.add_argument("--filter-only", action="store_true",
                     help="set up, run one filter (m launches of the CSR step per slab) and exit: a profiling case")
-    ap.add_argument("--schedule", default="f64", help="filter-only schedule: f64 | f32:L | bf16:L | f32x2:L")
+    ap.add_argument("--schedule", default="f64",
+                    help="filter-only schedule: f64 | f32:L | bf16:L | f32x2:L | ozaki (BSR or hybrid layout)")
     ap.add_argument("--layout", default="csr", choices=["csr", "bsr", "hybrid"], help="filter-only operator layout")
     ap.add_argument("--closure-only", action="store_true",
                     help="set up, run one CholQR2 + Rayleigh-Ritz on X and exit: a profiling case")
@@ -877,7 +878,9 @@ def run_filter_only(P, torch, dev, wl, H, Hd, Xd, v0d, args):
             P.CsrMatrix.from_arrays(Hp["row_ptr"], Hp["col"], Hp["val"], device=dev), Bd)
         Xd = Xd[torch.as_tensor(B["perm"]).to(dev)].contiguous()
     sched = None
-    if args.schedule != "f64":
+    if args.schedule == "ozaki":
+        sched = ["ozaki"] * wl.m
+    elif args.schedule != "f64":
         low, L = args.schedule.split(":")
         sched = P.mixed_schedule(wl.m, int(L), low)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
