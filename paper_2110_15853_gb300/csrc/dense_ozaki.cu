@@ -58,7 +58,6 @@ using namespace tc;
 constexpr int kSlices = 7;
 constexpr int kPairs = kSlices * (kSlices + 1) / 2;   // slice pairs with t + u <= 8 (1-based)
 constexpr int kAccs = 7;                              // E2 .. E8
-constexpr int kGroupX = 10;                           // pairs 0-9 (E2 .. E5); pairs 10-27 are group Y
 constexpr int kMaxItemKB = 256;                       // K-blocks per work item (8192 K)
 constexpr int kTileM = 128;                           // output rows per tile (TMEM lanes)
 constexpr int kTileN = 64;                            // output columns per tile
@@ -75,21 +74,23 @@ constexpr int kColsPerThread = kTileN / (kEpiWarps / 4);   // 16
 constexpr int kThreads = 32 * (2 + kEpiWarps);
 constexpr int kSmemBytes = kStages * kStageBytes + 1024;
 constexpr uint32_t kTmemCols = 512;
-constexpr uint32_t kIdesc = idesc_bf16(kTileM, kTileN);
 constexpr int kXEvent = 1, kYEvent = 2, kFullEvent = 3;
 static_assert(kSmemBytes + 1024 <= 227 * 1024, "shared memory per CTA");
 static_assert(kAccs * kTileN <= (int)kTmemCols, "seven accumulators in TMEM");
 static_assert(kSliceB % 512 == 0 && kStageBytes % 1024 == 0, "swizzle-atom alignment of the tiles");
 static_assert(kColsPerThread == 16, "16-column TMEM loads");
 
-// Slice pairs (t, u), 0-based, by level, and their accumulator (level - 2).  The first
-// pair of each accumulator: 0, 1, 3, 6, 10, 15, 21.
-__constant__ int8_t kPairA[kPairs] = {0, 0, 1, 0, 1, 2, 0, 1, 2, 3, 0, 1, 2, 3, 4,
-                                      0, 1, 2, 3, 4, 5, 0, 1, 2, 3, 4, 5, 6};
-__constant__ int8_t kPairB[kPairs] = {0, 1, 0, 2, 1, 0, 3, 2, 1, 0, 4, 3, 2, 1, 0,
-                                      5, 4, 3, 2, 1, 0, 6, 5, 4, 3, 2, 1, 0};
-__constant__ int8_t kPairAcc[kPairs] = {0, 1, 1, 2, 2, 2, 3, 3, 3, 3, 4, 4, 4, 4, 4,
-                                        5, 5, 5, 5, 5, 5, 6, 6, 6, 6, 6, 6, 6};
+// The 28 slice pairs (t, u), 0-based, with t + u <= 6 go to accumulator t + u (level
+// t + u + 2).  For one slice t of A, the slices u of B that fall into one accumulator
+// group are consecutive, and so are their accumulators, so they run as one MMA with the
+// B slices stacked along N (N = 64 c <= 256): 4 MMAs for group X (accumulators 0-3,
+// E2 .. E5) and 7 for group Y (accumulators 4-6, E6 .. E8), 11 per K-step instead of 28
+// (fewer, wider MMAs: less shared-memory operand traffic per product).  The first MMA of
+// each group has t = 0 and covers all of the group's accumulators.
+constexpr int kMmaX = 4, kMmas = 11;
+__constant__ int8_t kMmaT[kMmas] = {0, 1, 2, 3, 0, 1, 2, 3, 4, 5, 6};
+__constant__ int8_t kMmaU[kMmas] = {0, 0, 0, 0, 4, 3, 2, 1, 0, 0, 0};
+__constant__ int8_t kMmaC[kMmas] = {4, 3, 2, 1, 3, 3, 3, 3, 3, 2, 1};
 
 // The drain after K-block kb of an item of KB blocks: 0 none, kXEvent (E2 .. E5),
 // kYEvent (E6 .. E8) or kFullEvent (all seven, then the output).
@@ -231,7 +232,9 @@ __device__ __forceinline__ double combine(long long hi, long long lo, int e) {
     return v;
 }
 
-__global__ void __launch_bounds__(kThreads, 1)
+// 112 registers a thread: 18 warps x 32 x 112 = 64,512 of the SM's 65,536 (one CTA per SM)
+static_assert(kThreads * 112 <= 65536, "register file of one SM");
+__global__ void __maxnreg__(112)
 oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, OzArgs g,
                int64_t total) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -333,23 +336,26 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                     asm volatile("tcgen05.fence::after_thread_sync;");
                     return w;
                 };
-                // the pairs of each accumulator are consecutive: the first MMA of a fresh
-                // accumulator overwrites it
-                auto issue = [&](int p0, int p1) {
-                    for (int p = p0; p < p1; p++) {
-                        const int acc = kPairAcc[p];
-                        const bool head = p == 0 || p == 1 || p == 3 || p == 6 || p == 10 || p == 15 || p == 21;
-                        const bool first = head && (p < kGroupX ? resetX : resetY);
-                        const uint64_t da = desc_kmajor(st + kPairA[p] * kSliceA, 64);
-                        const uint64_t db = desc_kmajor(st + kSlices * kSliceA + kPairB[p] * kSliceB, 64);
-                        const uint32_t dt = tmem + (uint32_t)(acc * kTileN);
+                // MMA q multiplies slice kMmaT[q] of A by the kMmaC[q] slices of B from
+                // kMmaU[q] on, stacked along N (consecutive in shared memory), into the
+                // accumulators kMmaT + kMmaU .. (consecutive TMEM columns); the first MMA
+                // of each group covers all of the group's accumulators, so it overwrites
+                // them when the group starts fresh
+                auto issue = [&](int q0, int q1) {
+                    for (int q = q0; q < q1; q++) {
+                        const int t = kMmaT[q], u0 = kMmaU[q], c = kMmaC[q];
+                        const bool first = (q == 0 || q == kMmaX) && (q < kMmaX ? resetX : resetY);
+                        const uint64_t da = desc_kmajor(st + t * kSliceA, 64);
+                        const uint64_t db = desc_kmajor(st + kSlices * kSliceA + u0 * kSliceB, 64);
+                        const uint32_t dt = tmem + (uint32_t)((t + u0) * kTileN);
+                        const uint32_t idesc = idesc_bf16(kTileM, kTileN * c);
 #pragma unroll
                         for (int k = 0; k < kKB / 16; k++) {
                             const uint32_t accumulate = (first && k == 0) ? 0u : 1u;
                             asm volatile(
                                 "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
                                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n"
-                                :: "r"(dt), "l"(da + 2 * k), "l"(db + 2 * k), "r"(kIdesc), "r"(accumulate));
+                                :: "r"(dt), "l"(da + 2 * k), "l"(db + 2 * k), "r"(idesc), "r"(accumulate));
                         }
                     }
                     issued = true;
@@ -359,17 +365,17 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                 bool w = true;
                 if (kb == 0) {
                     if (ev_commit > 0) w = wait_drain();     // the previous item's output drain
-                    if (w) issue(0, kPairs);
+                    if (w) issue(0, kMmas);
                 } else if (resetX) {                           // E2 .. E5 drained after the last block
-                    issue(kGroupX, kPairs);
+                    issue(kMmaX, kMmas);
                     w = wait_drain();
-                    if (w) issue(0, kGroupX);
+                    if (w) issue(0, kMmaX);
                 } else if (resetY) {                           // E6 .. E8 drained after the last block
-                    issue(0, kGroupX);
+                    issue(0, kMmaX);
                     w = wait_drain();
-                    if (w) issue(kGroupX, kPairs);
+                    if (w) issue(kMmaX, kMmas);
                 } else {
-                    issue(0, kPairs);
+                    issue(0, kMmas);
                 }
                 umma_commit(&empty[s]);
                 if (!w) { ok = false; sc++; break; }

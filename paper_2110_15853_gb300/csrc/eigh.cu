@@ -122,10 +122,18 @@ __global__ void __launch_bounds__(32 * kTriRows) tri_product_kernel(const double
     const int64_t r = (int64_t)blockIdx.x * kTriRows + warp;
     double pv = 0.0;
     if (r < m) {
+        // four independent partial sums per lane (more loads in flight), combined in a fixed order
         const double* row = A + (j + 1 + r) * lda + j + 1;
-        double acc = 0.0;
-        for (int64_t i = lane; i < m; i += 32) acc = fma(row[i], v_at(i), acc);
-        const double pr = t * warp_sum(acc);
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+        int64_t i = lane;
+        for (; i + 96 < m; i += 128) {
+            a0 = fma(row[i], v_at(i), a0);
+            a1 = fma(row[i + 32], v_at(i + 32), a1);
+            a2 = fma(row[i + 64], v_at(i + 64), a2);
+            a3 = fma(row[i + 96], v_at(i + 96), a3);
+        }
+        for (; i < m; i += 32) a0 = fma(row[i], v_at(i), a0);
+        const double pr = t * warp_sum((a0 + a1) + (a2 + a3));
         if (lane == 0) pbuf[r] = pr;
         pv = pr * v_at(r);
     }
@@ -155,6 +163,8 @@ __global__ void __launch_bounds__(32 * kTriRows) tri_product_kernel(const double
     }
 }
 
+constexpr int kTriUpdRows = 8;   // rows of A22 per thread of the update kernel
+
 __global__ void __launch_bounds__(256) tri_update_kernel(double* A, int64_t lda, int64_t n, int64_t j,
                                                          TriScalars* tri, double* part,
                                                          const double* __restrict__ tau,
@@ -162,21 +172,32 @@ __global__ void __launch_bounds__(256) tri_update_kernel(double* A, int64_t lda,
                                                          const double* __restrict__ pbuf) {
     const int64_t m = n - j - 1;
     const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t r = blockIdx.y;
+    const int64_t r0 = (int64_t)blockIdx.y * kTriUpdRows;
     const double K = 0.5 * tau[j] * tri->dot;
     double sq = 0.0;
     if (c < m) {
-        const double vr = vbuf[r], vc = vbuf[c];
-        const double wr = pbuf[r] - K * vr, wc = pbuf[c] - K * vc;
-        double* a = A + (j + 1 + r) * lda + j + 1 + c;
-        const double v = *a - (vr * wc + wr * vc);
-        *a = v;
-        if (r == 0) {
-            if (c >= 2) sq = v * v;            // the next reflector's row past its leading entry
-            A[j * lda + j + 1 + c] = vc;       // v kept in row j for the back-transformation
+        const double vc = vbuf[c];
+        const double wc = pbuf[c] - K * vc;
+        const int64_t nr = m - r0 < kTriUpdRows ? m - r0 : kTriUpdRows;
+        double* a = A + (j + 1 + r0) * lda + j + 1 + c;
+        double cur[kTriUpdRows];
+#pragma unroll
+        for (int q = 0; q < kTriUpdRows; q++)
+            if (q < nr) cur[q] = a[q * lda];          // the rows' loads all in flight
+#pragma unroll
+        for (int q = 0; q < kTriUpdRows; q++) {
+            if (q >= nr) break;
+            const double vr = vbuf[r0 + q];
+            const double wr = pbuf[r0 + q] - K * vr;
+            const double v = cur[q] - (vr * wc + wr * vc);
+            a[q * lda] = v;
+            if (r0 + q == 0) {
+                if (c >= 2) sq = v * v;                // the next reflector's row past its leading entry
+                A[j * lda + j + 1 + c] = vc;           // v kept in row j for the back-transformation
+            }
         }
     }
-    if (r == 0) {   // block-uniform: the blocks of the first row sum the next reflector's squares
+    if (blockIdx.y == 0) {   // block-uniform: the blocks of the first rows sum the next reflector's squares
         __shared__ bool last;
         const double bs = block_sum(sq);
         if (threadIdx.x == 0) {
@@ -810,8 +831,8 @@ int eigh(double* A, int64_t lda, int64_t n, double* w, double* Q, int64_t ldq, v
         tri_product_kernel<<<(unsigned)((m + kTriRows - 1) / kTriRows), 32 * kTriRows, 0, s>>>(
             A, lda, n, j, u.tri, u.part_a, d, e, tau, u.vbuf, u.pbuf);
         CHFSI_LAUNCH_CHECK();
-        tri_update_kernel<<<dim3((unsigned)((m + 255) / 256), (unsigned)m), 256, 0, s>>>(A, lda, n, j, u.tri, u.part_b,
-                                                                                       tau, u.vbuf, u.pbuf);
+        tri_update_kernel<<<dim3((unsigned)((m + 255) / 256), (unsigned)((m + kTriUpdRows - 1) / kTriUpdRows)), 256, 0,
+                            s>>>(A, lda, n, j, u.tri, u.part_b, tau, u.vbuf, u.pbuf);
         CHFSI_LAUNCH_CHECK();
     }
     tridiag_tail_kernel<<<1, 32, 0, s>>>(A, lda, n, d, e, tau);

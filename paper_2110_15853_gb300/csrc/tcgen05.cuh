@@ -80,7 +80,7 @@ __device__ __forceinline__ uint64_t desc_kmajor(uint32_t addr, int swizzle_bytes
 
 // tcgen05.mma kind::f16 instruction descriptor: BF16 x BF16 -> FP32, A and B K-major,
 // M x N tile.
-constexpr uint32_t idesc_bf16(int M, int N) {
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
