@@ -159,9 +159,10 @@ __device__ __forceinline__ void bsr_row_range(const OzArgs& g, int64_t R, int& q
 // First column tile of row tile tm that reaches the upper triangle (j >= i).
 __device__ __host__ __forceinline__ int first_upper_tn(int tm) { return (tm * kTileM) / kTileN; }
 
+template <bool kBsr>
 __device__ __forceinline__ Item decode(const OzArgs& g, int64_t item) {
     Item it;
-    if (g.bsr) {
+    if (kBsr) {
         // the state tiles of a block row are consecutive, so its H slices are shared
         // through L2
         const int64_t R = item / g.tilesM;
@@ -232,9 +233,13 @@ __device__ __forceinline__ double combine(long long hi, long long lo, int e) {
     return v;
 }
 
-// 112 registers a thread: 18 warps x 32 x 112 = 64,512 of the SM's 65,536 (one CTA per SM)
-static_assert(kThreads * 112 <= 65536, "register file of one SM");
-__global__ void __maxnreg__(112)
+// One CTA of 18 warps per SM: the register file is split among the SM's four schedulers
+// (16,384 registers each) and five of the warps share one of them, which allows 96
+// registers a thread; ptxas keeps to that under these launch bounds.  kBsr: the BSR
+// filter-step mode (its own instantiation, so that neither mode carries the other's
+// epilogue registers).
+template <bool kBsr>
+__global__ void __launch_bounds__(kThreads, 1)
 oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, OzArgs g,
                int64_t total) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -272,8 +277,8 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         // ---------------- TMA producer
         int64_t sc = 0;
         for (int64_t item = blockIdx.x; item < total && !*abort_v; item += gridDim.x) {
-            const Item it = decode(g, item);
-            if (g.bsr) {
+            const Item it = decode<kBsr>(g, item);
+            if (kBsr) {
                 int qb, nq;
                 bsr_row_range(g, it.tn, qb, nq, bad_pattern);
             }
@@ -286,7 +291,7 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                 // K offset in A_hat and in B_hat, and B_hat's first row
                 int xa = (it.kb0 + kb) * kKB, xb = xa;
                 int64_t rb = it.batch * g.b_batch_rows + (int64_t)it.tn * kTileN;
-                if (g.bsr) {
+                if (kBsr) {
                     const int q = it.qb + kb / 2, half = kb & 1;
                     int C = g.bcol[q];
                     if (C < 0 || (int64_t)C >= g.nbr) { C = 0; bad_pattern = true; }   // still a valid tile
@@ -317,7 +322,7 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         int64_t sc = 0, ev_commit = 0, ev_wait = 0;
         bool issued = false;
         for (int64_t item = blockIdx.x; item < total && !*abort_v; item += gridDim.x) {
-            const Item it = decode(g, item);
+            const Item it = decode<kBsr>(g, item);
             bool ok = true;
             for (int kb = 0; kb < it.KB; kb++, sc++) {
                 const int s = (int)(sc % kStages);
@@ -416,10 +421,10 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             }
         };
         for (int64_t item = blockIdx.x; item < total; item += gridDim.x) {
-            const Item it = decode(g, item);
+            const Item it = decode<kBsr>(g, item);
 #pragma unroll
             for (int c = 0; c < kColsPerThread; c++) hi[c] = lo[c] = 0;
-            if (g.bsr && it.KB == 0) {   // empty block row: no MMA, no drain
+            if (kBsr && it.KB == 0) {   // empty block row: no MMA, no drain
                 if (*abort_v) break;
                 bsr_out(it, false);
                 continue;
@@ -454,7 +459,7 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&eempty);
                 ev++;
-                if (kind == kFullEvent && g.bsr) {
+                if (kind == kFullEvent && kBsr) {
                     bsr_out(it, true);
                 } else if (kind == kFullEvent) {
                     const int64_t row = (int64_t)it.tm * kTileM + 32 * q + lane;        // within the batch
@@ -733,13 +738,17 @@ int launch_oz(const CUtensorMap& tmA, const CUtensorMap& tmB, const OzArgs& g, i
     if (dev < 0) return CHFSI_ERR_CUDA;
     static bool attr[kMaxDevices] = {};
     if (!attr[dev]) {
-        CHFSI_CUDA_TRY(cudaFuncSetAttribute(oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
+        CHFSI_CUDA_TRY(
+            cudaFuncSetAttribute(oz_gemm_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
+        CHFSI_CUDA_TRY(
+            cudaFuncSetAttribute(oz_gemm_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
         attr[dev] = true;
     }
     const int sms = sm_count();
     if (sms <= 0) return CHFSI_ERR_CUDA;
     const unsigned grid = (unsigned)(total < sms ? total : sms);
-    oz_gemm_kernel<<<grid, kThreads, kSmemBytes, s>>>(tmA, tmB, g, total);
+    if (g.bsr) oz_gemm_kernel<true><<<grid, kThreads, kSmemBytes, s>>>(tmA, tmB, g, total);
+    else oz_gemm_kernel<false><<<grid, kThreads, kSmemBytes, s>>>(tmA, tmB, g, total);
     CHFSI_LAUNCH_CHECK();
     return CHFSI_OK;
 }
