@@ -50,7 +50,7 @@ extern "C" {
 #define CHFSI_ERR_PATTERN 3     /* bad CSR/BSR pattern (device found a column out of range) */
 #define CHFSI_ERR_CHOL 4        /* Gram matrix not positive definite (Cholesky pivot <= 0) */
 #define CHFSI_ERR_NONFINITE 5   /* a kernel produced or read a NaN / Inf                 */
-#define CHFSI_ERR_CUDA 6        /* a CUDA runtime or cuSOLVER call failed                */
+#define CHFSI_ERR_CUDA 6        /* a CUDA runtime call failed                            */
 #define CHFSI_ERR_TIMEOUT 7     /* a bounded device wait gave up                         */
 #define CHFSI_ERR_NOMEM 8       /* workspace smaller than the *_workspace_size answer    */
 #define CHFSI_ERR_UNSUPPORTED 9 /* combination not implemented (e.g. a precision on BSR) */
@@ -273,13 +273,15 @@ int chfsi_rayleigh_ritz_workspace_size(const chfsi_matrix* H, int64_t n_cols,
  *   2. X_F = Orth(Y) by Cholesky-QR: S = Y^T Y, S = R^T R, X_F = Y R^-1
  *      (cholqr_passes = 2 repeats it on X_F: CholQR2);
  *   3. H_F = X_F^T (H X_F);
- *   4. H_F Q = Q Lambda (ascending eigenvalues);
+ *   4. H_F Q = Q Lambda (ascending eigenvalues), by the library's dense eigensolver
+ *      (the algorithm of chfsi_eigh, which synchronises `stream` once per merge of
+ *      its divide and conquer);
  *   5. Psi = X_F Q.
  * Y: N x n_cols (ldy), read only.  Psi: N x n_cols (ldpsi), written.
  * ritz: device array of n_cols doubles, written ascending.  n_cols <= N.
- * Synchronises `stream` before returning (it reads the Cholesky and eigensolver
- * status); returns CHFSI_ERR_CHOL if a pivot was not positive, CHFSI_ERR_CUDA if
- * the eigensolver failed.
+ * Synchronises `stream` before returning (it reads the status word); returns
+ * CHFSI_ERR_CHOL if a Cholesky pivot was not positive, CHFSI_ERR_NONFINITE if a
+ * non-finite value was met, CHFSI_ERR_CUDA if a launch failed.
  */
 int chfsi_rayleigh_ritz(const chfsi_matrix* H, const double* Y, int64_t ldy, int64_t n_cols,
                         double* Psi, int64_t ldpsi, double* ritz, int32_t cholqr_passes,
@@ -401,7 +403,7 @@ int chfsi_clear_status(void* ws, void* stream);
 int chfsi_measure_pipe_peak(int32_t precision, double* flops_per_second, void* stream);
 
 /* Number of kernels this library has launched in this process (all devices, all
- * threads; library calls such as the cuSOLVER eigensolver are not counted).
+ * threads).
  * Diagnostics only: the paper has no counterpart. */
 unsigned long long chfsi_kernel_launches(void);
 

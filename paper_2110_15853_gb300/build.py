@@ -3,8 +3,8 @@
     python -m paper_2110_15853_gb300.build [--force]
 
 Translation units compile in parallel into _build/, then link into
-paper_2110_15853_gb300/libchfsi.so with cuSOLVER (dense eigensolver of the
-Rayleigh-Ritz step) and the static CUDA runtime.
+paper_2110_15853_gb300/libchfsi.so with the static CUDA runtime (no other library:
+every step, the dense eigensolver included, runs in this library's kernels).
 """
 from __future__ import annotations
 
@@ -66,8 +66,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         objs = list(ex.map(compile_one, SOURCES))
     tmp = LIB + f".tmp{os.getpid()}"
     libdir = os.path.join(home, "lib64")
-    cmd = [nvcc, "-shared", *ARCH, "-o", tmp, *objs, "-L" + libdir, "-lcusolver",
-           "-Xlinker", "-rpath," + libdir]
+    cmd = [nvcc, "-shared", *ARCH, "-o", tmp, *objs, "-L" + libdir, "-Xlinker", "-rpath," + libdir]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

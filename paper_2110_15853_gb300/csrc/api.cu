@@ -10,7 +10,6 @@
 #include <mutex>
 #include <vector>
 
-#include <cusolverDn.h>
 
 #include "common.cuh"
 #include "kernels.cuh"
@@ -240,28 +239,6 @@ void make_devs(const chfsi_matrix* H, const void* csr_val, const void* bsr_val, 
         *bsr = BsrDev{H->bsr.n_block_rows, H->bsr.n_blocks, H->bsr.bdim, H->bsr.brow_ptr, H->bsr.bcol, bsr_val, vt};
 }
 
-// cuSOLVER handle per device, created on first use.
-cusolverDnHandle_t solver_handle() {
-    static std::mutex mu;
-    static cusolverDnHandle_t handles[64] = {};
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
-    std::lock_guard<std::mutex> g(mu);
-    if (!handles[dev]) {
-        if (cusolverDnCreate(&handles[dev]) != CUSOLVER_STATUS_SUCCESS) handles[dev] = nullptr;
-    }
-    return handles[dev];
-}
-
-int syevd_lwork(int64_t n, int* lwork) {
-    cusolverDnHandle_t h = solver_handle();
-    if (!h) return CHFSI_ERR_CUDA;
-    if (cusolverDnDsyevd_bufferSize(h, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_UPPER, (int)n, nullptr, (int)n,
-                                    nullptr, lwork) != CUSOLVER_STATUS_SUCCESS)
-        return CHFSI_ERR_CUDA;
-    return CHFSI_OK;
-}
-
 }  // namespace
 
 // Exported entry points (C linkage comes from the declarations in chfsi.h).
@@ -274,7 +251,7 @@ const char* chfsi_status_string(int st) {
         case CHFSI_ERR_PATTERN: return "invalid sparsity pattern (index out of range)";
         case CHFSI_ERR_CHOL: return "Cholesky-QR failed: Gram matrix not positive definite";
         case CHFSI_ERR_NONFINITE: return "non-finite value produced or read";
-        case CHFSI_ERR_CUDA: return "CUDA runtime or cuSOLVER error";
+        case CHFSI_ERR_CUDA: return "CUDA runtime error";
         case CHFSI_ERR_TIMEOUT: return "bounded device wait timed out";
         case CHFSI_ERR_NOMEM: return "workspace too small";
         case CHFSI_ERR_UNSUPPORTED: return "unsupported combination of layout and precision";
@@ -783,10 +760,9 @@ namespace {
 
 struct RRLayout {
     double *S = nullptr, *part = nullptr, *XF = nullptr, *T = nullptr, *Rinv = nullptr, *Q = nullptr;
-    double* work = nullptr;
-    int* info = nullptr;
+    unsigned char* eig = nullptr;    // scratch of the dense eigensolver
+    size_t eig_bytes = 0;
     int splits = 1;
-    int lwork = 0;
     // two-float closure
     float2 *Y2 = nullptr, *B2[2] = {nullptr, nullptr}, *HX2 = nullptr, *R2 = nullptr, *Q2 = nullptr, *H2 = nullptr;
     // Ozaki closure: scratch of the tensor-core products, reused by the two-float H X_F
@@ -811,18 +787,17 @@ size_t rr_ozaki_bytes(int64_t N, int64_t n, int64_t nnz, bool csr) {
 }
 
 template <typename Ar>
-void rr_layout(Ar& ar, int64_t N, int64_t n, int lwork, int precision, int64_t nnz, bool csr, RRLayout* out) {
+void rr_layout(Ar& ar, int64_t N, int64_t n, int precision, int64_t nnz, bool csr, RRLayout* out) {
     RRLayout rl;
     const int64_t ldw = pad8(n);
     rl.splits = gemm_tn_splits(N, n);
-    rl.lwork = lwork;
     ar.template take<unsigned char>(kStatusBytes);
     rl.S = ar.template take<double>((size_t)(n * n));
     rl.part = ar.template take<double>((size_t)(rl.splits * n * n));
     rl.Rinv = ar.template take<double>((size_t)(n * n));
     rl.Q = ar.template take<double>((size_t)(n * n));
-    rl.work = ar.template take<double>((size_t)(lwork > 0 ? lwork : 1));
-    rl.info = ar.template take<int>(1);
+    rl.eig_bytes = eigh_workspace_bytes(n);
+    rl.eig = ar.template take<unsigned char>(rl.eig_bytes);
     if (precision == CHFSI_F32X2) {
         rl.Y2 = ar.template take<float2>((size_t)(N * ldw));
         rl.B2[0] = ar.template take<float2>((size_t)(N * ldw));
@@ -851,27 +826,19 @@ int rr_check(const chfsi_matrix* H, int64_t n_cols, int32_t cholqr_passes, int32
     return CHFSI_OK;
 }
 
-// Step 4 (eigensolve) and the status read-back shared by both precisions.
-int rr_eig(const RRLayout& rl, int64_t n, double* ritz, cudaStream_t s) {
-    cusolverDnHandle_t hs = solver_handle();
-    if (!hs) return CHFSI_ERR_CUDA;
-    if (cusolverDnSetStream(hs, s) != CUSOLVER_STATUS_SUCCESS) return CHFSI_ERR_CUDA;
-    if (cusolverDnDsyevd(hs, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_UPPER, (int)n, rl.S, (int)n, ritz, rl.work,
-                         rl.lwork, rl.info) != CUSOLVER_STATUS_SUCCESS)
-        return CHFSI_ERR_CUDA;
-    // eigenvector i is row i of the row-major view; Q[k][i] = that row transposed
-    return transpose(rl.S, n, rl.Q, n, n, s);
+// Step 4 (eigensolve, the library's divide-and-conquer solver) and the status read-back
+// shared by all precisions.  Q[k][i] = component k of the eigenvector of ritz[i].
+int rr_eig(const RRLayout& rl, int64_t n, double* ritz, unsigned* st, cudaStream_t s) {
+    return eigh(rl.S, n, n, ritz, rl.Q, n, rl.eig, rl.eig_bytes, st, s);
 }
 
 int rr_finish(const RRLayout& rl, unsigned* st, cudaStream_t s) {
-    int info = 0;
-    CHFSI_CUDA_TRY(cudaMemcpyAsync(&info, rl.info, sizeof(int), cudaMemcpyDeviceToHost, s));
+    (void)rl;
     CHFSI_CUDA_TRY(cudaStreamSynchronize(s));
     unsigned word = 0;
     CHFSI_CUDA_TRY(cudaMemcpy(&word, st, sizeof(unsigned), cudaMemcpyDeviceToHost));
     if (word & DEV_PATTERN) return CHFSI_ERR_PATTERN;
     if (word & DEV_CHOL) return CHFSI_ERR_CHOL;
-    if (info != 0) return CHFSI_ERR_CUDA;
     if (word & DEV_NONFINITE) return CHFSI_ERR_NONFINITE;
     return CHFSI_OK;
 }
@@ -904,7 +871,7 @@ int rr_run_f32x2(const chfsi_matrix* H, const double* Y, int64_t ldy, int64_t N,
     // mirrored, and the diagonal tiles averaged with their transposes
     if ((rc = gemm_tn_f32x2(XF, ldw, HXF, ldw, N, n, rl.S, n, true, rl.part, rl.splits, s))) return rc;
     if ((rc = symmetrize(rl.S, n, n, s))) return rc;
-    if ((rc = rr_eig(rl, n, ritz, s))) return rc;
+    if ((rc = rr_eig(rl, n, ritz, st, s))) return rc;
     if ((rc = to_f32x2(rl.Q, n, rl.Q2, n, n, n, false, s))) return rc;
     if ((rc = gemm_nn_f32x2(XF, ldw, rl.Q2, n, Psi, ldpsi, true, N, n, false, s))) return rc;
     return rr_finish(rl, st, s);
@@ -959,7 +926,7 @@ int rr_run_ozaki(const chfsi_matrix* H, const double* Y, int64_t ldy, int64_t N,
     // tiles averaged with their transposes
     if ((rc = ozaki_gemm_tn(XF, ldw, HXF, ldw, N, n, n, rl.S, n, true, rl.oz, rl.oz_bytes, st, s))) return rc;
     if ((rc = symmetrize(rl.S, n, n, s))) return rc;
-    if ((rc = rr_eig(rl, n, ritz, s))) return rc;
+    if ((rc = rr_eig(rl, n, ritz, st, s))) return rc;
     if ((rc = ozaki_gemm_nn(XF, ldw, rl.Q, n, N, n, n, Psi, ldpsi, false, rl.oz, rl.oz_bytes, st, s))) return rc;
     return rr_finish(rl, st, s);
 }
@@ -972,10 +939,8 @@ int chfsi_rayleigh_ritz_ex_workspace_size(const chfsi_matrix* H, int64_t n_cols,
     int64_t N = 0;
     int rc = rr_check(H, n_cols, cholqr_passes, precision, &N);
     if (rc) return rc;
-    int lwork = 0;
-    if ((rc = syevd_lwork(n_cols, &lwork))) return rc;
     SizeOnly sz;
-    rr_layout(sz, N, n_cols, lwork, precision, has_csr(H) ? H->csr.nnz : 0, has_csr(H), nullptr);
+    rr_layout(sz, N, n_cols, precision, has_csr(H) ? H->csr.nnz : 0, has_csr(H), nullptr);
     *bytes = sz.used;
     return CHFSI_OK;
 }
@@ -993,15 +958,13 @@ int chfsi_rayleigh_ritz_ex(const chfsi_matrix* H, const double* Y, int64_t ldy, 
     if ((rc = check_block(Y, ldy, n_cols)) || (rc = check_block(Psi, ldpsi, n_cols))) return rc;
     if (!ritz || Psi == Y) return CHFSI_ERR_ARG;
     if (!ws || !aligned16(ws)) return CHFSI_ERR_ARG;
-    int lwork = 0;
-    if ((rc = syevd_lwork(n_cols, &lwork))) return rc;
     const int64_t nnz = has_csr(H) ? H->csr.nnz : 0;
     SizeOnly sz;
-    rr_layout(sz, N, n_cols, lwork, precision, nnz, has_csr(H), nullptr);
+    rr_layout(sz, N, n_cols, precision, nnz, has_csr(H), nullptr);
     if (ws_bytes < sz.used) return CHFSI_ERR_NOMEM;
     Arena ar(ws, ws_bytes);
     RRLayout rl;
-    rr_layout(ar, N, n_cols, lwork, precision, nnz, has_csr(H), &rl);
+    rr_layout(ar, N, n_cols, precision, nnz, has_csr(H), &rl);
     cudaStream_t s = as_stream(stream);
     unsigned* st = status_word(ws);
     CHFSI_CUDA_TRY(cudaMemsetAsync(st, 0, sizeof(unsigned), s));
@@ -1042,8 +1005,8 @@ int chfsi_rayleigh_ritz_ex(const chfsi_matrix* H, const double* Y, int64_t ldy, 
     // mirrored, and the diagonal tiles averaged with their transposes
     if ((rc = gemm_tn(XF, ldw, HXF, ldw, N, n, rl.S, n, true, rl.part, rl.splits, s))) return rc;
     if ((rc = symmetrize(rl.S, n, n, s))) return rc;
-    // step 4: H_F Q = Q Lambda (cuSOLVER; column-major view of the symmetric H_F)
-    if ((rc = rr_eig(rl, n, ritz, s))) return rc;
+    // step 4: H_F Q = Q Lambda
+    if ((rc = rr_eig(rl, n, ritz, st, s))) return rc;
     // step 5: Psi = X_F Q
     if ((rc = gemm_nn(XF, ldw, rl.Q, n, Psi, ldpsi, N, n, false, s))) return rc;
     return rr_finish(rl, st, s);
