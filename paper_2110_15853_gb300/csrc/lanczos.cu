@@ -208,11 +208,40 @@ __device__ int sturm_count(const double* d, const double* e, int k, double x) {
     return cnt;
 }
 
-// Smallest and largest eigenvalue of T_k by bisection, then the bounds.
+// The point of (a, b) where the Sturm count reaches `target` (the target-th smallest
+// eigenvalue of T_k), by multisection on one warp: each lane counts at one of 32
+// equally spaced interior points, and the bracket shrinks to the interval between the
+// last point below the target and the first at or above it (a factor 33 per round, where
+// bisection gives 2).  Every lane ends with the same bracket.
+__device__ double sturm_edge(const double* d, const double* e, int k, double a, double b, int target) {
+    const int lane = threadIdx.x & 31;
+    for (int it = 0; it < 64; it++) {
+        const double h = (b - a) / 33.0;
+        const double x = a + h * (double)(lane + 1);
+        const bool ge = !(x < b) || sturm_count(d, e, k, x) >= target;
+        const unsigned mask = __ballot_sync(0xffffffffu, ge);
+        double na, nb;
+        if (mask == 0) {
+            na = __shfl_sync(0xffffffffu, x, 31);
+            nb = b;
+        } else {
+            const int f = __ffs(mask) - 1;
+            nb = __shfl_sync(0xffffffffu, x, f);
+            const double xl = __shfl_sync(0xffffffffu, x, f > 0 ? f - 1 : 0);
+            na = f > 0 ? xl : a;
+        }
+        if (!(na > a) && !(nb < b)) break;   // the bracket is at rounding resolution
+        a = na > a ? na : a;
+        b = nb < b ? nb : b;
+    }
+    return 0.5 * (a + b);
+}
+
+// Smallest and largest eigenvalue of T_k by multisection (one warp), then the bounds.
 __global__ void bounds_kernel(const double* scal, int64_t N, int64_t n_wanted, double* out) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    if (blockIdx.x != 0 || threadIdx.x >= 32) return;
     if (scal[S_STOP] == 2.0) {
-        out[0] = out[1] = out[2] = nan("");
+        if (threadIdx.x == 0) out[0] = out[1] = out[2] = nan("");
         return;
     }
     int k = (int)scal[S_K];
@@ -227,21 +256,9 @@ __global__ void bounds_kernel(const double* scal, int64_t N, int64_t n_wanted, d
     double span = hi - lo;
     lo -= 1e-12 * (span + 1.0);
     hi += 1e-12 * (span + 1.0);
-    // smallest: largest x with count(x) == 0
-    double a = lo, b = hi;
-    for (int it = 0; it < 200; it++) {
-        double m = 0.5 * (a + b);
-        if (m <= a || m >= b) break;
-        if (sturm_count(d, e, k, m) >= 1) b = m; else a = m;
-    }
-    const double theta_min = 0.5 * (a + b);
-    a = lo; b = hi;
-    for (int it = 0; it < 200; it++) {
-        double m = 0.5 * (a + b);
-        if (m <= a || m >= b) break;
-        if (sturm_count(d, e, k, m) >= k) b = m; else a = m;
-    }
-    const double theta_max = 0.5 * (a + b);
+    const double theta_min = sturm_edge(d, e, k, lo, hi, 1);
+    const double theta_max = sturm_edge(d, e, k, lo, hi, k);
+    if (threadIdx.x != 0) return;
     const double resid = fabs(e[k - 1]);
     const double a0 = theta_min;
     const double bb = theta_max + resid;
