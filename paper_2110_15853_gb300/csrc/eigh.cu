@@ -107,7 +107,8 @@ __global__ void tri_init_kernel(const double* A, int64_t n, TriScalars* tri) {
     }
 }
 
-constexpr int kTriRows = 8;   // rows (one warp each) per block of the product kernel
+constexpr int kTriRows = 8;     // rows (one warp each) per block of the product kernel
+constexpr int kTriUnroll = 8;   // loads in flight per lane in the product kernel
 
 __global__ void __launch_bounds__(32 * kTriRows) tri_product_kernel(const double* __restrict__ A, int64_t lda,
                                                                     int64_t n, int64_t j, TriScalars* tri,
@@ -122,18 +123,26 @@ __global__ void __launch_bounds__(32 * kTriRows) tri_product_kernel(const double
     const int64_t r = (int64_t)blockIdx.x * kTriRows + warp;
     double pv = 0.0;
     if (r < m) {
-        // four independent partial sums per lane (more loads in flight), combined in a fixed order
+        // eight independent partial sums per lane (eight loads in flight), combined in a
+        // fixed order
         const double* row = A + (j + 1 + r) * lda + j + 1;
-        double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+        double acc[kTriUnroll];
+#pragma unroll
+        for (int q = 0; q < kTriUnroll; q++) acc[q] = 0.0;
         int64_t i = lane;
-        for (; i + 96 < m; i += 128) {
-            a0 = fma(row[i], v_at(i), a0);
-            a1 = fma(row[i + 32], v_at(i + 32), a1);
-            a2 = fma(row[i + 64], v_at(i + 64), a2);
-            a3 = fma(row[i + 96], v_at(i + 96), a3);
+        for (; i + 32 * (kTriUnroll - 1) < m; i += 32 * kTriUnroll) {
+            double rv[kTriUnroll];
+#pragma unroll
+            for (int q = 0; q < kTriUnroll; q++) rv[q] = row[i + 32 * q];
+#pragma unroll
+            for (int q = 0; q < kTriUnroll; q++) acc[q] = fma(rv[q], v_at(i + 32 * q), acc[q]);
         }
-        for (; i < m; i += 32) a0 = fma(row[i], v_at(i), a0);
-        const double pr = t * warp_sum((a0 + a1) + (a2 + a3));
+        for (; i < m; i += 32) acc[0] = fma(row[i], v_at(i), acc[0]);
+#pragma unroll
+        for (int w = kTriUnroll / 2; w > 0; w /= 2)
+#pragma unroll
+            for (int q = 0; q < w; q++) acc[q] += acc[q + w];
+        const double pr = t * warp_sum(acc[0]);
         if (lane == 0) pbuf[r] = pr;
         pv = pr * v_at(r);
     }
@@ -163,7 +172,7 @@ __global__ void __launch_bounds__(32 * kTriRows) tri_product_kernel(const double
     }
 }
 
-constexpr int kTriUpdRows = 8;   // rows of A22 per thread of the update kernel
+constexpr int kTriUpdRows = 16;  // rows of A22 per thread of the update kernel
 
 __global__ void __launch_bounds__(256) tri_update_kernel(double* A, int64_t lda, int64_t n, int64_t j,
                                                          TriScalars* tri, double* part,
