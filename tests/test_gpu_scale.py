@@ -3,10 +3,13 @@
 * 48^3 grid, w = 3, 4096 states, m = 24 and 64^3 grid, w = 4, 6000 states, m = 30:
   the GPU filters every column at full N (FP64 and two-float), the oracle filters
   a seeded column subset (the filter is column-independent) and the two are
-  compared on those columns at 1e-12; the GPU Lanczos bounds agree with the
+  compared on those columns at 1e-12, for the FP64, two-float and Ozaki (H's 64 x 64
+  blocks on the tensor cores) schedules; the GPU Lanczos bounds agree with the
   oracle's at 1e-10.
 * 48^3/4096/m = 24: the two-float schedule's Ritz values (two-float filter and
-  closure products) within 1e-8 of the all-FP64 run's, the mixed-precision target.
+  closure products), and those of the FP64-accurate tensor-core step (Ozaki BSR
+  filter and Ozaki closure), within 1e-8 of the all-FP64 run's, the mixed-precision
+  target.
 * 32^3 grid, w = 2, 512 states, m = 16: the hand-written adjoint's dL/dH against
   central finite differences (h = 1e-6) of L = tr(Y^T W Y) through the GPU forward
   filter on 200 seeded random stored entries, at 1e-6 of max |dL/dH|.
@@ -58,6 +61,20 @@ def test_full_size_filter_sampled_columns(P, oracle_mod, name, cols):
         assert P.read_status(ws) == 0
         err = rel_fro(Y[:, idx].cpu().numpy(), Yref)
         assert err <= 1e-12, (sched is not None, err)
+    # FP64-accurate steps with H's 64 x 64 blocks as Ozaki products, in the blocked row order
+    B = W.bsr_from_csr(H, wl.g)
+    perm = torch.as_tensor(B["perm"], device=dev)
+    Bd = P.BsrMatrix.from_arrays(B["brow_ptr"], B["bcol"], B["val"], device=dev)
+    del B
+    Xp = Xd[perm].contiguous()
+    Yb = torch.empty_like(Xp)
+    wso = P.Workspace(dev)
+    P.filter(Bd, Xp, wl.m, a, b, a0, schedule=["ozaki"] * wl.m, out=Yb, workspace=wso)
+    assert P.read_status(wso) == 0
+    del Xp, wso
+    Y[perm] = Yb
+    err = rel_fro(Y[:, idx].cpu().numpy(), Yref)
+    assert err <= 1e-12, ("ozaki", err)
 
 
 def test_two_float_ritz_values_meet_mixed_target_48cube(P, oracle_mod):
@@ -74,6 +91,34 @@ def test_two_float_ritz_values_meet_mixed_target_48cube(P, oracle_mod):
     assert np.all(np.diff(t64) >= 0) and np.all(np.diff(t2) >= 0)
     err = float(np.max(np.abs(t2 - t64)) / np.max(np.abs(t64)))
     assert err <= 1e-8, err
+
+
+def test_ozaki_step_ritz_values_meet_mixed_target_48cube(P, oracle_mod):
+    """The whole step FP64-accurate on the tensor cores (Ozaki BSR filter steps and the
+    Ozaki closure, in the blocked row order) against the all-FP64 run: Ritz values within
+    1e-8 relative, and within 1e-10 of the FP64 Ritz values' scale below the filter edge a."""
+    wl, H, X, v0, (a, b, a0), Hd, Xd = _setup(P, oracle_mod, "g48_w3_n4096_m24")
+    del X
+    dev = Xd.device
+    Y = torch.empty_like(Xd)
+    P.filter(Hd, Xd, wl.m, a, b, a0, out=Y)
+    theta64, _ = P.rayleigh_ritz(Hd, Y, 2)
+    B = W.bsr_from_csr(H, wl.g)
+    perm = torch.as_tensor(B["perm"], device=dev)
+    Hp = W.permute_csr(H, B["perm"])
+    Hy = P.HybridMatrix(P.CsrMatrix.from_arrays(Hp["row_ptr"], Hp["col"], Hp["val"], device=dev),
+                        P.BsrMatrix.from_arrays(B["brow_ptr"], B["bcol"], B["val"], device=dev))
+    del B, Hp, Hd
+    Xp = Xd[perm].contiguous()
+    del Xd
+    P.filter(Hy, Xp, wl.m, a, b, a0, schedule=["ozaki"] * wl.m, out=Y)
+    theta_oz, _ = P.rayleigh_ritz(Hy, Y, 2, precision="ozaki")
+    t64, toz = theta64.cpu().numpy(), theta_oz.cpu().numpy()
+    assert np.all(np.diff(toz) >= 0)
+    scale = np.max(np.abs(t64))
+    assert float(np.max(np.abs(toz - t64)) / scale) <= 1e-8
+    below = t64 < a
+    assert float(np.max(np.abs(toz[below] - t64[below])) / scale) <= 1e-10
 
 
 def test_adjoint_central_differences_32cube_200_entries(P, oracle_mod):
