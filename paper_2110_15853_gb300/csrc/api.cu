@@ -166,6 +166,21 @@ int schedule_prefix(const chfsi_schedule* sched, int m, int* L, int* low_kind, i
     return CHFSI_OK;
 }
 
+// Whether every block row of a 64 x 64 BSR operator has at most 128 blocks (8192
+// columns), the K one Ozaki work item accumulates exactly; copies the block-row
+// pointers to the host and synchronises `s`.
+int bsr_rows_fit_ozaki(const chfsi_matrix* H, cudaStream_t s, bool* fit) {
+    *fit = false;
+    if (!has_bsr(H) || H->bsr.bdim != 64) return CHFSI_OK;
+    std::vector<int32_t> bp((size_t)H->bsr.n_block_rows + 1);
+    CHFSI_CUDA_TRY(cudaMemcpyAsync(bp.data(), H->bsr.brow_ptr, sizeof(int32_t) * bp.size(), cudaMemcpyDeviceToHost, s));
+    CHFSI_CUDA_TRY(cudaStreamSynchronize(s));
+    for (size_t r = 0; r + 1 < bp.size(); r++)
+        if (bp[r + 1] - bp[r] > 128) return CHFSI_OK;
+    *fit = true;
+    return CHFSI_OK;
+}
+
 // Scratch of the Ozaki BSR steps (0 when the schedule has none).
 size_t ozaki_tail_bytes(const chfsi_matrix* H, int64_t n, int m, int L, int tail) {
     if (tail != CHFSI_F64_OZAKI || L >= m || !has_bsr(H)) return 0;
@@ -464,13 +479,9 @@ int chfsi_filter(const chfsi_matrix* H, const double* X, int64_t ldx, double* Y,
     if (L > 0 && low == CHFSI_F32X2 && !has_csr(H)) return CHFSI_ERR_UNSUPPORTED;
     if (oz_tail) {
         // an Ozaki work item holds one block row: at most 128 blocks (8192 columns) per row
-        std::vector<int32_t> bp((size_t)H->bsr.n_block_rows + 1);
-        cudaStream_t s0 = as_stream(stream);
-        CHFSI_CUDA_TRY(cudaMemcpyAsync(bp.data(), H->bsr.brow_ptr, sizeof(int32_t) * bp.size(), cudaMemcpyDeviceToHost,
-                                       s0));
-        CHFSI_CUDA_TRY(cudaStreamSynchronize(s0));
-        for (size_t r = 0; r + 1 < bp.size(); r++)
-            if (bp[r + 1] - bp[r] > 128) return CHFSI_ERR_UNSUPPORTED;
+        bool fit = false;
+        if ((rc = bsr_rows_fit_ozaki(H, as_stream(stream), &fit))) return rc;
+        if (!fit) return CHFSI_ERR_UNSUPPORTED;
     }
 
     std::vector<double> al, be;
@@ -786,8 +797,15 @@ size_t rr_ozaki_bytes(int64_t N, int64_t n, int64_t nnz, bool csr) {
     return b;
 }
 
+// Scratch of the Ozaki closure's H X_F as an Ozaki BSR step (operators with 64 x 64
+// blocks), 0 otherwise.
+size_t rr_bsr_ozaki_bytes(const chfsi_matrix* H, int64_t n, int precision) {
+    if (precision != CHFSI_F64_OZAKI || !has_bsr(H) || H->bsr.bdim != 64) return 0;
+    return ozaki_bsr_bytes(H->bsr.n_block_rows, H->bsr.n_blocks, n);
+}
+
 template <typename Ar>
-void rr_layout(Ar& ar, int64_t N, int64_t n, int precision, int64_t nnz, bool csr, RRLayout* out) {
+void rr_layout(Ar& ar, int64_t N, int64_t n, int precision, int64_t nnz, bool csr, size_t bsr_oz, RRLayout* out) {
     RRLayout rl;
     const int64_t ldw = pad8(n);
     rl.splits = gemm_tn_splits(N, n);
@@ -810,7 +828,7 @@ void rr_layout(Ar& ar, int64_t N, int64_t n, int precision, int64_t nnz, bool cs
         rl.T = ar.template take<double>((size_t)(N * ldw));
     }
     if (precision == CHFSI_F64_OZAKI) {
-        rl.oz_bytes = rr_ozaki_bytes(N, n, nnz, csr);
+        rl.oz_bytes = std::max(rr_ozaki_bytes(N, n, nnz, csr), bsr_oz);
         rl.oz = ar.template take<unsigned char>(rl.oz_bytes);
     }
     if (out) *out = rl;
@@ -881,7 +899,8 @@ int rr_run_f32x2(const chfsi_matrix* H, const double* Y, int64_t ldy, int64_t N,
 // H X_F in two-float arithmetic (FP64 on a BSR-only operator); the Cholesky
 // factorisation, the triangular inverse and the eigensolve stay FP64.
 int rr_run_ozaki(const chfsi_matrix* H, const double* Y, int64_t ldy, int64_t N, int64_t n, double* Psi,
-                 int64_t ldpsi, double* ritz, int passes, const RRLayout& rl, unsigned* st, cudaStream_t s) {
+                 int64_t ldpsi, double* ritz, int passes, bool bsr_hx, const RRLayout& rl, unsigned* st,
+                 cudaStream_t s) {
     const int64_t ldw = pad8(n);
     int rc;
     const double* cur = Y;
@@ -902,7 +921,15 @@ int rr_run_ozaki(const chfsi_matrix* H, const double* Y, int64_t ldy, int64_t N,
     }
     double* XF = const_cast<double*>(cur);
     double* HXF = bufs[which];
-    if (has_csr(H)) {
+    if (bsr_hx) {
+        // H's 64 x 64 blocks as Ozaki products (the BSR step with alpha = 1, c = 0)
+        CsrDev csr{};
+        BsrDev bsr{};
+        make_devs(H, H->csr.val, H->bsr.val, Buf::F64, &csr, &bsr);
+        if ((rc = ozaki_bsr_prepare(bsr, n, rl.oz, rl.oz_bytes, st, s))) return rc;
+        if ((rc = ozaki_bsr_step(bsr, n, XF, ldw, nullptr, 0, HXF, ldw, 1.0, 0.0, 0.0, rl.oz, rl.oz_bytes, st, s)))
+            return rc;
+    } else if (has_csr(H)) {
         Arena ar(rl.oz, rl.oz_bytes);
         float2* X2 = ar.take<float2>((size_t)(N * ldw));
         float2* HX2 = ar.take<float2>((size_t)(N * ldw));
@@ -940,7 +967,8 @@ int chfsi_rayleigh_ritz_ex_workspace_size(const chfsi_matrix* H, int64_t n_cols,
     int rc = rr_check(H, n_cols, cholqr_passes, precision, &N);
     if (rc) return rc;
     SizeOnly sz;
-    rr_layout(sz, N, n_cols, precision, has_csr(H) ? H->csr.nnz : 0, has_csr(H), nullptr);
+    rr_layout(sz, N, n_cols, precision, has_csr(H) ? H->csr.nnz : 0, has_csr(H), rr_bsr_ozaki_bytes(H, n_cols, precision),
+              nullptr);
     *bytes = sz.used;
     return CHFSI_OK;
 }
@@ -960,18 +988,22 @@ int chfsi_rayleigh_ritz_ex(const chfsi_matrix* H, const double* Y, int64_t ldy, 
     if (!ws || !aligned16(ws)) return CHFSI_ERR_ARG;
     const int64_t nnz = has_csr(H) ? H->csr.nnz : 0;
     SizeOnly sz;
-    rr_layout(sz, N, n_cols, precision, nnz, has_csr(H), nullptr);
+    const size_t bsr_oz = rr_bsr_ozaki_bytes(H, n_cols, precision);
+    rr_layout(sz, N, n_cols, precision, nnz, has_csr(H), bsr_oz, nullptr);
     if (ws_bytes < sz.used) return CHFSI_ERR_NOMEM;
     Arena ar(ws, ws_bytes);
     RRLayout rl;
-    rr_layout(ar, N, n_cols, precision, nnz, has_csr(H), &rl);
+    rr_layout(ar, N, n_cols, precision, nnz, has_csr(H), bsr_oz, &rl);
     cudaStream_t s = as_stream(stream);
     unsigned* st = status_word(ws);
     CHFSI_CUDA_TRY(cudaMemsetAsync(st, 0, sizeof(unsigned), s));
     const int64_t n = n_cols, ldw = pad8(n);
     if (precision == CHFSI_F32X2) return rr_run_f32x2(H, Y, ldy, N, n, Psi, ldpsi, ritz, cholqr_passes, rl, st, s);
-    if (precision == CHFSI_F64_OZAKI)
-        return rr_run_ozaki(H, Y, ldy, N, n, Psi, ldpsi, ritz, cholqr_passes, rl, st, s);
+    if (precision == CHFSI_F64_OZAKI) {
+        bool bsr_hx = false;
+        if (bsr_oz && (rc = bsr_rows_fit_ozaki(H, s, &bsr_hx))) return rc;
+        return rr_run_ozaki(H, Y, ldy, N, n, Psi, ldpsi, ritz, cholqr_passes, bsr_hx, rl, st, s);
+    }
 
     // step 2: X_F = Y R^-1 with S = Y^T Y = R^T R (repeated on X_F for CholQR2)
     const double* cur = Y;

@@ -312,3 +312,23 @@ def test_bsr_ozaki_filter_many_blocks(P, oracle_mod):
     assert P.read_status(ws) == 0
     Y = _unpermute(Yb.cpu().numpy(), B["perm"])
     assert rel_fro(Y, oracle_mod.filter(H, X, m, a, b, a0)) <= 1e-12
+
+
+def test_rayleigh_ritz_ozaki_hybrid_uses_block_products(P, oracle_mod):
+    """The Ozaki closure on a hybrid operator (its H X_F as an Ozaki BSR step on the 64 x 64
+    blocks, rows in the blocked order) against the oracle's closure on the original
+    operator: the Ritz values do not depend on the row order."""
+    g, w, n, m = 12, 3, 90, 8
+    H = W.csr_grid(g, w, 0.1, 61)
+    X = W.start_block(H["N"], n, 62)
+    a, b, a0 = oracle_mod.lanczos_bounds(H, W.lanczos_start(H["N"], 63), 20, n)
+    Yref = oracle_mod.filter(H, X, m, a, b, a0)
+    theta, _, _ = oracle_mod.rayleigh_ritz(H, Yref)
+    B = W.bsr_from_csr(H, g)
+    Hp = W.permute_csr(H, B["perm"])
+    Hy = P.HybridMatrix(P.CsrMatrix.from_arrays(Hp["row_ptr"], Hp["col"], Hp["val"], device="cuda"), _bsr_dev(P, B))
+    Yb = P.filter(Hy, _dev(X[B["perm"]]), m, a, b, a0, schedule=["ozaki"] * m)
+    ritz, psi = P.rayleigh_ritz(Hy, Yb, cholqr_passes=2, precision="ozaki")
+    assert np.max(np.abs(ritz.cpu().numpy() - theta)) <= 1e-10 * np.max(np.abs(theta))
+    p = psi.cpu().numpy()
+    assert np.max(np.abs(p.T @ p - np.eye(n))) <= 1e-12
