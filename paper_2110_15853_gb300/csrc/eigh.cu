@@ -66,10 +66,13 @@ __device__ double block_sum(double v) {
 // and sums the squares of the next reflector's row, A[j+1][j+3:].  The two sums are
 // reduced in block order by the last block to finish (a completion counter, no
 // waiting), so the results do not depend on the blocks' timing.
+constexpr int kPanel32 = 32;   // columns per panel of the blocked tridiagonalisation
+
 struct TriScalars {
     double sumsq;            // sum_{i>=1} x_i^2 of the current reflector's row
-    double dot;              // p . v of the current column
+    double dot;              // p . v of the current column (blocked: (tau / 2) p . v)
     unsigned cnt_a, cnt_b;   // completion counters of the two kernels
+    double c12[2 * kPanel32];   // blocked: W_t . v (t < i), then V_t . v
 };
 
 // Sum of the nparts partial sums written by the other blocks (called by the whole block
@@ -221,6 +224,193 @@ __global__ void __launch_bounds__(256) tri_update_kernel(double* A, int64_t lda,
                 tri->sumsq = tot;
                 tri->cnt_b = 0;
             }
+        }
+    }
+}
+
+// ---- blocked tridiagonalisation (n >= kBlockedMinN)
+// A panel reduces kPanel32 columns j0 .. j0 + 31 against the trailing matrix as it stood at
+// the panel's start (A0); the reflectors v_t and the vectors w_t of the panel's columns
+// are kept as rows of PV = [V; W; V] (length n each, zero left of their column), so that
+// the matrix current at column j is A0 - sum_t (v_t w_t^T + w_t v_t^T).  Per column
+// j = j0 + i: the row kernel brings row j up to date (and writes the previous column's
+// v, w rows of PV); the product kernel forms y = A0[j+1:, j+1:] v (the only pass over the
+// trailing matrix) and the dots W_t . v, V_t . v; the p kernel corrects
+// p = tau (y - V (W^T v) - W (V^T v)) and stores v in A's row j.  After the panel the
+// trailing matrix takes A -= V^T W + W^T V in one product of depth 2 * 32.
+
+// Writes rows i of V, W (both copies of V) for the column jc whose v and p are in vbuf and
+// pbuf and whose (tau / 2) p . v is kw: v_c, and w_c = p_c - kw v_c, for c in [c0, n).
+__device__ __forceinline__ void blk_store_vw(double* PV, int64_t n, int i, int64_t c, const double* vbuf,
+                                             const double* pbuf, double kw, double* vo, double* wo) {
+    const double v = vbuf[c];
+    const double w = pbuf[c] - kw * v;
+    PV[(int64_t)i * n + c] = v;
+    PV[(int64_t)(kPanel32 + i) * n + c] = w;
+    PV[(int64_t)(2 * kPanel32 + i) * n + c] = v;
+    *vo = v;
+    *wo = w;
+}
+
+// Row j = j0 + i brought up to date over columns c in [j, n):
+// a_c = A0[j][c] - sum_{t < i} (V_t[j] W_t[c] + W_t[j] V_t[c]); for i >= 1 the previous
+// column's rows of V and W are written first (from vbuf, pbuf, tri->dot).  The sum of
+// squares of a_c for c >= j + 2 (the next reflector's row past x_0) goes to tri->sumsq.
+__global__ void __launch_bounds__(256) blk_row_kernel(double* A, int64_t lda, int64_t n, int64_t j, int i,
+                                                      double* PV, TriScalars* tri, double* part,
+                                                      const double* __restrict__ vbuf,
+                                                      const double* __restrict__ pbuf) {
+    __shared__ double cv[kPanel32], cw[kPanel32];
+    const double kw = tri->dot;
+    if (threadIdx.x < i) {
+        const int t = threadIdx.x;
+        if (t == i - 1) {   // the previous column's entries at row j, from its vbuf / pbuf
+            cv[t] = vbuf[j];
+            cw[t] = pbuf[j] - kw * vbuf[j];
+        } else {
+            cv[t] = PV[(int64_t)t * n + j];
+            cw[t] = PV[(int64_t)(kPanel32 + t) * n + j];
+        }
+    }
+    __syncthreads();
+    const int64_t c = j + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double sq = 0.0;
+    if (c < n) {
+        double a = A[j * lda + c];
+        for (int t = 0; t < i; t++) {
+            double vt, wt;
+            if (t == i - 1) blk_store_vw(PV, n, t, c, vbuf, pbuf, kw, &vt, &wt);
+            else {
+                vt = PV[(int64_t)t * n + c];
+                wt = PV[(int64_t)(kPanel32 + t) * n + c];
+            }
+            a -= cv[t] * wt + cw[t] * vt;
+        }
+        A[j * lda + c] = a;
+        if (c >= j + 2) sq = a * a;
+    }
+    __shared__ bool last;
+    const double bs = block_sum(sq);
+    if (threadIdx.x == 0) {
+        part[blockIdx.x] = bs;
+        __threadfence();
+        last = atomicAdd(&tri->cnt_b, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (last) {
+        const double tot = last_block_sum(part, gridDim.x);
+        if (threadIdx.x == 0) {
+            tri->sumsq = tot;
+            tri->cnt_b = 0;
+        }
+    }
+}
+
+// The rows i of V and W for the panel's last column jc (before the trailing update):
+// c in [jc + 1, n).
+__global__ void blk_finish_kernel(double* PV, int64_t n, int64_t jc, int i, const TriScalars* tri,
+                                  const double* __restrict__ vbuf, const double* __restrict__ pbuf) {
+    const int64_t c = jc + 1 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n) return;
+    double v, w;
+    blk_store_vw(PV, n, i, c, vbuf, pbuf, tri->dot, &v, &w);
+}
+
+// y = A0[j+1:, j+1:] v (one warp per row, blocks 0 .. nsymv-1; y stored unscaled) for the
+// reflector of row j (formed in every block from x_0 and tri->sumsq, as in the unblocked
+// product), and in blocks nsymv .. nsymv + 2i - 1 the dots W_t . v (t < i) and V_t . v.
+// Block 0 also writes v (vbuf) and d[j], e[j], tau[j].
+__global__ void __launch_bounds__(32 * kTriRows) blk_product_kernel(const double* __restrict__ A, int64_t lda,
+                                                                    int64_t n, int64_t j, int i,
+                                                                    const double* __restrict__ PV, TriScalars* tri,
+                                                                    double* d, double* e, double* tau, double* vbuf,
+                                                                    double* ybuf, unsigned nsymv) {
+    const int64_t m = n - j - 1;
+    const double* x = A + j * lda + j + 1;
+    double beta, t, scale;
+    reflector(x[0], tri->sumsq, beta, t, scale);
+    auto v_at = [&](int64_t q) { return q == 0 ? 1.0 : x[q] * scale; };
+    if (blockIdx.x >= nsymv) {   // block-uniform: one dot product per block
+        const int tp = (int)(blockIdx.x - nsymv);
+        const double* row = tp < i ? PV + (int64_t)(kPanel32 + tp) * n : PV + (int64_t)(tp - i) * n;
+        double acc = 0.0;
+        for (int64_t q = threadIdx.x; q < m; q += blockDim.x) acc = fma(row[j + 1 + q], v_at(q), acc);
+        acc = block_sum(acc);
+        if (threadIdx.x == 0) tri->c12[tp] = acc;
+        return;
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t r = (int64_t)blockIdx.x * kTriRows + warp;
+    if (r < m) {
+        const double* arow = A + (j + 1 + r) * lda + j + 1;
+        double acc[kTriUnroll];
+#pragma unroll
+        for (int q = 0; q < kTriUnroll; q++) acc[q] = 0.0;
+        int64_t q0 = lane;
+        for (; q0 + 32 * (kTriUnroll - 1) < m; q0 += 32 * kTriUnroll) {
+            double rv[kTriUnroll];
+#pragma unroll
+            for (int q = 0; q < kTriUnroll; q++) rv[q] = arow[q0 + 32 * q];
+#pragma unroll
+            for (int q = 0; q < kTriUnroll; q++) acc[q] = fma(rv[q], v_at(q0 + 32 * q), acc[q]);
+        }
+        for (; q0 < m; q0 += 32) acc[0] = fma(arow[q0], v_at(q0), acc[0]);
+#pragma unroll
+        for (int w = kTriUnroll / 2; w > 0; w /= 2)
+#pragma unroll
+            for (int q = 0; q < w; q++) acc[q] += acc[q + w];
+        const double y = warp_sum(acc[0]);
+        if (lane == 0) ybuf[j + 1 + r] = y;
+    }
+    if (blockIdx.x == 0) {
+        for (int64_t q = threadIdx.x; q < m; q += blockDim.x) vbuf[j + 1 + q] = v_at(q);
+        if (threadIdx.x == 0) {
+            d[j] = A[j * lda + j];
+            e[j] = beta;
+            tau[j] = t;
+        }
+    }
+}
+
+// p = tau (y - sum_t (V_t W_t . v + W_t V_t . v)) over rows r in [j+1, n), v stored in A's
+// row j for the back-transformation, and (tau / 2) p . v to tri->dot (reduced in a fixed
+// order by the last block to finish).
+__global__ void __launch_bounds__(256) blk_p_kernel(double* A, int64_t lda, int64_t n, int64_t j, int i,
+                                                    const double* __restrict__ PV, TriScalars* tri, double* part,
+                                                    const double* __restrict__ tau, const double* __restrict__ vbuf,
+                                                    const double* __restrict__ ybuf, double* pbuf) {
+    __shared__ double c1[kPanel32], c2[kPanel32];
+    if (threadIdx.x < 2 * i) {
+        if ((int)threadIdx.x < i) c1[threadIdx.x] = tri->c12[threadIdx.x];
+        else c2[threadIdx.x - i] = tri->c12[threadIdx.x];
+    }
+    __syncthreads();
+    const double tj = tau[j];
+    const int64_t r = j + 1 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double pv = 0.0;
+    if (r < n) {
+        double y = ybuf[r];
+        for (int t = 0; t < i; t++)
+            y -= PV[(int64_t)t * n + r] * c1[t] + PV[(int64_t)(kPanel32 + t) * n + r] * c2[t];
+        const double pr = tj * y;
+        pbuf[r] = pr;
+        const double v = vbuf[r];
+        pv = pr * v;
+        A[j * lda + r] = v;
+    }
+    __shared__ bool last;
+    const double bs = block_sum(pv);
+    if (threadIdx.x == 0) {
+        part[blockIdx.x] = bs;
+        __threadfence();
+        last = atomicAdd(&tri->cnt_a, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (last) {
+        const double tot = last_block_sum(part, gridDim.x);
+        if (threadIdx.x == 0) {
+            tri->dot = 0.5 * tj * tot;
+            tri->cnt_a = 0;
         }
     }
 }
@@ -732,9 +922,11 @@ inline int64_t round8(int64_t x) { return (x + 7) / 8 * 8; }
 // 8192), otherwise as FP64 products on the DFMA pipe (small n: a few tiles, where the
 // slicing passes would cost more than they save).
 constexpr int64_t kOzakiMinN = 256, kOzakiMaxN = 8192;
+constexpr int64_t kBlockedMinN = 2048;   // the blocked tridiagonalisation from this n on
 
 struct EighBufs {
     double *d, *e, *tau, *ebak, *vbuf, *pbuf, *part_a, *part_b;
+    double *PV, *ybuf;      // blocked tridiagonalisation: [V; W; V] of a panel, y = A0 v
     TriScalars* tri;
     MergeBufs mb;
     double *Vp, *Gv, *T, *W1, *W2;
@@ -760,6 +952,8 @@ void eigh_layout(Ar& ar, int64_t n, EighBufs* out) {
     u.part_a = ar.template take<double>((size_t)(n / kTriRows + 1));
     u.part_b = ar.template take<double>((size_t)(n / 256 + 1));
     u.tri = ar.template take<TriScalars>(1);
+    u.PV = ar.template take<double>((size_t)(3 * kPanel32) * n);
+    u.ybuf = ar.template take<double>(n);
     MergeBufs& b = u.mb;
     b.D = ar.template take<double>(n);
     b.z = ar.template take<double>(n);
@@ -830,12 +1024,51 @@ int eigh(double* A, int64_t lda, int64_t n, double* w, double* Q, int64_t ldq, v
     MergeBufs& mb = u.mb;
     const bool oz = u.oz != nullptr;
 
-    // 1. tridiagonalisation, two launches per column
-    if (n >= 3) {
+    // 1. tridiagonalisation: blocked for large n (one pass over the trailing matrix per
+    // column plus one product per panel), else two launches per column
+    if (n >= kBlockedMinN) {
+        CHFSI_CUDA_TRY(cudaMemsetAsync(u.tri, 0, sizeof(TriScalars), s));
+        for (int64_t j0 = 0; j0 + 2 < n; j0 += kPanel32) {
+            const int nc = (int)std::min<int64_t>(kPanel32, (n - 2) - j0);
+            if (nc < kPanel32)   // rows nc .. 31 of V and W take part in the trailing product
+                CHFSI_CUDA_TRY(cudaMemsetAsync(u.PV, 0, sizeof(double) * (size_t)(3 * kPanel32) * n, s));
+            for (int i = 0; i < nc; i++) {
+                const int64_t j = j0 + i, m = n - j - 1;
+                blk_row_kernel<<<(unsigned)((n - j + 255) / 256), 256, 0, s>>>(A, lda, n, j, i, u.PV, u.tri,
+                                                                               u.part_b, u.vbuf, u.pbuf);
+                CHFSI_LAUNCH_CHECK();
+                const unsigned nsymv = (unsigned)((m + kTriRows - 1) / kTriRows);
+                blk_product_kernel<<<nsymv + 2 * i, 32 * kTriRows, 0, s>>>(A, lda, n, j, i, u.PV, u.tri, d, e, tau,
+                                                                          u.vbuf, u.ybuf, nsymv);
+                CHFSI_LAUNCH_CHECK();
+                blk_p_kernel<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(A, lda, n, j, i, u.PV, u.tri, u.part_a, tau,
+                                                                         u.vbuf, u.ybuf, u.pbuf);
+                CHFSI_LAUNCH_CHECK();
+            }
+            const int64_t jl = j0 + nc - 1, jn = j0 + nc, mp = n - jn;
+            blk_finish_kernel<<<(unsigned)((n - jl - 1 + 255) / 256), 256, 0, s>>>(u.PV, n, jl, nc - 1, u.tri, u.vbuf,
+                                                                                   u.pbuf);
+            CHFSI_LAUNCH_CHECK();
+            // trailing matrix: A[jn:, jn:] -= V^T W + W^T V over the panel's rows of PV
+            const double* Vop = u.PV + jn;
+            const double* Wop = u.PV + (int64_t)kPanel32 * n + jn;
+            double* C22 = A + jn * lda + jn;
+            int rc;
+            if (oz && mp >= kOzakiMinN) {
+                if ((rc = ozaki_gemm_tn(Vop, n, Wop, n, 2 * kPanel32, mp, mp, mb.G, mp, true, u.oz, u.oz_bytes, status,
+                                        s)))
+                    return rc;
+                sub_block_kernel<<<(unsigned)((mp * mp + 255) / 256), 256, 0, s>>>(C22, lda, mb.G, mp, mp);
+                CHFSI_LAUNCH_CHECK();
+            } else if ((rc = gemm_general(Vop, n, true, Wop, n, C22, lda, mp, mp, 2 * kPanel32, -1.0, true, s))) {
+                return rc;
+            }
+        }
+    } else if (n >= 3) {
         tri_init_kernel<<<1, 1024, 0, s>>>(A, n, u.tri);
         CHFSI_LAUNCH_CHECK();
     }
-    for (int64_t j = 0; j + 2 < n; j++) {
+    for (int64_t j = 0; n < kBlockedMinN && j + 2 < n; j++) {
         const int64_t m = n - j - 1;
         tri_product_kernel<<<(unsigned)((m + kTriRows - 1) / kTriRows), 32 * kTriRows, 0, s>>>(
             A, lda, n, j, u.tri, u.part_a, d, e, tau, u.vbuf, u.pbuf);

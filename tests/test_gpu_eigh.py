@@ -63,3 +63,21 @@ def test_eigh_zero_matrix(P):
     w, Q = P.eigh(torch.zeros(40, 40, dtype=torch.float64, device="cuda"))
     assert torch.all(w == 0)
     assert np.max(np.abs(Q.cpu().numpy().T @ Q.cpu().numpy() - np.eye(40))) <= 1e-12
+
+
+@pytest.mark.parametrize("n", [2048, 2100])
+def test_eigh_blocked_tridiagonalisation(P, n):
+    """n >= 2048 takes the blocked tridiagonalisation (panels of 32 reflectors, the
+    trailing matrix updated once per panel): random symmetric matrices, a full panel
+    count (2048) and a ragged last panel (2100)."""
+    rng = np.random.default_rng(n)
+    A = rng.standard_normal((n, n))
+    _check(P, (A + A.T) / 2)
+
+
+def test_eigh_blocked_clustered(P):
+    rng = np.random.default_rng(11)
+    n = 2200
+    Qr, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    lam = np.repeat(np.linspace(-3.0, 1.0, n // 8), 8) + 1e-12 * rng.standard_normal(n)
+    _check(P, (Qr * lam) @ Qr.T)
