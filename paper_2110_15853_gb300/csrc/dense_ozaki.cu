@@ -58,17 +58,25 @@ using namespace tc;
 constexpr int kSlices = 7;
 constexpr int kPairs = kSlices * (kSlices + 1) / 2;   // slice pairs with t + u <= 8 (1-based)
 constexpr int kAccs = 7;                              // E2 .. E8
-constexpr int kMaxItemKB = 256;                       // K-blocks per work item (8192 K)
 constexpr int kTileM = 128;                           // output rows per tile (TMEM lanes)
 constexpr int kTileN = 64;                            // output columns per tile
 constexpr int kRowPad = 128;                          // operand rows are padded to this
-constexpr int kKB = 32;                               // K per stage (64-byte rows)
-constexpr int kSliceA = kTileM * kKB * 2;             // 8 KB
-constexpr int kSliceB = kTileN * kKB * 2;             // 4 KB
+// K per stage (a K-block): 32 BF16 = 64-byte rows under the 64-byte swizzle; a stage of
+// 7 + 7 slice tiles is 84 KB and two fit in shared memory.  K-blocks of 16 (32-byte
+// swizzle, 42 KB stages, five of them) measured slower: 114.7 against 98.4 ms for the
+// 20-step BSR filter at 40^3 with 1024 states, since the MMAs of one group that overlap
+// the other group's drain halve with the stage.
+constexpr int kKB = 32;
+constexpr int kSwizzleBytes = 2 * kKB;
+constexpr int kMaxItemKB = 8192 / kKB;                // K-blocks per work item (8192 K)
+constexpr int kBlockKB = 64 / kKB;                    // K-blocks per 64-wide BSR block
+constexpr int kSliceA = kTileM * kKB * 2;             // 4 KB
+constexpr int kSliceB = kTileN * kKB * 2;             // 2 KB
 constexpr int kStageBytes = kSlices * (kSliceA + kSliceB);
-constexpr int kStages = 2;
-constexpr int kPeriodX = 8;                           // K-blocks between drains of group X (256 K)
-constexpr int kPeriodY = 4;                           // K-blocks between drains of group Y (128 K)
+constexpr int kStages = (224 * 1024) / kStageBytes;
+constexpr int kPeriodX = 256 / kKB;                   // K-blocks between drains of group X (256 K)
+constexpr int kPeriodY = 128 / kKB;                   // K-blocks between drains of group Y (128 K)
+constexpr CUtensorMapSwizzle kTmaSwizzle = kKB == 16 ? CU_TENSOR_MAP_SWIZZLE_32B : CU_TENSOR_MAP_SWIZZLE_64B;
 constexpr int kEpiWarps = 16;
 constexpr int kColsPerThread = kTileN / (kEpiWarps / 4);   // 16
 constexpr int kThreads = 32 * (2 + kEpiWarps);
@@ -77,7 +85,8 @@ constexpr uint32_t kTmemCols = 512;
 constexpr int kXEvent = 1, kYEvent = 2, kFullEvent = 3;
 static_assert(kSmemBytes + 1024 <= 227 * 1024, "shared memory per CTA");
 static_assert(kAccs * kTileN <= (int)kTmemCols, "seven accumulators in TMEM");
-static_assert(kSliceB % 512 == 0 && kStageBytes % 1024 == 0, "swizzle-atom alignment of the tiles");
+static_assert(kSliceB % (8 * kSwizzleBytes) == 0 && kStageBytes % 1024 == 0, "swizzle-atom alignment of the tiles");
+static_assert(kKB == 16 || kKB == 32, "K-block of one or two 16-wide MMA steps");
 static_assert(kColsPerThread == 16, "16-column TMEM loads");
 
 // The 28 slice pairs (t, u), 0-based, with t + u <= 6 go to accumulator t + u (level
@@ -144,14 +153,14 @@ struct Item {
     int qb;                   // BSR mode: first block of the row
 };
 
-// Stored block range of block row R, clamped to [0, nblocks] and to kMaxItemKB / 2
+// Stored block range of block row R, clamped to [0, nblocks] and to kMaxItemKB / kBlockKB
 // blocks (the host rejects longer rows); `bad` is set for a malformed row pointer.
 __device__ __forceinline__ void bsr_row_range(const OzArgs& g, int64_t R, int& qb, int& nq, bool& bad) {
     int b0 = g.brow_ptr[R], b1 = g.brow_ptr[R + 1];
     if (b0 < 0) { b0 = 0; bad = true; }
     if (b1 > g.nblocks) { b1 = (int)g.nblocks; bad = true; }
     if (b1 < b0) { b1 = b0; bad = true; }
-    if (b1 - b0 > kMaxItemKB / 2) { b1 = b0 + kMaxItemKB / 2; bad = true; }
+    if (b1 - b0 > kMaxItemKB / kBlockKB) { b1 = b0 + kMaxItemKB / kBlockKB; bad = true; }
     qb = b0;
     nq = b1 - b0;
 }
@@ -173,7 +182,7 @@ __device__ __forceinline__ Item decode(const OzArgs& g, int64_t item) {
         it.tm = (int)(item % g.tilesM);
         it.tn = (int)R;
         it.kb0 = 0;
-        it.KB = 2 * nq;
+        it.KB = kBlockKB * nq;
         return it;
     }
     it.qb = 0;
@@ -292,7 +301,7 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                 int xa = (it.kb0 + kb) * kKB, xb = xa;
                 int64_t rb = it.batch * g.b_batch_rows + (int64_t)it.tn * kTileN;
                 if (kBsr) {
-                    const int q = it.qb + kb / 2, half = kb & 1;
+                    const int q = it.qb + kb / kBlockKB, half = kb % kBlockKB;
                     int C = g.bcol[q];
                     if (C < 0 || (int64_t)C >= g.nbr) { C = 0; bad_pattern = true; }   // still a valid tile
                     xa = C * 64 + half * kKB;
@@ -350,8 +359,8 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                     for (int q = q0; q < q1; q++) {
                         const int t = kMmaT[q], u0 = kMmaU[q], c = kMmaC[q];
                         const bool first = (q == 0 || q == kMmaX) && (q < kMmaX ? resetX : resetY);
-                        const uint64_t da = desc_kmajor(st + t * kSliceA, 64);
-                        const uint64_t db = desc_kmajor(st + kSlices * kSliceA + u0 * kSliceB, 64);
+                        const uint64_t da = desc_kmajor(st + t * kSliceA, kSwizzleBytes);
+                        const uint64_t db = desc_kmajor(st + kSlices * kSliceA + u0 * kSliceB, kSwizzleBytes);
                         const uint32_t dt = tmem + (uint32_t)((t + u0) * kTileN);
                         const uint32_t idesc = idesc_bf16(kTileM, kTileN * c);
 #pragma unroll
@@ -663,7 +672,7 @@ void oz_operand_layout(Ar& ar, int64_t rows, int64_t K, int nbatch, int64_t row_
     o.K = K;
     o.nbatch = nbatch;
     o.rows_pad = round_up(rows, row_pad);
-    o.K_pad = round_up(K, kKB);
+    o.K_pad = round_up(K, 32);   // the slicing kernel's tiles are 32 wide in K
     o.exps = ar.template take<int>((size_t)o.plane_rows());
     o.slices = ar.template take<__nv_bfloat16>((size_t)kSlices * o.plane_rows() * o.K_pad);
     if (op) *op = o;
@@ -698,11 +707,12 @@ int oz_prepare(const double* src, int64_t ld, bool trans, const OzOperand& o, in
 
 // Split-K count for a product whose output has `tiles` tiles: at most kMaxItemKB
 // K-blocks per work item (the range of the 64-bit accumulators), and enough items
-// for about one per SM while each split keeps at least 64 K-blocks (2048 K).
+// for about one per SM while each split keeps at least 2048 K.
 int oz_splits(int64_t tiles, int kb_total, int sms) {
     const int64_t need = (kb_total + kMaxItemKB - 1) / kMaxItemKB;
     int64_t want = (sms + tiles - 1) / tiles;
-    const int64_t maxs = (kb_total + 63) / 64;
+    constexpr int64_t kMinSplitKB = 2048 / kKB;
+    const int64_t maxs = (kb_total + kMinSplitKB - 1) / kMinSplitKB;
     if (want > maxs) want = maxs;
     const int64_t sp = want > need ? want : need;
     return (int)(sp < 1 ? 1 : sp);
@@ -768,10 +778,10 @@ int oz_run(const OzPlan& p, bool tn_form, double* C, int64_t ldc, int64_t M, int
     CUtensorMap tmA, tmB;
     int rc;
     if ((rc = make_map_bf16(&tmA, p.A.slices, K_pad, kSlices * p.A.plane_rows(), kKB, kTileM,
-                            CU_TENSOR_MAP_SWIZZLE_64B)))
+                            kTmaSwizzle)))
         return rc;
     if ((rc = make_map_bf16(&tmB, p.B.slices, K_pad, kSlices * p.B.plane_rows(), kKB, kTileN,
-                            CU_TENSOR_MAP_SWIZZLE_64B)))
+                            kTmaSwizzle)))
         return rc;
     OzArgs g{};
     const int64_t mb = nbatch > 1 ? m_batch : M;
@@ -920,10 +930,10 @@ int ozaki_bsr_step(const BsrDev& h, int64_t n, const double* Yc, int64_t ldc, co
     if ((rc = oz_prepare(Yc, ldc, true, b.Y, N, 0, status, s))) return rc;
     CUtensorMap tmA, tmB;
     if ((rc = make_map_bf16(&tmA, b.Y.slices, b.Y.K_pad, kSlices * b.Y.plane_rows(), kKB, kTileM,
-                            CU_TENSOR_MAP_SWIZZLE_64B)))
+                            kTmaSwizzle)))
         return rc;
     if ((rc = make_map_bf16(&tmB, b.H.slices, b.H.K_pad, kSlices * b.H.plane_rows(), kKB, kTileN,
-                            CU_TENSOR_MAP_SWIZZLE_64B)))
+                            kTmaSwizzle)))
         return rc;
     OzArgs g{};
     g.M = n;

@@ -66,15 +66,16 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
 }
 
 // UMMA shared-memory descriptor of a K-major operand tile written by TMA with a
-// 128-byte (rows of 64 BF16, 8-row atoms of 1024 B) or 64-byte (rows of 32 BF16,
-// 8-row atoms of 512 B) swizzle.
+// 128-byte (rows of 64 BF16, 8-row atoms of 1024 B), 64-byte (rows of 32 BF16, atoms of
+// 512 B) or 32-byte (rows of 16 BF16, atoms of 256 B) swizzle.
 __device__ __forceinline__ uint64_t desc_kmajor(uint32_t addr, int swizzle_bytes) {
     uint64_t d = 0;
     d |= (uint64_t)((addr & 0x3FFFF) >> 4);                      // start address
     d |= (uint64_t)1 << 16;                                      // leading byte offset (unused when swizzled)
     d |= (uint64_t)((8 * swizzle_bytes) >> 4) << 32;             // stride byte offset: one 8-row atom
     d |= (uint64_t)1 << 46;                                      // descriptor version
-    d |= (uint64_t)(swizzle_bytes == 128 ? 2 : 4) << 61;         // 128-byte or 64-byte swizzle
+    const uint64_t layout = swizzle_bytes == 128 ? 2 : (swizzle_bytes == 64 ? 4 : 6);
+    d |= layout << 61;                                           // swizzle mode
     return d;
 }
 
@@ -102,7 +103,8 @@ inline EncodeTiledFn encode_fn() {
 }
 
 // 2-D BF16 tensor map over a row-major [rows x cols] array with a [box_rows x box_cols]
-// box and the given swizzle (box_cols * 2 bytes must equal the swizzle width).
+// box and the given swizzle (box_cols * 2 bytes must equal the swizzle width: 32, 64 or
+// 128 bytes).
 inline int make_map_bf16(CUtensorMap* map, const void* base, int64_t cols, int64_t rows, int box_cols, int box_rows,
                          CUtensorMapSwizzle swizzle) {
     EncodeTiledFn enc = encode_fn();
