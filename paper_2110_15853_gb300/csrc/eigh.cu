@@ -342,19 +342,35 @@ __global__ void __launch_bounds__(32 * kTriRows) blk_product_kernel(const double
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t r = (int64_t)blockIdx.x * kTriRows + warp;
     if (r < m) {
+        // 16-byte loads of the row (two entries a lane), after one peeled entry when the
+        // row segment does not start on a 16-byte boundary
         const double* arow = A + (j + 1 + r) * lda + j + 1;
+        const int64_t head = (reinterpret_cast<uintptr_t>(arow) & 15u) ? 1 : 0;
+        const int64_t m2 = (m - head) / 2;
+        const double2* a2 = reinterpret_cast<const double2*>(arow + head);
         double acc[kTriUnroll];
 #pragma unroll
         for (int q = 0; q < kTriUnroll; q++) acc[q] = 0.0;
+        if (head && lane == 0) acc[0] = arow[0] * v_at(0);
         int64_t q0 = lane;
-        for (; q0 + 32 * (kTriUnroll - 1) < m; q0 += 32 * kTriUnroll) {
-            double rv[kTriUnroll];
+        for (; q0 + 32 * (kTriUnroll - 1) < m2; q0 += 32 * kTriUnroll) {
+            double2 rv[kTriUnroll];
 #pragma unroll
-            for (int q = 0; q < kTriUnroll; q++) rv[q] = arow[q0 + 32 * q];
+            for (int q = 0; q < kTriUnroll; q++) rv[q] = a2[q0 + 32 * q];
 #pragma unroll
-            for (int q = 0; q < kTriUnroll; q++) acc[q] = fma(rv[q], v_at(q0 + 32 * q), acc[q]);
+            for (int q = 0; q < kTriUnroll; q++) {
+                const int64_t e0 = head + 2 * (q0 + 32 * q);
+                acc[q] = fma(rv[q].x, v_at(e0), acc[q]);
+                acc[q] = fma(rv[q].y, v_at(e0 + 1), acc[q]);
+            }
         }
-        for (; q0 < m; q0 += 32) acc[0] = fma(arow[q0], v_at(q0), acc[0]);
+        for (; q0 < m2; q0 += 32) {
+            const double2 rv = a2[q0];
+            const int64_t e0 = head + 2 * q0;
+            acc[0] = fma(rv.x, v_at(e0), acc[0]);
+            acc[0] = fma(rv.y, v_at(e0 + 1), acc[0]);
+        }
+        if (((m - head) & 1) && lane == 0) acc[1] = fma(arow[m - 1], v_at(m - 1), acc[1]);
 #pragma unroll
         for (int w = kTriUnroll / 2; w > 0; w /= 2)
 #pragma unroll
