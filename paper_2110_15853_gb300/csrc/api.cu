@@ -873,7 +873,7 @@ int rr_run_f32x2(const chfsi_matrix* H, const double* Y, int64_t ldy, int64_t N,
     for (int pass = 0; pass < passes; pass++) {
         if ((rc = gemm_tn_f32x2(cur, ldw, cur, ldw, N, n, rl.S, n, true, rl.part, rl.splits, s))) return rc;
         if ((rc = cholesky_upper(rl.S, n, n, st, s))) return rc;
-        if ((rc = tri_inverse_upper(rl.S, n, rl.Rinv, n, n, s))) return rc;
+        if ((rc = tri_inverse_upper_blocked(rl.S, n, rl.Rinv, n, n, rl.Q, n, nullptr, 0, st, s))) return rc;
         if ((rc = to_f32x2(rl.Rinv, n, rl.R2, n, n, n, false, s))) return rc;
         float2* out = rl.B2[which];
         if ((rc = gemm_nn_f32x2(cur, ldw, rl.R2, n, out, ldw, false, N, n, true, s))) return rc;
@@ -911,7 +911,8 @@ int rr_run_ozaki(const chfsi_matrix* H, const double* Y, int64_t ldy, int64_t N,
         if ((rc = ozaki_gemm_tn(cur, cur_ld, cur, cur_ld, N, n, n, rl.S, n, true, rl.oz, rl.oz_bytes, st, s)))
             return rc;
         if ((rc = cholesky_upper(rl.S, n, n, st, s))) return rc;
-        if ((rc = tri_inverse_upper(rl.S, n, rl.Rinv, n, n, s))) return rc;
+        if ((rc = tri_inverse_upper_blocked(rl.S, n, rl.Rinv, n, n, rl.Q, n, rl.oz, rl.oz_bytes, st, s)))
+            return rc;
         double* out = bufs[which];
         if ((rc = ozaki_gemm_nn(cur, cur_ld, rl.Rinv, n, N, n, n, out, ldw, true, rl.oz, rl.oz_bytes, st, s)))
             return rc;
@@ -1013,7 +1014,7 @@ int chfsi_rayleigh_ritz_ex(const chfsi_matrix* H, const double* Y, int64_t ldy, 
     for (int pass = 0; pass < cholqr_passes; pass++) {
         if ((rc = gemm_tn(cur, cur_ld, cur, cur_ld, N, n, rl.S, n, true, rl.part, rl.splits, s))) return rc;
         if ((rc = cholesky_upper(rl.S, n, n, st, s))) return rc;
-        if ((rc = tri_inverse_upper(rl.S, n, rl.Rinv, n, n, s))) return rc;
+        if ((rc = tri_inverse_upper_blocked(rl.S, n, rl.Rinv, n, n, rl.Q, n, nullptr, 0, st, s))) return rc;
         double* out = bufs[which];
         if ((rc = gemm_nn(cur, cur_ld, rl.Rinv, n, out, ldw, N, n, true, s))) return rc;
         cur = out;

@@ -361,6 +361,48 @@ int tri_inverse_upper(const double* R, int64_t ldr, double* Rinv, int64_t ldi, i
     return CHFSI_OK;
 }
 
+namespace {
+
+__global__ void negate_block_kernel(double* X, int64_t ldx, int64_t rows, int64_t cols) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= rows * cols) return;
+    X[(idx / cols) * ldx + idx % cols] = -X[(idx / cols) * ldx + idx % cols];
+}
+
+constexpr int64_t kTriInvLeaf = 1024;   // the column-per-warp kernel below this size
+
+}  // namespace
+
+// R^-1 of an upper-triangular R by halves: with R = [R11 R12; 0 R22],
+// R^-1 = [X11, -X11 R12 X22; 0, X22] (X11 = R11^-1, X22 = R22^-1, both recursively), the
+// off-diagonal block from two products (T = R12 X22 into `tmp`, then X11 T) -- Ozaki
+// products on the tensor cores when oz_ws is given and the depth fits (<= 8192), FP64
+// products otherwise; blocks of at most kTriInvLeaf columns by back substitution.
+int tri_inverse_upper_blocked(const double* R, int64_t ldr, double* X, int64_t ldx, int64_t n, double* tmp,
+                              int64_t ldt, void* oz_ws, size_t oz_bytes, unsigned* status, cudaStream_t s) {
+    if (n <= kTriInvLeaf) return tri_inverse_upper(R, ldr, X, ldx, n, s);
+    const int64_t h = (n / 2 + 63) / 64 * 64, r = n - h;
+    int rc;
+    if ((rc = tri_inverse_upper_blocked(R, ldr, X, ldx, h, tmp, ldt, oz_ws, oz_bytes, status, s))) return rc;
+    if ((rc = tri_inverse_upper_blocked(R + h * ldr + h, ldr, X + h * ldx + h, ldx, r, tmp, ldt, oz_ws, oz_bytes, status,
+                                        s)))
+        return rc;
+    CHFSI_CUDA_TRY(cudaMemset2DAsync(X + h * ldx, sizeof(double) * (size_t)ldx, 0, sizeof(double) * (size_t)h,
+                                     (size_t)r, s));
+    const double* R12 = R + h;
+    const double* X22 = X + h * ldx + h;
+    double* X12 = X + h;
+    if (oz_ws && r <= 8192 && h <= 8192 && oz_bytes >= ozaki_workspace_bytes(false, h, r, r, false)) {
+        if ((rc = ozaki_gemm_nn(R12, ldr, X22, ldx, h, r, r, tmp, ldt, true, oz_ws, oz_bytes, status, s))) return rc;
+        if ((rc = ozaki_gemm_nn(X, ldx, tmp, ldt, h, h, r, X12, ldx, false, oz_ws, oz_bytes, status, s))) return rc;
+        negate_block_kernel<<<(unsigned)((h * r + 255) / 256), 256, 0, s>>>(X12, ldx, h, r);
+        CHFSI_LAUNCH_CHECK();
+        return CHFSI_OK;
+    }
+    if ((rc = gemm_general(R12, ldr, false, X22, ldx, tmp, ldt, h, r, r, 1.0, false, s))) return rc;
+    return gemm_general(X, ldx, false, tmp, ldt, X12, ldx, h, r, h, -1.0, false, s);
+}
+
 int transpose(const double* A, int64_t lda, double* B, int64_t ldb, int64_t n, cudaStream_t s) {
     if (n <= 0) return CHFSI_OK;
     dim3 grid((unsigned)((n + 31) / 32), (unsigned)((n + 31) / 32));

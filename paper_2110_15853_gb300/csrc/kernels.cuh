@@ -103,9 +103,13 @@ int gemm_general(const double* A, int64_t lda, bool a_t, const double* B, int64_
                  int64_t M, int64_t Nc, int64_t K, double alpha, bool accumulate, cudaStream_t s);
 // In place: upper Cholesky S = R^T R (R in the upper triangle, lower zeroed).
 int cholesky_upper(double* S, int64_t n, int64_t lds, unsigned* status, cudaStream_t s);
-// Rinv (n x n) = R^-1 for upper-triangular R.
+// Rinv (n x n) = R^-1 for upper-triangular R (column per warp, n <= 20480).
 int tri_inverse_upper(const double* R, int64_t ldr, double* Rinv, int64_t ldi, int64_t n,
                       cudaStream_t s);
+// The same by halves with products for the off-diagonal blocks (Ozaki products when oz_ws
+// is given); tmp: at least ceil(n/2) x ceil(n/2) doubles (ldt >= n / 2 + 64).
+int tri_inverse_upper_blocked(const double* R, int64_t ldr, double* X, int64_t ldx, int64_t n, double* tmp,
+                              int64_t ldt, void* oz_ws, size_t oz_bytes, unsigned* status, cudaStream_t s);
 // B = A^T (n x n).
 int transpose(const double* A, int64_t lda, double* B, int64_t ldb, int64_t n, cudaStream_t s);
 // S = (S + S^T)/2 in place.

@@ -610,6 +610,18 @@ def test_rayleigh_ritz_f32x2_config_40cube(P, oracle_mod):
     assert np.max(np.abs(p.T @ p - np.eye(wl.n))) <= 1e-12
 
 
+@pytest.mark.parametrize("precision", ["f64", "f32x2", "ozaki"])
+def test_rayleigh_ritz_blocked_triangular_inverse(P, oracle_mod, precision):
+    """2100 states: R^-1 of CholQR is formed by halves (1088 + 1012, the first half again
+    by halves 576 + 512), the off-diagonal blocks by products (Ozaki products in the
+    Ozaki closure) -- Ritz values and vectors at the FP64 closure's tolerances."""
+    H, X = make_case(20, 2, 2100, seed=47)
+    (a, b, a0), _ = bounds_for(oracle_mod, H, 2100, 47)
+    Y = oracle_mod.filter(H, X, 6, a, b, a0)
+    ritz, psi = P.rayleigh_ritz(to_dev(P, H), dev(Y), cholqr_passes=2, precision=precision)
+    _check_ritz(oracle_mod, H, Y, ritz.cpu().numpy(), psi.cpu().numpy())
+
+
 def test_rayleigh_ritz_rank_deficient_reports_cholesky(P, oracle_mod):
     H, X = make_case(6, 2, 8, seed=44)
     X[:, 3] = 0.0
