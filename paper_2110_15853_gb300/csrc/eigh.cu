@@ -73,6 +73,7 @@ struct TriScalars {
     double dot;              // p . v of the current column (blocked: (tau / 2) p . v)
     unsigned cnt_a, cnt_b;   // completion counters of the two kernels
     double c12[2 * kPanel32];   // blocked: W_t . v (t < i), then V_t . v
+    double scale;               // blocked: v_q = scale x_q (q >= 1) of the current reflector
 };
 
 // Sum of the nparts partial sums written by the other blocks (called by the whole block
@@ -254,13 +255,19 @@ __device__ __forceinline__ void blk_store_vw(double* PV, int64_t n, int i, int64
 
 // Row j = j0 + i brought up to date over columns c in [j, n):
 // a_c = A0[j][c] - sum_{t < i} (V_t[j] W_t[c] + W_t[j] V_t[c]); for i >= 1 the previous
-// column's rows of V and W are written first (from vbuf, pbuf, tri->dot).  The sum of
+// column's rows of V and W are formed from vbuf, pbuf, tri->dot (and written).  The sum of
 // squares of a_c for c >= j + 2 (the next reflector's row past x_0) goes to tri->sumsq.
-__global__ void __launch_bounds__(256) blk_row_kernel(double* A, int64_t lda, int64_t n, int64_t j, int i,
-                                                      double* PV, TriScalars* tri, double* part,
-                                                      const double* __restrict__ vbuf,
-                                                      const double* __restrict__ pbuf) {
+// A block takes 32 columns; its 8 groups of 32 threads share the terms t < i - 1 (t = g,
+// g + 8, ...: all loads of a thread in flight at once) and group 0 adds their sums in order.
+constexpr int kColGroups = 8, kGroupCols = 32;
+
+__global__ void __launch_bounds__(kColGroups * kGroupCols) blk_row_kernel(double* A, int64_t lda, int64_t n,
+                                                                          int64_t j, int i, double* PV,
+                                                                          TriScalars* tri, double* part,
+                                                                          const double* __restrict__ vbuf,
+                                                                          const double* __restrict__ pbuf) {
     __shared__ double cv[kPanel32], cw[kPanel32];
+    __shared__ double red[kColGroups][kGroupCols];
     const double kw = tri->dot;
     if (threadIdx.x < i) {
         const int t = threadIdx.x;
@@ -273,18 +280,38 @@ __global__ void __launch_bounds__(256) blk_row_kernel(double* A, int64_t lda, in
         }
     }
     __syncthreads();
-    const int64_t c = j + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    double sq = 0.0;
+    const int cl = threadIdx.x % kGroupCols, g = threadIdx.x / kGroupCols;
+    const int64_t c = j + (int64_t)blockIdx.x * kGroupCols + cl;
+    double acc = 0.0;
     if (c < n) {
-        double a = A[j * lda + c];
-        for (int t = 0; t < i; t++) {
+        const double* __restrict__ Vr = PV;
+        const double* __restrict__ Wr = PV + (int64_t)kPanel32 * n;
+        double vt[kPanel32 / kColGroups], wt[kPanel32 / kColGroups];
+#pragma unroll
+        for (int u = 0; u < kPanel32 / kColGroups; u++) {
+            const int t = g + kColGroups * u;
+            const bool in = t < i - 1;
+            vt[u] = in ? Vr[(int64_t)t * n + c] : 0.0;
+            wt[u] = in ? Wr[(int64_t)t * n + c] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < kPanel32 / kColGroups; u++) {
+            const int t = g + kColGroups * u;
+            if (t < i - 1) acc += cv[t] * wt[u] + cw[t] * vt[u];
+        }
+    }
+    red[g][cl] = acc;
+    __syncthreads();
+    double sq = 0.0;
+    if (g == 0 && c < n) {
+        double sum = 0.0;
+#pragma unroll
+        for (int h = 0; h < kColGroups; h++) sum += red[h][cl];
+        double a = A[j * lda + c] - sum;
+        if (i >= 1) {
             double vt, wt;
-            if (t == i - 1) blk_store_vw(PV, n, t, c, vbuf, pbuf, kw, &vt, &wt);
-            else {
-                vt = PV[(int64_t)t * n + c];
-                wt = PV[(int64_t)(kPanel32 + t) * n + c];
-            }
-            a -= cv[t] * wt + cw[t] * vt;
+            blk_store_vw(PV, n, i - 1, c, vbuf, pbuf, kw, &vt, &wt);
+            a -= cv[i - 1] * wt + cw[i - 1] * vt;
         }
         A[j * lda + c] = a;
         if (c >= j + 2) sq = a * a;
@@ -316,22 +343,35 @@ __global__ void blk_finish_kernel(double* PV, int64_t n, int64_t jc, int i, cons
     blk_store_vw(PV, n, i, c, vbuf, pbuf, tri->dot, &v, &w);
 }
 
-// y = A0[j+1:, j+1:] v (one warp per row, blocks 0 .. nsymv-1; y stored unscaled) for the
-// reflector of row j (formed in every block from x_0 and tri->sumsq, as in the unblocked
-// product), and in blocks nsymv .. nsymv + 2i - 1 the dots W_t . v (t < i) and V_t . v.
-// Block 0 also writes v (vbuf) and d[j], e[j], tau[j].
-__global__ void __launch_bounds__(32 * kTriRows) blk_product_kernel(const double* __restrict__ A, int64_t lda,
+// y = A0[j+1:, j+1:] v (one warp per row, blocks 0 .. nsymv-1) for the reflector of row j
+// (formed in every block from x_0 and tri->sumsq, as in the unblocked product), and in
+// blocks 0 .. 2i - 1 (first, so that they overlap the rows) the dots W_t . v (t < i) and
+// V_t . v.  The FP64 pipe, not
+// memory, bounds this pass on GB300 (one multiply-add per 8-byte entry is above the
+// ridge), so v is not formed per entry: with v = scale x except v_0 = 1,
+// y_r = scale (sum_q A[r][q] x_q - beta A[r][0]) (1 - scale x_0 = -scale beta), one FMA an
+// entry with x read straight from A's row j; when sum_{q>=1} x_q^2 = 0 (scale = 0, v = e_0)
+// y_r = A[r][0].  Block 0 also writes d[j], e[j], tau[j] and the scale of v.
+constexpr int kBlkRows = 4;   // rows (one warp each) per block of the blocked product
+
+__global__ void __launch_bounds__(32 * kBlkRows) blk_product_kernel(const double* __restrict__ A, int64_t lda,
                                                                     int64_t n, int64_t j, int i,
                                                                     const double* __restrict__ PV, TriScalars* tri,
-                                                                    double* d, double* e, double* tau, double* vbuf,
-                                                                    double* ybuf, unsigned nsymv) {
+                                                                    double* d, double* e, double* tau,
+                                                                    double* ybuf) {
     const int64_t m = n - j - 1;
     const double* x = A + j * lda + j + 1;
     double beta, t, scale;
     reflector(x[0], tri->sumsq, beta, t, scale);
-    auto v_at = [&](int64_t q) { return q == 0 ? 1.0 : x[q] * scale; };
-    if (blockIdx.x >= nsymv) {   // block-uniform: one dot product per block
-        const int tp = (int)(blockIdx.x - nsymv);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        d[j] = A[j * lda + j];
+        e[j] = beta;
+        tau[j] = t;
+        tri->scale = scale;
+    }
+    if ((int)blockIdx.x < 2 * i) {   // block-uniform: one dot product per block
+        auto v_at = [&](int64_t q) { return q == 0 ? 1.0 : x[q] * scale; };
+        const int tp = (int)blockIdx.x;
         const double* row = tp < i ? PV + (int64_t)(kPanel32 + tp) * n : PV + (int64_t)(tp - i) * n;
         double acc = 0.0;
         for (int64_t q = threadIdx.x; q < m; q += blockDim.x) acc = fma(row[j + 1 + q], v_at(q), acc);
@@ -340,77 +380,104 @@ __global__ void __launch_bounds__(32 * kTriRows) blk_product_kernel(const double
         return;
     }
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t r = (int64_t)blockIdx.x * kTriRows + warp;
+    const int64_t r = (int64_t)(blockIdx.x - 2 * i) * kBlkRows + warp;
     if (r < m) {
-        // 16-byte loads of the row (two entries a lane), after one peeled entry when the
-        // row segment does not start on a 16-byte boundary
         const double* arow = A + (j + 1 + r) * lda + j + 1;
-        const int64_t head = (reinterpret_cast<uintptr_t>(arow) & 15u) ? 1 : 0;
-        const int64_t m2 = (m - head) / 2;
-        const double2* a2 = reinterpret_cast<const double2*>(arow + head);
-        double acc[kTriUnroll];
+        if (scale == 0.0) {
+            if (lane == 0) ybuf[j + 1 + r] = arow[0];
+        } else {
+            // 16-byte loads of the row and of x (two entries a lane) after one peeled entry
+            // when the segment does not start on a 16-byte boundary (A's rows and row j
+            // share the alignment when lda is even)
+            const bool pair_ok = (lda % 2) == 0;
+            const int64_t head = (reinterpret_cast<uintptr_t>(arow) & 15u) ? 1 : 0;
+            double acc[kTriUnroll];
 #pragma unroll
-        for (int q = 0; q < kTriUnroll; q++) acc[q] = 0.0;
-        if (head && lane == 0) acc[0] = arow[0] * v_at(0);
-        int64_t q0 = lane;
-        for (; q0 + 32 * (kTriUnroll - 1) < m2; q0 += 32 * kTriUnroll) {
-            double2 rv[kTriUnroll];
+            for (int q = 0; q < kTriUnroll; q++) acc[q] = 0.0;
+            if (pair_ok) {
+                const int64_t m2 = (m - head) / 2;
+                const double2* a2 = reinterpret_cast<const double2*>(arow + head);
+                const double2* x2 = reinterpret_cast<const double2*>(x + head);
+                if (head && lane == 0) acc[0] = arow[0] * x[0];
+                int64_t q0 = lane;
+                for (; q0 + 32 * (kTriUnroll - 1) < m2; q0 += 32 * kTriUnroll) {
+                    double2 rv[kTriUnroll], xv[kTriUnroll];
 #pragma unroll
-            for (int q = 0; q < kTriUnroll; q++) rv[q] = a2[q0 + 32 * q];
+                    for (int q = 0; q < kTriUnroll; q++) {
+                        rv[q] = a2[q0 + 32 * q];
+                        xv[q] = x2[q0 + 32 * q];
+                    }
 #pragma unroll
-            for (int q = 0; q < kTriUnroll; q++) {
-                const int64_t e0 = head + 2 * (q0 + 32 * q);
-                acc[q] = fma(rv[q].x, v_at(e0), acc[q]);
-                acc[q] = fma(rv[q].y, v_at(e0 + 1), acc[q]);
+                    for (int q = 0; q < kTriUnroll; q++) {
+                        acc[q] = fma(rv[q].x, xv[q].x, acc[q]);
+                        acc[q] = fma(rv[q].y, xv[q].y, acc[q]);
+                    }
+                }
+                for (; q0 < m2; q0 += 32) {
+                    const double2 rv = a2[q0], xv = x2[q0];
+                    acc[0] = fma(rv.x, xv.x, acc[0]);
+                    acc[0] = fma(rv.y, xv.y, acc[0]);
+                }
+                if (((m - head) & 1) && lane == 0) acc[1] = fma(arow[m - 1], x[m - 1], acc[1]);
+            } else {
+                for (int64_t q = lane; q < m; q += 32) acc[0] = fma(arow[q], x[q], acc[0]);
             }
-        }
-        for (; q0 < m2; q0 += 32) {
-            const double2 rv = a2[q0];
-            const int64_t e0 = head + 2 * q0;
-            acc[0] = fma(rv.x, v_at(e0), acc[0]);
-            acc[0] = fma(rv.y, v_at(e0 + 1), acc[0]);
-        }
-        if (((m - head) & 1) && lane == 0) acc[1] = fma(arow[m - 1], v_at(m - 1), acc[1]);
 #pragma unroll
-        for (int w = kTriUnroll / 2; w > 0; w /= 2)
+            for (int w = kTriUnroll / 2; w > 0; w /= 2)
 #pragma unroll
-            for (int q = 0; q < w; q++) acc[q] += acc[q + w];
-        const double y = warp_sum(acc[0]);
-        if (lane == 0) ybuf[j + 1 + r] = y;
-    }
-    if (blockIdx.x == 0) {
-        for (int64_t q = threadIdx.x; q < m; q += blockDim.x) vbuf[j + 1 + q] = v_at(q);
-        if (threadIdx.x == 0) {
-            d[j] = A[j * lda + j];
-            e[j] = beta;
-            tau[j] = t;
+                for (int q = 0; q < w; q++) acc[q] += acc[q + w];
+            const double y = warp_sum(acc[0]);
+            if (lane == 0) ybuf[j + 1 + r] = scale * fma(-beta, arow[0], y);
         }
     }
 }
 
-// p = tau (y - sum_t (V_t W_t . v + W_t V_t . v)) over rows r in [j+1, n), v stored in A's
-// row j for the back-transformation, and (tau / 2) p . v to tri->dot (reduced in a fixed
-// order by the last block to finish).
-__global__ void __launch_bounds__(256) blk_p_kernel(double* A, int64_t lda, int64_t n, int64_t j, int i,
-                                                    const double* __restrict__ PV, TriScalars* tri, double* part,
-                                                    const double* __restrict__ tau, const double* __restrict__ vbuf,
-                                                    const double* __restrict__ ybuf, double* pbuf) {
+// p = tau (y - sum_t (V_t W_t . v + W_t V_t . v)) over rows r in [j+1, n), v (from x and
+// the scale) stored in vbuf and in A's row j for the back-transformation, and (tau / 2) p . v
+// to tri->dot (reduced in a fixed order by the last block to finish).  A block takes 32
+// rows; its 8 groups share the terms t < i as in the row kernel.
+__global__ void __launch_bounds__(kColGroups * kGroupCols) blk_p_kernel(double* A, int64_t lda, int64_t n, int64_t j,
+                                                                        int i, const double* __restrict__ PV,
+                                                                        TriScalars* tri, double* part,
+                                                                        const double* __restrict__ tau, double* vbuf,
+                                                                        const double* __restrict__ ybuf, double* pbuf) {
     __shared__ double c1[kPanel32], c2[kPanel32];
-    if (threadIdx.x < 2 * i) {
-        if ((int)threadIdx.x < i) c1[threadIdx.x] = tri->c12[threadIdx.x];
-        else c2[threadIdx.x - i] = tri->c12[threadIdx.x];
+    __shared__ double red[kColGroups][kGroupCols];
+    if (threadIdx.x < kPanel32) {
+        c1[threadIdx.x] = (int)threadIdx.x < i ? tri->c12[threadIdx.x] : 0.0;
+        c2[threadIdx.x] = (int)threadIdx.x < i ? tri->c12[i + threadIdx.x] : 0.0;
     }
     __syncthreads();
-    const double tj = tau[j];
-    const int64_t r = j + 1 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    double pv = 0.0;
+    const int rl = threadIdx.x % kGroupCols, g = threadIdx.x / kGroupCols;
+    const int64_t r = j + 1 + (int64_t)blockIdx.x * kGroupCols + rl;
+    double acc = 0.0;
     if (r < n) {
-        double y = ybuf[r];
-        for (int t = 0; t < i; t++)
-            y -= PV[(int64_t)t * n + r] * c1[t] + PV[(int64_t)(kPanel32 + t) * n + r] * c2[t];
-        const double pr = tj * y;
+        double vt[kPanel32 / kColGroups], wt[kPanel32 / kColGroups];
+#pragma unroll
+        for (int u = 0; u < kPanel32 / kColGroups; u++) {
+            const int t = g + kColGroups * u;
+            const bool in = t < i;
+            vt[u] = in ? PV[(int64_t)t * n + r] : 0.0;
+            wt[u] = in ? PV[(int64_t)(kPanel32 + t) * n + r] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < kPanel32 / kColGroups; u++) {
+            const int t = g + kColGroups * u;
+            if (t < i) acc += vt[u] * c1[t] + wt[u] * c2[t];
+        }
+    }
+    red[g][rl] = acc;
+    __syncthreads();
+    const double tj = tau[j];
+    double pv = 0.0;
+    if (g == 0 && r < n) {
+        double sum = 0.0;
+#pragma unroll
+        for (int h = 0; h < kColGroups; h++) sum += red[h][rl];
+        const double pr = tj * (ybuf[r] - sum);
         pbuf[r] = pr;
-        const double v = vbuf[r];
+        const double v = r == j + 1 ? 1.0 : A[j * lda + r] * tri->scale;   // x_r read, then v_r stored
+        vbuf[r] = v;
         pv = pr * v;
         A[j * lda + r] = v;
     }
@@ -966,7 +1033,7 @@ void eigh_layout(Ar& ar, int64_t n, EighBufs* out) {
     u.vbuf = ar.template take<double>(n);
     u.pbuf = ar.template take<double>(n);
     u.part_a = ar.template take<double>((size_t)(n / kTriRows + 1));
-    u.part_b = ar.template take<double>((size_t)(n / 256 + 1));
+    u.part_b = ar.template take<double>((size_t)(n / 32 + 1));
     u.tri = ar.template take<TriScalars>(1);
     u.PV = ar.template take<double>((size_t)(3 * kPanel32) * n);
     u.ybuf = ar.template take<double>(n);
@@ -1050,15 +1117,15 @@ int eigh(double* A, int64_t lda, int64_t n, double* w, double* Q, int64_t ldq, v
                 CHFSI_CUDA_TRY(cudaMemsetAsync(u.PV, 0, sizeof(double) * (size_t)(3 * kPanel32) * n, s));
             for (int i = 0; i < nc; i++) {
                 const int64_t j = j0 + i, m = n - j - 1;
-                blk_row_kernel<<<(unsigned)((n - j + 255) / 256), 256, 0, s>>>(A, lda, n, j, i, u.PV, u.tri,
-                                                                               u.part_b, u.vbuf, u.pbuf);
+                blk_row_kernel<<<(unsigned)((n - j + kGroupCols - 1) / kGroupCols), kColGroups * kGroupCols, 0, s>>>(
+                    A, lda, n, j, i, u.PV, u.tri, u.part_b, u.vbuf, u.pbuf);
                 CHFSI_LAUNCH_CHECK();
-                const unsigned nsymv = (unsigned)((m + kTriRows - 1) / kTriRows);
-                blk_product_kernel<<<nsymv + 2 * i, 32 * kTriRows, 0, s>>>(A, lda, n, j, i, u.PV, u.tri, d, e, tau,
-                                                                          u.vbuf, u.ybuf, nsymv);
+                const unsigned nrowb = (unsigned)((m + kBlkRows - 1) / kBlkRows);
+                blk_product_kernel<<<nrowb + 2 * i, 32 * kBlkRows, 0, s>>>(A, lda, n, j, i, u.PV, u.tri, d, e, tau,
+                                                                          u.ybuf);
                 CHFSI_LAUNCH_CHECK();
-                blk_p_kernel<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(A, lda, n, j, i, u.PV, u.tri, u.part_a, tau,
-                                                                         u.vbuf, u.ybuf, u.pbuf);
+                blk_p_kernel<<<(unsigned)((m + kGroupCols - 1) / kGroupCols), kColGroups * kGroupCols, 0, s>>>(
+                    A, lda, n, j, i, u.PV, u.tri, u.part_a, tau, u.vbuf, u.ybuf, u.pbuf);
                 CHFSI_LAUNCH_CHECK();
             }
             const int64_t jl = j0 + nc - 1, jn = j0 + nc, mp = n - jn;
