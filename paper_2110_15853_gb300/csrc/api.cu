@@ -910,7 +910,7 @@ int rr_run_ozaki(const chfsi_matrix* H, const double* Y, int64_t ldy, int64_t N,
     for (int pass = 0; pass < passes; pass++) {
         if ((rc = ozaki_gemm_tn(cur, cur_ld, cur, cur_ld, N, n, n, rl.S, n, true, rl.oz, rl.oz_bytes, st, s)))
             return rc;
-        if ((rc = cholesky_upper(rl.S, n, n, st, s))) return rc;
+        if ((rc = cholesky_upper(rl.S, n, n, st, s, rl.oz, rl.oz_bytes, rl.Q))) return rc;
         if ((rc = tri_inverse_upper_blocked(rl.S, n, rl.Rinv, n, n, rl.Q, n, rl.oz, rl.oz_bytes, st, s)))
             return rc;
         double* out = bufs[which];

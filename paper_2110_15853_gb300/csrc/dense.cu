@@ -326,7 +326,22 @@ int gemm_general(const double* A, int64_t lda, bool a_t, const double* B, int64_
     return run_gemm(g, s);
 }
 
-int cholesky_upper(double* S, int64_t n, int64_t lds, unsigned* status, cudaStream_t s) {
+namespace {
+
+// Z -= D on the upper triangle of a rows x rows block (D dense, leading dimension rows).
+__global__ void sub_upper_kernel(double* Z, int64_t ldz, const double* __restrict__ D, int64_t rows) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= rows * rows) return;
+    const int64_t i = idx / rows, c = idx % rows;
+    if (c >= i) Z[i * ldz + c] -= D[idx];
+}
+
+constexpr int64_t kCholOzakiMin = 256;   // trailing blocks from this size on as Ozaki products
+
+}  // namespace
+
+int cholesky_upper(double* S, int64_t n, int64_t lds, unsigned* status, cudaStream_t s, void* oz_ws, size_t oz_bytes,
+                   double* scratch) {
     for (int64_t k0 = 0; k0 < n; k0 += NB) {
         int nb = (int)((n - k0) < NB ? (n - k0) : NB);
         chol_diag_kernel<<<1, 256, 0, s>>>(S, lds, k0, nb, status);
@@ -335,12 +350,22 @@ int cholesky_upper(double* S, int64_t n, int64_t lds, unsigned* status, cudaStre
         if (rest <= 0) break;
         chol_panel_kernel<<<(unsigned)((rest + 63) / 64), 64, 0, s>>>(S, lds, n, k0, nb);
         CHFSI_LAUNCH_CHECK();
-        // trailing update S22 -= R12^T R12 (upper tiles)
+        // trailing update S22 -= R12^T R12 (upper tiles): an Ozaki product on the tensor
+        // cores into the scratch block when one is given, else FP64 on the DFMA pipe
         const double* R12 = S + k0 * lds + (k0 + nb);
         double* S22 = S + (k0 + nb) * lds + (k0 + nb);
+        int rc;
+        if (oz_ws && scratch && rest >= kCholOzakiMin &&
+            oz_bytes >= ozaki_workspace_bytes(true, rest, rest, nb, true)) {
+            if ((rc = ozaki_gemm_tn(R12, lds, R12, lds, nb, rest, rest, scratch, rest, true, oz_ws, oz_bytes, status,
+                                    s)))
+                return rc;
+            sub_upper_kernel<<<(unsigned)((rest * rest + 255) / 256), 256, 0, s>>>(S22, lds, scratch, rest);
+            CHFSI_LAUNCH_CHECK();
+            continue;
+        }
         GemmArgs g{R12, lds, true, R12, lds, S22, lds, rest, rest, nb, -1.0, true, true, false, 1, nullptr};
-        int rc = run_gemm(g, s);
-        if (rc) return rc;
+        if ((rc = run_gemm(g, s))) return rc;
     }
     int64_t total = n * n;
     zero_lower_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(S, lds, n);

@@ -102,7 +102,10 @@ int gemm_nn(const double* A, int64_t lda, const double* B, int64_t ldb, double* 
 int gemm_general(const double* A, int64_t lda, bool a_t, const double* B, int64_t ldb, double* C, int64_t ldc,
                  int64_t M, int64_t Nc, int64_t K, double alpha, bool accumulate, cudaStream_t s);
 // In place: upper Cholesky S = R^T R (R in the upper triangle, lower zeroed).
-int cholesky_upper(double* S, int64_t n, int64_t lds, unsigned* status, cudaStream_t s);
+// With oz_ws and scratch (at least (n - 64)^2 doubles) the trailing updates of 256 rows
+// and more run as Ozaki products on the tensor cores.
+int cholesky_upper(double* S, int64_t n, int64_t lds, unsigned* status, cudaStream_t s, void* oz_ws = nullptr,
+                   size_t oz_bytes = 0, double* scratch = nullptr);
 // Rinv (n x n) = R^-1 for upper-triangular R (column per warp, n <= 20480).
 int tri_inverse_upper(const double* R, int64_t ldr, double* Rinv, int64_t ldi, int64_t n,
                       cudaStream_t s);
