@@ -277,6 +277,9 @@ int chfsi_rayleigh_ritz_workspace_size(const chfsi_matrix* H, int64_t n_cols,
  *      (the algorithm of chfsi_eigh, which synchronises `stream` once per merge of
  *      its divide and conquer);
  *   5. Psi = X_F Q.
+ * With cholqr_passes = 2 the second pass's X_F = X1 R2^-1 is not formed: steps 3 and 5
+ * use H_F = R2^-T (X1^T H X1) R2^-1 and Psi = X1 (R2^-1 Q), the same quantities in exact
+ * arithmetic (n x n products in place of one N x n product).
  * Y: N x n_cols (ldy), read only.  Psi: N x n_cols (ldpsi), written.
  * ritz: device array of n_cols doubles, written ascending.  n_cols <= N.
  * Synchronises `stream` before returning (it reads the status word); returns

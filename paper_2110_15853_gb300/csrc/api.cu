@@ -861,6 +861,30 @@ int rr_finish(const RRLayout& rl, unsigned* st, cudaStream_t s) {
     return CHFSI_OK;
 }
 
+// CholQR2 without the last product: with X1 the first pass's basis and X1^T X1 = R2^T R2,
+// X_F = X1 R2^-1 is not formed.  Its projection is R2^-T (X1^T H X1) R2^-1 and its Ritz
+// vectors are X1 (R2^-1 Q): in exact arithmetic the same quantities (Algorithm 1 steps
+// 2, 3, 5), for n x n x n products in place of one N x n x n product.  rr_fold_projection
+// takes P = X1^T H X1 in rl.S and leaves H_F there (T = P R2^-1 in rl.Q, then R2^-T T,
+// symmetric); rr_fold_vectors leaves G = R2^-1 Q in rl.part.  Ozaki products when oz,
+// FP64 otherwise.
+int rr_fold_projection(const RRLayout& rl, int64_t n, bool oz, unsigned* st, cudaStream_t s) {
+    int rc;
+    if (oz) {
+        if ((rc = ozaki_gemm_nn(rl.S, n, rl.Rinv, n, n, n, n, rl.Q, n, true, rl.oz, rl.oz_bytes, st, s))) return rc;
+        if ((rc = ozaki_gemm_tn(rl.Rinv, n, rl.Q, n, n, n, n, rl.S, n, true, rl.oz, rl.oz_bytes, st, s))) return rc;
+    } else {
+        if ((rc = gemm_general(rl.S, n, false, rl.Rinv, n, rl.Q, n, n, n, n, 1.0, false, s))) return rc;
+        if ((rc = gemm_general(rl.Rinv, n, true, rl.Q, n, rl.S, n, n, n, n, 1.0, false, s))) return rc;
+    }
+    return symmetrize(rl.S, n, n, s);
+}
+
+int rr_fold_vectors(const RRLayout& rl, int64_t n, bool oz, unsigned* st, cudaStream_t s) {
+    if (oz) return ozaki_gemm_nn(rl.Rinv, n, rl.Q, n, n, n, n, rl.part, n, false, rl.oz, rl.oz_bytes, st, s);
+    return gemm_general(rl.Rinv, n, false, rl.Q, n, rl.part, n, n, n, n, 1.0, false, s);
+}
+
 // Steps 2, 3 and 5 with two-float products (Cholesky, triangular inverse and the
 // eigensolve stay FP64).
 int rr_run_f32x2(const chfsi_matrix* H, const double* Y, int64_t ldy, int64_t N, int64_t n, double* Psi,
@@ -870,10 +894,12 @@ int rr_run_f32x2(const chfsi_matrix* H, const double* Y, int64_t ldy, int64_t N,
     if ((rc = to_f32x2(Y, ldy, rl.Y2, ldw, N, n, true, s))) return rc;
     const float2* cur = rl.Y2;
     int which = 0;
+    const bool fold = passes == 2;
     for (int pass = 0; pass < passes; pass++) {
         if ((rc = gemm_tn_f32x2(cur, ldw, cur, ldw, N, n, rl.S, n, true, rl.part, rl.splits, s))) return rc;
         if ((rc = cholesky_upper(rl.S, n, n, st, s))) return rc;
         if ((rc = tri_inverse_upper_blocked(rl.S, n, rl.Rinv, n, n, rl.Q, n, nullptr, 0, st, s))) return rc;
+        if (fold && pass == passes - 1) break;   // X_F = X1 R2^-1 is not formed
         if ((rc = to_f32x2(rl.Rinv, n, rl.R2, n, n, n, false, s))) return rc;
         float2* out = rl.B2[which];
         if ((rc = gemm_nn_f32x2(cur, ldw, rl.R2, n, out, ldw, false, N, n, true, s))) return rc;
@@ -889,8 +915,10 @@ int rr_run_f32x2(const chfsi_matrix* H, const double* Y, int64_t ldy, int64_t N,
     // mirrored, and the diagonal tiles averaged with their transposes
     if ((rc = gemm_tn_f32x2(XF, ldw, HXF, ldw, N, n, rl.S, n, true, rl.part, rl.splits, s))) return rc;
     if ((rc = symmetrize(rl.S, n, n, s))) return rc;
+    if (fold && (rc = rr_fold_projection(rl, n, false, st, s))) return rc;
     if ((rc = rr_eig(rl, n, ritz, st, s))) return rc;
-    if ((rc = to_f32x2(rl.Q, n, rl.Q2, n, n, n, false, s))) return rc;
+    if (fold && (rc = rr_fold_vectors(rl, n, false, st, s))) return rc;
+    if ((rc = to_f32x2(fold ? rl.part : rl.Q, n, rl.Q2, n, n, n, false, s))) return rc;
     if ((rc = gemm_nn_f32x2(XF, ldw, rl.Q2, n, Psi, ldpsi, true, N, n, false, s))) return rc;
     return rr_finish(rl, st, s);
 }
@@ -907,12 +935,14 @@ int rr_run_ozaki(const chfsi_matrix* H, const double* Y, int64_t ldy, int64_t N,
     int64_t cur_ld = ldy;
     double* bufs[2] = {rl.XF, rl.T};
     int which = 0;
+    const bool fold = passes == 2;
     for (int pass = 0; pass < passes; pass++) {
         if ((rc = ozaki_gemm_tn(cur, cur_ld, cur, cur_ld, N, n, n, rl.S, n, true, rl.oz, rl.oz_bytes, st, s)))
             return rc;
         if ((rc = cholesky_upper(rl.S, n, n, st, s, rl.oz, rl.oz_bytes, rl.Q))) return rc;
         if ((rc = tri_inverse_upper_blocked(rl.S, n, rl.Rinv, n, n, rl.Q, n, rl.oz, rl.oz_bytes, st, s)))
             return rc;
+        if (fold && pass == passes - 1) break;   // X_F = X1 R2^-1 is not formed
         double* out = bufs[which];
         if ((rc = ozaki_gemm_nn(cur, cur_ld, rl.Rinv, n, N, n, n, out, ldw, true, rl.oz, rl.oz_bytes, st, s)))
             return rc;
@@ -954,8 +984,12 @@ int rr_run_ozaki(const chfsi_matrix* H, const double* Y, int64_t ldy, int64_t N,
     // tiles averaged with their transposes
     if ((rc = ozaki_gemm_tn(XF, ldw, HXF, ldw, N, n, n, rl.S, n, true, rl.oz, rl.oz_bytes, st, s))) return rc;
     if ((rc = symmetrize(rl.S, n, n, s))) return rc;
+    if (fold && (rc = rr_fold_projection(rl, n, true, st, s))) return rc;
     if ((rc = rr_eig(rl, n, ritz, st, s))) return rc;
-    if ((rc = ozaki_gemm_nn(XF, ldw, rl.Q, n, N, n, n, Psi, ldpsi, false, rl.oz, rl.oz_bytes, st, s))) return rc;
+    if (fold && (rc = rr_fold_vectors(rl, n, true, st, s))) return rc;
+    if ((rc = ozaki_gemm_nn(XF, ldw, fold ? rl.part : rl.Q, n, N, n, n, Psi, ldpsi, false, rl.oz, rl.oz_bytes, st,
+                            s)))
+        return rc;
     return rr_finish(rl, st, s);
 }
 
@@ -1006,15 +1040,18 @@ int chfsi_rayleigh_ritz_ex(const chfsi_matrix* H, const double* Y, int64_t ldy, 
         return rr_run_ozaki(H, Y, ldy, N, n, Psi, ldpsi, ritz, cholqr_passes, bsr_hx, rl, st, s);
     }
 
-    // step 2: X_F = Y R^-1 with S = Y^T Y = R^T R (repeated on X_F for CholQR2)
+    // step 2: X_F = Y R^-1 with S = Y^T Y = R^T R (repeated on X_F for CholQR2, whose last
+    // product is folded into steps 3 and 5)
     const double* cur = Y;
     int64_t cur_ld = ldy;
     double* bufs[2] = {rl.XF, rl.T};
     int which = 0;
+    const bool fold = cholqr_passes == 2;
     for (int pass = 0; pass < cholqr_passes; pass++) {
         if ((rc = gemm_tn(cur, cur_ld, cur, cur_ld, N, n, rl.S, n, true, rl.part, rl.splits, s))) return rc;
         if ((rc = cholesky_upper(rl.S, n, n, st, s))) return rc;
         if ((rc = tri_inverse_upper_blocked(rl.S, n, rl.Rinv, n, n, rl.Q, n, nullptr, 0, st, s))) return rc;
+        if (fold && pass == cholqr_passes - 1) break;   // X_F = X1 R2^-1 is not formed
         double* out = bufs[which];
         if ((rc = gemm_nn(cur, cur_ld, rl.Rinv, n, out, ldw, N, n, true, s))) return rc;
         cur = out;
@@ -1038,10 +1075,12 @@ int chfsi_rayleigh_ritz_ex(const chfsi_matrix* H, const double* Y, int64_t ldy, 
     // mirrored, and the diagonal tiles averaged with their transposes
     if ((rc = gemm_tn(XF, ldw, HXF, ldw, N, n, rl.S, n, true, rl.part, rl.splits, s))) return rc;
     if ((rc = symmetrize(rl.S, n, n, s))) return rc;
+    if (fold && (rc = rr_fold_projection(rl, n, false, st, s))) return rc;
     // step 4: H_F Q = Q Lambda
     if ((rc = rr_eig(rl, n, ritz, st, s))) return rc;
-    // step 5: Psi = X_F Q
-    if ((rc = gemm_nn(XF, ldw, rl.Q, n, Psi, ldpsi, N, n, false, s))) return rc;
+    // step 5: Psi = X_F Q (= X1 (R2^-1 Q) after CholQR2)
+    if (fold && (rc = rr_fold_vectors(rl, n, false, st, s))) return rc;
+    if ((rc = gemm_nn(XF, ldw, fold ? rl.part : rl.Q, n, Psi, ldpsi, N, n, false, s))) return rc;
     return rr_finish(rl, st, s);
 }
 
