@@ -92,10 +92,14 @@ def lanczos_flops(nnz, N, k):
 
 
 def closure_flops(nnz, N, n, passes):
-    """Gram N n^2 and triangular solve N n^2 per CholQR pass, H X_F (2 nnz n),
-    projection N n^2 (H_F is symmetric: one triangle, like the Gram), rotation
-    2 N n^2 (eigensolve not counted)."""
-    return passes * 2.0 * N * n * n + 2.0 * nnz * n + 1.0 * N * n * n + 2.0 * N * n * n
+    """Gram N n^2 (one triangle) per CholQR pass and triangular product X = Y R^-1
+    (N n^2) per pass except the last one of CholQR2, whose R2^-1 the library folds
+    into the projection and the Ritz vectors (P R2^-1 and R2^-1 Q, n^3 each, and the
+    upper triangle of R2^-T (P R2^-1), n^3 / 3); H X_F (2 nnz n), projection N n^2
+    (H_F is symmetric: one triangle), rotation 2 N n^2 (eigensolve not counted)."""
+    tri = passes - 1 if passes == 2 else passes
+    fold = 7.0 / 3.0 * n ** 3 if passes == 2 else 0.0
+    return (passes + tri) * 1.0 * N * n * n + fold + 2.0 * nnz * n + 1.0 * N * n * n + 2.0 * N * n * n
 
 
 def hbm_peak_gbs():
