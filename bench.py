@@ -67,7 +67,8 @@ def parse_args(argv=None):
     ap.add_argument("--filter-only", action="store_true",
                     help="set up, run one filter (m launches of the CSR step per slab) and exit: a profiling case")
     ap.add_argument("--schedule", default="f64",
-                    help="filter-only schedule: f64 | f32:L | bf16:L | f32x2:L | ozaki (BSR or hybrid layout)")
+                    help="filter-only schedule: f64 | f32:L | bf16:L | f32x2:L | ozaki | ozaki40 | ozaki40:L "
+                         "(the ozaki ones on the BSR or hybrid layout)")
     ap.add_argument("--layout", default="csr", choices=["csr", "bsr", "hybrid"], help="filter-only operator layout")
     ap.add_argument("--closure-only", action="store_true",
                     help="set up, run one CholQR2 + Rayleigh-Ritz on X and exit: a profiling case")
@@ -505,8 +506,9 @@ def run_ours(args):
             line["mixed_precision"] = mixed_variants(P, torch, dev, stream, wl, Hd, Xd, v0d, Ym, theta_ref,
                                                      (a, b, a0), line)
             try:
-                line["mixed_precision"]["whole_step_ozaki_bsr_filter_ozaki_closure"] = ozaki_whole_step(
-                    P, torch, dev, stream, wl, H, Xd, Ym, theta_ref, (a, b, a0), line)
+                oz = ozaki_whole_step(P, torch, dev, stream, wl, H, Xd, Ym, theta_ref, (a, b, a0), line)
+                line["mixed_precision"]["whole_step_ozaki_bsr_filter_ozaki_closure"] = oz["ozaki"]
+                line["mixed_precision"]["whole_step_ozaki40_prefix_filter_ozaki_closure"] = oz["ozaki40_prefix"]
             except Exception as e:  # noqa: BLE001 - report, do not hide
                 line["mixed_precision"]["ozaki_bsr_error"] = repr(e)
         del Ym
@@ -612,11 +614,27 @@ def mixed_variants(P, torch, dev, stream, wl, Hd, Xd, v0d, Yref, theta_ref, boun
     return out
 
 
+OZAKI40_TAIL = 4   # FP64-accurate Ozaki steps closing a schedule of 40-bit Ozaki steps
+
+
+def ozaki_schedules(m):
+    """The Ozaki filter schedules measured on the whole step: every step FP64-accurate
+    (seven digit slices, 28 slice products), and the 40-bit steps (five slices, 15
+    products) for all but the last OZAKI40_TAIL steps."""
+    return {"ozaki": ["ozaki"] * m,
+            "ozaki40_prefix": ["ozaki40"] * (m - OZAKI40_TAIL) + ["ozaki"] * OZAKI40_TAIL}
+
+
+def slice_products(schedule):
+    """BF16 slice products per stored block element and state, summed over the steps."""
+    return sum(15 if p == "ozaki40" else 28 for p in schedule)
+
+
 def ozaki_whole_step(P, torch, dev, stream, wl, H, Xd, Yref, theta_ref, bounds, line):
-    """The whole step FP64-accurate on the tensor cores: the filter with H's 64 x 64
-    blocks (4 x 4 x 4 sub-cubes) as Ozaki products, then the Ozaki closure, in the
-    blocked row order (X permuted on the device; the layout conversion on the host is
-    not timed).  Lanczos as in the FP64 step."""
+    """The whole step on the tensor cores: the filter with H's 64 x 64 blocks (4 x 4 x 4
+    sub-cubes) as Ozaki products, then the Ozaki closure, in the blocked row order (X
+    permuted on the device; the layout conversion on the host is not timed), for each
+    schedule of ozaki_schedules.  Lanczos as in the FP64 step."""
     a, b, a0 = bounds
     N, n, m = H["N"], wl.n, wl.m
     t0 = time.time()
@@ -630,39 +648,46 @@ def ozaki_whole_step(P, torch, dev, stream, wl, H, Xd, Yref, theta_ref, bounds, 
     del B, Hp
     Xp = Xd[perm].contiguous()
     Yp = torch.empty_like(Xp)
-    sched = ["ozaki"] * m
-    ws = P.Workspace(dev)
-    ws.get(P.filter_workspace_bytes(Bd, n, m, sched))
-    e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
-    P.filter(Bd, Xp[:, :8], 2, a, b, a0, schedule=["ozaki"] * 2)   # first call: attributes, code load
+    for warm in (["ozaki"] * 2, ["ozaki40"] * 2):   # first calls: attributes, code load
+        P.filter(Bd, Xp[:, :8], 2, a, b, a0, schedule=warm)
     torch.cuda.synchronize(dev)
-    e[0].record(stream)
-    P.filter(Bd, Xp, m, a, b, a0, schedule=sched, out=Yp, workspace=ws)
-    e[1].record(stream)
-    torch.cuda.synchronize(dev)
-    status = P.read_status(ws)
-    del ws
-    t_f = e[0].elapsed_time(e[1])
-    Yback = torch.empty_like(Yp)
-    Yback[perm] = Yp
-    y_err = float(torch.linalg.norm(Yback - Yref) / torch.linalg.norm(Yref))
-    del Yback, Xp
-    wso = P.Workspace(dev)
-    wso.get(P.rayleigh_ritz_workspace_bytes(Hy, n, 2, "ozaki"))
-    e[2].record(stream)
-    th, _ = P.rayleigh_ritz(Hy, Yp, 2, workspace=wso, precision="ozaki")
-    e[3].record(stream)
-    torch.cuda.synchronize(dev)
-    t_c = e[2].elapsed_time(e[3])
-    del wso, Yp
-    fl = filter_flops(H["nnz"], N, n, m)
-    t_step = line["phases"]["lanczos_ms"] + t_f + t_c
-    return dict(filter_ms=t_f, filter_gflops=fl / (t_f * 1e-3) / 1e9,
-                filter_speedup_vs_f64=line["phases"]["filter_ms"] / t_f,
-                slice_product_tflops=m * 28 * 2.0 * nblocks * 4096 * n / (t_f * 1e-3) / 1e12,
-                y_rel_fro_err_vs_f64=y_err, status=status, closure_ms=t_c, ms=t_step,
-                speedup_vs_f64_step=line["phases"]["whole_step_ms"] / t_step,
-                host_layout_seconds_untimed=host_s, **_ritz_errors(th.cpu().numpy(), theta_ref, a))
+    out = {}
+    for name, sched in ozaki_schedules(m).items():
+        ws = P.Workspace(dev)
+        ws.get(P.filter_workspace_bytes(Bd, n, m, sched))
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        e[0].record(stream)
+        P.filter(Bd, Xp, m, a, b, a0, schedule=sched, out=Yp, workspace=ws)
+        e[1].record(stream)
+        torch.cuda.synchronize(dev)
+        status = P.read_status(ws)
+        del ws
+        t_f = e[0].elapsed_time(e[1])
+        Yback = torch.empty_like(Yp)
+        Yback[perm] = Yp
+        y_err = float(torch.linalg.norm(Yback - Yref) / torch.linalg.norm(Yref))
+        del Yback
+        wso = P.Workspace(dev)
+        wso.get(P.rayleigh_ritz_workspace_bytes(Hy, n, 2, "ozaki"))
+        e[2].record(stream)
+        th, _ = P.rayleigh_ritz(Hy, Yp, 2, workspace=wso, precision="ozaki")
+        e[3].record(stream)
+        torch.cuda.synchronize(dev)
+        t_c = e[2].elapsed_time(e[3])
+        del wso
+        fl = filter_flops(H["nnz"], N, n, m)
+        t_step = line["phases"]["lanczos_ms"] + t_f + t_c
+        res = dict(schedule=f"{sched.count('ozaki40')} x ozaki40 + {sched.count('ozaki')} x ozaki",
+                   filter_ms=t_f, filter_gflops=fl / (t_f * 1e-3) / 1e9,
+                   filter_speedup_vs_f64=line["phases"]["filter_ms"] / t_f,
+                   slice_product_tflops=slice_products(sched) * 2.0 * nblocks * 4096 * n / (t_f * 1e-3) / 1e12,
+                   y_rel_fro_err_vs_f64=y_err, status=status, closure_ms=t_c, ms=t_step,
+                   speedup_vs_f64_step=line["phases"]["whole_step_ms"] / t_step,
+                   host_layout_seconds_untimed=host_s, **_ritz_errors(th.cpu().numpy(), theta_ref, a))
+        res["meets_target"] = bool(res["ritz_max_rel_err_vs_f64"] <= RITZ_TARGET)
+        out[name] = res
+    del Xp, Yp
+    return out
 
 
 def secondary_variants(P, torch, dev, stream):
@@ -853,21 +878,25 @@ def layout_variants(P, torch, dev, stream, wl, H, Hd, Xd, bounds):
         out[f"filter_hybrid_{low}x{L}_f64x{m - L}"] = dict(
             ms=t, gflops=fl / (t * 1e-3) / 1e9, speedup_vs_f64=out["filter_csr_f64"]["ms"] / t,
             y_rel_fro_err_vs_f64=err_vs_ref(), **ritz_err())
-    out["filter_bsr_ozaki_f64"] = ozaki_bsr_variant(P, torch, dev, stream, Bd, Xp, Yb, m, a, b, a0, fl,
-                                                    B["n_blocks"], out["filter_csr_f64"]["ms"], err_vs_ref, ritz_err)
+    scheds = ozaki_schedules(m)
+    for key, name in (("filter_bsr_ozaki_f64", "ozaki"), (f"filter_bsr_ozaki40x{m - OZAKI40_TAIL}_ozaki"
+                                                           f"x{OZAKI40_TAIL}", "ozaki40_prefix")):
+        out[key] = ozaki_bsr_variant(P, torch, dev, stream, Bd, Xp, Yb, m, a, b, a0, fl, B["n_blocks"],
+                                     out["filter_csr_f64"]["ms"], err_vs_ref, ritz_err, scheds[name])
     return out
 
 
-def ozaki_bsr_variant(P, torch, dev, stream, Bd, Xp, Yb, m, a, b, a0, fl, nblocks, t_f64, err_vs_ref, ritz_err):
-    """All m steps FP64-accurate with H's 64 x 64 blocks as Ozaki products on the tensor
-    cores (28 BF16 slice products per stored block element and state), against the FP64
-    CSR filter of the same run."""
+def ozaki_bsr_variant(P, torch, dev, stream, Bd, Xp, Yb, m, a, b, a0, fl, nblocks, t_f64, err_vs_ref, ritz_err,
+                      sched):
+    """A filter with H's 64 x 64 blocks as Ozaki products on the tensor cores (28 BF16
+    slice products per stored block element and state in an FP64-accurate step, 15 in a
+    40-bit step), against the FP64 CSR filter of the same run."""
     ws = P.Workspace(dev)
     t = _timeit(torch, dev, stream,
-                lambda: P.filter(Bd, Xp, m, a, b, a0, schedule=["ozaki"] * m, out=Yb, workspace=ws), reps=1)
+                lambda: P.filter(Bd, Xp, m, a, b, a0, schedule=sched, out=Yb, workspace=ws), reps=1)
     n = Xp.shape[1]
     return dict(ms=t, ms_per_step=t / m, gflops=fl / (t * 1e-3) / 1e9, speedup_vs_f64=t_f64 / t,
-                slice_product_tflops=m * 28 * 2.0 * nblocks * 4096 * n / (t * 1e-3) / 1e12,
+                slice_product_tflops=slice_products(sched) * 2.0 * nblocks * 4096 * n / (t * 1e-3) / 1e12,
                 status=P.read_status(ws), y_rel_fro_err_vs_f64=err_vs_ref(), **ritz_err())
 
 
@@ -882,8 +911,11 @@ def run_filter_only(P, torch, dev, wl, H, Hd, Xd, v0d, args):
             P.CsrMatrix.from_arrays(Hp["row_ptr"], Hp["col"], Hp["val"], device=dev), Bd)
         Xd = Xd[torch.as_tensor(B["perm"]).to(dev)].contiguous()
     sched = None
-    if args.schedule == "ozaki":
-        sched = ["ozaki"] * wl.m
+    if args.schedule in ("ozaki", "ozaki40"):
+        sched = [args.schedule] * wl.m
+    elif args.schedule.startswith("ozaki40:"):
+        L = int(args.schedule.split(":")[1])
+        sched = ["ozaki40"] * L + ["ozaki"] * (wl.m - L)
     elif args.schedule != "f64":
         low, L = args.schedule.split(":")
         sched = P.mixed_schedule(wl.m, int(L), low)

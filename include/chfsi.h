@@ -145,13 +145,23 @@ typedef struct {
                                  schedule the FP64 steps of a BSR or hybrid operator, its
                                  64 x 64 blocks as Ozaki products (rows of at most 128
                                  blocks), FP64 iterates and recurrence                   */
+#define CHFSI_F40_OZAKI 5     /* filter schedules only, wherever CHFSI_F64_OZAKI steps may
+                                 run: the same step with the first five of the seven
+                                 slices of each operand (40-bit operands, truncated) and
+                                 the 15 slice pairs of weight 2^-48 and above, each term
+                                 within about 2^-40 of its row scales (2^16 finer than
+                                 FP32) for about half the tensor-core work; FP64 iterates
+                                 and recurrence.  Not in the paper: a precision knob of
+                                 this library, for the early steps of a schedule whose
+                                 last steps are CHFSI_F64_OZAKI                          */
 
 /*
  * Per-step precision of the filter: step_prec[k-1] is the precision of the step
  * that produces Y_k (k = 1..m).  Low-precision steps (CHFSI_F32, CHFSI_BF16_F32ACC,
- * CHFSI_F32X2, one kind) must form a prefix; the steps after it are all CHFSI_F64 or
- * all CHFSI_F64_OZAKI (the two iterates carried across the switch are widened
- * exactly).  A NULL schedule (or step_prec == NULL) means every step in FP64.
+ * CHFSI_F32X2, one kind) must form a prefix; the steps after it are all CHFSI_F64, or
+ * all Ozaki steps (CHFSI_F64_OZAKI and CHFSI_F40_OZAKI in any order; both keep FP64
+ * iterates).  The two iterates carried across the switch are widened exactly.  A NULL
+ * schedule (or step_prec == NULL) means every step in FP64.
  */
 typedef struct {
     int32_t m;

@@ -32,6 +32,7 @@ CHFSI_F32 = 1
 CHFSI_BF16_F32ACC = 2
 CHFSI_F32X2 = 3
 CHFSI_F64_OZAKI = 4
+CHFSI_F40_OZAKI = 5
 
 CHFSI_OP_TN = 0
 CHFSI_OP_NN = 1

@@ -23,11 +23,11 @@ import numpy as np
 import torch
 
 from . import _abi
-from ._abi import (CHFSI_BF16_F32ACC, CHFSI_BSR, CHFSI_CSR, CHFSI_F32, CHFSI_F32X2, CHFSI_F64, CHFSI_F64_OZAKI,
-                   ChfsiError, check, load)
+from ._abi import (CHFSI_BF16_F32ACC, CHFSI_BSR, CHFSI_CSR, CHFSI_F32, CHFSI_F32X2, CHFSI_F40_OZAKI, CHFSI_F64,
+                   CHFSI_F64_OZAKI, ChfsiError, check, load)
 
 PRECISIONS = {"f64": CHFSI_F64, "f32": CHFSI_F32, "bf16": CHFSI_BF16_F32ACC, "f32x2": CHFSI_F32X2,
-              "ozaki": CHFSI_F64_OZAKI}
+              "ozaki": CHFSI_F64_OZAKI, "ozaki40": CHFSI_F40_OZAKI}
 
 
 def _ptr(t: Optional[torch.Tensor]) -> Optional[int]:

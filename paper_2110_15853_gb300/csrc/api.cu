@@ -142,15 +142,16 @@ void coefficients(int m, double a, double b, double a0, std::vector<double>& alp
 }
 
 // Low-precision prefix length of a schedule (validated) and the kind of its FP64
-// tail: plain FP64 steps or FP64-accurate Ozaki steps (CHFSI_F64_OZAKI), one kind for
-// the whole tail.
+// tail: plain FP64 steps, or Ozaki steps (CHFSI_F64_OZAKI, with CHFSI_F40_OZAKI steps
+// anywhere among them; tail kind CHFSI_F64_OZAKI), one kind for the whole tail.
 int schedule_prefix(const chfsi_schedule* sched, int m, int* L, int* low_kind, int* tail_kind) {
     *L = 0;
     *low_kind = CHFSI_F64;
     *tail_kind = CHFSI_F64;
     if (!sched || !sched->step_prec) return CHFSI_OK;
     if (sched->m != m) return CHFSI_ERR_ARG;
-    auto is_tail = [](int p) { return p == CHFSI_F64 || p == CHFSI_F64_OZAKI; };
+    auto is_oz = [](int p) { return p == CHFSI_F64_OZAKI || p == CHFSI_F40_OZAKI; };
+    auto is_tail = [&](int p) { return p == CHFSI_F64 || is_oz(p); };
     int k = 0;
     while (k < m && !is_tail(sched->step_prec[k])) {
         int p = sched->step_prec[k];
@@ -159,9 +160,11 @@ int schedule_prefix(const chfsi_schedule* sched, int m, int* L, int* low_kind, i
         *low_kind = p;
         k++;
     }
-    if (k < m) *tail_kind = sched->step_prec[k];
-    for (int r = k; r < m; r++)
-        if (sched->step_prec[r] != *tail_kind) return CHFSI_ERR_ARG;
+    if (k < m) *tail_kind = is_oz(sched->step_prec[k]) ? CHFSI_F64_OZAKI : CHFSI_F64;
+    for (int r = k; r < m; r++) {
+        const int p = sched->step_prec[r];
+        if (*tail_kind == CHFSI_F64_OZAKI ? !is_oz(p) : p != CHFSI_F64) return CHFSI_ERR_ARG;
+    }
     *L = k;
     return CHFSI_OK;
 }
@@ -330,6 +333,7 @@ struct FilterRun {
     const chfsi_matrix* H;
     int64_t N;
     int m, L, low, tail;
+    const int32_t* prec;      // the schedule's per-step precisions, or nullptr (all FP64)
     const std::vector<double>* al;
     const std::vector<double>* be;
     double c;
@@ -433,9 +437,10 @@ int filter_columns(const FilterRun& R, const double* X, int64_t ldx, double* Y, 
         io.out = f64_buf(k); io.out_t = Buf::F64; io.ldo = f64_ld(k);
         if (oz_tail) {
             // H's blocks as Ozaki products on the tensor cores, FP64 recurrence
+            const int slices = R.prec && R.prec[k - 1] == CHFSI_F40_OZAKI ? 5 : 7;
             rc = ozaki_bsr_step(R.bsr64, n, static_cast<const double*>(io.cur), io.ldc,
                                 static_cast<const double*>(io.prev), io.ldp, static_cast<double*>(io.out), io.ldo,
-                                al[k], c, k >= 2 ? be[k] : 0.0, fl.oz, fl.oz_bytes, st, s);
+                                al[k], c, k >= 2 ? be[k] : 0.0, fl.oz, fl.oz_bytes, st, s, slices);
         } else if (H->kind == CHFSI_SPLIT) {
             // dense diagonal blocks on the tensor cores, then the sparse rest with that sum added
             rc = ozaki_blockdiag_apply(static_cast<const double*>(io.cur), io.ldc, N, H->split.block, n, fl.T, ldw,
@@ -492,6 +497,7 @@ int chfsi_filter(const chfsi_matrix* H, const double* X, int64_t ldx, double* Y,
     R.L = L;
     R.low = low;
     R.tail = tail;
+    R.prec = sched ? sched->step_prec : nullptr;
     R.al = &al;
     R.be = &be;
     R.ldw = pad8(slab);

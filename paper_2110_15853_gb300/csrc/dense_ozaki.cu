@@ -30,6 +30,13 @@
 // only errors are the 56-bit rounding of the inputs and the dropped pairs (weights
 // 2^{-72} and below).
 //
+// Five-slice steps.  A filter step may also use only the first five digits of each
+// operand (a 40-bit fixed-point value, truncation below 2^{-41} of the row scale) and
+// the 15 pairs of weight 2^{-48} and above (levels 2 .. 6): about 2^{-40} of the row
+// scales per term, some 2^{16} times finer than FP32, for 15 slice products instead
+// of 28 and three operand stages instead of two.  The digits are the same as above,
+// so the same slices serve both step kinds.
+//
 // Kernel.  Persistent, warp-specialised, one CTA per SM, 128 x 64 output tiles:
 //   warp 0, lane 0 : TMA producer -- per K-block of 32, the seven A (128-row) and
 //                    seven B (64-row) slice tiles (64-byte swizzle) into a two-stage ring;
@@ -55,9 +62,7 @@ namespace {
 
 using namespace tc;
 
-constexpr int kSlices = 7;
-constexpr int kPairs = kSlices * (kSlices + 1) / 2;   // slice pairs with t + u <= 8 (1-based)
-constexpr int kAccs = 7;                              // E2 .. E8
+constexpr int kSlices = 7;                            // digit planes stored per operand
 constexpr int kTileM = 128;                           // output rows per tile (TMEM lanes)
 constexpr int kTileN = 64;                            // output columns per tile
 constexpr int kRowPad = 128;                          // operand rows are padded to this
@@ -70,24 +75,37 @@ constexpr int kKB = 32;
 constexpr int kSwizzleBytes = 2 * kKB;
 constexpr int kMaxItemKB = 8192 / kKB;                // K-blocks per work item (8192 K)
 constexpr int kBlockKB = 64 / kKB;                    // K-blocks per 64-wide BSR block
-constexpr int kSliceA = kTileM * kKB * 2;             // 4 KB
-constexpr int kSliceB = kTileN * kKB * 2;             // 2 KB
-constexpr int kStageBytes = kSlices * (kSliceA + kSliceB);
-constexpr int kStages = (224 * 1024) / kStageBytes;
+constexpr int kSliceA = kTileM * kKB * 2;             // 8 KB
+constexpr int kSliceB = kTileN * kKB * 2;             // 4 KB
 constexpr int kPeriodX = 256 / kKB;                   // K-blocks between drains of group X (256 K)
 constexpr int kPeriodY = 128 / kKB;                   // K-blocks between drains of group Y (128 K)
 constexpr CUtensorMapSwizzle kTmaSwizzle = kKB == 16 ? CU_TENSOR_MAP_SWIZZLE_32B : CU_TENSOR_MAP_SWIZZLE_64B;
 constexpr int kEpiWarps = 16;
 constexpr int kColsPerThread = kTileN / (kEpiWarps / 4);   // 16
 constexpr int kThreads = 32 * (2 + kEpiWarps);
-constexpr int kSmemBytes = kStages * kStageBytes + 1024;
 constexpr uint32_t kTmemCols = 512;
+constexpr int kMaxStages = 3;
 constexpr int kXEvent = 1, kYEvent = 2, kFullEvent = 3;
-static_assert(kSmemBytes + 1024 <= 227 * 1024, "shared memory per CTA");
-static_assert(kAccs * kTileN <= (int)kTmemCols, "seven accumulators in TMEM");
-static_assert(kSliceB % (8 * kSwizzleBytes) == 0 && kStageBytes % 1024 == 0, "swizzle-atom alignment of the tiles");
+static_assert(kSliceB % (8 * kSwizzleBytes) == 0, "swizzle-atom alignment of the tiles");
 static_assert(kKB == 16 || kKB == 32, "K-block of one or two 16-wide MMA steps");
 static_assert(kColsPerThread == 16, "16-column TMEM loads");
+
+// Shape of a product with NS digit slices per operand (7: FP64-accurate; 5: the
+// 40-bit steps): a stage holds NS A and NS B slice tiles; levels 2 .. NS + 1 each have
+// an accumulator (E2 .. E_{NS+1}), group X = E2 .. E5, group Y = the rest.
+template <int NS>
+struct OzShape {
+    static constexpr int kStageBytes = NS * (kSliceA + kSliceB);
+    static constexpr int kStages = (224 * 1024) / kStageBytes;
+    static constexpr int kSmemBytes = kStages * kStageBytes + 1024;
+    static constexpr int kAccs = NS;
+    static constexpr int kMmas = NS == 7 ? 11 : 9;
+    static_assert(NS == 7 || NS == 5, "seven or five slices");
+    static_assert(kStages >= 2 && kStages <= kMaxStages, "two or three operand stages");
+    static_assert(kSmemBytes + 1024 <= 227 * 1024, "shared memory per CTA");
+    static_assert(kAccs * kTileN <= (int)kTmemCols, "accumulators in TMEM");
+    static_assert(kStageBytes % 1024 == 0, "swizzle-atom alignment of the stages");
+};
 
 // The 28 slice pairs (t, u), 0-based, with t + u <= 6 go to accumulator t + u (level
 // t + u + 2).  For one slice t of A, the slices u of B that fall into one accumulator
@@ -96,10 +114,15 @@ static_assert(kColsPerThread == 16, "16-column TMEM loads");
 // E2 .. E5) and 7 for group Y (accumulators 4-6, E6 .. E8), 11 per K-step instead of 28
 // (fewer, wider MMAs: less shared-memory operand traffic per product).  The first MMA of
 // each group has t = 0 and covers all of the group's accumulators.
-constexpr int kMmaX = 4, kMmas = 11;
-__constant__ int8_t kMmaT[kMmas] = {0, 1, 2, 3, 0, 1, 2, 3, 4, 5, 6};
-__constant__ int8_t kMmaU[kMmas] = {0, 0, 0, 0, 4, 3, 2, 1, 0, 0, 0};
-__constant__ int8_t kMmaC[kMmas] = {4, 3, 2, 1, 3, 3, 3, 3, 3, 2, 1};
+// With five slices the 15 pairs with t + u <= 4 take the same 4 MMAs for group X and
+// one MMA per pair of level 6 (accumulator 4, E6) for group Y: 9 per K-step.
+constexpr int kMmaX = 4;
+__constant__ int8_t kMmaT7[11] = {0, 1, 2, 3, 0, 1, 2, 3, 4, 5, 6};
+__constant__ int8_t kMmaU7[11] = {0, 0, 0, 0, 4, 3, 2, 1, 0, 0, 0};
+__constant__ int8_t kMmaC7[11] = {4, 3, 2, 1, 3, 3, 3, 3, 3, 2, 1};
+__constant__ int8_t kMmaT5[9] = {0, 1, 2, 3, 0, 1, 2, 3, 4};
+__constant__ int8_t kMmaU5[9] = {0, 0, 0, 0, 4, 3, 2, 1, 0};
+__constant__ int8_t kMmaC5[9] = {4, 3, 2, 1, 1, 1, 1, 1, 1};
 
 // The drain after K-block kb of an item of KB blocks: 0 none, kXEvent (E2 .. E5),
 // kYEvent (E6 .. E8) or kFullEvent (all seven, then the output).
@@ -137,6 +160,7 @@ struct OzArgs {
     // columns of the row, and the epilogue applies the recurrence
     // Y_out = alpha (H Y_cur - c Y_cur) - beta Y_prev in FP64 (output in C, ldc).
     int bsr;
+    int slices;               // digit slices per operand in the products: 7, or 5 (BSR mode)
     const int32_t* brow_ptr;
     const int32_t* bcol;
     int64_t nbr, nblocks;
@@ -246,14 +270,19 @@ __device__ __forceinline__ double combine(long long hi, long long lo, int e) {
 // (16,384 registers each) and five of the warps share one of them, which allows 96
 // registers a thread; ptxas keeps to that under these launch bounds.  kBsr: the BSR
 // filter-step mode (its own instantiation, so that neither mode carries the other's
-// epilogue registers).
-template <bool kBsr>
+// epilogue registers).  NS: digit slices per operand (7, or 5 for the 40-bit steps).
+template <bool kBsr, int NS>
 __global__ void __launch_bounds__(kThreads, 1)
 oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, OzArgs g,
                int64_t total) {
+    using Sh = OzShape<NS>;
+    constexpr int kStages = Sh::kStages, kStageBytes = Sh::kStageBytes, kMmas = Sh::kMmas, kAccs = Sh::kAccs;
+    const int8_t* kMmaT = NS == 7 ? kMmaT7 : kMmaT5;
+    const int8_t* kMmaU = NS == 7 ? kMmaU7 : kMmaU5;
+    const int8_t* kMmaC = NS == 7 ? kMmaC7 : kMmaC5;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    __shared__ __align__(8) uint64_t full[kStages], empty[kStages], efull, eempty, done;
+    __shared__ __align__(8) uint64_t full[kMaxStages], empty[kMaxStages], efull, eempty, done;
     __shared__ uint32_t tmem_slot;
     __shared__ int abort_flag;
 
@@ -310,13 +339,13 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                 }
                 mbar_expect_tx(&full[s], kStageBytes);
 #pragma unroll
-                for (int t = 0; t < kSlices; t++)
+                for (int t = 0; t < NS; t++)
                     tma_load_2d(st + t * kSliceA, &tmA, xa,
                                 (int)(t * g.rowsA_pad + it.batch * g.a_batch_rows + (int64_t)it.tm * kTileM),
                                 sa(&full[s]));
 #pragma unroll
-                for (int t = 0; t < kSlices; t++)
-                    tma_load_2d(st + kSlices * kSliceA + t * kSliceB, &tmB, xb, (int)(t * g.rowsB_pad + rb),
+                for (int t = 0; t < NS; t++)
+                    tma_load_2d(st + NS * kSliceA + t * kSliceB, &tmB, xb, (int)(t * g.rowsB_pad + rb),
                                 sa(&full[s]));
             }
             if (!ok) { *abort_v = 1; break; }
@@ -360,7 +389,7 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                         const int t = kMmaT[q], u0 = kMmaU[q], c = kMmaC[q];
                         const bool first = (q == 0 || q == kMmaX) && (q < kMmaX ? resetX : resetY);
                         const uint64_t da = desc_kmajor(st + t * kSliceA, kSwizzleBytes);
-                        const uint64_t db = desc_kmajor(st + kSlices * kSliceA + u0 * kSliceB, kSwizzleBytes);
+                        const uint64_t db = desc_kmajor(st + NS * kSliceA + u0 * kSliceB, kSwizzleBytes);
                         const uint32_t dt = tmem + (uint32_t)((t + u0) * kTileN);
                         const uint32_t idesc = idesc_bf16(kTileM, kTileN * c);
 #pragma unroll
@@ -384,7 +413,7 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                     issue(kMmaX, kMmas);
                     w = wait_drain();
                     if (w) issue(0, kMmaX);
-                } else if (resetY) {                           // E6 .. E8 drained after the last block
+                } else if (resetY) {                           // E6 .. drained after the last block
                     issue(0, kMmaX);
                     w = wait_drain();
                     if (w) issue(kMmaX, kMmas);
@@ -587,12 +616,13 @@ __device__ __forceinline__ void digits_of(double x, int efm, __nv_bfloat16 (&out
 
 // Slices of A_hat into [kSlices][nbatch * rows_pad][K_pad] (K contiguous), zero in
 // the padding; batch z = blockIdx.z as in oz_exponents_kernel, at rows z * rows_pad.
+// Only the first nplanes planes are written (the five-slice steps read no others).
 // 32 x 32 tiles through shared memory so that reads and writes are both coalesced
 // when A_hat is the transpose of src.
 template <bool kTrans>
 __global__ void oz_slice_kernel(const double* __restrict__ src, int64_t ld, int64_t rows, int64_t Kb, int64_t Ktot,
                                 int64_t src_bstride, const int* __restrict__ exps, int64_t rows_pad, int64_t K_pad,
-                                size_t plane, __nv_bfloat16* __restrict__ slices) {
+                                size_t plane, int nplanes, __nv_bfloat16* __restrict__ slices) {
     __shared__ double tile[32][33];
     const int64_t z = blockIdx.z;
     src += z * src_bstride;
@@ -625,7 +655,8 @@ __global__ void oz_slice_kernel(const double* __restrict__ src, int64_t ld, int6
             __nv_bfloat16 dg[kSlices];
             digits_of(tile[tx][i], efm, dg);
 #pragma unroll
-            for (int t = 0; t < kSlices; t++) slices[t * plane + (size_t)r * K_pad + k] = dg[t];
+            for (int t = 0; t < kSlices; t++)
+                if (t < nplanes) slices[t * plane + (size_t)r * K_pad + k] = dg[t];
         }
     }
 }
@@ -679,9 +710,9 @@ void oz_operand_layout(Ar& ar, int64_t rows, int64_t K, int nbatch, int64_t row_
 }
 
 // Exponents and slices of an operand; batch b reads src + b * src_bstride over
-// min(o.K, Ktot - b o.K) of the K dimension.
+// min(o.K, Ktot - b o.K) of the K dimension.  nplanes: slice planes written.
 int oz_prepare(const double* src, int64_t ld, bool trans, const OzOperand& o, int64_t Ktot, int64_t src_bstride,
-               unsigned* status, cudaStream_t s) {
+               unsigned* status, cudaStream_t s, int nplanes = kSlices) {
     CHFSI_CUDA_TRY(cudaMemsetAsync(o.exps, 0, sizeof(int) * (size_t)o.plane_rows(), s));
     if (trans) {
         dim3 grid((unsigned)((o.rows + 255) / 256), (unsigned)((o.K + 255) / 256), (unsigned)o.nbatch);
@@ -697,10 +728,10 @@ int oz_prepare(const double* src, int64_t ld, bool trans, const OzOperand& o, in
     const size_t plane = (size_t)o.plane_rows() * o.K_pad;
     if (trans)
         oz_slice_kernel<true><<<grid, dim3(32, 8), 0, s>>>(src, ld, o.rows, o.K, Ktot, src_bstride, o.exps, o.rows_pad,
-                                                          o.K_pad, plane, o.slices);
+                                                          o.K_pad, plane, nplanes, o.slices);
     else
         oz_slice_kernel<false><<<grid, dim3(32, 8), 0, s>>>(src, ld, o.rows, o.K, Ktot, src_bstride, o.exps,
-                                                           o.rows_pad, o.K_pad, plane, o.slices);
+                                                           o.rows_pad, o.K_pad, plane, nplanes, o.slices);
     CHFSI_LAUNCH_CHECK();
     return CHFSI_OK;
 }
@@ -746,19 +777,26 @@ int launch_oz(const CUtensorMap& tmA, const CUtensorMap& tmB, const OzArgs& g, i
     if (total <= 0) return CHFSI_OK;
     const int dev = current_device();
     if (dev < 0) return CHFSI_ERR_CUDA;
+    if (g.slices != 7 && !(g.slices == 5 && g.bsr)) return CHFSI_ERR_ARG;
     static bool attr[kMaxDevices] = {};
     if (!attr[dev]) {
-        CHFSI_CUDA_TRY(
-            cudaFuncSetAttribute(oz_gemm_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
-        CHFSI_CUDA_TRY(
-            cudaFuncSetAttribute(oz_gemm_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
+        CHFSI_CUDA_TRY(cudaFuncSetAttribute(oz_gemm_kernel<false, 7>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            OzShape<7>::kSmemBytes));
+        CHFSI_CUDA_TRY(cudaFuncSetAttribute(oz_gemm_kernel<true, 7>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            OzShape<7>::kSmemBytes));
+        CHFSI_CUDA_TRY(cudaFuncSetAttribute(oz_gemm_kernel<true, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            OzShape<5>::kSmemBytes));
         attr[dev] = true;
     }
     const int sms = sm_count();
     if (sms <= 0) return CHFSI_ERR_CUDA;
     const unsigned grid = (unsigned)(total < sms ? total : sms);
-    if (g.bsr) oz_gemm_kernel<true><<<grid, kThreads, kSmemBytes, s>>>(tmA, tmB, g, total);
-    else oz_gemm_kernel<false><<<grid, kThreads, kSmemBytes, s>>>(tmA, tmB, g, total);
+    if (g.bsr && g.slices == 5)
+        oz_gemm_kernel<true, 5><<<grid, kThreads, OzShape<5>::kSmemBytes, s>>>(tmA, tmB, g, total);
+    else if (g.bsr)
+        oz_gemm_kernel<true, 7><<<grid, kThreads, OzShape<7>::kSmemBytes, s>>>(tmA, tmB, g, total);
+    else
+        oz_gemm_kernel<false, 7><<<grid, kThreads, OzShape<7>::kSmemBytes, s>>>(tmA, tmB, g, total);
     CHFSI_LAUNCH_CHECK();
     return CHFSI_OK;
 }
@@ -806,6 +844,7 @@ int oz_run(const OzPlan& p, bool tn_form, double* C, int64_t ldc, int64_t M, int
     g.splits = (g.kb_total + g.kb_split - 1) / g.kb_split;   // no empty split
     g.symmetric = symmetric ? 1 : 0;
     g.b_upper = b_upper ? 1 : 0;
+    g.slices = kSlices;
     g.wait_ns = pipeline_wait_ns();
     g.status = status;
     g.C = tn_form ? nullptr : C;
@@ -912,14 +951,16 @@ int ozaki_bsr_prepare(const BsrDev& h, int64_t n, void* ws, size_t ws_bytes, uns
     CHFSI_LAUNCH_CHECK();
     dim3 grid((unsigned)(b.H.K_pad / 32), (unsigned)std::min<int64_t>(b.H.rows_pad / 32, 65535), 1);
     oz_slice_kernel<false><<<grid, dim3(32, 8), 0, s>>>(val, 64, h.nblocks * 64, 64, 64, 0, b.H.exps, b.H.rows_pad,
-                                                       b.H.K_pad, (size_t)b.H.plane_rows() * b.H.K_pad, b.H.slices);
+                                                       b.H.K_pad, (size_t)b.H.plane_rows() * b.H.K_pad, kSlices,
+                                                       b.H.slices);
     CHFSI_LAUNCH_CHECK();
     return CHFSI_OK;
 }
 
 int ozaki_bsr_step(const BsrDev& h, int64_t n, const double* Yc, int64_t ldc, const double* Yp, int64_t ldp,
                    double* Yo, int64_t ldo, double alpha, double c, double beta, void* ws, size_t ws_bytes,
-                   unsigned* status, cudaStream_t s) {
+                   unsigned* status, cudaStream_t s, int slices) {
+    if (slices != 7 && slices != 5) return CHFSI_ERR_ARG;
     if (n <= 0 || h.nbr <= 0) return CHFSI_OK;
     if (ws_bytes < ozaki_bsr_bytes(h.nbr, h.nblocks, n)) return CHFSI_ERR_NOMEM;
     Arena ar(ws, ws_bytes);
@@ -927,7 +968,7 @@ int ozaki_bsr_step(const BsrDev& h, int64_t n, const double* Yc, int64_t ldc, co
     oz_bsr_layout(ar, h.nbr, h.nblocks, n, &b);
     const int64_t N = h.nbr * 64;
     int rc;
-    if ((rc = oz_prepare(Yc, ldc, true, b.Y, N, 0, status, s))) return rc;
+    if ((rc = oz_prepare(Yc, ldc, true, b.Y, N, 0, status, s, slices))) return rc;
     CUtensorMap tmA, tmB;
     if ((rc = make_map_bf16(&tmA, b.Y.slices, b.Y.K_pad, kSlices * b.Y.plane_rows(), kKB, kTileM,
                             kTmaSwizzle)))
@@ -956,6 +997,7 @@ int ozaki_bsr_step(const BsrDev& h, int64_t n, const double* Yc, int64_t ldc, co
     g.wait_ns = pipeline_wait_ns();
     g.status = status;
     g.bsr = 1;
+    g.slices = slices;
     g.brow_ptr = h.brow_ptr;
     g.bcol = h.bcol;
     g.nbr = h.nbr;

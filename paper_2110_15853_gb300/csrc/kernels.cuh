@@ -162,11 +162,13 @@ int ozaki_gemm_nn(const double* A, int64_t lda, const double* B, int64_t ldb, in
 // cores: Y_out = alpha (H Y_cur - c Y_cur) - beta Y_prev (Y_prev may be null), FP64
 // iterates.  ozaki_bsr_prepare slices H once (rows of at most 128 blocks);
 // ozaki_bsr_step slices Y_cur and runs the step.  Both use one workspace (ozaki_bsr_bytes).
+// slices = 7: FP64-accurate; slices = 5: the 40-bit step (five digits per operand, the
+// 15 slice pairs of weight 2^-48 and above).
 size_t ozaki_bsr_bytes(int64_t nbr, int64_t nblocks, int64_t n);
 int ozaki_bsr_prepare(const BsrDev& h, int64_t n, void* ws, size_t ws_bytes, unsigned* status, cudaStream_t s);
 int ozaki_bsr_step(const BsrDev& h, int64_t n, const double* Yc, int64_t ldc, const double* Yp, int64_t ldp,
                    double* Yo, int64_t ldo, double alpha, double c, double beta, void* ws, size_t ws_bytes,
-                   unsigned* status, cudaStream_t s);
+                   unsigned* status, cudaStream_t s, int slices = 7);
 size_t ozaki_blockdiag_bytes(int64_t N, int B, int64_t n);
 int ozaki_blockdiag_prepare(const double* diag, int64_t N, int B, int64_t n, void* ws, size_t ws_bytes,
                             unsigned* status, cudaStream_t s);
