@@ -116,13 +116,66 @@ struct OzShape {
 // each group has t = 0 and covers all of the group's accumulators.
 // With five slices the 15 pairs with t + u <= 4 take the same 4 MMAs for group X and
 // one MMA per pair of level 6 (accumulator 4, E6) for group Y: 9 per K-step.
+// MMA q takes slice mma_t(q) of A and the mma_c(q) slices of B from mma_u(q) on:
+//   seven slices: t = {0,1,2,3, 0,1,2,3,4,5,6}, u = {0,0,0,0, 4,3,2,1,0,0,0},
+//                 c = {4,3,2,1, 3,3,3,3,3,2,1};
+//   five slices:  t = {0,1,2,3, 0,1,2,3,4},     u = {0,0,0,0, 4,3,2,1,0},
+//                 c = {4,3,2,1, 1,1,1,1,1}.
+// Compile-time functions of q, so that the unrolled issue sequence folds them into
+// immediate descriptor offsets (one thread issues every MMA; table loads and
+// descriptor rebuilds per MMA made that thread the pace of the pipeline).
 constexpr int kMmaX = 4;
-__constant__ int8_t kMmaT7[11] = {0, 1, 2, 3, 0, 1, 2, 3, 4, 5, 6};
-__constant__ int8_t kMmaU7[11] = {0, 0, 0, 0, 4, 3, 2, 1, 0, 0, 0};
-__constant__ int8_t kMmaC7[11] = {4, 3, 2, 1, 3, 3, 3, 3, 3, 2, 1};
-__constant__ int8_t kMmaT5[9] = {0, 1, 2, 3, 0, 1, 2, 3, 4};
-__constant__ int8_t kMmaU5[9] = {0, 0, 0, 0, 4, 3, 2, 1, 0};
-__constant__ int8_t kMmaC5[9] = {4, 3, 2, 1, 1, 1, 1, 1, 1};
+__host__ __device__ constexpr int mma_t(int q) { return q < kMmaX ? q : q - kMmaX; }
+__host__ __device__ constexpr int mma_u(int q) { return q < kMmaX ? 0 : (q <= 2 * kMmaX ? 2 * kMmaX - q : 0); }
+template <int NS>
+__host__ __device__ constexpr int mma_c(int q) {
+    return q < kMmaX ? kMmaX - q : (NS == 5 ? 1 : (11 - q < 3 ? 11 - q : 3));
+}
+// Every pair (t, u) with t + u <= NS - 1 exactly once, accumulator t + u.
+template <int NS>
+constexpr bool mma_covers_pairs(int nmmas) {
+    int seen[7][7] = {};
+    for (int q = 0; q < nmmas; q++)
+        for (int j = 0; j < mma_c<NS>(q); j++) {
+            const int t = mma_t(q), u = mma_u(q) + j;
+            if (t >= NS || u >= NS || t + u > NS - 1) return false;
+            if ((q < kMmaX) != (t + u < kMmaX)) return false;   // groups X (E2 .. E5) and Y
+            seen[t][u]++;
+        }
+    for (int t = 0; t < NS; t++)
+        for (int u = 0; u < NS; u++)
+            if (seen[t][u] != (t + u <= NS - 1 ? 1 : 0)) return false;
+    return true;
+}
+static_assert(mma_covers_pairs<7>(11) && mma_covers_pairs<5>(9), "slice-pair tables");
+static_assert(mma_t(10) == 6 && mma_u(9) == 0 && mma_c<7>(9) == 2 && mma_c<7>(8) == 3, "seven-slice table");
+
+// The MMAs Q0 .. Q1 - 1 of one stage: A slices from descriptor da0, B slices from db0
+// (descriptors of the stage's first A and first B tile; a tile's start address is
+// da0 + offset / 16, which stays inside the 14-bit field below 256 KB).  The first MMA
+// of a group (q = 0 for X, q = kMmaX for Y) covers all of the group's accumulators and
+// overwrites them when the group starts fresh.
+template <int NS, int Q0, int Q1>
+__device__ __forceinline__ void issue_mmas(uint64_t da0, uint64_t db0, uint32_t tmem, bool freshX, bool freshY) {
+#pragma unroll
+    for (int q = Q0; q < Q1; q++) {
+        const int t = mma_t(q), u0 = mma_u(q), c = mma_c<NS>(q);
+        const bool fresh = (q == 0 && freshX) || (q == kMmaX && freshY);
+        const uint64_t da = da0 + (uint64_t)((t * kSliceA) >> 4);
+        const uint64_t db = db0 + (uint64_t)((u0 * kSliceB) >> 4);
+        const uint32_t dt = tmem + (uint32_t)((t + u0) * kTileN);
+        constexpr uint32_t kIdesc1 = idesc_bf16(kTileM, kTileN);
+        const uint32_t idesc = kIdesc1 + (uint32_t)(((kTileN * (c - 1)) >> 3) << 17);
+#pragma unroll
+        for (int k = 0; k < kKB / 16; k++) {
+            const uint32_t accumulate = (fresh && k == 0) ? 0u : 1u;
+            asm volatile(
+                "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n"
+                :: "r"(dt), "l"(da + 2 * k), "l"(db + 2 * k), "r"(idesc), "r"(accumulate));
+        }
+    }
+}
 
 // The drain after K-block kb of an item of KB blocks: 0 none, kXEvent (E2 .. E5),
 // kYEvent (E6 .. E8) or kFullEvent (all seven, then the output).
@@ -277,9 +330,6 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                int64_t total) {
     using Sh = OzShape<NS>;
     constexpr int kStages = Sh::kStages, kStageBytes = Sh::kStageBytes, kMmas = Sh::kMmas, kAccs = Sh::kAccs;
-    const int8_t* kMmaT = NS == 7 ? kMmaT7 : kMmaT5;
-    const int8_t* kMmaU = NS == 7 ? kMmaU7 : kMmaU5;
-    const int8_t* kMmaC = NS == 7 ? kMmaC7 : kMmaC5;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     __shared__ __align__(8) uint64_t full[kMaxStages], empty[kMaxStages], efull, eempty, done;
@@ -379,47 +429,27 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                     asm volatile("tcgen05.fence::after_thread_sync;");
                     return w;
                 };
-                // MMA q multiplies slice kMmaT[q] of A by the kMmaC[q] slices of B from
-                // kMmaU[q] on, stacked along N (consecutive in shared memory), into the
-                // accumulators kMmaT + kMmaU .. (consecutive TMEM columns); the first MMA
-                // of each group covers all of the group's accumulators, so it overwrites
-                // them when the group starts fresh
-                auto issue = [&](int q0, int q1) {
-                    for (int q = q0; q < q1; q++) {
-                        const int t = kMmaT[q], u0 = kMmaU[q], c = kMmaC[q];
-                        const bool first = (q == 0 || q == kMmaX) && (q < kMmaX ? resetX : resetY);
-                        const uint64_t da = desc_kmajor(st + t * kSliceA, kSwizzleBytes);
-                        const uint64_t db = desc_kmajor(st + NS * kSliceA + u0 * kSliceB, kSwizzleBytes);
-                        const uint32_t dt = tmem + (uint32_t)((t + u0) * kTileN);
-                        const uint32_t idesc = idesc_bf16(kTileM, kTileN * c);
-#pragma unroll
-                        for (int k = 0; k < kKB / 16; k++) {
-                            const uint32_t accumulate = (first && k == 0) ? 0u : 1u;
-                            asm volatile(
-                                "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n"
-                                :: "r"(dt), "l"(da + 2 * k), "l"(db + 2 * k), "r"(idesc), "r"(accumulate));
-                        }
-                    }
-                    issued = true;
-                };
+                // descriptors of the stage's first A and first B slice tile
+                const uint64_t da0 = desc_kmajor(st, kSwizzleBytes);
+                const uint64_t db0 = desc_kmajor(st + NS * kSliceA, kSwizzleBytes);
                 // after a drain wait that gave up, nothing more is issued into the
                 // accumulators that the epilogue may still be reading
                 bool w = true;
                 if (kb == 0) {
                     if (ev_commit > 0) w = wait_drain();     // the previous item's output drain
-                    if (w) issue(0, kMmas);
+                    if (w) issue_mmas<NS, 0, kMmas>(da0, db0, tmem, resetX, resetY);
                 } else if (resetX) {                           // E2 .. E5 drained after the last block
-                    issue(kMmaX, kMmas);
+                    issue_mmas<NS, kMmaX, kMmas>(da0, db0, tmem, false, resetY);
                     w = wait_drain();
-                    if (w) issue(0, kMmaX);
+                    if (w) issue_mmas<NS, 0, kMmaX>(da0, db0, tmem, true, false);
                 } else if (resetY) {                           // E6 .. drained after the last block
-                    issue(0, kMmaX);
+                    issue_mmas<NS, 0, kMmaX>(da0, db0, tmem, resetX, false);
                     w = wait_drain();
-                    if (w) issue(kMmaX, kMmas);
+                    if (w) issue_mmas<NS, kMmaX, kMmas>(da0, db0, tmem, false, true);
                 } else {
-                    issue(0, kMmas);
+                    issue_mmas<NS, 0, kMmas>(da0, db0, tmem, false, false);
                 }
+                issued = true;
                 umma_commit(&empty[s]);
                 if (!w) { ok = false; sc++; break; }
                 if (event_at(kb, it.KB)) {
