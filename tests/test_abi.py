@@ -163,3 +163,32 @@ def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(abi, "LIB_PATH", str(tmp_path / "missing.so"))
     with pytest.raises(ImportError):
         abi.load()
+
+
+def test_ozaki_schedules_validated_on_host(lib):
+    """Filter schedules with 40-bit Ozaki steps (CHFSI_F40_OZAKI): they join the Ozaki
+    tail in any order with FP64-accurate Ozaki steps, after an optional low-precision
+    prefix, and need the same workspace; they mix neither with plain FP64 steps nor with
+    a later low-precision step, and need 64 x 64 blocks."""
+    from paper_2110_15853_gb300 import _abi
+    F40, OZ, F64, F32 = _abi.CHFSI_F40_OZAKI, _abi.CHFSI_F64_OZAKI, _abi.CHFSI_F64, _abi.CHFSI_F32
+    b = _abi.chfsi_matrix()
+    b.kind = _abi.CHFSI_BSR
+    b.bsr = _abi.chfsi_bsr(16, 40, 64, 0x1000, 0x2000, 0x3000)    # N = 1024
+
+    def size(desc, steps):
+        prec = (ctypes.c_int32 * len(steps))(*steps)
+        sch = _abi.chfsi_schedule(len(steps), ctypes.cast(prec, ctypes.POINTER(ctypes.c_int32)))
+        sz = ctypes.c_size_t()
+        rc = lib.chfsi_filter_workspace_size(ctypes.byref(desc), 200, len(steps), ctypes.byref(sch),
+                                             ctypes.byref(sz))
+        return rc, sz.value
+
+    rc, full = size(b, [OZ] * 10)
+    assert rc == 0
+    for steps in ([F40] * 6 + [OZ] * 4, [F40] * 10, [OZ] * 5 + [F40] * 5, [OZ, F40] * 5):
+        assert size(b, steps) == (0, full)
+    assert size(b, [F32] * 3 + [F40] * 5 + [OZ] * 2)[0] == 0
+    for steps in ([F40] * 5 + [F64] * 5, [F64] * 5 + [F40] * 5, [F40] * 3 + [F32] * 7):
+        assert size(b, steps)[0] == _abi.CHFSI_ERR_ARG
+    assert size(_csr_desc(1000, 5000), [F40] * 4)[0] == _abi.CHFSI_ERR_UNSUPPORTED
