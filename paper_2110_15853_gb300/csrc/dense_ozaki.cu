@@ -37,16 +37,19 @@
 // of 28 and three operand stages instead of two.  The digits are the same as above,
 // so the same slices serve both step kinds.
 //
-// Kernel.  Persistent, warp-specialised, one CTA per SM, 128 x 64 output tiles:
-//   warp 0, lane 0 : TMA producer -- per K-block of 32, the seven A (128-row) and
-//                    seven B (64-row) slice tiles (64-byte swizzle) into a two-stage ring;
-//   warp 1         : owns 512 TMEM columns, seven 64-column FP32 accumulators E2 .. E8;
-//                    lane 0 issues the 28 x 2 MMAs (M = 128, N = 64, K = 16) per stage;
+// Kernel.  Persistent, warp-specialised, one CTA per SM, 128 x 64 output tiles; NS = 7
+// slices per operand (or 5 for the 40-bit filter steps):
+//   warp 0, lane 0 : TMA producer -- per K-block of 32, the NS A (128-row) and NS B
+//                    (64-row) slice tiles (64-byte swizzle) into a ring of two stages
+//                    (84 KB each) or, with five slices, three (60 KB each);
+//   warp 1         : owns 512 TMEM columns, NS 64-column FP32 accumulators E2 .. E_{NS+1};
+//                    lane 0 issues the slice-pair products of a stage as 11 (or 9) MMAs
+//                    of M = 128, N = 64 c (B slices stacked), K = 16, twice per K-block;
 //   warps 2-17     : epilogue; warp w reads TMEM lanes 32 (w % 4) .. + 31 (one output
 //                    row per thread), columns 16 ((w - 2) / 4) .. + 15, and keeps those
 //                    16 x 2 integers in registers.
 // Drains alternate between group X (E2 .. E5, after K-blocks 5, 13, 21, ...) and group
-// Y (E6 .. E8, after K-blocks 3, 7, 11, ...); the issuer runs the other group's MMAs of
+// Y (E6 .., after K-blocks 3, 7, 11, ...); the issuer runs the other group's MMAs of
 // the next stage before it waits for a drain.  Every mbarrier wait is bounded; on a
 // timeout the CTA flags DEV_TIMEOUT, stops, waits (bounded) for its copies and MMAs in
 // flight, frees TMEM and exits.
