@@ -181,7 +181,7 @@ __device__ __forceinline__ void issue_mmas(uint64_t da0, uint64_t db0, uint32_t 
 }
 
 // The drain after K-block kb of an item of KB blocks: 0 none, kXEvent (E2 .. E5),
-// kYEvent (E6 .. E8) or kFullEvent (all seven, then the output).
+// kYEvent (E6 ..) or kFullEvent (every accumulator, then the output).
 __device__ __forceinline__ int event_at(int kb, int KB) {
     if (kb == KB - 1) return kFullEvent;
     if (kb % kPeriodY == kPeriodY - 1) return kYEvent;
