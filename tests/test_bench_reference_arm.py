@@ -49,3 +49,26 @@ def test_bench_uses_only_exported_binding_names():
     src = open(os.path.join(ROOT, "bench.py")).read()
     names = set(re.findall(r"\bP\.([A-Za-z_]+)", src))
     assert names and not [n for n in names if not hasattr(P, n)]
+
+
+def test_flop_model_counts():
+    """The algorithmic FLOP counts behind `value` and the closure rate, counted again
+    product by product: one step 2 nnz n + 5 N n (3 N n for the first); CholQR2 with the
+    last pass's X_F folded away: two symmetric Grams (N n^2 each), one triangular
+    product (N n^2), the n^3 fold products (P R2^-1 and R2^-1 Q, n^3 each; the upper
+    triangle of R2^-T T, n^3 / 3), H X_F (2 nnz n), the symmetric projection (N n^2) and
+    the rotation (2 N n^2); the Ozaki schedules' slice products per element and state."""
+    sys.path.insert(0, ROOT)
+    import bench
+    nnz, N, n = 171879616, 262144, 6000
+    assert bench.filter_flops(nnz, N, n, 1) == 2 * nnz * n + 3 * N * n
+    assert bench.filter_flops(nnz, N, n, 30) == 30 * 2 * nnz * n + 3 * N * n + 29 * 5 * N * n
+    gram, tri, proj, rot = N * n * n, N * n * n, N * n * n, 2 * N * n * n
+    fold = n ** 3 + n ** 3 + n ** 3 / 3
+    assert abs(bench.closure_flops(nnz, N, n, 2) - (2 * gram + tri + fold + 2 * nnz * n + proj + rot)) < 1e-6 * gram
+    assert abs(bench.closure_flops(nnz, N, n, 1) - (gram + tri + 2 * nnz * n + proj + rot)) < 1e-6 * gram
+    s = bench.ozaki_schedules(30)
+    assert s["ozaki"] == ["ozaki"] * 30
+    assert s["ozaki40_prefix"] == ["ozaki40"] * 26 + ["ozaki"] * 4
+    assert bench.slice_products(s["ozaki"]) == 30 * 28
+    assert bench.slice_products(s["ozaki40_prefix"]) == 26 * 15 + 4 * 28
