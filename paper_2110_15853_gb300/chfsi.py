@@ -268,7 +268,13 @@ def filter_workspace_bytes(H, n_cols: int, m: int, schedule=None) -> int:
 
 def filter(H, X: torch.Tensor, m: int, a: float, b: float, a0: float, schedule=None,
            out: Optional[torch.Tensor] = None, workspace: Optional[Workspace] = None) -> torch.Tensor:
-    """Y_m of the scaled Chebyshev filter (Algorithm 1 step 1) on the GPU."""
+    """Y_m of the scaled Chebyshev filter (Algorithm 1 step 1) on the GPU.
+
+    schedule: None (every step FP64) or one precision per step, by name or code:
+    "f64"; "f32", "bf16", "f32x2" (a leading low-precision prefix of one kind); "ozaki"
+    (FP64-accurate products on the tensor cores) and "ozaki40" (40-bit Ozaki products),
+    in any order after the prefix, for operators with 64 x 64 blocks (BsrMatrix or
+    HybridMatrix).  The rules are chfsi_filter's (include/chfsi.h)."""
     _check_block(X, "X")
     N, n = X.shape
     if out is None:
