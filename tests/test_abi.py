@@ -38,6 +38,17 @@ def test_every_declared_symbol_is_exported(lib):
         assert name in _abi.SIGNATURES, f"{name} has no ctypes signature"
 
 
+def test_binding_constants_match_the_header():
+    """Every integer #define CHFSI_* of include/chfsi.h has the same value in the
+    binding (status codes, layouts, precisions, product flags)."""
+    from paper_2110_15853_gb300 import _abi
+    text = open(os.path.join(ROOT, "include", "chfsi.h")).read()
+    defs = dict(re.findall(r"^#define (CHFSI_[A-Z0-9_]+) (\d+)", text, flags=re.M))
+    assert len(defs) >= 24 and "CHFSI_F40_OZAKI" in defs
+    for name, value in defs.items():
+        assert getattr(_abi, name) == int(value), name
+
+
 def test_status_strings(lib):
     assert lib.chfsi_version() >= 10000
     for code in range(10):
